@@ -1,0 +1,203 @@
+/*
+ * gsnfs.h -- C ABI of the GB300 (sm_103a) implementation of the GS-NFS
+ * per-frame codec hot path (arxiv 2606.05650): octree geometry coding of
+ * voxelised Gaussian positions and RAHT attribute coding with quantisation
+ * and entropy coding, plus the matching decoder.
+ *
+ * Conventions for every entry point
+ *   - Pointers named d_* are DEVICE memory owned by the caller; h_* are host
+ *     memory owned by the caller.  The library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Work is enqueued in stream order.  Calls that return
+ *     host scalars (out_* pointers) synchronise `stream` once before
+ *     returning; everything else returns after enqueueing.
+ *   - A gsnfs_ctx owns the device scratch for one stream at a time; calls on
+ *     one context must not overlap (use one context per concurrent stream).
+ *   - No exception crosses the ABI.  Errors are negative gsnfs_status
+ *     values; gsnfs_status_string() names them.  Decoders validate stream
+ *     headers on the host and check every device read of a stream against
+ *     its length; a malformed stream yields GSNFS_ERR_CORRUPT, never a trap.
+ *   - Arrays of points are row-major: positions N x 3 float32, attributes
+ *     N x C float32.  Decoded voxels are in ascending Morton order.
+ *   - The bitstream layout is this library's own (the paper fixes only the
+ *     octree header); it is described beside the implementation.
+ */
+#ifndef GSNFS_H
+#define GSNFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gsnfs_ctx gsnfs_ctx;
+typedef struct gsnfs_raht_plan gsnfs_raht_plan;
+
+typedef enum {
+    GSNFS_OK = 0,
+    GSNFS_ERR_INVALID_ARG = -1, /* bad argument: depth, sizes, steps, pointers */
+    GSNFS_ERR_CAPACITY = -2,    /* output buffer too small; required size reported */
+    GSNFS_ERR_CORRUPT = -3,     /* malformed bitstream */
+    GSNFS_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+    GSNFS_ERR_TIMEOUT = -5,     /* a bounded device wait expired */
+    GSNFS_ERR_OOM = -6,         /* device allocation failed */
+    GSNFS_ERR_UNSUPPORTED = -7  /* valid request outside what this build supports */
+} gsnfs_status;
+
+/* Quantisation and entropy-coder parameters (Sec. 3.4).
+ * Attribute channels are split into groups, one quantisation step per group
+ * (coefficients of different attributes are quantised to different levels).
+ * q = sign(y) floor(|y| / step + tau); tau = 0.5 is the uniform mid-tread
+ * quantiser, smaller tau widens the dead zone.  Coefficients of a channel
+ * are RLGR-coded in blocks of rlgr_block (Sec. 3.4, Table A.5). */
+typedef struct {
+    uint32_t num_channels;         /* C, 0..256 (0 = geometry only) */
+    uint32_t num_groups;           /* G, 1..255 when C > 0 */
+    const uint8_t *channel_group;  /* host, length C, values < G */
+    const double *steps;           /* host, length G, each > 0 */
+    double tau;                    /* rounding offset in (0, 0.5] */
+    uint32_t rlgr_block;           /* B: power of two in [32, 65536] */
+    uint32_t rans_chunk;           /* occupancy symbols per rANS chunk: multiple of 32 in [32, 1<<20] */
+} gsnfs_quant;
+
+/* Creates a context on CUDA device `cuda_device` (made current for the
+ * call).  Returns GSNFS_OK and *out, or GSNFS_ERR_CUDA / GSNFS_ERR_OOM. */
+gsnfs_status gsnfs_create(gsnfs_ctx **out, int cuda_device);
+
+/* Frees the context and its scratch (synchronises the device first). */
+void gsnfs_destroy(gsnfs_ctx *ctx);
+
+/* Static description of a status code. */
+const char *gsnfs_status_string(gsnfs_status s);
+
+/* Grows the context's scratch so that frames of up to n points with C
+ * channels at depth J encode and decode without further allocation (call
+ * before capturing the codec into a CUDA graph). */
+gsnfs_status gsnfs_reserve(gsnfs_ctx *ctx, uint64_t n, uint32_t C, uint32_t J, const gsnfs_quant *q);
+
+/* Upper bound of the encoded size of a frame of n points (host only). */
+gsnfs_status gsnfs_max_bitstream_bytes(uint64_t n, uint32_t J, const gsnfs_quant *q, uint64_t *out);
+
+/* Encodes one frame (Sec. 2, Sec. 3; Algorithm 1 for geometry, Algorithms
+ * 4-6 and Sec. 3.4 for attributes):
+ *   voxelise to a 2^J grid over the bounding cube, Morton-code, radix-sort,
+ *   merge Gaussians sharing a voxel by averaging, emit the octree header and
+ *   breadth-first occupancy bytes (rANS coded), RAHT-transform the merged
+ *   attributes over all 3J binary levels, quantise per group and RLGR-code
+ *   each channel in blocks.
+ * d_pos: N x 3 float32; d_attr: N x C float32 (may be NULL when C == 0);
+ * n may be 0 (valid empty stream); J in 1..21.
+ * d_bitstream receives the stream; on GSNFS_ERR_CAPACITY *out_bytes holds
+ * the required size and nothing beyond `capacity` is written.
+ * Optional reconstruction (the decoder's output, computed inside the
+ * encoder): d_recon_pos (N_v x 3) and d_recon_attr (N_v x C), each may be
+ * NULL; they must hold N_v <= n rows.  *out_nv receives N_v. */
+gsnfs_status gsnfs_encode_frame(gsnfs_ctx *ctx, void *stream, const float *d_pos, const float *d_attr,
+                                uint64_t n, uint32_t J, const gsnfs_quant *q, uint8_t *d_bitstream,
+                                uint64_t capacity, uint64_t *out_bytes, float *d_recon_pos,
+                                float *d_recon_attr, uint64_t *out_nv);
+
+/* Reads the fixed header of a stream held in HOST memory (>= 96 bytes):
+ * number of voxels, channels and depth. */
+gsnfs_status gsnfs_peek_frame(const uint8_t *h_header, uint64_t bytes, uint64_t *out_nv, uint32_t *out_C,
+                              uint32_t *out_J);
+
+/* Decodes one frame (Sec. 2.3, Algorithms 2-3; inverse of Algorithm 6):
+ * occupancy rANS decode, level-synchronous octree expansion, voxel centres,
+ * RLGR decode and dequantisation, inverse RAHT.  d_bitstream (device) holds
+ * `bytes` bytes.  d_pos receives N_v x 3 float32 voxel centres, d_attr
+ * N_v x C float32 attributes (either may be NULL); capacity_nv is the row
+ * capacity of both.  *out_nv receives N_v. */
+gsnfs_status gsnfs_decode_frame(gsnfs_ctx *ctx, void *stream, const uint8_t *d_bitstream, uint64_t bytes,
+                                float *d_pos, float *d_attr, uint64_t capacity_nv, uint64_t *out_nv);
+
+/* Batched bandwidth ladder (frames x rungs): encodes `frames` frames, frame f
+ * with n[f] points at depth J[f] (16..19 supported together, any mix),
+ * each at `rungs` quantisation rungs whose steps are q->steps scaled by
+ * rung_scale[r].  Geometry and RAHT run once per frame; quantisation and
+ * RLGR run per rung.  Stream (f, r) is written to
+ * d_out[h_offsets[f*rungs + r] .. h_offsets[f*rungs + r + 1]).
+ * h_pos/h_attr are host arrays of `frames` device pointers; h_n, h_J host
+ * arrays of length `frames`; h_offsets (host) has frames*rungs + 1 entries.
+ * frames <= 64, rungs <= 8. */
+gsnfs_status gsnfs_encode_batch(gsnfs_ctx *ctx, void *stream, uint32_t frames, const float *const *h_pos,
+                                const float *const *h_attr, const uint64_t *h_n, const uint32_t *h_J,
+                                uint32_t rungs, const double *h_rung_scale, const gsnfs_quant *q,
+                                uint8_t *d_out, uint64_t capacity, uint64_t *h_offsets);
+
+/* Batched decoder: decodes `frames` streams; stream f lives at
+ * d_in + h_in_offsets[f] with h_in_offsets[f+1] - h_in_offsets[f] bytes.
+ * Voxels of frame f are written to rows h_out_rows[f] .. of d_pos / d_attr
+ * (host array of frames + 1 row offsets, filled by this call; capacity_rows
+ * bounds the total). */
+gsnfs_status gsnfs_decode_batch(gsnfs_ctx *ctx, void *stream, uint32_t frames, const uint8_t *d_in,
+                                const uint64_t *h_in_offsets, float *d_pos, float *d_attr,
+                                uint64_t capacity_rows, uint64_t *h_out_rows);
+
+/* ---- stage entry points (each is one step of the path above) ---------- */
+
+/* Voxelisation and Morton coding (Sec. 2.1, Sec. 2.2): the distinct voxel
+ * codes in ascending order (d_codes, n entries of capacity) and the grid
+ * (h_grid[0..3] = lo_x, lo_y, lo_z, ext as float64).  *out_nv receives N_v. */
+gsnfs_status gsnfs_voxelize(gsnfs_ctx *ctx, void *stream, const float *d_pos, uint64_t n, uint32_t J,
+                            uint64_t *d_codes, double *h_grid, uint64_t *out_nv);
+
+/* Octree occupancy bytes (Algorithm 1) of nv distinct ascending Morton codes
+ * at depth J: d_occ receives sum_{d<J} |L_d| bytes in breadth-first order
+ * (capacity occ_capacity), h_level_sizes (J+1 entries) the header. */
+gsnfs_status gsnfs_octree_encode(gsnfs_ctx *ctx, void *stream, const uint64_t *d_codes, uint64_t nv,
+                                 uint32_t J, uint8_t *d_occ, uint64_t occ_capacity, uint32_t *h_level_sizes,
+                                 uint64_t *out_occ_bytes);
+
+/* Octree decoding (Sec. 2.3, Algorithms 2-3): ascending leaf codes from
+ * occupancy bytes and the header.  Returns GSNFS_ERR_CORRUPT when the bytes
+ * contradict the level sizes. */
+gsnfs_status gsnfs_octree_decode(gsnfs_ctx *ctx, void *stream, const uint8_t *d_occ, uint64_t occ_bytes,
+                                 uint32_t J, const uint32_t *h_level_sizes, uint64_t *d_codes);
+
+/* Occupancy entropy stage (Sec. 2.2 last paragraph; own rANS): codes n
+ * bytes into an occupancy section (d_out, capacity) / decodes a section. */
+gsnfs_status gsnfs_occupancy_section_encode(gsnfs_ctx *ctx, void *stream, const uint8_t *d_in, uint64_t n,
+                                            uint32_t rans_chunk, uint8_t *d_out, uint64_t capacity,
+                                            uint64_t *out_bytes);
+gsnfs_status gsnfs_occupancy_section_decode(gsnfs_ctx *ctx, void *stream, const uint8_t *d_sec,
+                                            uint64_t sec_bytes, uint8_t *d_out, uint64_t n);
+
+/* RAHT plan (Sec. 3.2 prelude, Algorithms 4-5): the butterfly schedule of nv
+ * distinct ascending Morton codes at depth J for C channels.  The plan owns
+ * its device memory; it is bound to the context's device. */
+gsnfs_status gsnfs_raht_plan_create(gsnfs_ctx *ctx, void *stream, const uint64_t *d_codes, uint64_t nv,
+                                    uint32_t J, uint32_t C, gsnfs_raht_plan **out);
+void gsnfs_raht_plan_destroy(gsnfs_raht_plan *plan);
+
+/* RAHT forward (Eq. 1, Algorithm 6 bottom-up over all 3J levels):
+ * d_in (nv x C, Morton order) -> d_out (nv x C coefficients in place
+ * layout: DC at row 0, each high pass at its right sibling's first row).
+ * d_in and d_out may alias. */
+gsnfs_status gsnfs_raht_forward(gsnfs_raht_plan *plan, void *stream, const float *d_in, float *d_out);
+
+/* RAHT inverse (Algorithm 6 top-down, transposed rotations).  When
+ * q != NULL each coefficient is first quantised and dequantised with q
+ * (the encoder's reconstruction).  d_in and d_out may alias. */
+gsnfs_status gsnfs_raht_inverse(gsnfs_raht_plan *plan, void *stream, const float *d_in, float *d_out,
+                                const gsnfs_quant *q);
+
+/* Block RLGR of int32 quantisation indices (Sec. 3.4): d_q is nv x C
+ * row-major; each channel is cut into blocks of B coefficients and block
+ * (c, b) (nb = ceil(nv / B) blocks per channel) is one RLGR stream written at
+ * d_slots + (c * nb + b) * gsnfs_rlgr_slot_words(B); d_block_words[c*nb+b]
+ * receives its length in 32-bit words.  Decoding reads the same layout and
+ * writes d_q (GSNFS_ERR_CORRUPT on a malformed block). */
+uint32_t gsnfs_rlgr_slot_words(uint32_t B);
+gsnfs_status gsnfs_rlgr_encode_indices(gsnfs_ctx *ctx, void *stream, const int32_t *d_q, uint64_t nv, uint32_t C,
+                                       uint32_t B, uint32_t *d_slots, uint32_t *d_block_words);
+gsnfs_status gsnfs_rlgr_decode_indices(gsnfs_ctx *ctx, void *stream, const uint32_t *d_slots,
+                                       const uint32_t *d_block_words, uint64_t nv, uint32_t C, uint32_t B,
+                                       int32_t *d_q);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSNFS_H */

@@ -1,0 +1,1540 @@
+// C ABI of the GS-NFS GB300 codec: context and scratch arena, stream-ordered
+// orchestration of the encode / decode kernels, and the bitstream container
+// (header of Algorithm 1 plus this codec's own section layout).
+//
+// Container (little endian, every section 8-aligned):
+//   header 96 B: u32 magic "GSN1", u32 version 1, u32 header_bytes, u32 J,
+//     u32 C, u32 G, u64 N_v, f64 lo[3], f64 ext, f64 tau,
+//     u64 occupancy_section_bytes, u64 attribute_section_bytes, u32 flags,
+//     u32 reserved; then u32 level_size[J+1], u8 group[C], pad to 8,
+//     f64 step[G].
+//   occupancy section: u64 n_occ, u32 mode, u32 aux; mode 0 raw bytes,
+//     mode 2 one constant byte (aux), mode 1 rANS: aux = chunks, u32 chunk
+//     symbols, u32 0, u16 freq[256], u32 chunk_bytes[], pad 8, chunks
+//     (32 u32 states + u16 words, padded to 4); rANS only when smaller.
+//   attribute section (C > 0 and N_v > 0): u32 B, u32 nb, u32
+//     block_words[C*nb] (channel-major), payload words, pad 8.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/gsnfs.h"
+#include "kernels.cuh"
+
+using namespace gsnfs;
+
+struct gsnfs_ctx {
+    int device = 0;
+    int num_sms = 0;
+    void *arena = nullptr;
+    size_t arena_cap = 0;
+    unsigned char *pinned = nullptr;
+    size_t pinned_cap = 0;
+    DevState *st = nullptr;
+};
+
+struct gsnfs_raht_plan {
+    gsnfs_ctx *ctx = nullptr;
+    void *mem = nullptr;
+    RahtPlanDev dev{};
+    float *pool = nullptr;
+    float *qparams = nullptr;  // inv_step[C], step[C]
+    DevState *st = nullptr;
+    uint64_t nv = 0;
+    uint32_t C = 0, J = 0;
+};
+
+namespace {
+
+const uint32_t kMagic = 0x314E5347u;
+thread_local char g_last_error[256];
+
+#define CK(x)                                                                          \
+    do {                                                                               \
+        cudaError_t e_ = (x);                                                          \
+        if (e_ != cudaSuccess) {                                                       \
+            snprintf(g_last_error, sizeof(g_last_error), "%s: %s", #x, cudaGetErrorString(e_)); \
+            return e_ == cudaErrorMemoryAllocation ? GSNFS_ERR_OOM : GSNFS_ERR_CUDA;   \
+        }                                                                              \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d)
+    {
+        cudaGetDevice(&prev);
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Sub-allocator over one buffer: the first pass (base == nullptr) measures.
+struct Carve {
+    unsigned char *base;
+    size_t off = 0;
+    explicit Carve(void *b) : base((unsigned char *)b) {}
+    template <typename T>
+    T *take(uint64_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += (size_t)count * sizeof(T) + 16;
+        return p;
+    }
+};
+
+gsnfs_status grow_arena(gsnfs_ctx *ctx, size_t need, cudaStream_t s)
+{
+    if (need <= ctx->arena_cap) return GSNFS_OK;
+    CK(cudaStreamSynchronize(s));
+    if (ctx->arena) CK(cudaFree(ctx->arena));
+    ctx->arena = nullptr;
+    ctx->arena_cap = 0;
+    size_t cap = need + need / 8 + (64 << 20);
+    CK(cudaMalloc(&ctx->arena, cap));
+    ctx->arena_cap = cap;
+    return GSNFS_OK;
+}
+
+gsnfs_status grow_pinned(gsnfs_ctx *ctx, size_t need)
+{
+    if (need <= ctx->pinned_cap) return GSNFS_OK;
+    if (ctx->pinned) CK(cudaFreeHost(ctx->pinned));
+    ctx->pinned = nullptr;
+    size_t cap = need + (1 << 16);
+    CK(cudaMallocHost((void **)&ctx->pinned, cap));
+    ctx->pinned_cap = cap;
+    return GSNFS_OK;
+}
+
+gsnfs_status map_dev_error(uint32_t e)
+{
+    switch (e) {
+    case 0: return GSNFS_OK;
+    case kErrCorrupt: return GSNFS_ERR_CORRUPT;
+    case kErrCapacity: return GSNFS_ERR_CAPACITY;
+    case kErrTimeout: return GSNFS_ERR_TIMEOUT;
+    default: return GSNFS_ERR_CUDA;
+    }
+}
+
+__host__ __device__ inline uint64_t pad8(uint64_t x) { return (x + 7) & ~7ull; }
+
+uint64_t header_bytes(uint32_t J, uint32_t C, uint32_t G) { return pad8(96 + 4ull * (J + 1) + C) + 8ull * G; }
+
+uint64_t occ_bound(uint64_t n, uint32_t J)
+{
+    uint64_t t = 0, p = 1;
+    for (uint32_t d = 0; d < J; ++d) {
+        t += std::min<uint64_t>(p, n);
+        if (p < (1ull << 60)) p *= 8;
+    }
+    return t;
+}
+
+bool pow2(uint32_t x) { return x && !(x & (x - 1)); }
+
+gsnfs_status check_quant(const gsnfs_quant *q)
+{
+    if (!q) return GSNFS_ERR_INVALID_ARG;
+    if (q->num_channels > (uint32_t)kMaxC) return GSNFS_ERR_INVALID_ARG;
+    if (q->rans_chunk < 32 || q->rans_chunk > (1u << 20) || (q->rans_chunk % 32)) return GSNFS_ERR_INVALID_ARG;
+    if (q->num_channels == 0) return GSNFS_OK;
+    if (q->num_groups < 1 || q->num_groups > 255 || !q->channel_group || !q->steps) return GSNFS_ERR_INVALID_ARG;
+    if (!pow2(q->rlgr_block) || q->rlgr_block < 32 || q->rlgr_block > 65536) return GSNFS_ERR_INVALID_ARG;
+    if (!(q->tau > 0.0 && q->tau <= 0.5)) return GSNFS_ERR_INVALID_ARG;
+    for (uint32_t c = 0; c < q->num_channels; ++c)
+        if (q->channel_group[c] >= q->num_groups) return GSNFS_ERR_INVALID_ARG;
+    for (uint32_t g = 0; g < q->num_groups; ++g)
+        if (!(q->steps[g] > 0.0) || !std::isfinite(q->steps[g])) return GSNFS_ERR_INVALID_ARG;
+    return GSNFS_OK;
+}
+
+// ------------------------------------------------------ container kernels ---
+struct StreamInfo {
+    uint64_t off, hb, occ, attr;
+};
+
+struct HdrParams {
+    uint32_t F, R, C, G, B, chunk;
+    double tau;
+    uint64_t capacity;
+};
+
+__device__ __forceinline__ void wr32(uint8_t *p, uint32_t v)
+{
+    for (int i = 0; i < 4; ++i) p[i] = (uint8_t)(v >> (8 * i));
+}
+__device__ __forceinline__ void wr64(uint8_t *p, uint64_t v)
+{
+    for (int i = 0; i < 8; ++i) p[i] = (uint8_t)(v >> (8 * i));
+}
+
+__global__ void sizes_kernel(HdrParams hp, const uint32_t *J, const uint32_t *vstart, const uint64_t *sec_bytes,
+                             const uint64_t *blk_off, const uint64_t *block_off, StreamInfo *si, DevState *st)
+{
+    if (threadIdx.x != 0) return;
+    uint64_t run = 0;
+    for (uint32_t f = 0; f < hp.F; ++f) {
+        const uint64_t nv = vstart[f + 1] - vstart[f];
+        const uint64_t nb = (nv + hp.B - 1) / hp.B;
+        for (uint32_t r = 0; r < hp.R; ++r) {
+            StreamInfo x;
+            x.hb = pad8(96 + 4ull * (J[f] + 1) + hp.C) + 8ull * (hp.C ? hp.G : 0);
+            x.occ = sec_bytes[f];
+            x.attr = 0;
+            if (hp.C && nv) {
+                const uint64_t b0 = blk_off[f] + (uint64_t)r * hp.C * nb;
+                const uint64_t words = block_off[b0 + hp.C * nb] - block_off[b0];
+                x.attr = pad8(8 + 4 * hp.C * nb + 4 * words);
+            }
+            x.off = run;
+            run += x.hb + x.occ + x.attr;
+            si[f * hp.R + r] = x;
+        }
+    }
+    si[hp.F * hp.R].off = run;
+    st->total_bytes = run;
+    if (run > hp.capacity) set_error(&st->err, kErrCapacity);
+}
+
+__global__ void header_kernel(HdrParams hp, const uint32_t *J, const uint32_t *vstart, const FrameGrid *grid,
+                              const uint32_t *lsz, const uint8_t *groups, const double *steps_rg,
+                              const StreamInfo *si, const DevState *st, uint8_t *out)
+{
+    if (st->total_bytes > hp.capacity) return;
+    const uint32_t s = blockIdx.x, f = s / hp.R, r = s % hp.R;
+    const StreamInfo x = si[s];
+    uint8_t *h = out + x.off;
+    const uint32_t Jf = J[f];
+    const uint32_t G = hp.C ? hp.G : 0;
+    for (uint32_t i = threadIdx.x; i < x.hb; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        wr32(h + 0, kMagic);
+        wr32(h + 4, 1);
+        wr32(h + 8, (uint32_t)x.hb);
+        wr32(h + 12, Jf);
+        wr32(h + 16, hp.C);
+        wr32(h + 20, G);
+        wr64(h + 24, vstart[f + 1] - vstart[f]);
+        const FrameGrid g = grid[f];
+        for (int a = 0; a < 3; ++a) wr64(h + 32 + 8 * a, (uint64_t)__double_as_longlong(g.lo[a]));
+        wr64(h + 56, (uint64_t)__double_as_longlong(g.ext));
+        wr64(h + 64, (uint64_t)__double_as_longlong(hp.tau));
+        wr64(h + 72, x.occ);
+        wr64(h + 80, x.attr);
+    }
+    for (uint32_t d = threadIdx.x; d <= Jf; d += blockDim.x) wr32(h + 96 + 4 * d, lsz[f * 22 + d]);
+    for (uint32_t c = threadIdx.x; c < hp.C; c += blockDim.x) h[96 + 4 * (Jf + 1) + c] = groups[c];
+    const uint64_t so = pad8(96 + 4ull * (Jf + 1) + hp.C);
+    for (uint32_t g = threadIdx.x; g < G; g += blockDim.x)
+        wr64(h + so + 8 * g, (uint64_t)__double_as_longlong(steps_rg[r * G + g]));
+}
+
+struct OccCopyArgs {
+    const uint8_t *occ;
+    const uint64_t *occ_off;
+    const uint32_t *mode;
+    const uint64_t *chunk_off;
+    const uint16_t *freq;
+    const uint32_t *chunk_words, *chunk_top, *chunk_pos;
+    const uint8_t *slots;
+    uint64_t slot_bytes;
+};
+
+__global__ void occ_copy_kernel(HdrParams hp, OccCopyArgs a, const StreamInfo *si, const DevState *st, uint8_t *out)
+{
+    if (st->total_bytes > hp.capacity) return;
+    const uint32_t s = blockIdx.y, f = s / hp.R;
+    const StreamInfo x = si[s];
+    uint8_t *sec = out + x.off + x.hb;
+    const uint64_t n = a.occ_off[f + 1] - a.occ_off[f];
+    const uint32_t mode = a.mode[f];
+    const uint8_t *src = a.occ + a.occ_off[f];
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    if (tid == 0) {
+        wr64(sec, n);
+        wr32(sec + 8, mode);
+    }
+    if (mode == 2) {
+        if (tid == 0) wr32(sec + 12, n ? src[0] : 0u);
+        return;
+    }
+    if (mode == 0) {
+        if (tid == 0) wr32(sec + 12, 0);
+        for (uint64_t i = tid; i < x.occ - 16; i += nt) sec[16 + i] = (i < n) ? src[i] : (uint8_t)0;
+        return;
+    }
+    const uint64_t c0 = a.chunk_off[f], nch = a.chunk_off[f + 1] - c0;
+    const uint64_t table = pad8(16 + 8 + 512 + 4 * nch);
+    if (tid == 0) {
+        wr32(sec + 12, (uint32_t)nch);
+        wr32(sec + 16, hp.chunk);
+        wr32(sec + 20, 0);
+    }
+    for (uint64_t i = tid; i < 256; i += nt) {
+        uint16_t v = a.freq[f * 256 + i];
+        sec[24 + 2 * i] = (uint8_t)v;
+        sec[24 + 2 * i + 1] = (uint8_t)(v >> 8);
+    }
+    for (uint64_t c = tid; c < nch; c += nt) {
+        uint32_t b = (uint32_t)((128 + 2 * (uint64_t)a.chunk_words[c0 + c] + 3) & ~3ull);
+        wr32(sec + 24 + 512 + 4 * c, b);
+    }
+    for (uint64_t i = 24 + 512 + 4 * nch + tid; i < table; i += nt) sec[i] = 0;
+    // chunks: one block-stride loop over chunks, threads over bytes
+    for (uint64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        const uint64_t gc = c0 + c;
+        const uint8_t *slot = a.slots + gc * a.slot_bytes;
+        const uint32_t w = a.chunk_words[gc], top = a.chunk_top[gc];
+        uint8_t *dst = sec + a.chunk_pos[gc];
+        const uint32_t bytes = (uint32_t)((128 + 2 * (uint64_t)w + 3) & ~3ull);
+        for (uint32_t i = threadIdx.x; i < bytes; i += blockDim.x) {
+            uint8_t v;
+            if (i < 128) v = slot[i];
+            else if (i < 128 + 2 * w) v = slot[128 + 2 * top + (i - 128)];
+            else v = 0;
+            dst[i] = v;
+        }
+    }
+    if (tid == 0) {  // tail padding of the section
+        uint64_t end = nch ? (a.chunk_pos[c0 + nch - 1] + ((128 + 2 * (uint64_t)a.chunk_words[c0 + nch - 1] + 3) & ~3ull)) : table;
+        for (uint64_t i = end; i < x.occ; ++i) sec[i] = 0;
+    }
+}
+
+struct AttrCopyArgs {
+    const uint32_t *vstart;
+    const uint64_t *blk_off;
+    const uint64_t *block_off;  // scanned word offsets of all blocks
+    const uint32_t *block_words;
+    const uint32_t *slots;
+    uint32_t slot_words;
+};
+
+__global__ void attr_copy_kernel(HdrParams hp, AttrCopyArgs a, const StreamInfo *si, const DevState *st, uint8_t *out)
+{
+    if (st->total_bytes > hp.capacity) return;
+    const uint32_t s = blockIdx.y, f = s / hp.R, r = s % hp.R;
+    const StreamInfo x = si[s];
+    if (x.attr == 0) return;
+    const uint64_t nv = a.vstart[f + 1] - a.vstart[f];
+    const uint32_t nb = (uint32_t)((nv + hp.B - 1) / hp.B);
+    const uint64_t nblk = (uint64_t)hp.C * nb;
+    const uint64_t b0 = a.blk_off[f] + (uint64_t)r * nblk;
+    uint32_t *sec = reinterpret_cast<uint32_t *>(out + x.off + x.hb + x.occ);
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    if (tid == 0) {
+        sec[0] = hp.B;
+        sec[1] = nb;
+    }
+    for (uint64_t k = tid; k < nblk; k += nt) sec[2 + k] = a.block_words[b0 + k];
+    uint32_t *pay = sec + 2 + nblk;
+    const uint64_t base = a.block_off[b0];
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t wid = tid >> 5, nwarps = nt >> 5;
+    for (uint64_t k = wid; k < nblk; k += nwarps) {
+        const uint32_t w = a.block_words[b0 + k];
+        const uint32_t *src = a.slots + (b0 + k) * a.slot_words;
+        uint32_t *dst = pay + (a.block_off[b0 + k] - base);
+        for (uint32_t i = lane; i < w; i += 32) dst[i] = src[i];
+    }
+    const uint64_t used = 8 + 4 * nblk + 4 * (a.block_off[b0 + nblk] - base);
+    if (tid == 0 && used < x.attr) wr32(reinterpret_cast<uint8_t *>(sec) + used, 0);
+}
+
+// ------------------------------------------------------------- encoder ---
+struct EncodeReq {
+    uint32_t F = 1;
+    const float *const *pos = nullptr;
+    const float *const *attr = nullptr;
+    const uint64_t *n = nullptr;
+    const uint32_t *J = nullptr;
+    uint32_t R = 1;
+    const double *rung_scale = nullptr;
+    const gsnfs_quant *q = nullptr;
+    uint8_t *out = nullptr;
+    uint64_t capacity = 0;
+    float *recon_pos = nullptr;
+    float *recon_attr = nullptr;
+    // results
+    uint64_t total_bytes = 0;
+    uint64_t nv = 0;
+    std::vector<uint64_t> offsets;
+};
+
+struct EncLayout {
+    FrameGrid *grid;
+    uint32_t *Jd, *vstart, *lsz, *hoff, *mode, *dpart, *opart, *seg, *vals, *vals_alt, *hist, *chunk_words,
+        *chunk_top, *chunk_pos, *cum, *slots, *block_words, *overflow;
+    const float **posp, **attrp;
+    uint64_t *poff, *keys, *keys_alt, *codes, *occ_off, *chunk_off, *sec_bytes, *job_off, *blk_off, *block_off,
+        *spart;
+    uint16_t *freq;
+    uint8_t *gap, *occ, *chunk_slots, *groups;
+    float *inv_step, *step, *Y, *pool;
+    double *steps_rg;
+    StreamInfo *si;
+    RahtPlanDev plan;
+    uint64_t occ_cap, max_chunks, jobs_bound, blocks_bound;
+    uint32_t slot_words;
+};
+
+void carve_plan(Carve &cv, RahtPlanDev &p, uint64_t nv_cap, uint32_t T)
+{
+    uint64_t elems, tiles, surv;
+    raht_plan_sizes(nv_cap, T, &elems, &tiles, &surv);
+    p.T = T;
+    p.cap_elems = (uint32_t)elems;
+    p.cap_tiles = (uint32_t)tiles;
+    p.cap_surv = (uint32_t)surv;
+    p.pos = cv.take<uint32_t>(elems);
+    p.gapseq = cv.take<uint8_t>(elems);
+    p.dest = cv.take<uint32_t>(elems);
+    p.tile_nbf = cv.take<uint32_t>(tiles);
+    p.tile_nr = cv.take<uint32_t>(tiles);
+    p.round_end = cv.take<uint16_t>(tiles * 64);
+    p.bf_idx = cv.take<uint32_t>(tiles * T);
+    p.bf_ab = cv.take<float2>(tiles * T);
+    p.tile_carry = cv.take<uint32_t>(tiles);
+    p.passes = cv.take<RahtPass>(kRahtMaxPasses + 1);
+    p.npasses = cv.take<uint32_t>(1);
+}
+
+size_t carve_encode(Carve &cv, EncLayout &L, const EncodeReq &rq, int num_sms, bool worst_slots)
+{
+    const uint32_t F = rq.F, R = rq.R, C = rq.q->num_channels;
+    uint64_t N = 0, occ_cap = 0, max_chunks = 0, jobs = 0;
+    for (uint32_t f = 0; f < F; ++f) {
+        N += rq.n[f];
+        uint64_t ob = occ_bound(rq.n[f], rq.J[f]);
+        occ_cap += ob;
+        max_chunks += (ob + rq.q->rans_chunk - 1) / rq.q->rans_chunk;
+        jobs += (uint64_t)R * ((rq.n[f] + rq.q->rlgr_block - 1) / rq.q->rlgr_block);
+    }
+    L.occ_cap = (occ_cap + 64) & ~(uint64_t)63;
+    L.max_chunks = max_chunks;
+    L.jobs_bound = C ? jobs : 0;
+    L.blocks_bound = L.jobs_bound * C;
+    L.slot_words = rlgr_slot_words(rq.q->rlgr_block, worst_slots);
+    L.grid = cv.take<FrameGrid>(F);
+    L.Jd = cv.take<uint32_t>(F);
+    L.posp = (const float **)cv.take<const float *>(F);
+    L.attrp = (const float **)cv.take<const float *>(F);
+    L.poff = cv.take<uint64_t>(F + 1);
+    L.inv_step = cv.take<float>((uint64_t)R * C + 1);
+    L.step = cv.take<float>((uint64_t)R * C + 1);
+    L.steps_rg = cv.take<double>((uint64_t)R * 256);
+    L.groups = cv.take<uint8_t>(256);
+    L.vstart = cv.take<uint32_t>(F + 1);
+    L.lsz = cv.take<uint32_t>((uint64_t)F * 22);
+    L.hoff = cv.take<uint32_t>((uint64_t)F * 22);
+    L.occ_off = cv.take<uint64_t>(F + 1);
+    L.chunk_off = cv.take<uint64_t>(F + 1);
+    L.freq = cv.take<uint16_t>((uint64_t)F * 256);
+    L.cum = cv.take<uint32_t>((uint64_t)F * 256);
+    L.mode = cv.take<uint32_t>(F);
+    L.sec_bytes = cv.take<uint64_t>(F);
+    L.job_off = cv.take<uint64_t>(F + 1);
+    L.blk_off = cv.take<uint64_t>(F + 1);
+    L.si = cv.take<StreamInfo>((uint64_t)F * R + 1);
+    L.overflow = cv.take<uint32_t>(4);
+    L.keys = cv.take<uint64_t>(N + 1);
+    L.keys_alt = cv.take<uint64_t>(N + 1);
+    L.vals = cv.take<uint32_t>(N + 1);
+    L.vals_alt = cv.take<uint32_t>(N + 1);
+    L.hist = cv.take<uint32_t>(radix_sort_hist_words(N, num_sms));
+    L.codes = cv.take<uint64_t>(N + 1);
+    L.seg = cv.take<uint32_t>(N + 2);
+    L.gap = cv.take<uint8_t>(N + 2);
+    L.dpart = cv.take<uint32_t>(dedup_partial_words(N, num_sms) + 1);
+    L.occ = cv.take<uint8_t>(L.occ_cap);
+    L.opart = cv.take<uint32_t>(occupancy_partial_words(F, num_sms));
+    L.chunk_slots = cv.take<uint8_t>(max_chunks * rans_chunk_slot_bytes(rq.q->rans_chunk) + 16);
+    L.chunk_words = cv.take<uint32_t>(max_chunks + 1);
+    L.chunk_top = cv.take<uint32_t>(max_chunks + 1);
+    L.chunk_pos = cv.take<uint32_t>(max_chunks + 1);
+    if (C) {
+        carve_plan(cv, L.plan, N, raht_tile_size(C));
+        uint64_t elems, tiles, surv;
+        raht_plan_sizes(N, L.plan.T, &elems, &tiles, &surv);
+        L.pool = cv.take<float>(surv * C);
+        L.Y = cv.take<float>(N * C + 4);
+        L.slots = cv.take<uint32_t>(L.blocks_bound * L.slot_words + 4);
+        L.block_words = cv.take<uint32_t>(L.blocks_bound + 1);
+        L.block_off = cv.take<uint64_t>(L.blocks_bound + 2);
+        L.spart = cv.take<uint64_t>(scan_partial_words(L.blocks_bound, num_sms) + 1);
+    } else {
+        L.plan = RahtPlanDev{};
+        L.pool = L.Y = nullptr;
+        L.slots = L.block_words = nullptr;
+        L.block_off = nullptr;
+        L.spart = cv.take<uint64_t>(4);
+    }
+    return cv.off;
+}
+
+gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool worst_slots)
+{
+    const uint32_t F = rq.F, R = rq.R;
+    const gsnfs_quant *q = rq.q;
+    const uint32_t C = q->num_channels, G = C ? q->num_groups : 0;
+    uint64_t N = 0, nmax = 0;
+    uint32_t Jmax = 0;
+    for (uint32_t f = 0; f < F; ++f) {
+        N += rq.n[f];
+        nmax = std::max(nmax, rq.n[f]);
+        Jmax = std::max(Jmax, rq.J[f]);
+    }
+    if (N >= 0x7FFFFFF0ull) return GSNFS_ERR_UNSUPPORTED;
+    const uint32_t frame_shift = (F == 1) ? 64u : 3u * Jmax;
+    uint32_t fbits = 0;
+    while ((1u << fbits) < F) ++fbits;
+    const uint32_t nbits = (F == 1) ? 3u * rq.J[0] : frame_shift + fbits;
+    if (nbits > 64) return GSNFS_ERR_UNSUPPORTED;
+
+    EncLayout L;
+    Carve measure(nullptr);
+    size_t need = carve_encode(measure, L, rq, ctx->num_sms, worst_slots);
+    gsnfs_status st = grow_arena(ctx, need, s);
+    if (st) return st;
+    Carve cv(ctx->arena);
+    carve_encode(cv, L, rq, ctx->num_sms, worst_slots);
+
+    // ---- host parameters -> pinned staging -> one copy
+    std::vector<unsigned char> hbuf;
+    size_t o_pos = 0, o_attr, o_poff, o_J, o_inv, o_step, o_srg, o_grp, o_end;
+    o_attr = o_pos + 8 * F;
+    o_poff = o_attr + 8 * F;
+    o_J = o_poff + 8 * (F + 1);
+    o_inv = o_J + 4 * F;
+    o_step = o_inv + 4 * (size_t)R * C;
+    o_srg = (o_step + 4 * (size_t)R * C + 7) & ~(size_t)7;
+    o_grp = o_srg + 8 * (size_t)R * 256;
+    o_end = o_grp + 256;
+    st = grow_pinned(ctx, o_end + 64);
+    if (st) return st;
+    CK(cudaStreamSynchronize(s));  // previous call's staging copies are done
+    unsigned char *hp = ctx->pinned;
+    uint64_t acc = 0;
+    for (uint32_t f = 0; f < F; ++f) {
+        ((const float **)(hp + o_pos))[f] = rq.pos[f];
+        ((const float **)(hp + o_attr))[f] = rq.attr ? rq.attr[f] : nullptr;
+        ((uint64_t *)(hp + o_poff))[f] = acc;
+        acc += rq.n[f];
+        ((uint32_t *)(hp + o_J))[f] = rq.J[f];
+    }
+    ((uint64_t *)(hp + o_poff))[F] = acc;
+    for (uint32_t r = 0; r < R; ++r) {
+        const double sc = rq.rung_scale ? rq.rung_scale[r] : 1.0;
+        for (uint32_t c = 0; c < C; ++c) {
+            const double stp = q->steps[q->channel_group[c]] * sc;
+            ((float *)(hp + o_inv))[r * C + c] = (float)(1.0 / stp);
+            ((float *)(hp + o_step))[r * C + c] = (float)stp;
+        }
+        for (uint32_t g = 0; g < G; ++g) ((double *)(hp + o_srg))[r * G + g] = q->steps[g] * sc;
+    }
+    for (uint32_t c = 0; c < C; ++c) hp[o_grp + c] = q->channel_group[c];
+    CK(cudaMemcpyAsync((void *)L.posp, hp + o_pos, 8 * F, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync((void *)L.attrp, hp + o_attr, 8 * F, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(L.poff, hp + o_poff, 8 * (F + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(L.Jd, hp + o_J, 4 * F, cudaMemcpyHostToDevice, s));
+    if (C) {
+        CK(cudaMemcpyAsync(L.inv_step, hp + o_inv, 4 * (size_t)R * C, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(L.step, hp + o_step, 4 * (size_t)R * C, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(L.steps_rg, hp + o_srg, 8 * (size_t)R * G, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(L.groups, hp + o_grp, C, cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaMemsetAsync(L.overflow, 0, 16, s));
+
+    DevState *dst = ctx->st;
+    const int sms = ctx->num_sms;
+    FrameSet fs;
+    fs.F = F;
+    fs.frame_shift = frame_shift;
+    fs.pos = L.posp;
+    fs.attr = L.attrp;
+    fs.poff = L.poff;
+    fs.J = L.Jd;
+    fs.grid = L.grid;
+
+    // a1: voxelise + Morton
+    launch_voxelize(fs, dst, N, nmax, L.keys, L.vals, sms, s);
+    // a2: radix sort
+    bool alt = radix_sort(L.keys, L.vals, L.keys_alt, L.vals_alt, L.hist, N, nbits, sms, s);
+    const uint64_t *skeys = alt ? L.keys_alt : L.keys;
+    const uint32_t *svals = alt ? L.vals_alt : L.vals;
+    // a3: dedup
+    launch_dedup(skeys, N, frame_shift, F, L.codes, L.seg, L.gap, L.vstart, L.dpart, dst, sms, s);
+    // a4: octree occupancy
+    OccupancyOut oo{L.occ, L.occ_cap, L.lsz, L.occ_off, L.hoff, L.opart};
+    launch_occupancy(L.codes, L.gap, L.vstart, L.Jd, F, frame_shift, oo, dst, sms, s);
+    // a5: occupancy rANS
+    RansFrames rf{F, L.occ, L.occ_off, q->rans_chunk, L.chunk_off, L.freq, L.cum, L.mode, L.chunk_words,
+                  L.chunk_top, L.chunk_pos, L.chunk_slots, L.sec_bytes};
+    launch_rans_encode(rf, dst, L.max_chunks, sms, s);
+
+    HdrParams hpar{F, R, C, G, C ? q->rlgr_block : 1u, q->rans_chunk, q->tau, rq.capacity};
+    if (C) {
+        // a6: RAHT prelude; a7: forward transform with the cluster average fused into the first pass
+        launch_raht_prelude(L.plan, L.gap, dst, nullptr, sms, s);
+        RahtIO io{};
+        io.C = C;
+        io.seg = L.seg;
+        io.vals = svals;
+        io.codes = L.codes;
+        io.attr = L.attrp;
+        io.frame_shift = frame_shift;
+        io.Y = L.Y;
+        io.pool = L.pool;
+        launch_raht_forward(L.plan, io, N, sms, s);
+        // a8 + a9: quantise + block RLGR for every rung
+        launch_rlgr_offsets(L.vstart, F, q->rlgr_block, R, C, L.job_off, L.blk_off, s);
+        RlgrJob j{};
+        j.C = C;
+        j.B = q->rlgr_block;
+        j.R = R;
+        j.Y = L.Y;
+        j.vstart = L.vstart;
+        j.F = F;
+        j.inv_step = L.inv_step;
+        j.tau = (float)q->tau;
+        j.slots = L.slots;
+        j.block_words = L.block_words;
+        j.blk_off = L.blk_off;
+        j.slot_words = L.slot_words;
+        j.overflow = L.overflow;
+        launch_rlgr_encode(j, L.job_off, L.jobs_bound, s);
+        launch_scan_u32_to_u64(L.block_words, L.blocks_bound, L.block_off, L.spart, sms, s);
+    }
+    // a10: container
+    sizes_kernel<<<1, 32, 0, s>>>(hpar, L.Jd, L.vstart, L.sec_bytes, L.blk_off, L.block_off, L.si, dst);
+    header_kernel<<<F * R, 128, 0, s>>>(hpar, L.Jd, L.vstart, L.grid, L.lsz, L.groups, L.steps_rg, L.si, dst,
+                                        rq.out);
+    OccCopyArgs oa{L.occ, L.occ_off, L.mode, L.chunk_off, L.freq, L.chunk_words, L.chunk_top, L.chunk_pos,
+                   L.chunk_slots, rans_chunk_slot_bytes(q->rans_chunk)};
+    occ_copy_kernel<<<dim3(std::max<uint32_t>(1, (uint32_t)sms * 2 / (F * R)), F * R), 256, 0, s>>>(hpar, oa, L.si,
+                                                                                                  dst, rq.out);
+    if (C) {
+        AttrCopyArgs aa{L.vstart, L.blk_off, L.block_off, L.block_words, L.slots, L.slot_words};
+        attr_copy_kernel<<<dim3(std::max<uint32_t>(1, (uint32_t)sms * 4 / (F * R)), F * R), 256, 0, s>>>(
+            hpar, aa, L.si, dst, rq.out);
+    }
+    // a13: optional reconstruction (first frame, first rung)
+    if (F == 1 && rq.recon_pos) launch_voxel_centres_batch(L.codes, dst, N, frame_shift, L.Jd, L.grid, rq.recon_pos, s);
+    if (F == 1 && C && rq.recon_attr) {
+        RahtIO io{};
+        io.C = C;
+        io.Y = L.Y;
+        io.out = rq.recon_attr;
+        io.pool = L.pool;
+        io.inv_step = L.inv_step;
+        io.step = L.step;
+        io.tau = (float)q->tau;
+        io.frame_shift = frame_shift;
+        launch_raht_inverse(L.plan, io, N, sms, s);
+    }
+    CK(cudaGetLastError());
+    // results
+    uint64_t *res = (uint64_t *)(hp + ((o_end + 63) & ~(size_t)63));
+    CK(cudaMemcpyAsync(res, &dst->err, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(res + 1, &dst->nv_total, 16, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(res + 3, L.overflow, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint32_t derr = (uint32_t)(res[0] & 0xFFFFFFFFu);
+    rq.nv = res[1];
+    rq.total_bytes = res[2];
+    const uint32_t ovf = (uint32_t)(res[3] & 0xFFFFFFFFu);
+    if (ovf && !worst_slots) return encode_impl(ctx, s, rq, true);
+    if (derr == kErrCapacity) return GSNFS_ERR_CAPACITY;
+    if (derr) return map_dev_error(derr);
+    if (!rq.offsets.empty()) {
+        std::vector<StreamInfo> si((size_t)F * R + 1);
+        CK(cudaMemcpy(si.data(), L.si, sizeof(StreamInfo) * si.size(), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < si.size(); ++i) rq.offsets[i] = si[i].off;
+    }
+    return GSNFS_OK;
+}
+
+// ------------------------------------------------------------- decoder ---
+struct ParsedHeader {
+    uint32_t J, C, G, hb;
+    uint64_t nv, occ_bytes, attr_bytes, n_occ;
+    double lo[3], ext, tau;
+    uint32_t lsz[22];
+    uint8_t groups[256];
+    double steps[256];
+    uint32_t occ_mode, occ_aux, chunk;
+    uint32_t B, nb;
+};
+
+uint32_t rd32(const uint8_t *p) { uint32_t v; memcpy(&v, p, 4); return v; }
+uint64_t rd64(const uint8_t *p) { uint64_t v; memcpy(&v, p, 8); return v; }
+double rdf64(const uint8_t *p) { double v; memcpy(&v, p, 8); return v; }
+
+gsnfs_status parse_fixed(const uint8_t *h, uint64_t bytes, ParsedHeader &P)
+{
+    if (bytes < 96 || rd32(h) != kMagic || rd32(h + 4) != 1) return GSNFS_ERR_CORRUPT;
+    P.hb = rd32(h + 8);
+    P.J = rd32(h + 12);
+    P.C = rd32(h + 16);
+    P.G = rd32(h + 20);
+    P.nv = rd64(h + 24);
+    for (int a = 0; a < 3; ++a) P.lo[a] = rdf64(h + 32 + 8 * a);
+    P.ext = rdf64(h + 56);
+    P.tau = rdf64(h + 64);
+    P.occ_bytes = rd64(h + 72);
+    P.attr_bytes = rd64(h + 80);
+    if (P.J < 1 || P.J > (uint32_t)kMaxJ || P.C > (uint32_t)kMaxC || P.G > 255) return GSNFS_ERR_CORRUPT;
+    if (P.C > 0 && P.G == 0) return GSNFS_ERR_CORRUPT;
+    if (P.hb != header_bytes(P.J, P.C, P.C ? P.G : 0)) return GSNFS_ERR_CORRUPT;
+    if (P.occ_bytes < 16 || P.occ_bytes > bytes || P.attr_bytes > bytes ||
+        (uint64_t)P.hb + P.occ_bytes + P.attr_bytes > bytes)
+        return GSNFS_ERR_CORRUPT;
+    if (!(P.ext > 0.0) || !std::isfinite(P.ext)) return GSNFS_ERR_CORRUPT;
+    if (P.nv >= 0x7FFFFFF0ull) return GSNFS_ERR_UNSUPPORTED;
+    return GSNFS_OK;
+}
+
+gsnfs_status parse_tables(const uint8_t *h, ParsedHeader &P)
+{
+    P.n_occ = 0;
+    for (uint32_t d = 0; d <= P.J; ++d) {
+        P.lsz[d] = rd32(h + 96 + 4 * d);
+        if (d < P.J) P.n_occ += P.lsz[d];
+    }
+    if (P.lsz[P.J] != P.nv) return GSNFS_ERR_CORRUPT;
+    if (P.nv == 0) {
+        for (uint32_t d = 0; d <= P.J; ++d)
+            if (P.lsz[d]) return GSNFS_ERR_CORRUPT;
+    } else {
+        if (P.lsz[0] != 1) return GSNFS_ERR_CORRUPT;
+        for (uint32_t d = 0; d < P.J; ++d)
+            if (P.lsz[d + 1] < P.lsz[d] || (uint64_t)P.lsz[d + 1] > 8ull * P.lsz[d]) return GSNFS_ERR_CORRUPT;
+    }
+    for (uint32_t c = 0; c < P.C; ++c) {
+        P.groups[c] = h[96 + 4 * (P.J + 1) + c];
+        if (P.groups[c] >= P.G) return GSNFS_ERR_CORRUPT;
+    }
+    const uint64_t so = pad8(96 + 4ull * (P.J + 1) + P.C);
+    for (uint32_t g = 0; g < (P.C ? P.G : 0); ++g) {
+        P.steps[g] = rdf64(h + so + 8 * g);
+        if (!(P.steps[g] > 0.0) || !std::isfinite(P.steps[g])) return GSNFS_ERR_CORRUPT;
+    }
+    return GSNFS_OK;
+}
+
+gsnfs_status parse_sections(const uint8_t *occ_hdr, const uint8_t *attr_hdr, ParsedHeader &P)
+{
+    if (rd64(occ_hdr) != P.n_occ) return GSNFS_ERR_CORRUPT;
+    P.occ_mode = rd32(occ_hdr + 8);
+    P.occ_aux = rd32(occ_hdr + 12);
+    P.chunk = rd32(occ_hdr + 16);
+    if (P.occ_mode == 0) {
+        if (16 + P.n_occ > P.occ_bytes) return GSNFS_ERR_CORRUPT;
+    } else if (P.occ_mode == 2) {
+        if (P.occ_aux > 255) return GSNFS_ERR_CORRUPT;
+    } else if (P.occ_mode == 1) {
+        if (P.chunk < 32 || P.chunk % 32 || P.chunk > (1u << 20)) return GSNFS_ERR_CORRUPT;
+        if ((uint64_t)P.occ_aux != (P.n_occ + P.chunk - 1) / P.chunk) return GSNFS_ERR_CORRUPT;
+        if (pad8(16 + 8 + 512 + 4ull * P.occ_aux) > P.occ_bytes) return GSNFS_ERR_CORRUPT;
+    } else {
+        return GSNFS_ERR_CORRUPT;
+    }
+    P.B = 1;
+    P.nb = 0;
+    if (P.C > 0 && P.nv > 0) {
+        if (P.attr_bytes < 8) return GSNFS_ERR_CORRUPT;
+        P.B = rd32(attr_hdr);
+        P.nb = rd32(attr_hdr + 4);
+        if (!pow2(P.B) || P.B < 32 || P.B > 65536) return GSNFS_ERR_CORRUPT;
+        if ((uint64_t)P.nb != (P.nv + P.B - 1) / P.B) return GSNFS_ERR_CORRUPT;
+        if (8 + 4ull * P.C * P.nb > P.attr_bytes) return GSNFS_ERR_CORRUPT;
+    } else if (P.attr_bytes != 0) {
+        return GSNFS_ERR_CORRUPT;
+    }
+    return GSNFS_OK;
+}
+
+gsnfs_status read_headers(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, uint64_t bytes, ParsedHeader &P)
+{
+    gsnfs_status st = grow_pinned(ctx, 8192);
+    if (st) return st;
+    CK(cudaStreamSynchronize(s));
+    uint8_t *hp = ctx->pinned;
+    if (bytes < 96) return GSNFS_ERR_CORRUPT;
+    CK(cudaMemcpyAsync(hp, d_in, 96, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    st = parse_fixed(hp, bytes, P);
+    if (st) return st;
+    CK(cudaMemcpyAsync(hp, d_in, P.hb, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hp + 4096, d_in + P.hb, 24, cudaMemcpyDeviceToHost, s));
+    if (P.attr_bytes >= 8) CK(cudaMemcpyAsync(hp + 4096 + 64, d_in + P.hb + P.occ_bytes, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    st = parse_tables(hp, P);
+    if (st) return st;
+    return parse_sections(hp + 4096, hp + 4096 + 64, P);
+}
+
+struct DecLayout {
+    uint8_t *occ, *gap;
+    uint64_t *nodes, *codes, *nvdev, *block_off, *spart;
+    uint32_t *pref, *ppart;
+    float *Y, *pool, *step;
+    FrameGrid *grid;
+    RahtPlanDev plan;
+};
+
+size_t carve_decode(Carve &cv, DecLayout &L, const ParsedHeader &P, int num_sms)
+{
+    L.grid = cv.take<FrameGrid>(1);
+    L.nvdev = cv.take<uint64_t>(1);
+    L.step = cv.take<float>(P.C + 1);
+    L.occ = cv.take<uint8_t>(P.n_occ + 8);
+    L.pref = cv.take<uint32_t>(P.n_occ + 2);
+    L.ppart = cv.take<uint32_t>(2 * (uint64_t)num_sms + 8);
+    uint64_t nodes = 0;
+    for (uint32_t d = 0; d < P.J; ++d) nodes += P.lsz[d];
+    L.nodes = cv.take<uint64_t>(nodes + 1);
+    L.codes = cv.take<uint64_t>(P.nv + 1);
+    L.gap = cv.take<uint8_t>(P.nv + 2);
+    if (P.C && P.nv) {
+        carve_plan(cv, L.plan, P.nv, raht_tile_size(P.C));
+        uint64_t elems, tiles, surv;
+        raht_plan_sizes(P.nv, L.plan.T, &elems, &tiles, &surv);
+        L.pool = cv.take<float>(surv * P.C);
+        L.Y = cv.take<float>(P.nv * P.C + 4);
+        L.block_off = cv.take<uint64_t>((uint64_t)P.C * P.nb + 2);
+        L.spart = cv.take<uint64_t>(scan_partial_words((uint64_t)P.C * P.nb, num_sms) + 1);
+    }
+    return cv.off;
+}
+
+gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, uint64_t bytes, float *d_pos,
+                         float *d_attr, uint64_t capacity_nv, uint64_t *out_nv)
+{
+    ParsedHeader P;
+    gsnfs_status st = read_headers(ctx, s, d_in, bytes, P);
+    if (st) return st;
+    if (out_nv) *out_nv = P.nv;
+    if (P.nv > capacity_nv) return GSNFS_ERR_CAPACITY;
+    if (P.nv == 0) return GSNFS_OK;
+    DecLayout L;
+    Carve m(nullptr);
+    size_t need = carve_decode(m, L, P, ctx->num_sms);
+    st = grow_arena(ctx, need, s);
+    if (st) return st;
+    Carve cv(ctx->arena);
+    carve_decode(cv, L, P, ctx->num_sms);
+    DevState *dst = ctx->st;
+    // host-computed grid and steps
+    unsigned char *hp = ctx->pinned;
+    FrameGrid g;
+    for (int a = 0; a < 3; ++a) g.lo[a] = P.lo[a];
+    g.ext = P.ext;
+    g.scale = std::ldexp(1.0, (int)P.J) / P.ext;
+    g.cell = P.ext / std::ldexp(1.0, (int)P.J);
+    memcpy(hp, &g, sizeof(g));
+    memcpy(hp + 128, &P.nv, 8);
+    for (uint32_t c = 0; c < P.C; ++c) ((float *)(hp + 256))[c] = (float)P.steps[P.groups[c]];
+    CK(cudaMemcpyAsync(L.grid, hp, sizeof(g), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(L.nvdev, hp + 128, 8, cudaMemcpyHostToDevice, s));
+    if (P.C) CK(cudaMemcpyAsync(L.step, hp + 256, 4 * P.C, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(dst, 0, 8, s));
+    const int sms = ctx->num_sms;
+    // a11: occupancy bytes
+    const uint8_t *sec = d_in + P.hb;
+    const uint8_t *occ = L.occ;
+    if (P.occ_mode == 0)
+        occ = sec + 16;
+    else if (P.occ_mode == 2)
+        launch_fill(L.occ, P.n_occ, (uint8_t)P.occ_aux, s);
+    else
+        launch_rans_decode(sec, P.occ_bytes, P.n_occ, P.occ_aux, P.chunk, L.occ, dst, sms, s);
+    launch_octree_decode(occ, P.n_occ, P.J, P.lsz, L.nodes, L.pref, L.ppart, L.codes, dst, sms, s);
+    if (d_pos) launch_voxel_centres(L.codes, P.nv, P.J, L.grid, d_pos, s);
+    // a12: attributes
+    if (P.C && d_attr) {
+        launch_gap_levels(L.codes, P.nv, L.gap, s);
+        launch_raht_prelude(L.plan, L.gap, dst, L.nvdev, sms, s);
+        const uint8_t *as = d_in + P.hb + P.occ_bytes;
+        const uint32_t *bw = reinterpret_cast<const uint32_t *>(as + 8);
+        const uint64_t nblk = (uint64_t)P.C * P.nb;
+        const uint32_t *payload = bw + nblk;
+        const uint64_t payload_words = (P.attr_bytes - 8 - 4 * nblk) / 4;
+        launch_scan_u32_to_u64(bw, nblk, L.block_off, L.spart, sms, s);
+        launch_rlgr_decode(payload, payload_words, bw, L.block_off, P.nv, P.C, P.B, L.step, L.Y, dst, s);
+        RahtIO io{};
+        io.C = P.C;
+        io.Y = L.Y;
+        io.out = d_attr;
+        io.pool = L.pool;
+        io.frame_shift = 64;
+        launch_raht_inverse(L.plan, io, P.nv, sms, s);
+    }
+    CK(cudaGetLastError());
+    uint32_t *res = (uint32_t *)(hp + 1024);
+    CK(cudaMemcpyAsync(res, &dst->err, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return map_dev_error(res[0]);
+}
+
+}  // namespace
+
+// ======================================================================
+extern "C" {
+
+const char *gsnfs_status_string(gsnfs_status s)
+{
+    switch (s) {
+    case GSNFS_OK: return "ok";
+    case GSNFS_ERR_INVALID_ARG: return "invalid argument";
+    case GSNFS_ERR_CAPACITY: return "output capacity too small";
+    case GSNFS_ERR_CORRUPT: return "corrupt bitstream";
+    case GSNFS_ERR_CUDA: return g_last_error[0] ? g_last_error : "CUDA error";
+    case GSNFS_ERR_TIMEOUT: return "bounded device wait expired";
+    case GSNFS_ERR_OOM: return "device allocation failed";
+    case GSNFS_ERR_UNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+gsnfs_status gsnfs_create(gsnfs_ctx **out, int cuda_device)
+{
+    if (!out) return GSNFS_ERR_INVALID_ARG;
+    *out = nullptr;
+    DeviceGuard dg(cuda_device);
+    int n = 0;
+    CK(cudaGetDeviceCount(&n));
+    if (cuda_device < 0 || cuda_device >= n) return GSNFS_ERR_INVALID_ARG;
+    gsnfs_ctx *c = new (std::nothrow) gsnfs_ctx();
+    if (!c) return GSNFS_ERR_OOM;
+    c->device = cuda_device;
+    cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, cuda_device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->st, sizeof(DevState));
+    if (e == cudaSuccess) e = cudaMemset(c->st, 0, sizeof(DevState));
+    if (e != cudaSuccess) {
+        snprintf(g_last_error, sizeof(g_last_error), "gsnfs_create: %s", cudaGetErrorString(e));
+        if (c->st) cudaFree(c->st);
+        delete c;
+        return GSNFS_ERR_CUDA;
+    }
+    *out = c;
+    return GSNFS_OK;
+}
+
+void gsnfs_destroy(gsnfs_ctx *ctx)
+{
+    if (!ctx) return;
+    DeviceGuard dg(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->arena) cudaFree(ctx->arena);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    if (ctx->st) cudaFree(ctx->st);
+    delete ctx;
+}
+
+gsnfs_status gsnfs_max_bitstream_bytes(uint64_t n, uint32_t J, const gsnfs_quant *q, uint64_t *out)
+{
+    if (!out || J < 1 || J > (uint32_t)kMaxJ) return GSNFS_ERR_INVALID_ARG;
+    gsnfs_status st = check_quant(q);
+    if (st) return st;
+    const uint32_t C = q->num_channels;
+    uint64_t b = header_bytes(J, C, C ? q->num_groups : 0);
+    b += 16 + pad8(occ_bound(n, J));
+    if (C) {
+        uint64_t nb = (n + q->rlgr_block - 1) / q->rlgr_block;
+        b += 8 + 4ull * C * nb + 4ull * C * nb * rlgr_slot_words(q->rlgr_block, true) + 8;
+    }
+    *out = b;
+    return GSNFS_OK;
+}
+
+gsnfs_status gsnfs_reserve(gsnfs_ctx *ctx, uint64_t n, uint32_t C, uint32_t J, const gsnfs_quant *q)
+{
+    if (!ctx || !q || J < 1 || J > (uint32_t)kMaxJ) return GSNFS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    EncodeReq rq;
+    gsnfs_quant qq = *q;
+    qq.num_channels = C;
+    rq.q = &qq;
+    rq.n = &n;
+    rq.J = &J;
+    EncLayout L;
+    Carve m(nullptr);
+    size_t need = carve_encode(m, L, rq, ctx->num_sms, false);
+    return grow_arena(ctx, need, 0);
+}
+
+gsnfs_status gsnfs_encode_frame(gsnfs_ctx *ctx, void *stream, const float *d_pos, const float *d_attr, uint64_t n,
+                                uint32_t J, const gsnfs_quant *q, uint8_t *d_bitstream, uint64_t capacity,
+                                uint64_t *out_bytes, float *d_recon_pos, float *d_recon_attr, uint64_t *out_nv)
+{
+    if (!ctx || J < 1 || J > (uint32_t)kMaxJ || !d_bitstream) return GSNFS_ERR_INVALID_ARG;
+    gsnfs_status st = check_quant(q);
+    if (st) return st;
+    if (n > 0 && !d_pos) return GSNFS_ERR_INVALID_ARG;
+    if (n > 0 && q->num_channels > 0 && !d_attr) return GSNFS_ERR_INVALID_ARG;
+    if ((uintptr_t)d_bitstream % 8 || (uintptr_t)d_attr % 16) return GSNFS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    EncodeReq rq;
+    rq.F = 1;
+    const float *pp[1] = {d_pos};
+    const float *ap[1] = {d_attr};
+    rq.pos = pp;
+    rq.attr = ap;
+    rq.n = &n;
+    rq.J = &J;
+    rq.q = q;
+    rq.out = d_bitstream;
+    rq.capacity = capacity;
+    rq.recon_pos = d_recon_pos;
+    rq.recon_attr = d_recon_attr;
+    st = encode_impl(ctx, (cudaStream_t)stream, rq, false);
+    if (out_bytes) *out_bytes = rq.total_bytes;
+    if (out_nv) *out_nv = rq.nv;
+    return st;
+}
+
+gsnfs_status gsnfs_encode_batch(gsnfs_ctx *ctx, void *stream, uint32_t frames, const float *const *h_pos,
+                                const float *const *h_attr, const uint64_t *h_n, const uint32_t *h_J, uint32_t rungs,
+                                const double *h_rung_scale, const gsnfs_quant *q, uint8_t *d_out, uint64_t capacity,
+                                uint64_t *h_offsets)
+{
+    if (!ctx || frames < 1 || frames > (uint32_t)kMaxFrames || rungs < 1 || rungs > (uint32_t)kMaxRungs || !h_pos ||
+        !h_n || !h_J || !d_out || !h_offsets)
+        return GSNFS_ERR_INVALID_ARG;
+    gsnfs_status st = check_quant(q);
+    if (st) return st;
+    for (uint32_t f = 0; f < frames; ++f) {
+        if (h_J[f] < 1 || h_J[f] > 19) return GSNFS_ERR_INVALID_ARG;
+        if (h_n[f] > 0 && !h_pos[f]) return GSNFS_ERR_INVALID_ARG;
+        if (q->num_channels && h_n[f] > 0 && (!h_attr || !h_attr[f] || (uintptr_t)h_attr[f] % 16))
+            return GSNFS_ERR_INVALID_ARG;
+    }
+    if (h_rung_scale)
+        for (uint32_t r = 0; r < rungs; ++r)
+            if (!(h_rung_scale[r] > 0.0)) return GSNFS_ERR_INVALID_ARG;
+    if ((uintptr_t)d_out % 8) return GSNFS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    EncodeReq rq;
+    rq.F = frames;
+    rq.pos = h_pos;
+    rq.attr = h_attr;
+    rq.n = h_n;
+    rq.J = h_J;
+    rq.R = rungs;
+    rq.rung_scale = h_rung_scale;
+    rq.q = q;
+    rq.out = d_out;
+    rq.capacity = capacity;
+    rq.offsets.assign((size_t)frames * rungs + 1, 0);
+    st = encode_impl(ctx, (cudaStream_t)stream, rq, false);
+    if (st == GSNFS_OK)
+        for (size_t i = 0; i < rq.offsets.size(); ++i) h_offsets[i] = rq.offsets[i];
+    else if (st == GSNFS_ERR_CAPACITY)
+        h_offsets[(size_t)frames * rungs] = rq.total_bytes;
+    return st;
+}
+
+gsnfs_status gsnfs_peek_frame(const uint8_t *h_header, uint64_t bytes, uint64_t *out_nv, uint32_t *out_C,
+                              uint32_t *out_J)
+{
+    if (!h_header) return GSNFS_ERR_INVALID_ARG;
+    ParsedHeader P;
+    if (bytes < 96 || rd32(h_header) != kMagic || rd32(h_header + 4) != 1) return GSNFS_ERR_CORRUPT;
+    P.J = rd32(h_header + 12);
+    P.C = rd32(h_header + 16);
+    P.nv = rd64(h_header + 24);
+    if (P.J < 1 || P.J > (uint32_t)kMaxJ) return GSNFS_ERR_CORRUPT;
+    if (out_nv) *out_nv = P.nv;
+    if (out_C) *out_C = P.C;
+    if (out_J) *out_J = P.J;
+    return GSNFS_OK;
+}
+
+gsnfs_status gsnfs_decode_frame(gsnfs_ctx *ctx, void *stream, const uint8_t *d_bitstream, uint64_t bytes, float *d_pos,
+                                float *d_attr, uint64_t capacity_nv, uint64_t *out_nv)
+{
+    if (!ctx || !d_bitstream) return GSNFS_ERR_INVALID_ARG;
+    if ((uintptr_t)d_bitstream % 8 || (uintptr_t)d_attr % 16) return GSNFS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    return decode_impl(ctx, (cudaStream_t)stream, d_bitstream, bytes, d_pos, d_attr, capacity_nv, out_nv);
+}
+
+gsnfs_status gsnfs_decode_batch(gsnfs_ctx *ctx, void *stream, uint32_t frames, const uint8_t *d_in,
+                                const uint64_t *h_in_offsets, float *d_pos, float *d_attr, uint64_t capacity_rows,
+                                uint64_t *h_out_rows)
+{
+    if (!ctx || !d_in || !h_in_offsets || !h_out_rows || frames == 0) return GSNFS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t row = 0;
+    h_out_rows[0] = 0;
+    for (uint32_t f = 0; f < frames; ++f) {
+        ParsedHeader P;
+        const uint64_t b = h_in_offsets[f], e = h_in_offsets[f + 1];
+        if (e < b) return GSNFS_ERR_INVALID_ARG;
+        gsnfs_status st = read_headers(ctx, s, d_in + b, e - b, P);
+        if (st) return st;
+        if (row + P.nv > capacity_rows) return GSNFS_ERR_CAPACITY;
+        uint64_t nv = 0;
+        st = decode_impl(ctx, s, d_in + b, e - b, d_pos ? d_pos + 3 * row : nullptr,
+                         d_attr ? d_attr + P.C * row : nullptr, capacity_rows - row, &nv);
+        if (st) return st;
+        row += nv;
+        h_out_rows[f + 1] = row;
+    }
+    return GSNFS_OK;
+}
+
+}  // extern "C"
+
+// ====================================================== stage entry points
+namespace {
+
+__global__ void stage_si_kernel(const uint64_t *sec_bytes, StreamInfo *si, DevState *st)
+{
+    StreamInfo x{0, 0, sec_bytes[0], 0};
+    si[0] = x;
+    si[1].off = sec_bytes[0];
+    st->total_bytes = sec_bytes[0];
+}
+
+struct GeoLayout {
+    FrameGrid *grid;
+    uint32_t *Jd, *vstart, *vals, *vals_alt, *hist, *seg, *dpart, *lsz, *hoff, *opart;
+    const float **posp;
+    uint64_t *poff, *keys, *keys_alt, *codes, *occ_off;
+    uint8_t *gap, *occ;
+};
+
+size_t carve_geo(Carve &cv, GeoLayout &L, uint64_t n, uint64_t occ_cap, int sms)
+{
+    L.grid = cv.take<FrameGrid>(1);
+    L.Jd = cv.take<uint32_t>(1);
+    L.posp = (const float **)cv.take<const float *>(1);
+    L.poff = cv.take<uint64_t>(2);
+    L.vstart = cv.take<uint32_t>(2);
+    L.keys = cv.take<uint64_t>(n + 1);
+    L.keys_alt = cv.take<uint64_t>(n + 1);
+    L.vals = cv.take<uint32_t>(n + 1);
+    L.vals_alt = cv.take<uint32_t>(n + 1);
+    L.hist = cv.take<uint32_t>(radix_sort_hist_words(n, sms));
+    L.codes = cv.take<uint64_t>(n + 1);
+    L.seg = cv.take<uint32_t>(n + 2);
+    L.gap = cv.take<uint8_t>(n + 2);
+    L.dpart = cv.take<uint32_t>(dedup_partial_words(n, sms) + 1);
+    L.lsz = cv.take<uint32_t>(22);
+    L.hoff = cv.take<uint32_t>(22);
+    L.occ_off = cv.take<uint64_t>(2);
+    L.opart = cv.take<uint32_t>(occupancy_partial_words(1, sms));
+    L.occ = cv.take<uint8_t>(occ_cap + 64);
+    return cv.off;
+}
+
+}  // namespace
+
+extern "C" {
+
+gsnfs_status gsnfs_voxelize(gsnfs_ctx *ctx, void *stream, const float *d_pos, uint64_t n, uint32_t J,
+                            uint64_t *d_codes, double *h_grid, uint64_t *out_nv)
+{
+    if (!ctx || J < 1 || J > (uint32_t)kMaxJ || (n && (!d_pos || !d_codes))) return GSNFS_ERR_INVALID_ARG;
+    if (n >= 0x7FFFFFF0ull) return GSNFS_ERR_UNSUPPORTED;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    GeoLayout L;
+    Carve m(nullptr);
+    gsnfs_status st = grow_arena(ctx, carve_geo(m, L, n, 0, ctx->num_sms), s);
+    if (st) return st;
+    Carve cv(ctx->arena);
+    carve_geo(cv, L, n, 0, ctx->num_sms);
+    st = grow_pinned(ctx, 4096);
+    if (st) return st;
+    CK(cudaStreamSynchronize(s));
+    unsigned char *hp = ctx->pinned;
+    ((const float **)hp)[0] = d_pos;
+    ((uint64_t *)(hp + 64))[0] = 0;
+    ((uint64_t *)(hp + 64))[1] = n;
+    ((uint32_t *)(hp + 128))[0] = J;
+    CK(cudaMemcpyAsync((void *)L.posp, hp, 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(L.poff, hp + 64, 16, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(L.Jd, hp + 128, 4, cudaMemcpyHostToDevice, s));
+    FrameSet fs{1, 64, L.posp, nullptr, L.poff, L.Jd, L.grid};
+    launch_voxelize(fs, ctx->st, n, n, L.keys, L.vals, ctx->num_sms, s);
+    bool alt = radix_sort(L.keys, L.vals, L.keys_alt, L.vals_alt, L.hist, n, 3 * J, ctx->num_sms, s);
+    launch_dedup(alt ? L.keys_alt : L.keys, n, 64, 1, L.codes, L.seg, L.gap, L.vstart, L.dpart, ctx->st,
+                 ctx->num_sms, s);
+    if (n) CK(cudaMemcpyAsync(d_codes, L.codes, 8 * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(hp + 256, L.grid, sizeof(FrameGrid), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hp + 512, &ctx->st->nv_total, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    FrameGrid g;
+    memcpy(&g, hp + 256, sizeof(g));
+    if (h_grid) {
+        for (int a = 0; a < 3; ++a) h_grid[a] = g.lo[a];
+        h_grid[3] = g.ext;
+    }
+    if (out_nv) memcpy(out_nv, hp + 512, 8);
+    return GSNFS_OK;
+}
+
+gsnfs_status gsnfs_octree_encode(gsnfs_ctx *ctx, void *stream, const uint64_t *d_codes, uint64_t nv, uint32_t J,
+                                 uint8_t *d_occ, uint64_t occ_capacity, uint32_t *h_level_sizes,
+                                 uint64_t *out_occ_bytes)
+{
+    if (!ctx || J < 1 || J > (uint32_t)kMaxJ || (nv && !d_codes) || !h_level_sizes) return GSNFS_ERR_INVALID_ARG;
+    if (nv >= 0x7FFFFFF0ull) return GSNFS_ERR_UNSUPPORTED;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t ob = occ_bound(nv, J);
+    GeoLayout L;
+    Carve m(nullptr);
+    gsnfs_status st = grow_arena(ctx, carve_geo(m, L, nv, ob, ctx->num_sms), s);
+    if (st) return st;
+    Carve cv(ctx->arena);
+    carve_geo(cv, L, nv, ob, ctx->num_sms);
+    st = grow_pinned(ctx, 4096);
+    if (st) return st;
+    CK(cudaStreamSynchronize(s));
+    unsigned char *hp = ctx->pinned;
+    ((uint32_t *)hp)[0] = 0;
+    ((uint32_t *)hp)[1] = (uint32_t)nv;
+    ((uint32_t *)hp)[2] = J;
+    CK(cudaMemcpyAsync(L.vstart, hp, 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(L.Jd, hp + 8, 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->st, 0, 8, s));
+    if (nv) CK(cudaMemcpyAsync(L.codes, d_codes, 8 * nv, cudaMemcpyDeviceToDevice, s));
+    launch_gap_levels(L.codes, nv, L.gap, s);
+    OccupancyOut oo{L.occ, (ob + 64) & ~(uint64_t)63, L.lsz, L.occ_off, L.hoff, L.opart};
+    launch_occupancy(L.codes, L.gap, L.vstart, L.Jd, 1, 64, oo, ctx->st, ctx->num_sms, s);
+    CK(cudaMemcpyAsync(hp + 256, L.lsz, 4 * 22, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hp + 512, L.occ_off, 16, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hp + 640, ctx->st, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    if (((uint32_t *)(hp + 640))[0]) return map_dev_error(((uint32_t *)(hp + 640))[0]);
+    const uint64_t nb = ((uint64_t *)(hp + 512))[1];
+    for (uint32_t d = 0; d <= J; ++d) h_level_sizes[d] = ((uint32_t *)(hp + 256))[d];
+    if (out_occ_bytes) *out_occ_bytes = nb;
+    if (nb > occ_capacity) return GSNFS_ERR_CAPACITY;
+    if (nb) CK(cudaMemcpyAsync(d_occ, L.occ, nb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return GSNFS_OK;
+}
+
+gsnfs_status gsnfs_octree_decode(gsnfs_ctx *ctx, void *stream, const uint8_t *d_occ, uint64_t occ_bytes, uint32_t J,
+                                 const uint32_t *h_level_sizes, uint64_t *d_codes)
+{
+    if (!ctx || J < 1 || J > (uint32_t)kMaxJ || !h_level_sizes) return GSNFS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    ParsedHeader P;
+    P.J = J;
+    P.nv = h_level_sizes[J];
+    P.n_occ = 0;
+    for (uint32_t d = 0; d <= J; ++d) {
+        P.lsz[d] = h_level_sizes[d];
+        if (d < J) P.n_occ += P.lsz[d];
+    }
+    if (P.n_occ != occ_bytes) return GSNFS_ERR_CORRUPT;
+    if (P.nv == 0) return P.n_occ == 0 ? GSNFS_OK : GSNFS_ERR_CORRUPT;
+    if (P.lsz[0] != 1) return GSNFS_ERR_CORRUPT;
+    for (uint32_t d = 0; d < J; ++d)
+        if (P.lsz[d + 1] < P.lsz[d] || (uint64_t)P.lsz[d + 1] > 8ull * P.lsz[d]) return GSNFS_ERR_CORRUPT;
+    if (!d_occ || !d_codes) return GSNFS_ERR_INVALID_ARG;
+    P.C = 0;
+    P.nb = 0;
+    DecLayout L;
+    Carve m(nullptr);
+    gsnfs_status st = grow_arena(ctx, carve_decode(m, L, P, ctx->num_sms), s);
+    if (st) return st;
+    Carve cv(ctx->arena);
+    carve_decode(cv, L, P, ctx->num_sms);
+    st = grow_pinned(ctx, 4096);
+    if (st) return st;
+    CK(cudaMemsetAsync(ctx->st, 0, 8, s));
+    launch_octree_decode(d_occ, P.n_occ, J, P.lsz, L.nodes, L.pref, L.ppart, d_codes, ctx->st, ctx->num_sms, s);
+    CK(cudaMemcpyAsync(ctx->pinned, ctx->st, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    return map_dev_error(((uint32_t *)ctx->pinned)[0]);
+}
+
+gsnfs_status gsnfs_occupancy_section_encode(gsnfs_ctx *ctx, void *stream, const uint8_t *d_in, uint64_t n,
+                                            uint32_t rans_chunk, uint8_t *d_out, uint64_t capacity,
+                                            uint64_t *out_bytes)
+{
+    if (!ctx || (n && !d_in) || !d_out || rans_chunk < 32 || rans_chunk % 32 || rans_chunk > (1u << 20))
+        return GSNFS_ERR_INVALID_ARG;
+    if ((uintptr_t)d_out % 8) return GSNFS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t nch = (n + rans_chunk - 1) / rans_chunk;
+    auto carve = [&](Carve &cv, uint64_t **occ_off, uint64_t **chunk_off, uint16_t **freq, uint32_t **cum,
+                     uint32_t **mode, uint32_t **cw, uint32_t **ct, uint32_t **cp, uint8_t **slots, uint64_t **sec,
+                     StreamInfo **si) {
+        *occ_off = cv.take<uint64_t>(2);
+        *chunk_off = cv.take<uint64_t>(2);
+        *freq = cv.take<uint16_t>(256);
+        *cum = cv.take<uint32_t>(256);
+        *mode = cv.take<uint32_t>(1);
+        *cw = cv.take<uint32_t>(nch + 1);
+        *ct = cv.take<uint32_t>(nch + 1);
+        *cp = cv.take<uint32_t>(nch + 1);
+        *slots = cv.take<uint8_t>(nch * rans_chunk_slot_bytes(rans_chunk) + 16);
+        *sec = cv.take<uint64_t>(1);
+        *si = cv.take<StreamInfo>(2);
+        return cv.off;
+    };
+    uint64_t *occ_off, *chunk_off, *sec;
+    uint16_t *freq;
+    uint32_t *cum, *mode, *cw, *ct, *cp;
+    uint8_t *slots;
+    StreamInfo *si;
+    Carve m(nullptr);
+    gsnfs_status st = grow_arena(ctx, carve(m, &occ_off, &chunk_off, &freq, &cum, &mode, &cw, &ct, &cp, &slots, &sec, &si), s);
+    if (st) return st;
+    Carve cv(ctx->arena);
+    carve(cv, &occ_off, &chunk_off, &freq, &cum, &mode, &cw, &ct, &cp, &slots, &sec, &si);
+    st = grow_pinned(ctx, 4096);
+    if (st) return st;
+    CK(cudaStreamSynchronize(s));
+    uint64_t *hp = (uint64_t *)ctx->pinned;
+    hp[0] = 0;
+    hp[1] = n;
+    CK(cudaMemcpyAsync(occ_off, hp, 16, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->st, 0, 8, s));
+    RansFrames rf{1, d_in, occ_off, rans_chunk, chunk_off, freq, cum, mode, cw, ct, cp, slots, sec};
+    launch_rans_encode(rf, ctx->st, nch, ctx->num_sms, s);
+    stage_si_kernel<<<1, 1, 0, s>>>(sec, si, ctx->st);
+    HdrParams hpar{1, 1, 0, 0, 1, rans_chunk, 0.5, capacity};
+    OccCopyArgs oa{d_in, occ_off, mode, chunk_off, freq, cw, ct, cp, slots, rans_chunk_slot_bytes(rans_chunk)};
+    occ_copy_kernel<<<dim3(ctx->num_sms, 1), 256, 0, s>>>(hpar, oa, si, ctx->st, d_out);
+    CK(cudaMemcpyAsync(hp + 8, sec, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    if (out_bytes) *out_bytes = hp[8];
+    return hp[8] > capacity ? GSNFS_ERR_CAPACITY : GSNFS_OK;
+}
+
+gsnfs_status gsnfs_occupancy_section_decode(gsnfs_ctx *ctx, void *stream, const uint8_t *d_sec, uint64_t sec_bytes,
+                                            uint8_t *d_out, uint64_t n)
+{
+    if (!ctx || !d_sec || (n && !d_out) || sec_bytes < 16) return GSNFS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    gsnfs_status st = grow_pinned(ctx, 4096);
+    if (st) return st;
+    CK(cudaStreamSynchronize(s));
+    uint8_t *hp = ctx->pinned;
+    CK(cudaMemcpyAsync(hp, d_sec, sec_bytes < 24 ? 16 : 24, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ParsedHeader P;
+    P.n_occ = n;
+    P.occ_bytes = sec_bytes;
+    P.C = 0;
+    P.nv = 0;
+    st = parse_sections(hp, nullptr, P);
+    if (st) return st;
+    CK(cudaMemsetAsync(ctx->st, 0, 8, s));
+    if (P.occ_mode == 0) {
+        if (n) CK(cudaMemcpyAsync(d_out, d_sec + 16, n, cudaMemcpyDeviceToDevice, s));
+    } else if (P.occ_mode == 2) {
+        launch_fill(d_out, n, (uint8_t)P.occ_aux, s);
+    } else {
+        launch_rans_decode(d_sec, sec_bytes, n, P.occ_aux, P.chunk, d_out, ctx->st, ctx->num_sms, s);
+    }
+    CK(cudaMemcpyAsync(hp + 64, ctx->st, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    return map_dev_error(((uint32_t *)(hp + 64))[0]);
+}
+
+gsnfs_status gsnfs_raht_plan_create(gsnfs_ctx *ctx, void *stream, const uint64_t *d_codes, uint64_t nv, uint32_t J,
+                                    uint32_t C, gsnfs_raht_plan **out)
+{
+    if (!ctx || !out || J < 1 || J > (uint32_t)kMaxJ || C < 1 || C > (uint32_t)kMaxC || (nv && !d_codes))
+        return GSNFS_ERR_INVALID_ARG;
+    if (nv >= 0x7FFFFFF0ull) return GSNFS_ERR_UNSUPPORTED;
+    *out = nullptr;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    gsnfs_raht_plan *pl = new (std::nothrow) gsnfs_raht_plan();
+    if (!pl) return GSNFS_ERR_OOM;
+    pl->ctx = ctx;
+    pl->nv = nv;
+    pl->C = C;
+    pl->J = J;
+    uint8_t *gap = nullptr;
+    uint64_t *nvd = nullptr;
+    auto carve = [&](Carve &cv) {
+        carve_plan(cv, pl->dev, nv, raht_tile_size(C));
+        uint64_t elems, tiles, surv;
+        raht_plan_sizes(nv, pl->dev.T, &elems, &tiles, &surv);
+        pl->pool = cv.take<float>(surv * C);
+        pl->qparams = cv.take<float>(2 * (uint64_t)C);
+        pl->st = cv.take<DevState>(1);
+        gap = cv.take<uint8_t>(nv + 2);
+        nvd = cv.take<uint64_t>(1);
+        return cv.off;
+    };
+    Carve m(nullptr);
+    size_t need = carve(m);
+    cudaError_t e = cudaMalloc(&pl->mem, need);
+    if (e != cudaSuccess) {
+        delete pl;
+        return GSNFS_ERR_OOM;
+    }
+    Carve cv(pl->mem);
+    carve(cv);
+    CK(cudaMemsetAsync(pl->st, 0, sizeof(DevState), s));
+    CK(cudaMemcpyAsync(nvd, &pl->nv, 8, cudaMemcpyHostToDevice, s));
+    if (nv) launch_gap_levels(d_codes, nv, gap, s);
+    launch_raht_prelude(pl->dev, gap, pl->st, nvd, ctx->num_sms, s);
+    CK(cudaStreamSynchronize(s));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        snprintf(g_last_error, sizeof(g_last_error), "raht plan: %s", cudaGetErrorString(e));
+        cudaFree(pl->mem);
+        delete pl;
+        return GSNFS_ERR_CUDA;
+    }
+    *out = pl;
+    return GSNFS_OK;
+}
+
+void gsnfs_raht_plan_destroy(gsnfs_raht_plan *plan)
+{
+    if (!plan) return;
+    DeviceGuard dg(plan->ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(plan->mem);
+    delete plan;
+}
+
+gsnfs_status gsnfs_raht_forward(gsnfs_raht_plan *plan, void *stream, const float *d_in, float *d_out)
+{
+    if (!plan || (plan->nv && (!d_in || !d_out))) return GSNFS_ERR_INVALID_ARG;
+    if ((uintptr_t)d_in % 16 || (uintptr_t)d_out % 16) return GSNFS_ERR_INVALID_ARG;
+    DeviceGuard dg(plan->ctx->device);
+    if (plan->nv == 0) return GSNFS_OK;
+    RahtIO io{};
+    io.C = plan->C;
+    io.in = d_in;
+    io.Y = d_out;
+    io.pool = plan->pool;
+    io.frame_shift = 64;
+    launch_raht_forward(plan->dev, io, plan->nv, plan->ctx->num_sms, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return GSNFS_OK;
+}
+
+gsnfs_status gsnfs_raht_inverse(gsnfs_raht_plan *plan, void *stream, const float *d_in, float *d_out,
+                                const gsnfs_quant *q)
+{
+    if (!plan || (plan->nv && (!d_in || !d_out))) return GSNFS_ERR_INVALID_ARG;
+    if ((uintptr_t)d_in % 16 || (uintptr_t)d_out % 16) return GSNFS_ERR_INVALID_ARG;
+    if (q) {
+        gsnfs_status st = check_quant(q);
+        if (st) return st;
+        if (q->num_channels != plan->C) return GSNFS_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(plan->ctx->device);
+    if (plan->nv == 0) return GSNFS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    RahtIO io{};
+    io.C = plan->C;
+    io.Y = const_cast<float *>(d_in);
+    io.out = d_out;
+    io.pool = plan->pool;
+    io.frame_shift = 64;
+    if (q) {
+        std::vector<float> h(2 * plan->C);
+        for (uint32_t c = 0; c < plan->C; ++c) {
+            const double stp = q->steps[q->channel_group[c]];
+            h[c] = (float)(1.0 / stp);
+            h[plan->C + c] = (float)stp;
+        }
+        CK(cudaMemcpyAsync(plan->qparams, h.data(), 8 * plan->C, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        io.inv_step = plan->qparams;
+        io.step = plan->qparams + plan->C;
+        io.tau = (float)q->tau;
+    }
+    launch_raht_inverse(plan->dev, io, plan->nv, plan->ctx->num_sms, s);
+    CK(cudaGetLastError());
+    return GSNFS_OK;
+}
+
+uint32_t gsnfs_rlgr_slot_words(uint32_t B) { return rlgr_slot_words(B, true); }
+
+gsnfs_status gsnfs_rlgr_encode_indices(gsnfs_ctx *ctx, void *stream, const int32_t *d_q, uint64_t nv, uint32_t C,
+                                       uint32_t B, uint32_t *d_slots, uint32_t *d_block_words)
+{
+    if (!ctx || !pow2(B) || B < 32 || B > 65536 || C < 1 || C > (uint32_t)kMaxC) return GSNFS_ERR_INVALID_ARG;
+    if (nv && (!d_q || !d_slots || !d_block_words)) return GSNFS_ERR_INVALID_ARG;
+    if (nv >= 0x7FFFFFF0ull) return GSNFS_ERR_UNSUPPORTED;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    gsnfs_status st = grow_pinned(ctx, 4096);
+    if (st) return st;
+    Carve m(nullptr);
+    m.take<uint32_t>(4);
+    m.take<uint64_t>(4);
+    m.take<uint64_t>(4);
+    m.take<uint32_t>(4);
+    st = grow_arena(ctx, m.off, s);
+    if (st) return st;
+    Carve cv(ctx->arena);
+    uint32_t *vstart = cv.take<uint32_t>(4);
+    uint64_t *job_off = cv.take<uint64_t>(4);
+    uint64_t *blk_off = cv.take<uint64_t>(4);
+    uint32_t *ovf = cv.take<uint32_t>(4);
+    CK(cudaStreamSynchronize(s));
+    uint32_t *hp = (uint32_t *)ctx->pinned;
+    hp[0] = 0;
+    hp[1] = (uint32_t)nv;
+    CK(cudaMemcpyAsync(vstart, hp, 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ovf, 0, 16, s));
+    launch_rlgr_offsets(vstart, 1, B, 1, C, job_off, blk_off, s);
+    launch_rlgr_encode_indices(d_q, vstart, C, B, d_slots, rlgr_slot_words(B, true), d_block_words, job_off, blk_off,
+                               (nv + B - 1) / B, ovf, s);
+    CK(cudaGetLastError());
+    return GSNFS_OK;
+}
+
+gsnfs_status gsnfs_rlgr_decode_indices(gsnfs_ctx *ctx, void *stream, const uint32_t *d_slots,
+                                       const uint32_t *d_block_words, uint64_t nv, uint32_t C, uint32_t B,
+                                       int32_t *d_q)
+{
+    if (!ctx || !pow2(B) || B < 32 || B > 65536 || C < 1 || C > (uint32_t)kMaxC) return GSNFS_ERR_INVALID_ARG;
+    if (nv && (!d_q || !d_slots || !d_block_words)) return GSNFS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    gsnfs_status st = grow_pinned(ctx, 4096);
+    if (st) return st;
+    CK(cudaMemsetAsync(ctx->st, 0, 8, s));
+    const uint32_t sw = rlgr_slot_words(B, true);
+    const uint64_t nb = (nv + B - 1) / B;
+    launch_rlgr_decode_indices(d_slots, (uint64_t)C * nb * sw, d_block_words, sw, nv, C, B, d_q, ctx->st, s);
+    CK(cudaMemcpyAsync(ctx->pinned, ctx->st, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    return map_dev_error(((uint32_t *)ctx->pinned)[0]);
+}
+
+}  // extern "C"

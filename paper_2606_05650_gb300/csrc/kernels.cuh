@@ -1,0 +1,182 @@
+// Host-side launchers of the codec's kernels (one translation unit each).
+#pragma once
+
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace gsnfs {
+
+// Device description of a batch of frames (F = 1 for the plain path).
+struct FrameSet {
+    uint32_t F;
+    uint32_t frame_shift;        // key bit where the frame id starts (64 when F == 1)
+    const float *const *pos;     // device array of F device pointers (N_f x 3)
+    const float *const *attr;    // device array of F device pointers (N_f x C) or null
+    const uint64_t *poff;        // device, F + 1 point offsets into the key arrays
+    const uint32_t *J;           // device, F depths
+    FrameGrid *grid;             // device, F grids
+};
+
+// ---- voxel.cu: bounding box, grid, Morton keys (Sec. 2.1, Sec. 2.2) ------
+void launch_voxelize(const FrameSet &fs, DevState *st, uint64_t n_total, uint64_t n_max, uint64_t *keys,
+                     uint32_t *vals, int num_sms, cudaStream_t s);
+
+// ---- sort.cu: LSD radix sort of (key, value) over bits [0, nbits) -------
+// Returns true when the result is in (keys_alt, vals_alt).
+bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint32_t *hist,
+                uint64_t n, uint32_t nbits, int num_sms, cudaStream_t s);
+uint64_t radix_sort_hist_words(uint64_t n, int num_sms);
+
+// ---- geometry.cu ----------------------------------------------------------
+// Dedup of sorted keys: codes[v], seg[v] (first sorted point of voxel v,
+// seg[nv] = n), gap[v] (gap level to v-1, kInfLevel at frame starts and at
+// gap[nv]), vstart[F+1] (voxel offset of each frame), nv -> st->nv_total.
+void launch_dedup(const uint64_t *keys, uint64_t n, uint32_t frame_shift, uint32_t F, uint64_t *codes,
+                  uint32_t *seg, uint8_t *gap, uint32_t *vstart, uint32_t *partials, DevState *st, int num_sms,
+                  cudaStream_t s);
+uint64_t dedup_partial_words(uint64_t n, int num_sms);
+
+// Octree occupancy bytes of every frame, all levels at once (Algorithm 1).
+// level_sizes[f * 22 + d], occ_off[F+1] (byte offset of each frame's bytes).
+struct OccupancyOut {
+    uint8_t *occ;            // capacity occ_capacity bytes
+    uint64_t occ_capacity;
+    uint32_t *level_sizes;   // F x 22
+    uint64_t *occ_off;       // F + 1
+    uint32_t *hoff;          // F x 22: byte offset of height h inside the frame
+    uint32_t *partials;      // scratch
+};
+void launch_occupancy(const uint64_t *codes, const uint8_t *gap, const uint32_t *vstart, const uint32_t *J,
+                      uint32_t F, uint32_t frame_shift, const OccupancyOut &o, DevState *st, int num_sms,
+                      cudaStream_t s);
+uint64_t occupancy_partial_words(uint32_t F, int num_sms);
+
+// Octree decoding of one frame (Algorithms 2-3): level sizes known on host.
+void launch_octree_decode(const uint8_t *occ, uint64_t n_occ, uint32_t J, const uint32_t *h_level_sizes,
+                          uint64_t *nodes, uint32_t *pref, uint32_t *partials, uint64_t *leaves,
+                          DevState *st, int num_sms, cudaStream_t s);
+uint64_t octree_decode_node_words(const uint32_t *h_level_sizes, uint32_t J);
+
+// gap levels of ascending codes (one frame), gap[0] = gap[nv] = kInfLevel
+void launch_gap_levels(const uint64_t *codes, uint64_t nv, uint8_t *gap, cudaStream_t s);
+// voxel centres of the codes of one frame (Sec. 2.1)
+void launch_voxel_centres(const uint64_t *codes, uint64_t nv, uint32_t J, const FrameGrid *grid, float *pos,
+                          cudaStream_t s);
+// voxel centres of a batch: codes carry frame ids above frame_shift
+void launch_voxel_centres_batch(const uint64_t *codes, const DevState *st, uint64_t nv_bound,
+                                uint32_t frame_shift, const uint32_t *J, const FrameGrid *grid, float *pos,
+                                cudaStream_t s);
+
+// ---- raht.cu: prelude and tile transforms (Sec. 3, Algorithms 4-6) -------
+constexpr int kRahtMultiPasses = 3;  // passes launched grid-wide; the rest run in one CTA
+constexpr int kRahtMaxPasses = 40;
+
+struct RahtPass {  // device-resident description of one pass
+    uint32_t n;        // elements in this pass
+    uint32_t ntiles;
+    uint32_t seq_off;  // offset of pos/gap/dest arrays (elements)
+    uint32_t tile_off; // first tile index in the schedule arrays
+    uint32_t surv_off; // row offset of this pass's input rows in the survivor pool (pass >= 2)
+    uint32_t pad[3];
+};
+
+struct RahtPlanDev {  // device pointers of a plan
+    uint32_t T;            // tile size (elements)
+    uint32_t cap_elems;    // capacity of the pooled sequence arrays
+    uint32_t cap_tiles;
+    uint32_t cap_surv;     // rows in the survivor pool
+    uint32_t *pos;         // pooled sequence arrays
+    uint8_t *gapseq;
+    uint32_t *dest;
+    uint32_t *tile_nbf;    // per tile: number of butterflies
+    uint32_t *tile_nr;     // per tile: number of rounds
+    uint16_t *round_end;   // per tile x 64
+    uint32_t *bf_idx;      // per tile x T: i0 | i1 << 16
+    float2 *bf_ab;         // per tile x T
+    uint32_t *tile_carry;  // per tile carried count, then exclusive base
+    RahtPass *passes;      // kRahtMaxPasses
+    uint32_t *npasses;     // device counter
+};
+
+uint32_t raht_tile_size(uint32_t C);
+void raht_plan_sizes(uint64_t nv_cap, uint32_t T, uint64_t *elems, uint64_t *tiles, uint64_t *surv_rows);
+void launch_raht_prelude(const RahtPlanDev &p, const uint8_t *gap, const DevState *st, const uint64_t *nv_host,
+                         int num_sms, cudaStream_t s);
+
+struct RahtIO {
+    uint32_t C;
+    const float *in;        // forward: nv x C input rows (if gather == null)
+    const uint32_t *seg;    // forward gather: first sorted point of each voxel
+    const uint32_t *vals;   // forward gather: local point index of sorted points
+    const uint64_t *codes;  // forward gather: voxel codes (frame id) for the attr pointer
+    const float *const *attr;  // forward gather: per-frame attribute pointers
+    uint32_t frame_shift;
+    float *Y;               // coefficients nv x C
+    float *out;             // inverse output nv x C
+    float *pool;            // survivor rows
+    const float *inv_step;  // inverse with quantise->dequantise: per channel 1/step (device), or null
+    const float *step;      // per channel step (device)
+    float tau;
+};
+void launch_raht_forward(const RahtPlanDev &p, const RahtIO &io, uint64_t nv_bound, int num_sms, cudaStream_t s);
+void launch_raht_inverse(const RahtPlanDev &p, const RahtIO &io, uint64_t nv_bound, int num_sms, cudaStream_t s);
+
+// ---- rlgr.cu: quantiser + block RLGR (Sec. 3.4) ----------------------------
+struct RlgrJob {
+    uint32_t C;
+    uint32_t B;
+    uint32_t R;                 // rungs
+    const float *Y;             // coefficients, rows = voxels of all frames
+    const uint32_t *vstart;     // F + 1 voxel offsets
+    uint32_t F;
+    const float *inv_step;      // R x C (device)
+    float tau;
+    uint32_t *slots;            // word slots, one per (frame, rung, channel, block)
+    uint32_t *block_words;      // per block: words needed
+    const uint64_t *blk_off;    // F + 1: first block of each frame (R x C x nb_f blocks per frame)
+    uint32_t slot_words;        // words per slot (a block needing more sets *overflow)
+    uint32_t *overflow;
+};
+uint32_t rlgr_slot_words(uint32_t B, bool worst_case);
+void launch_rlgr_offsets(const uint32_t *vstart, uint32_t F, uint32_t B, uint32_t R, uint32_t C, uint64_t *job_off,
+                         uint64_t *blk_off, cudaStream_t s);
+void launch_rlgr_encode(const RlgrJob &j, const uint64_t *job_off, uint64_t jobs_bound, cudaStream_t s);
+void launch_rlgr_encode_indices(const int32_t *q, const uint32_t *vstart, uint32_t C, uint32_t B, uint32_t *slots,
+                                uint32_t slot_words, uint32_t *bw, const uint64_t *job_off, const uint64_t *blk_off,
+                                uint64_t jobs_bound, uint32_t *overflow, cudaStream_t s);
+void launch_rlgr_decode(const uint32_t *payload, uint64_t payload_words, const uint32_t *block_words,
+                        const uint64_t *block_off, uint64_t nv, uint32_t C, uint32_t B, const float *step, float *Y,
+                        DevState *st, cudaStream_t s);
+void launch_rlgr_decode_indices(const uint32_t *words, uint64_t total_words, const uint32_t *bw, uint32_t stride,
+                                uint64_t nv, uint32_t C, uint32_t B, int32_t *q, DevState *st, cudaStream_t s);
+
+// ---- rans.cu: occupancy entropy stage ------------------------------------
+struct RansFrames {
+    uint32_t F;
+    const uint8_t *occ;        // all frames' bytes
+    const uint64_t *occ_off;   // F + 1
+    uint32_t chunk;            // symbols per chunk
+    uint64_t *chunk_off;       // F + 1 global chunk index (computed)
+    uint16_t *freq;            // F x 256
+    uint32_t *cum;             // F x 256
+    uint32_t *mode;            // F: 0 raw, 1 rANS, 2 constant (decided after sizing)
+    uint32_t *chunk_words;     // per global chunk: 16-bit words
+    uint32_t *chunk_top;       // per global chunk: first used stack entry
+    uint32_t *chunk_pos;       // per global chunk: byte offset inside the section
+    uint8_t *chunk_slots;      // per global chunk: rans_chunk_slot_bytes(chunk)
+    uint64_t *sec_bytes;       // F: occupancy section size
+};
+uint64_t rans_chunk_slot_bytes(uint32_t chunk);
+void launch_rans_encode(const RansFrames &r, DevState *st, uint64_t max_chunks, int num_sms, cudaStream_t s);
+void launch_rans_decode(const uint8_t *sec, uint64_t sec_bytes, uint64_t n, uint32_t nch, uint32_t chunk,
+                        uint8_t *out, DevState *st, int num_sms, cudaStream_t s);
+void launch_fill(uint8_t *out, uint64_t n, uint8_t v, cudaStream_t s);
+
+// ---- scan.cu / api.cu helpers -------------------------------------------
+// exclusive scan of n u32 values into u64 offsets (out has n + 1 entries)
+void launch_scan_u32_to_u64(const uint32_t *in, uint64_t n, uint64_t *out, uint64_t *partials, int num_sms,
+                            cudaStream_t s);
+uint64_t scan_partial_words(uint64_t n, int num_sms);
+
+}  // namespace gsnfs

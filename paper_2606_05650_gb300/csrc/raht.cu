@@ -1,0 +1,613 @@
+// RAHT prelude and transform (Sec. 3.1 Eq. 1, Sec. 3.2-3.3, App. D,
+// Algorithms 4-6).
+//
+// Schedule from gap levels.  For ascending distinct codes, gap i (between
+// voxels i-1 and i) has level g_i = msb(m_{i-1} xor m_i) + 1: the binary
+// level at which the two voxels' branches merge.  Every gap is exactly one
+// butterfly of Algorithm 6: its high pass lands at i1 = i, its low pass at
+// i0 = the nearest gap to the left with a larger level (the start of the
+// merged node), and the weights are run lengths w0 = i - i0, w1 = e - i with
+// e the nearest larger gap to the right.  This is the level list of
+// Algorithm 4 without materialising I_l / F_l for all 3J levels.
+//
+// Tiles instead of one launch per level.  The voxel sequence is cut into
+// tiles of T elements.  A gap whose enclosing node lies inside its tile is
+// processed in shared memory (all its descendants are in the tile too); the
+// tile's maximal subtrees ("survivors") carry their low-pass rows to the
+// next pass, which runs the same tile procedure on the survivor sequence
+// (gap levels between survivors are the original gaps at their starts,
+// weights are differences of original positions).  Passes shrink the
+// sequence by a factor of ~T/(survivors per tile); the first three passes
+// run grid-wide, the remainder inside one CTA.  A survivor bounded by frame
+// boundaries on both sides is a frame's DC and is written in place.
+// In-tile butterflies are ordered by level, so each level is one round
+// between barriers.  The inverse runs the passes top-down with the rounds
+// reversed and the transposed rotation.
+#include "kernels.cuh"
+
+namespace gsnfs {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRounds = 64;
+constexpr uint32_t kSmemRowBytes = 56 * 1024;
+
+// ------------------------------------------------------------- prelude ---
+struct PreludeArgs {
+    RahtPlanDev p;
+    const uint8_t *gap0;  // gap levels of pass 0 (voxel sequence)
+    const DevState *st;
+};
+
+__device__ __forceinline__ uint32_t seq_pos(const RahtPlanDev &p, const RahtPass &ps, int q, uint64_t j)
+{
+    return q == 0 ? (uint32_t)j : p.pos[ps.seq_off + j];
+}
+
+__device__ __forceinline__ uint8_t seq_gap(const PreludeArgs &a, const RahtPass &ps, int q, uint64_t j)
+{
+    return q == 0 ? a.gap0[j] : a.p.gapseq[ps.seq_off + j];
+}
+
+struct PreludeSmem {
+    uint8_t g[4097];
+    uint8_t flags[4096];  // bit0 in-tile gap, bit1 survivor
+    uint8_t carry[4096];  // carried to the next pass
+    uint32_t p[4097];
+    uint16_t prv[4096];
+    uint16_t nxt[4096];
+    uint32_t lvl_cnt[kRounds + 1];
+    uint32_t lvl_off[kRounds + 1];
+    uint32_t scan[33];
+    uint32_t ncarry;
+};
+
+// Builds the schedule of tile t of pass q (one CTA).
+__device__ void prelude_tile(const PreludeArgs &a, PreludeSmem &S, int q, const RahtPass &ps, uint32_t t)
+{
+    const RahtPlanDev &p = a.p;
+    const uint32_t T = p.T;
+    const uint64_t j0 = (uint64_t)t * T;
+    const uint32_t m = (uint32_t)((ps.n - j0) < T ? (ps.n - j0) : T);
+    const int tid = threadIdx.x;
+    for (uint32_t i = tid; i <= m; i += kThreads) {
+        S.g[i] = seq_gap(a, ps, q, j0 + i);
+        S.p[i] = seq_pos(p, ps, q, j0 + i);
+    }
+    for (int i = tid; i <= kRounds; i += kThreads) S.lvl_cnt[i] = 0;
+    __syncthreads();
+    // nearest larger gap on each side (tile boundaries count as candidates)
+    for (uint32_t i = tid; i < m; i += kThreads) {
+        uint8_t f = 0;
+        if (i > 0) {
+            const uint8_t gi = S.g[i];
+            uint32_t l = i - 1;
+            while (l > 0 && S.g[l] <= gi) --l;
+            uint32_t r = i + 1;
+            while (r < m && S.g[r] <= gi) ++r;
+            if (S.g[l] > gi && S.g[r] > gi) {
+                f = 1;
+                S.prv[i] = (uint16_t)l;
+                S.nxt[i] = (uint16_t)r;
+                atomicAdd(&S.lvl_cnt[gi], 1u);
+            }
+        }
+        if (!(f & 1)) f |= 2;  // survivor: starts a maximal in-tile subtree
+        S.flags[i] = f;
+    }
+    __syncthreads();
+    if (tid < 32) {  // exclusive scan of level counts (65 entries) by one warp
+        uint32_t run = 0;
+        for (int base = 0; base <= kRounds; base += 32) {
+            int l = base + tid;
+            uint32_t c = (l <= kRounds) ? S.lvl_cnt[l] : 0u;
+            uint32_t inc = warp_inclusive_sum(c);
+            if (l <= kRounds) S.lvl_off[l] = run + inc - c;
+            run += __shfl_sync(0xFFFFFFFFu, inc, 31);
+        }
+        if (tid == 0) {  // rounds = nonempty levels in ascending order
+            uint32_t nr = 0, tot = 0;
+            uint16_t *re = p.round_end + (uint64_t)(ps.tile_off + t) * kRounds;
+            for (int l = 1; l <= kRounds; ++l)
+                if (S.lvl_cnt[l]) {
+                    tot += S.lvl_cnt[l];
+                    re[nr++] = (uint16_t)tot;
+                }
+            p.tile_nbf[ps.tile_off + t] = tot;
+            p.tile_nr[ps.tile_off + t] = nr;
+        }
+        for (int l = tid; l <= kRounds; l += 32) S.lvl_cnt[l] = 0;  // reused as fill counters
+    }
+    __syncthreads();
+    // butterflies, survivors, destinations
+    const uint64_t sbase = (uint64_t)(ps.tile_off + t) * T;
+    for (uint32_t i = tid; i < m; i += kThreads) {
+        const uint8_t f = S.flags[i];
+        uint8_t c = 0;
+        if (f & 1) {
+            uint32_t l = S.prv[i], r = S.nxt[i];
+            uint32_t w0 = S.p[i] - S.p[l], w1 = S.p[r] - S.p[i];
+            float fw0 = (float)w0, fw1 = (float)w1, fs = (float)(w0 + w1);
+            float ca = __fsqrt_rn(__fdiv_rn(fw0, fs)), cb = __fsqrt_rn(__fdiv_rn(fw1, fs));
+            uint32_t slot = S.lvl_off[S.g[i]] + atomicAdd(&S.lvl_cnt[S.g[i]], 1u);
+            p.bf_idx[sbase + slot] = l | (i << 16);
+            p.bf_ab[sbase + slot] = make_float2(ca, cb);
+            p.dest[ps.seq_off + j0 + i] = S.p[i];
+        } else {
+            // survivor: a frame root (final) iff both bounding gaps are frame boundaries
+            uint32_t r = i + 1;
+            while (r < m && !(S.flags[r] & 2)) ++r;
+            if (S.g[i] >= kInfLevel && S.g[r] >= kInfLevel)
+                p.dest[ps.seq_off + j0 + i] = S.p[i];
+            else
+                c = 1;
+        }
+        S.carry[i] = c;
+    }
+    __syncthreads();
+    // local carried ranks in element order
+    uint32_t run = 0, tot;
+    for (uint32_t k = 0; k < (T + kThreads - 1) / kThreads; ++k) {
+        uint32_t i = tid + k * kThreads;
+        uint32_t c = (i < m) ? S.carry[i] : 0u;
+        uint32_t pre = block_exclusive_sum<uint32_t>(c, S.scan, &tot);
+        if (c) p.dest[ps.seq_off + j0 + i] = kCarry | (run + pre);
+        run += tot;
+    }
+    if (tid == 0) p.tile_carry[ps.tile_off + t] = run;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) prelude_init_kernel(RahtPlanDev p, const DevState *st,
+                                                                 const uint64_t *nv_override)
+{
+    if (threadIdx.x == 0) {
+        uint32_t n = (uint32_t)(nv_override ? *nv_override : st->nv_total);
+        RahtPass ps = {};
+        ps.n = n;
+        ps.ntiles = (n + p.T - 1) / p.T;
+        p.passes[0] = ps;
+        for (int q = 1; q <= kRahtMaxPasses; ++q) p.passes[q] = RahtPass{};
+        *p.npasses = n ? 1u : 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) prelude_tiles_kernel(PreludeArgs a, int q)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PreludeSmem &S = *reinterpret_cast<PreludeSmem *>(smem_raw);
+    const RahtPass ps = a.p.passes[q];
+    for (uint32_t t = blockIdx.x; t < ps.ntiles; t += gridDim.x) prelude_tile(a, S, q, ps, t);
+}
+
+// one CTA: exclusive scan of carried counts over the pass's tiles, next pass
+__device__ void prelude_scan_body(const RahtPlanDev &p, int q, uint32_t *sh)
+{
+    const RahtPass ps = p.passes[q];
+    uint32_t run = 0;
+    for (uint32_t b = 0; b < ps.ntiles; b += blockDim.x) {
+        uint32_t t = b + threadIdx.x;
+        uint32_t c = (t < ps.ntiles) ? p.tile_carry[ps.tile_off + t] : 0u;
+        uint32_t tot;
+        uint32_t pre = block_exclusive_sum<uint32_t>(c, sh, &tot);
+        if (t < ps.ntiles) p.tile_carry[ps.tile_off + t] = run + pre;
+        run += tot;
+    }
+    if (threadIdx.x == 0) {
+        RahtPass nx = {};
+        if (q + 1 < kRahtMaxPasses) {
+            nx.n = run;
+            nx.ntiles = (run + p.T - 1) / p.T;
+            nx.seq_off = ps.seq_off + ps.n + 1;
+            nx.tile_off = ps.tile_off + ps.ntiles;
+            nx.surv_off = (q == 0) ? 0u : ps.surv_off + ps.n;
+            p.passes[q + 1] = nx;
+            if (run) *p.npasses = (uint32_t)(q + 2);
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) prelude_scan_kernel(RahtPlanDev p, int q)
+{
+    __shared__ uint32_t sh[33];
+    if (p.passes[q].n == 0) return;
+    prelude_scan_body(p, q, sh);
+}
+
+// carried elements: global index, next sequence arrays, sentinel
+__device__ void prelude_compact_body(const PreludeArgs &a, int q, uint64_t first, uint64_t stride)
+{
+    const RahtPlanDev &p = a.p;
+    const RahtPass ps = p.passes[q];
+    const RahtPass nx = p.passes[q + 1];
+    for (uint64_t j = first; j < ps.n; j += stride) {
+        uint32_t d = p.dest[ps.seq_off + j];
+        if (d & kCarry) {
+            uint32_t gi = p.tile_carry[ps.tile_off + (uint32_t)(j / p.T)] + (d & ~kCarry);
+            p.dest[ps.seq_off + j] = kCarry | gi;
+            p.pos[nx.seq_off + gi] = seq_pos(p, ps, q, j);
+            p.gapseq[nx.seq_off + gi] = seq_gap(a, ps, q, j);
+        }
+    }
+    if (first == 0 && nx.n) {
+        p.pos[nx.seq_off + nx.n] = seq_pos(p, ps, q, ps.n);
+        p.gapseq[nx.seq_off + nx.n] = (uint8_t)kInfLevel;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) prelude_compact_kernel(PreludeArgs a, int q)
+{
+    if (a.p.passes[q].n == 0 || q + 1 >= kRahtMaxPasses) return;
+    prelude_compact_body(a, q, (uint64_t)blockIdx.x * kThreads + threadIdx.x, (uint64_t)gridDim.x * kThreads);
+}
+
+// remaining passes inside one CTA
+__global__ void __launch_bounds__(kThreads) prelude_finish_kernel(PreludeArgs a, int q0)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PreludeSmem &S = *reinterpret_cast<PreludeSmem *>(smem_raw);
+    for (int q = q0; q + 1 < kRahtMaxPasses; ++q) {
+        const RahtPass ps = a.p.passes[q];
+        if (ps.n == 0) break;
+        for (uint32_t t = 0; t < ps.ntiles; ++t) prelude_tile(a, S, q, ps, t);
+        __syncthreads();
+        prelude_scan_body(a.p, q, S.scan);
+        __syncthreads();
+        prelude_compact_body(a, q, threadIdx.x, kThreads);
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------- transform ---
+struct TileSched {
+    uint32_t nbf, nr;
+    uint16_t re[kRounds];
+};
+
+template <int VEC>
+struct Vec;
+template <>
+struct Vec<1> {
+    typedef float T;
+    __device__ static T ld(const float *p) { return *p; }
+    __device__ static void st(float *p, T v) { *p = v; }
+    __device__ static T zero() { return 0.0f; }
+};
+template <>
+struct Vec<4> {
+    typedef float4 T;
+    __device__ static T ld(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+    __device__ static void st(float *p, T v) { *reinterpret_cast<float4 *>(p) = v; }
+    __device__ static T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+
+__device__ __forceinline__ float bfly_lo(float a, float b, float y0, float y1) { return __fadd_rn(__fmul_rn(a, y0), __fmul_rn(b, y1)); }
+__device__ __forceinline__ float bfly_hi(float a, float b, float y0, float y1) { return __fsub_rn(__fmul_rn(a, y1), __fmul_rn(b, y0)); }
+__device__ __forceinline__ float ibfly_0(float a, float b, float y0, float y1) { return __fsub_rn(__fmul_rn(a, y0), __fmul_rn(b, y1)); }
+__device__ __forceinline__ float ibfly_1(float a, float b, float y0, float y1) { return __fadd_rn(__fmul_rn(b, y0), __fmul_rn(a, y1)); }
+
+template <bool INV>
+__device__ __forceinline__ void rot(float a, float b, float &y0, float &y1)
+{
+    float u = y0, v = y1;
+    if (!INV) {
+        y0 = bfly_lo(a, b, u, v);
+        y1 = bfly_hi(a, b, u, v);
+    } else {
+        y0 = ibfly_0(a, b, u, v);
+        y1 = ibfly_1(a, b, u, v);
+    }
+}
+
+template <bool INV>
+__device__ __forceinline__ void rot(float a, float b, float4 &y0, float4 &y1)
+{
+    rot<INV>(a, b, y0.x, y1.x);
+    rot<INV>(a, b, y0.y, y1.y);
+    rot<INV>(a, b, y0.z, y1.z);
+    rot<INV>(a, b, y0.w, y1.w);
+}
+
+__device__ __forceinline__ float qdq(float y, float inv, float step, float tau)
+{
+    return __fmul_rn((float)quantize_f32(y, inv, tau), step);
+}
+
+struct XformArgs {
+    RahtPlanDev p;
+    RahtIO io;
+    uint32_t Cg;  // channels per group held in shared memory
+};
+
+// Processes tile t of pass q for channel group [c0, c0 + Cg).
+template <bool INV, int VEC, bool GATHER, bool QDQ>
+__device__ void xform_tile(const XformArgs &A, float *rows, uint32_t *s_idx, float2 *s_ab, TileSched &sch, int q,
+                           const RahtPass &ps, const RahtPass &nx, uint32_t t)
+{
+    typedef typename Vec<VEC>::T V;
+    const RahtPlanDev &p = A.p;
+    const RahtIO &io = A.io;
+    const uint32_t T = p.T, C = io.C;
+    const uint64_t j0 = (uint64_t)t * T;
+    const uint32_t m = (uint32_t)((ps.n - j0) < T ? (ps.n - j0) : T);
+    const int tid = threadIdx.x;
+    const uint32_t tile = ps.tile_off + t;
+    if (tid == 0) {
+        sch.nbf = p.tile_nbf[tile];
+        sch.nr = p.tile_nr[tile];
+    }
+    __syncthreads();
+    for (uint32_t r = tid; r < sch.nr; r += kThreads) sch.re[r] = p.round_end[(uint64_t)tile * kRounds + r];
+    for (uint32_t k = tid; k < sch.nbf; k += kThreads) {
+        s_idx[k] = p.bf_idx[(uint64_t)tile * T + k];
+        s_ab[k] = p.bf_ab[(uint64_t)tile * T + k];
+    }
+    for (uint32_t c0 = 0; c0 < C; c0 += A.Cg) {
+        const uint32_t Cg = (C - c0) < A.Cg ? (C - c0) : A.Cg;
+        const uint32_t L = Cg / VEC;           // vector lanes per row
+        const uint32_t slots = kThreads / L;   // rows processed per sweep
+        const uint32_t slot = tid / L, lane = tid - slot * L;
+        const uint32_t c = c0 + lane * VEC;
+        const bool act = slot < slots;
+        // ---- load rows
+        if (act) {
+            for (uint32_t i = slot; i < m; i += slots) {
+                const uint64_t j = j0 + i;
+                V v;
+                if (!INV) {
+                    if (q == 0) {
+                        if (GATHER) {
+                            const uint32_t s0 = io.seg[j], s1 = io.seg[j + 1];
+                            const uint32_t f = (io.frame_shift < 64) ? (uint32_t)(io.codes[j] >> io.frame_shift) : 0u;
+                            const float *base = io.attr[f];
+                            V acc = Vec<VEC>::zero();
+                            for (uint32_t g = s0; g < s1; ++g) {
+                                V x = Vec<VEC>::ld(base + (uint64_t)io.vals[g] * C + c);
+                                if (VEC == 1) {
+                                    *reinterpret_cast<float *>(&acc) = __fadd_rn(*reinterpret_cast<float *>(&acc), *reinterpret_cast<float *>(&x));
+                                } else {
+                                    float *pa = reinterpret_cast<float *>(&acc);
+                                    const float *px = reinterpret_cast<const float *>(&x);
+#pragma unroll
+                                    for (int e = 0; e < VEC; ++e) pa[e] = __fadd_rn(pa[e], px[e]);
+                                }
+                            }
+                            const float cntf = (float)(s1 - s0);
+                            float *pa = reinterpret_cast<float *>(&acc);
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e) pa[e] = __fdiv_rn(pa[e], cntf);
+                            v = acc;
+                        } else {
+                            v = Vec<VEC>::ld(io.in + j * C + c);
+                        }
+                    } else {
+                        v = Vec<VEC>::ld(io.pool + ((uint64_t)ps.surv_off + j) * C + c);
+                    }
+                } else {
+                    const uint32_t d = p.dest[ps.seq_off + j];
+                    if (d & kCarry) {
+                        v = Vec<VEC>::ld(io.pool + ((uint64_t)nx.surv_off + (d & ~kCarry)) * C + c);
+                    } else {
+                        v = Vec<VEC>::ld(io.Y + (uint64_t)d * C + c);
+                        if (QDQ) {
+                            float *pv = reinterpret_cast<float *>(&v);
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e) pv[e] = qdq(pv[e], io.inv_step[c + e], io.step[c + e], io.tau);
+                        }
+                    }
+                }
+                Vec<VEC>::st(rows + (uint64_t)i * Cg + lane * VEC, v);
+            }
+        }
+        __syncthreads();
+        // ---- rounds
+        for (uint32_t rr = 0; rr < sch.nr; ++rr) {
+            const uint32_t r = INV ? (sch.nr - 1 - rr) : rr;
+            const uint32_t kb = r ? sch.re[r - 1] : 0u, ke = sch.re[r];
+            if (act) {
+                for (uint32_t k = kb + slot; k < ke; k += slots) {
+                    const uint32_t ix = s_idx[k];
+                    const float2 ab = s_ab[k];
+                    float *r0 = rows + (uint64_t)(ix & 0xFFFFu) * Cg + lane * VEC;
+                    float *r1 = rows + (uint64_t)(ix >> 16) * Cg + lane * VEC;
+                    V y0 = Vec<VEC>::ld(r0), y1 = Vec<VEC>::ld(r1);
+                    rot<INV>(ab.x, ab.y, y0, y1);
+                    Vec<VEC>::st(r0, y0);
+                    Vec<VEC>::st(r1, y1);
+                }
+            }
+            __syncthreads();
+        }
+        // ---- store rows
+        if (act) {
+            for (uint32_t i = slot; i < m; i += slots) {
+                const uint64_t j = j0 + i;
+                V v = Vec<VEC>::ld(rows + (uint64_t)i * Cg + lane * VEC);
+                if (!INV) {
+                    const uint32_t d = p.dest[ps.seq_off + j];
+                    if (d & kCarry)
+                        Vec<VEC>::st(io.pool + ((uint64_t)nx.surv_off + (d & ~kCarry)) * C + c, v);
+                    else
+                        Vec<VEC>::st(io.Y + (uint64_t)d * C + c, v);
+                } else {
+                    if (q == 0)
+                        Vec<VEC>::st(io.out + j * C + c, v);
+                    else
+                        Vec<VEC>::st(io.pool + ((uint64_t)ps.surv_off + j) * C + c, v);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <bool INV, int VEC, bool GATHER, bool QDQ>
+__global__ void __launch_bounds__(kThreads) xform_pass_kernel(XformArgs A, int q)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ TileSched sch;
+    const uint32_t T = A.p.T;
+    uint32_t *s_idx = reinterpret_cast<uint32_t *>(smem_raw);
+    float2 *s_ab = reinterpret_cast<float2 *>(smem_raw + 4 * T);
+    float *rows = reinterpret_cast<float *>(smem_raw + 12 * T);
+    const RahtPass ps = A.p.passes[q];
+    const RahtPass nx = A.p.passes[q + 1];
+    for (uint32_t t = blockIdx.x; t < ps.ntiles; t += gridDim.x)
+        xform_tile<INV, VEC, GATHER, QDQ>(A, rows, s_idx, s_ab, sch, q, ps, nx, t);
+}
+
+// passes q0 .. npasses-1 in one CTA (forward: ascending; inverse: descending)
+template <bool INV, int VEC, bool QDQ>
+__global__ void __launch_bounds__(kThreads) xform_finish_kernel(XformArgs A, int q0)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ TileSched sch;
+    const uint32_t T = A.p.T;
+    uint32_t *s_idx = reinterpret_cast<uint32_t *>(smem_raw);
+    float2 *s_ab = reinterpret_cast<float2 *>(smem_raw + 4 * T);
+    float *rows = reinterpret_cast<float *>(smem_raw + 12 * T);
+    const int np = (int)*A.p.npasses;
+    for (int k = 0; k < np - q0; ++k) {
+        const int q = INV ? (np - 1 - k) : (q0 + k);
+        const RahtPass ps = A.p.passes[q];
+        const RahtPass nx = A.p.passes[q + 1];
+        for (uint32_t t = 0; t < ps.ntiles; ++t)
+            xform_tile<INV, VEC, false, QDQ>(A, rows, s_idx, s_ab, sch, q, ps, nx, t);
+        __threadfence_block();
+        __syncthreads();
+    }
+}
+
+uint32_t channel_group(uint32_t C, uint32_t T)
+{
+    uint32_t cg = kSmemRowBytes / (4u * T);
+    if (cg >= C) return C;
+    if (C % 4 == 0) cg &= ~3u;
+    return cg < 1 ? 1 : cg;
+}
+
+size_t xform_smem(uint32_t T, uint32_t Cg) { return (size_t)12 * T + (size_t)4 * T * Cg; }
+
+template <bool INV, int VEC, bool GATHER, bool QDQ>
+void launch_pass(const XformArgs &A, int q, uint32_t grid, size_t smem, cudaStream_t s)
+{
+    auto k = xform_pass_kernel<INV, VEC, GATHER, QDQ>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<grid, kThreads, smem, s>>>(A, q);
+}
+
+template <bool INV, int VEC, bool QDQ>
+void launch_finish(const XformArgs &A, int q0, size_t smem, cudaStream_t s)
+{
+    auto k = xform_finish_kernel<INV, VEC, QDQ>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<1, kThreads, smem, s>>>(A, q0);
+}
+
+template <int VEC>
+void forward_all(const XformArgs &A, uint64_t nv_bound, int num_sms, cudaStream_t s)
+{
+    const uint32_t T = A.p.T;
+    const size_t smem = xform_smem(T, A.Cg);
+    uint64_t tiles = (nv_bound + T - 1) / T;
+    uint32_t grid0 = (uint32_t)(tiles < 1 ? 1 : (tiles < (uint64_t)num_sms * 4 ? tiles : (uint64_t)num_sms * 4));
+    for (int q = 0; q < kRahtMultiPasses; ++q) {
+        uint32_t g = q == 0 ? grid0 : (grid0 < (uint32_t)num_sms ? grid0 : (uint32_t)num_sms);
+        if (q == 0 && A.io.seg)
+            launch_pass<false, VEC, true, false>(A, q, g, smem, s);
+        else
+            launch_pass<false, VEC, false, false>(A, q, g, smem, s);
+    }
+    launch_finish<false, VEC, false>(A, kRahtMultiPasses, smem, s);
+}
+
+template <int VEC>
+void inverse_all(const XformArgs &A, uint64_t nv_bound, int num_sms, cudaStream_t s)
+{
+    const uint32_t T = A.p.T;
+    const size_t smem = xform_smem(T, A.Cg);
+    uint64_t tiles = (nv_bound + T - 1) / T;
+    uint32_t grid0 = (uint32_t)(tiles < 1 ? 1 : (tiles < (uint64_t)num_sms * 4 ? tiles : (uint64_t)num_sms * 4));
+    const bool qd = A.io.inv_step != nullptr;
+    if (qd)
+        launch_finish<true, VEC, true>(A, kRahtMultiPasses, smem, s);
+    else
+        launch_finish<true, VEC, false>(A, kRahtMultiPasses, smem, s);
+    for (int q = kRahtMultiPasses - 1; q >= 0; --q) {
+        uint32_t g = q == 0 ? grid0 : (grid0 < (uint32_t)num_sms ? grid0 : (uint32_t)num_sms);
+        if (qd)
+            launch_pass<true, VEC, false, true>(A, q, g, smem, s);
+        else
+            launch_pass<true, VEC, false, false>(A, q, g, smem, s);
+    }
+}
+
+}  // namespace
+
+uint32_t raht_tile_size(uint32_t C)
+{
+    if (C == 0) return 4096;
+    uint32_t t = kSmemRowBytes / (4u * C);
+    uint32_t T = 256;
+    while (T * 2 <= t && T < 4096) T *= 2;
+    return T;
+}
+
+void raht_plan_sizes(uint64_t nv_cap, uint32_t T, uint64_t *elems, uint64_t *tiles, uint64_t *surv_rows)
+{
+    // a full tile keeps at most 2*63+1 < T/2 survivors, so every pass at least
+    // halves the sequence up to one partial tile (<= 127 extra per pass)
+    *elems = 2 * nv_cap + 130 * (kRahtMaxPasses + 1);
+    *tiles = 2 * ((nv_cap + T - 1) / T) + 2 * (kRahtMaxPasses + 1);
+    *surv_rows = nv_cap + 128 * (kRahtMaxPasses + 1);
+}
+
+void launch_raht_prelude(const RahtPlanDev &p, const uint8_t *gap, const DevState *st, const uint64_t *nv_dev,
+                         int num_sms, cudaStream_t s)
+{
+    PreludeArgs a;
+    a.p = p;
+    a.gap0 = gap;
+    a.st = st;
+    const size_t smem = sizeof(PreludeSmem);
+    cudaFuncSetAttribute(prelude_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(prelude_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    prelude_init_kernel<<<1, 32, 0, s>>>(p, st, nv_dev);
+    uint32_t grid = (uint32_t)num_sms * 4;
+    for (int q = 0; q < kRahtMultiPasses; ++q) {
+        prelude_tiles_kernel<<<grid, kThreads, smem, s>>>(a, q);
+        prelude_scan_kernel<<<1, 1024, 0, s>>>(p, q);
+        prelude_compact_kernel<<<grid, kThreads, 0, s>>>(a, q);
+    }
+    prelude_finish_kernel<<<1, kThreads, smem, s>>>(a, kRahtMultiPasses);
+}
+
+void launch_raht_forward(const RahtPlanDev &p, const RahtIO &io, uint64_t nv_bound, int num_sms, cudaStream_t s)
+{
+    if (io.C == 0) return;
+    XformArgs A;
+    A.p = p;
+    A.io = io;
+    A.Cg = channel_group(io.C, p.T);
+    if (A.Cg % 4 == 0 && io.C % 4 == 0)
+        forward_all<4>(A, nv_bound, num_sms, s);
+    else
+        forward_all<1>(A, nv_bound, num_sms, s);
+}
+
+void launch_raht_inverse(const RahtPlanDev &p, const RahtIO &io, uint64_t nv_bound, int num_sms, cudaStream_t s)
+{
+    if (io.C == 0) return;
+    XformArgs A;
+    A.p = p;
+    A.io = io;
+    A.Cg = channel_group(io.C, p.T);
+    if (A.Cg % 4 == 0 && io.C % 4 == 0)
+        inverse_all<4>(A, nv_bound, num_sms, s);
+    else
+        inverse_all<1>(A, nv_bound, num_sms, s);
+}
+
+}  // namespace gsnfs

@@ -1,0 +1,294 @@
+// Occupancy entropy stage (Sec. 2.2 last paragraph: the occupancy bytes are
+// entropy coded with ANS; the paper uses a closed library, this codec its
+// own static order-0 rANS after Duda 2013 with 32 interleaved states after
+// Giesen 2014, so that one warp codes one chunk with one state per lane).
+//
+// Model: M = 2^15; f_s = floor(cnt_s * M / n), at least 1 for a present
+// symbol; the most frequent symbol (lowest value on ties) absorbs M - sum f.
+// 32-bit states, L = 2^16, 16-bit renormalisation words.  Symbol j of a
+// chunk is coded by state j mod 32.  The encoder walks the chunk's groups of
+// 32 symbols from last to first (lanes 31..0 within a group) pushing words on
+// a stack; the decoder walks forward and pops them in lane order.
+#include "kernels.cuh"
+
+namespace gsnfs {
+
+namespace {
+
+constexpr uint32_t kProbBits = 15;
+constexpr uint32_t kM = 1u << kProbBits;
+constexpr uint32_t kL = 1u << 16;
+
+__global__ void __launch_bounds__(256) hist_kernel(const uint8_t *__restrict__ occ, const uint64_t *occ_off,
+                                                   DevState *st)
+{
+    __shared__ uint32_t h[256];
+    const uint32_t f = blockIdx.y;
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t b = occ_off[f], n = occ_off[f + 1] - b;
+    for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (uint64_t)gridDim.x * 256)
+        atomicAdd(&h[occ[b + i]], 1u);
+    __syncthreads();
+    if (h[threadIdx.x]) atomicAdd(&st->hist[f][threadIdx.x], h[threadIdx.x]);
+}
+
+// one CTA (256 threads) per frame: frequencies, cumulative table, mode
+__global__ void __launch_bounds__(256) norm_kernel(const uint64_t *occ_off, DevState *st, uint16_t *freq,
+                                                   uint32_t *cum, uint32_t *mode)
+{
+    const uint32_t f = blockIdx.x, s = threadIdx.x;
+    const uint64_t n = occ_off[f + 1] - occ_off[f];
+    const uint32_t cnt = st->hist[f][s];
+    __shared__ uint32_t sh[33];
+    __shared__ unsigned long long best;
+    __shared__ uint32_t distinct;
+    if (s == 0) {
+        best = 0;
+        distinct = 0;
+    }
+    __syncthreads();
+    uint32_t fs = 0;
+    if (cnt) {
+        fs = (uint32_t)(((uint64_t)cnt * kM) / n);
+        if (fs == 0) fs = 1;
+        atomicAdd(&distinct, 1u);
+        atomicMax(&best, ((unsigned long long)cnt << 8) | (255u - s));
+    }
+    uint32_t tot;
+    block_exclusive_sum<uint32_t>(fs, sh, &tot);
+    const uint32_t bs = 255u - (uint32_t)(best & 255u);
+    if (cnt && s == bs) fs += kM - tot;
+    uint32_t t2;
+    uint32_t c = block_exclusive_sum<uint32_t>(fs, sh, &t2);
+    freq[f * 256 + s] = (uint16_t)fs;
+    cum[f * 256 + s] = c;
+    if (s == 0) mode[f] = (n == 0) ? 0u : (distinct == 1 ? 2u : 1u);
+}
+
+__global__ void chunk_offsets_kernel(const uint64_t *occ_off, const uint32_t *mode, uint32_t F, uint32_t chunk,
+                                     uint64_t *chunk_off)
+{
+    if (threadIdx.x) return;
+    uint64_t run = 0;
+    for (uint32_t f = 0; f < F; ++f) {
+        chunk_off[f] = run;
+        uint64_t n = occ_off[f + 1] - occ_off[f];
+        if (mode[f] == 1) run += (n + chunk - 1) / chunk;
+    }
+    chunk_off[F] = run;
+}
+
+__device__ __forceinline__ uint32_t frame_of(const uint64_t *off, uint32_t F, uint64_t x)
+{
+    uint32_t lo = 0, hi = F;
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// warp per chunk; slot layout: u32 state[32] at 0, u16 word stack [128, 128 + 2*chunk)
+__global__ void __launch_bounds__(128) encode_kernel(const uint8_t *__restrict__ occ, const uint64_t *occ_off,
+                                                     const uint64_t *chunk_off, uint32_t F, uint32_t chunk,
+                                                     const uint16_t *freq, const uint32_t *cum, uint8_t *slots,
+                                                     uint64_t slot_bytes, uint32_t *chunk_words,
+                                                     uint32_t *chunk_top)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t total = chunk_off[F];
+    for (uint64_t gc = gw; gc < total; gc += nw) {
+        const uint32_t f = frame_of(chunk_off, F, gc);
+        const uint64_t c = gc - chunk_off[f];
+        const uint64_t n = occ_off[f + 1] - occ_off[f];
+        const uint8_t *sym = occ + occ_off[f] + c * chunk;
+        const uint32_t len = (uint32_t)((n - c * chunk) < chunk ? (n - c * chunk) : chunk);
+        const uint16_t *fr = freq + f * 256;
+        const uint32_t *cm = cum + f * 256;
+        uint8_t *slot = slots + gc * slot_bytes;
+        uint16_t *stack = reinterpret_cast<uint16_t *>(slot + 128);
+        uint32_t top = chunk;
+        uint32_t x = kL;
+        const uint32_t G = (len + 31) / 32;
+        for (int g = (int)G - 1; g >= 0; --g) {
+            const uint32_t j = (uint32_t)g * 32 + lane;
+            const bool valid = j < len;
+            const uint32_t s = valid ? sym[j] : 0u;
+            const uint32_t fs = fr[s], cs = cm[s];
+            const bool need = valid && ((uint64_t)x >= ((uint64_t)fs << 17));
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
+            if (need) {
+                const uint32_t above = __popc(m >> lane) - 1u;  // emitting lanes above this one
+                stack[top - 1 - above] = (uint16_t)(x & 0xFFFFu);
+                x >>= 16;
+            }
+            top -= __popc(m);
+            if (valid) x = ((x / fs) << kProbBits) + (x % fs) + cs;
+        }
+        reinterpret_cast<uint32_t *>(slot)[lane] = x;
+        if (lane == 0) {
+            chunk_words[gc] = chunk - top;
+            chunk_top[gc] = top;
+        }
+    }
+}
+
+// per frame: occupancy section size and final mode (rANS only when smaller than raw)
+__global__ void section_size_kernel(const uint64_t *occ_off, const uint64_t *chunk_off, uint32_t F,
+                                    const uint32_t *chunk_words, uint32_t *chunk_pos, uint32_t *mode,
+                                    uint64_t *sec_bytes)
+{
+    const uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    const uint64_t n = occ_off[f + 1] - occ_off[f];
+    const uint64_t raw = 16 + ((n + 7) & ~7ull);
+    if (mode[f] == 2) {
+        sec_bytes[f] = 16;
+        return;
+    }
+    if (mode[f] == 1) {
+        const uint64_t nch = chunk_off[f + 1] - chunk_off[f];
+        uint64_t t = (16 + 8 + 512 + 4 * nch + 7) & ~7ull;
+        for (uint64_t c = 0; c < nch; ++c) {
+            chunk_pos[chunk_off[f] + c] = (uint32_t)t;
+            t += (128 + 2 * (uint64_t)chunk_words[chunk_off[f] + c] + 3) & ~3ull;
+        }
+        t = (t + 7) & ~7ull;
+        if (t < raw) {
+            sec_bytes[f] = t;
+            return;
+        }
+        mode[f] = 0;
+    }
+    sec_bytes[f] = raw;
+}
+
+// ---- decoder: warp per chunk of one frame -------------------------------
+__global__ void __launch_bounds__(128) decode_kernel(const uint8_t *__restrict__ sec, uint64_t sec_bytes, uint64_t n,
+                                                     uint32_t nch, uint32_t chunk, uint8_t *out, DevState *st)
+{
+    __shared__ uint8_t slot2sym[kM];
+    __shared__ uint16_t fr[256];
+    __shared__ uint32_t cm[256];
+    const uint8_t *ftab = sec + 24;
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int s = 0; s < 256; ++s) {
+            uint16_t v = (uint16_t)(ftab[2 * s] | (ftab[2 * s + 1] << 8));
+            fr[s] = v;
+            cm[s] = acc;
+            acc += v;
+        }
+        if (acc != kM) set_error(&st->err, kErrCorrupt);
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < kM; t += blockDim.x) {  // symbol of each slot: last s with cm[s] <= t
+        uint32_t lo = 0, hi = 256;
+        while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (cm[mid] <= t) lo = mid; else hi = mid;
+        }
+        while (lo > 0 && fr[lo] == 0) --lo;
+        slot2sym[t] = (uint8_t)lo;
+    }
+    __syncthreads();
+    const uint8_t *ctab = sec + 24 + 512;
+    const uint64_t table = (16 + 8 + 512 + 4 * (uint64_t)nch + 7) & ~7ull;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t ltm = lanemask_lt();
+    for (uint32_t c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nch; c += gridDim.x * (blockDim.x >> 5)) {
+        uint64_t off = 0;
+        for (uint32_t k = lane; k < c; k += 32) {
+            const uint8_t *p = ctab + 4 * k;
+            off += (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+        }
+        for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xFFFFFFFFu, off, o);
+        const uint8_t *cp = ctab + 4 * c;
+        const uint32_t cbytes = (uint32_t)cp[0] | ((uint32_t)cp[1] << 8) | ((uint32_t)cp[2] << 16) | ((uint32_t)cp[3] << 24);
+        const uint64_t start = table + off;
+        if (cbytes < 128 || (cbytes & 3) || start + cbytes > sec_bytes) {
+            if (lane == 0) set_error(&st->err, kErrCorrupt);
+            continue;
+        }
+        const uint8_t *ch = sec + start;
+        const uint32_t W = (cbytes - 128) / 2;
+        const uint8_t *wp8 = ch + 128;
+        uint32_t x = (uint32_t)ch[4 * lane] | ((uint32_t)ch[4 * lane + 1] << 8) | ((uint32_t)ch[4 * lane + 2] << 16) |
+                     ((uint32_t)ch[4 * lane + 3] << 24);
+        const uint64_t s0 = (uint64_t)c * chunk;
+        const uint32_t len = (uint32_t)((n - s0) < chunk ? (n - s0) : chunk);
+        uint32_t wp = 0;
+        bool bad = false;
+        for (uint32_t g = 0; g * 32 < len; ++g) {
+            const uint32_t j = g * 32 + lane;
+            const bool valid = j < len;
+            bool need = false;
+            if (valid) {
+                const uint32_t slot = x & (kM - 1);
+                const uint32_t s = slot2sym[slot];
+                out[s0 + j] = (uint8_t)s;
+                x = (uint32_t)fr[s] * (x >> kProbBits) + slot - cm[s];
+                need = x < kL;
+            }
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
+            if (need) {
+                const uint32_t k = wp + __popc(m & ltm);
+                if (k < W) {
+                    x = (x << 16) | (uint32_t)wp8[2 * k] | ((uint32_t)wp8[2 * k + 1] << 8);
+                } else {
+                    bad = true;
+                }
+            }
+            wp += __popc(m);
+        }
+        if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) set_error(&st->err, kErrCorrupt);
+    }
+}
+
+__global__ void fill_kernel(uint8_t *out, uint64_t n, uint8_t v)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = v;
+}
+
+}  // namespace
+
+uint64_t rans_chunk_slot_bytes(uint32_t chunk) { return 128 + 2 * (uint64_t)chunk + 16; }
+
+void launch_rans_encode(const RansFrames &r, DevState *st, uint64_t max_chunks, int num_sms, cudaStream_t s)
+{
+    cudaMemsetAsync(&st->hist[0][0], 0, sizeof(uint32_t) * 256 * r.F, s);
+    dim3 g(num_sms, r.F);
+    if (r.F > 8) g.x = (num_sms * 8 + r.F - 1) / r.F;
+    hist_kernel<<<g, 256, 0, s>>>(r.occ, r.occ_off, st);
+    norm_kernel<<<r.F, 256, 0, s>>>(r.occ_off, st, r.freq, r.cum, r.mode);
+    chunk_offsets_kernel<<<1, 32, 0, s>>>(r.occ_off, r.mode, r.F, r.chunk, r.chunk_off);
+    if (max_chunks) {
+        uint64_t blocks = (max_chunks + 3) / 4;
+        if (blocks > (uint64_t)num_sms * 16) blocks = (uint64_t)num_sms * 16;
+        encode_kernel<<<(uint32_t)blocks, 128, 0, s>>>(r.occ, r.occ_off, r.chunk_off, r.F, r.chunk, r.freq, r.cum,
+                                                        r.chunk_slots, rans_chunk_slot_bytes(r.chunk), r.chunk_words,
+                                                        r.chunk_top);
+    }
+    section_size_kernel<<<(r.F + 63) / 64, 64, 0, s>>>(r.occ_off, r.chunk_off, r.F, r.chunk_words, r.chunk_pos,
+                                                       r.mode, r.sec_bytes);
+}
+
+void launch_rans_decode(const uint8_t *sec, uint64_t sec_bytes, uint64_t n, uint32_t nch, uint32_t chunk,
+                        uint8_t *out, DevState *st, int num_sms, cudaStream_t s)
+{
+    if (nch == 0) return;
+    uint32_t blocks = (nch + 3) / 4;
+    if (blocks > (uint32_t)num_sms * 4) blocks = (uint32_t)num_sms * 4;
+    decode_kernel<<<blocks, 128, 0, s>>>(sec, sec_bytes, n, nch, chunk, out, st);
+}
+
+void launch_fill(uint8_t *out, uint64_t n, uint8_t v, cudaStream_t s)
+{
+    if (n) fill_kernel<<<64, 256, 0, s>>>(out, n, v);
+}
+
+}  // namespace gsnfs

@@ -1,0 +1,420 @@
+// Quantisation and block RLGR entropy coding of RAHT coefficients
+// (Sec. 3.4 "Quantization and Entropy Coding"; App. H, Table A.5).
+//
+// Each attribute channel is cut into blocks of B consecutive coefficients
+// (Morton / in-place order of the transform output) and every block is one
+// independent adaptive run-length Golomb-Rice stream coded by one thread
+// (the paper's block parallelisation).  Threads of a CTA are the channels of
+// one block of rows, so the row-major coefficient matrix is read row by row
+// with coalesced loads; the quantiser (dead-zone / uniform, per group step)
+// is applied on the fly.  RLGR constants (Malvar 2006 reading):
+//   u = zigzag(q); k = K >> 4, kR = KR >> 4; K = 0, KR = 32 at block start.
+//   k == 0: GR(u, kR); u == 0 -> K += 3 (cap 240), else K -= 3 (floor 0).
+//   k >  0: a full run of 2^k zeros -> bit 0, K += 4; r < 2^k zeros then
+//           u != 0 -> bit 1, r in k bits, GR(u - 1, kR), K -= 6; a run cut
+//           by the block end -> bit 0 (the decoder clamps).
+//   GR(v, k): p = v >> k; p < 24 -> p ones, a zero, the k low bits of v;
+//            else 24 ones, 6-bit length n of v, the n bits of v.
+//            p == 0 -> KR -= 2 (floor 0); p > 1 -> KR += p + 1 (cap 384).
+//   Bits are packed least-significant first into 32-bit words; a block ends
+//   on a word boundary.  At most 78 bits per coefficient.
+#include "kernels.cuh"
+
+namespace gsnfs {
+
+namespace {
+
+constexpr int kUnaryEsc = 24;
+
+struct BitWriter {  // words beyond `cap` are counted but not stored
+    uint64_t acc;
+    uint32_t nacc;
+    uint32_t nw;
+    uint32_t *out;
+    uint32_t cap;
+    __device__ __forceinline__ void emit(uint32_t w)
+    {
+        if (nw < cap) out[nw] = w;
+        ++nw;
+    }
+    __device__ __forceinline__ void put(uint64_t v, uint32_t n)  // n <= 32
+    {
+        acc |= v << nacc;
+        nacc += n;
+        if (nacc >= 32) {
+            emit((uint32_t)acc);
+            acc >>= 32;
+            nacc -= 32;
+        }
+    }
+    __device__ __forceinline__ void flush()
+    {
+        if (nacc) {
+            emit((uint32_t)acc);
+            acc = 0;
+            nacc = 0;
+        }
+    }
+};
+
+__device__ __forceinline__ uint32_t zz(int32_t q)
+{
+    return q >= 0 ? ((uint32_t)q << 1) : ((((uint32_t)(-(q + 1))) << 1) | 1u);
+}
+
+__device__ __forceinline__ int32_t unzz(uint32_t u)
+{
+    return (u & 1u) ? -(int32_t)(u >> 1) - 1 : (int32_t)(u >> 1);
+}
+
+__device__ __forceinline__ void gr_put(BitWriter &bw, uint32_t v, uint32_t k, int &KR)
+{
+    const uint32_t p = v >> k;
+    if (p < (uint32_t)kUnaryEsc) {
+        bw.put((1u << p) - 1u, p + 1);  // p ones then a zero
+        if (k) bw.put(v & ((k < 32) ? ((1u << k) - 1u) : 0xFFFFFFFFu), k);
+    } else {
+        const uint32_t n = 32u - (uint32_t)__clz(v);
+        bw.put((1u << kUnaryEsc) - 1u, kUnaryEsc);
+        bw.put(n, 6);
+        bw.put(v, n);
+    }
+    if (p == 0) {
+        KR = KR >= 2 ? KR - 2 : 0;
+    } else if (p > 1) {
+        uint32_t t = (uint32_t)KR + (p > 384u ? 384u : p) + 1u;
+        KR = t > 384u ? 384 : (int)t;
+    }
+}
+
+// Streaming RLGR coder state of one block.
+struct Rlgr {
+    int K, KR;
+    uint32_t z;  // pending zeros of an open run
+    __device__ __forceinline__ void init()
+    {
+        K = 0;
+        KR = 32;
+        z = 0;
+    }
+    __device__ __forceinline__ void code(BitWriter &bw, uint32_t u)
+    {
+        const uint32_t k = (uint32_t)K >> 4;
+        if (k == 0) {
+            gr_put(bw, u, (uint32_t)KR >> 4, KR);
+            if (u == 0) {
+                K += 3;
+                if (K > 240) K = 240;
+            } else {
+                K = K >= 3 ? K - 3 : 0;
+            }
+        } else if (u == 0) {
+            if (++z == (1u << k)) {
+                bw.put(0, 1);
+                K += 4;
+                if (K > 240) K = 240;
+                z = 0;
+            }
+        } else {
+            bw.put(1, 1);
+            bw.put(z, k);
+            gr_put(bw, u - 1u, (uint32_t)KR >> 4, KR);
+            K = K >= 6 ? K - 6 : 0;
+            z = 0;
+        }
+    }
+    __device__ __forceinline__ void finish(BitWriter &bw)
+    {
+        if (z) bw.put(0, 1);
+        bw.flush();
+    }
+};
+
+struct BitReader {
+    const uint32_t *w;
+    uint32_t nw, pos;
+    uint64_t acc;
+    uint32_t nacc;
+    bool bad;
+    __device__ __forceinline__ void refill()
+    {
+        while (nacc <= 32 && pos < nw) {
+            acc |= (uint64_t)w[pos++] << nacc;
+            nacc += 32;
+        }
+    }
+    __device__ __forceinline__ uint32_t get(uint32_t n)  // n <= 32
+    {
+        if (n == 0) return 0;
+        if (nacc < n) refill();
+        if (nacc < n) {
+            bad = true;
+            return 0;
+        }
+        uint32_t v = (uint32_t)(acc & ((n < 32) ? ((1ull << n) - 1) : 0xFFFFFFFFull));
+        acc = (n < 64) ? (acc >> n) : 0;
+        nacc -= n;
+        return v;
+    }
+    // reads a unary prefix: p < 24 ones terminated by a zero, or 24 ones (escape)
+    __device__ __forceinline__ uint32_t ones()
+    {
+        if (nacc < 32) refill();
+        const uint64_t x = ~acc;
+        uint32_t p = x ? (uint32_t)(__ffsll((long long)x) - 1) : 64u;
+        if (p >= (uint32_t)kUnaryEsc) {
+            if (nacc < (uint32_t)kUnaryEsc) {
+                bad = true;
+                return 0;
+            }
+            acc >>= kUnaryEsc;
+            nacc -= kUnaryEsc;
+            return kUnaryEsc;
+        }
+        if (p + 1 > nacc) {
+            bad = true;
+            return 0;
+        }
+        acc >>= (p + 1);
+        nacc -= p + 1;
+        return p;
+    }
+};
+
+__device__ __forceinline__ uint32_t gr_get(BitReader &br, uint32_t k, int &KR)
+{
+    uint32_t p = br.ones();
+    uint32_t v;
+    if (p < (uint32_t)kUnaryEsc) {
+        v = (p << k) | br.get(k);
+    } else {
+        uint32_t n = br.get(6);
+        if (n > 32) {
+            br.bad = true;
+            return 0;
+        }
+        v = br.get(n);
+        p = v >> k;
+    }
+    if (p == 0) {
+        KR = KR >= 2 ? KR - 2 : 0;
+    } else if (p > 1) {
+        uint32_t t = (uint32_t)KR + (p > 384u ? 384u : p) + 1u;
+        KR = t > 384u ? 384 : (int)t;
+    }
+    return v;
+}
+
+// ---- encoder: one CTA per (frame, row block, rung); thread = channel ------
+struct EncJobs {
+    RlgrJob j;
+    const uint64_t *job_off;  // F + 1: first job of each frame (jobs = nb_f * R)
+};
+
+template <bool FROM_INT>
+__global__ void __launch_bounds__(256) rlgr_encode_kernel(EncJobs E, const int32_t *qin)
+{
+    const RlgrJob &j = E.j;
+    const uint64_t job = blockIdx.x;
+    if (job >= E.job_off[j.F]) return;
+    uint32_t lo = 0, hi = j.F;  // frame of this job
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (E.job_off[mid] <= job) lo = mid; else hi = mid;
+    }
+    const uint32_t f = lo;
+    const uint64_t local = job - E.job_off[f];
+    const uint32_t r = (uint32_t)(local % j.R);
+    const uint32_t b = (uint32_t)(local / j.R);
+    const uint32_t vs = j.vstart[f], nv = j.vstart[f + 1] - vs;
+    const uint32_t nb = (nv + j.B - 1) / j.B;
+    const uint32_t row0 = b * j.B;
+    const uint32_t len = (nv - row0) < j.B ? (nv - row0) : j.B;
+    for (uint32_t c = threadIdx.x; c < j.C; c += blockDim.x) {
+        const uint64_t blk = j.blk_off[f] + ((uint64_t)r * j.C + c) * nb + b;
+        BitWriter bw{0ull, 0u, 0u, j.slots + blk * j.slot_words, j.slot_words};
+        Rlgr st;
+        st.init();
+        const float inv = FROM_INT ? 0.f : j.inv_step[r * j.C + c];
+        const uint64_t base = ((uint64_t)vs + row0) * j.C + c;
+        uint32_t i = 0;
+        for (; i + 8 <= len; i += 8) {
+            uint32_t u[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                int32_t q = FROM_INT ? qin[base + (uint64_t)(i + e) * j.C]
+                                     : quantize_f32(j.Y[base + (uint64_t)(i + e) * j.C], inv, j.tau);
+                u[e] = zz(q);
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) st.code(bw, u[e]);
+        }
+        for (; i < len; ++i) {
+            int32_t q = FROM_INT ? qin[base + (uint64_t)i * j.C] : quantize_f32(j.Y[base + (uint64_t)i * j.C], inv, j.tau);
+            st.code(bw, zz(q));
+        }
+        st.finish(bw);
+        j.block_words[blk] = bw.nw;
+        if (bw.nw > j.slot_words) atomicExch(j.overflow, 1u);
+    }
+}
+
+// ---- decoder: thread = channel of one row block of one frame -------------
+template <bool TO_INT>
+__global__ void __launch_bounds__(64) rlgr_decode_kernel(const uint32_t *payload, uint64_t payload_words,
+                                                         const uint32_t *block_words, const uint64_t *block_off,
+                                                         uint32_t stride, uint32_t nv, uint32_t C, uint32_t B,
+                                                         const float *step, float *Y, int32_t *qout, DevState *st)
+{
+    const uint32_t nb = (nv + B - 1) / B;
+    const uint32_t b = blockIdx.x;
+    const uint32_t row0 = b * B;
+    const uint32_t len = (nv - row0) < B ? (nv - row0) : B;
+    for (uint32_t c = threadIdx.x; c < C; c += blockDim.x) {
+        const uint64_t blk = (uint64_t)c * nb + b;
+        const uint64_t off = block_off ? block_off[blk] : blk * stride;
+        uint32_t nw = block_words[blk];
+        if (off + nw > payload_words) {
+            set_error(&st->err, kErrCorrupt);
+            nw = 0;
+        }
+        BitReader br{payload + off, nw, 0u, 0ull, 0u, false};
+        int K = 0, KR = 32;
+        const float sc = TO_INT ? 0.f : step[c];
+        uint32_t i = 0;
+        while (i < len && !br.bad) {
+            const uint32_t k = (uint32_t)K >> 4;
+            if (k == 0) {
+                uint32_t u = gr_get(br, (uint32_t)KR >> 4, KR);
+                int32_t q = unzz(u);
+                const uint64_t o = ((uint64_t)row0 + i) * C + c;
+                if (TO_INT) qout[o] = q; else Y[o] = __fmul_rn((float)q, sc);
+                if (u == 0) {
+                    K += 3;
+                    if (K > 240) K = 240;
+                } else {
+                    K = K >= 3 ? K - 3 : 0;
+                }
+                ++i;
+            } else {
+                uint32_t bit = br.get(1);
+                if (br.bad) break;
+                if (bit == 0) {
+                    uint32_t run = 1u << k;
+                    if (run > len - i) run = len - i;
+                    for (uint32_t t = 0; t < run; ++t) {
+                        const uint64_t o = ((uint64_t)row0 + i + t) * C + c;
+                        if (TO_INT) qout[o] = 0; else Y[o] = 0.0f;
+                    }
+                    i += run;
+                    K += 4;
+                    if (K > 240) K = 240;
+                } else {
+                    uint32_t rr = br.get(k);
+                    uint32_t v = gr_get(br, (uint32_t)KR >> 4, KR);
+                    if (br.bad || rr >= len - i || v == 0xFFFFFFFFu) {
+                        br.bad = true;
+                        break;
+                    }
+                    for (uint32_t t = 0; t < rr; ++t) {
+                        const uint64_t o = ((uint64_t)row0 + i + t) * C + c;
+                        if (TO_INT) qout[o] = 0; else Y[o] = 0.0f;
+                    }
+                    int32_t q = unzz(v + 1u);
+                    const uint64_t o = ((uint64_t)row0 + i + rr) * C + c;
+                    if (TO_INT) qout[o] = q; else Y[o] = __fmul_rn((float)q, sc);
+                    i += rr + 1;
+                    K = K >= 6 ? K - 6 : 0;
+                }
+            }
+        }
+        if (br.bad) set_error(&st->err, kErrCorrupt);
+    }
+}
+
+__global__ void job_offsets_kernel(const uint32_t *vstart, uint32_t F, uint32_t B, uint32_t R, uint32_t C,
+                                   uint64_t *job_off, uint64_t *blk_off)
+{
+    if (threadIdx.x != 0) return;
+    uint64_t jo = 0, bo = 0;
+    for (uint32_t f = 0; f < F; ++f) {
+        job_off[f] = jo;
+        blk_off[f] = bo;
+        uint64_t nb = ((uint64_t)(vstart[f + 1] - vstart[f]) + B - 1) / B;
+        jo += nb * R;
+        bo += nb * R * C;
+    }
+    job_off[F] = jo;
+    blk_off[F] = bo;
+}
+
+}  // namespace
+
+// A slot holds 16 bits per coefficient on average (ample for quantised
+// attribute coefficients); the worst case is 78 bits per coefficient.
+uint32_t rlgr_slot_words(uint32_t B, bool worst_case)
+{
+    return worst_case ? (uint32_t)(((uint64_t)78 * B + 31) / 32 + 2) : (uint32_t)(B / 2 + 4);
+}
+
+void launch_rlgr_offsets(const uint32_t *vstart, uint32_t F, uint32_t B, uint32_t R, uint32_t C, uint64_t *job_off,
+                         uint64_t *blk_off, cudaStream_t s)
+{
+    job_offsets_kernel<<<1, 32, 0, s>>>(vstart, F, B, R, C, job_off, blk_off);
+}
+
+void launch_rlgr_encode(const RlgrJob &j, const uint64_t *job_off, uint64_t jobs_bound, cudaStream_t s)
+{
+    if (jobs_bound == 0 || j.C == 0) return;
+    EncJobs E{j, job_off};
+    uint32_t threads = (j.C + 31) / 32 * 32;
+    if (threads > 256) threads = 256;
+    rlgr_encode_kernel<false><<<(uint32_t)jobs_bound, threads, 0, s>>>(E, nullptr);
+}
+
+void launch_rlgr_encode_indices(const int32_t *q, const uint32_t *vstart, uint32_t C, uint32_t B, uint32_t *slots,
+                                uint32_t slot_words, uint32_t *bw, const uint64_t *job_off, const uint64_t *blk_off,
+                                uint64_t jobs_bound, uint32_t *overflow, cudaStream_t s)
+{
+    if (jobs_bound == 0 || C == 0) return;
+    RlgrJob j{};
+    j.C = C;
+    j.B = B;
+    j.R = 1;
+    j.vstart = vstart;
+    j.F = 1;
+    j.slots = slots;
+    j.block_words = bw;
+    j.blk_off = blk_off;
+    j.slot_words = slot_words;
+    j.overflow = overflow;
+    EncJobs E{j, job_off};
+    uint32_t threads = (C + 31) / 32 * 32;
+    if (threads > 256) threads = 256;
+    rlgr_encode_kernel<true><<<(uint32_t)jobs_bound, threads, 0, s>>>(E, q);
+}
+
+void launch_rlgr_decode(const uint32_t *payload, uint64_t payload_words, const uint32_t *block_words,
+                        const uint64_t *block_off, uint64_t nv, uint32_t C, uint32_t B, const float *step, float *Y,
+                        DevState *st, cudaStream_t s)
+{
+    if (nv == 0 || C == 0) return;
+    uint32_t nb = (uint32_t)((nv + B - 1) / B);
+    uint32_t threads = (C + 31) / 32 * 32;
+    if (threads > 64) threads = 64;
+    rlgr_decode_kernel<false><<<nb, threads, 0, s>>>(payload, payload_words, block_words, block_off, 0u,
+                                                     (uint32_t)nv, C, B, step, Y, nullptr, st);
+}
+
+void launch_rlgr_decode_indices(const uint32_t *words, uint64_t total_words, const uint32_t *bw, uint32_t stride,
+                                uint64_t nv, uint32_t C, uint32_t B, int32_t *q, DevState *st, cudaStream_t s)
+{
+    if (nv == 0 || C == 0) return;
+    uint32_t nb = (uint32_t)((nv + B - 1) / B);
+    uint32_t threads = (C + 31) / 32 * 32;
+    if (threads > 64) threads = 64;
+    rlgr_decode_kernel<true><<<nb, threads, 0, s>>>(words, total_words, bw, nullptr, stride, (uint32_t)nv, C, B,
+                                                    nullptr, nullptr, q, st);
+}
+
+}  // namespace gsnfs

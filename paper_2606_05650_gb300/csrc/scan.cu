@@ -1,0 +1,84 @@
+// Exclusive prefix sums used to lay out variable-length outputs (block word
+// offsets of the RLGR payload).  Reduce-then-scan: no CTA waits on another.
+#include "kernels.cuh"
+
+namespace gsnfs {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Geom {
+    uint32_t P;
+    uint64_t chunk;
+};
+
+Geom geom(uint64_t n, int num_sms)
+{
+    Geom g;
+    uint64_t t = (n + 2047) / 2048;
+    uint64_t pmax = (uint64_t)num_sms * 2;
+    g.P = (uint32_t)(t < 1 ? 1 : (t < pmax ? t : pmax));
+    g.chunk = (n + g.P - 1) / g.P;
+    if (g.chunk == 0) g.chunk = 1;
+    return g;
+}
+
+__global__ void __launch_bounds__(kThreads) up_kernel(const uint32_t *in, uint64_t n, uint64_t chunk, uint64_t *part)
+{
+    uint64_t b = (uint64_t)blockIdx.x * chunk, e = b + chunk;
+    if (e > n) e = n;
+    uint64_t s = 0;
+    for (uint64_t i = b + threadIdx.x; i < e; i += kThreads) s += in[i];
+    __shared__ uint64_t sh[33];
+    uint64_t tot;
+    block_exclusive_sum<uint64_t>(s, sh, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) mid_kernel(uint64_t *part, uint32_t P)
+{
+    __shared__ uint64_t sh[33];
+    uint64_t v = (threadIdx.x < P) ? part[threadIdx.x] : 0ull;
+    uint64_t tot;
+    uint64_t pre = block_exclusive_sum<uint64_t>(v, sh, &tot);
+    if (threadIdx.x < P) part[threadIdx.x] = pre;
+    if (threadIdx.x == 0) part[P] = tot;
+}
+
+__global__ void __launch_bounds__(kThreads) down_kernel(const uint32_t *in, uint64_t n, uint64_t chunk,
+                                                        const uint64_t *part, uint64_t *out)
+{
+    __shared__ uint64_t sh[33];
+    uint64_t b = (uint64_t)blockIdx.x * chunk, e = b + chunk;
+    if (e > n) e = n;
+    uint64_t run = part[blockIdx.x];
+    for (uint64_t t0 = b; t0 < e; t0 += kThreads) {
+        uint64_t i = t0 + threadIdx.x;
+        uint64_t v = (i < e) ? in[i] : 0ull;
+        uint64_t tot;
+        uint64_t pre = block_exclusive_sum<uint64_t>(v, sh, &tot);
+        if (i < e) out[i] = run + pre;
+        run += tot;
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = part[gridDim.x];
+}
+
+}  // namespace
+
+uint64_t scan_partial_words(uint64_t n, int num_sms) { return geom(n, num_sms).P + 1; }
+
+void launch_scan_u32_to_u64(const uint32_t *in, uint64_t n, uint64_t *out, uint64_t *partials, int num_sms,
+                            cudaStream_t s)
+{
+    Geom g = geom(n, num_sms);
+    if (n == 0) {
+        cudaMemsetAsync(out, 0, sizeof(uint64_t), s);
+        return;
+    }
+    up_kernel<<<g.P, kThreads, 0, s>>>(in, n, g.chunk, partials);
+    mid_kernel<<<1, 1024, 0, s>>>(partials, g.P);
+    down_kernel<<<g.P, kThreads, 0, s>>>(in, n, g.chunk, partials, out);
+}
+
+}  // namespace gsnfs

@@ -1,0 +1,177 @@
+// LSD radix sort of (64-bit Morton key, 32-bit point index) pairs
+// (Algorithm 1: "RadixSort" of the Morton codes).  Only the 3J significant
+// key bits (plus the frame-id bits of a batch) are sorted, 8 bits per pass.
+//
+// Each pass is reduce-then-scan: every CTA owns one contiguous chunk of the
+// array, counts its digits (upsweep), one CTA scans the digit-major count
+// matrix, and every CTA re-reads its chunk tile by tile, ranks keys stably
+// with warp match/popc, stages the tile digit-sorted in shared memory and
+// writes it out in runs (downsweep).  No CTA waits on another CTA.
+#include "kernels.cuh"
+
+namespace gsnfs {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kKeysPerThread = 8;
+constexpr int kTile = kThreads * kKeysPerThread;  // 2048
+constexpr int kRadix = 256;
+
+struct SortGeom {
+    uint32_t P;       // CTAs
+    uint64_t chunk;   // elements per CTA
+};
+
+SortGeom sort_geom(uint64_t n, int num_sms)
+{
+    SortGeom g;
+    uint64_t tiles = (n + kTile - 1) / kTile;
+    uint64_t pmax = (uint64_t)num_sms * 2;
+    g.P = (uint32_t)(tiles < 1 ? 1 : (tiles < pmax ? tiles : pmax));
+    g.chunk = (n + g.P - 1) / g.P;
+    return g;
+}
+
+__global__ void __launch_bounds__(kThreads) upsweep_kernel(const uint64_t *__restrict__ keys, uint64_t n,
+                                                           uint32_t shift, uint64_t chunk, uint32_t *hist)
+{
+    __shared__ uint32_t h[kRadix];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    uint64_t b = (uint64_t)blockIdx.x * chunk, e = b + chunk;
+    if (e > n) e = n;
+    for (uint64_t i = b + threadIdx.x; i < e; i += kThreads) atomicAdd(&h[(keys[i] >> shift) & 0xFF], 1u);
+    __syncthreads();
+    hist[(uint64_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of m words in place, one CTA of 1024 threads
+__global__ void __launch_bounds__(1024) scan_kernel(uint32_t *a, uint64_t m)
+{
+    __shared__ uint32_t sh[33];
+    uint64_t per = (m + 1023) / 1024;
+    uint64_t b = per * threadIdx.x, e = b + per;
+    if (e > m) e = m;
+    uint32_t s = 0;
+    for (uint64_t i = b; i < e; ++i) s += a[i];
+    uint32_t tot;
+    uint32_t run = block_exclusive_sum<uint32_t>(s, sh, &tot);
+    for (uint64_t i = b; i < e; ++i) {
+        uint32_t v = a[i];
+        a[i] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) downsweep_kernel(const uint64_t *__restrict__ keys,
+                                                             const uint32_t *__restrict__ vals, uint64_t n,
+                                                             uint32_t shift, uint64_t chunk,
+                                                             const uint32_t *__restrict__ hist,
+                                                             uint64_t *__restrict__ keys_out,
+                                                             uint32_t *__restrict__ vals_out)
+{
+    __shared__ uint32_t s_base[kRadix];
+    __shared__ uint32_t s_wcnt[kWarps][kRadix];
+    __shared__ uint32_t s_tcnt[kRadix];
+    __shared__ uint32_t s_toff[kRadix];
+    __shared__ uint64_t s_keys[kTile];
+    __shared__ uint32_t s_vals[kTile];
+    __shared__ uint32_t s_scan[33];
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    s_base[tid] = hist[(uint64_t)tid * gridDim.x + blockIdx.x];
+    uint64_t cb = (uint64_t)blockIdx.x * chunk, ce = cb + chunk;
+    if (ce > n) ce = n;
+    const uint32_t ltmask = lanemask_lt();
+    for (uint64_t t0 = cb; t0 < ce; t0 += kTile) {
+        for (int i = tid; i < kWarps * kRadix; i += kThreads) (&s_wcnt[0][0])[i] = 0;
+        __syncthreads();
+        uint64_t k[kKeysPerThread];
+        uint32_t v[kKeysPerThread], rk[kKeysPerThread];
+        uint32_t dg[kKeysPerThread];
+#pragma unroll
+        for (int r = 0; r < kKeysPerThread; ++r) {
+            uint64_t p = t0 + (uint64_t)w * (32 * kKeysPerThread) + (uint64_t)r * 32 + lane;
+            bool ok = p < ce;
+            k[r] = ok ? keys[p] : 0ull;
+            v[r] = ok ? vals[p] : 0u;
+            uint32_t d = ok ? (uint32_t)((k[r] >> shift) & 0xFF) : (kRadix + lane);
+            dg[r] = d;
+            uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+            uint32_t before = __popc(peers & ltmask);
+            uint32_t base = ok ? s_wcnt[w][d] : 0u;
+            rk[r] = base + before;
+            __syncwarp();
+            if (ok && before == 0) s_wcnt[w][d] = base + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {  // per digit: exclusive prefix over warps, tile totals
+            uint32_t run = 0;
+#pragma unroll
+            for (int ww = 0; ww < kWarps; ++ww) {
+                uint32_t c = s_wcnt[ww][tid];
+                s_wcnt[ww][tid] = run;
+                run += c;
+            }
+            s_tcnt[tid] = run;
+            uint32_t tot;
+            s_toff[tid] = block_exclusive_sum<uint32_t>(run, s_scan, &tot);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kKeysPerThread; ++r) {
+            if (dg[r] < kRadix) {
+                uint32_t slot = s_toff[dg[r]] + s_wcnt[w][dg[r]] + rk[r];
+                s_keys[slot] = k[r];
+                s_vals[slot] = v[r];
+            }
+        }
+        __syncthreads();
+        uint32_t cnt = (uint32_t)((ce - t0) < (uint64_t)kTile ? (ce - t0) : (uint64_t)kTile);
+        for (uint32_t slot = tid; slot < cnt; slot += kThreads) {
+            uint64_t key = s_keys[slot];
+            uint32_t d = (uint32_t)((key >> shift) & 0xFF);
+            uint64_t op = (uint64_t)s_base[d] + (slot - s_toff[d]);
+            keys_out[op] = key;
+            vals_out[op] = s_vals[slot];
+        }
+        __syncthreads();
+        s_base[tid] += s_tcnt[tid];
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+uint64_t radix_sort_hist_words(uint64_t n, int num_sms)
+{
+    return (uint64_t)kRadix * sort_geom(n, num_sms).P;
+}
+
+bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint32_t *hist,
+                uint64_t n, uint32_t nbits, int num_sms, cudaStream_t s)
+{
+    if (n <= 1 || nbits == 0) return false;
+    SortGeom g = sort_geom(n, num_sms);
+    uint64_t *ki = keys, *ko = keys_alt;
+    uint32_t *vi = vals, *vo = vals_alt;
+    bool flipped = false;
+    for (uint32_t shift = 0; shift < nbits; shift += 8) {
+        upsweep_kernel<<<g.P, kThreads, 0, s>>>(ki, n, shift, g.chunk, hist);
+        scan_kernel<<<1, 1024, 0, s>>>(hist, (uint64_t)kRadix * g.P);
+        downsweep_kernel<<<g.P, kThreads, 0, s>>>(ki, vi, n, shift, g.chunk, hist, ko, vo);
+        uint64_t *tk = ki;
+        ki = ko;
+        ko = tk;
+        uint32_t *tv = vi;
+        vi = vo;
+        vo = tv;
+        flipped = !flipped;
+    }
+    return flipped;
+}
+
+}  // namespace gsnfs

@@ -1,0 +1,366 @@
+"""Python binding of libgsnfs.so (include/gsnfs.h).
+
+Argument marshalling only: every step of the codec runs in the CUDA library.
+Tensors are torch CUDA tensors (PyTorch provides device memory and streams);
+calls are enqueued on torch's current stream of the tensor's device.  The
+library is loaded on first use and a missing or unloadable library raises
+immediately (there is no fallback implementation).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgsnfs.so")
+
+GSNFS_OK = 0
+STATUS = {0: "ok", -1: "invalid argument", -2: "capacity", -3: "corrupt bitstream", -4: "cuda error",
+          -5: "timeout", -6: "out of memory", -7: "unsupported"}
+
+
+class GsnfsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code}: {STATUS.get(code, '?')})")
+        self.code = code
+
+
+class Quant(ct.Structure):
+    _fields_ = [("num_channels", ct.c_uint32), ("num_groups", ct.c_uint32),
+                ("channel_group", ct.POINTER(ct.c_uint8)), ("steps", ct.POINTER(ct.c_double)),
+                ("tau", ct.c_double), ("rlgr_block", ct.c_uint32), ("rans_chunk", ct.c_uint32)]
+
+
+_lock = threading.Lock()
+_lib = None
+_ctx = {}
+
+
+def lib():
+    """Loads libgsnfs.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libgsnfs.so not built ({LIB_PATH}); run paper_2606_05650_gb300/build.py")
+            L = ct.CDLL(LIB_PATH)
+            p, u32, u64, i32 = ct.c_void_p, ct.c_uint32, ct.c_uint64, ct.c_int
+            P64 = ct.POINTER(ct.c_uint64)
+            Q = ct.POINTER(Quant)
+            sig = {
+                "gsnfs_create": ([ct.POINTER(p), i32], i32),
+                "gsnfs_destroy": ([p], None),
+                "gsnfs_status_string": ([i32], ct.c_char_p),
+                "gsnfs_reserve": ([p, u64, u32, u32, Q], i32),
+                "gsnfs_max_bitstream_bytes": ([u64, u32, Q, P64], i32),
+                "gsnfs_encode_frame": ([p, p, p, p, u64, u32, Q, p, u64, P64, p, p, P64], i32),
+                "gsnfs_peek_frame": ([p, u64, P64, ct.POINTER(u32), ct.POINTER(u32)], i32),
+                "gsnfs_decode_frame": ([p, p, p, u64, p, p, u64, P64], i32),
+                "gsnfs_encode_batch": ([p, p, u32, p, p, p, p, u32, p, Q, p, u64, p], i32),
+                "gsnfs_decode_batch": ([p, p, u32, p, p, p, p, u64, p], i32),
+                "gsnfs_voxelize": ([p, p, p, u64, u32, p, p, P64], i32),
+                "gsnfs_octree_encode": ([p, p, p, u64, u32, p, u64, p, P64], i32),
+                "gsnfs_octree_decode": ([p, p, p, u64, u32, p, p], i32),
+                "gsnfs_occupancy_section_encode": ([p, p, p, u64, u32, p, u64, P64], i32),
+                "gsnfs_occupancy_section_decode": ([p, p, p, u64, p, u64], i32),
+                "gsnfs_raht_plan_create": ([p, p, p, u64, u32, u32, ct.POINTER(p)], i32),
+                "gsnfs_raht_plan_destroy": ([p], None),
+                "gsnfs_raht_forward": ([p, p, p, p], i32),
+                "gsnfs_raht_inverse": ([p, p, p, p, Q], i32),
+                "gsnfs_rlgr_slot_words": ([u32], u32),
+                "gsnfs_rlgr_encode_indices": ([p, p, p, u64, u32, u32, p, p], i32),
+                "gsnfs_rlgr_decode_indices": ([p, p, p, p, u64, u32, u32, p], i32),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(code, what):
+    if code != GSNFS_OK:
+        raise GsnfsError(code, f"{what}: {lib().gsnfs_status_string(code).decode()}")
+
+
+def context(device=None):
+    """One library context per CUDA device."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else
+                       (device.index if isinstance(device, torch.device) else int(device)))
+    with _lock:
+        c = _ctx.get(dev.index)
+    if c is None:
+        h = ct.c_void_p()
+        _check(lib().gsnfs_create(ct.byref(h), dev.index), "gsnfs_create")
+        with _lock:
+            _ctx[dev.index] = h
+        c = h
+    return c
+
+
+def _stream(t: torch.Tensor):
+    return ct.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _ptr(t):
+    return ct.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ct.c_void_p(0)
+
+
+def _cuda_f32(t, cols):
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.dim() == 2 and t.shape[1] == cols):
+        raise ValueError(f"expected a contiguous CUDA float32 tensor of shape [N, {cols}]")
+    return t
+
+
+class QuantParams:
+    """Quantisation / entropy parameters (Sec. 3.4): group id per channel, one
+    step per group, rounding offset tau, RLGR block size, rANS chunk size."""
+
+    def __init__(self, groups, steps, tau=0.5, rlgr_block=512, rans_chunk=16384):
+        self.groups = np.ascontiguousarray(np.asarray(groups, dtype=np.uint8).reshape(-1))
+        self.steps = np.ascontiguousarray(np.asarray(steps, dtype=np.float64).reshape(-1))
+        self.tau = float(tau)
+        self.rlgr_block = int(rlgr_block)
+        self.rans_chunk = int(rans_chunk)
+
+    @property
+    def C(self):
+        return int(self.groups.shape[0])
+
+    def struct(self, C=None):
+        C = self.C if C is None else C
+        q = Quant()
+        q.num_channels = C
+        q.num_groups = int(self.steps.shape[0])
+        q.channel_group = self.groups.ctypes.data_as(ct.POINTER(ct.c_uint8))
+        q.steps = self.steps.ctypes.data_as(ct.POINTER(ct.c_double))
+        q.tau = self.tau
+        q.rlgr_block = self.rlgr_block
+        q.rans_chunk = self.rans_chunk
+        return q
+
+
+def geometry_only(rans_chunk=16384):
+    return QuantParams(np.zeros(0, np.uint8), [1.0], rans_chunk=rans_chunk)
+
+
+def max_bitstream_bytes(n, J, qp: QuantParams):
+    out = ct.c_uint64()
+    q = qp.struct()
+    _check(lib().gsnfs_max_bitstream_bytes(n, J, ct.byref(q), ct.byref(out)), "gsnfs_max_bitstream_bytes")
+    return out.value
+
+
+def reserve(n, J, qp: QuantParams, device=None):
+    q = qp.struct()
+    _check(lib().gsnfs_reserve(context(device), n, qp.C, J, ct.byref(q)), "gsnfs_reserve")
+
+
+def encode_frame(pos: torch.Tensor, attr, J: int, qp: QuantParams, recon=False, out=None):
+    """gsnfs_encode_frame.  Returns (bitstream uint8 tensor view, nv, recon_pos, recon_attr)."""
+    _cuda_f32(pos, 3)
+    n = pos.shape[0]
+    C = qp.C
+    if C:
+        _cuda_f32(attr, C)
+        if attr.shape[0] != n:
+            raise ValueError("pos and attr rows differ")
+    cap = max_bitstream_bytes(n, J, qp)
+    if out is None or out.numel() < cap:
+        out = torch.empty(cap, dtype=torch.uint8, device=pos.device)
+    rp = torch.empty((max(n, 1), 3), dtype=torch.float32, device=pos.device) if recon else None
+    ra = torch.empty((max(n, 1), max(C, 1)), dtype=torch.float32, device=pos.device) if recon and C else None
+    q = qp.struct()
+    nbytes, nv = ct.c_uint64(), ct.c_uint64()
+    _check(lib().gsnfs_encode_frame(context(pos.device), _stream(pos), _ptr(pos), _ptr(attr) if C else None, n, J,
+                                    ct.byref(q), _ptr(out), out.numel(), ct.byref(nbytes), _ptr(rp), _ptr(ra),
+                                    ct.byref(nv)), "gsnfs_encode_frame")
+    m = nv.value
+    return (out[: nbytes.value], m, rp[:m] if rp is not None else None,
+            ra[:m, :C] if ra is not None else None)
+
+
+def peek_frame(header: bytes | np.ndarray):
+    h = np.frombuffer(bytes(header), dtype=np.uint8) if not isinstance(header, np.ndarray) else header
+    h = np.ascontiguousarray(h, dtype=np.uint8)
+    nv, C, J = ct.c_uint64(), ct.c_uint32(), ct.c_uint32()
+    _check(lib().gsnfs_peek_frame(h.ctypes.data_as(ct.c_void_p), h.shape[0], ct.byref(nv), ct.byref(C), ct.byref(J)),
+           "gsnfs_peek_frame")
+    return nv.value, C.value, J.value
+
+
+def decode_frame(bitstream: torch.Tensor, with_attr=True):
+    """gsnfs_decode_frame.  Returns (pos [N_v,3], attr [N_v,C] or None)."""
+    if not (bitstream.is_cuda and bitstream.dtype == torch.uint8):
+        raise ValueError("bitstream must be a CUDA uint8 tensor")
+    head = bitstream[:96].cpu().numpy()
+    nv, C, J = peek_frame(head)
+    pos = torch.empty((max(nv, 1), 3), dtype=torch.float32, device=bitstream.device)
+    attr = torch.empty((max(nv, 1), max(C, 1)), dtype=torch.float32, device=bitstream.device) if with_attr and C else None
+    got = ct.c_uint64()
+    _check(lib().gsnfs_decode_frame(context(bitstream.device), _stream(bitstream), _ptr(bitstream), bitstream.numel(),
+                                    _ptr(pos), _ptr(attr), max(nv, 1), ct.byref(got)), "gsnfs_decode_frame")
+    m = got.value
+    return pos[:m], (attr[:m, :C] if attr is not None else None)
+
+
+def encode_batch(pos_list, attr_list, J_list, rung_scales, qp: QuantParams, out=None):
+    """gsnfs_encode_batch: frames x rungs.  Returns (out uint8 tensor, offsets np.uint64[F*R+1])."""
+    F = len(pos_list)
+    R = len(rung_scales)
+    dev = pos_list[0].device
+    C = qp.C
+    for p in pos_list:
+        _cuda_f32(p, 3)
+    if C:
+        for a, p in zip(attr_list, pos_list):
+            _cuda_f32(a, C)
+    cap = 0
+    for p, J in zip(pos_list, J_list):
+        cap += max_bitstream_bytes(p.shape[0], int(J), qp) * R
+    if out is None or out.numel() < cap:
+        out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    hp = (ct.c_void_p * F)(*[p.data_ptr() for p in pos_list])
+    ha = (ct.c_void_p * F)(*[(a.data_ptr() if C else 0) for a in (attr_list if C else pos_list)])
+    hn = (ct.c_uint64 * F)(*[p.shape[0] for p in pos_list])
+    hJ = (ct.c_uint32 * F)(*[int(j) for j in J_list])
+    hs = (ct.c_double * R)(*[float(s) for s in rung_scales])
+    offs = (ct.c_uint64 * (F * R + 1))()
+    q = qp.struct()
+    _check(lib().gsnfs_encode_batch(context(dev), _stream(out), F, hp, ha, hn, hJ, R, hs, ct.byref(q), _ptr(out),
+                                    out.numel(), offs), "gsnfs_encode_batch")
+    return out, np.array(offs[:], dtype=np.uint64)
+
+
+def decode_batch(data: torch.Tensor, offsets, C: int, rows_cap: int):
+    """gsnfs_decode_batch over streams data[offsets[f]:offsets[f+1]].
+    Returns (pos, attr, row offsets)."""
+    F = len(offsets) - 1
+    hin = (ct.c_uint64 * (F + 1))(*[int(o) for o in offsets])
+    rows = (ct.c_uint64 * (F + 1))()
+    pos = torch.empty((max(rows_cap, 1), 3), dtype=torch.float32, device=data.device)
+    attr = torch.empty((max(rows_cap, 1), max(C, 1)), dtype=torch.float32, device=data.device) if C else None
+    _check(lib().gsnfs_decode_batch(context(data.device), _stream(data), F, _ptr(data), hin, _ptr(pos), _ptr(attr),
+                                    rows_cap, rows), "gsnfs_decode_batch")
+    r = np.array(rows[:], dtype=np.uint64)
+    n = int(r[-1])
+    return pos[:n], (attr[:n, :C] if attr is not None else None), r
+
+
+# ---- stage entry points ---------------------------------------------------
+def voxelize(pos: torch.Tensor, J: int):
+    """gsnfs_voxelize: ascending distinct Morton codes and (lo, ext)."""
+    _cuda_f32(pos, 3)
+    n = pos.shape[0]
+    codes = torch.empty(max(n, 1), dtype=torch.int64, device=pos.device)
+    grid = (ct.c_double * 4)()
+    nv = ct.c_uint64()
+    _check(lib().gsnfs_voxelize(context(pos.device), _stream(pos), _ptr(pos), n, J, _ptr(codes), grid, ct.byref(nv)),
+           "gsnfs_voxelize")
+    return codes[: nv.value], np.array(grid[:3]), float(grid[3])
+
+
+def octree_encode(codes: torch.Tensor, J: int):
+    """gsnfs_octree_encode: breadth-first occupancy bytes and level sizes."""
+    nv = codes.shape[0]
+    cap = 8 * max(nv, 1) * J + 64
+    occ = torch.empty(cap, dtype=torch.uint8, device=codes.device)
+    lsz = (ct.c_uint32 * (J + 1))()
+    nb = ct.c_uint64()
+    _check(lib().gsnfs_octree_encode(context(codes.device), _stream(codes), _ptr(codes), nv, J, _ptr(occ), cap, lsz,
+                                     ct.byref(nb)), "gsnfs_octree_encode")
+    return occ[: nb.value], np.array(lsz[:], dtype=np.uint32)
+
+
+def octree_decode(occ: torch.Tensor, J: int, level_sizes):
+    lsz = (ct.c_uint32 * (J + 1))(*[int(x) for x in level_sizes])
+    nv = int(level_sizes[J])
+    codes = torch.empty(max(nv, 1), dtype=torch.int64, device=occ.device)
+    _check(lib().gsnfs_octree_decode(context(occ.device), _stream(occ), _ptr(occ), occ.numel(), J, lsz, _ptr(codes)),
+           "gsnfs_octree_decode")
+    return codes[:nv]
+
+
+def occupancy_section_encode(data: torch.Tensor, rans_chunk=16384):
+    n = data.numel()
+    cap = 64 + 2 * n + 1024 + (n // 32 + 1) * 256
+    out = torch.empty(cap, dtype=torch.uint8, device=data.device)
+    nb = ct.c_uint64()
+    _check(lib().gsnfs_occupancy_section_encode(context(data.device), _stream(data), _ptr(data), n, rans_chunk,
+                                                _ptr(out), cap, ct.byref(nb)), "gsnfs_occupancy_section_encode")
+    return out[: nb.value]
+
+
+def occupancy_section_decode(sec: torch.Tensor, n: int):
+    out = torch.empty(max(n, 1), dtype=torch.uint8, device=sec.device)
+    _check(lib().gsnfs_occupancy_section_decode(context(sec.device), _stream(sec), _ptr(sec), sec.numel(), _ptr(out),
+                                                n), "gsnfs_occupancy_section_decode")
+    return out[:n]
+
+
+class RahtPlan:
+    """gsnfs_raht_plan_*: the butterfly schedule of a voxel set (Sec. 3.2
+    prelude) with forward / inverse transforms (Algorithm 6)."""
+
+    def __init__(self, codes: torch.Tensor, J: int, C: int):
+        self.device = codes.device
+        self.nv = codes.shape[0]
+        self.C = C
+        self.J = J
+        h = ct.c_void_p()
+        _check(lib().gsnfs_raht_plan_create(context(codes.device), _stream(codes), _ptr(codes), self.nv, J, C,
+                                            ct.byref(h)), "gsnfs_raht_plan_create")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.gsnfs_raht_plan_destroy(h)
+            self._h = None
+
+    def _io(self, x):
+        _cuda_f32(x, self.C)
+        if x.shape[0] != self.nv:
+            raise ValueError("row count differs from the plan's voxel count")
+
+    def forward(self, A: torch.Tensor, out=None):
+        self._io(A)
+        out = torch.empty_like(A) if out is None else out
+        _check(lib().gsnfs_raht_forward(self._h, _stream(A), _ptr(A), _ptr(out)), "gsnfs_raht_forward")
+        return out
+
+    def inverse(self, Y: torch.Tensor, out=None, qp: QuantParams | None = None):
+        self._io(Y)
+        out = torch.empty_like(Y) if out is None else out
+        q = qp.struct() if qp is not None else None
+        _check(lib().gsnfs_raht_inverse(self._h, _stream(Y), _ptr(Y), _ptr(out), ct.byref(q) if q is not None else None),
+               "gsnfs_raht_inverse")
+        return out
+
+
+def rlgr_slot_words(B: int) -> int:
+    return int(lib().gsnfs_rlgr_slot_words(B))
+
+
+def rlgr_encode_indices(q: torch.Tensor, B: int):
+    """Block RLGR of int32 indices [nv, C]; returns (slots, block_words)."""
+    nv, C = q.shape
+    nb = (nv + B - 1) // B
+    sw = rlgr_slot_words(B)
+    slots = torch.zeros(max(C * nb * sw, 1), dtype=torch.int32, device=q.device)
+    bw = torch.zeros(max(C * nb, 1), dtype=torch.int32, device=q.device)
+    _check(lib().gsnfs_rlgr_encode_indices(context(q.device), _stream(q), _ptr(q), nv, C, B, _ptr(slots), _ptr(bw)),
+           "gsnfs_rlgr_encode_indices")
+    return slots, bw[: C * nb]
+
+
+def rlgr_decode_indices(slots: torch.Tensor, block_words: torch.Tensor, nv: int, C: int, B: int):
+    q = torch.empty((max(nv, 1), C), dtype=torch.int32, device=slots.device)
+    _check(lib().gsnfs_rlgr_decode_indices(context(slots.device), _stream(slots), _ptr(slots), _ptr(block_words), nv,
+                                           C, B, _ptr(q)), "gsnfs_rlgr_decode_indices")
+    return q[:nv]

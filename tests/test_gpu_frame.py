@@ -1,0 +1,187 @@
+"""Whole-frame parity through gsnfs_encode_frame / gsnfs_decode_frame:
+GPU streams decode in the oracle decoder with the oracle's exact voxel set,
+occupancy bytes and positions; quantised indices equal the oracle's except
+at rounding boundaries (counted, < 1e-6 of all coefficients); GPU decoding of
+any stream matches the oracle's decoding of it; edge cases and corrupt
+streams; the batched frames x rungs path is byte-identical to the plain path.
+"""
+import numpy as np
+import pytest
+
+from paper_2606_05650_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_05650_gb300 import gsnfs
+    return gsnfs
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _qp(G, C, steps=None, **kw):
+    if C == 56:
+        return G.QuantParams(syn.gs_channel_groups(), syn.GS_BASE_STEPS if steps is None else steps, **kw)
+    return G.QuantParams(np.zeros(C, np.uint8), [0.05] if steps is None else steps, **kw)
+
+
+def check_frame(G, orc, pos, attr, J, qp, sample_rows=None):
+    """Encodes on the GPU and checks the stream against the oracle."""
+    n = pos.shape[0]
+    C = qp.C
+    bs, nv, rpos, rattr = G.encode_frame(_dev(pos), _dev(attr) if C else None, J, qp, recon=True)
+    host = bs.cpu().numpy()
+    ref = orc.encode_frame(pos, attr if C else None, J, qp.groups, qp.steps, qp.tau, qp.rlgr_block, qp.rans_chunk,
+                           with_coeffs=True)
+    refbs = ref["bitstream"]
+    assert nv == ref["nv"]
+    # header and occupancy section are integer work: byte-identical
+    hb = int.from_bytes(refbs[8:12].tobytes(), "little")
+    occb = int.from_bytes(refbs[72:80].tobytes(), "little")
+    assert np.array_equal(host[:hb + occb][:72], refbs[:72])
+    assert np.array_equal(host[88:hb + occb], refbs[88:hb + occb])
+    dec = orc.decode_frame(host)  # GPU stream in the oracle decoder
+    assert np.array_equal(dec["codes"], ref["codes"])
+    gpos, gattr = G.decode_frame(bs)
+    assert np.array_equal(gpos.cpu().numpy(), dec["pos"])
+    assert np.array_equal(rpos.cpu().numpy(), dec["pos"])
+    out = {"nv": nv, "bytes": host.size}
+    if C and nv:
+        q_ref, y64 = ref["q"], ref["coeffs"]
+        steps = qp.steps[qp.groups]
+        dis = dec["q"] != q_ref
+        t = np.abs(y64) / steps + qp.tau
+        frac = t - np.floor(t)
+        zone = np.minimum(frac, 1 - frac) < 1e-4
+        assert not (dis & ~zone).any(), "index disagreement outside the rounding-boundary zone"
+        out["disagree"] = int(dis.sum())
+        assert dis.sum() <= max(1e-6 * dis.size, 0) + (1 if dis.size < 1e6 else 0), dis.sum()
+        # GPU decoding of the GPU stream matches the oracle's decoding of the same stream
+        ga = gattr.cpu().numpy().astype(np.float64)
+        scale = np.sqrt((dec["attr"] ** 2).mean(0)) + steps
+        err = np.abs(ga - dec["attr"]) / scale
+        assert err.max() < 1e-4, err.max()
+        # the encoder's reconstruction is the decoder's output
+        assert np.abs(rattr.cpu().numpy() - gattr.cpu().numpy()).max() <= 1e-6 * (1 + np.abs(ga).max())
+    return out
+
+
+@pytest.mark.parametrize("n,J,seed", [(10_000, 10, 0), (3001, 10, 1), (25_000, 16, 2), (999, 21, 3), (500, 1, 4),
+                                      (4000, 2, 5)])
+def test_static_frames(G, orc, n, J, seed):
+    pos, attr = syn.static_gs_frame(seed, n)
+    check_frame(G, orc, pos, attr, J, _qp(G, 56))
+
+
+def test_dynamic_frame_depth16(G, orc):
+    pos, attr = syn.DynamicScene(1).frame(3, n=250_000)
+    out = check_frame(G, orc, pos, attr, 16, _qp(G, 56))
+    assert out["nv"] > 200_000
+
+
+def test_point_cloud_frame_with_duplicates(G, orc):
+    pos, attr = syn.capsule_humanoids_frame(2, 1, 200_000)
+    out = check_frame(G, orc, pos, attr, 10, _qp(G, 3, [0.1]))
+    assert out["nv"] < 200_000  # duplicates merged
+
+
+@pytest.mark.parametrize("C", [1, 3, 11, 35])
+def test_channel_counts(G, orc, C):
+    pos, _ = syn.static_gs_frame(40 + C, 6000)
+    attr = np.random.default_rng(C).normal(0, 1, (6000, C)).astype(np.float32)
+    check_frame(G, orc, pos, attr, 12, _qp(G, C, [0.07]))
+
+
+@pytest.mark.parametrize("B,tau,chunk", [(32, 0.5, 32), (256, 1 / 3, 4096), (4096, 0.5, 16384),
+                                         (65536, 0.25, 1 << 20)])
+def test_block_sizes_deadzone_chunks(G, orc, B, tau, chunk):
+    pos, attr = syn.static_gs_frame(50, 9000)
+    check_frame(G, orc, pos, attr, 11, _qp(G, 56, tau=tau, rlgr_block=B, rans_chunk=chunk))
+
+
+def test_edge_cases(G, orc):
+    qp = _qp(G, 3, [0.1])
+    # empty frame
+    e, nv, _, _ = G.encode_frame(torch.zeros((0, 3), device="cuda"), torch.zeros((0, 3), device="cuda"), 8, qp)
+    assert nv == 0
+    d = orc.decode_frame(e.cpu().numpy())
+    assert d["pos"].shape[0] == 0
+    p, a = G.decode_frame(e)
+    assert p.shape[0] == 0
+    # one point; all points in one voxel
+    check_frame(G, orc, np.array([[0.1, 0.2, 0.3]], np.float32), np.array([[1, 2, 3]], np.float32), 8, qp)
+    pos = np.full((300, 3), 0.5, np.float32)
+    attr = np.random.default_rng(0).normal(size=(300, 3)).astype(np.float32)
+    check_frame(G, orc, pos, attr, 9, qp)
+    # two points that only merge at the last binary level (z siblings)
+    check_frame(G, orc, np.array([[0, 0, 0], [0, 0, 1]], np.float32), np.array([[1, 0, 0], [3, 0, 0]], np.float32),
+                1, qp)
+
+
+def test_geometry_only(G, orc):
+    pos, _ = syn.static_gs_frame(60, 20_000)
+    qp = G.geometry_only()
+    bs, nv, rpos, _ = G.encode_frame(_dev(pos), None, 14, qp, recon=True)
+    ref = orc.encode_frame(pos, None, 14, np.zeros(0, np.uint8), np.array([1.0]))
+    assert np.array_equal(bs.cpu().numpy(), ref["bitstream"])
+    p, a = G.decode_frame(bs)
+    assert a is None and np.array_equal(p.cpu().numpy(), orc.decode_frame(ref["bitstream"])["pos"])
+
+
+def test_oracle_streams_decode_on_gpu(G, orc):
+    pos, attr = syn.static_gs_frame(70, 7000)
+    ref = orc.encode_frame(pos, attr, 10, syn.gs_channel_groups(), syn.GS_BASE_STEPS, with_coeffs=True)
+    p, a = G.decode_frame(_dev(ref["bitstream"]))
+    d = orc.decode_frame(ref["bitstream"])
+    assert np.array_equal(p.cpu().numpy(), d["pos"])
+    scale = np.sqrt((d["attr"] ** 2).mean(0)) + 0.02
+    assert (np.abs(a.cpu().numpy() - d["attr"]) / scale).max() < 1e-4
+
+
+def test_corrupt_streams_fail_cleanly(G, orc):
+    pos, attr = syn.static_gs_frame(80, 5000)
+    bs, *_ = G.encode_frame(_dev(pos), _dev(attr), 10, _qp(G, 56))
+    host = bs.cpu().numpy()
+    for cut in (50, 100, 700, host.size // 2, host.size - 8):
+        with pytest.raises(G.GsnfsError):
+            G.decode_frame(_dev(host[:cut].copy()))
+    rng = np.random.default_rng(0)
+    for _ in range(20):  # random byte flips: error or a valid decode, never a fault
+        bad = host.copy()
+        k = int(rng.integers(96, host.size))
+        bad[k] ^= np.uint8(1 << int(rng.integers(0, 8)))
+        try:
+            G.decode_frame(_dev(bad))
+        except G.GsnfsError:
+            pass
+    torch.cuda.synchronize()
+    # the context still works afterwards
+    check_frame(G, orc, pos[:1000], attr[:1000], 10, _qp(G, 56))
+
+
+def test_batched_ladder_equals_plain(G, orc):
+    sizes = [5000, 120_000, 777, 33_333]
+    Js = [16, 17, 18, 16]
+    frames = [syn.DynamicScene(9).frame(t, n=n) for t, n in enumerate(sizes)]
+    scales = [1.0, 2.0, 4.0]
+    qp = _qp(G, 56)
+    out, offs = G.encode_batch([_dev(p) for p, _ in frames], [_dev(a) for _, a in frames], Js, scales, qp)
+    host = out.cpu().numpy()
+    for f, ((pos, attr), J) in enumerate(zip(frames, Js)):
+        for r, s in enumerate(scales):
+            k = f * len(scales) + r
+            got = host[int(offs[k]):int(offs[k + 1])]
+            qps = _qp(G, 56, syn.GS_BASE_STEPS * s)
+            plain, *_ = G.encode_frame(_dev(pos), _dev(attr), J, qps)
+            assert np.array_equal(got, plain.cpu().numpy()), (f, r)
+    d = orc.decode_frame(host[int(offs[0]):int(offs[1])])
+    assert d["codes"].size > 0
