@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of the GS-NFS per-frame codec on GB300.
+
+Workload: dynamic 3DGS frames of 1,000,000 Gaussians (56 float32 attributes,
+octree depth 16, 5 quantisation groups), seeded synthetic frames shaped like
+the paper's dynamic-scene workloads.  One step = the whole hot path on a
+batch of F frames: batched encode (voxelise, sort, merge, occupancy, rANS,
+RAHT prelude + forward, quantise + RLGR, container) followed by decoding
+every stream (rANS, octree, RLGR, inverse RAHT).  `value` = frames encoded
+AND decoded per second over all ranks, inputs resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gsnfs|reference]
+
+Under torchrun (N > 1) each rank codes its own frames (weak scaling, no
+data-path collective).  `--impl reference` times the FP64 CPU oracle on the
+host cores (the comparison arm).  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encode/decode frames/s at 1M Gaussians, batched vs plain; % HBM roofline"
+UNIT = "frames/s"
+N_GAUSS = 1_000_000
+C = 56
+J = 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gsnfs", choices=["gsnfs", "reference"])
+    ap.add_argument("--frames", type=int, default=8, help="frames per rank per step")
+    ap.add_argument("--block", type=int, default=512, help="RLGR block size")
+    ap.add_argument("--no-extras", action="store_true", help="skip plain-path, e2e and CPU-baseline legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def make_frames(rank, F):
+    from paper_2606_05650_gb300 import synthetic as syn
+    scene = syn.DynamicScene(1000 + rank)
+    return [scene.frame(t, n=N_GAUSS) for t in range(F)]
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    __graft_entry__.build()
+    from paper_2606_05650_gb300 import gsnfs as G, synthetic as syn
+
+    F = args.frames
+    frames = make_frames(rank, F)
+    P = [torch.from_numpy(p).to(dev) for p, _ in frames]
+    A = [torch.from_numpy(a).to(dev) for _, a in frames]
+    qp = G.QuantParams(syn.gs_channel_groups(), syn.GS_BASE_STEPS, rlgr_block=args.block)
+    Js = [J] * F
+    out = None
+
+    def step():
+        nonlocal out
+        out, offs = G.encode_batch(P, A, Js, [1.0], qp, out=out)
+        pos, attr, rows = G.decode_batch(out, offs, C, F * N_GAUSS)
+        return offs, rows
+
+    for _ in range(max(args.warmup, 1)):
+        offs, rows = step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- timed region (device-resident inputs; inputs 1.9 GB per step >> 129 MB L2)
+    G.profile_enable(True)
+    G.profile_read()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = G.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        offs, rows = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = G.launch_count() - l0
+    ck = clocks.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    stages = G.profile_read()
+    G.profile_enable(False)
+    t = torch.tensor([elapsed_ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed_ms = float(t.item())
+    value = world * F * args.steps / (elapsed_ms / 1e3)
+    nv_frames = np.diff(rows).astype(np.int64)
+    stream_bytes = np.diff(offs).astype(np.int64)
+
+    extras = {}
+    if not args.no_extras:
+        extras = gpu_extras(args, G, torch, P, A, frames, qp, out, offs, dev, stream)
+
+    if rank == 0:
+        peaks, src = measured_peaks()
+        hbm = float(peaks["hbm_gbs"])
+        roof = roofline(stages, frames, nv_frames, stream_bytes, args.steps, F, hbm, src)
+        res = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"dynamic 3DGS frames, {N_GAUSS} Gaussians x {C} float32 attributes, depth {J}, "
+                                   f"{F} frames per GPU per step, batched encode + decode of every frame",
+                       "frames_per_step_per_gpu": F, "gaussians_per_frame": N_GAUSS, "channels": C, "depth": J,
+                       "rlgr_block": args.block, "rans_chunk": qp.rans_chunk, "parallelism": f"frames x {world}",
+                       "l2": "inputs 1.9 GB per step > 129 MB L2 (no flush needed)"},
+            "encode_decode_fps": round(value, 2),
+            "voxels_per_frame": int(nv_frames.mean()), "bytes_per_frame": int(stream_bytes.mean()),
+            "bits_per_gaussian": round(8 * float(stream_bytes.mean()) / N_GAUSS, 3),
+            "roofline": roof,
+            "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in stages.items() if v[1]},
+            "gpu_launches": int(launches),
+            "clocks": ck,
+        }
+        res.update(extras)
+        if not args.no_extras:
+            res["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def roofline(stages, frames, nv_frames, stream_bytes, steps, F, hbm, src):
+    """Dominant kernel of the step with its algorithmic bytes per launch."""
+    n_in = sum(p.shape[0] for p, _ in frames)
+    nv = int(nv_frames.sum())
+    comp = int(stream_bytes.sum())
+    # algorithmic bytes per launch (all F frames of one step are one launch)
+    alg = {
+        # cluster average gathered from the N x C input, N_v x C coefficients written
+        "raht_forward_pass0": 4 * C * (n_in + nv),
+        # dequantised coefficients read, attributes written
+        "raht_inverse_pass0": 4 * C * (nv + nv),
+        # coefficients read, compressed attribute payload written
+        "rlgr_encode": 4 * C * nv + comp,
+        # compressed payload read, dequantised coefficients written (per frame launch)
+        "rlgr_decode": comp + 4 * C * nv,
+    }
+    best, best_ms = None, -1.0
+    for k in alg:
+        ms, cnt = stages.get(k, (0.0, 0))
+        if cnt and ms > best_ms:
+            best, best_ms = k, ms
+    if best is None:
+        return None
+    ms, cnt = stages[best]
+    launches_per_step = cnt / steps
+    bytes_per_launch = alg[best] / launches_per_step
+    avg_ms = ms / cnt
+    ach = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    return {"kernel": best, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(ach / hbm, 4), "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)",
+            "traffic": None, "bytes_per_launch": int(bytes_per_launch), "avg_launch_ms": round(avg_ms, 4),
+            "all": {k: {"ms_per_launch": round(stages[k][0] / stages[k][1], 4),
+                        "GBs": round(alg[k] / (stages[k][1] / steps) / (stages[k][0] / stages[k][1] / 1e3) / 1e9, 1),
+                        "frac": round(alg[k] / (stages[k][1] / steps) / (stages[k][0] / stages[k][1] / 1e3) / 1e9 / hbm, 4)}
+                    for k in alg if stages.get(k, (0, 0))[1]}}
+
+
+def gpu_extras(args, G, torch, P, A, frames, qp, out, offs, dev, stream):
+    """Plain one-frame-at-a-time path (fps, p50/p99), batched encode-only and
+    decode-only rates, and the end-to-end rate through host buffers."""
+    import numpy as np
+    F = len(P)
+    res = {}
+    # batched encode only / decode only
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    K = max(2, min(args.steps, 5))
+    ev[0].record(stream)
+    for _ in range(K):
+        out, offs = G.encode_batch(P, A, [J] * F, [1.0], qp, out=out)
+    ev[1].record(stream)
+    for _ in range(K):
+        G.decode_batch(out, offs, C, F * N_GAUSS)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    res["batched"] = {"encode_fps": round(F * K / (ev[0].elapsed_time(ev[1]) / 1e3), 2),
+                      "decode_fps": round(F * K / (ev[1].elapsed_time(ev[2]) / 1e3), 2)}
+    # plain path, one frame per call
+    enc_ms, dec_ms = [], []
+    buf = torch.empty(G.max_bitstream_bytes(N_GAUSS, J, qp), dtype=torch.uint8, device=dev)
+    for rep in range(2):
+        for f in range(F):
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            bs, nv, _, _ = G.encode_frame(P[f], A[f], J, qp, out=buf)
+            b.record(stream)
+            G.decode_frame(bs)
+            c.record(stream)
+            torch.cuda.synchronize()
+            if rep:
+                enc_ms.append(a.elapsed_time(b))
+                dec_ms.append(b.elapsed_time(c))
+    q = lambda v, p: float(np.percentile(v, p))
+    res["plain"] = {"encode_fps": round(1e3 / statistics.mean(enc_ms), 2),
+                    "decode_fps": round(1e3 / statistics.mean(dec_ms), 2),
+                    "encode_decode_fps": round(1e3 / (statistics.mean(enc_ms) + statistics.mean(dec_ms)), 2),
+                    "encode_ms_p50": round(q(enc_ms, 50), 3), "encode_ms_p99": round(q(enc_ms, 99), 3),
+                    "decode_ms_p50": round(q(dec_ms, 50), 3), "decode_ms_p99": round(q(dec_ms, 99), 3)}
+    # end to end: pinned host inputs -> H2D -> encode -> D2H streams -> decode -> D2H frames
+    hp = [torch.from_numpy(p).pin_memory() for p, _ in frames]
+    ha = [torch.from_numpy(a).pin_memory() for _, a in frames]
+    dp = [torch.empty_like(x, device=dev) for x in hp]
+    da = [torch.empty_like(x, device=dev) for x in ha]
+    total = int(offs[-1])
+    hout = torch.empty(out.numel(), dtype=torch.uint8).pin_memory()
+    hpos = torch.empty((F * N_GAUSS, 3), dtype=torch.float32).pin_memory()
+    hatt = torch.empty((F * N_GAUSS, C), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        for x, y in zip(hp + ha, dp + da):
+            y.copy_(x, non_blocking=True)
+        o, off = G.encode_batch(dp, da, [J] * F, [1.0], qp, out=out)
+        n = int(off[-1])
+        hout[:n].copy_(o[:n], non_blocking=True)
+        pos, attr, rows = G.decode_batch(o, off, C, F * N_GAUSS)
+        m = int(rows[-1])
+        hpos[:m].copy_(pos, non_blocking=True)
+        hatt[:m].copy_(attr, non_blocking=True)
+        torch.cuda.synchronize()
+        return n, m
+
+    e2e_step()
+    t0 = time.perf_counter()
+    K2 = max(2, min(args.steps, 5))
+    for _ in range(K2):
+        n, m = e2e_step()
+    dt = (time.perf_counter() - t0) / K2
+    h2d = sum(x.numel() * 4 for x in hp + ha)
+    d2h = n + m * (3 + C) * 4
+    res["e2e"] = {"value": round(F / dt, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                  "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 3)}
+    return res
+
+
+# ------------------------------------------------------------ CPU oracle
+def _oracle_frame(seed_t):
+    """Encode + decode of one 1M-Gaussian frame by the FP64 oracle (one core)."""
+    import numpy as np  # noqa: F401
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as orc
+    from paper_2606_05650_gb300 import synthetic as syn
+    seed, t = seed_t
+    pos, attr = syn.DynamicScene(seed).frame(t, n=N_GAUSS)
+    t0 = time.perf_counter()
+    r = orc.encode_frame(pos, attr, J, syn.gs_channel_groups(), syn.GS_BASE_STEPS)
+    orc.decode_frame(r["bitstream"])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline():
+    """The oracle as it stands, one 1M-Gaussian frame on one host core."""
+    from oracle import oracle as orc
+    orc.build()
+    dt = _oracle_frame((1000, 0))
+    return {"value": round(1.0 / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 frame of {N_GAUSS} Gaussians (encode + decode, FP64 C oracle, single thread), {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Comparison arm: the FP64 oracle on the host cores, frames in parallel."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    from oracle import oracle as orc
+    orc.build()
+    cores = os.cpu_count() or 1
+    workers = max(1, min(cores, 8))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        for w in range(args.warmup):
+            pool.map(_oracle_frame, [(1000 + i, w) for i in range(workers)])
+        t0 = time.perf_counter()
+        busy = 0.0
+        for s in range(args.steps):
+            busy += sum(pool.map(_oracle_frame, [(1000 + i, args.warmup + s) for i in range(workers)]))
+        dt = time.perf_counter() - t0
+    value = workers * args.steps / dt
+    res = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"dynamic 3DGS frames, {N_GAUSS} Gaussians x {C} float32 attributes, depth {J}, "
+                                  f"encode + decode of every frame", "frames_per_step": workers},
+           "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": workers, "kind": "oracle",
+                            "sample": f"{workers} frames per step, one per process ({args.steps} steps)"},
+           "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -197,6 +197,21 @@ gsnfs_status gsnfs_rlgr_decode_indices(gsnfs_ctx *ctx, void *stream, const uint3
                                        const uint32_t *d_block_words, uint64_t nv, uint32_t C, uint32_t B,
                                        int32_t *d_q);
 
+/* ---- instrumentation (no counterpart in the paper) --------------------- */
+
+/* Number of kernels this library has enqueued since it was loaded. */
+uint64_t gsnfs_launch_count(void);
+
+/* Per-stage timing: when enabled, every stage of encode / decode records a
+ * pair of CUDA events on the launching stream.  gsnfs_profile_read
+ * synchronises on the recorded events, returns the accumulated milliseconds
+ * and interval counts per stage (cap entries; names from
+ * gsnfs_profile_stage_names, which returns the number of stages) and resets
+ * the accumulators. */
+gsnfs_status gsnfs_profile_enable(int enable);
+int gsnfs_profile_stage_names(const char **names, int cap);
+gsnfs_status gsnfs_profile_read(double *ms, uint64_t *count, int cap);
+
 #ifdef __cplusplus
 }
 #endif

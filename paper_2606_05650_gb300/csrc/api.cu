@@ -17,7 +17,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -27,6 +29,63 @@
 #include "kernels.cuh"
 
 using namespace gsnfs;
+
+// ---------------------------------------------------- launches / profiling
+namespace {
+std::atomic<uint64_t> g_launches{0};
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    struct Rec {
+        int id;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> open[kStCount];
+    std::vector<Rec> done;
+    double ms[kStCount] = {};
+    uint64_t cnt[kStCount] = {};
+    cudaEvent_t get()
+    {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+Profiler g_prof;
+const char *kStageNames[kStCount] = {"voxelize", "sort", "dedup", "occupancy", "rans", "raht_prelude", "raht_forward",
+                                     "raht_forward_pass0", "rlgr_encode", "container", "reconstruction",
+                                     "occupancy_decode", "octree_decode", "rlgr_decode", "raht_inverse",
+                                     "raht_inverse_pass0"};
+}  // namespace
+
+namespace gsnfs {
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void stage_begin(cudaStream_t s, int id)
+{
+    if (!g_prof.on) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    cudaEvent_t e = g_prof.get();
+    cudaEventRecord(e, s);
+    g_prof.open[id].push_back({id, e, nullptr});
+}
+void stage_end(cudaStream_t s, int id)
+{
+    if (!g_prof.on) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (g_prof.open[id].empty()) return;
+    auto r = g_prof.open[id].back();
+    g_prof.open[id].pop_back();
+    r.b = g_prof.get();
+    cudaEventRecord(r.b, s);
+    g_prof.done.push_back(r);
+}
+}  // namespace gsnfs
 
 struct gsnfs_ctx {
     int device = 0;
@@ -400,6 +459,8 @@ void carve_plan(Carve &cv, RahtPlanDev &p, uint64_t nv_cap, uint32_t T)
     p.cap_tiles = (uint32_t)tiles;
     p.cap_surv = (uint32_t)surv;
     p.pos = cv.take<uint32_t>(elems);
+    p.endseq = cv.take<uint32_t>(elems);
+    p.send = cv.take<uint32_t>(elems);
     p.gapseq = cv.take<uint8_t>(elems);
     p.dest = cv.take<uint32_t>(elems);
     p.tile_nbf = cv.take<uint32_t>(tiles);
@@ -570,25 +631,37 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
     fs.grid = L.grid;
 
     // a1: voxelise + Morton
+    stage_begin(s, kStVoxelize);
     launch_voxelize(fs, dst, N, nmax, L.keys, L.vals, sms, s);
+    stage_end(s, kStVoxelize);
     // a2: radix sort
+    stage_begin(s, kStSort);
     bool alt = radix_sort(L.keys, L.vals, L.keys_alt, L.vals_alt, L.hist, N, nbits, sms, s);
+    stage_end(s, kStSort);
     const uint64_t *skeys = alt ? L.keys_alt : L.keys;
     const uint32_t *svals = alt ? L.vals_alt : L.vals;
     // a3: dedup
+    stage_begin(s, kStDedup);
     launch_dedup(skeys, N, frame_shift, F, L.codes, L.seg, L.gap, L.vstart, L.dpart, dst, sms, s);
+    stage_end(s, kStDedup);
     // a4: octree occupancy
     OccupancyOut oo{L.occ, L.occ_cap, L.lsz, L.occ_off, L.hoff, L.opart};
+    stage_begin(s, kStOccupancy);
     launch_occupancy(L.codes, L.gap, L.vstart, L.Jd, F, frame_shift, oo, dst, sms, s);
+    stage_end(s, kStOccupancy);
     // a5: occupancy rANS
     RansFrames rf{F, L.occ, L.occ_off, q->rans_chunk, L.chunk_off, L.freq, L.cum, L.mode, L.chunk_words,
                   L.chunk_top, L.chunk_pos, L.chunk_slots, L.sec_bytes};
+    stage_begin(s, kStRans);
     launch_rans_encode(rf, dst, L.max_chunks, sms, s);
+    stage_end(s, kStRans);
 
     HdrParams hpar{F, R, C, G, C ? q->rlgr_block : 1u, q->rans_chunk, q->tau, rq.capacity};
     if (C) {
         // a6: RAHT prelude; a7: forward transform with the cluster average fused into the first pass
+        stage_begin(s, kStPrelude);
         launch_raht_prelude(L.plan, L.gap, dst, nullptr, sms, s);
+        stage_end(s, kStPrelude);
         RahtIO io{};
         io.C = C;
         io.seg = L.seg;
@@ -598,7 +671,9 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
         io.frame_shift = frame_shift;
         io.Y = L.Y;
         io.pool = L.pool;
+        stage_begin(s, kStRahtFwd);
         launch_raht_forward(L.plan, io, N, sms, s);
+        stage_end(s, kStRahtFwd);
         // a8 + a9: quantise + block RLGR for every rung
         launch_rlgr_offsets(L.vstart, F, q->rlgr_block, R, C, L.job_off, L.blk_off, s);
         RlgrJob j{};
@@ -615,23 +690,32 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
         j.blk_off = L.blk_off;
         j.slot_words = L.slot_words;
         j.overflow = L.overflow;
+        stage_begin(s, kStRlgrEnc);
         launch_rlgr_encode(j, L.job_off, L.jobs_bound, s);
+        stage_end(s, kStRlgrEnc);
         launch_scan_u32_to_u64(L.block_words, L.blocks_bound, L.block_off, L.spart, sms, s);
     }
     // a10: container
+    stage_begin(s, kStContainer);
     sizes_kernel<<<1, 32, 0, s>>>(hpar, L.Jd, L.vstart, L.sec_bytes, L.blk_off, L.block_off, L.si, dst);
+    count_launch();
     header_kernel<<<F * R, 128, 0, s>>>(hpar, L.Jd, L.vstart, L.grid, L.lsz, L.groups, L.steps_rg, L.si, dst,
                                         rq.out);
+    count_launch();
     OccCopyArgs oa{L.occ, L.occ_off, L.mode, L.chunk_off, L.freq, L.chunk_words, L.chunk_top, L.chunk_pos,
                    L.chunk_slots, rans_chunk_slot_bytes(q->rans_chunk)};
     occ_copy_kernel<<<dim3(std::max<uint32_t>(1, (uint32_t)sms * 2 / (F * R)), F * R), 256, 0, s>>>(hpar, oa, L.si,
                                                                                                   dst, rq.out);
+    count_launch();
     if (C) {
         AttrCopyArgs aa{L.vstart, L.blk_off, L.block_off, L.block_words, L.slots, L.slot_words};
         attr_copy_kernel<<<dim3(std::max<uint32_t>(1, (uint32_t)sms * 4 / (F * R)), F * R), 256, 0, s>>>(
             hpar, aa, L.si, dst, rq.out);
+        count_launch();
     }
+    stage_end(s, kStContainer);
     // a13: optional reconstruction (first frame, first rung)
+    stage_begin(s, kStRecon);
     if (F == 1 && rq.recon_pos) launch_voxel_centres_batch(L.codes, dst, N, frame_shift, L.Jd, L.grid, rq.recon_pos, s);
     if (F == 1 && C && rq.recon_attr) {
         RahtIO io{};
@@ -645,6 +729,7 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
         io.frame_shift = frame_shift;
         launch_raht_inverse(L.plan, io, N, sms, s);
     }
+    stage_end(s, kStRecon);
     CK(cudaGetLastError());
     // results
     uint64_t *res = (uint64_t *)(hp + ((o_end + 63) & ~(size_t)63));
@@ -856,32 +941,42 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
     // a11: occupancy bytes
     const uint8_t *sec = d_in + P.hb;
     const uint8_t *occ = L.occ;
+    stage_begin(s, kStOccDecode);
     if (P.occ_mode == 0)
         occ = sec + 16;
     else if (P.occ_mode == 2)
         launch_fill(L.occ, P.n_occ, (uint8_t)P.occ_aux, s);
     else
         launch_rans_decode(sec, P.occ_bytes, P.n_occ, P.occ_aux, P.chunk, L.occ, dst, sms, s);
+    stage_end(s, kStOccDecode);
+    stage_begin(s, kStOctreeDecode);
     launch_octree_decode(occ, P.n_occ, P.J, P.lsz, L.nodes, L.pref, L.ppart, L.codes, dst, sms, s);
     if (d_pos) launch_voxel_centres(L.codes, P.nv, P.J, L.grid, d_pos, s);
+    stage_end(s, kStOctreeDecode);
     // a12: attributes
     if (P.C && d_attr) {
+        stage_begin(s, kStPrelude);
         launch_gap_levels(L.codes, P.nv, L.gap, s);
         launch_raht_prelude(L.plan, L.gap, dst, L.nvdev, sms, s);
+        stage_end(s, kStPrelude);
         const uint8_t *as = d_in + P.hb + P.occ_bytes;
         const uint32_t *bw = reinterpret_cast<const uint32_t *>(as + 8);
         const uint64_t nblk = (uint64_t)P.C * P.nb;
         const uint32_t *payload = bw + nblk;
         const uint64_t payload_words = (P.attr_bytes - 8 - 4 * nblk) / 4;
         launch_scan_u32_to_u64(bw, nblk, L.block_off, L.spart, sms, s);
+        stage_begin(s, kStRlgrDec);
         launch_rlgr_decode(payload, payload_words, bw, L.block_off, P.nv, P.C, P.B, L.step, L.Y, dst, s);
+        stage_end(s, kStRlgrDec);
         RahtIO io{};
         io.C = P.C;
         io.Y = L.Y;
         io.out = d_attr;
         io.pool = L.pool;
         io.frame_shift = 64;
+        stage_begin(s, kStRahtInv);
         launch_raht_inverse(L.plan, io, P.nv, sms, s);
+        stage_end(s, kStRahtInv);
     }
     CK(cudaGetLastError());
     uint32_t *res = (uint32_t *)(hp + 1024);
@@ -1321,9 +1416,11 @@ gsnfs_status gsnfs_occupancy_section_encode(gsnfs_ctx *ctx, void *stream, const 
     RansFrames rf{1, d_in, occ_off, rans_chunk, chunk_off, freq, cum, mode, cw, ct, cp, slots, sec};
     launch_rans_encode(rf, ctx->st, nch, ctx->num_sms, s);
     stage_si_kernel<<<1, 1, 0, s>>>(sec, si, ctx->st);
+    count_launch();
     HdrParams hpar{1, 1, 0, 0, 1, rans_chunk, 0.5, capacity};
     OccCopyArgs oa{d_in, occ_off, mode, chunk_off, freq, cw, ct, cp, slots, rans_chunk_slot_bytes(rans_chunk)};
     occ_copy_kernel<<<dim3(ctx->num_sms, 1), 256, 0, s>>>(hpar, oa, si, ctx->st, d_out);
+    count_launch();
     CK(cudaMemcpyAsync(hp + 8, sec, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
@@ -1535,6 +1632,48 @@ gsnfs_status gsnfs_rlgr_decode_indices(gsnfs_ctx *ctx, void *stream, const uint3
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
     return map_dev_error(((uint32_t *)ctx->pinned)[0]);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+uint64_t gsnfs_launch_count(void) { return g_launches.load(); }
+
+gsnfs_status gsnfs_profile_enable(int enable)
+{
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.on = enable != 0;
+    return GSNFS_OK;
+}
+
+int gsnfs_profile_stage_names(const char **names, int cap)
+{
+    for (int i = 0; i < cap && i < kStCount; ++i) names[i] = kStageNames[i];
+    return kStCount;
+}
+
+gsnfs_status gsnfs_profile_read(double *ms, uint64_t *count, int cap)
+{
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    for (auto &r : g_prof.done) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess) return GSNFS_ERR_CUDA;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            g_prof.ms[r.id] += t;
+            g_prof.cnt[r.id] += 1;
+        }
+        g_prof.pool.push_back(r.a);
+        g_prof.pool.push_back(r.b);
+    }
+    g_prof.done.clear();
+    for (int i = 0; i < cap && i < kStCount; ++i) {
+        if (ms) ms[i] = g_prof.ms[i];
+        if (count) count[i] = g_prof.cnt[i];
+        g_prof.ms[i] = 0;
+        g_prof.cnt[i] = 0;
+    }
+    return GSNFS_OK;
 }
 
 }  // extern "C"

@@ -414,11 +414,15 @@ void launch_dedup(const uint64_t *keys, uint64_t n, uint32_t frame_shift, uint32
         cudaMemsetAsync(gap, (int)kInfLevel, 1, s);
     } else {
         dedup_up_kernel<<<c.P, kThreads, 0, s>>>(keys, n, c.chunk, partials);
+        count_launch();
         scan_total_kernel<<<1, 1024, 0, s>>>(partials, c.P);
+        count_launch();
         dedup_down_kernel<<<c.P, kThreads, 0, s>>>(keys, n, c.chunk, partials, frame_shift, codes, seg, gap,
                                                    vstart);
+        count_launch();
     }
     dedup_fix_kernel<<<1, 1, 0, s>>>(partials, c.P, vstart, F, st);
+    count_launch();
 }
 
 uint64_t occupancy_partial_words(uint32_t F, int num_sms) { return (uint64_t)F * occ_x(F, num_sms) * kH; }
@@ -431,10 +435,14 @@ void launch_occupancy(const uint64_t *codes, const uint8_t *gap, const uint32_t 
     uint32_t X = occ_x(F, num_sms);
     dim3 grid(X, F);
     occ_up_kernel<<<grid, kThreads, 0, s>>>(gap, vstart, J, o.partials);
+    count_launch();
     occ_scan_kernel<<<1, 1024, 0, s>>>(o.partials, X, F, vstart, J, o.level_sizes, o.hoff, o.occ_off);
+    count_launch();
     zero_words_kernel<<<num_sms * 2, 256, 0, s>>>((uint32_t *)o.occ, o.occ_off + F, o.occ_capacity / 4);
+    count_launch();
     occ_down_kernel<<<grid, kThreads, 0, s>>>(codes, gap, vstart, J, o.partials, o.hoff, o.occ_off,
                                               (uint32_t *)o.occ, o.occ_capacity, st);
+    count_launch();
 }
 
 uint64_t octree_decode_node_words(const uint32_t *h_level_sizes, uint32_t J)
@@ -451,15 +459,20 @@ void launch_octree_decode(const uint8_t *occ, uint64_t n_occ, uint32_t J, const 
     if (h_level_sizes[0] == 0) return;
     Chunks c = chunks_for(n_occ, num_sms);
     popc_up_kernel<<<c.P, kThreads, 0, s>>>(occ, n_occ, c.chunk, partials);
+    count_launch();
     scan_total_kernel<<<1, 1024, 0, s>>>(partials, c.P);
+    count_launch();
     popc_down_kernel<<<c.P, kThreads, 0, s>>>(occ, n_occ, c.chunk, partials, pref);
+    count_launch();
     root_kernel<<<1, 1, 0, s>>>(nodes);
+    count_launch();
     uint64_t noff = 0, boff = 0;
     for (uint32_t d = 0; d < J; ++d) {
         uint32_t Md = h_level_sizes[d], Md1 = h_level_sizes[d + 1];
         uint64_t *Ld = nodes + noff;
         uint64_t *Ld1 = (d + 1 == J) ? leaves : nodes + noff + Md;
         expand_kernel<<<grid_for(Md, num_sms), kThreads, 0, s>>>(Ld, Md, occ, boff, pref, Ld1, Md1, st);
+        count_launch();
         noff += Md;
         boff += Md;
     }
@@ -468,6 +481,7 @@ void launch_octree_decode(const uint8_t *occ, uint64_t n_occ, uint32_t J, const 
 void launch_gap_levels(const uint64_t *codes, uint64_t nv, uint8_t *gap, cudaStream_t s)
 {
     gap_kernel<<<grid_for(nv + 1, 152), kThreads, 0, s>>>(codes, nv, gap);
+    count_launch();
 }
 
 void launch_voxel_centres(const uint64_t *codes, uint64_t nv, uint32_t J, const FrameGrid *grid, float *pos,
@@ -476,6 +490,7 @@ void launch_voxel_centres(const uint64_t *codes, uint64_t nv, uint32_t J, const 
     (void)J;
     if (nv == 0) return;
     centres_kernel<<<grid_for(nv, 152), kThreads, 0, s>>>(codes, nv, grid, pos);
+    count_launch();
 }
 
 void launch_voxel_centres_batch(const uint64_t *codes, const DevState *st, uint64_t nv_bound,
@@ -485,6 +500,7 @@ void launch_voxel_centres_batch(const uint64_t *codes, const DevState *st, uint6
     (void)J;
     if (nv_bound == 0) return;
     centres_batch_kernel<<<grid_for(nv_bound, 152), kThreads, 0, s>>>(codes, st, frame_shift, grid, pos);
+    count_launch();
 }
 
 }  // namespace gsnfs

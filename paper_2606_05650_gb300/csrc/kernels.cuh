@@ -7,6 +7,17 @@
 
 namespace gsnfs {
 
+// Every kernel launch of the library is counted (gsnfs_launch_count).
+void count_launch();
+
+// Optional per-stage timing with CUDA events on the launching stream.
+enum StageId {
+    kStVoxelize, kStSort, kStDedup, kStOccupancy, kStRans, kStPrelude, kStRahtFwd, kStRahtFwd0, kStRlgrEnc,
+    kStContainer, kStRecon, kStOccDecode, kStOctreeDecode, kStRlgrDec, kStRahtInv, kStRahtInv0, kStCount
+};
+void stage_begin(cudaStream_t s, int id);
+void stage_end(cudaStream_t s, int id);
+
 // Device description of a batch of frames (F = 1 for the plain path).
 struct FrameSet {
     uint32_t F;
@@ -86,8 +97,10 @@ struct RahtPlanDev {  // device pointers of a plan
     uint32_t cap_elems;    // capacity of the pooled sequence arrays
     uint32_t cap_tiles;
     uint32_t cap_surv;     // rows in the survivor pool
-    uint32_t *pos;         // pooled sequence arrays
-    uint8_t *gapseq;
+    uint32_t *pos;         // pooled sequence arrays: first voxel of each element,
+    uint32_t *endseq;      // one past its last voxel,
+    uint32_t *send;        // (scratch) subtree end of each carried survivor,
+    uint8_t *gapseq;       // gap level to the previous element
     uint32_t *dest;
     uint32_t *tile_nbf;    // per tile: number of butterflies
     uint32_t *tile_nr;     // per tile: number of rounds

@@ -50,11 +50,18 @@ __device__ __forceinline__ uint8_t seq_gap(const PreludeArgs &a, const RahtPass 
     return q == 0 ? a.gap0[j] : a.p.gapseq[ps.seq_off + j];
 }
 
+// one past the last voxel covered by element j (its subtree is contiguous)
+__device__ __forceinline__ uint32_t seq_end(const RahtPlanDev &p, const RahtPass &ps, int q, uint64_t j)
+{
+    return q == 0 ? (uint32_t)(j + 1) : p.endseq[ps.seq_off + j];
+}
+
 struct PreludeSmem {
     uint8_t g[4097];
     uint8_t flags[4096];  // bit0 in-tile gap, bit1 survivor
     uint8_t carry[4096];  // carried to the next pass
     uint32_t p[4097];
+    uint32_t e[4096];
     uint16_t prv[4096];
     uint16_t nxt[4096];
     uint32_t lvl_cnt[kRounds + 1];
@@ -74,6 +81,7 @@ __device__ void prelude_tile(const PreludeArgs &a, PreludeSmem &S, int q, const 
     for (uint32_t i = tid; i <= m; i += kThreads) {
         S.g[i] = seq_gap(a, ps, q, j0 + i);
         S.p[i] = seq_pos(p, ps, q, j0 + i);
+        if (i < m) S.e[i] = seq_end(p, ps, q, j0 + i);
     }
     for (int i = tid; i <= kRounds; i += kThreads) S.lvl_cnt[i] = 0;
     __syncthreads();
@@ -117,8 +125,9 @@ __device__ void prelude_tile(const PreludeArgs &a, PreludeSmem &S, int q, const 
             p.tile_nbf[ps.tile_off + t] = tot;
             p.tile_nr[ps.tile_off + t] = nr;
         }
-        for (int l = tid; l <= kRounds; l += 32) S.lvl_cnt[l] = 0;  // reused as fill counters
     }
+    __syncthreads();
+    for (int l = tid; l <= kRounds; l += kThreads) S.lvl_cnt[l] = 0;  // reused as fill counters
     __syncthreads();
     // butterflies, survivors, destinations
     const uint64_t sbase = (uint64_t)(ps.tile_off + t) * T;
@@ -126,8 +135,12 @@ __device__ void prelude_tile(const PreludeArgs &a, PreludeSmem &S, int q, const 
         const uint8_t f = S.flags[i];
         uint8_t c = 0;
         if (f & 1) {
+            // children cover elements [l, i) and [i, r); neither range crosses a frame
+            // boundary, so their voxels are contiguous.  The right end is taken from
+            // the last element's own end: a frame finished in an earlier pass may have
+            // been dropped between this frame and the element at r.
             uint32_t l = S.prv[i], r = S.nxt[i];
-            uint32_t w0 = S.p[i] - S.p[l], w1 = S.p[r] - S.p[i];
+            uint32_t w0 = S.p[i] - S.p[l], w1 = S.e[r - 1] - S.p[i];
             float fw0 = (float)w0, fw1 = (float)w1, fs = (float)(w0 + w1);
             float ca = __fsqrt_rn(__fdiv_rn(fw0, fs)), cb = __fsqrt_rn(__fdiv_rn(fw1, fs));
             uint32_t slot = S.lvl_off[S.g[i]] + atomicAdd(&S.lvl_cnt[S.g[i]], 1u);
@@ -138,10 +151,12 @@ __device__ void prelude_tile(const PreludeArgs &a, PreludeSmem &S, int q, const 
             // survivor: a frame root (final) iff both bounding gaps are frame boundaries
             uint32_t r = i + 1;
             while (r < m && !(S.flags[r] & 2)) ++r;
-            if (S.g[i] >= kInfLevel && S.g[r] >= kInfLevel)
+            if (S.g[i] >= kInfLevel && S.g[r] >= kInfLevel) {
                 p.dest[ps.seq_off + j0 + i] = S.p[i];
-            else
+            } else {
                 c = 1;
+                p.send[ps.seq_off + j0 + i] = S.e[r - 1];  // the survivor's subtree ends with element r-1
+            }
         }
         S.carry[i] = c;
     }
@@ -229,6 +244,7 @@ __device__ void prelude_compact_body(const PreludeArgs &a, int q, uint64_t first
             p.dest[ps.seq_off + j] = kCarry | gi;
             p.pos[nx.seq_off + gi] = seq_pos(p, ps, q, j);
             p.gapseq[nx.seq_off + gi] = seq_gap(a, ps, q, j);
+            p.endseq[nx.seq_off + gi] = p.send[ps.seq_off + j];
         }
     }
     if (first == 0 && nx.n) {
@@ -496,6 +512,7 @@ void launch_pass(const XformArgs &A, int q, uint32_t grid, size_t smem, cudaStre
     auto k = xform_pass_kernel<INV, VEC, GATHER, QDQ>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<grid, kThreads, smem, s>>>(A, q);
+    count_launch();
 }
 
 template <bool INV, int VEC, bool QDQ>
@@ -504,6 +521,7 @@ void launch_finish(const XformArgs &A, int q0, size_t smem, cudaStream_t s)
     auto k = xform_finish_kernel<INV, VEC, QDQ>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<1, kThreads, smem, s>>>(A, q0);
+    count_launch();
 }
 
 template <int VEC>
@@ -515,10 +533,12 @@ void forward_all(const XformArgs &A, uint64_t nv_bound, int num_sms, cudaStream_
     uint32_t grid0 = (uint32_t)(tiles < 1 ? 1 : (tiles < (uint64_t)num_sms * 4 ? tiles : (uint64_t)num_sms * 4));
     for (int q = 0; q < kRahtMultiPasses; ++q) {
         uint32_t g = q == 0 ? grid0 : (grid0 < (uint32_t)num_sms ? grid0 : (uint32_t)num_sms);
+        if (q == 0) stage_begin(s, kStRahtFwd0);
         if (q == 0 && A.io.seg)
             launch_pass<false, VEC, true, false>(A, q, g, smem, s);
         else
             launch_pass<false, VEC, false, false>(A, q, g, smem, s);
+        if (q == 0) stage_end(s, kStRahtFwd0);
     }
     launch_finish<false, VEC, false>(A, kRahtMultiPasses, smem, s);
 }
@@ -537,10 +557,12 @@ void inverse_all(const XformArgs &A, uint64_t nv_bound, int num_sms, cudaStream_
         launch_finish<true, VEC, false>(A, kRahtMultiPasses, smem, s);
     for (int q = kRahtMultiPasses - 1; q >= 0; --q) {
         uint32_t g = q == 0 ? grid0 : (grid0 < (uint32_t)num_sms ? grid0 : (uint32_t)num_sms);
+        if (q == 0) stage_begin(s, kStRahtInv0);
         if (qd)
             launch_pass<true, VEC, false, true>(A, q, g, smem, s);
         else
             launch_pass<true, VEC, false, false>(A, q, g, smem, s);
+        if (q == 0) stage_end(s, kStRahtInv0);
     }
 }
 
@@ -575,13 +597,18 @@ void launch_raht_prelude(const RahtPlanDev &p, const uint8_t *gap, const DevStat
     cudaFuncSetAttribute(prelude_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(prelude_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     prelude_init_kernel<<<1, 32, 0, s>>>(p, st, nv_dev);
+    count_launch();
     uint32_t grid = (uint32_t)num_sms * 4;
     for (int q = 0; q < kRahtMultiPasses; ++q) {
         prelude_tiles_kernel<<<grid, kThreads, smem, s>>>(a, q);
+        count_launch();
         prelude_scan_kernel<<<1, 1024, 0, s>>>(p, q);
+        count_launch();
         prelude_compact_kernel<<<grid, kThreads, 0, s>>>(a, q);
+        count_launch();
     }
     prelude_finish_kernel<<<1, kThreads, smem, s>>>(a, kRahtMultiPasses);
+    count_launch();
 }
 
 void launch_raht_forward(const RahtPlanDev &p, const RahtIO &io, uint64_t nv_bound, int num_sms, cudaStream_t s)

@@ -264,17 +264,22 @@ void launch_rans_encode(const RansFrames &r, DevState *st, uint64_t max_chunks, 
     dim3 g(num_sms, r.F);
     if (r.F > 8) g.x = (num_sms * 8 + r.F - 1) / r.F;
     hist_kernel<<<g, 256, 0, s>>>(r.occ, r.occ_off, st);
+    count_launch();
     norm_kernel<<<r.F, 256, 0, s>>>(r.occ_off, st, r.freq, r.cum, r.mode);
+    count_launch();
     chunk_offsets_kernel<<<1, 32, 0, s>>>(r.occ_off, r.mode, r.F, r.chunk, r.chunk_off);
+    count_launch();
     if (max_chunks) {
         uint64_t blocks = (max_chunks + 3) / 4;
         if (blocks > (uint64_t)num_sms * 16) blocks = (uint64_t)num_sms * 16;
         encode_kernel<<<(uint32_t)blocks, 128, 0, s>>>(r.occ, r.occ_off, r.chunk_off, r.F, r.chunk, r.freq, r.cum,
                                                         r.chunk_slots, rans_chunk_slot_bytes(r.chunk), r.chunk_words,
                                                         r.chunk_top);
+        count_launch();
     }
     section_size_kernel<<<(r.F + 63) / 64, 64, 0, s>>>(r.occ_off, r.chunk_off, r.F, r.chunk_words, r.chunk_pos,
                                                        r.mode, r.sec_bytes);
+    count_launch();
 }
 
 void launch_rans_decode(const uint8_t *sec, uint64_t sec_bytes, uint64_t n, uint32_t nch, uint32_t chunk,
@@ -284,11 +289,15 @@ void launch_rans_decode(const uint8_t *sec, uint64_t sec_bytes, uint64_t n, uint
     uint32_t blocks = (nch + 3) / 4;
     if (blocks > (uint32_t)num_sms * 4) blocks = (uint32_t)num_sms * 4;
     decode_kernel<<<blocks, 128, 0, s>>>(sec, sec_bytes, n, nch, chunk, out, st);
+    count_launch();
 }
 
 void launch_fill(uint8_t *out, uint64_t n, uint8_t v, cudaStream_t s)
 {
-    if (n) fill_kernel<<<64, 256, 0, s>>>(out, n, v);
+    if (n) {
+        fill_kernel<<<64, 256, 0, s>>>(out, n, v);
+        count_launch();
+    }
 }
 
 }  // namespace gsnfs

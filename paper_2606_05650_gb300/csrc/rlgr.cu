@@ -361,6 +361,7 @@ void launch_rlgr_offsets(const uint32_t *vstart, uint32_t F, uint32_t B, uint32_
                          uint64_t *blk_off, cudaStream_t s)
 {
     job_offsets_kernel<<<1, 32, 0, s>>>(vstart, F, B, R, C, job_off, blk_off);
+    count_launch();
 }
 
 void launch_rlgr_encode(const RlgrJob &j, const uint64_t *job_off, uint64_t jobs_bound, cudaStream_t s)
@@ -370,6 +371,7 @@ void launch_rlgr_encode(const RlgrJob &j, const uint64_t *job_off, uint64_t jobs
     uint32_t threads = (j.C + 31) / 32 * 32;
     if (threads > 256) threads = 256;
     rlgr_encode_kernel<false><<<(uint32_t)jobs_bound, threads, 0, s>>>(E, nullptr);
+    count_launch();
 }
 
 void launch_rlgr_encode_indices(const int32_t *q, const uint32_t *vstart, uint32_t C, uint32_t B, uint32_t *slots,
@@ -392,6 +394,7 @@ void launch_rlgr_encode_indices(const int32_t *q, const uint32_t *vstart, uint32
     uint32_t threads = (C + 31) / 32 * 32;
     if (threads > 256) threads = 256;
     rlgr_encode_kernel<true><<<(uint32_t)jobs_bound, threads, 0, s>>>(E, q);
+    count_launch();
 }
 
 void launch_rlgr_decode(const uint32_t *payload, uint64_t payload_words, const uint32_t *block_words,
@@ -404,6 +407,7 @@ void launch_rlgr_decode(const uint32_t *payload, uint64_t payload_words, const u
     if (threads > 64) threads = 64;
     rlgr_decode_kernel<false><<<nb, threads, 0, s>>>(payload, payload_words, block_words, block_off, 0u,
                                                      (uint32_t)nv, C, B, step, Y, nullptr, st);
+    count_launch();
 }
 
 void launch_rlgr_decode_indices(const uint32_t *words, uint64_t total_words, const uint32_t *bw, uint32_t stride,
@@ -415,6 +419,7 @@ void launch_rlgr_decode_indices(const uint32_t *words, uint64_t total_words, con
     if (threads > 64) threads = 64;
     rlgr_decode_kernel<true><<<nb, threads, 0, s>>>(words, total_words, bw, nullptr, stride, (uint32_t)nv, C, B,
                                                     nullptr, nullptr, q, st);
+    count_launch();
 }
 
 }  // namespace gsnfs

@@ -77,8 +77,11 @@ void launch_scan_u32_to_u64(const uint32_t *in, uint64_t n, uint64_t *out, uint6
         return;
     }
     up_kernel<<<g.P, kThreads, 0, s>>>(in, n, g.chunk, partials);
+    count_launch();
     mid_kernel<<<1, 1024, 0, s>>>(partials, g.P);
+    count_launch();
     down_kernel<<<g.P, kThreads, 0, s>>>(in, n, g.chunk, partials, out);
+    count_launch();
 }
 
 }  // namespace gsnfs

@@ -161,8 +161,11 @@ bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *va
     bool flipped = false;
     for (uint32_t shift = 0; shift < nbits; shift += 8) {
         upsweep_kernel<<<g.P, kThreads, 0, s>>>(ki, n, shift, g.chunk, hist);
+        count_launch();
         scan_kernel<<<1, 1024, 0, s>>>(hist, (uint64_t)kRadix * g.P);
+        count_launch();
         downsweep_kernel<<<g.P, kThreads, 0, s>>>(ki, vi, n, shift, g.chunk, hist, ko, vo);
+        count_launch();
         uint64_t *tk = ki;
         ki = ko;
         ko = tk;

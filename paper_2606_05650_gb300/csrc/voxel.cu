@@ -140,15 +140,23 @@ void launch_voxelize(const FrameSet &fs, DevState *st, uint64_t n_total, uint64_
                      uint32_t *vals, int num_sms, cudaStream_t s)
 {
     init_bbox_kernel<<<1, 256, 0, s>>>(st, fs.F);
+    count_launch();
     // X blocks per frame: enough for the largest frame, ~4 CTAs per SM overall
     uint64_t want = (n_max + kThreads - 1) / kThreads;
     uint64_t cap = (uint64_t)num_sms * 4 / fs.F;
     if (cap < 16) cap = 16;
     uint32_t X = (uint32_t)(want < 1 ? 1 : (want > cap ? cap : want));
     dim3 grid(X, fs.F);
-    if (n_total > 0) bbox_kernel<<<grid, kThreads, 0, s>>>(fs, st);
+    if (n_total > 0) {
+        bbox_kernel<<<grid, kThreads, 0, s>>>(fs, st);
+        count_launch();
+    }
     grid_kernel<<<1, 64, 0, s>>>(fs, st);
-    if (n_total > 0) morton_kernel<<<grid, kThreads, 0, s>>>(fs, keys, vals);
+    count_launch();
+    if (n_total > 0) {
+        morton_kernel<<<grid, kThreads, 0, s>>>(fs, keys, vals);
+        count_launch();
+    }
 }
 
 }  // namespace gsnfs

@@ -74,6 +74,10 @@ def lib():
                 "gsnfs_rlgr_slot_words": ([u32], u32),
                 "gsnfs_rlgr_encode_indices": ([p, p, p, u64, u32, u32, p, p], i32),
                 "gsnfs_rlgr_decode_indices": ([p, p, p, p, u64, u32, u32, p], i32),
+                "gsnfs_launch_count": ([], u64),
+                "gsnfs_profile_enable": ([i32], i32),
+                "gsnfs_profile_stage_names": ([ct.POINTER(ct.c_char_p), i32], i32),
+                "gsnfs_profile_read": ([ct.POINTER(ct.c_double), ct.POINTER(ct.c_uint64), i32], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -364,3 +368,24 @@ def rlgr_decode_indices(slots: torch.Tensor, block_words: torch.Tensor, nv: int,
     _check(lib().gsnfs_rlgr_decode_indices(context(slots.device), _stream(slots), _ptr(slots), _ptr(block_words), nv,
                                            C, B, _ptr(q)), "gsnfs_rlgr_decode_indices")
     return q[:nv]
+
+
+# ---- instrumentation ----------------------------------------------------------
+def launch_count() -> int:
+    """Kernels enqueued by the library since it was loaded."""
+    return int(lib().gsnfs_launch_count())
+
+
+def profile_enable(on: bool = True):
+    _check(lib().gsnfs_profile_enable(1 if on else 0), "gsnfs_profile_enable")
+
+
+def profile_read():
+    """{stage: (total ms, intervals)} since the last read (synchronises)."""
+    n = lib().gsnfs_profile_stage_names(None, 0) if False else 32
+    names = (ct.c_char_p * n)()
+    k = lib().gsnfs_profile_stage_names(names, n)
+    ms = (ct.c_double * k)()
+    cnt = (ct.c_uint64 * k)()
+    _check(lib().gsnfs_profile_read(ms, cnt, k), "gsnfs_profile_read")
+    return {names[i].decode(): (ms[i], int(cnt[i])) for i in range(k)}

@@ -36,14 +36,13 @@ def gs_channel_groups(C: int = GS_CHANNELS) -> np.ndarray:
 
 def gs_attributes(rng: np.random.Generator, n: int) -> np.ndarray:
     """N x 56 float32 attributes with the 3DGS distributions."""
-    a = np.empty((n, GS_CHANNELS), dtype=np.float32)
-    a[:, 0:3] = rng.normal(-4.0, 0.5, size=(n, 3))
-    q = rng.normal(0.0, 1.0, size=(n, 4))
-    q /= np.maximum(np.linalg.norm(q, axis=1, keepdims=True), 1e-12)
-    a[:, 3:7] = q
-    a[:, 7] = rng.normal(0.0, 2.0, size=n)
-    a[:, 8:11] = rng.normal(0.0, 0.5, size=(n, 3))
-    a[:, 11:56] = rng.normal(0.0, 0.05, size=(n, 45))
+    a = rng.standard_normal((n, GS_CHANNELS), dtype=np.float32)
+    a[:, 0:3] = a[:, 0:3] * np.float32(0.5) - np.float32(4.0)      # log-scale N(-4, 0.5)
+    q = a[:, 3:7]
+    q /= np.maximum(np.sqrt((q * q).sum(1, keepdims=True)), np.float32(1e-12))  # unit quaternion
+    a[:, 7] *= np.float32(2.0)                                      # opacity logit N(0, 2)
+    a[:, 8:11] *= np.float32(0.5)                                   # SH DC N(0, 0.5)
+    a[:, 11:56] *= np.float32(0.05)                                 # SH AC N(0, 0.05)
     return a
 
 
