@@ -909,7 +909,7 @@ size_t carve_decode(Carve &cv, DecLayout &L, const ParsedHeader &P, int num_sms)
 gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, uint64_t bytes, float *d_pos,
                          float *d_attr, uint64_t capacity_nv, uint64_t *out_nv)
 {
-    ParsedHeader P;
+    ParsedHeader P{};
     gsnfs_status st = read_headers(ctx, s, d_in, bytes, P);
     if (st) return st;
     if (out_nv) *out_nv = P.nv;
@@ -1147,7 +1147,7 @@ gsnfs_status gsnfs_peek_frame(const uint8_t *h_header, uint64_t bytes, uint64_t 
                               uint32_t *out_J)
 {
     if (!h_header) return GSNFS_ERR_INVALID_ARG;
-    ParsedHeader P;
+    ParsedHeader P{};
     if (bytes < 96 || rd32(h_header) != kMagic || rd32(h_header + 4) != 1) return GSNFS_ERR_CORRUPT;
     P.J = rd32(h_header + 12);
     P.C = rd32(h_header + 16);
@@ -1178,7 +1178,7 @@ gsnfs_status gsnfs_decode_batch(gsnfs_ctx *ctx, void *stream, uint32_t frames, c
     uint64_t row = 0;
     h_out_rows[0] = 0;
     for (uint32_t f = 0; f < frames; ++f) {
-        ParsedHeader P;
+        ParsedHeader P{};
         const uint64_t b = h_in_offsets[f], e = h_in_offsets[f + 1];
         if (e < b) return GSNFS_ERR_INVALID_ARG;
         gsnfs_status st = read_headers(ctx, s, d_in + b, e - b, P);
@@ -1337,7 +1337,7 @@ gsnfs_status gsnfs_octree_decode(gsnfs_ctx *ctx, void *stream, const uint8_t *d_
     if (!ctx || J < 1 || J > (uint32_t)kMaxJ || !h_level_sizes) return GSNFS_ERR_INVALID_ARG;
     DeviceGuard dg(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    ParsedHeader P;
+    ParsedHeader P{};
     P.J = J;
     P.nv = h_level_sizes[J];
     P.n_occ = 0;
@@ -1440,7 +1440,7 @@ gsnfs_status gsnfs_occupancy_section_decode(gsnfs_ctx *ctx, void *stream, const 
     uint8_t *hp = ctx->pinned;
     CK(cudaMemcpyAsync(hp, d_sec, sec_bytes < 24 ? 16 : 24, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    ParsedHeader P;
+    ParsedHeader P{};
     P.n_occ = n;
     P.occ_bytes = sec_bytes;
     P.C = 0;

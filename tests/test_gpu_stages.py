@@ -89,7 +89,7 @@ def test_octree_decode_rejects_corrupt(G, orc):
     with pytest.raises(G.GsnfsError):
         G.octree_decode(bad, 8, lsz)
     bad2 = occ.clone()
-    bad2[5] = 0xFF
+    bad2[5] ^= 1  # changes the popcount of one byte: the level sizes no longer add up
     with pytest.raises(G.GsnfsError):
         G.octree_decode(bad2, 8, lsz)
 
@@ -153,6 +153,7 @@ def test_raht_energy_and_dc_on_gpu(G, orc):
 
 
 def test_raht_inverse_with_quantiser(G, orc):
+    # encoder reconstruction: quantise -> dequantise -> inverse (Sec. 3.4, Algorithm 6)
     pos, attr = syn.static_gs_frame(30, 8000)
     J = 10
     codes, A, _, _, _ = orc.voxelize(pos, attr, J)
@@ -160,12 +161,20 @@ def test_raht_inverse_with_quantiser(G, orc):
     plan = G.RahtPlan(_dev(codes.astype(np.int64)), J, 56)
     Y = plan.forward(_dev(A.astype(np.float32)))
     R = plan.inverse(Y, qp=qp).cpu().numpy().astype(np.float64)
-    Y64 = orc.raht_forward(codes, A, J)
+    # the indices the FP32 path takes: floor(|y| * (1/step) + tau) in FP32, each op rounded
+    y32 = Y.cpu().numpy()
     steps = syn.GS_BASE_STEPS[syn.gs_channel_groups()]
-    Q = orc.quantize(Y64, syn.gs_channel_groups(), syn.GS_BASE_STEPS)
-    R64 = orc.raht_inverse(codes, Q * steps, J)
-    # tolerance: indices may differ only at rounding boundaries; compare where they agree in every coefficient
-    assert np.abs(R - R64).max() < 1e-3
+    inv32 = (1.0 / steps).astype(np.float32)
+    q = np.floor((np.abs(y32) * inv32).astype(np.float32) + np.float32(0.5)) * np.sign(y32)
+    # they agree with the FP64 oracle's indices except at rounding boundaries
+    Y64 = orc.raht_forward(codes, A, J)
+    q64 = orc.quantize(Y64, syn.gs_channel_groups(), syn.GS_BASE_STEPS)
+    t = np.abs(Y64) / steps + 0.5
+    zone = np.minimum(t - np.floor(t), np.ceil(t) - t) < 1e-4
+    assert not ((q != q64) & ~zone).any()
+    R64 = orc.raht_inverse(codes, q * steps, J)
+    scale = np.sqrt((R64 ** 2).mean(0)) + steps
+    assert (np.abs(R - R64) / scale).max() < 1e-4
 
 
 @pytest.mark.parametrize("nv,C,B", [(1, 1, 32), (1000, 3, 64), (5000, 56, 512), (4097, 7, 4096), (30000, 2, 256)])
