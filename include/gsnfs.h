@@ -197,6 +197,34 @@ gsnfs_status gsnfs_rlgr_decode_indices(gsnfs_ctx *ctx, void *stream, const uint3
                                        const uint32_t *d_block_words, uint64_t nv, uint32_t C, uint32_t B,
                                        int32_t *d_q);
 
+/* ---- allocation-free occupancy encoder (no counterpart in the paper) ---- */
+
+/* Largest voxel count gsnfs_octree_encode_static accepts. */
+#define GSNFS_STATIC_MAX_VOXELS 1048576u
+
+/* The occupancy bytes and level sizes of gsnfs_octree_encode, computed
+ * without allocating anything: for callers that may not allocate device
+ * memory while running (hosts that give all device memory to their own pool
+ * at start-up, real-time loops that cannot take the synchronisation and
+ * locks of cudaMalloc / cudaFree).  Needs no context.  Its scratch is one
+ * fixed device array of about 1.2 MB that the library reserves on every GPU
+ * that loads it, kept until the process exits.
+ *   d_codes       nv distinct ascending Morton codes (device), nv <=
+ *                 GSNFS_STATIC_MAX_VOXELS, else GSNFS_ERR_UNSUPPORTED
+ *   d_occ         output bytes (device, 4-byte aligned); written in whole
+ *                 32-bit words, so occ_capacity must cover the byte count
+ *                 rounded up to 4 (else GSNFS_ERR_CAPACITY, with the byte
+ *                 count in *out_occ_bytes)
+ *   h_level_sizes J + 1 level sizes (host)
+ * Runs on the current CUDA device and synchronises `stream` before it
+ * returns.  The first call on a device looks up the array's device address;
+ * make that first call before any stream capture.  All calls on a device
+ * share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller. */
+gsnfs_status gsnfs_octree_encode_static(void *stream, const uint64_t *d_codes, uint64_t nv, uint32_t J,
+                                        uint8_t *d_occ, uint64_t occ_capacity, uint32_t *h_level_sizes,
+                                        uint64_t *out_occ_bytes);
+
 /* ---- instrumentation (no counterpart in the paper) --------------------- */
 
 /* Number of kernels this library has enqueued since it was loaded. */
