@@ -121,7 +121,7 @@ gsnfs_status gsnfs_decode_frame(gsnfs_ctx *ctx, void *stream, const uint8_t *d_b
  * d_out[h_offsets[f*rungs + r] .. h_offsets[f*rungs + r + 1]).
  * h_pos/h_attr are host arrays of `frames` device pointers; h_n, h_J host
  * arrays of length `frames`; h_offsets (host) has frames*rungs + 1 entries.
- * frames <= 64, rungs <= 8. */
+ * frames <= 64, rungs <= 8, rungs x channels <= 1024. */
 gsnfs_status gsnfs_encode_batch(gsnfs_ctx *ctx, void *stream, uint32_t frames, const float *const *h_pos,
                                 const float *const *h_attr, const uint64_t *h_n, const uint32_t *h_J,
                                 uint32_t rungs, const double *h_rung_scale, const gsnfs_quant *q,
@@ -185,9 +185,9 @@ gsnfs_status gsnfs_raht_inverse(gsnfs_raht_plan *plan, void *stream, const float
                                 const gsnfs_quant *q);
 
 /* Block RLGR of int32 quantisation indices (Sec. 3.4): d_q is nv x C
- * row-major; each channel is cut into blocks of B coefficients and block
- * (c, b) (nb = ceil(nv / B) blocks per channel) is one RLGR stream written at
- * d_slots + (c * nb + b) * gsnfs_rlgr_slot_words(B); d_block_words[c*nb+b]
+ * row-major; each channel is cut into blocks of B coefficients and block b of
+ * channel c (nb = ceil(nv / B) blocks per channel) is one RLGR stream written
+ * at d_slots + (b * C + c) * gsnfs_rlgr_slot_words(B); d_block_words[b*C+c]
  * receives its length in 32-bit words.  Decoding reads the same layout and
  * writes d_q (GSNFS_ERR_CORRUPT on a malformed block). */
 uint32_t gsnfs_rlgr_slot_words(uint32_t B);
@@ -207,7 +207,7 @@ gsnfs_status gsnfs_rlgr_decode_indices(gsnfs_ctx *ctx, void *stream, const uint3
  * memory while running (hosts that give all device memory to their own pool
  * at start-up, real-time loops that cannot take the synchronisation and
  * locks of cudaMalloc / cudaFree).  Needs no context.  Its scratch is one
- * fixed device array of about 1.2 MB that the library reserves on every GPU
+ * fixed device array of about 1.3 MB that the library reserves on every GPU
  * that loads it, kept until the process exits.
  *   d_codes       nv distinct ascending Morton codes (device), nv <=
  *                 GSNFS_STATIC_MAX_VOXELS, else GSNFS_ERR_UNSUPPORTED

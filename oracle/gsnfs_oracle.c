@@ -987,7 +987,7 @@ int64_t orc_occ_section_decode(const uint8_t *in, int64_t nbytes, uint8_t *occ, 
  *   occupancy section (above).
  *   attribute section (absent when C == 0 or N_v == 0):
  *     u32 B (coefficients per block), u32 nb = ceil(N_v / B),
- *     u32 block_words[C * nb] (channel-major: c * nb + b),
+ *     u32 block_words[nb * C] (block-major: b * C + c),
  *     payload words in the same order, pad to 8.
  *   Coefficients of channel c in Morton (in-place) order are cut into
  *   blocks of B; each block is one RLGR stream.                           */
@@ -1063,12 +1063,12 @@ int64_t orc_encode_frame(const float *pos, const float *attr, int64_t n, int C, 
         put32(attrsec, B);
         put32(attrsec + 4, (uint32_t)nb);
         int64_t pw = 8 + 4 * (int64_t)C * nb;
-        for (int c = 0; c < C; ++c)
-            for (int64_t b = 0; b < nb; ++b) {
+        for (int64_t b = 0; b < nb; ++b)
+            for (int c = 0; c < C; ++c) {
                 int64_t s0 = b * B;
                 int64_t len = (nv - s0 < (int64_t)B) ? nv - s0 : (int64_t)B;
                 int64_t w = orc_rlgr_encode(Q + (size_t)s0 * C + c, len, C, blk, blk_cap);
-                put32(attrsec + 8 + 4 * ((int64_t)c * nb + b), (uint32_t)w);
+                put32(attrsec + 8 + 4 * (b * C + c), (uint32_t)w);
                 if (pw + 4 * w + 8 > total_cap) {
                     int64_t ncap = 2 * total_cap + 4 * w + 16;
                     uint8_t *grown = (uint8_t *)realloc(attrsec, (size_t)ncap);
@@ -1189,10 +1189,10 @@ int64_t orc_decode_frame(const uint8_t *in, int64_t nbytes, int64_t cap_nv, floa
         uint32_t *w = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(attr_bytes / 4 + 1));
         for (int64_t t = 0; t < attr_bytes / 4; ++t) w[t] = get32(as + 4 * t);
         int64_t pw = 2 + (int64_t)C * nb;
-        for (int c = 0; c < C; ++c)
-            for (int64_t b = 0; b < nb; ++b) {
+        for (int64_t b = 0; b < nb; ++b)
+            for (int c = 0; c < C; ++c) {
                 int64_t len = (nv - b * B < (int64_t)B) ? nv - b * B : (int64_t)B;
-                int64_t bw = w[2 + (int64_t)c * nb + b];
+                int64_t bw = w[2 + b * C + c];
                 if (pw + bw > attr_bytes / 4 ||
                     orc_rlgr_decode(w + pw, bw, len, C, Q + (size_t)b * B * C + c) != ORC_OK) {
                     free(Q); free(w); free(codes);

@@ -13,7 +13,7 @@
 //     symbols, u32 0, u16 freq[256], u32 chunk_bytes[], pad 8, chunks
 //     (32 u32 states + u16 words, padded to 4); rANS only when smaller.
 //   attribute section (C > 0 and N_v > 0): u32 B, u32 nb, u32
-//     block_words[C*nb] (channel-major), payload words, pad 8.
+//     block_words[nb*C] (block-major: b*C + c), payload words, pad 8.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -482,12 +482,12 @@ size_t carve_encode(Carve &cv, EncLayout &L, const EncodeReq &rq, int num_sms, b
         uint64_t ob = occ_bound(rq.n[f], rq.J[f]);
         occ_cap += ob;
         max_chunks += (ob + rq.q->rans_chunk - 1) / rq.q->rans_chunk;
-        jobs += (uint64_t)R * ((rq.n[f] + rq.q->rlgr_block - 1) / rq.q->rlgr_block);
+        jobs += (rq.n[f] + rq.q->rlgr_block - 1) / rq.q->rlgr_block;  // row blocks (all rungs in one CTA)
     }
     L.occ_cap = (occ_cap + 64) & ~(uint64_t)63;
     L.max_chunks = max_chunks;
     L.jobs_bound = C ? jobs : 0;
-    L.blocks_bound = L.jobs_bound * C;
+    L.blocks_bound = L.jobs_bound * C * R;
     L.slot_words = rlgr_slot_words(rq.q->rlgr_block, worst_slots);
     L.grid = cv.take<FrameGrid>(F);
     L.Jd = cv.take<uint32_t>(F);
@@ -1112,6 +1112,7 @@ gsnfs_status gsnfs_encode_batch(gsnfs_ctx *ctx, void *stream, uint32_t frames, c
         return GSNFS_ERR_INVALID_ARG;
     gsnfs_status st = check_quant(q);
     if (st) return st;
+    if ((uint64_t)rungs * q->num_channels > 1024) return GSNFS_ERR_UNSUPPORTED;  // rungs x channels threads per block
     for (uint32_t f = 0; f < frames; ++f) {
         if (h_J[f] < 1 || h_J[f] > 19) return GSNFS_ERR_INVALID_ARG;
         if (h_n[f] > 0 && !h_pos[f]) return GSNFS_ERR_INVALID_ARG;

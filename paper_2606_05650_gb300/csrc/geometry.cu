@@ -136,51 +136,54 @@ __global__ void __launch_bounds__(kThreads) occ_up_kernel(const uint8_t *__restr
         for (int h = 1; h <= s; ++h) atomicAdd(&cnt[h], 1u);
     }
     __syncthreads();
-    if (threadIdx.x < kH) partials[((uint64_t)f * X + x) * kH + threadIdx.x] = cnt[threadIdx.x];
+    if (threadIdx.x < kH) partials[((uint64_t)f * kH + threadIdx.x) * X + x] = cnt[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(1024) occ_scan_kernel(uint32_t *partials, uint32_t X, uint32_t F,
-                                                        const uint32_t *__restrict__ vstart,
-                                                        const uint32_t *__restrict__ Jarr, uint32_t *lsz,
-                                                        uint32_t *hoff, uint64_t *occ_off)
+// one CTA of 32 x kH threads per frame: warp h scans the CTA counts of height h
+// (exclusive, in place), then level sizes and byte offsets of the frame
+__global__ void __launch_bounds__(32 * kH) occ_scan_kernel(uint32_t *partials, uint32_t X,
+                                                           const uint32_t *__restrict__ vstart,
+                                                           const uint32_t *__restrict__ Jarr, uint32_t *lsz,
+                                                           uint32_t *hoff, uint64_t *nocc)
 {
-    __shared__ uint64_t nocc[kMaxFrames];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (uint32_t f = w; f < F; f += 32) {
+    __shared__ uint32_t tot[kH];
+    const uint32_t f = blockIdx.x, lane = threadIdx.x & 31, h = threadIdx.x >> 5;
+    uint32_t *row = partials + ((uint64_t)f * kH + h) * X;
+    uint32_t run = 0;
+    for (uint32_t b = 0; b < X; b += 32) {
+        const uint32_t x = b + lane;
+        const uint32_t v = (x < X) ? row[x] : 0u;
+        const uint32_t inc = warp_inclusive_sum(v);
+        if (x < X) row[x] = run + inc - v;
+        run += __shfl_sync(0xFFFFFFFFu, inc, 31);
+    }
+    if (lane == 0) tot[h] = run;
+    __syncthreads();
+    if (h == 0) {
         const uint32_t J = Jarr[f];
-        uint32_t tot = 0;
-        if (lane >= 1 && lane < kH) {
-            for (uint32_t x = 0; x < X; ++x) {
-                uint32_t *p = partials + ((uint64_t)f * X + x) * kH + lane;
-                uint32_t t = *p;
-                *p = tot;
-                tot += t;
-            }
-        }
         // bytes of height h come after all heights above it (depth 0 first)
-        uint32_t sz = (lane >= 1 && lane <= (int)J) ? tot : 0u;
+        const uint32_t sz = (lane >= 1 && lane <= J && lane < kH) ? tot[lane] : 0u;
         uint32_t above = 0;
         for (int h2 = 31; h2 >= 1; --h2) {
-            uint32_t t = __shfl_sync(0xFFFFFFFFu, sz, h2);
-            if (h2 > lane) above += t;
+            const uint32_t t = __shfl_sync(0xFFFFFFFFu, sz, h2);
+            if (h2 > (int)lane) above += t;
         }
-        uint32_t all = __reduce_add_sync(0xFFFFFFFFu, sz);
+        const uint32_t all = __reduce_add_sync(0xFFFFFFFFu, sz);
         if (lane < kH) hoff[f * kH + lane] = above;
-        if (lane <= (int)J && lane < kH) {
-            int d = (int)J - lane;
-            lsz[f * kH + d] = (lane == 0) ? (vstart[f + 1] - vstart[f]) : tot;
-        }
+        if (lane <= J && lane < kH) lsz[f * kH + (J - lane)] = (lane == 0) ? (vstart[f + 1] - vstart[f]) : tot[lane];
         if (lane == 0) nocc[f] = all;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint64_t run = 0;
-        for (uint32_t f = 0; f < F; ++f) {
-            occ_off[f] = run;
-            run += nocc[f];
-        }
-        occ_off[F] = run;
+}
+
+__global__ void occ_offsets_kernel(const uint64_t *nocc, uint32_t F, uint64_t *occ_off)
+{
+    if (threadIdx.x) return;
+    uint64_t run = 0;
+    for (uint32_t f = 0; f < F; ++f) {
+        occ_off[f] = run;
+        run += nocc[f];
     }
+    occ_off[F] = run;
 }
 
 __global__ void zero_words_kernel(uint32_t *p, const uint64_t *nbytes_at, uint64_t cap_words)
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(kThreads) occ_down_kernel(const uint64_t *__re
     __shared__ uint32_t s_w[kThreads / 32][kH];
     __shared__ int s_hm;
     if (tid < kH) {
-        s_run[tid] = partials[((uint64_t)f * X + x) * kH + tid];
+        s_run[tid] = partials[((uint64_t)f * kH + tid) * X + x];
         s_hoff[tid] = hoff[f * kH + tid];
     }
     const uint64_t base = occ_off[f];
@@ -394,8 +397,8 @@ Chunks chunks_for(uint64_t n, int num_sms)
 
 uint32_t occ_x(uint32_t F, int num_sms)
 {
-    uint32_t X = (uint32_t)(num_sms * 2) / F;
-    return X < 4 ? 4 : X;
+    uint32_t X = (uint32_t)(num_sms * 8) / F;
+    return X < 16 ? 16 : X;
 }
 
 }  // namespace
@@ -425,7 +428,7 @@ void launch_dedup(const uint64_t *keys, uint64_t n, uint32_t frame_shift, uint32
     count_launch();
 }
 
-uint64_t occupancy_partial_words(uint32_t F, int num_sms) { return (uint64_t)F * occ_x(F, num_sms) * kH; }
+uint64_t occupancy_partial_words(uint32_t F, int num_sms) { return (uint64_t)F * occ_x(F, num_sms) * kH + 2 * kMaxFrames + 8; }
 
 void launch_occupancy(const uint64_t *codes, const uint8_t *gap, const uint32_t *vstart, const uint32_t *J,
                       uint32_t F, uint32_t frame_shift, const OccupancyOut &o, DevState *st, int num_sms,
@@ -436,7 +439,10 @@ void launch_occupancy(const uint64_t *codes, const uint8_t *gap, const uint32_t 
     dim3 grid(X, F);
     occ_up_kernel<<<grid, kThreads, 0, s>>>(gap, vstart, J, o.partials);
     count_launch();
-    occ_scan_kernel<<<1, 1024, 0, s>>>(o.partials, X, F, vstart, J, o.level_sizes, o.hoff, o.occ_off);
+    uint64_t *nocc = reinterpret_cast<uint64_t *>(o.partials + (uint64_t)F * X * kH + ((F * X * kH) & 1u));
+    occ_scan_kernel<<<F, 32 * kH, 0, s>>>(o.partials, X, vstart, J, o.level_sizes, o.hoff, nocc);
+    count_launch();
+    occ_offsets_kernel<<<1, 32, 0, s>>>(nocc, F, o.occ_off);
     count_launch();
     zero_words_kernel<<<num_sms * 2, 256, 0, s>>>((uint32_t *)o.occ, o.occ_off + F, o.occ_capacity / 4);
     count_launch();

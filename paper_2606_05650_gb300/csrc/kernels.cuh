@@ -62,6 +62,8 @@ void launch_occupancy(const uint64_t *codes, const uint8_t *gap, const uint32_t 
                       uint32_t F, uint32_t frame_shift, const OccupancyOut &o, DevState *st, int num_sms,
                       cudaStream_t s);
 uint64_t occupancy_partial_words(uint32_t F, int num_sms);
+// the same bound for one frame on a GPU with at most max_sms SMs
+constexpr uint64_t occupancy_partial_words_one_frame(int max_sms) { return 8ull * max_sms * 22 + 2 * kMaxFrames + 8; }
 
 // Octree decoding of one frame (Algorithms 2-3): level sizes known on host.
 void launch_octree_decode(const uint8_t *occ, uint64_t n_occ, uint32_t J, const uint32_t *h_level_sizes,

@@ -30,10 +30,10 @@ constexpr uint64_t kMaxVoxels = GSNFS_STATIC_MAX_VOXELS;
 constexpr int kMaxSms = 256;  // bound on SMs used to size the per-CTA partial counts
 constexpr size_t kStatePart = (sizeof(DevState) + 255) & ~(size_t)255;
 constexpr size_t kSmallPart = 1024;                        // vstart, J, level sizes, height offsets, byte offsets
-constexpr size_t kPartials = (size_t)2 * kMaxSms * 22 * 4 + 256;  // per-CTA height counts
+constexpr size_t kPartials = (size_t)occupancy_partial_words_one_frame(kMaxSms) * 4 + 256;  // per-CTA height counts
 constexpr size_t kScratchBytes = kStatePart + kSmallPart + kPartials + ((kMaxVoxels + 2 + 255) & ~(uint64_t)255);
 
-// Every GPU that loads the library holds this array (about 1.2 MB) until exit.
+// Every GPU that loads the library holds this array (about 1.3 MB) until exit.
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
 struct DeviceScratch {

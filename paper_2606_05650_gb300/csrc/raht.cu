@@ -56,28 +56,61 @@ __device__ __forceinline__ uint32_t seq_end(const RahtPlanDev &p, const RahtPass
     return q == 0 ? (uint32_t)(j + 1) : p.endseq[ps.seq_off + j];
 }
 
+template <int TMAX>
 struct PreludeSmem {
-    uint8_t g[4097];
-    uint8_t flags[4096];  // bit0 in-tile gap, bit1 survivor
-    uint8_t carry[4096];  // carried to the next pass
-    uint32_t p[4097];
-    uint32_t e[4096];
-    uint16_t prv[4096];
-    uint16_t nxt[4096];
+    static constexpr int kWords = (TMAX + 1 + 31) / 32;  // bit words covering positions 0..T
+    uint8_t g[TMAX + 1];
+    uint8_t inl[TMAX];        // gap i is processed inside the tile
+    uint32_t p[TMAX + 1];
+    uint32_t e[TMAX];
+    uint16_t prv[TMAX];
+    uint16_t nxt[TMAX];
+    uint32_t lvl[kRounds + 1][kWords];  // bit i of lvl[L] : g[i] >= L
+    uint32_t surv[kWords];    // survivors (start a maximal in-tile subtree)
+    uint32_t carry[kWords];   // survivors carried to the next pass
+    uint32_t cpre[kWords];    // exclusive prefix of carry popcounts
     uint32_t lvl_cnt[kRounds + 1];
     uint32_t lvl_off[kRounds + 1];
     uint32_t scan[33];
-    uint32_t ncarry;
 };
 
+// highest set bit of mask at a position < i, or -1
+__device__ __forceinline__ int prev_set(const uint32_t *mask, uint32_t i)
+{
+    int w = (int)(i >> 5);
+    uint32_t b = mask[w] & ((1u << (i & 31)) - 1u);
+    while (!b) {
+        if (--w < 0) return -1;
+        b = mask[w];
+    }
+    return w * 32 + 31 - __clz(b);
+}
+
+// lowest set bit of mask at a position in (i, lim], or -1
+__device__ __forceinline__ int next_set(const uint32_t *mask, uint32_t i, uint32_t lim)
+{
+    const uint32_t j = i + 1;
+    int w = (int)(j >> 5);
+    const int wl = (int)(lim >> 5);
+    uint32_t b = mask[w] & (~0u << (j & 31));
+    while (!b) {
+        if (++w > wl) return -1;
+        b = mask[w];
+    }
+    const int r = w * 32 + __ffs(b) - 1;
+    return r <= (int)lim ? r : -1;
+}
+
 // Builds the schedule of tile t of pass q (one CTA).
-__device__ void prelude_tile(const PreludeArgs &a, PreludeSmem &S, int q, const RahtPass &ps, uint32_t t)
+template <int TMAX>
+__device__ void prelude_tile(const PreludeArgs &a, PreludeSmem<TMAX> &S, int q, const RahtPass &ps, uint32_t t)
 {
     const RahtPlanDev &p = a.p;
     const uint32_t T = p.T;
     const uint64_t j0 = (uint64_t)t * T;
     const uint32_t m = (uint32_t)((ps.n - j0) < T ? (ps.n - j0) : T);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t W = (m + 1 + 31) / 32;  // words covering positions 0..m
     for (uint32_t i = tid; i <= m; i += kThreads) {
         S.g[i] = seq_gap(a, ps, q, j0 + i);
         S.p[i] = seq_pos(p, ps, q, j0 + i);
@@ -85,92 +118,116 @@ __device__ void prelude_tile(const PreludeArgs &a, PreludeSmem &S, int q, const 
     }
     for (int i = tid; i <= kRounds; i += kThreads) S.lvl_cnt[i] = 0;
     __syncthreads();
-    // nearest larger gap on each side (tile boundaries count as candidates)
+    // level masks by ballots: one warp per 32 positions
+    for (uint32_t w = wid; w < W; w += kThreads / 32) {
+        const uint32_t i = w * 32 + lane;
+        const uint32_t gi = (i <= m) ? S.g[i] : 0u;
+        for (int L = 1; L <= kRounds; ++L) {
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, gi >= (uint32_t)L);
+            if (lane == 0) S.lvl[L][w] = b;
+        }
+    }
+    __syncthreads();
+    // nearest larger gap on each side (the tile's boundary gaps g[0], g[m] count)
     for (uint32_t i = tid; i < m; i += kThreads) {
         uint8_t f = 0;
         if (i > 0) {
-            const uint8_t gi = S.g[i];
-            uint32_t l = i - 1;
-            while (l > 0 && S.g[l] <= gi) --l;
-            uint32_t r = i + 1;
-            while (r < m && S.g[r] <= gi) ++r;
-            if (S.g[l] > gi && S.g[r] > gi) {
-                f = 1;
-                S.prv[i] = (uint16_t)l;
-                S.nxt[i] = (uint16_t)r;
-                atomicAdd(&S.lvl_cnt[gi], 1u);
+            const uint32_t gi = S.g[i];  // < kInfLevel whenever a larger gap exists
+            if (gi < (uint32_t)kRounds) {
+                const int l = prev_set(S.lvl[gi + 1], i);
+                const int r = (l >= 0) ? next_set(S.lvl[gi + 1], i, m) : -1;
+                if (l >= 0 && r >= 0) {
+                    f = 1;
+                    S.prv[i] = (uint16_t)l;
+                    S.nxt[i] = (uint16_t)r;
+                    atomicAdd(&S.lvl_cnt[gi], 1u);
+                }
             }
         }
-        if (!(f & 1)) f |= 2;  // survivor: starts a maximal in-tile subtree
-        S.flags[i] = f;
+        S.inl[i] = f;
     }
     __syncthreads();
-    if (tid < 32) {  // exclusive scan of level counts (65 entries) by one warp
-        uint32_t run = 0;
+    // survivor mask; rounds = nonempty levels in ascending order (one warp)
+    for (uint32_t w = wid; w < W; w += kThreads / 32) {
+        const uint32_t i = w * 32 + lane;
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, i < m && !S.inl[i]);
+        if (lane == 0) S.surv[w] = b;
+    }
+    if (wid == 0) {
+        uint32_t run = 0, nr = 0;
+        uint16_t *re = p.round_end + (uint64_t)(ps.tile_off + t) * kRounds;
         for (int base = 0; base <= kRounds; base += 32) {
-            int l = base + tid;
-            uint32_t c = (l <= kRounds) ? S.lvl_cnt[l] : 0u;
-            uint32_t inc = warp_inclusive_sum(c);
+            const int l = base + lane;
+            const uint32_t c = (l <= kRounds) ? S.lvl_cnt[l] : 0u;
+            const uint32_t inc = warp_inclusive_sum(c);
             if (l <= kRounds) S.lvl_off[l] = run + inc - c;
+            const uint32_t ne = __ballot_sync(0xFFFFFFFFu, c != 0);
+            if (c) re[nr + __popc(ne & lanemask_lt())] = (uint16_t)(run + inc);
+            nr += __popc(ne);
             run += __shfl_sync(0xFFFFFFFFu, inc, 31);
         }
-        if (tid == 0) {  // rounds = nonempty levels in ascending order
-            uint32_t nr = 0, tot = 0;
-            uint16_t *re = p.round_end + (uint64_t)(ps.tile_off + t) * kRounds;
-            for (int l = 1; l <= kRounds; ++l)
-                if (S.lvl_cnt[l]) {
-                    tot += S.lvl_cnt[l];
-                    re[nr++] = (uint16_t)tot;
-                }
-            p.tile_nbf[ps.tile_off + t] = tot;
+        if (lane == 0) {
+            p.tile_nbf[ps.tile_off + t] = run;
             p.tile_nr[ps.tile_off + t] = nr;
         }
     }
     __syncthreads();
     for (int l = tid; l <= kRounds; l += kThreads) S.lvl_cnt[l] = 0;  // reused as fill counters
     __syncthreads();
-    // butterflies, survivors, destinations
+    // butterflies, destinations, frame roots; carried survivors marked in S.inl (2)
     const uint64_t sbase = (uint64_t)(ps.tile_off + t) * T;
     for (uint32_t i = tid; i < m; i += kThreads) {
-        const uint8_t f = S.flags[i];
-        uint8_t c = 0;
-        if (f & 1) {
+        if (S.inl[i]) {
             // children cover elements [l, i) and [i, r); neither range crosses a frame
             // boundary, so their voxels are contiguous.  The right end is taken from
             // the last element's own end: a frame finished in an earlier pass may have
             // been dropped between this frame and the element at r.
-            uint32_t l = S.prv[i], r = S.nxt[i];
-            uint32_t w0 = S.p[i] - S.p[l], w1 = S.e[r - 1] - S.p[i];
-            float fw0 = (float)w0, fw1 = (float)w1, fs = (float)(w0 + w1);
-            float ca = __fsqrt_rn(__fdiv_rn(fw0, fs)), cb = __fsqrt_rn(__fdiv_rn(fw1, fs));
-            uint32_t slot = S.lvl_off[S.g[i]] + atomicAdd(&S.lvl_cnt[S.g[i]], 1u);
+            const uint32_t l = S.prv[i], r = S.nxt[i];
+            const uint32_t w0 = S.p[i] - S.p[l], w1 = S.e[r - 1] - S.p[i];
+            const float fw0 = (float)w0, fw1 = (float)w1, fs = (float)(w0 + w1);
+            const float ca = __fsqrt_rn(__fdiv_rn(fw0, fs)), cb = __fsqrt_rn(__fdiv_rn(fw1, fs));
+            const uint32_t slot = S.lvl_off[S.g[i]] + atomicAdd(&S.lvl_cnt[S.g[i]], 1u);
             p.bf_idx[sbase + slot] = l | (i << 16);
             p.bf_ab[sbase + slot] = make_float2(ca, cb);
             p.dest[ps.seq_off + j0 + i] = S.p[i];
         } else {
             // survivor: a frame root (final) iff both bounding gaps are frame boundaries
-            uint32_t r = i + 1;
-            while (r < m && !(S.flags[r] & 2)) ++r;
+            int r = next_set(S.surv, i, m - 1);
+            if (r < 0) r = (int)m;
             if (S.g[i] >= kInfLevel && S.g[r] >= kInfLevel) {
                 p.dest[ps.seq_off + j0 + i] = S.p[i];
             } else {
-                c = 1;
+                S.inl[i] = 2;
                 p.send[ps.seq_off + j0 + i] = S.e[r - 1];  // the survivor's subtree ends with element r-1
             }
         }
-        S.carry[i] = c;
     }
     __syncthreads();
-    // local carried ranks in element order
-    uint32_t run = 0, tot;
-    for (uint32_t k = 0; k < (T + kThreads - 1) / kThreads; ++k) {
-        uint32_t i = tid + k * kThreads;
-        uint32_t c = (i < m) ? S.carry[i] : 0u;
-        uint32_t pre = block_exclusive_sum<uint32_t>(c, S.scan, &tot);
-        if (c) p.dest[ps.seq_off + j0 + i] = kCarry | (run + pre);
-        run += tot;
+    // local carried ranks: popcounts of the carried mask
+    for (uint32_t w = wid; w < W; w += kThreads / 32) {
+        const uint32_t i = w * 32 + lane;
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, i < m && S.inl[i] == 2);
+        if (lane == 0) S.carry[w] = b;
     }
-    if (tid == 0) p.tile_carry[ps.tile_off + t] = run;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t run = 0;
+        for (uint32_t base = 0; base < W; base += 32) {
+            const uint32_t w = base + lane;
+            const uint32_t c = (w < W) ? __popc(S.carry[w]) : 0u;
+            const uint32_t inc = warp_inclusive_sum(c);
+            if (w < W) S.cpre[w] = run + inc - c;
+            run += __shfl_sync(0xFFFFFFFFu, inc, 31);
+        }
+        if (lane == 0) p.tile_carry[ps.tile_off + t] = run;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < m; i += kThreads)
+        if (S.inl[i] == 2) {
+            const uint32_t w = i >> 5;
+            const uint32_t rank = S.cpre[w] + __popc(S.carry[w] & ((1u << (i & 31)) - 1u));
+            p.dest[ps.seq_off + j0 + i] = kCarry | rank;
+        }
     __syncthreads();
 }
 
@@ -188,10 +245,11 @@ __global__ void __launch_bounds__(kThreads) prelude_init_kernel(RahtPlanDev p, c
     }
 }
 
+template <int TMAX>
 __global__ void __launch_bounds__(kThreads) prelude_tiles_kernel(PreludeArgs a, int q)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PreludeSmem &S = *reinterpret_cast<PreludeSmem *>(smem_raw);
+    PreludeSmem<TMAX> &S = *reinterpret_cast<PreludeSmem<TMAX> *>(smem_raw);
     const RahtPass ps = a.p.passes[q];
     for (uint32_t t = blockIdx.x; t < ps.ntiles; t += gridDim.x) prelude_tile(a, S, q, ps, t);
 }
@@ -260,10 +318,11 @@ __global__ void __launch_bounds__(kThreads) prelude_compact_kernel(PreludeArgs a
 }
 
 // remaining passes inside one CTA
+template <int TMAX>
 __global__ void __launch_bounds__(kThreads) prelude_finish_kernel(PreludeArgs a, int q0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PreludeSmem &S = *reinterpret_cast<PreludeSmem *>(smem_raw);
+    PreludeSmem<TMAX> &S = *reinterpret_cast<PreludeSmem<TMAX> *>(smem_raw);
     for (int q = q0; q + 1 < kRahtMaxPasses; ++q) {
         const RahtPass ps = a.p.passes[q];
         if (ps.n == 0) break;
@@ -337,10 +396,38 @@ struct XformArgs {
     uint32_t Cg;  // channels per group held in shared memory
 };
 
+// Shared-memory carve of the transform kernels (T = tile size).
+struct XformSmem {
+    uint32_t *s_idx;   // T: butterfly i0 | i1 << 16
+    float2 *s_ab;      // T: butterfly coefficients
+    uint32_t *s_src;   // T + 1: gather segment starts (forward pass 0) or row sources (inverse)
+    uint32_t *s_dst;   // T: row destinations (forward)
+    uint32_t *s_vals;  // 2T: point indices of the tile's gather
+    uint8_t *s_frame;  // T: frame of each voxel (batched gather)
+    float *rows;       // T x Cg
+};
+
+__host__ __device__ inline size_t xform_meta_bytes(uint32_t T) { return (size_t)4 * T + 8 * T + 4 * (T + 1) + 4 * T + 8 * T + T + 64; }
+
+__device__ inline XformSmem carve_xform(unsigned char *raw, uint32_t T)
+{
+    XformSmem S;
+    S.s_ab = reinterpret_cast<float2 *>(raw);
+    S.s_idx = reinterpret_cast<uint32_t *>(raw + 8 * T);
+    S.s_src = S.s_idx + T;
+    S.s_dst = S.s_src + T + 1;
+    S.s_vals = S.s_dst + T;
+    S.s_frame = reinterpret_cast<uint8_t *>(S.s_vals + 2 * T);
+    S.rows = reinterpret_cast<float *>(raw + ((xform_meta_bytes(T) + 15) & ~(size_t)15));
+    return S;
+}
+
+constexpr int kUnroll = 4;  // rows loaded per thread before they are used
+
 // Processes tile t of pass q for channel group [c0, c0 + Cg).
 template <bool INV, int VEC, bool GATHER, bool QDQ>
-__device__ void xform_tile(const XformArgs &A, float *rows, uint32_t *s_idx, float2 *s_ab, TileSched &sch, int q,
-                           const RahtPass &ps, const RahtPass &nx, uint32_t t)
+__device__ void xform_tile(const XformArgs &A, const XformSmem &S, TileSched &sch, int q, const RahtPass &ps,
+                           const RahtPass &nx, uint32_t t)
 {
     typedef typename Vec<VEC>::T V;
     const RahtPlanDev &p = A.p;
@@ -350,15 +437,36 @@ __device__ void xform_tile(const XformArgs &A, float *rows, uint32_t *s_idx, flo
     const uint32_t m = (uint32_t)((ps.n - j0) < T ? (ps.n - j0) : T);
     const int tid = threadIdx.x;
     const uint32_t tile = ps.tile_off + t;
+    const bool gather = GATHER && q == 0;
+    // ---- schedule and per-row metadata, coalesced into shared memory
     if (tid == 0) {
         sch.nbf = p.tile_nbf[tile];
         sch.nr = p.tile_nr[tile];
     }
+    for (uint32_t i = tid; i < m; i += kThreads) {
+        const uint32_t d = p.dest[ps.seq_off + j0 + i];
+        if (INV) S.s_src[i] = d; else S.s_dst[i] = d;
+        if (gather) {
+            S.s_src[i] = io.seg[j0 + i];
+            if (io.frame_shift < 64) S.s_frame[i] = (uint8_t)(io.codes[j0 + i] >> io.frame_shift);
+        }
+    }
+    if (gather && tid == 0) S.s_src[m] = io.seg[j0 + m];
     __syncthreads();
     for (uint32_t r = tid; r < sch.nr; r += kThreads) sch.re[r] = p.round_end[(uint64_t)tile * kRounds + r];
     for (uint32_t k = tid; k < sch.nbf; k += kThreads) {
-        s_idx[k] = p.bf_idx[(uint64_t)tile * T + k];
-        s_ab[k] = p.bf_ab[(uint64_t)tile * T + k];
+        S.s_idx[k] = p.bf_idx[(uint64_t)tile * T + k];
+        S.s_ab[k] = p.bf_ab[(uint64_t)tile * T + k];
+    }
+    uint32_t g0 = 0;
+    bool staged = false;
+    if (gather) {
+        g0 = S.s_src[0];
+        const uint32_t gcount = S.s_src[m] - g0;
+        staged = gcount <= 2 * T;
+        if (staged)
+            for (uint32_t k = tid; k < gcount; k += kThreads) S.s_vals[k] = io.vals[g0 + k];
+        __syncthreads();
     }
     for (uint32_t c0 = 0; c0 < C; c0 += A.Cg) {
         const uint32_t Cg = (C - c0) < A.Cg ? (C - c0) : A.Cg;
@@ -367,54 +475,64 @@ __device__ void xform_tile(const XformArgs &A, float *rows, uint32_t *s_idx, flo
         const uint32_t slot = tid / L, lane = tid - slot * L;
         const uint32_t c = c0 + lane * VEC;
         const bool act = slot < slots;
-        // ---- load rows
+        // ---- load rows: kUnroll independent loads in flight per thread
         if (act) {
-            for (uint32_t i = slot; i < m; i += slots) {
-                const uint64_t j = j0 + i;
-                V v;
-                if (!INV) {
-                    if (q == 0) {
-                        if (GATHER) {
-                            const uint32_t s0 = io.seg[j], s1 = io.seg[j + 1];
-                            const uint32_t f = (io.frame_shift < 64) ? (uint32_t)(io.codes[j] >> io.frame_shift) : 0u;
-                            const float *base = io.attr[f];
-                            V acc = Vec<VEC>::zero();
-                            for (uint32_t g = s0; g < s1; ++g) {
-                                V x = Vec<VEC>::ld(base + (uint64_t)io.vals[g] * C + c);
-                                if (VEC == 1) {
-                                    *reinterpret_cast<float *>(&acc) = __fadd_rn(*reinterpret_cast<float *>(&acc), *reinterpret_cast<float *>(&x));
-                                } else {
-                                    float *pa = reinterpret_cast<float *>(&acc);
-                                    const float *px = reinterpret_cast<const float *>(&x);
+            for (uint32_t ib = slot; ib < m; ib += kUnroll * slots) {
+                V v[kUnroll];
 #pragma unroll
-                                    for (int e = 0; e < VEC; ++e) pa[e] = __fadd_rn(pa[e], px[e]);
-                                }
-                            }
-                            const float cntf = (float)(s1 - s0);
-                            float *pa = reinterpret_cast<float *>(&acc);
-#pragma unroll
-                            for (int e = 0; e < VEC; ++e) pa[e] = __fdiv_rn(pa[e], cntf);
-                            v = acc;
+                for (int u = 0; u < kUnroll; ++u) {
+                    const uint32_t i = ib + (uint32_t)u * slots;
+                    if (i >= m) break;
+                    const uint64_t j = j0 + i;
+                    if (!INV) {
+                        if (gather) {
+                            const uint32_t s0 = S.s_src[i];
+                            const uint32_t row = staged ? S.s_vals[s0 - g0] : io.vals[s0];
+                            const float *base = io.attr[io.frame_shift < 64 ? S.s_frame[i] : 0];
+                            v[u] = Vec<VEC>::ld(base + (uint64_t)row * C + c);
+                        } else if (q == 0) {
+                            v[u] = Vec<VEC>::ld(io.in + j * C + c);
                         } else {
-                            v = Vec<VEC>::ld(io.in + j * C + c);
+                            v[u] = Vec<VEC>::ld(io.pool + ((uint64_t)ps.surv_off + j) * C + c);
                         }
                     } else {
-                        v = Vec<VEC>::ld(io.pool + ((uint64_t)ps.surv_off + j) * C + c);
-                    }
-                } else {
-                    const uint32_t d = p.dest[ps.seq_off + j];
-                    if (d & kCarry) {
-                        v = Vec<VEC>::ld(io.pool + ((uint64_t)nx.surv_off + (d & ~kCarry)) * C + c);
-                    } else {
-                        v = Vec<VEC>::ld(io.Y + (uint64_t)d * C + c);
-                        if (QDQ) {
-                            float *pv = reinterpret_cast<float *>(&v);
+                        const uint32_t d = S.s_src[i];
+                        if (d & kCarry) {
+                            v[u] = Vec<VEC>::ld(io.pool + ((uint64_t)nx.surv_off + (d & ~kCarry)) * C + c);
+                        } else {
+                            v[u] = Vec<VEC>::ld(io.Y + (uint64_t)d * C + c);
+                            if (QDQ) {
+                                float *pv = reinterpret_cast<float *>(&v[u]);
 #pragma unroll
-                            for (int e = 0; e < VEC; ++e) pv[e] = qdq(pv[e], io.inv_step[c + e], io.step[c + e], io.tau);
+                                for (int e = 0; e < VEC; ++e)
+                                    pv[e] = qdq(pv[e], io.inv_step[c + e], io.step[c + e], io.tau);
+                            }
                         }
                     }
                 }
-                Vec<VEC>::st(rows + (uint64_t)i * Cg + lane * VEC, v);
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) {
+                    const uint32_t i = ib + (uint32_t)u * slots;
+                    if (i >= m) break;
+                    if (gather) {  // voxels holding several points: average in input order
+                        const uint32_t s0 = S.s_src[i], s1 = S.s_src[i + 1];
+                        if (s1 - s0 > 1) {
+                            float *pa = reinterpret_cast<float *>(&v[u]);
+                            const float *base = io.attr[io.frame_shift < 64 ? S.s_frame[i] : 0];
+                            for (uint32_t g = s0 + 1; g < s1; ++g) {
+                                const uint32_t row = staged ? S.s_vals[g - g0] : io.vals[g];
+                                V x = Vec<VEC>::ld(base + (uint64_t)row * C + c);
+                                const float *px = reinterpret_cast<const float *>(&x);
+#pragma unroll
+                                for (int e = 0; e < VEC; ++e) pa[e] = __fadd_rn(pa[e], px[e]);
+                            }
+                            const float cntf = (float)(s1 - s0);
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e) pa[e] = __fdiv_rn(pa[e], cntf);
+                        }
+                    }
+                    Vec<VEC>::st(S.rows + (uint64_t)i * Cg + lane * VEC, v[u]);
+                }
             }
         }
         __syncthreads();
@@ -424,10 +542,10 @@ __device__ void xform_tile(const XformArgs &A, float *rows, uint32_t *s_idx, flo
             const uint32_t kb = r ? sch.re[r - 1] : 0u, ke = sch.re[r];
             if (act) {
                 for (uint32_t k = kb + slot; k < ke; k += slots) {
-                    const uint32_t ix = s_idx[k];
-                    const float2 ab = s_ab[k];
-                    float *r0 = rows + (uint64_t)(ix & 0xFFFFu) * Cg + lane * VEC;
-                    float *r1 = rows + (uint64_t)(ix >> 16) * Cg + lane * VEC;
+                    const uint32_t ix = S.s_idx[k];
+                    const float2 ab = S.s_ab[k];
+                    float *r0 = S.rows + (uint64_t)(ix & 0xFFFFu) * Cg + lane * VEC;
+                    float *r1 = S.rows + (uint64_t)(ix >> 16) * Cg + lane * VEC;
                     V y0 = Vec<VEC>::ld(r0), y1 = Vec<VEC>::ld(r1);
                     rot<INV>(ab.x, ab.y, y0, y1);
                     Vec<VEC>::st(r0, y0);
@@ -440,9 +558,9 @@ __device__ void xform_tile(const XformArgs &A, float *rows, uint32_t *s_idx, flo
         if (act) {
             for (uint32_t i = slot; i < m; i += slots) {
                 const uint64_t j = j0 + i;
-                V v = Vec<VEC>::ld(rows + (uint64_t)i * Cg + lane * VEC);
+                V v = Vec<VEC>::ld(S.rows + (uint64_t)i * Cg + lane * VEC);
                 if (!INV) {
-                    const uint32_t d = p.dest[ps.seq_off + j];
+                    const uint32_t d = S.s_dst[i];
                     if (d & kCarry)
                         Vec<VEC>::st(io.pool + ((uint64_t)nx.surv_off + (d & ~kCarry)) * C + c, v);
                     else
@@ -464,14 +582,11 @@ __global__ void __launch_bounds__(kThreads) xform_pass_kernel(XformArgs A, int q
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TileSched sch;
-    const uint32_t T = A.p.T;
-    uint32_t *s_idx = reinterpret_cast<uint32_t *>(smem_raw);
-    float2 *s_ab = reinterpret_cast<float2 *>(smem_raw + 4 * T);
-    float *rows = reinterpret_cast<float *>(smem_raw + 12 * T);
+    const XformSmem S = carve_xform(smem_raw, A.p.T);
     const RahtPass ps = A.p.passes[q];
     const RahtPass nx = A.p.passes[q + 1];
     for (uint32_t t = blockIdx.x; t < ps.ntiles; t += gridDim.x)
-        xform_tile<INV, VEC, GATHER, QDQ>(A, rows, s_idx, s_ab, sch, q, ps, nx, t);
+        xform_tile<INV, VEC, GATHER, QDQ>(A, S, sch, q, ps, nx, t);
 }
 
 // passes q0 .. npasses-1 in one CTA (forward: ascending; inverse: descending)
@@ -480,17 +595,14 @@ __global__ void __launch_bounds__(kThreads) xform_finish_kernel(XformArgs A, int
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TileSched sch;
-    const uint32_t T = A.p.T;
-    uint32_t *s_idx = reinterpret_cast<uint32_t *>(smem_raw);
-    float2 *s_ab = reinterpret_cast<float2 *>(smem_raw + 4 * T);
-    float *rows = reinterpret_cast<float *>(smem_raw + 12 * T);
+    const XformSmem S = carve_xform(smem_raw, A.p.T);
     const int np = (int)*A.p.npasses;
     for (int k = 0; k < np - q0; ++k) {
         const int q = INV ? (np - 1 - k) : (q0 + k);
         const RahtPass ps = A.p.passes[q];
         const RahtPass nx = A.p.passes[q + 1];
         for (uint32_t t = 0; t < ps.ntiles; ++t)
-            xform_tile<INV, VEC, false, QDQ>(A, rows, s_idx, s_ab, sch, q, ps, nx, t);
+            xform_tile<INV, VEC, false, QDQ>(A, S, sch, q, ps, nx, t);
         __threadfence_block();
         __syncthreads();
     }
@@ -504,7 +616,7 @@ uint32_t channel_group(uint32_t C, uint32_t T)
     return cg < 1 ? 1 : cg;
 }
 
-size_t xform_smem(uint32_t T, uint32_t Cg) { return (size_t)12 * T + (size_t)4 * T * Cg; }
+size_t xform_smem(uint32_t T, uint32_t Cg) { return ((xform_meta_bytes(T) + 15) & ~(size_t)15) + (size_t)4 * T * Cg; }
 
 template <bool INV, int VEC, bool GATHER, bool QDQ>
 void launch_pass(const XformArgs &A, int q, uint32_t grid, size_t smem, cudaStream_t s)
@@ -586,6 +698,28 @@ void raht_plan_sizes(uint64_t nv_cap, uint32_t T, uint64_t *elems, uint64_t *til
     *surv_rows = nv_cap + 128 * (kRahtMaxPasses + 1);
 }
 
+template <int TMAX>
+void prelude_launches(const PreludeArgs &a, const RahtPlanDev &p, const DevState *st, const uint64_t *nv_dev,
+                      int num_sms, cudaStream_t s)
+{
+    const size_t smem = sizeof(PreludeSmem<TMAX>);
+    cudaFuncSetAttribute(prelude_tiles_kernel<TMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(prelude_finish_kernel<TMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    prelude_init_kernel<<<1, 32, 0, s>>>(p, st, nv_dev);
+    count_launch();
+    uint32_t grid = (uint32_t)num_sms * 8;
+    for (int q = 0; q < kRahtMultiPasses; ++q) {
+        prelude_tiles_kernel<TMAX><<<grid, kThreads, smem, s>>>(a, q);
+        count_launch();
+        prelude_scan_kernel<<<1, 1024, 0, s>>>(p, q);
+        count_launch();
+        prelude_compact_kernel<<<grid, kThreads, 0, s>>>(a, q);
+        count_launch();
+    }
+    prelude_finish_kernel<TMAX><<<1, kThreads, smem, s>>>(a, kRahtMultiPasses);
+    count_launch();
+}
+
 void launch_raht_prelude(const RahtPlanDev &p, const uint8_t *gap, const DevState *st, const uint64_t *nv_dev,
                          int num_sms, cudaStream_t s)
 {
@@ -593,22 +727,12 @@ void launch_raht_prelude(const RahtPlanDev &p, const uint8_t *gap, const DevStat
     a.p = p;
     a.gap0 = gap;
     a.st = st;
-    const size_t smem = sizeof(PreludeSmem);
-    cudaFuncSetAttribute(prelude_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(prelude_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    prelude_init_kernel<<<1, 32, 0, s>>>(p, st, nv_dev);
-    count_launch();
-    uint32_t grid = (uint32_t)num_sms * 4;
-    for (int q = 0; q < kRahtMultiPasses; ++q) {
-        prelude_tiles_kernel<<<grid, kThreads, smem, s>>>(a, q);
-        count_launch();
-        prelude_scan_kernel<<<1, 1024, 0, s>>>(p, q);
-        count_launch();
-        prelude_compact_kernel<<<grid, kThreads, 0, s>>>(a, q);
-        count_launch();
-    }
-    prelude_finish_kernel<<<1, kThreads, smem, s>>>(a, kRahtMultiPasses);
-    count_launch();
+    if (p.T <= 256)
+        prelude_launches<256>(a, p, st, nv_dev, num_sms, s);
+    else if (p.T <= 1024)
+        prelude_launches<1024>(a, p, st, nv_dev, num_sms, s);
+    else
+        prelude_launches<4096>(a, p, st, nv_dev, num_sms, s);
 }
 
 void launch_raht_forward(const RahtPlanDev &p, const RahtIO &io, uint64_t nv_bound, int num_sms, cudaStream_t s)

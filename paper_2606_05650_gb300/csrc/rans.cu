@@ -89,16 +89,22 @@ __device__ __forceinline__ uint32_t frame_of(const uint64_t *off, uint32_t F, ui
     return lo;
 }
 
-// warp per chunk; slot layout: u32 state[32] at 0, u16 word stack [128, 128 + 2*chunk)
-__global__ void __launch_bounds__(128) encode_kernel(const uint8_t *__restrict__ occ, const uint64_t *occ_off,
-                                                     const uint64_t *chunk_off, uint32_t F, uint32_t chunk,
-                                                     const uint16_t *freq, const uint32_t *cum, uint8_t *slots,
-                                                     uint64_t slot_bytes, uint32_t *chunk_words,
-                                                     uint32_t *chunk_top)
+// warp per chunk; slot layout: u32 state[32] at 0, u16 word stack [128, 128 + 2*chunk).
+// The chunk's symbols and the frame's tables are staged in shared memory first.
+constexpr int kEncWarps = 4;
+constexpr uint32_t kStageSyms = 8192;  // symbols staged per pass
+
+__global__ void __launch_bounds__(32 * kEncWarps) encode_kernel(const uint8_t *__restrict__ occ, const uint64_t *occ_off,
+                                                               const uint64_t *chunk_off, uint32_t F, uint32_t chunk,
+                                                               const uint16_t *freq, const uint32_t *cum, uint8_t *slots,
+                                                               uint64_t slot_bytes, uint32_t *chunk_words,
+                                                               uint32_t *chunk_top)
 {
-    const uint32_t lane = threadIdx.x & 31;
-    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    __shared__ uint8_t s_sym[kEncWarps][kStageSyms];
+    __shared__ uint32_t s_fc[kEncWarps][256];  // freq << 16 | cum (cum < 2^15)
+    const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const uint64_t gw = (uint64_t)blockIdx.x * kEncWarps + wl;
+    const uint64_t nw = (uint64_t)gridDim.x * kEncWarps;
     const uint64_t total = chunk_off[F];
     for (uint64_t gc = gw; gc < total; gc += nw) {
         const uint32_t f = frame_of(chunk_off, F, gc);
@@ -106,33 +112,42 @@ __global__ void __launch_bounds__(128) encode_kernel(const uint8_t *__restrict__
         const uint64_t n = occ_off[f + 1] - occ_off[f];
         const uint8_t *sym = occ + occ_off[f] + c * chunk;
         const uint32_t len = (uint32_t)((n - c * chunk) < chunk ? (n - c * chunk) : chunk);
-        const uint16_t *fr = freq + f * 256;
-        const uint32_t *cm = cum + f * 256;
+        for (uint32_t k = lane; k < 256; k += 32) s_fc[wl][k] = ((uint32_t)freq[f * 256 + k] << 16) | cum[f * 256 + k];
         uint8_t *slot = slots + gc * slot_bytes;
         uint16_t *stack = reinterpret_cast<uint16_t *>(slot + 128);
         uint32_t top = chunk;
         uint32_t x = kL;
         const uint32_t G = (len + 31) / 32;
-        for (int g = (int)G - 1; g >= 0; --g) {
-            const uint32_t j = (uint32_t)g * 32 + lane;
-            const bool valid = j < len;
-            const uint32_t s = valid ? sym[j] : 0u;
-            const uint32_t fs = fr[s], cs = cm[s];
-            const bool need = valid && ((uint64_t)x >= ((uint64_t)fs << 17));
-            const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
-            if (need) {
-                const uint32_t above = __popc(m >> lane) - 1u;  // emitting lanes above this one
-                stack[top - 1 - above] = (uint16_t)(x & 0xFFFFu);
-                x >>= 16;
+        // stage windows of symbols from the end of the chunk backwards
+        int g = (int)G - 1;
+        while (g >= 0) {
+            const uint32_t win_lo_g = (uint32_t)g + 1 > kStageSyms / 32 ? (uint32_t)g + 1 - kStageSyms / 32 : 0u;
+            const uint32_t b0 = win_lo_g * 32, b1 = ((uint32_t)g + 1) * 32 < len ? ((uint32_t)g + 1) * 32 : len;
+            __syncwarp();
+            for (uint32_t k = b0 + lane; k < b1; k += 32) s_sym[wl][k - b0] = sym[k];
+            __syncwarp();
+            for (; g >= (int)win_lo_g; --g) {
+                const uint32_t j = (uint32_t)g * 32 + lane;
+                const bool valid = j < len;
+                const uint32_t fc = s_fc[wl][valid ? s_sym[wl][j - b0] : 0u];
+                const uint32_t fs = fc >> 16, cs = fc & 0xFFFFu;
+                const bool need = valid && ((uint64_t)x >= ((uint64_t)fs << 17));
+                const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
+                if (need) {
+                    const uint32_t above = __popc(m >> lane) - 1u;  // emitting lanes above this one
+                    stack[top - 1 - above] = (uint16_t)(x & 0xFFFFu);
+                    x >>= 16;
+                }
+                top -= __popc(m);
+                if (valid) x = ((x / fs) << kProbBits) + (x % fs) + cs;
             }
-            top -= __popc(m);
-            if (valid) x = ((x / fs) << kProbBits) + (x % fs) + cs;
         }
         reinterpret_cast<uint32_t *>(slot)[lane] = x;
         if (lane == 0) {
             chunk_words[gc] = chunk - top;
             chunk_top[gc] = top;
         }
+        __syncwarp();
     }
 }
 
@@ -166,40 +181,51 @@ __global__ void section_size_kernel(const uint64_t *occ_off, const uint64_t *chu
     sec_bytes[f] = raw;
 }
 
-// ---- decoder: warp per chunk of one frame -------------------------------
-__global__ void __launch_bounds__(128) decode_kernel(const uint8_t *__restrict__ sec, uint64_t sec_bytes, uint64_t n,
-                                                     uint32_t nch, uint32_t chunk, uint8_t *out, DevState *st)
+// ---- decoder: warp per chunk of one frame; the chunk (states and words) is
+// copied to shared memory with coalesced loads, then decoded from there.
+constexpr int kDecWarps = 2;
+
+__global__ void __launch_bounds__(32 * kDecWarps) decode_kernel(const uint8_t *__restrict__ sec, uint64_t sec_bytes,
+                                                               uint64_t n, uint32_t nch, uint32_t chunk, uint8_t *out,
+                                                               DevState *st, bool staged)
 {
-    __shared__ uint8_t slot2sym[kM];
-    __shared__ uint16_t fr[256];
-    __shared__ uint32_t cm[256];
+    extern __shared__ __align__(16) unsigned char dsm[];
+    uint8_t *slot2sym = dsm;                                               // kM
+    uint32_t *fc = reinterpret_cast<uint32_t *>(dsm + kM);                 // 256: freq << 16 | cum
+    const uint32_t stage_bytes = staged ? 128 + 2 * chunk : 0u;
+    const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    uint8_t *cbuf = dsm + kM + 1024 + (size_t)wl * ((stage_bytes + 15) & ~15u);
     const uint8_t *ftab = sec + 24;
+    __shared__ uint32_t s_cm[256];
+    __shared__ uint32_t s_bad;
     if (threadIdx.x == 0) {
         uint32_t acc = 0;
-        for (int s = 0; s < 256; ++s) {
-            uint16_t v = (uint16_t)(ftab[2 * s] | (ftab[2 * s + 1] << 8));
-            fr[s] = v;
-            cm[s] = acc;
+        for (int s2 = 0; s2 < 256; ++s2) {
+            const uint32_t v = (uint32_t)(ftab[2 * s2] | (ftab[2 * s2 + 1] << 8));
+            fc[s2] = (v << 16) | (acc & 0xFFFFu);
+            s_cm[s2] = acc;
             acc += v;
         }
-        if (acc != kM) set_error(&st->err, kErrCorrupt);
+        s_bad = (acc != kM);
     }
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < kM; t += blockDim.x) {  // symbol of each slot: last s with cm[s] <= t
+    if (s_bad) {
+        if (threadIdx.x == 0) set_error(&st->err, kErrCorrupt);
+        return;
+    }
+    for (uint32_t t = threadIdx.x; t < kM; t += blockDim.x) {  // symbol of each slot: last s with cum[s] <= t
         uint32_t lo = 0, hi = 256;
         while (hi - lo > 1) {
-            uint32_t mid = (lo + hi) >> 1;
-            if (cm[mid] <= t) lo = mid; else hi = mid;
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_cm[mid] <= t) lo = mid; else hi = mid;
         }
-        while (lo > 0 && fr[lo] == 0) --lo;
         slot2sym[t] = (uint8_t)lo;
     }
     __syncthreads();
     const uint8_t *ctab = sec + 24 + 512;
     const uint64_t table = (16 + 8 + 512 + 4 * (uint64_t)nch + 7) & ~7ull;
-    const uint32_t lane = threadIdx.x & 31;
     const uint32_t ltm = lanemask_lt();
-    for (uint32_t c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nch; c += gridDim.x * (blockDim.x >> 5)) {
+    for (uint32_t c = blockIdx.x * kDecWarps + wl; c < nch; c += gridDim.x * kDecWarps) {
         uint64_t off = 0;
         for (uint32_t k = lane; k < c; k += 32) {
             const uint8_t *p = ctab + 4 * k;
@@ -209,15 +235,22 @@ __global__ void __launch_bounds__(128) decode_kernel(const uint8_t *__restrict__
         const uint8_t *cp = ctab + 4 * c;
         const uint32_t cbytes = (uint32_t)cp[0] | ((uint32_t)cp[1] << 8) | ((uint32_t)cp[2] << 16) | ((uint32_t)cp[3] << 24);
         const uint64_t start = table + off;
-        if (cbytes < 128 || (cbytes & 3) || start + cbytes > sec_bytes) {
+        if (cbytes < 128 || (cbytes & 3) || cbytes > 128 + 2 * chunk + 2 || start + cbytes > sec_bytes) {
             if (lane == 0) set_error(&st->err, kErrCorrupt);
             continue;
         }
-        const uint8_t *ch = sec + start;
+        const uint8_t *ch = sec + start;  // 4-byte aligned (sections 8-aligned, chunks padded to 4)
+        const uint8_t *src = ch;
+        if (staged) {
+            __syncwarp();
+            for (uint32_t k = lane; k < cbytes / 4; k += 32)
+                reinterpret_cast<uint32_t *>(cbuf)[k] = reinterpret_cast<const uint32_t *>(ch)[k];
+            __syncwarp();
+            src = cbuf;
+        }
         const uint32_t W = (cbytes - 128) / 2;
-        const uint8_t *wp8 = ch + 128;
-        uint32_t x = (uint32_t)ch[4 * lane] | ((uint32_t)ch[4 * lane + 1] << 8) | ((uint32_t)ch[4 * lane + 2] << 16) |
-                     ((uint32_t)ch[4 * lane + 3] << 24);
+        const uint16_t *words = reinterpret_cast<const uint16_t *>(src + 128);
+        uint32_t x = reinterpret_cast<const uint32_t *>(src)[lane];
         const uint64_t s0 = (uint64_t)c * chunk;
         const uint32_t len = (uint32_t)((n - s0) < chunk ? (n - s0) : chunk);
         uint32_t wp = 0;
@@ -228,19 +261,17 @@ __global__ void __launch_bounds__(128) decode_kernel(const uint8_t *__restrict__
             bool need = false;
             if (valid) {
                 const uint32_t slot = x & (kM - 1);
-                const uint32_t s = slot2sym[slot];
-                out[s0 + j] = (uint8_t)s;
-                x = (uint32_t)fr[s] * (x >> kProbBits) + slot - cm[s];
+                const uint32_t sy = slot2sym[slot];
+                const uint32_t f = fc[sy];
+                out[s0 + j] = (uint8_t)sy;
+                x = (f >> 16) * (x >> kProbBits) + slot - (f & 0xFFFFu);
                 need = x < kL;
             }
             const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
             if (need) {
                 const uint32_t k = wp + __popc(m & ltm);
-                if (k < W) {
-                    x = (x << 16) | (uint32_t)wp8[2 * k] | ((uint32_t)wp8[2 * k + 1] << 8);
-                } else {
-                    bad = true;
-                }
+                if (k < W) x = (x << 16) | words[k];
+                else bad = true;
             }
             wp += __popc(m);
         }
@@ -270,9 +301,9 @@ void launch_rans_encode(const RansFrames &r, DevState *st, uint64_t max_chunks, 
     chunk_offsets_kernel<<<1, 32, 0, s>>>(r.occ_off, r.mode, r.F, r.chunk, r.chunk_off);
     count_launch();
     if (max_chunks) {
-        uint64_t blocks = (max_chunks + 3) / 4;
+        uint64_t blocks = (max_chunks + kEncWarps - 1) / kEncWarps;
         if (blocks > (uint64_t)num_sms * 16) blocks = (uint64_t)num_sms * 16;
-        encode_kernel<<<(uint32_t)blocks, 128, 0, s>>>(r.occ, r.occ_off, r.chunk_off, r.F, r.chunk, r.freq, r.cum,
+        encode_kernel<<<(uint32_t)blocks, 32 * kEncWarps, 0, s>>>(r.occ, r.occ_off, r.chunk_off, r.F, r.chunk, r.freq, r.cum,
                                                         r.chunk_slots, rans_chunk_slot_bytes(r.chunk), r.chunk_words,
                                                         r.chunk_top);
         count_launch();
@@ -286,9 +317,13 @@ void launch_rans_decode(const uint8_t *sec, uint64_t sec_bytes, uint64_t n, uint
                         uint8_t *out, DevState *st, int num_sms, cudaStream_t s)
 {
     if (nch == 0) return;
-    uint32_t blocks = (nch + 3) / 4;
+    uint32_t blocks = (nch + kDecWarps - 1) / kDecWarps;
     if (blocks > (uint32_t)num_sms * 4) blocks = (uint32_t)num_sms * 4;
-    decode_kernel<<<blocks, 128, 0, s>>>(sec, sec_bytes, n, nch, chunk, out, st);
+    // chunks of up to 32768 symbols are staged in shared memory; larger ones are read in place
+    const bool staged = chunk <= 32768;
+    const size_t smem = kM + 1024 + (staged ? (size_t)kDecWarps * ((128 + 2 * (size_t)chunk + 15) & ~(size_t)15) : 0);
+    cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    decode_kernel<<<blocks, 32 * kDecWarps, smem, s>>>(sec, sec_bytes, n, nch, chunk, out, st, staged);
     count_launch();
 }
 

@@ -205,80 +205,141 @@ __device__ __forceinline__ uint32_t gr_get(BitReader &br, uint32_t k, int &KR)
     return v;
 }
 
-// ---- encoder: one CTA per (frame, row block, rung); thread = channel ------
+// ---- encoder: one CTA per (frame, row block); thread = (rung, channel) ----
+// Rows of the block are staged through shared memory in chunks of kChunkRows
+// with asynchronous copies (double-buffered), so every rung's streams are
+// coded from one read of the coefficients and no thread waits on HBM.
 struct EncJobs {
     RlgrJob j;
-    const uint64_t *job_off;  // F + 1: first job of each frame (jobs = nb_f * R)
+    const uint64_t *job_off;  // F + 1: first job (row block) of each frame
 };
 
-template <bool FROM_INT>
-__global__ void __launch_bounds__(256) rlgr_encode_kernel(EncJobs E, const int32_t *qin)
+constexpr uint32_t kChunkRows = 32;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+template <bool FROM_INT>
+__global__ void __launch_bounds__(1024) rlgr_encode_kernel(EncJobs E, const int32_t *qin)
+{
+    extern __shared__ __align__(16) unsigned char esm[];
     const RlgrJob &j = E.j;
     const uint64_t job = blockIdx.x;
     if (job >= E.job_off[j.F]) return;
-    uint32_t lo = 0, hi = j.F;  // frame of this job
+    uint32_t lo = 0, hi = j.F;  // frame of this row block
     while (hi - lo > 1) {
-        uint32_t mid = (lo + hi) >> 1;
+        const uint32_t mid = (lo + hi) >> 1;
         if (E.job_off[mid] <= job) lo = mid; else hi = mid;
     }
     const uint32_t f = lo;
-    const uint64_t local = job - E.job_off[f];
-    const uint32_t r = (uint32_t)(local % j.R);
-    const uint32_t b = (uint32_t)(local / j.R);
+    const uint32_t b = (uint32_t)(job - E.job_off[f]);
     const uint32_t vs = j.vstart[f], nv = j.vstart[f + 1] - vs;
     const uint32_t nb = (nv + j.B - 1) / j.B;
     const uint32_t row0 = b * j.B;
     const uint32_t len = (nv - row0) < j.B ? (nv - row0) : j.B;
-    for (uint32_t c = threadIdx.x; c < j.C; c += blockDim.x) {
-        const uint64_t blk = j.blk_off[f] + ((uint64_t)r * j.C + c) * nb + b;
-        BitWriter bw{0ull, 0u, 0u, j.slots + blk * j.slot_words, j.slot_words};
-        Rlgr st;
-        st.init();
-        const float inv = FROM_INT ? 0.f : j.inv_step[r * j.C + c];
-        const uint64_t base = ((uint64_t)vs + row0) * j.C + c;
-        uint32_t i = 0;
-        for (; i + 8 <= len; i += 8) {
-            uint32_t u[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                int32_t q = FROM_INT ? qin[base + (uint64_t)(i + e) * j.C]
-                                     : quantize_f32(j.Y[base + (uint64_t)(i + e) * j.C], inv, j.tau);
-                u[e] = zz(q);
+    const uint32_t C = j.C;
+    const uint32_t chunk_elems = kChunkRows * C;
+    uint32_t *buf = reinterpret_cast<uint32_t *>(esm);  // 2 x chunk_elems words
+    const uint32_t *src = FROM_INT ? reinterpret_cast<const uint32_t *>(qin) : reinterpret_cast<const uint32_t *>(j.Y);
+    const uint64_t gbase = ((uint64_t)vs + row0) * C;
+    const bool vec = (C % 4 == 0) && ((gbase & 3) == 0) && (((uintptr_t)src & 15) == 0);
+    const uint32_t nchunks = (len + kChunkRows - 1) / kChunkRows;
+    auto issue = [&](uint32_t k) {
+        const uint32_t r0 = k * kChunkRows;
+        const uint32_t rows = (len - r0) < kChunkRows ? (len - r0) : kChunkRows;
+        uint32_t *dst = buf + (k & 1) * chunk_elems;
+        const uint32_t *gs = src + gbase + (uint64_t)r0 * C;
+        if (vec) {
+            for (uint32_t v = threadIdx.x; v < rows * C / 4; v += blockDim.x) cp_async16(dst + 4 * v, gs + 4 * v);
+        } else {
+            for (uint32_t v = threadIdx.x; v < rows * C; v += blockDim.x) cp_async4(dst + v, gs + v);
+        }
+        cp_async_commit();
+    };
+    const uint32_t t = threadIdx.x;
+    const bool act = t < j.R * C;
+    const uint32_t r = act ? t / C : 0u, c = act ? t - r * C : 0u;
+    const uint64_t blk = j.blk_off[f] + ((uint64_t)r * nb + b) * C + c;
+    BitWriter bw{0ull, 0u, 0u, j.slots + blk * j.slot_words, j.slot_words};
+    Rlgr st;
+    st.init();
+    const float inv = (FROM_INT || !act) ? 0.f : j.inv_step[r * C + c];
+    if (nchunks) issue(0);
+    for (uint32_t k = 0; k < nchunks; ++k) {
+        if (k + 1 < nchunks) {
+            issue(k + 1);
+            cp_async_wait_one();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncthreads();
+        const uint32_t rows = (len - k * kChunkRows) < kChunkRows ? (len - k * kChunkRows) : kChunkRows;
+        const uint32_t *cb = buf + (k & 1) * chunk_elems;
+        if (act) {
+            for (uint32_t i = 0; i < rows; ++i) {
+                const uint32_t w = cb[i * C + c];
+                const int32_t q = FROM_INT ? (int32_t)w : quantize_f32(__uint_as_float(w), inv, j.tau);
+                st.code(bw, zz(q));
             }
-#pragma unroll
-            for (int e = 0; e < 8; ++e) st.code(bw, u[e]);
         }
-        for (; i < len; ++i) {
-            int32_t q = FROM_INT ? qin[base + (uint64_t)i * j.C] : quantize_f32(j.Y[base + (uint64_t)i * j.C], inv, j.tau);
-            st.code(bw, zz(q));
-        }
+        __syncthreads();
+    }
+    if (act) {
         st.finish(bw);
         j.block_words[blk] = bw.nw;
         if (bw.nw > j.slot_words) atomicExch(j.overflow, 1u);
     }
 }
 
-// ---- decoder: thread = channel of one row block of one frame -------------
+// ---- decoder: one CTA per row block of one frame; thread = channel --------
+// The block's C streams are contiguous (block-major order); they are copied
+// to shared memory when they fit, then every thread decodes its channel.
 template <bool TO_INT>
-__global__ void __launch_bounds__(64) rlgr_decode_kernel(const uint32_t *payload, uint64_t payload_words,
-                                                         const uint32_t *block_words, const uint64_t *block_off,
-                                                         uint32_t stride, uint32_t nv, uint32_t C, uint32_t B,
-                                                         const float *step, float *Y, int32_t *qout, DevState *st)
+__global__ void __launch_bounds__(256) rlgr_decode_kernel(const uint32_t *payload, uint64_t payload_words,
+                                                          const uint32_t *block_words, const uint64_t *block_off,
+                                                          uint32_t stride, uint32_t nv, uint32_t C, uint32_t B,
+                                                          const float *step, float *Y, int32_t *qout, DevState *st,
+                                                          uint32_t stage_cap)
 {
-    const uint32_t nb = (nv + B - 1) / B;
+    extern __shared__ __align__(16) unsigned char dsm2[];
+    uint32_t *sw = reinterpret_cast<uint32_t *>(dsm2);
     const uint32_t b = blockIdx.x;
     const uint32_t row0 = b * B;
     const uint32_t len = (nv - row0) < B ? (nv - row0) : B;
+    const uint64_t first = (uint64_t)b * C;
+    uint64_t base = 0, end = 0;
+    bool staged = false;
+    if (block_off) {
+        base = block_off[first];
+        end = block_off[first + C];
+        staged = end >= base && end - base <= stage_cap && end <= payload_words;
+        if (staged)
+            for (uint64_t k = threadIdx.x; k < end - base; k += blockDim.x) sw[k] = payload[base + k];
+    }
+    __syncthreads();
     for (uint32_t c = threadIdx.x; c < C; c += blockDim.x) {
-        const uint64_t blk = (uint64_t)c * nb + b;
+        const uint64_t blk = first + c;
         const uint64_t off = block_off ? block_off[blk] : blk * stride;
         uint32_t nw = block_words[blk];
+        const uint32_t *wp = payload + off;
         if (off + nw > payload_words) {
             set_error(&st->err, kErrCorrupt);
             nw = 0;
+        } else if (staged) {
+            wp = sw + (off - base);
         }
-        BitReader br{payload + off, nw, 0u, 0ull, 0u, false};
+        BitReader br{wp, nw, 0u, 0ull, 0u, false};
         int K = 0, KR = 32;
         const float sc = TO_INT ? 0.f : step[c];
         uint32_t i = 0;
@@ -341,7 +402,7 @@ __global__ void job_offsets_kernel(const uint32_t *vstart, uint32_t F, uint32_t 
         job_off[f] = jo;
         blk_off[f] = bo;
         uint64_t nb = ((uint64_t)(vstart[f + 1] - vstart[f]) + B - 1) / B;
-        jo += nb * R;
+        jo += nb;
         bo += nb * R * C;
     }
     job_off[F] = jo;
@@ -364,13 +425,17 @@ void launch_rlgr_offsets(const uint32_t *vstart, uint32_t F, uint32_t B, uint32_
     count_launch();
 }
 
+static size_t enc_smem(uint32_t C) { return (size_t)2 * kChunkRows * C * 4; }
+static constexpr uint32_t kDecStageWords = 12288;  // 48 KB of staged payload per CTA
+
 void launch_rlgr_encode(const RlgrJob &j, const uint64_t *job_off, uint64_t jobs_bound, cudaStream_t s)
 {
     if (jobs_bound == 0 || j.C == 0) return;
     EncJobs E{j, job_off};
-    uint32_t threads = (j.C + 31) / 32 * 32;
-    if (threads > 256) threads = 256;
-    rlgr_encode_kernel<false><<<(uint32_t)jobs_bound, threads, 0, s>>>(E, nullptr);
+    uint32_t threads = (j.R * j.C + 31) / 32 * 32;
+    const size_t smem = enc_smem(j.C);
+    cudaFuncSetAttribute(rlgr_encode_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    rlgr_encode_kernel<false><<<(uint32_t)jobs_bound, threads, smem, s>>>(E, nullptr);
     count_launch();
 }
 
@@ -392,8 +457,9 @@ void launch_rlgr_encode_indices(const int32_t *q, const uint32_t *vstart, uint32
     j.overflow = overflow;
     EncJobs E{j, job_off};
     uint32_t threads = (C + 31) / 32 * 32;
-    if (threads > 256) threads = 256;
-    rlgr_encode_kernel<true><<<(uint32_t)jobs_bound, threads, 0, s>>>(E, q);
+    const size_t smem = enc_smem(C);
+    cudaFuncSetAttribute(rlgr_encode_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    rlgr_encode_kernel<true><<<(uint32_t)jobs_bound, threads, smem, s>>>(E, q);
     count_launch();
 }
 
@@ -404,9 +470,11 @@ void launch_rlgr_decode(const uint32_t *payload, uint64_t payload_words, const u
     if (nv == 0 || C == 0) return;
     uint32_t nb = (uint32_t)((nv + B - 1) / B);
     uint32_t threads = (C + 31) / 32 * 32;
-    if (threads > 64) threads = 64;
-    rlgr_decode_kernel<false><<<nb, threads, 0, s>>>(payload, payload_words, block_words, block_off, 0u,
-                                                     (uint32_t)nv, C, B, step, Y, nullptr, st);
+    if (threads > 256) threads = 256;
+    const size_t smem = (size_t)kDecStageWords * 4;
+    cudaFuncSetAttribute(rlgr_decode_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    rlgr_decode_kernel<false><<<nb, threads, smem, s>>>(payload, payload_words, block_words, block_off, 0u,
+                                                       (uint32_t)nv, C, B, step, Y, nullptr, st, kDecStageWords);
     count_launch();
 }
 
@@ -416,9 +484,9 @@ void launch_rlgr_decode_indices(const uint32_t *words, uint64_t total_words, con
     if (nv == 0 || C == 0) return;
     uint32_t nb = (uint32_t)((nv + B - 1) / B);
     uint32_t threads = (C + 31) / 32 * 32;
-    if (threads > 64) threads = 64;
+    if (threads > 256) threads = 256;
     rlgr_decode_kernel<true><<<nb, threads, 0, s>>>(words, total_words, bw, nullptr, stride, (uint32_t)nv, C, B,
-                                                    nullptr, nullptr, q, st);
+                                                   nullptr, nullptr, q, st, 0u);
     count_launch();
 }
 

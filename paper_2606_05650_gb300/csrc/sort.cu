@@ -47,22 +47,21 @@ __global__ void __launch_bounds__(kThreads) upsweep_kernel(const uint64_t *__res
     hist[(uint64_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of m words in place, one CTA of 1024 threads
-__global__ void __launch_bounds__(1024) scan_kernel(uint32_t *a, uint64_t m)
+// hist is digit-major [256][P]: warp d scans row d in place (exclusive) and
+// stores the digit total at hist[256 * P + d]
+__global__ void __launch_bounds__(256) scan_cols_kernel(uint32_t *hist, uint32_t P)
 {
-    __shared__ uint32_t sh[33];
-    uint64_t per = (m + 1023) / 1024;
-    uint64_t b = per * threadIdx.x, e = b + per;
-    if (e > m) e = m;
-    uint32_t s = 0;
-    for (uint64_t i = b; i < e; ++i) s += a[i];
-    uint32_t tot;
-    uint32_t run = block_exclusive_sum<uint32_t>(s, sh, &tot);
-    for (uint64_t i = b; i < e; ++i) {
-        uint32_t v = a[i];
-        a[i] = run;
-        run += v;
+    const uint32_t d = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    uint32_t *row = hist + (uint64_t)d * P;
+    uint32_t run = 0;
+    for (uint32_t b = 0; b < P; b += 32) {
+        const uint32_t c = b + lane;
+        const uint32_t v = (c < P) ? row[c] : 0u;
+        const uint32_t inc = warp_inclusive_sum(v);
+        if (c < P) row[c] = run + inc - v;
+        run += __shfl_sync(0xFFFFFFFFu, inc, 31);
     }
+    if (lane == 0) hist[(uint64_t)kRadix * P + d] = run;
 }
 
 __global__ void __launch_bounds__(kThreads) downsweep_kernel(const uint64_t *__restrict__ keys,
@@ -81,7 +80,11 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(const uint64_t *__r
     __shared__ uint32_t s_scan[33];
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    s_base[tid] = hist[(uint64_t)tid * gridDim.x + blockIdx.x];
+    {  // digit d starts after all smaller digits, then after the same digit of earlier CTAs
+        uint32_t tot;
+        const uint32_t doff = block_exclusive_sum<uint32_t>(hist[(uint64_t)kRadix * gridDim.x + tid], s_scan, &tot);
+        s_base[tid] = doff + hist[(uint64_t)tid * gridDim.x + blockIdx.x];
+    }
     uint64_t cb = (uint64_t)blockIdx.x * chunk, ce = cb + chunk;
     if (ce > n) ce = n;
     const uint32_t ltmask = lanemask_lt();
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(const uint64_t *__r
 
 uint64_t radix_sort_hist_words(uint64_t n, int num_sms)
 {
-    return (uint64_t)kRadix * sort_geom(n, num_sms).P;
+    return (uint64_t)kRadix * sort_geom(n, num_sms).P + kRadix;
 }
 
 bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint32_t *hist,
@@ -162,7 +165,7 @@ bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *va
     for (uint32_t shift = 0; shift < nbits; shift += 8) {
         upsweep_kernel<<<g.P, kThreads, 0, s>>>(ki, n, shift, g.chunk, hist);
         count_launch();
-        scan_kernel<<<1, 1024, 0, s>>>(hist, (uint64_t)kRadix * g.P);
+        scan_cols_kernel<<<kRadix / 8, 256, 0, s>>>(hist, g.P);
         count_launch();
         downsweep_kernel<<<g.P, kThreads, 0, s>>>(ki, vi, n, shift, g.chunk, hist, ko, vo);
         count_launch();

@@ -190,7 +190,7 @@ def test_rlgr_byte_identical(G, orc, nv, C, B):
     for c in range(C):
         for b in range(nb):
             ref = orc.rlgr_encode(q[b * B:(b + 1) * B, c])
-            k = c * nb + b
+            k = b * C + c
             assert bw[k] == ref.size
             assert np.array_equal(slots[k * sw: k * sw + bw[k]], ref)
     back = G.rlgr_decode_indices(_dev(slots.view(np.int32)), _dev(bw), nv, C, B)
