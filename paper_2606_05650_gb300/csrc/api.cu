@@ -873,6 +873,7 @@ gsnfs_status read_headers(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, u
 }
 
 struct DecLayout {
+    uint32_t *tabs;
     uint8_t *occ, *gap;
     uint64_t *nodes, *codes, *nvdev, *block_off, *spart;
     uint32_t *pref, *ppart;
@@ -884,6 +885,7 @@ struct DecLayout {
 size_t carve_decode(Carve &cv, DecLayout &L, const ParsedHeader &P, int num_sms)
 {
     L.grid = cv.take<FrameGrid>(1);
+    L.tabs = cv.take<uint32_t>(rans_table_words());
     L.nvdev = cv.take<uint64_t>(1);
     L.step = cv.take<float>(P.C + 1);
     L.occ = cv.take<uint8_t>(P.n_occ + 8);
@@ -947,7 +949,7 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
     else if (P.occ_mode == 2)
         launch_fill(L.occ, P.n_occ, (uint8_t)P.occ_aux, s);
     else
-        launch_rans_decode(sec, P.occ_bytes, P.n_occ, P.occ_aux, P.chunk, L.occ, dst, sms, s);
+        launch_rans_decode(sec, P.occ_bytes, P.n_occ, P.occ_aux, P.chunk, L.occ, L.tabs, dst, sms, s);
     stage_end(s, kStOccDecode);
     stage_begin(s, kStOctreeDecode);
     launch_octree_decode(occ, P.n_occ, P.J, P.lsz, L.nodes, L.pref, L.ppart, L.codes, dst, sms, s);
@@ -980,6 +982,241 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
     }
     CK(cudaGetLastError());
     uint32_t *res = (uint32_t *)(hp + 1024);
+    CK(cudaMemcpyAsync(res, &dst->err, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return map_dev_error(res[0]);
+}
+
+// ------------------------------------------------------- batched decoder ---
+// All frames of a batch are decoded by one sequence of launches: headers are
+// read with two host synchronisations for the whole batch, then every stage
+// runs over all frames at once (frame tables on the device).
+gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const uint8_t *d_in, const uint64_t *offs,
+                               float *d_pos, float *d_attr, uint64_t capacity_rows, uint64_t *rows_out)
+{
+    std::vector<ParsedHeader> P(F);
+    gsnfs_status st = grow_pinned(ctx, (size_t)F * 8192 + 65536);
+    if (st) return st;
+    CK(cudaStreamSynchronize(s));
+    uint8_t *hp = ctx->pinned;
+    for (uint32_t f = 0; f < F; ++f) {
+        if (offs[f + 1] - offs[f] < 96) return GSNFS_ERR_CORRUPT;
+        CK(cudaMemcpyAsync(hp + (size_t)f * 8192, d_in + offs[f], 96, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    for (uint32_t f = 0; f < F; ++f) {
+        st = parse_fixed(hp + (size_t)f * 8192, offs[f + 1] - offs[f], P[f]);
+        if (st) return st;
+        if (P[f].hb > 4096) return GSNFS_ERR_CORRUPT;
+    }
+    for (uint32_t f = 0; f < F; ++f) {
+        uint8_t *h = hp + (size_t)f * 8192;
+        CK(cudaMemcpyAsync(h, d_in + offs[f], P[f].hb, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h + 4096, d_in + offs[f] + P[f].hb, 24, cudaMemcpyDeviceToHost, s));
+        if (P[f].attr_bytes >= 8)
+            CK(cudaMemcpyAsync(h + 4096 + 64, d_in + offs[f] + P[f].hb + P[f].occ_bytes, 8, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    uint32_t C = 0, Jmax = 0;
+    uint64_t N = 0, n_occ = 0, nodes = 0, nblk = 0, jobs = 0, max_occ = 0;
+    uint32_t max_nch = 0, chunk_max = 0;
+    bool any_rans = false;
+    for (uint32_t f = 0; f < F; ++f) {
+        uint8_t *h = hp + (size_t)f * 8192;
+        st = parse_tables(h, P[f]);
+        if (st) return st;
+        st = parse_sections(h + 4096, h + 4096 + 64, P[f]);
+        if (st) return st;
+        if (f == 0) C = P[f].C;
+        if (P[f].C != C) return GSNFS_ERR_UNSUPPORTED;  // one attribute layout per batch
+        Jmax = std::max(Jmax, P[f].J);
+        N += P[f].nv;
+        n_occ += P[f].n_occ;
+        max_occ = std::max(max_occ, P[f].n_occ);
+        for (uint32_t d = 0; d < P[f].J; ++d) nodes += P[f].lsz[d];
+        if (C && P[f].nv) {
+            nblk += (uint64_t)P[f].nb * C;
+            jobs += P[f].nb;
+        }
+        if (P[f].occ_mode == 1) {
+            any_rans = true;
+            max_nch = std::max(max_nch, P[f].occ_aux);
+            chunk_max = std::max(chunk_max, P[f].chunk);
+        }
+    }
+    rows_out[0] = 0;
+    for (uint32_t f = 0; f < F; ++f) rows_out[f + 1] = rows_out[f] + P[f].nv;
+    if (N > capacity_rows) return GSNFS_ERR_CAPACITY;
+    if (N >= 0x7FFFFFF0ull) return GSNFS_ERR_UNSUPPORTED;
+    if (N == 0) return GSNFS_OK;
+
+    // ---- layout
+    struct L_ {
+        DecFrame *fr;
+        uint32_t *vstart, *bw_all, *tabs, *pref, *ppart;
+        uint64_t *lvl_pref, *job_off, *blk_pref, *boff_all, *spart, *nodes, *codes, *nvdev;
+        float *steps, *Y, *pool;
+        uint8_t *occ, *gap;
+        RahtPlanDev plan;
+    } L;
+    auto carve = [&](Carve &cv) {
+        L.fr = cv.take<DecFrame>(F);
+        L.vstart = cv.take<uint32_t>(F + 1);
+        L.lvl_pref = cv.take<uint64_t>((uint64_t)(Jmax + 1) * (F + 1));
+        L.job_off = cv.take<uint64_t>(F + 1);
+        L.blk_pref = cv.take<uint64_t>(F + 1);
+        L.nvdev = cv.take<uint64_t>(1);
+        L.steps = cv.take<float>((uint64_t)F * C + 1);
+        L.tabs = cv.take<uint32_t>(any_rans ? (uint64_t)F * rans_table_words() : 1);
+        L.occ = cv.take<uint8_t>(n_occ + 8);
+        L.pref = cv.take<uint32_t>(n_occ + 2);
+        L.ppart = cv.take<uint32_t>(2 * (uint64_t)ctx->num_sms + 8);
+        L.nodes = cv.take<uint64_t>(nodes + 1);
+        L.codes = cv.take<uint64_t>(N + 1);
+        L.gap = cv.take<uint8_t>(N + 2);
+        if (C) {
+            carve_plan(cv, L.plan, N, raht_tile_size(C));
+            uint64_t elems, tiles, surv;
+            raht_plan_sizes(N, L.plan.T, &elems, &tiles, &surv);
+            L.pool = cv.take<float>(surv * C);
+            L.Y = cv.take<float>(N * C + 4);
+            L.bw_all = cv.take<uint32_t>(nblk + 1);
+            L.boff_all = cv.take<uint64_t>(nblk + 2);
+            L.spart = cv.take<uint64_t>(scan_partial_words(nblk, ctx->num_sms) + 1);
+        }
+        return cv.off;
+    };
+    Carve m(nullptr);
+    st = grow_arena(ctx, carve(m), s);
+    if (st) return st;
+    Carve cv(ctx->arena);
+    carve(cv);
+
+    // ---- frame tables, packed into pinned memory after the headers
+    unsigned char *tp = hp + (size_t)F * 8192;
+    size_t o_fr = 0, o_vs = o_fr + sizeof(DecFrame) * F, o_lp = (o_vs + 4 * (F + 1) + 7) & ~(size_t)7;
+    size_t o_jo = o_lp + 8 * (size_t)(Jmax + 1) * (F + 1), o_bp = o_jo + 8 * (F + 1), o_nv = o_bp + 8 * (F + 1);
+    size_t o_st = o_nv + 8, o_end = o_st + 4 * (size_t)F * C;
+    if ((size_t)F * 8192 + o_end > ctx->pinned_cap) {
+        st = grow_pinned(ctx, (size_t)F * 8192 + o_end + 64);  // keeps nothing needed: headers are parsed
+        if (st) return st;
+        hp = ctx->pinned;
+        tp = hp + (size_t)F * 8192;
+    }
+    DecFrame *hf = reinterpret_cast<DecFrame *>(tp + o_fr);
+    uint32_t *hvs = reinterpret_cast<uint32_t *>(tp + o_vs);
+    uint64_t *hlp = reinterpret_cast<uint64_t *>(tp + o_lp);
+    uint64_t *hjo = reinterpret_cast<uint64_t *>(tp + o_jo);
+    uint64_t *hbp = reinterpret_cast<uint64_t *>(tp + o_bp);
+    float *hst = reinterpret_cast<float *>(tp + o_st);
+    uint64_t vs = 0, oo = 0, no = 0, bo = 0, jo = 0;
+    for (uint32_t f = 0; f < F; ++f) {
+        const ParsedHeader &H = P[f];
+        DecFrame d{};
+        const uint8_t *base = d_in + offs[f];
+        d.occ_sec = base + H.hb;
+        d.occ_bytes = H.occ_bytes;
+        const uint8_t *as = base + H.hb + H.occ_bytes;
+        d.bw = reinterpret_cast<const uint32_t *>(as + 8);
+        d.payload = d.bw + (uint64_t)H.nb * C;
+        d.payload_words = (C && H.nv) ? (H.attr_bytes - 8 - 4ull * C * H.nb) / 4 : 0;
+        d.occ_off = oo;
+        d.n_occ = H.n_occ;
+        d.blk_off = bo;
+        d.vstart = (uint32_t)vs;
+        d.nv = (uint32_t)H.nv;
+        d.J = H.J;
+        d.mode = H.occ_mode;
+        d.aux = H.occ_aux;
+        d.chunk = H.chunk;
+        d.B = H.B;
+        d.nb = H.nb;
+        for (int a = 0; a < 3; ++a) d.grid.lo[a] = H.lo[a];
+        d.grid.ext = H.ext;
+        d.grid.scale = std::ldexp(1.0, (int)H.J) / H.ext;
+        d.grid.cell = H.ext / std::ldexp(1.0, (int)H.J);
+        uint64_t b2 = 0;
+        for (uint32_t lv = 0; lv <= H.J; ++lv) {
+            d.lsz[lv] = H.lsz[lv];
+            d.boff[lv] = b2;
+            if (lv < H.J) {
+                d.noff[lv] = no;
+                no += H.lsz[lv];
+                b2 += H.lsz[lv];
+            }
+        }
+        hf[f] = d;
+        hvs[f] = (uint32_t)vs;
+        hjo[f] = jo;
+        hbp[f] = bo;
+        for (uint32_t c = 0; c < C; ++c) hst[(uint64_t)f * C + c] = (float)H.steps[H.groups[c]];
+        vs += H.nv;
+        oo += H.n_occ;
+        if (C && H.nv) {
+            bo += (uint64_t)H.nb * C;
+            jo += H.nb;
+        }
+    }
+    hvs[F] = (uint32_t)vs;
+    hjo[F] = jo;
+    hbp[F] = bo;
+    for (uint32_t lv = 0; lv <= Jmax; ++lv) {
+        uint64_t run = 0;
+        for (uint32_t f = 0; f < F; ++f) {
+            hlp[(uint64_t)lv * (F + 1) + f] = run;
+            if (lv < P[f].J) run += P[f].lsz[lv];
+        }
+        hlp[(uint64_t)lv * (F + 1) + F] = run;
+    }
+    memcpy(tp + o_nv, &N, 8);
+    CK(cudaMemcpyAsync(L.fr, tp + o_fr, sizeof(DecFrame) * F, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(L.vstart, tp + o_vs, 4 * (F + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(L.lvl_pref, tp + o_lp, 8 * (size_t)(Jmax + 1) * (F + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(L.job_off, tp + o_jo, 8 * (F + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(L.blk_pref, tp + o_bp, 8 * (F + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(L.nvdev, tp + o_nv, 8, cudaMemcpyHostToDevice, s));
+    if (C) CK(cudaMemcpyAsync(L.steps, tp + o_st, 4 * (size_t)F * C, cudaMemcpyHostToDevice, s));
+    DevState *dst = ctx->st;
+    CK(cudaMemsetAsync(dst, 0, 8, s));
+    const int sms = ctx->num_sms;
+
+    // a11: occupancy bytes of every frame, octree levels, voxel centres
+    stage_begin(s, kStOccDecode);
+    launch_batch_occ_bytes(L.fr, F, L.occ, max_occ, sms, s);
+    if (any_rans) launch_batch_rans_decode(L.fr, F, max_nch, chunk_max, L.occ, L.tabs, dst, s);
+    stage_end(s, kStOccDecode);
+    stage_begin(s, kStOctreeDecode);
+    launch_popc_scan(L.occ, n_occ, L.pref, L.ppart, sms, s);
+    launch_batch_roots(L.fr, F, L.nodes, L.codes, s);
+    for (uint32_t lv = 0; lv < Jmax; ++lv) {
+        const uint64_t count = hlp[(uint64_t)lv * (F + 1) + F];
+        launch_batch_expand(L.fr, F, lv, L.lvl_pref + (uint64_t)lv * (F + 1), count, L.occ, L.pref, L.nodes, L.codes,
+                            dst, sms, s);
+    }
+    launch_batch_centres_gaps(L.fr, F, L.vstart, N, L.codes, d_pos, L.gap, sms, s);
+    stage_end(s, kStOctreeDecode);
+    // a12: RAHT schedule, RLGR decode + dequantise, inverse RAHT
+    if (C && d_attr) {
+        stage_begin(s, kStPrelude);
+        launch_raht_prelude(L.plan, L.gap, dst, L.nvdev, sms, s);
+        stage_end(s, kStPrelude);
+        stage_begin(s, kStRlgrDec);
+        launch_batch_block_tables(L.fr, F, L.blk_pref, nblk, L.bw_all, sms, s);
+        launch_scan_u32_to_u64(L.bw_all, nblk, L.boff_all, L.spart, sms, s);
+        launch_rlgr_decode_batch(L.fr, F, L.job_off, jobs, L.bw_all, L.boff_all, L.steps, C, L.Y, dst, s);
+        stage_end(s, kStRlgrDec);
+        RahtIO io{};
+        io.C = C;
+        io.Y = L.Y;
+        io.out = d_attr;
+        io.pool = L.pool;
+        io.frame_shift = 64;
+        stage_begin(s, kStRahtInv);
+        launch_raht_inverse(L.plan, io, N, sms, s);
+        stage_end(s, kStRahtInv);
+    }
+    CK(cudaGetLastError());
+    uint32_t *res = reinterpret_cast<uint32_t *>(tp + ((o_end + 63) & ~(size_t)63));
     CK(cudaMemcpyAsync(res, &dst->err, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return map_dev_error(res[0]);
@@ -1173,26 +1410,14 @@ gsnfs_status gsnfs_decode_batch(gsnfs_ctx *ctx, void *stream, uint32_t frames, c
                                 const uint64_t *h_in_offsets, float *d_pos, float *d_attr, uint64_t capacity_rows,
                                 uint64_t *h_out_rows)
 {
-    if (!ctx || !d_in || !h_in_offsets || !h_out_rows || frames == 0) return GSNFS_ERR_INVALID_ARG;
+    if (!ctx || !d_in || !h_in_offsets || !h_out_rows || frames == 0 || frames > (uint32_t)kMaxFrames)
+        return GSNFS_ERR_INVALID_ARG;
+    for (uint32_t f = 0; f < frames; ++f)
+        if (h_in_offsets[f + 1] < h_in_offsets[f] || (h_in_offsets[f] % 8)) return GSNFS_ERR_INVALID_ARG;
+    if ((uintptr_t)d_in % 8 || (uintptr_t)d_attr % 16) return GSNFS_ERR_INVALID_ARG;
     DeviceGuard dg(ctx->device);
-    cudaStream_t s = (cudaStream_t)stream;
-    uint64_t row = 0;
-    h_out_rows[0] = 0;
-    for (uint32_t f = 0; f < frames; ++f) {
-        ParsedHeader P{};
-        const uint64_t b = h_in_offsets[f], e = h_in_offsets[f + 1];
-        if (e < b) return GSNFS_ERR_INVALID_ARG;
-        gsnfs_status st = read_headers(ctx, s, d_in + b, e - b, P);
-        if (st) return st;
-        if (row + P.nv > capacity_rows) return GSNFS_ERR_CAPACITY;
-        uint64_t nv = 0;
-        st = decode_impl(ctx, s, d_in + b, e - b, d_pos ? d_pos + 3 * row : nullptr,
-                         d_attr ? d_attr + P.C * row : nullptr, capacity_rows - row, &nv);
-        if (st) return st;
-        row += nv;
-        h_out_rows[f + 1] = row;
-    }
-    return GSNFS_OK;
+    return decode_batch_impl(ctx, (cudaStream_t)stream, frames, d_in, h_in_offsets, d_pos, d_attr, capacity_rows,
+                             h_out_rows);
 }
 
 }  // extern "C"
@@ -1454,7 +1679,13 @@ gsnfs_status gsnfs_occupancy_section_decode(gsnfs_ctx *ctx, void *stream, const 
     } else if (P.occ_mode == 2) {
         launch_fill(d_out, n, (uint8_t)P.occ_aux, s);
     } else {
-        launch_rans_decode(d_sec, sec_bytes, n, P.occ_aux, P.chunk, d_out, ctx->st, ctx->num_sms, s);
+        Carve m(nullptr);
+        m.take<uint32_t>(rans_table_words());
+        st = grow_arena(ctx, m.off, s);
+        if (st) return st;
+        Carve cv(ctx->arena);
+        uint32_t *tabs = cv.take<uint32_t>(rans_table_words());
+        launch_rans_decode(d_sec, sec_bytes, n, P.occ_aux, P.chunk, d_out, tabs, ctx->st, ctx->num_sms, s);
     }
     CK(cudaMemcpyAsync(hp + 64, ctx->st, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

@@ -1,0 +1,300 @@
+// Batch-wide decoding steps: many frames (streams) decoded by one sequence
+// of launches (Sec. 2.3 / Algorithms 2-3 for geometry, Sec. 3.4 and the
+// inverse of Algorithm 6 for attributes, applied to every frame at once).
+// Frames are described by a device table (DecFrame); every kernel finds the
+// frame of its work item with a binary search over per-frame prefix sums.
+#include "kernels.cuh"
+
+namespace gsnfs {
+
+namespace {
+
+constexpr uint32_t kProbBits = 15;
+constexpr uint32_t kM = 1u << kProbBits;
+constexpr uint32_t kL = 1u << 16;
+constexpr int kWarpsPerCta = 2;
+
+template <typename T>
+__device__ __forceinline__ uint32_t find_frame(const T *pref, uint32_t F, uint64_t x)
+{
+    uint32_t lo = 0, hi = F;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((uint64_t)pref[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// raw and constant occupancy sections: bytes straight into the batch buffer
+__global__ void occ_bytes_kernel(const DecFrame *fr, uint8_t *occ_all)
+{
+    const DecFrame &d = fr[blockIdx.y];
+    if (d.mode == 1) return;
+    uint8_t *dst = occ_all + d.occ_off;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < d.n_occ; i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] = (d.mode == 2) ? (uint8_t)d.aux : d.occ_sec[16 + i];
+}
+
+// per frame: slot -> symbol table and freq << 16 | cum, then a corruption flag
+__global__ void __launch_bounds__(1024) tables_kernel(const DecFrame *fr, uint32_t *tabs, uint64_t tab_words,
+                                                      DevState *st)
+{
+    const DecFrame &d = fr[blockIdx.x];
+    if (d.mode != 1) return;
+    uint32_t *tab = tabs + (uint64_t)blockIdx.x * tab_words;
+    __shared__ uint32_t s_cm[256];
+    __shared__ uint32_t s_fc[256];
+    const uint8_t *ftab = d.occ_sec + 24;
+    if (threadIdx.x < 32) {
+        uint32_t run = 0;
+        for (int b = 0; b < 256; b += 32) {
+            const int s2 = b + threadIdx.x;
+            const uint32_t v = (uint32_t)(ftab[2 * s2] | (ftab[2 * s2 + 1] << 8));
+            const uint32_t inc = warp_inclusive_sum(v);
+            s_cm[s2] = run + inc - v;
+            s_fc[s2] = (v << 16) | ((run + inc - v) & 0xFFFFu);
+            run += __shfl_sync(0xFFFFFFFFu, inc, 31);
+        }
+        if (threadIdx.x == 0) {
+            tab[kM / 4 + 256] = (run != kM);
+            if (run != kM) set_error(&st->err, kErrCorrupt);
+        }
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < 256; t += blockDim.x) tab[kM / 4 + t] = s_fc[t];
+    uint8_t *slot2sym = reinterpret_cast<uint8_t *>(tab);
+    for (uint32_t t = threadIdx.x; t < kM; t += blockDim.x) {
+        uint32_t lo = 0, hi = 256;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_cm[mid] <= t) lo = mid; else hi = mid;
+        }
+        slot2sym[t] = (uint8_t)lo;
+    }
+}
+
+// grid (chunk groups, frames): warp per chunk of frame blockIdx.y
+__global__ void __launch_bounds__(32 * kWarpsPerCta) rans_batch_kernel(const DecFrame *fr, const uint32_t *tabs,
+                                                                       uint64_t tab_words, uint32_t stage_bytes,
+                                                                       uint8_t *occ_all, DevState *st)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const DecFrame &d = fr[blockIdx.y];
+    if (d.mode != 1) return;
+    const uint32_t *tab = tabs + (uint64_t)blockIdx.y * tab_words;
+    if (tab[kM / 4 + 256] != 0) return;
+    for (uint32_t k = threadIdx.x; k < kM / 4 + 256; k += blockDim.x) reinterpret_cast<uint32_t *>(dsm)[k] = tab[k];
+    __syncthreads();
+    const uint8_t *slot2sym = dsm;
+    const uint32_t *fc = reinterpret_cast<const uint32_t *>(dsm + kM);
+    const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    uint8_t *cbuf = dsm + kM + 1024 + (size_t)wl * ((stage_bytes + 15) & ~15u);
+    const uint32_t nch = d.aux, chunk = d.chunk;
+    const uint8_t *ctab = d.occ_sec + 24 + 512;
+    const uint64_t table = (16 + 8 + 512 + 4 * (uint64_t)nch + 7) & ~7ull;
+    const uint32_t ltm = lanemask_lt();
+    for (uint32_t c = blockIdx.x * kWarpsPerCta + wl; c < nch; c += gridDim.x * kWarpsPerCta) {
+        uint64_t off = 0;
+        for (uint32_t k = lane; k < c; k += 32) {
+            const uint8_t *p = ctab + 4 * k;
+            off += (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+        }
+        for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xFFFFFFFFu, off, o);
+        const uint8_t *cp = ctab + 4 * c;
+        const uint32_t cbytes = (uint32_t)cp[0] | ((uint32_t)cp[1] << 8) | ((uint32_t)cp[2] << 16) | ((uint32_t)cp[3] << 24);
+        const uint64_t start = table + off;
+        if (cbytes < 128 || (cbytes & 3) || cbytes > 128 + 2 * chunk + 2 || start + cbytes > d.occ_bytes) {
+            if (lane == 0) set_error(&st->err, kErrCorrupt);
+            continue;
+        }
+        const uint8_t *ch = d.occ_sec + start;
+        const uint8_t *src = ch;
+        if (stage_bytes) {
+            __syncwarp();
+            for (uint32_t k = lane; k < cbytes / 4; k += 32)
+                reinterpret_cast<uint32_t *>(cbuf)[k] = reinterpret_cast<const uint32_t *>(ch)[k];
+            __syncwarp();
+            src = cbuf;
+        }
+        const uint32_t W = (cbytes - 128) / 2;
+        const uint16_t *words = reinterpret_cast<const uint16_t *>(src + 128);
+        uint32_t x = reinterpret_cast<const uint32_t *>(src)[lane];
+        const uint64_t s0 = (uint64_t)c * chunk;
+        const uint32_t len = (uint32_t)((d.n_occ - s0) < chunk ? (d.n_occ - s0) : chunk);
+        uint8_t *out = occ_all + d.occ_off;
+        uint32_t wp = 0;
+        bool bad = false;
+        for (uint32_t g = 0; g * 32 < len; ++g) {
+            const uint32_t j = g * 32 + lane;
+            const bool valid = j < len;
+            bool need = false;
+            if (valid) {
+                const uint32_t slot = x & (kM - 1);
+                const uint32_t sy = slot2sym[slot];
+                const uint32_t f = fc[sy];
+                out[s0 + j] = (uint8_t)sy;
+                x = (f >> 16) * (x >> kProbBits) + slot - (f & 0xFFFFu);
+                need = x < kL;
+            }
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
+            if (need) {
+                const uint32_t k = wp + __popc(m & ltm);
+                if (k < W) x = (x << 16) | words[k];
+                else bad = true;
+            }
+            wp += __popc(m);
+        }
+        if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) set_error(&st->err, kErrCorrupt);
+    }
+}
+
+__global__ void roots_kernel(const DecFrame *fr, uint32_t F, uint64_t *nodes, uint64_t *codes)
+{
+    const uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F || fr[f].nv == 0) return;
+    nodes[fr[f].noff[0]] = 0ull;  // implicit root code of Algorithm 2
+    (void)codes;
+}
+
+// one level d of Algorithm 3 for every frame with J > d
+__global__ void __launch_bounds__(256) expand_batch_kernel(const DecFrame *fr, uint32_t F, uint32_t d,
+                                                           const uint64_t *lvl_pref, uint64_t count,
+                                                           const uint8_t *__restrict__ occ_all,
+                                                           const uint32_t *__restrict__ pref, uint64_t *nodes,
+                                                           uint64_t *codes, DevState *st)
+{
+    for (uint64_t gp = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; gp < count;
+         gp += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t f = find_frame(lvl_pref, F, gp);
+        const DecFrame &fd = fr[f];
+        const uint32_t p = (uint32_t)(gp - lvl_pref[f]);
+        const uint32_t Md1 = fd.lsz[d + 1];
+        const uint64_t bo = fd.occ_off + fd.boff[d];
+        const uint32_t base = pref[bo];
+        if (p == 0 && pref[bo + fd.lsz[d]] - base != Md1) set_error(&st->err, kErrCorrupt);
+        const uint32_t byte = occ_all[bo + p];
+        if (byte == 0) {
+            set_error(&st->err, kErrCorrupt);
+            continue;
+        }
+        const uint64_t c = nodes[fd.noff[d] + p] << 3;
+        uint64_t *dst = (d + 1 == fd.J) ? codes + fd.vstart : nodes + fd.noff[d + 1];
+        uint32_t w = pref[bo + p] - base;
+        for (uint32_t i = 0; i < 8; ++i)
+            if (byte & (1u << i)) {
+                if (w < Md1) dst[w] = c + i;
+                ++w;
+            }
+    }
+}
+
+__device__ __forceinline__ uint32_t compact3b(uint64_t m)
+{
+    m &= 0x1249249249249249ull;
+    m = (m | (m >> 2)) & 0x10C30C30C30C30C3ull;
+    m = (m | (m >> 4)) & 0x100F00F00F00F00Full;
+    m = (m | (m >> 8)) & 0x001F0000FF0000FFull;
+    m = (m | (m >> 16)) & 0x001F00000000FFFFull;
+    m = (m | (m >> 32)) & 0x00000000001FFFFFull;
+    return (uint32_t)m;
+}
+
+// voxel centres (Sec. 2.1) and gap levels of every frame's voxels
+__global__ void centres_gaps_kernel(const DecFrame *fr, uint32_t F, const uint32_t *vstart, uint64_t nv_total,
+                                    const uint64_t *__restrict__ codes, float *pos, uint8_t *gap)
+{
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= nv_total;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        if (v == nv_total) {
+            gap[v] = (uint8_t)kInfLevel;
+            continue;
+        }
+        const uint32_t f = find_frame(vstart, F, v);
+        const uint64_t m = codes[v];
+        gap[v] = (v == vstart[f]) ? (uint8_t)kInfLevel : (uint8_t)gap_level(codes[v - 1], m, 64);
+        if (pos) {
+            const FrameGrid g = fr[f].grid;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double off = __dmul_rn(__dadd_rn((double)compact3b(m >> a), 0.5), g.cell);
+                pos[3 * v + a] = (float)__dadd_rn(g.lo[a], off);
+            }
+        }
+    }
+}
+
+__global__ void block_tables_kernel(const DecFrame *fr, uint32_t F, const uint64_t *blk_pref, uint64_t nblk,
+                                    uint32_t *bw_all)
+{
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nblk; k += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t f = find_frame(blk_pref, F, k);
+        bw_all[k] = fr[f].bw[k - blk_pref[f]];
+    }
+}
+
+uint32_t grid_for(uint64_t n, int num_sms)
+{
+    uint64_t b = (n + 255) / 256;
+    const uint64_t cap = (uint64_t)num_sms * 8;
+    if (b < 1) b = 1;
+    return (uint32_t)(b < cap ? b : cap);
+}
+
+}  // namespace
+
+void launch_batch_occ_bytes(const DecFrame *fr, uint32_t F, uint8_t *occ_all, uint64_t max_occ, int num_sms,
+                            cudaStream_t s)
+{
+    if (max_occ == 0) return;
+    uint32_t X = grid_for(max_occ, num_sms) / F + 1;
+    occ_bytes_kernel<<<dim3(X, F), 256, 0, s>>>(fr, occ_all);
+    count_launch();
+}
+
+void launch_batch_rans_decode(const DecFrame *fr, uint32_t F, uint32_t max_chunks_per_frame, uint32_t chunk_max,
+                              uint8_t *occ_all, uint32_t *tabs, DevState *st, cudaStream_t s)
+{
+    if (max_chunks_per_frame == 0) return;
+    const uint64_t tab_words = kM / 4 + 256 + 4;
+    tables_kernel<<<F, 1024, 0, s>>>(fr, tabs, tab_words, st);
+    count_launch();
+    const uint32_t stage = chunk_max <= 32768 ? 128 + 2 * chunk_max : 0u;
+    const size_t smem = kM + 1024 + (size_t)kWarpsPerCta * ((stage + 15) & ~15u);
+    cudaFuncSetAttribute(rans_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const uint32_t X = (max_chunks_per_frame + kWarpsPerCta - 1) / kWarpsPerCta;
+    rans_batch_kernel<<<dim3(X, F), 32 * kWarpsPerCta, smem, s>>>(fr, tabs, tab_words, stage, occ_all, st);
+    count_launch();
+}
+
+void launch_batch_roots(const DecFrame *fr, uint32_t F, uint64_t *nodes, uint64_t *codes, cudaStream_t s)
+{
+    roots_kernel<<<(F + 63) / 64, 64, 0, s>>>(fr, F, nodes, codes);
+    count_launch();
+}
+
+void launch_batch_expand(const DecFrame *fr, uint32_t F, uint32_t d, const uint64_t *lvl_pref, uint64_t count,
+                         const uint8_t *occ_all, const uint32_t *pref, uint64_t *nodes, uint64_t *codes,
+                         DevState *st, int num_sms, cudaStream_t s)
+{
+    if (count == 0) return;
+    expand_batch_kernel<<<grid_for(count, num_sms), 256, 0, s>>>(fr, F, d, lvl_pref, count, occ_all, pref, nodes,
+                                                                 codes, st);
+    count_launch();
+}
+
+void launch_batch_centres_gaps(const DecFrame *fr, uint32_t F, const uint32_t *vstart, uint64_t nv_total,
+                               const uint64_t *codes, float *pos, uint8_t *gap, int num_sms, cudaStream_t s)
+{
+    centres_gaps_kernel<<<grid_for(nv_total + 1, num_sms), 256, 0, s>>>(fr, F, vstart, nv_total, codes, pos, gap);
+    count_launch();
+}
+
+void launch_batch_block_tables(const DecFrame *fr, uint32_t F, const uint64_t *blk_pref, uint64_t nblk,
+                               uint32_t *bw_all, int num_sms, cudaStream_t s)
+{
+    if (nblk == 0) return;
+    block_tables_kernel<<<grid_for(nblk, num_sms), 256, 0, s>>>(fr, F, blk_pref, nblk, bw_all);
+    count_launch();
+}
+
+}  // namespace gsnfs

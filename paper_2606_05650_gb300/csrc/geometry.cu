@@ -325,6 +325,44 @@ __global__ void __launch_bounds__(kThreads) expand_kernel(const uint64_t *__rest
     }
 }
 
+// Algorithm 3 for the small top levels d < d_end in one CTA (levels are
+// separated by block barriers), saving one launch per level.
+struct LevelTable {
+    uint32_t M[kH];      // level sizes
+    uint64_t noff[kH];   // node offset of each level in the node array
+    uint64_t boff[kH];   // byte offset of each level in the occupancy stream
+};
+
+__global__ void __launch_bounds__(1024) expand_top_kernel(LevelTable lt, uint32_t d_end, uint64_t *nodes,
+                                                          const uint8_t *__restrict__ occ,
+                                                          const uint32_t *__restrict__ pref, DevState *st)
+{
+    for (uint32_t d = 0; d < d_end; ++d) {
+        const uint32_t Md = lt.M[d], Md1 = lt.M[d + 1];
+        const uint64_t boff = lt.boff[d];
+        const uint64_t *Ld = nodes + lt.noff[d];
+        uint64_t *Ld1 = nodes + lt.noff[d + 1];
+        const uint32_t base = pref[boff];
+        if (threadIdx.x == 0 && pref[boff + Md] - base != Md1) set_error(&st->err, kErrCorrupt);
+        for (uint32_t p = threadIdx.x; p < Md; p += blockDim.x) {
+            const uint32_t byte = occ[boff + p];
+            if (byte == 0) {
+                set_error(&st->err, kErrCorrupt);
+                continue;
+            }
+            const uint64_t c = Ld[p] << 3;
+            uint32_t w = pref[boff + p] - base;
+            for (uint32_t i = 0; i < 8; ++i)
+                if (byte & (1u << i)) {
+                    if (w < Md1) Ld1[w] = c + i;
+                    ++w;
+                }
+        }
+        __threadfence_block();
+        __syncthreads();
+    }
+}
+
 __global__ void gap_kernel(const uint64_t *__restrict__ codes, uint64_t nv, uint8_t *gap)
 {
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= nv; v += (uint64_t)gridDim.x * blockDim.x)
@@ -472,16 +510,41 @@ void launch_octree_decode(const uint8_t *occ, uint64_t n_occ, uint32_t J, const 
     count_launch();
     root_kernel<<<1, 1, 0, s>>>(nodes);
     count_launch();
+    // levels whose children fit one CTA comfortably are expanded together
+    LevelTable lt{};
     uint64_t noff = 0, boff = 0;
-    for (uint32_t d = 0; d < J; ++d) {
-        uint32_t Md = h_level_sizes[d], Md1 = h_level_sizes[d + 1];
-        uint64_t *Ld = nodes + noff;
-        uint64_t *Ld1 = (d + 1 == J) ? leaves : nodes + noff + Md;
-        expand_kernel<<<grid_for(Md, num_sms), kThreads, 0, s>>>(Ld, Md, occ, boff, pref, Ld1, Md1, st);
-        count_launch();
-        noff += Md;
-        boff += Md;
+    for (uint32_t d = 0; d <= J; ++d) {
+        lt.M[d] = h_level_sizes[d];
+        lt.noff[d] = noff;
+        lt.boff[d] = boff;
+        noff += h_level_sizes[d];
+        boff += h_level_sizes[d];
     }
+    uint32_t d_end = 0;
+    while (d_end + 1 < J && h_level_sizes[d_end + 1] <= 8192) ++d_end;
+    if (d_end) {
+        expand_top_kernel<<<1, 1024, 0, s>>>(lt, d_end, nodes, occ, pref, st);
+        count_launch();
+    }
+    for (uint32_t d = d_end; d < J; ++d) {
+        const uint32_t Md = h_level_sizes[d], Md1 = h_level_sizes[d + 1];
+        uint64_t *Ld = nodes + lt.noff[d];
+        uint64_t *Ld1 = (d + 1 == J) ? leaves : nodes + lt.noff[d + 1];
+        expand_kernel<<<grid_for(Md, num_sms), kThreads, 0, s>>>(Ld, Md, occ, lt.boff[d], pref, Ld1, Md1, st);
+        count_launch();
+    }
+}
+
+void launch_popc_scan(const uint8_t *occ, uint64_t n, uint32_t *pref, uint32_t *partials, int num_sms,
+                      cudaStream_t s)
+{
+    Chunks c = chunks_for(n, num_sms);
+    popc_up_kernel<<<c.P, kThreads, 0, s>>>(occ, n, c.chunk, partials);
+    count_launch();
+    scan_total_kernel<<<1, 1024, 0, s>>>(partials, c.P);
+    count_launch();
+    popc_down_kernel<<<c.P, kThreads, 0, s>>>(occ, n, c.chunk, partials, pref);
+    count_launch();
 }
 
 void launch_gap_levels(const uint64_t *codes, uint64_t nv, uint8_t *gap, cudaStream_t s)

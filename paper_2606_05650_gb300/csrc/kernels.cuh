@@ -137,6 +137,26 @@ struct RahtIO {
 void launch_raht_forward(const RahtPlanDev &p, const RahtIO &io, uint64_t nv_bound, int num_sms, cudaStream_t s);
 void launch_raht_inverse(const RahtPlanDev &p, const RahtIO &io, uint64_t nv_bound, int num_sms, cudaStream_t s);
 
+// ---- batched decoding: one description per frame (device) -------------------
+struct DecFrame {
+    const uint8_t *occ_sec;     // occupancy section of the frame's stream
+    uint64_t occ_bytes;         // its size
+    const uint32_t *bw;         // block word counts (attribute section)
+    const uint32_t *payload;    // attribute payload words
+    uint64_t payload_words;
+    uint64_t occ_off;           // first byte of the frame's occupancy bytes in the batch buffer
+    uint64_t n_occ;
+    uint64_t blk_off;           // first RLGR block of the frame (nb * C blocks)
+    uint64_t chunk_off;         // first rANS chunk of the frame
+    uint32_t vstart, nv;        // first output row, voxels
+    uint32_t J, mode, aux, chunk;
+    uint32_t B, nb;
+    FrameGrid grid;
+    uint64_t noff[22];          // node-array offset of each level (level J lives in the voxel rows)
+    uint64_t boff[22];          // offset of each level's bytes inside the frame's occupancy bytes
+    uint32_t lsz[22];
+};
+
 // ---- rlgr.cu: quantiser + block RLGR (Sec. 3.4) ----------------------------
 struct RlgrJob {
     uint32_t C;
@@ -163,6 +183,9 @@ void launch_rlgr_encode_indices(const int32_t *q, const uint32_t *vstart, uint32
 void launch_rlgr_decode(const uint32_t *payload, uint64_t payload_words, const uint32_t *block_words,
                         const uint64_t *block_off, uint64_t nv, uint32_t C, uint32_t B, const float *step, float *Y,
                         DevState *st, cudaStream_t s);
+void launch_rlgr_decode_batch(const DecFrame *fr, uint32_t F, const uint64_t *job_off, uint64_t jobs_bound,
+                              const uint32_t *bw_all, const uint64_t *boff_all, const float *steps_all, uint32_t C,
+                              float *Y, DevState *st, cudaStream_t s);
 void launch_rlgr_decode_indices(const uint32_t *words, uint64_t total_words, const uint32_t *bw, uint32_t stride,
                                 uint64_t nv, uint32_t C, uint32_t B, int32_t *q, DevState *st, cudaStream_t s);
 
@@ -184,9 +207,26 @@ struct RansFrames {
 };
 uint64_t rans_chunk_slot_bytes(uint32_t chunk);
 void launch_rans_encode(const RansFrames &r, DevState *st, uint64_t max_chunks, int num_sms, cudaStream_t s);
+uint64_t rans_table_words();
 void launch_rans_decode(const uint8_t *sec, uint64_t sec_bytes, uint64_t n, uint32_t nch, uint32_t chunk,
-                        uint8_t *out, DevState *st, int num_sms, cudaStream_t s);
+                        uint8_t *out, uint32_t *tabs, DevState *st, int num_sms, cudaStream_t s);
 void launch_fill(uint8_t *out, uint64_t n, uint8_t v, cudaStream_t s);
+
+// ---- batchdec.cu: batch-wide decoding steps --------------------------------
+void launch_batch_occ_bytes(const DecFrame *fr, uint32_t F, uint8_t *occ_all, uint64_t max_occ, int num_sms,
+                            cudaStream_t s);
+void launch_batch_rans_decode(const DecFrame *fr, uint32_t F, uint32_t max_chunks_per_frame, uint32_t chunk_max,
+                              uint8_t *occ_all, uint32_t *tabs, DevState *st, cudaStream_t s);
+void launch_popc_scan(const uint8_t *occ, uint64_t n, uint32_t *pref, uint32_t *partials, int num_sms,
+                      cudaStream_t s);
+void launch_batch_expand(const DecFrame *fr, uint32_t F, uint32_t d, const uint64_t *lvl_pref, uint64_t count,
+                         const uint8_t *occ_all, const uint32_t *pref, uint64_t *nodes, uint64_t *codes,
+                         DevState *st, int num_sms, cudaStream_t s);
+void launch_batch_roots(const DecFrame *fr, uint32_t F, uint64_t *nodes, uint64_t *codes, cudaStream_t s);
+void launch_batch_centres_gaps(const DecFrame *fr, uint32_t F, const uint32_t *vstart, uint64_t nv_total,
+                               const uint64_t *codes, float *pos, uint8_t *gap, int num_sms, cudaStream_t s);
+void launch_batch_block_tables(const DecFrame *fr, uint32_t F, const uint64_t *blk_pref, uint64_t nblk,
+                               uint32_t *bw_all, int num_sms, cudaStream_t s);
 
 // ---- scan.cu / api.cu helpers -------------------------------------------
 // exclusive scan of n u32 values into u64 offsets (out has n + 1 entries)

@@ -185,34 +185,31 @@ __global__ void section_size_kernel(const uint64_t *occ_off, const uint64_t *chu
 // copied to shared memory with coalesced loads, then decoded from there.
 constexpr int kDecWarps = 2;
 
-__global__ void __launch_bounds__(32 * kDecWarps) decode_kernel(const uint8_t *__restrict__ sec, uint64_t sec_bytes,
-                                                               uint64_t n, uint32_t nch, uint32_t chunk, uint8_t *out,
-                                                               DevState *st, bool staged)
+// slot -> symbol table (kM bytes) and freq << 16 | cum (256 words) of one
+// section, followed by a corruption flag; one CTA of 1024 threads
+__global__ void __launch_bounds__(1024) table_kernel(const uint8_t *__restrict__ sec, uint32_t *tabs, DevState *st)
 {
-    extern __shared__ __align__(16) unsigned char dsm[];
-    uint8_t *slot2sym = dsm;                                               // kM
-    uint32_t *fc = reinterpret_cast<uint32_t *>(dsm + kM);                 // 256: freq << 16 | cum
-    const uint32_t stage_bytes = staged ? 128 + 2 * chunk : 0u;
-    const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    uint8_t *cbuf = dsm + kM + 1024 + (size_t)wl * ((stage_bytes + 15) & ~15u);
-    const uint8_t *ftab = sec + 24;
     __shared__ uint32_t s_cm[256];
-    __shared__ uint32_t s_bad;
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0;
-        for (int s2 = 0; s2 < 256; ++s2) {
+    __shared__ uint32_t s_fc[256];
+    uint8_t *slot2sym = reinterpret_cast<uint8_t *>(tabs);
+    const uint8_t *ftab = sec + 24;
+    if (threadIdx.x < 32) {
+        uint32_t run = 0;
+        for (int b = 0; b < 256; b += 32) {
+            const int s2 = b + threadIdx.x;
             const uint32_t v = (uint32_t)(ftab[2 * s2] | (ftab[2 * s2 + 1] << 8));
-            fc[s2] = (v << 16) | (acc & 0xFFFFu);
-            s_cm[s2] = acc;
-            acc += v;
+            const uint32_t inc = warp_inclusive_sum(v);
+            s_cm[s2] = run + inc - v;
+            s_fc[s2] = (v << 16) | ((run + inc - v) & 0xFFFFu);
+            run += __shfl_sync(0xFFFFFFFFu, inc, 31);
         }
-        s_bad = (acc != kM);
+        if (threadIdx.x == 0) {
+            tabs[kM / 4 + 256] = (run != kM);
+            if (run != kM) set_error(&st->err, kErrCorrupt);
+        }
     }
     __syncthreads();
-    if (s_bad) {
-        if (threadIdx.x == 0) set_error(&st->err, kErrCorrupt);
-        return;
-    }
+    for (uint32_t t = threadIdx.x; t < 256; t += blockDim.x) tabs[kM / 4 + t] = s_fc[t];
     for (uint32_t t = threadIdx.x; t < kM; t += blockDim.x) {  // symbol of each slot: last s with cum[s] <= t
         uint32_t lo = 0, hi = 256;
         while (hi - lo > 1) {
@@ -221,6 +218,22 @@ __global__ void __launch_bounds__(32 * kDecWarps) decode_kernel(const uint8_t *_
         }
         slot2sym[t] = (uint8_t)lo;
     }
+}
+
+__global__ void __launch_bounds__(32 * kDecWarps) decode_kernel(const uint8_t *__restrict__ sec, uint64_t sec_bytes,
+                                                               uint64_t n, uint32_t nch, uint32_t chunk, uint8_t *out,
+                                                               DevState *st, bool staged, const uint32_t *tabs)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    uint8_t *slot2sym = dsm;                                               // kM
+    uint32_t *fc = reinterpret_cast<uint32_t *>(dsm + kM);                 // 256: freq << 16 | cum
+    const uint32_t stage_bytes = staged ? 128 + 2 * chunk : 0u;
+    const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    uint8_t *cbuf = dsm + kM + 1024 + (size_t)wl * ((stage_bytes + 15) & ~15u);
+    // decoding tables built once by table_kernel: copy them in
+    if (tabs[kM / 4 + 256] != 0) return;  // frequencies did not sum to M (reported by table_kernel)
+    for (uint32_t k = threadIdx.x; k < kM / 4 + 256; k += blockDim.x)
+        reinterpret_cast<uint32_t *>(dsm)[k] = tabs[k];
     __syncthreads();
     const uint8_t *ctab = sec + 24 + 512;
     const uint64_t table = (16 + 8 + 512 + 4 * (uint64_t)nch + 7) & ~7ull;
@@ -313,17 +326,21 @@ void launch_rans_encode(const RansFrames &r, DevState *st, uint64_t max_chunks, 
     count_launch();
 }
 
+uint64_t rans_table_words() { return kM / 4 + 256 + 4; }
+
 void launch_rans_decode(const uint8_t *sec, uint64_t sec_bytes, uint64_t n, uint32_t nch, uint32_t chunk,
-                        uint8_t *out, DevState *st, int num_sms, cudaStream_t s)
+                        uint8_t *out, uint32_t *tabs, DevState *st, int num_sms, cudaStream_t s)
 {
     if (nch == 0) return;
+    table_kernel<<<1, 1024, 0, s>>>(sec, tabs, st);
+    count_launch();
     uint32_t blocks = (nch + kDecWarps - 1) / kDecWarps;
     if (blocks > (uint32_t)num_sms * 4) blocks = (uint32_t)num_sms * 4;
     // chunks of up to 32768 symbols are staged in shared memory; larger ones are read in place
     const bool staged = chunk <= 32768;
     const size_t smem = kM + 1024 + (staged ? (size_t)kDecWarps * ((128 + 2 * (size_t)chunk + 15) & ~(size_t)15) : 0);
     cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    decode_kernel<<<blocks, 32 * kDecWarps, smem, s>>>(sec, sec_bytes, n, nch, chunk, out, st, staged);
+    decode_kernel<<<blocks, 32 * kDecWarps, smem, s>>>(sec, sec_bytes, n, nch, chunk, out, st, staged, tabs);
     count_launch();
 }
 

@@ -302,6 +302,63 @@ __global__ void __launch_bounds__(1024) rlgr_encode_kernel(EncJobs E, const int3
     }
 }
 
+// Decodes one block stream (len coefficients of channel c) into rows
+// row0 .. row0 + len - 1 of a row-major C-channel array.
+template <bool TO_INT>
+__device__ __forceinline__ void decode_stream(const uint32_t *wp, uint32_t nw, uint32_t len, uint64_t row0, uint32_t C,
+                                              uint32_t c, float sc, float *Y, int32_t *qout, DevState *st)
+{
+        BitReader br{wp, nw, 0u, 0ull, 0u, false};
+        int K = 0, KR = 32;
+        // one output row per iteration in every lane: runs are kept as pending
+        // zeros (and the nonzero that ends a partial run as a pending value), so
+        // the lanes of a warp stay in step and their row stores coalesce
+        uint32_t zeros = 0;
+        bool has_pending = false;
+        int32_t pending = 0;
+        for (uint32_t i = 0; i < len; ++i) {
+            int32_t q = 0;
+            if (zeros) {
+                --zeros;
+            } else if (has_pending) {
+                q = pending;
+                has_pending = false;
+            } else if (!br.bad) {
+                const uint32_t k = (uint32_t)K >> 4;
+                if (k == 0) {
+                    const uint32_t u = gr_get(br, (uint32_t)KR >> 4, KR);
+                    q = unzz(u);
+                    if (u == 0) {
+                        K += 3;
+                        if (K > 240) K = 240;
+                    } else {
+                        K = K >= 3 ? K - 3 : 0;
+                    }
+                } else if (br.get(1) == 0) {  // a full run of 2^k zeros (clamped at the block end)
+                    const uint32_t run = 1u << k;
+                    zeros = (run < len - i ? run : len - i) - 1;
+                    K += 4;
+                    if (K > 240) K = 240;
+                } else {  // r < 2^k zeros, then a nonzero
+                    const uint32_t rr = br.get(k);
+                    const uint32_t v = gr_get(br, (uint32_t)KR >> 4, KR);
+                    if (rr >= len - i || v == 0xFFFFFFFFu) br.bad = true;
+                    K = K >= 6 ? K - 6 : 0;
+                    if (rr == 0) {
+                        q = unzz(v + 1u);
+                    } else {
+                        zeros = rr - 1;
+                        pending = unzz(v + 1u);
+                        has_pending = true;
+                    }
+                }
+            }
+            const uint64_t o = (row0 + i) * C + c;
+            if (TO_INT) qout[o] = q; else Y[o] = __fmul_rn((float)q, sc);
+        }
+        if (br.bad) set_error(&st->err, kErrCorrupt);
+}
+
 // ---- decoder: one CTA per row block of one frame; thread = channel --------
 // The block's C streams are contiguous (block-major order); they are copied
 // to shared memory when they fit, then every thread decodes its channel.
@@ -323,7 +380,7 @@ __global__ void __launch_bounds__(256) rlgr_decode_kernel(const uint32_t *payloa
     if (block_off) {
         base = block_off[first];
         end = block_off[first + C];
-        staged = end >= base && end - base <= stage_cap && end <= payload_words;
+        staged = stage_cap && end >= base && end - base <= stage_cap && end <= payload_words;
         if (staged)
             for (uint64_t k = threadIdx.x; k < end - base; k += blockDim.x) sw[k] = payload[base + k];
     }
@@ -339,57 +396,39 @@ __global__ void __launch_bounds__(256) rlgr_decode_kernel(const uint32_t *payloa
         } else if (staged) {
             wp = sw + (off - base);
         }
-        BitReader br{wp, nw, 0u, 0ull, 0u, false};
-        int K = 0, KR = 32;
-        const float sc = TO_INT ? 0.f : step[c];
-        uint32_t i = 0;
-        while (i < len && !br.bad) {
-            const uint32_t k = (uint32_t)K >> 4;
-            if (k == 0) {
-                uint32_t u = gr_get(br, (uint32_t)KR >> 4, KR);
-                int32_t q = unzz(u);
-                const uint64_t o = ((uint64_t)row0 + i) * C + c;
-                if (TO_INT) qout[o] = q; else Y[o] = __fmul_rn((float)q, sc);
-                if (u == 0) {
-                    K += 3;
-                    if (K > 240) K = 240;
-                } else {
-                    K = K >= 3 ? K - 3 : 0;
-                }
-                ++i;
-            } else {
-                uint32_t bit = br.get(1);
-                if (br.bad) break;
-                if (bit == 0) {
-                    uint32_t run = 1u << k;
-                    if (run > len - i) run = len - i;
-                    for (uint32_t t = 0; t < run; ++t) {
-                        const uint64_t o = ((uint64_t)row0 + i + t) * C + c;
-                        if (TO_INT) qout[o] = 0; else Y[o] = 0.0f;
-                    }
-                    i += run;
-                    K += 4;
-                    if (K > 240) K = 240;
-                } else {
-                    uint32_t rr = br.get(k);
-                    uint32_t v = gr_get(br, (uint32_t)KR >> 4, KR);
-                    if (br.bad || rr >= len - i || v == 0xFFFFFFFFu) {
-                        br.bad = true;
-                        break;
-                    }
-                    for (uint32_t t = 0; t < rr; ++t) {
-                        const uint64_t o = ((uint64_t)row0 + i + t) * C + c;
-                        if (TO_INT) qout[o] = 0; else Y[o] = 0.0f;
-                    }
-                    int32_t q = unzz(v + 1u);
-                    const uint64_t o = ((uint64_t)row0 + i + rr) * C + c;
-                    if (TO_INT) qout[o] = q; else Y[o] = __fmul_rn((float)q, sc);
-                    i += rr + 1;
-                    K = K >= 6 ? K - 6 : 0;
-                }
-            }
+        decode_stream<TO_INT>(wp, nw, len, (uint64_t)row0, C, c, TO_INT ? 0.f : step[c], Y, qout, st);
+    }
+}
+
+// Batched decoder: one CTA per (frame, row block) over all frames of a batch.
+__global__ void __launch_bounds__(256) rlgr_decode_batch_kernel(const DecFrame *fr, uint32_t F,
+                                                                const uint64_t *job_off, const uint32_t *bw_all,
+                                                                const uint64_t *boff_all, const float *steps_all,
+                                                                uint32_t C, float *Y, DevState *st)
+{
+    const uint64_t job = blockIdx.x;
+    if (job >= job_off[F]) return;
+    uint32_t lo = 0, hi = F;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (job_off[mid] <= job) lo = mid; else hi = mid;
+    }
+    const DecFrame &d = fr[lo];
+    const uint32_t b = (uint32_t)(job - job_off[lo]);
+    const uint32_t row0 = b * d.B;
+    const uint32_t len = (d.nv - row0) < d.B ? (d.nv - row0) : d.B;
+    const uint64_t base = boff_all[d.blk_off];
+    for (uint32_t c = threadIdx.x; c < C; c += blockDim.x) {
+        const uint64_t blk = d.blk_off + (uint64_t)b * C + c;
+        const uint64_t off = boff_all[blk] - base;
+        uint32_t nw = bw_all[blk];
+        const uint32_t *wp = d.payload + off;
+        if (off + nw > d.payload_words) {
+            set_error(&st->err, kErrCorrupt);
+            nw = 0;
         }
-        if (br.bad) set_error(&st->err, kErrCorrupt);
+        decode_stream<false>(wp, nw, len, (uint64_t)d.vstart + row0, C, c, steps_all[(uint64_t)lo * C + c], Y, nullptr,
+                             st);
     }
 }
 
@@ -426,7 +465,6 @@ void launch_rlgr_offsets(const uint32_t *vstart, uint32_t F, uint32_t B, uint32_
 }
 
 static size_t enc_smem(uint32_t C) { return (size_t)2 * kChunkRows * C * 4; }
-static constexpr uint32_t kDecStageWords = 12288;  // 48 KB of staged payload per CTA
 
 void launch_rlgr_encode(const RlgrJob &j, const uint64_t *job_off, uint64_t jobs_bound, cudaStream_t s)
 {
@@ -471,10 +509,22 @@ void launch_rlgr_decode(const uint32_t *payload, uint64_t payload_words, const u
     uint32_t nb = (uint32_t)((nv + B - 1) / B);
     uint32_t threads = (C + 31) / 32 * 32;
     if (threads > 256) threads = 256;
-    const size_t smem = (size_t)kDecStageWords * 4;
-    cudaFuncSetAttribute(rlgr_decode_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    rlgr_decode_kernel<false><<<nb, threads, smem, s>>>(payload, payload_words, block_words, block_off, 0u,
-                                                       (uint32_t)nv, C, B, step, Y, nullptr, st, kDecStageWords);
+    // Streams are read in place: staging them in shared memory would cap the
+    // number of resident threads, and this sequential decoder needs them all.
+    rlgr_decode_kernel<false><<<nb, threads, 0, s>>>(payload, payload_words, block_words, block_off, 0u,
+                                                    (uint32_t)nv, C, B, step, Y, nullptr, st, 0u);
+    count_launch();
+}
+
+void launch_rlgr_decode_batch(const DecFrame *fr, uint32_t F, const uint64_t *job_off, uint64_t jobs_bound,
+                              const uint32_t *bw_all, const uint64_t *boff_all, const float *steps_all, uint32_t C,
+                              float *Y, DevState *st, cudaStream_t s)
+{
+    if (jobs_bound == 0 || C == 0) return;
+    uint32_t threads = (C + 31) / 32 * 32;
+    if (threads > 256) threads = 256;
+    rlgr_decode_batch_kernel<<<(uint32_t)jobs_bound, threads, 0, s>>>(fr, F, job_off, bw_all, boff_all, steps_all, C,
+                                                                       Y, st);
     count_launch();
 }
 

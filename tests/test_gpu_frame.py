@@ -185,3 +185,33 @@ def test_batched_ladder_equals_plain(G, orc):
             assert np.array_equal(got, plain.cpu().numpy()), (f, r)
     d = orc.decode_frame(host[int(offs[0]):int(offs[1])])
     assert d["codes"].size > 0
+
+
+def test_batched_decoder_equals_per_frame_decoding(G, orc):
+    # frames of uneven size and depth (one empty, one tiny) decoded in one batch
+    frames = [syn.DynamicScene(11).frame(t, n=n) for t, n in enumerate([40_000, 3, 150_000, 0, 9_000])]
+    Js = [16, 9, 18, 12, 17]
+    qp = _qp(G, 56)
+    streams = []
+    for (pos, attr), J in zip(frames, Js):
+        bs, *_ = G.encode_frame(_dev(pos), _dev(attr), J, qp)
+        streams.append(bs.cpu().numpy())
+    offs = np.zeros(len(streams) + 1, np.uint64)
+    for i, b in enumerate(streams):
+        offs[i + 1] = offs[i] + ((b.size + 7) // 8) * 8
+    buf = np.zeros(int(offs[-1]), np.uint8)
+    for i, b in enumerate(streams):
+        buf[int(offs[i]):int(offs[i]) + b.size] = b
+    # each stream's true length
+    ends = [int(offs[i]) + streams[i].size for i in range(len(streams))]
+    bounds = np.array([int(o) for o in offs[:-1]] + [ends[-1]], np.uint64)
+    pos, attr, rows = G.decode_batch(_dev(buf), bounds, 56, sum(p.shape[0] for p, _ in frames) + 8)
+    pos, attr = pos.cpu().numpy(), attr.cpu().numpy()
+    for i, b in enumerate(streams):
+        p1, a1 = G.decode_frame(_dev(b))
+        r0, r1 = int(rows[i]), int(rows[i + 1])
+        assert r1 - r0 == p1.shape[0]
+        assert np.array_equal(pos[r0:r1], p1.cpu().numpy())
+        if a1 is not None and r1 > r0:
+            assert np.array_equal(attr[r0:r1], a1.cpu().numpy())
+        assert np.array_equal(pos[r0:r1], orc.decode_frame(b)["pos"])
