@@ -229,8 +229,11 @@ __global__ void __launch_bounds__(kThreads) occ_down_kernel(const uint64_t *__re
         if (lane == 0) atomicMax(&s_hm, wm);
         __syncthreads();
         const int hm = s_hm;
+        // this warp's own highest height: above it the warp holds no node start
+        // and no child, so its counts there are zero and it has nothing to emit
+        const int hw = (int)__reduce_max_sync(0xFFFFFFFFu, (uint32_t)cm);
         for (int h = 1; h <= hm; ++h) {
-            uint32_t b = __ballot_sync(0xFFFFFFFFu, s >= h);
+            const uint32_t b = (h <= hw) ? __ballot_sync(0xFFFFFFFFu, s >= h) : 0u;
             if (lane == 0) s_w[w][h] = __popc(b);
         }
         __syncthreads();
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(kThreads) occ_down_kernel(const uint64_t *__re
             s_tot[tid] = run;
         }
         __syncthreads();
-        for (int h = 1; h <= hm; ++h) {
+        for (int h = 1; h <= hw; ++h) {
             uint32_t b = __ballot_sync(0xFFFFFFFFu, s >= h);
             bool child = ok && (s + 1 >= h);
             uint32_t incl = s_run[h] + s_w[w][h] + __popc(b & lemask);

@@ -29,7 +29,8 @@ namespace gsnfs {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;   // prelude kernels
+constexpr int kXThreads = 512;  // transform kernels: 16 warps per tile, 3 tiles per SM
 constexpr int kRounds = 64;
 constexpr uint32_t kSmemRowBytes = 56 * 1024;
 
@@ -443,7 +444,7 @@ __device__ void xform_tile(const XformArgs &A, const XformSmem &S, TileSched &sc
         sch.nbf = p.tile_nbf[tile];
         sch.nr = p.tile_nr[tile];
     }
-    for (uint32_t i = tid; i < m; i += kThreads) {
+    for (uint32_t i = tid; i < m; i += kXThreads) {
         const uint32_t d = p.dest[ps.seq_off + j0 + i];
         if (INV) S.s_src[i] = d; else S.s_dst[i] = d;
         if (gather) {
@@ -453,8 +454,8 @@ __device__ void xform_tile(const XformArgs &A, const XformSmem &S, TileSched &sc
     }
     if (gather && tid == 0) S.s_src[m] = io.seg[j0 + m];
     __syncthreads();
-    for (uint32_t r = tid; r < sch.nr; r += kThreads) sch.re[r] = p.round_end[(uint64_t)tile * kRounds + r];
-    for (uint32_t k = tid; k < sch.nbf; k += kThreads) {
+    for (uint32_t r = tid; r < sch.nr; r += kXThreads) sch.re[r] = p.round_end[(uint64_t)tile * kRounds + r];
+    for (uint32_t k = tid; k < sch.nbf; k += kXThreads) {
         S.s_idx[k] = p.bf_idx[(uint64_t)tile * T + k];
         S.s_ab[k] = p.bf_ab[(uint64_t)tile * T + k];
     }
@@ -465,13 +466,13 @@ __device__ void xform_tile(const XformArgs &A, const XformSmem &S, TileSched &sc
         const uint32_t gcount = S.s_src[m] - g0;
         staged = gcount <= 2 * T;
         if (staged)
-            for (uint32_t k = tid; k < gcount; k += kThreads) S.s_vals[k] = io.vals[g0 + k];
+            for (uint32_t k = tid; k < gcount; k += kXThreads) S.s_vals[k] = io.vals[g0 + k];
         __syncthreads();
     }
     for (uint32_t c0 = 0; c0 < C; c0 += A.Cg) {
         const uint32_t Cg = (C - c0) < A.Cg ? (C - c0) : A.Cg;
         const uint32_t L = Cg / VEC;           // vector lanes per row
-        const uint32_t slots = kThreads / L;   // rows processed per sweep
+        const uint32_t slots = kXThreads / L;   // rows processed per sweep
         const uint32_t slot = tid / L, lane = tid - slot * L;
         const uint32_t c = c0 + lane * VEC;
         const bool act = slot < slots;
@@ -578,7 +579,7 @@ __device__ void xform_tile(const XformArgs &A, const XformSmem &S, TileSched &sc
 }
 
 template <bool INV, int VEC, bool GATHER, bool QDQ>
-__global__ void __launch_bounds__(kThreads) xform_pass_kernel(XformArgs A, int q)
+__global__ void __launch_bounds__(kXThreads, 3) xform_pass_kernel(XformArgs A, int q)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TileSched sch;
@@ -591,7 +592,7 @@ __global__ void __launch_bounds__(kThreads) xform_pass_kernel(XformArgs A, int q
 
 // passes q0 .. npasses-1 in one CTA (forward: ascending; inverse: descending)
 template <bool INV, int VEC, bool QDQ>
-__global__ void __launch_bounds__(kThreads) xform_finish_kernel(XformArgs A, int q0)
+__global__ void __launch_bounds__(kXThreads, 3) xform_finish_kernel(XformArgs A, int q0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TileSched sch;
@@ -623,7 +624,7 @@ void launch_pass(const XformArgs &A, int q, uint32_t grid, size_t smem, cudaStre
 {
     auto k = xform_pass_kernel<INV, VEC, GATHER, QDQ>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<grid, kThreads, smem, s>>>(A, q);
+    k<<<grid, kXThreads, smem, s>>>(A, q);
     count_launch();
 }
 
@@ -632,7 +633,7 @@ void launch_finish(const XformArgs &A, int q0, size_t smem, cudaStream_t s)
 {
     auto k = xform_finish_kernel<INV, VEC, QDQ>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<1, kThreads, smem, s>>>(A, q0);
+    k<<<1, kXThreads, smem, s>>>(A, q0);
     count_launch();
 }
 

@@ -70,7 +70,10 @@ __device__ __forceinline__ int32_t unzz(uint32_t u)
 __device__ __forceinline__ void gr_put(BitWriter &bw, uint32_t v, uint32_t k, int &KR)
 {
     const uint32_t p = v >> k;
-    if (p < (uint32_t)kUnaryEsc) {
+    if (p < (uint32_t)kUnaryEsc && p + 1 + k <= 32u) {  // common case: unary prefix and remainder in one write
+        const uint64_t low = (uint64_t)(v & ((1u << k) - 1u));
+        bw.put(((1ull << p) - 1ull) | (low << (p + 1)), p + 1 + k);
+    } else if (p < (uint32_t)kUnaryEsc) {
         bw.put((1u << p) - 1u, p + 1);  // p ones then a zero
         if (k) bw.put(v & ((k < 32) ? ((1u << k) - 1u) : 0xFFFFFFFFu), k);
     } else {
@@ -183,9 +186,15 @@ struct BitReader {
 
 __device__ __forceinline__ uint32_t gr_get(BitReader &br, uint32_t k, int &KR)
 {
-    uint32_t p = br.ones();
+    if (br.nacc < 32) br.refill();
+    const uint64_t a = br.acc;
+    uint32_t p = (~a) ? (uint32_t)(__ffsll((long long)~a) - 1) : 64u;
     uint32_t v;
-    if (p < (uint32_t)kUnaryEsc) {
+    if (p < (uint32_t)kUnaryEsc && p + 1 + k <= br.nacc) {  // common case: one shift consumes prefix and remainder
+        v = (p << k) | (uint32_t)((a >> (p + 1)) & ((1ull << k) - 1ull));
+        br.acc = a >> (p + 1 + k);
+        br.nacc -= p + 1 + k;
+    } else if ((p = br.ones()) < (uint32_t)kUnaryEsc) {
         v = (p << k) | br.get(k);
     } else {
         uint32_t n = br.get(6);
@@ -214,7 +223,7 @@ struct EncJobs {
     const uint64_t *job_off;  // F + 1: first job (row block) of each frame
 };
 
-constexpr uint32_t kChunkRows = 32;
+constexpr uint32_t kChunkRows = 16;
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
