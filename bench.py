@@ -304,6 +304,34 @@ def gpu_extras(args, G, torch, P, A, frames, qp, out, offs, dev, stream):
                     "encode_decode_fps": round(1e3 / (statistics.mean(enc_ms) + statistics.mean(dec_ms)), 2),
                     "encode_ms_p50": round(q(enc_ms, 50), 3), "encode_ms_p99": round(q(enc_ms, 99), 3),
                     "decode_ms_p50": round(q(dec_ms, 50), 3), "decode_ms_p99": round(q(dec_ms, 99), 3)}
+    # differentiable codec layer: 500,000 Gaussians at depth 16, forward
+    # A_hat = T^T(step q(T A)) and its straight-through backward T^T T g
+    from paper_2606_05650_gb300 import synthetic as syn
+    p5, _ = syn.DynamicScene(4000).frame(0, n=500_000)
+    codes5, _, _ = G.voxelize(torch.from_numpy(p5).to(dev), J)
+    plan5 = G.RahtPlan(codes5, J, C)
+    a5 = torch.randn(codes5.shape[0], C, device=dev, requires_grad=True)
+    g5 = torch.randn_like(a5)
+    fwd, bwd = [], []
+    for it in range(8):
+        x, y, z = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        x.record(stream)
+        rec = G.AttrCodecFn.apply(a5, plan5, qp)
+        y.record(stream)
+        rec.backward(g5)
+        z.record(stream)
+        torch.cuda.synchronize()
+        a5.grad = None
+        if it >= 3:
+            fwd.append(x.elapsed_time(y))
+            bwd.append(y.elapsed_time(z))
+    nv5 = int(codes5.shape[0])
+    res["codec_layer"] = {"gaussians": 500_000, "voxels": nv5, "depth": J, "channels": C,
+                          "forward_ms": round(statistics.median(fwd), 3),
+                          "backward_ms": round(statistics.median(bwd), 3),
+                          "backward_over_forward": round(statistics.median(bwd) / statistics.median(fwd), 3),
+                          "forward_GBs": round(16 * C * nv5 / (statistics.median(fwd) / 1e3) / 1e9, 1)}
+    del plan5
     # end to end: pinned host inputs -> H2D -> encode -> D2H streams -> decode -> D2H frames
     hp = [torch.from_numpy(p).pin_memory() for p, _ in frames]
     ha = [torch.from_numpy(a).pin_memory() for _, a in frames]

@@ -184,6 +184,16 @@ gsnfs_status gsnfs_raht_forward(gsnfs_raht_plan *plan, void *stream, const float
 gsnfs_status gsnfs_raht_inverse(gsnfs_raht_plan *plan, void *stream, const float *d_in, float *d_out,
                                 const gsnfs_quant *q);
 
+/* The same two transforms evaluated in FP64 by the same kernels, with the
+ * butterfly coefficients computed in FP64 from the plan's integer weights
+ * (w0, w1): for gradient checks and reference-precision runs.  Layout,
+ * aliasing and q as above; q's steps and tau are used in FP64.  The first
+ * call allocates an FP64 survivor pool (about 8 x nv x C bytes) that the
+ * plan keeps until it is destroyed (GSNFS_ERR_OOM if that fails). */
+gsnfs_status gsnfs_raht_forward_f64(gsnfs_raht_plan *plan, void *stream, const double *d_in, double *d_out);
+gsnfs_status gsnfs_raht_inverse_f64(gsnfs_raht_plan *plan, void *stream, const double *d_in, double *d_out,
+                                    const gsnfs_quant *q);
+
 /* Block RLGR of int32 quantisation indices (Sec. 3.4): d_q is nv x C
  * row-major; each channel is cut into blocks of B coefficients and block b of
  * channel c (nb = ceil(nv / B) blocks per channel) is one RLGR stream written

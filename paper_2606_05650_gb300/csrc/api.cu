@@ -103,6 +103,9 @@ struct gsnfs_raht_plan {
     RahtPlanDev dev{};
     float *pool = nullptr;
     float *qparams = nullptr;  // inv_step[C], step[C]
+    double *pool64 = nullptr;  // survivor rows of the FP64 transforms (allocated on first use)
+    double *qparams64 = nullptr;
+    uint64_t surv_rows = 0;
     DevState *st = nullptr;
     uint64_t nv = 0;
     uint32_t C = 0, J = 0;
@@ -468,6 +471,7 @@ void carve_plan(Carve &cv, RahtPlanDev &p, uint64_t nv_cap, uint32_t T)
     p.round_end = cv.take<uint16_t>(tiles * 64);
     p.bf_idx = cv.take<uint32_t>(tiles * T);
     p.bf_ab = cv.take<float2>(tiles * T);
+    p.bf_w = nullptr;
     p.tile_carry = cv.take<uint32_t>(tiles);
     p.passes = cv.take<RahtPass>(kRahtMaxPasses + 1);
     p.npasses = cv.take<uint32_t>(1);
@@ -1714,6 +1718,8 @@ gsnfs_status gsnfs_raht_plan_create(gsnfs_ctx *ctx, void *stream, const uint64_t
         carve_plan(cv, pl->dev, nv, raht_tile_size(C));
         uint64_t elems, tiles, surv;
         raht_plan_sizes(nv, pl->dev.T, &elems, &tiles, &surv);
+        pl->dev.bf_w = cv.take<uint2>(tiles * pl->dev.T);
+        pl->surv_rows = surv;
         pl->pool = cv.take<float>(surv * C);
         pl->qparams = cv.take<float>(2 * (uint64_t)C);
         pl->st = cv.take<DevState>(1);
@@ -1752,6 +1758,7 @@ void gsnfs_raht_plan_destroy(gsnfs_raht_plan *plan)
     DeviceGuard dg(plan->ctx->device);
     cudaDeviceSynchronize();
     cudaFree(plan->mem);
+    if (plan->pool64) cudaFree(plan->pool64);
     delete plan;
 }
 
@@ -1803,6 +1810,83 @@ gsnfs_status gsnfs_raht_inverse(gsnfs_raht_plan *plan, void *stream, const float
         io.inv_step = plan->qparams;
         io.step = plan->qparams + plan->C;
         io.tau = (float)q->tau;
+    }
+    launch_raht_inverse(plan->dev, io, plan->nv, plan->ctx->num_sms, s);
+    CK(cudaGetLastError());
+    return GSNFS_OK;
+}
+
+namespace {
+
+// survivor pool and step tables of the FP64 transforms, allocated on first use
+gsnfs_status plan_f64_buffers(gsnfs_raht_plan *plan)
+{
+    if (plan->pool64) return GSNFS_OK;
+    void *m = nullptr;
+    const size_t bytes = (plan->surv_rows * plan->C + 2 * (uint64_t)plan->C) * sizeof(double);
+    if (cudaMalloc(&m, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return GSNFS_ERR_OOM;
+    }
+    plan->pool64 = (double *)m;
+    plan->qparams64 = plan->pool64 + plan->surv_rows * plan->C;
+    return GSNFS_OK;
+}
+
+}  // namespace
+
+gsnfs_status gsnfs_raht_forward_f64(gsnfs_raht_plan *plan, void *stream, const double *d_in, double *d_out)
+{
+    if (!plan || (plan->nv && (!d_in || !d_out))) return GSNFS_ERR_INVALID_ARG;
+    if ((uintptr_t)d_in % 16 || (uintptr_t)d_out % 16) return GSNFS_ERR_INVALID_ARG;
+    DeviceGuard dg(plan->ctx->device);
+    if (plan->nv == 0) return GSNFS_OK;
+    gsnfs_status st = plan_f64_buffers(plan);
+    if (st) return st;
+    RahtIOT<double> io{};
+    io.C = plan->C;
+    io.in = d_in;
+    io.Y = d_out;
+    io.pool = plan->pool64;
+    io.frame_shift = 64;
+    launch_raht_forward(plan->dev, io, plan->nv, plan->ctx->num_sms, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return GSNFS_OK;
+}
+
+gsnfs_status gsnfs_raht_inverse_f64(gsnfs_raht_plan *plan, void *stream, const double *d_in, double *d_out,
+                                    const gsnfs_quant *q)
+{
+    if (!plan || (plan->nv && (!d_in || !d_out))) return GSNFS_ERR_INVALID_ARG;
+    if ((uintptr_t)d_in % 16 || (uintptr_t)d_out % 16) return GSNFS_ERR_INVALID_ARG;
+    if (q) {
+        gsnfs_status st = check_quant(q);
+        if (st) return st;
+        if (q->num_channels != plan->C) return GSNFS_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(plan->ctx->device);
+    if (plan->nv == 0) return GSNFS_OK;
+    gsnfs_status st = plan_f64_buffers(plan);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    RahtIOT<double> io{};
+    io.C = plan->C;
+    io.Y = const_cast<double *>(d_in);
+    io.out = d_out;
+    io.pool = plan->pool64;
+    io.frame_shift = 64;
+    if (q) {
+        std::vector<double> h(2 * plan->C);
+        for (uint32_t c = 0; c < plan->C; ++c) {
+            const double stp = q->steps[q->channel_group[c]];
+            h[c] = 1.0 / stp;
+            h[plan->C + c] = stp;
+        }
+        CK(cudaMemcpyAsync(plan->qparams64, h.data(), 16 * plan->C, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        io.inv_step = plan->qparams64;
+        io.step = plan->qparams64 + plan->C;
+        io.tau = q->tau;
     }
     launch_raht_inverse(plan->dev, io, plan->nv, plan->ctx->num_sms, s);
     CK(cudaGetLastError());

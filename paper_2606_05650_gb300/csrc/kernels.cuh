@@ -108,7 +108,8 @@ struct RahtPlanDev {  // device pointers of a plan
     uint32_t *tile_nr;     // per tile: number of rounds
     uint16_t *round_end;   // per tile x 64
     uint32_t *bf_idx;      // per tile x T: i0 | i1 << 16
-    float2 *bf_ab;         // per tile x T
+    float2 *bf_ab;         // per tile x T: FP32 coefficients (a, b)
+    uint2 *bf_w;           // per tile x T: integer weights (w0, w1), or null (not recorded)
     uint32_t *tile_carry;  // per tile carried count, then exclusive base
     RahtPass *passes;      // kRahtMaxPasses
     uint32_t *npasses;     // device counter
@@ -119,23 +120,28 @@ void raht_plan_sizes(uint64_t nv_cap, uint32_t T, uint64_t *elems, uint64_t *til
 void launch_raht_prelude(const RahtPlanDev &p, const uint8_t *gap, const DevState *st, const uint64_t *nv_host,
                          int num_sms, cudaStream_t s);
 
-struct RahtIO {
+template <typename S>
+struct RahtIOT {  // S = float (codec) or double (FP64 instantiation of the same kernels)
     uint32_t C;
-    const float *in;        // forward: nv x C input rows (if gather == null)
+    const S *in;            // forward: nv x C input rows (if gather == null)
     const uint32_t *seg;    // forward gather: first sorted point of each voxel
     const uint32_t *vals;   // forward gather: local point index of sorted points
     const uint64_t *codes;  // forward gather: voxel codes (frame id) for the attr pointer
-    const float *const *attr;  // forward gather: per-frame attribute pointers
+    const S *const *attr;   // forward gather: per-frame attribute pointers
     uint32_t frame_shift;
-    float *Y;               // coefficients nv x C
-    float *out;             // inverse output nv x C
-    float *pool;            // survivor rows
-    const float *inv_step;  // inverse with quantise->dequantise: per channel 1/step (device), or null
-    const float *step;      // per channel step (device)
-    float tau;
+    S *Y;                   // coefficients nv x C
+    S *out;                 // inverse output nv x C
+    S *pool;                // survivor rows
+    const S *inv_step;      // inverse with quantise->dequantise: per channel 1/step (device), or null
+    const S *step;          // per channel step (device)
+    S tau;
 };
-void launch_raht_forward(const RahtPlanDev &p, const RahtIO &io, uint64_t nv_bound, int num_sms, cudaStream_t s);
-void launch_raht_inverse(const RahtPlanDev &p, const RahtIO &io, uint64_t nv_bound, int num_sms, cudaStream_t s);
+typedef RahtIOT<float> RahtIO;
+// FP64 transforms need a plan built with integer weights recorded (bf_w)
+template <typename S>
+void launch_raht_forward(const RahtPlanDev &p, const RahtIOT<S> &io, uint64_t nv_bound, int num_sms, cudaStream_t s);
+template <typename S>
+void launch_raht_inverse(const RahtPlanDev &p, const RahtIOT<S> &io, uint64_t nv_bound, int num_sms, cudaStream_t s);
 
 // ---- batched decoding: one description per frame (device) -------------------
 struct DecFrame {

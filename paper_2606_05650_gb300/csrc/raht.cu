@@ -190,6 +190,7 @@ __device__ void prelude_tile(const PreludeArgs &a, PreludeSmem<TMAX> &S, int q, 
             const uint32_t slot = S.lvl_off[S.g[i]] + atomicAdd(&S.lvl_cnt[S.g[i]], 1u);
             p.bf_idx[sbase + slot] = l | (i << 16);
             p.bf_ab[sbase + slot] = make_float2(ca, cb);
+            if (p.bf_w) p.bf_w[sbase + slot] = make_uint2(w0, w1);
             p.dest[ps.seq_off + j0 + i] = S.p[i];
         } else {
             // survivor: a frame root (final) iff both bounding gaps are frame boundaries
@@ -342,38 +343,63 @@ struct TileSched {
     uint16_t re[kRounds];
 };
 
-template <int VEC>
+template <typename S, int VEC>
 struct Vec;
 template <>
-struct Vec<1> {
+struct Vec<float, 1> {
     typedef float T;
     __device__ static T ld(const float *p) { return *p; }
     __device__ static void st(float *p, T v) { *p = v; }
-    __device__ static T zero() { return 0.0f; }
 };
 template <>
-struct Vec<4> {
+struct Vec<float, 4> {
     typedef float4 T;
     __device__ static T ld(const float *p) { return *reinterpret_cast<const float4 *>(p); }
     __device__ static void st(float *p, T v) { *reinterpret_cast<float4 *>(p) = v; }
-    __device__ static T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <>
+struct Vec<double, 1> {
+    typedef double T;
+    __device__ static T ld(const double *p) { return *p; }
+    __device__ static void st(double *p, T v) { *p = v; }
+};
+template <>
+struct Vec<double, 2> {
+    typedef double2 T;
+    __device__ static T ld(const double *p) { return *reinterpret_cast<const double2 *>(p); }
+    __device__ static void st(double *p, T v) { *reinterpret_cast<double2 *>(p) = v; }
 };
 
-__device__ __forceinline__ float bfly_lo(float a, float b, float y0, float y1) { return __fadd_rn(__fmul_rn(a, y0), __fmul_rn(b, y1)); }
-__device__ __forceinline__ float bfly_hi(float a, float b, float y0, float y1) { return __fsub_rn(__fmul_rn(a, y1), __fmul_rn(b, y0)); }
-__device__ __forceinline__ float ibfly_0(float a, float b, float y0, float y1) { return __fsub_rn(__fmul_rn(a, y0), __fmul_rn(b, y1)); }
-__device__ __forceinline__ float ibfly_1(float a, float b, float y0, float y1) { return __fadd_rn(__fmul_rn(b, y0), __fmul_rn(a, y1)); }
+__device__ __forceinline__ float add_rn(float x, float y) { return __fadd_rn(x, y); }
+__device__ __forceinline__ double add_rn(double x, double y) { return __dadd_rn(x, y); }
+__device__ __forceinline__ float div_rn(float x, float y) { return __fdiv_rn(x, y); }
+__device__ __forceinline__ double div_rn(double x, double y) { return __ddiv_rn(x, y); }
 
+// Eq. (1): forward (a*y0 + b*y1, a*y1 - b*y0); inverse (transposed) (a*y0 - b*y1, b*y0 + a*y1).
+// Each product and sum rounds once (no contraction), in the scalar type.
 template <bool INV>
 __device__ __forceinline__ void rot(float a, float b, float &y0, float &y1)
 {
-    float u = y0, v = y1;
+    const float u = y0, v = y1;
     if (!INV) {
-        y0 = bfly_lo(a, b, u, v);
-        y1 = bfly_hi(a, b, u, v);
+        y0 = __fadd_rn(__fmul_rn(a, u), __fmul_rn(b, v));
+        y1 = __fsub_rn(__fmul_rn(a, v), __fmul_rn(b, u));
     } else {
-        y0 = ibfly_0(a, b, u, v);
-        y1 = ibfly_1(a, b, u, v);
+        y0 = __fsub_rn(__fmul_rn(a, u), __fmul_rn(b, v));
+        y1 = __fadd_rn(__fmul_rn(b, u), __fmul_rn(a, v));
+    }
+}
+
+template <bool INV>
+__device__ __forceinline__ void rot(double a, double b, double &y0, double &y1)
+{
+    const double u = y0, v = y1;
+    if (!INV) {
+        y0 = __dadd_rn(__dmul_rn(a, u), __dmul_rn(b, v));
+        y1 = __dsub_rn(__dmul_rn(a, v), __dmul_rn(b, u));
+    } else {
+        y0 = __dsub_rn(__dmul_rn(a, u), __dmul_rn(b, v));
+        y1 = __dadd_rn(__dmul_rn(b, u), __dmul_rn(a, v));
     }
 }
 
@@ -386,53 +412,92 @@ __device__ __forceinline__ void rot(float a, float b, float4 &y0, float4 &y1)
     rot<INV>(a, b, y0.w, y1.w);
 }
 
+template <bool INV>
+__device__ __forceinline__ void rot(double a, double b, double2 &y0, double2 &y1)
+{
+    rot<INV>(a, b, y0.x, y1.x);
+    rot<INV>(a, b, y0.y, y1.y);
+}
+
 __device__ __forceinline__ float qdq(float y, float inv, float step, float tau)
 {
     return __fmul_rn((float)quantize_f32(y, inv, tau), step);
 }
 
+// the same quantiser evaluated in FP64 (index bounded by 2^30 like the FP32 one)
+__device__ __forceinline__ double qdq(double y, double inv, double step, double tau)
+{
+    double t = floor(__dadd_rn(__dmul_rn(fabs(y), inv), tau));
+    t = fmin(t, 1073741824.0);
+    return __dmul_rn(y < 0.0 ? -t : t, step);
+}
+
+template <typename S>
 struct XformArgs {
     RahtPlanDev p;
-    RahtIO io;
+    RahtIOT<S> io;
     uint32_t Cg;  // channels per group held in shared memory
 };
 
 // Shared-memory carve of the transform kernels (T = tile size).
+template <typename S>
 struct XformSmem {
     uint32_t *s_idx;   // T: butterfly i0 | i1 << 16
-    float2 *s_ab;      // T: butterfly coefficients
+    S *s_ab;           // 2T: butterfly coefficients (a, b)
     uint32_t *s_src;   // T + 1: gather segment starts (forward pass 0) or row sources (inverse)
     uint32_t *s_dst;   // T: row destinations (forward)
     uint32_t *s_vals;  // 2T: point indices of the tile's gather
     uint8_t *s_frame;  // T: frame of each voxel (batched gather)
-    float *rows;       // T x Cg
+    S *rows;           // T x Cg
 };
 
-__host__ __device__ inline size_t xform_meta_bytes(uint32_t T) { return (size_t)4 * T + 8 * T + 4 * (T + 1) + 4 * T + 8 * T + T + 64; }
-
-__device__ inline XformSmem carve_xform(unsigned char *raw, uint32_t T)
+template <typename S>
+__host__ __device__ inline size_t xform_meta_bytes(uint32_t T)
 {
-    XformSmem S;
-    S.s_ab = reinterpret_cast<float2 *>(raw);
-    S.s_idx = reinterpret_cast<uint32_t *>(raw + 8 * T);
-    S.s_src = S.s_idx + T;
-    S.s_dst = S.s_src + T + 1;
-    S.s_vals = S.s_dst + T;
-    S.s_frame = reinterpret_cast<uint8_t *>(S.s_vals + 2 * T);
-    S.rows = reinterpret_cast<float *>(raw + ((xform_meta_bytes(T) + 15) & ~(size_t)15));
-    return S;
+    return 2 * sizeof(S) * T + 4 * T + 4 * (T + 1) + 4 * T + 8 * T + T + 64;
+}
+
+template <typename S>
+__device__ inline XformSmem<S> carve_xform(unsigned char *raw, uint32_t T)
+{
+    XformSmem<S> X;
+    X.s_ab = reinterpret_cast<S *>(raw);
+    X.s_idx = reinterpret_cast<uint32_t *>(raw + 2 * sizeof(S) * T);
+    X.s_src = X.s_idx + T;
+    X.s_dst = X.s_src + T + 1;
+    X.s_vals = X.s_dst + T;
+    X.s_frame = reinterpret_cast<uint8_t *>(X.s_vals + 2 * T);
+    X.rows = reinterpret_cast<S *>(raw + ((xform_meta_bytes<S>(T) + 15) & ~(size_t)15));
+    return X;
 }
 
 constexpr int kUnroll = 4;  // rows loaded per thread before they are used
 
+// butterfly k of a tile: FP32 coefficients come from the plan; FP64 ones are
+// computed here from the integer weights, a = sqrt(w0/(w0+w1)), b = sqrt(w1/(w0+w1))
+__device__ __forceinline__ void load_coeffs(const RahtPlanDev &p, uint64_t at, float *ab)
+{
+    const float2 c = p.bf_ab[at];
+    ab[0] = c.x;
+    ab[1] = c.y;
+}
+
+__device__ __forceinline__ void load_coeffs(const RahtPlanDev &p, uint64_t at, double *ab)
+{
+    const uint2 w = p.bf_w[at];
+    const double s = (double)w.x + (double)w.y;
+    ab[0] = __dsqrt_rn(__ddiv_rn((double)w.x, s));
+    ab[1] = __dsqrt_rn(__ddiv_rn((double)w.y, s));
+}
+
 // Processes tile t of pass q for channel group [c0, c0 + Cg).
-template <bool INV, int VEC, bool GATHER, bool QDQ>
-__device__ void xform_tile(const XformArgs &A, const XformSmem &S, TileSched &sch, int q, const RahtPass &ps,
+template <typename S, bool INV, int VEC, bool GATHER, bool QDQ>
+__device__ void xform_tile(const XformArgs<S> &A, const XformSmem<S> &X, TileSched &sch, int q, const RahtPass &ps,
                            const RahtPass &nx, uint32_t t)
 {
-    typedef typename Vec<VEC>::T V;
+    typedef typename Vec<S, VEC>::T V;
     const RahtPlanDev &p = A.p;
-    const RahtIO &io = A.io;
+    const RahtIOT<S> &io = A.io;
     const uint32_t T = p.T, C = io.C;
     const uint64_t j0 = (uint64_t)t * T;
     const uint32_t m = (uint32_t)((ps.n - j0) < T ? (ps.n - j0) : T);
@@ -446,27 +511,27 @@ __device__ void xform_tile(const XformArgs &A, const XformSmem &S, TileSched &sc
     }
     for (uint32_t i = tid; i < m; i += kXThreads) {
         const uint32_t d = p.dest[ps.seq_off + j0 + i];
-        if (INV) S.s_src[i] = d; else S.s_dst[i] = d;
+        if (INV) X.s_src[i] = d; else X.s_dst[i] = d;
         if (gather) {
-            S.s_src[i] = io.seg[j0 + i];
-            if (io.frame_shift < 64) S.s_frame[i] = (uint8_t)(io.codes[j0 + i] >> io.frame_shift);
+            X.s_src[i] = io.seg[j0 + i];
+            if (io.frame_shift < 64) X.s_frame[i] = (uint8_t)(io.codes[j0 + i] >> io.frame_shift);
         }
     }
-    if (gather && tid == 0) S.s_src[m] = io.seg[j0 + m];
+    if (gather && tid == 0) X.s_src[m] = io.seg[j0 + m];
     __syncthreads();
     for (uint32_t r = tid; r < sch.nr; r += kXThreads) sch.re[r] = p.round_end[(uint64_t)tile * kRounds + r];
     for (uint32_t k = tid; k < sch.nbf; k += kXThreads) {
-        S.s_idx[k] = p.bf_idx[(uint64_t)tile * T + k];
-        S.s_ab[k] = p.bf_ab[(uint64_t)tile * T + k];
+        X.s_idx[k] = p.bf_idx[(uint64_t)tile * T + k];
+        load_coeffs(p, (uint64_t)tile * T + k, X.s_ab + 2 * k);
     }
     uint32_t g0 = 0;
     bool staged = false;
     if (gather) {
-        g0 = S.s_src[0];
-        const uint32_t gcount = S.s_src[m] - g0;
+        g0 = X.s_src[0];
+        const uint32_t gcount = X.s_src[m] - g0;
         staged = gcount <= 2 * T;
         if (staged)
-            for (uint32_t k = tid; k < gcount; k += kXThreads) S.s_vals[k] = io.vals[g0 + k];
+            for (uint32_t k = tid; k < gcount; k += kXThreads) X.s_vals[k] = io.vals[g0 + k];
         __syncthreads();
     }
     for (uint32_t c0 = 0; c0 < C; c0 += A.Cg) {
@@ -487,23 +552,23 @@ __device__ void xform_tile(const XformArgs &A, const XformSmem &S, TileSched &sc
                     const uint64_t j = j0 + i;
                     if (!INV) {
                         if (gather) {
-                            const uint32_t s0 = S.s_src[i];
-                            const uint32_t row = staged ? S.s_vals[s0 - g0] : io.vals[s0];
-                            const float *base = io.attr[io.frame_shift < 64 ? S.s_frame[i] : 0];
-                            v[u] = Vec<VEC>::ld(base + (uint64_t)row * C + c);
+                            const uint32_t s0 = X.s_src[i];
+                            const uint32_t row = staged ? X.s_vals[s0 - g0] : io.vals[s0];
+                            const S *base = io.attr[io.frame_shift < 64 ? X.s_frame[i] : 0];
+                            v[u] = Vec<S, VEC>::ld(base + (uint64_t)row * C + c);
                         } else if (q == 0) {
-                            v[u] = Vec<VEC>::ld(io.in + j * C + c);
+                            v[u] = Vec<S, VEC>::ld(io.in + j * C + c);
                         } else {
-                            v[u] = Vec<VEC>::ld(io.pool + ((uint64_t)ps.surv_off + j) * C + c);
+                            v[u] = Vec<S, VEC>::ld(io.pool + ((uint64_t)ps.surv_off + j) * C + c);
                         }
                     } else {
-                        const uint32_t d = S.s_src[i];
+                        const uint32_t d = X.s_src[i];
                         if (d & kCarry) {
-                            v[u] = Vec<VEC>::ld(io.pool + ((uint64_t)nx.surv_off + (d & ~kCarry)) * C + c);
+                            v[u] = Vec<S, VEC>::ld(io.pool + ((uint64_t)nx.surv_off + (d & ~kCarry)) * C + c);
                         } else {
-                            v[u] = Vec<VEC>::ld(io.Y + (uint64_t)d * C + c);
+                            v[u] = Vec<S, VEC>::ld(io.Y + (uint64_t)d * C + c);
                             if (QDQ) {
-                                float *pv = reinterpret_cast<float *>(&v[u]);
+                                S *pv = reinterpret_cast<S *>(&v[u]);
 #pragma unroll
                                 for (int e = 0; e < VEC; ++e)
                                     pv[e] = qdq(pv[e], io.inv_step[c + e], io.step[c + e], io.tau);
@@ -516,23 +581,23 @@ __device__ void xform_tile(const XformArgs &A, const XformSmem &S, TileSched &sc
                     const uint32_t i = ib + (uint32_t)u * slots;
                     if (i >= m) break;
                     if (gather) {  // voxels holding several points: average in input order
-                        const uint32_t s0 = S.s_src[i], s1 = S.s_src[i + 1];
+                        const uint32_t s0 = X.s_src[i], s1 = X.s_src[i + 1];
                         if (s1 - s0 > 1) {
-                            float *pa = reinterpret_cast<float *>(&v[u]);
-                            const float *base = io.attr[io.frame_shift < 64 ? S.s_frame[i] : 0];
+                            S *pa = reinterpret_cast<S *>(&v[u]);
+                            const S *base = io.attr[io.frame_shift < 64 ? X.s_frame[i] : 0];
                             for (uint32_t g = s0 + 1; g < s1; ++g) {
-                                const uint32_t row = staged ? S.s_vals[g - g0] : io.vals[g];
-                                V x = Vec<VEC>::ld(base + (uint64_t)row * C + c);
-                                const float *px = reinterpret_cast<const float *>(&x);
+                                const uint32_t row = staged ? X.s_vals[g - g0] : io.vals[g];
+                                V x = Vec<S, VEC>::ld(base + (uint64_t)row * C + c);
+                                const S *px = reinterpret_cast<const S *>(&x);
 #pragma unroll
-                                for (int e = 0; e < VEC; ++e) pa[e] = __fadd_rn(pa[e], px[e]);
+                                for (int e = 0; e < VEC; ++e) pa[e] = add_rn(pa[e], px[e]);
                             }
-                            const float cntf = (float)(s1 - s0);
+                            const S cnt = (S)(s1 - s0);
 #pragma unroll
-                            for (int e = 0; e < VEC; ++e) pa[e] = __fdiv_rn(pa[e], cntf);
+                            for (int e = 0; e < VEC; ++e) pa[e] = div_rn(pa[e], cnt);
                         }
                     }
-                    Vec<VEC>::st(S.rows + (uint64_t)i * Cg + lane * VEC, v[u]);
+                    Vec<S, VEC>::st(X.rows + (uint64_t)i * Cg + lane * VEC, v[u]);
                 }
             }
         }
@@ -543,14 +608,14 @@ __device__ void xform_tile(const XformArgs &A, const XformSmem &S, TileSched &sc
             const uint32_t kb = r ? sch.re[r - 1] : 0u, ke = sch.re[r];
             if (act) {
                 for (uint32_t k = kb + slot; k < ke; k += slots) {
-                    const uint32_t ix = S.s_idx[k];
-                    const float2 ab = S.s_ab[k];
-                    float *r0 = S.rows + (uint64_t)(ix & 0xFFFFu) * Cg + lane * VEC;
-                    float *r1 = S.rows + (uint64_t)(ix >> 16) * Cg + lane * VEC;
-                    V y0 = Vec<VEC>::ld(r0), y1 = Vec<VEC>::ld(r1);
-                    rot<INV>(ab.x, ab.y, y0, y1);
-                    Vec<VEC>::st(r0, y0);
-                    Vec<VEC>::st(r1, y1);
+                    const uint32_t ix = X.s_idx[k];
+                    const S a = X.s_ab[2 * k], b = X.s_ab[2 * k + 1];
+                    S *r0 = X.rows + (uint64_t)(ix & 0xFFFFu) * Cg + lane * VEC;
+                    S *r1 = X.rows + (uint64_t)(ix >> 16) * Cg + lane * VEC;
+                    V y0 = Vec<S, VEC>::ld(r0), y1 = Vec<S, VEC>::ld(r1);
+                    rot<INV>(a, b, y0, y1);
+                    Vec<S, VEC>::st(r0, y0);
+                    Vec<S, VEC>::st(r1, y1);
                 }
             }
             __syncthreads();
@@ -559,18 +624,18 @@ __device__ void xform_tile(const XformArgs &A, const XformSmem &S, TileSched &sc
         if (act) {
             for (uint32_t i = slot; i < m; i += slots) {
                 const uint64_t j = j0 + i;
-                V v = Vec<VEC>::ld(S.rows + (uint64_t)i * Cg + lane * VEC);
+                V v = Vec<S, VEC>::ld(X.rows + (uint64_t)i * Cg + lane * VEC);
                 if (!INV) {
-                    const uint32_t d = S.s_dst[i];
+                    const uint32_t d = X.s_dst[i];
                     if (d & kCarry)
-                        Vec<VEC>::st(io.pool + ((uint64_t)nx.surv_off + (d & ~kCarry)) * C + c, v);
+                        Vec<S, VEC>::st(io.pool + ((uint64_t)nx.surv_off + (d & ~kCarry)) * C + c, v);
                     else
-                        Vec<VEC>::st(io.Y + (uint64_t)d * C + c, v);
+                        Vec<S, VEC>::st(io.Y + (uint64_t)d * C + c, v);
                 } else {
                     if (q == 0)
-                        Vec<VEC>::st(io.out + j * C + c, v);
+                        Vec<S, VEC>::st(io.out + j * C + c, v);
                     else
-                        Vec<VEC>::st(io.pool + ((uint64_t)ps.surv_off + j) * C + c, v);
+                        Vec<S, VEC>::st(io.pool + ((uint64_t)ps.surv_off + j) * C + c, v);
                 }
             }
         }
@@ -578,103 +643,107 @@ __device__ void xform_tile(const XformArgs &A, const XformSmem &S, TileSched &sc
     }
 }
 
-template <bool INV, int VEC, bool GATHER, bool QDQ>
-__global__ void __launch_bounds__(kXThreads, 3) xform_pass_kernel(XformArgs A, int q)
+template <typename S, bool INV, int VEC, bool GATHER, bool QDQ>
+__global__ void __launch_bounds__(kXThreads, 3) xform_pass_kernel(XformArgs<S> A, int q)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TileSched sch;
-    const XformSmem S = carve_xform(smem_raw, A.p.T);
+    const XformSmem<S> X = carve_xform<S>(smem_raw, A.p.T);
     const RahtPass ps = A.p.passes[q];
     const RahtPass nx = A.p.passes[q + 1];
     for (uint32_t t = blockIdx.x; t < ps.ntiles; t += gridDim.x)
-        xform_tile<INV, VEC, GATHER, QDQ>(A, S, sch, q, ps, nx, t);
+        xform_tile<S, INV, VEC, GATHER, QDQ>(A, X, sch, q, ps, nx, t);
 }
 
 // passes q0 .. npasses-1 in one CTA (forward: ascending; inverse: descending)
-template <bool INV, int VEC, bool QDQ>
-__global__ void __launch_bounds__(kXThreads, 3) xform_finish_kernel(XformArgs A, int q0)
+template <typename S, bool INV, int VEC, bool QDQ>
+__global__ void __launch_bounds__(kXThreads, 3) xform_finish_kernel(XformArgs<S> A, int q0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TileSched sch;
-    const XformSmem S = carve_xform(smem_raw, A.p.T);
+    const XformSmem<S> X = carve_xform<S>(smem_raw, A.p.T);
     const int np = (int)*A.p.npasses;
     for (int k = 0; k < np - q0; ++k) {
         const int q = INV ? (np - 1 - k) : (q0 + k);
         const RahtPass ps = A.p.passes[q];
         const RahtPass nx = A.p.passes[q + 1];
         for (uint32_t t = 0; t < ps.ntiles; ++t)
-            xform_tile<INV, VEC, false, QDQ>(A, S, sch, q, ps, nx, t);
+            xform_tile<S, INV, VEC, false, QDQ>(A, X, sch, q, ps, nx, t);
         __threadfence_block();
         __syncthreads();
     }
 }
 
-uint32_t channel_group(uint32_t C, uint32_t T)
+uint32_t channel_group(uint32_t C, uint32_t T, uint32_t elem)
 {
-    uint32_t cg = kSmemRowBytes / (4u * T);
+    uint32_t cg = kSmemRowBytes / (elem * T);
     if (cg >= C) return C;
     if (C % 4 == 0) cg &= ~3u;
     return cg < 1 ? 1 : cg;
 }
 
-size_t xform_smem(uint32_t T, uint32_t Cg) { return ((xform_meta_bytes(T) + 15) & ~(size_t)15) + (size_t)4 * T * Cg; }
-
-template <bool INV, int VEC, bool GATHER, bool QDQ>
-void launch_pass(const XformArgs &A, int q, uint32_t grid, size_t smem, cudaStream_t s)
+template <typename S>
+size_t xform_smem(uint32_t T, uint32_t Cg)
 {
-    auto k = xform_pass_kernel<INV, VEC, GATHER, QDQ>;
+    return ((xform_meta_bytes<S>(T) + 15) & ~(size_t)15) + sizeof(S) * T * Cg;
+}
+
+template <typename S, bool INV, int VEC, bool GATHER, bool QDQ>
+void launch_pass(const XformArgs<S> &A, int q, uint32_t grid, size_t smem, cudaStream_t s)
+{
+    auto k = xform_pass_kernel<S, INV, VEC, GATHER, QDQ>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<grid, kXThreads, smem, s>>>(A, q);
     count_launch();
 }
 
-template <bool INV, int VEC, bool QDQ>
-void launch_finish(const XformArgs &A, int q0, size_t smem, cudaStream_t s)
+template <typename S, bool INV, int VEC, bool QDQ>
+void launch_finish(const XformArgs<S> &A, int q0, size_t smem, cudaStream_t s)
 {
-    auto k = xform_finish_kernel<INV, VEC, QDQ>;
+    auto k = xform_finish_kernel<S, INV, VEC, QDQ>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<1, kXThreads, smem, s>>>(A, q0);
     count_launch();
 }
 
-template <int VEC>
-void forward_all(const XformArgs &A, uint64_t nv_bound, int num_sms, cudaStream_t s)
+template <typename S, int VEC>
+void forward_all(const XformArgs<S> &A, uint64_t nv_bound, int num_sms, cudaStream_t s)
 {
     const uint32_t T = A.p.T;
-    const size_t smem = xform_smem(T, A.Cg);
+    const size_t smem = xform_smem<S>(T, A.Cg);
     uint64_t tiles = (nv_bound + T - 1) / T;
     uint32_t grid0 = (uint32_t)(tiles < 1 ? 1 : (tiles < (uint64_t)num_sms * 4 ? tiles : (uint64_t)num_sms * 4));
     for (int q = 0; q < kRahtMultiPasses; ++q) {
         uint32_t g = q == 0 ? grid0 : (grid0 < (uint32_t)num_sms ? grid0 : (uint32_t)num_sms);
         if (q == 0) stage_begin(s, kStRahtFwd0);
         if (q == 0 && A.io.seg)
-            launch_pass<false, VEC, true, false>(A, q, g, smem, s);
+            launch_pass<S, false, VEC, true, false>(A, q, g, smem, s);
         else
-            launch_pass<false, VEC, false, false>(A, q, g, smem, s);
+            launch_pass<S, false, VEC, false, false>(A, q, g, smem, s);
         if (q == 0) stage_end(s, kStRahtFwd0);
     }
-    launch_finish<false, VEC, false>(A, kRahtMultiPasses, smem, s);
+    launch_finish<S, false, VEC, false>(A, kRahtMultiPasses, smem, s);
 }
 
-template <int VEC>
-void inverse_all(const XformArgs &A, uint64_t nv_bound, int num_sms, cudaStream_t s)
+template <typename S, int VEC>
+void inverse_all(const XformArgs<S> &A, uint64_t nv_bound, int num_sms, cudaStream_t s)
 {
     const uint32_t T = A.p.T;
-    const size_t smem = xform_smem(T, A.Cg);
+    const size_t smem = xform_smem<S>(T, A.Cg);
     uint64_t tiles = (nv_bound + T - 1) / T;
     uint32_t grid0 = (uint32_t)(tiles < 1 ? 1 : (tiles < (uint64_t)num_sms * 4 ? tiles : (uint64_t)num_sms * 4));
     const bool qd = A.io.inv_step != nullptr;
     if (qd)
-        launch_finish<true, VEC, true>(A, kRahtMultiPasses, smem, s);
+        launch_finish<S, true, VEC, true>(A, kRahtMultiPasses, smem, s);
     else
-        launch_finish<true, VEC, false>(A, kRahtMultiPasses, smem, s);
+        launch_finish<S, true, VEC, false>(A, kRahtMultiPasses, smem, s);
     for (int q = kRahtMultiPasses - 1; q >= 0; --q) {
         uint32_t g = q == 0 ? grid0 : (grid0 < (uint32_t)num_sms ? grid0 : (uint32_t)num_sms);
         if (q == 0) stage_begin(s, kStRahtInv0);
         if (qd)
-            launch_pass<true, VEC, false, true>(A, q, g, smem, s);
+            launch_pass<S, true, VEC, false, true>(A, q, g, smem, s);
         else
-            launch_pass<true, VEC, false, false>(A, q, g, smem, s);
+            launch_pass<S, true, VEC, false, false>(A, q, g, smem, s);
         if (q == 0) stage_end(s, kStRahtInv0);
     }
 }
@@ -736,30 +805,39 @@ void launch_raht_prelude(const RahtPlanDev &p, const uint8_t *gap, const DevStat
         prelude_launches<4096>(a, p, st, nv_dev, num_sms, s);
 }
 
-void launch_raht_forward(const RahtPlanDev &p, const RahtIO &io, uint64_t nv_bound, int num_sms, cudaStream_t s)
+template <typename S>
+void launch_raht_forward(const RahtPlanDev &p, const RahtIOT<S> &io, uint64_t nv_bound, int num_sms, cudaStream_t s)
 {
     if (io.C == 0) return;
-    XformArgs A;
+    XformArgs<S> A;
     A.p = p;
     A.io = io;
-    A.Cg = channel_group(io.C, p.T);
-    if (A.Cg % 4 == 0 && io.C % 4 == 0)
-        forward_all<4>(A, nv_bound, num_sms, s);
+    A.Cg = channel_group(io.C, p.T, sizeof(S));
+    constexpr int kV = 16 / sizeof(S);  // 16-byte vectors: 4 floats or 2 doubles
+    if (A.Cg % kV == 0 && io.C % kV == 0)
+        forward_all<S, kV>(A, nv_bound, num_sms, s);
     else
-        forward_all<1>(A, nv_bound, num_sms, s);
+        forward_all<S, 1>(A, nv_bound, num_sms, s);
 }
 
-void launch_raht_inverse(const RahtPlanDev &p, const RahtIO &io, uint64_t nv_bound, int num_sms, cudaStream_t s)
+template <typename S>
+void launch_raht_inverse(const RahtPlanDev &p, const RahtIOT<S> &io, uint64_t nv_bound, int num_sms, cudaStream_t s)
 {
     if (io.C == 0) return;
-    XformArgs A;
+    XformArgs<S> A;
     A.p = p;
     A.io = io;
-    A.Cg = channel_group(io.C, p.T);
-    if (A.Cg % 4 == 0 && io.C % 4 == 0)
-        inverse_all<4>(A, nv_bound, num_sms, s);
+    A.Cg = channel_group(io.C, p.T, sizeof(S));
+    constexpr int kV = 16 / sizeof(S);
+    if (A.Cg % kV == 0 && io.C % kV == 0)
+        inverse_all<S, kV>(A, nv_bound, num_sms, s);
     else
-        inverse_all<1>(A, nv_bound, num_sms, s);
+        inverse_all<S, 1>(A, nv_bound, num_sms, s);
 }
+
+template void launch_raht_forward<float>(const RahtPlanDev &, const RahtIOT<float> &, uint64_t, int, cudaStream_t);
+template void launch_raht_forward<double>(const RahtPlanDev &, const RahtIOT<double> &, uint64_t, int, cudaStream_t);
+template void launch_raht_inverse<float>(const RahtPlanDev &, const RahtIOT<float> &, uint64_t, int, cudaStream_t);
+template void launch_raht_inverse<double>(const RahtPlanDev &, const RahtIOT<double> &, uint64_t, int, cudaStream_t);
 
 }  // namespace gsnfs

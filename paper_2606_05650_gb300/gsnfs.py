@@ -71,6 +71,8 @@ def lib():
                 "gsnfs_raht_plan_destroy": ([p], None),
                 "gsnfs_raht_forward": ([p, p, p, p], i32),
                 "gsnfs_raht_inverse": ([p, p, p, p, Q], i32),
+                "gsnfs_raht_forward_f64": ([p, p, p, p], i32),
+                "gsnfs_raht_inverse_f64": ([p, p, p, p, Q], i32),
                 "gsnfs_rlgr_slot_words": ([u32], u32),
                 "gsnfs_rlgr_encode_indices": ([p, p, p, u64, u32, u32, p, p], i32),
                 "gsnfs_rlgr_decode_indices": ([p, p, p, p, u64, u32, u32, p], i32),
@@ -328,23 +330,79 @@ class RahtPlan:
             self._h = None
 
     def _io(self, x):
-        _cuda_f32(x, self.C)
+        if not (x.is_cuda and x.dtype in (torch.float32, torch.float64) and x.is_contiguous() and x.dim() == 2
+                and x.shape[1] == self.C):
+            raise ValueError(f"expected a contiguous CUDA float32 or float64 tensor of shape [nv, {self.C}]")
         if x.shape[0] != self.nv:
             raise ValueError("row count differs from the plan's voxel count")
 
     def forward(self, A: torch.Tensor, out=None):
+        """Forward RAHT (FP32, or FP64 for float64 tensors)."""
         self._io(A)
         out = torch.empty_like(A) if out is None else out
-        _check(lib().gsnfs_raht_forward(self._h, _stream(A), _ptr(A), _ptr(out)), "gsnfs_raht_forward")
+        f = lib().gsnfs_raht_forward_f64 if A.dtype == torch.float64 else lib().gsnfs_raht_forward
+        _check(f(self._h, _stream(A), _ptr(A), _ptr(out)), "gsnfs_raht_forward")
         return out
 
     def inverse(self, Y: torch.Tensor, out=None, qp: QuantParams | None = None):
+        """Inverse RAHT; with qp, each coefficient is quantised and dequantised first."""
         self._io(Y)
         out = torch.empty_like(Y) if out is None else out
         q = qp.struct() if qp is not None else None
-        _check(lib().gsnfs_raht_inverse(self._h, _stream(Y), _ptr(Y), _ptr(out), ct.byref(q) if q is not None else None),
+        f = lib().gsnfs_raht_inverse_f64 if Y.dtype == torch.float64 else lib().gsnfs_raht_inverse
+        _check(f(self._h, _stream(Y), _ptr(Y), _ptr(out), ct.byref(q) if q is not None else None),
                "gsnfs_raht_inverse")
         return out
+
+
+# ---- differentiable attribute codec ------------------------------------------
+# RAHT is orthonormal (Sec. 3.2: every butterfly of Eq. (1) is a rotation), so
+# the transpose of the forward transform is the inverse transform and the
+# transpose of the inverse is the forward: each backward pass is the other
+# kernel.  A plan's survivor pool is shared by its calls: use one plan from one
+# stream at a time.
+
+class RahtForwardFn(torch.autograd.Function):
+    """Y = T A; dL/dA = T^T dL/dY = inverse RAHT of dL/dY."""
+
+    @staticmethod
+    def forward(ctx, A, plan):
+        ctx.plan = plan
+        return plan.forward(A.contiguous())
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.plan.inverse(g.contiguous()), None
+
+
+class RahtInverseFn(torch.autograd.Function):
+    """A = T^T Y; dL/dY = T dL/dA = forward RAHT of dL/dA."""
+
+    @staticmethod
+    def forward(ctx, Y, plan):
+        ctx.plan = plan
+        return plan.inverse(Y.contiguous())
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.plan.forward(g.contiguous()), None
+
+
+class AttrCodecFn(torch.autograd.Function):
+    """The attribute codec as a differentiable layer (Sec. 3.2 with the
+    quantiser of Sec. 3.4): forward A_hat = T^T (step * q(T A)), the encoder's
+    reconstruction; the quantiser's gradient is taken as the identity
+    (straight-through), so dL/dA = T^T T dL/dA_hat, evaluated by the forward
+    kernel followed by the inverse kernel."""
+
+    @staticmethod
+    def forward(ctx, A, plan, qp):
+        ctx.plan = plan
+        return plan.inverse(plan.forward(A.contiguous()), qp=qp)
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.plan.inverse(ctx.plan.forward(g.contiguous())), None, None
 
 
 def rlgr_slot_words(B: int) -> int:
