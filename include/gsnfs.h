@@ -77,6 +77,21 @@ const char *gsnfs_status_string(gsnfs_status s);
  * before capturing the codec into a CUDA graph). */
 gsnfs_status gsnfs_reserve(gsnfs_ctx *ctx, uint64_t n, uint32_t C, uint32_t J, const gsnfs_quant *q);
 
+/* CUDA graphs for the encoder (off by default).  When on, the device work of
+ * gsnfs_encode_frame / gsnfs_encode_batch (from the parameter uploads to the
+ * result read-back) is captured into a graph the first time a request shape
+ * is seen and replayed afterwards.  The shape is: frame count, rungs, point
+ * count and depth of every frame, channels, groups, RLGR block, rANS chunk,
+ * tau, output buffer and capacity, reconstruction buffers, and the context's
+ * scratch addresses; point and attribute pointers, steps and rung scales may
+ * change between replays.  Up to 64 graphs are kept (least recently used
+ * dropped); growing the scratch drops them all.  The graph runs on a stream
+ * of the context ordered after the caller's stream and joined back to it.
+ * A capture that fails falls back to running the work directly. */
+gsnfs_status gsnfs_set_graphs(gsnfs_ctx *ctx, int enable);
+/* out[0] replays, out[1] captures, out[2] failed captures, out[3] graphs cached. */
+gsnfs_status gsnfs_graph_stats(gsnfs_ctx *ctx, uint64_t *out);
+
 /* Upper bound of the encoded size of a frame of n points (host only). */
 gsnfs_status gsnfs_max_bitstream_bytes(uint64_t n, uint32_t J, const gsnfs_quant *q, uint64_t *out);
 

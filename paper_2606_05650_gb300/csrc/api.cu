@@ -64,11 +64,22 @@ const char *kStageNames[kStCount] = {"voxelize", "sort", "dedup", "occupancy", "
                                      "raht_inverse_pass0"};
 }  // namespace
 
+// While a call is being captured into a CUDA graph, its launches are counted
+// into the graph (and added to the total at every replay) and stage events are
+// not recorded.
+thread_local uint64_t *t_capture_launches = nullptr;
+
 namespace gsnfs {
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch()
+{
+    if (t_capture_launches)
+        ++*t_capture_launches;
+    else
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 void stage_begin(cudaStream_t s, int id)
 {
-    if (!g_prof.on) return;
+    if (!g_prof.on || t_capture_launches) return;
     std::lock_guard<std::mutex> lk(g_prof.mu);
     cudaEvent_t e = g_prof.get();
     cudaEventRecord(e, s);
@@ -76,7 +87,7 @@ void stage_begin(cudaStream_t s, int id)
 }
 void stage_end(cudaStream_t s, int id)
 {
-    if (!g_prof.on) return;
+    if (!g_prof.on || t_capture_launches) return;
     std::lock_guard<std::mutex> lk(g_prof.mu);
     if (g_prof.open[id].empty()) return;
     auto r = g_prof.open[id].back();
@@ -87,6 +98,15 @@ void stage_end(cudaStream_t s, int id)
 }
 }  // namespace gsnfs
 
+// One captured encode: the request's shape and buffers (key) and the
+// instantiated graph that replays its device work.
+struct GraphEntry {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t launches = 0;  // kernels in the graph
+    uint64_t last_use = 0;
+};
+
 struct gsnfs_ctx {
     int device = 0;
     int num_sms = 0;
@@ -95,6 +115,12 @@ struct gsnfs_ctx {
     unsigned char *pinned = nullptr;
     size_t pinned_cap = 0;
     DevState *st = nullptr;
+    // CUDA graphs of the encoder (off by default)
+    bool graphs = false;
+    cudaStream_t gstream = nullptr;  // capture / replay stream, joined to the caller's by events
+    cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+    std::vector<GraphEntry> gcache;
+    uint64_t gtick = 0, ghits = 0, gcaptures = 0, gfailures = 0;
 };
 
 struct gsnfs_raht_plan {
@@ -155,10 +181,20 @@ struct Carve {
     }
 };
 
+// Captured graphs hold arena and staging addresses: drop them when either moves.
+void drop_graphs(gsnfs_ctx *ctx)
+{
+    for (auto &g : ctx->gcache)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    ctx->gcache.clear();
+}
+
 gsnfs_status grow_arena(gsnfs_ctx *ctx, size_t need, cudaStream_t s)
 {
     if (need <= ctx->arena_cap) return GSNFS_OK;
     CK(cudaStreamSynchronize(s));
+    if (ctx->gstream) CK(cudaStreamSynchronize(ctx->gstream));
+    drop_graphs(ctx);
     if (ctx->arena) CK(cudaFree(ctx->arena));
     ctx->arena = nullptr;
     ctx->arena_cap = 0;
@@ -171,6 +207,8 @@ gsnfs_status grow_arena(gsnfs_ctx *ctx, size_t need, cudaStream_t s)
 gsnfs_status grow_pinned(gsnfs_ctx *ctx, size_t need)
 {
     if (need <= ctx->pinned_cap) return GSNFS_OK;
+    if (ctx->gstream) CK(cudaStreamSynchronize(ctx->gstream));
+    drop_graphs(ctx);
     if (ctx->pinned) CK(cudaFreeHost(ctx->pinned));
     ctx->pinned = nullptr;
     size_t cap = need + (1 << 16);
@@ -550,6 +588,61 @@ size_t carve_encode(Carve &cv, EncLayout &L, const EncodeReq &rq, int num_sms, b
     return cv.off;
 }
 
+constexpr size_t kGraphCacheSize = 64;
+
+// Replays the graph captured for `key`, capturing it first on a miss.  The
+// graph runs on the context's own stream, ordered after the caller's stream
+// by one event and joined back by another.  A capture that fails runs the
+// work eagerly instead (counted in gfailures).
+template <typename Enqueue>
+gsnfs_status run_graphed(gsnfs_ctx *ctx, cudaStream_t s, std::vector<uint64_t> key, Enqueue &enqueue)
+{
+    if (!ctx->gstream) {
+        CK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ctx->gev_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->gev_out, cudaEventDisableTiming));
+    }
+    GraphEntry *hit = nullptr;
+    for (auto &g : ctx->gcache)
+        if (g.key == key) hit = &g;
+    if (!hit) {
+        uint64_t launches = 0;
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal));
+        t_capture_launches = &launches;
+        gsnfs_status st = enqueue(ctx->gstream);
+        t_capture_launches = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ctx->gstream, &graph);
+        cudaGraphExec_t exec = nullptr;
+        if (st == GSNFS_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (st != GSNFS_OK || e != cudaSuccess || !exec) {
+            cudaGetLastError();
+            ++ctx->gfailures;
+            return enqueue(s);
+        }
+        if (ctx->gcache.size() >= kGraphCacheSize) {
+            auto lru = std::min_element(ctx->gcache.begin(), ctx->gcache.end(),
+                                        [](const GraphEntry &a, const GraphEntry &b) { return a.last_use < b.last_use; });
+            cudaGraphExecDestroy(lru->exec);
+            ctx->gcache.erase(lru);
+        }
+        ctx->gcache.push_back(GraphEntry{std::move(key), exec, launches, 0});
+        hit = &ctx->gcache.back();
+        ++ctx->gcaptures;
+    } else {
+        ++ctx->ghits;
+    }
+    hit->last_use = ++ctx->gtick;
+    CK(cudaEventRecord(ctx->gev_in, s));
+    CK(cudaStreamWaitEvent(ctx->gstream, ctx->gev_in, 0));
+    CK(cudaGraphLaunch(hit->exec, ctx->gstream));
+    CK(cudaEventRecord(ctx->gev_out, ctx->gstream));
+    CK(cudaStreamWaitEvent(s, ctx->gev_out, 0));
+    g_launches.fetch_add(hit->launches, std::memory_order_relaxed);
+    return GSNFS_OK;
+}
+
 gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool worst_slots)
 {
     const uint32_t F = rq.F, R = rq.R;
@@ -611,135 +704,156 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
         for (uint32_t g = 0; g < G; ++g) ((double *)(hp + o_srg))[r * G + g] = q->steps[g] * sc;
     }
     for (uint32_t c = 0; c < C; ++c) hp[o_grp + c] = q->channel_group[c];
-    CK(cudaMemcpyAsync((void *)L.posp, hp + o_pos, 8 * F, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync((void *)L.attrp, hp + o_attr, 8 * F, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(L.poff, hp + o_poff, 8 * (F + 1), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(L.Jd, hp + o_J, 4 * F, cudaMemcpyHostToDevice, s));
-    if (C) {
-        CK(cudaMemcpyAsync(L.inv_step, hp + o_inv, 4 * (size_t)R * C, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(L.step, hp + o_step, 4 * (size_t)R * C, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(L.steps_rg, hp + o_srg, 8 * (size_t)R * G, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(L.groups, hp + o_grp, C, cudaMemcpyHostToDevice, s));
-    }
-    CK(cudaMemsetAsync(L.overflow, 0, 16, s));
-
-    DevState *dst = ctx->st;
-    const int sms = ctx->num_sms;
-    FrameSet fs;
-    fs.F = F;
-    fs.frame_shift = frame_shift;
-    fs.pos = L.posp;
-    fs.attr = L.attrp;
-    fs.poff = L.poff;
-    fs.J = L.Jd;
-    fs.grid = L.grid;
-
-    // a1: voxelise + Morton
-    stage_begin(s, kStVoxelize);
-    launch_voxelize(fs, dst, N, nmax, L.keys, L.vals, sms, s);
-    stage_end(s, kStVoxelize);
-    // a2: radix sort
-    stage_begin(s, kStSort);
-    bool alt = radix_sort(L.keys, L.vals, L.keys_alt, L.vals_alt, L.hist, N, nbits, sms, s);
-    stage_end(s, kStSort);
-    const uint64_t *skeys = alt ? L.keys_alt : L.keys;
-    const uint32_t *svals = alt ? L.vals_alt : L.vals;
-    // a3: dedup
-    stage_begin(s, kStDedup);
-    launch_dedup(skeys, N, frame_shift, F, L.codes, L.seg, L.gap, L.vstart, L.dpart, dst, sms, s);
-    stage_end(s, kStDedup);
-    // a4: octree occupancy
-    OccupancyOut oo{L.occ, L.occ_cap, L.lsz, L.occ_off, L.hoff, L.opart};
-    stage_begin(s, kStOccupancy);
-    launch_occupancy(L.codes, L.gap, L.vstart, L.Jd, F, frame_shift, oo, dst, sms, s);
-    stage_end(s, kStOccupancy);
-    // a5: occupancy rANS
-    RansFrames rf{F, L.occ, L.occ_off, q->rans_chunk, L.chunk_off, L.freq, L.cum, L.mode, L.chunk_words,
-                  L.chunk_top, L.chunk_pos, L.chunk_slots, L.sec_bytes};
-    stage_begin(s, kStRans);
-    launch_rans_encode(rf, dst, L.max_chunks, sms, s);
-    stage_end(s, kStRans);
-
-    HdrParams hpar{F, R, C, G, C ? q->rlgr_block : 1u, q->rans_chunk, q->tau, rq.capacity};
-    if (C) {
-        // a6: RAHT prelude; a7: forward transform with the cluster average fused into the first pass
-        stage_begin(s, kStPrelude);
-        launch_raht_prelude(L.plan, L.gap, dst, nullptr, sms, s);
-        stage_end(s, kStPrelude);
-        RahtIO io{};
-        io.C = C;
-        io.seg = L.seg;
-        io.vals = svals;
-        io.codes = L.codes;
-        io.attr = L.attrp;
-        io.frame_shift = frame_shift;
-        io.Y = L.Y;
-        io.pool = L.pool;
-        stage_begin(s, kStRahtFwd);
-        launch_raht_forward(L.plan, io, N, sms, s);
-        stage_end(s, kStRahtFwd);
-        // a8 + a9: quantise + block RLGR for every rung
-        launch_rlgr_offsets(L.vstart, F, q->rlgr_block, R, C, L.job_off, L.blk_off, s);
-        RlgrJob j{};
-        j.C = C;
-        j.B = q->rlgr_block;
-        j.R = R;
-        j.Y = L.Y;
-        j.vstart = L.vstart;
-        j.F = F;
-        j.inv_step = L.inv_step;
-        j.tau = (float)q->tau;
-        j.slots = L.slots;
-        j.block_words = L.block_words;
-        j.blk_off = L.blk_off;
-        j.slot_words = L.slot_words;
-        j.overflow = L.overflow;
-        stage_begin(s, kStRlgrEnc);
-        launch_rlgr_encode(j, L.job_off, L.jobs_bound, s);
-        stage_end(s, kStRlgrEnc);
-        launch_scan_u32_to_u64(L.block_words, L.blocks_bound, L.block_off, L.spart, sms, s);
-    }
-    // a10: container
-    stage_begin(s, kStContainer);
-    sizes_kernel<<<1, 32, 0, s>>>(hpar, L.Jd, L.vstart, L.sec_bytes, L.blk_off, L.block_off, L.si, dst);
-    count_launch();
-    header_kernel<<<F * R, 128, 0, s>>>(hpar, L.Jd, L.vstart, L.grid, L.lsz, L.groups, L.steps_rg, L.si, dst,
-                                        rq.out);
-    count_launch();
-    OccCopyArgs oa{L.occ, L.occ_off, L.mode, L.chunk_off, L.freq, L.chunk_words, L.chunk_top, L.chunk_pos,
-                   L.chunk_slots, rans_chunk_slot_bytes(q->rans_chunk)};
-    occ_copy_kernel<<<dim3(std::max<uint32_t>(1, (uint32_t)sms * 2 / (F * R)), F * R), 256, 0, s>>>(hpar, oa, L.si,
-                                                                                                  dst, rq.out);
-    count_launch();
-    if (C) {
-        AttrCopyArgs aa{L.vstart, L.blk_off, L.block_off, L.block_words, L.slots, L.slot_words};
-        attr_copy_kernel<<<dim3(std::max<uint32_t>(1, (uint32_t)sms * 4 / (F * R)), F * R), 256, 0, s>>>(
-            hpar, aa, L.si, dst, rq.out);
-        count_launch();
-    }
-    stage_end(s, kStContainer);
-    // a13: optional reconstruction (first frame, first rung)
-    stage_begin(s, kStRecon);
-    if (F == 1 && rq.recon_pos) launch_voxel_centres_batch(L.codes, dst, N, frame_shift, L.Jd, L.grid, rq.recon_pos, s);
-    if (F == 1 && C && rq.recon_attr) {
-        RahtIO io{};
-        io.C = C;
-        io.Y = L.Y;
-        io.out = rq.recon_attr;
-        io.pool = L.pool;
-        io.inv_step = L.inv_step;
-        io.step = L.step;
-        io.tau = (float)q->tau;
-        io.frame_shift = frame_shift;
-        launch_raht_inverse(L.plan, io, N, sms, s);
-    }
-    stage_end(s, kStRecon);
-    CK(cudaGetLastError());
-    // results
     uint64_t *res = (uint64_t *)(hp + ((o_end + 63) & ~(size_t)63));
-    CK(cudaMemcpyAsync(res, &dst->err, 8, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(res + 1, &dst->nv_total, 16, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(res + 3, L.overflow, 4, cudaMemcpyDeviceToHost, s));
+    // ---- device work: stream-ordered and sized from host values only, so it
+    // can be captured once per request shape and replayed as a CUDA graph
+    auto enqueue = [&](cudaStream_t s) -> gsnfs_status {
+        CK(cudaMemcpyAsync((void *)L.posp, hp + o_pos, 8 * F, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync((void *)L.attrp, hp + o_attr, 8 * F, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(L.poff, hp + o_poff, 8 * (F + 1), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(L.Jd, hp + o_J, 4 * F, cudaMemcpyHostToDevice, s));
+        if (C) {
+            CK(cudaMemcpyAsync(L.inv_step, hp + o_inv, 4 * (size_t)R * C, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(L.step, hp + o_step, 4 * (size_t)R * C, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(L.steps_rg, hp + o_srg, 8 * (size_t)R * G, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(L.groups, hp + o_grp, C, cudaMemcpyHostToDevice, s));
+        }
+        CK(cudaMemsetAsync(L.overflow, 0, 16, s));
+
+        DevState *dst = ctx->st;
+        const int sms = ctx->num_sms;
+        FrameSet fs;
+        fs.F = F;
+        fs.frame_shift = frame_shift;
+        fs.pos = L.posp;
+        fs.attr = L.attrp;
+        fs.poff = L.poff;
+        fs.J = L.Jd;
+        fs.grid = L.grid;
+
+        // a1: voxelise + Morton
+        stage_begin(s, kStVoxelize);
+        launch_voxelize(fs, dst, N, nmax, L.keys, L.vals, sms, s);
+        stage_end(s, kStVoxelize);
+        // a2: radix sort
+        stage_begin(s, kStSort);
+        bool alt = radix_sort(L.keys, L.vals, L.keys_alt, L.vals_alt, L.hist, N, nbits, sms, s);
+        stage_end(s, kStSort);
+        const uint64_t *skeys = alt ? L.keys_alt : L.keys;
+        const uint32_t *svals = alt ? L.vals_alt : L.vals;
+        // a3: dedup
+        stage_begin(s, kStDedup);
+        launch_dedup(skeys, N, frame_shift, F, L.codes, L.seg, L.gap, L.vstart, L.dpart, dst, sms, s);
+        stage_end(s, kStDedup);
+        // a4: octree occupancy
+        OccupancyOut oo{L.occ, L.occ_cap, L.lsz, L.occ_off, L.hoff, L.opart};
+        stage_begin(s, kStOccupancy);
+        launch_occupancy(L.codes, L.gap, L.vstart, L.Jd, F, frame_shift, oo, dst, sms, s);
+        stage_end(s, kStOccupancy);
+        // a5: occupancy rANS
+        RansFrames rf{F, L.occ, L.occ_off, q->rans_chunk, L.chunk_off, L.freq, L.cum, L.mode, L.chunk_words,
+                      L.chunk_top, L.chunk_pos, L.chunk_slots, L.sec_bytes};
+        stage_begin(s, kStRans);
+        launch_rans_encode(rf, dst, L.max_chunks, sms, s);
+        stage_end(s, kStRans);
+
+        HdrParams hpar{F, R, C, G, C ? q->rlgr_block : 1u, q->rans_chunk, q->tau, rq.capacity};
+        if (C) {
+            // a6: RAHT prelude; a7: forward transform with the cluster average fused into the first pass
+            stage_begin(s, kStPrelude);
+            launch_raht_prelude(L.plan, L.gap, dst, nullptr, sms, s);
+            stage_end(s, kStPrelude);
+            RahtIO io{};
+            io.C = C;
+            io.seg = L.seg;
+            io.vals = svals;
+            io.codes = L.codes;
+            io.attr = L.attrp;
+            io.frame_shift = frame_shift;
+            io.Y = L.Y;
+            io.pool = L.pool;
+            stage_begin(s, kStRahtFwd);
+            launch_raht_forward(L.plan, io, N, sms, s);
+            stage_end(s, kStRahtFwd);
+            // a8 + a9: quantise + block RLGR for every rung
+            launch_rlgr_offsets(L.vstart, F, q->rlgr_block, R, C, L.job_off, L.blk_off, s);
+            RlgrJob j{};
+            j.C = C;
+            j.B = q->rlgr_block;
+            j.R = R;
+            j.Y = L.Y;
+            j.vstart = L.vstart;
+            j.F = F;
+            j.inv_step = L.inv_step;
+            j.tau = (float)q->tau;
+            j.slots = L.slots;
+            j.block_words = L.block_words;
+            j.blk_off = L.blk_off;
+            j.slot_words = L.slot_words;
+            j.overflow = L.overflow;
+            stage_begin(s, kStRlgrEnc);
+            launch_rlgr_encode(j, L.job_off, L.jobs_bound, s);
+            stage_end(s, kStRlgrEnc);
+            launch_scan_u32_to_u64(L.block_words, L.blocks_bound, L.block_off, L.spart, sms, s);
+        }
+        // a10: container
+        stage_begin(s, kStContainer);
+        sizes_kernel<<<1, 32, 0, s>>>(hpar, L.Jd, L.vstart, L.sec_bytes, L.blk_off, L.block_off, L.si, dst);
+        count_launch();
+        header_kernel<<<F * R, 128, 0, s>>>(hpar, L.Jd, L.vstart, L.grid, L.lsz, L.groups, L.steps_rg, L.si, dst,
+                                            rq.out);
+        count_launch();
+        OccCopyArgs oa{L.occ, L.occ_off, L.mode, L.chunk_off, L.freq, L.chunk_words, L.chunk_top, L.chunk_pos,
+                       L.chunk_slots, rans_chunk_slot_bytes(q->rans_chunk)};
+        occ_copy_kernel<<<dim3(std::max<uint32_t>(1, (uint32_t)sms * 2 / (F * R)), F * R), 256, 0, s>>>(hpar, oa, L.si,
+                                                                                                      dst, rq.out);
+        count_launch();
+        if (C) {
+            AttrCopyArgs aa{L.vstart, L.blk_off, L.block_off, L.block_words, L.slots, L.slot_words};
+            attr_copy_kernel<<<dim3(std::max<uint32_t>(1, (uint32_t)sms * 4 / (F * R)), F * R), 256, 0, s>>>(
+                hpar, aa, L.si, dst, rq.out);
+            count_launch();
+        }
+        stage_end(s, kStContainer);
+        // a13: optional reconstruction (first frame, first rung)
+        stage_begin(s, kStRecon);
+        if (F == 1 && rq.recon_pos) launch_voxel_centres_batch(L.codes, dst, N, frame_shift, L.Jd, L.grid, rq.recon_pos, s);
+        if (F == 1 && C && rq.recon_attr) {
+            RahtIO io{};
+            io.C = C;
+            io.Y = L.Y;
+            io.out = rq.recon_attr;
+            io.pool = L.pool;
+            io.inv_step = L.inv_step;
+            io.step = L.step;
+            io.tau = (float)q->tau;
+            io.frame_shift = frame_shift;
+            launch_raht_inverse(L.plan, io, N, sms, s);
+        }
+        stage_end(s, kStRecon);
+        CK(cudaGetLastError());
+        // results
+        CK(cudaMemcpyAsync(res, &dst->err, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(res + 1, &dst->nv_total, 16, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(res + 3, L.overflow, 4, cudaMemcpyDeviceToHost, s));
+        return GSNFS_OK;
+    };
+    if (ctx->graphs) {
+        std::vector<uint64_t> key = {F, R, C, G, C ? q->rlgr_block : 0u, q->rans_chunk, 0, rq.capacity,
+                                     (uint64_t)(uintptr_t)rq.out, (uint64_t)(uintptr_t)rq.recon_pos,
+                                     (uint64_t)(uintptr_t)rq.recon_attr, worst_slots ? 1u : 0u,
+                                     (uint64_t)(uintptr_t)ctx->arena, ctx->arena_cap,
+                                     (uint64_t)(uintptr_t)ctx->pinned, rq.attr ? 1u : 0u};
+        memcpy(&key[6], &q->tau, 8);
+        for (uint32_t f = 0; f < F; ++f) {
+            key.push_back(rq.n[f]);
+            key.push_back(rq.J[f]);
+        }
+        st = run_graphed(ctx, s, std::move(key), enqueue);
+    } else {
+        st = enqueue(s);
+    }
+    if (st) return st;
     CK(cudaStreamSynchronize(s));
     const uint32_t derr = (uint32_t)(res[0] & 0xFFFFFFFFu);
     rq.nv = res[1];
@@ -1275,10 +1389,36 @@ void gsnfs_destroy(gsnfs_ctx *ctx)
     if (!ctx) return;
     DeviceGuard dg(ctx->device);
     cudaDeviceSynchronize();
+    drop_graphs(ctx);
+    if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+    if (ctx->gev_in) cudaEventDestroy(ctx->gev_in);
+    if (ctx->gev_out) cudaEventDestroy(ctx->gev_out);
     if (ctx->arena) cudaFree(ctx->arena);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->st) cudaFree(ctx->st);
     delete ctx;
+}
+
+gsnfs_status gsnfs_set_graphs(gsnfs_ctx *ctx, int enable)
+{
+    if (!ctx) return GSNFS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    if (!enable && ctx->gstream) {
+        CK(cudaStreamSynchronize(ctx->gstream));
+        drop_graphs(ctx);
+    }
+    ctx->graphs = enable != 0;
+    return GSNFS_OK;
+}
+
+gsnfs_status gsnfs_graph_stats(gsnfs_ctx *ctx, uint64_t *out /* 4: replays, captures, failures, cached */)
+{
+    if (!ctx || !out) return GSNFS_ERR_INVALID_ARG;
+    out[0] = ctx->ghits;
+    out[1] = ctx->gcaptures;
+    out[2] = ctx->gfailures;
+    out[3] = ctx->gcache.size();
+    return GSNFS_OK;
 }
 
 gsnfs_status gsnfs_max_bitstream_bytes(uint64_t n, uint32_t J, const gsnfs_quant *q, uint64_t *out)

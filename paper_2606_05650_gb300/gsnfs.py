@@ -76,6 +76,8 @@ def lib():
                 "gsnfs_rlgr_slot_words": ([u32], u32),
                 "gsnfs_rlgr_encode_indices": ([p, p, p, u64, u32, u32, p, p], i32),
                 "gsnfs_rlgr_decode_indices": ([p, p, p, p, u64, u32, u32, p], i32),
+                "gsnfs_set_graphs": ([p, i32], i32),
+                "gsnfs_graph_stats": ([p, P64], i32),
                 "gsnfs_launch_count": ([], u64),
                 "gsnfs_profile_enable": ([i32], i32),
                 "gsnfs_profile_stage_names": ([ct.POINTER(ct.c_char_p), i32], i32),
@@ -107,6 +109,18 @@ def context(device=None):
             _ctx[dev.index] = h
         c = h
     return c
+
+
+def set_graphs(enable: bool, device=None):
+    """Turns CUDA-graph capture / replay of the encoder on or off."""
+    _check(lib().gsnfs_set_graphs(context(device), 1 if enable else 0), "gsnfs_set_graphs")
+
+
+def graph_stats(device=None):
+    """(replays, captures, failed captures, graphs cached) of the encoder graphs."""
+    out = (ct.c_uint64 * 4)()
+    _check(lib().gsnfs_graph_stats(context(device), out), "gsnfs_graph_stats")
+    return tuple(int(v) for v in out)
 
 
 def _stream(t: torch.Tensor):
@@ -226,10 +240,10 @@ def encode_batch(pos_list, attr_list, J_list, rung_scales, qp: QuantParams, out=
     if C:
         for a, p in zip(attr_list, pos_list):
             _cuda_f32(a, C)
-    cap = 0
-    for p, J in zip(pos_list, J_list):
-        cap += max_bitstream_bytes(p.shape[0], int(J), qp) * R
-    if out is None or out.numel() < cap:
+    if out is None:  # worst-case size; a smaller caller buffer is grown on demand below
+        cap = 0
+        for p, J in zip(pos_list, J_list):
+            cap += max_bitstream_bytes(p.shape[0], int(J), qp) * R
         out = torch.empty(cap, dtype=torch.uint8, device=dev)
     hp = (ct.c_void_p * F)(*[p.data_ptr() for p in pos_list])
     ha = (ct.c_void_p * F)(*[(a.data_ptr() if C else 0) for a in (attr_list if C else pos_list)])
@@ -238,8 +252,13 @@ def encode_batch(pos_list, attr_list, J_list, rung_scales, qp: QuantParams, out=
     hs = (ct.c_double * R)(*[float(s) for s in rung_scales])
     offs = (ct.c_uint64 * (F * R + 1))()
     q = qp.struct()
-    _check(lib().gsnfs_encode_batch(context(dev), _stream(out), F, hp, ha, hn, hJ, R, hs, ct.byref(q), _ptr(out),
-                                    out.numel(), offs), "gsnfs_encode_batch")
+    rc = lib().gsnfs_encode_batch(context(dev), _stream(out), F, hp, ha, hn, hJ, R, hs, ct.byref(q), _ptr(out),
+                                  out.numel(), offs)
+    if rc == -2:  # GSNFS_ERR_CAPACITY: offs[F*R] holds the size needed
+        out = torch.empty(int(offs[F * R]) + 4096, dtype=torch.uint8, device=dev)
+        rc = lib().gsnfs_encode_batch(context(dev), _stream(out), F, hp, ha, hn, hJ, R, hs, ct.byref(q), _ptr(out),
+                                      out.numel(), offs)
+    _check(rc, "gsnfs_encode_batch")
     return out, np.array(offs[:], dtype=np.uint64)
 
 
