@@ -158,6 +158,9 @@ def run_gpu(args):
         pos, attr, rows = G.decode_batch(out, offs, C, F * N_GAUSS)
         return offs, rows
 
+    # launch shapes tuned on this workload (outputs checked identical for every candidate)
+    from paper_2606_05650_gb300 import autotune
+    tuning = autotune.tune_round_trip(P, A, Js, qp, use_cache=False)
     for _ in range(max(args.warmup, 1)):
         offs, rows = step()
     torch.cuda.synchronize()
@@ -211,7 +214,9 @@ def run_gpu(args):
                                    f"{F} frames per GPU per step, batched encode + decode of every frame",
                        "frames_per_step_per_gpu": F, "gaussians_per_frame": N_GAUSS, "channels": C, "depth": J,
                        "rlgr_block": args.block, "rans_chunk": qp.rans_chunk, "parallelism": f"frames x {world}",
-                       "l2": "inputs 1.9 GB per step > 129 MB L2 (no flush needed)"},
+                       "l2": "inputs 1.9 GB per step > 129 MB L2 (no flush needed)",
+                       "tuning": {"params": tuning["params"], "tuned_ms": tuning["ms"],
+                                  "default_ms": tuning["default_ms"]}},
             "encode_decode_fps": round(value, 2),
             "voxels_per_frame": int(nv_frames.mean()), "bytes_per_frame": int(stream_bytes.mean()),
             "bits_per_gaussian": round(8 * float(stream_bytes.mean()) / N_GAUSS, 3),

@@ -92,6 +92,19 @@ gsnfs_status gsnfs_set_graphs(gsnfs_ctx *ctx, int enable);
 /* out[0] replays, out[1] captures, out[2] failed captures, out[3] graphs cached. */
 gsnfs_status gsnfs_graph_stats(gsnfs_ctx *ctx, uint64_t *out);
 
+/* Launch-shape tunables of a context.  Bitstreams and decoded values do not
+ * depend on them (each butterfly and each code is computed the same way
+ * whatever the tiling); only the speed does.  Value 0 restores the built-in
+ * default.  Changing one drops the context's captured graphs.
+ *   GSNFS_TUNE_RAHT_TILE     RAHT tile size in voxels: power of two in
+ *                            [256, 4096] (default: largest whose C rows fit
+ *                            56 KB of shared memory, at least 256)
+ *   GSNFS_TUNE_RAHT_GRID     CTAs per SM of the first transform pass, 1..32 (4)
+ *   GSNFS_TUNE_PRELUDE_GRID  CTAs per SM of the prelude tile passes, 1..32 (8) */
+enum { GSNFS_TUNE_RAHT_TILE = 0, GSNFS_TUNE_RAHT_GRID = 1, GSNFS_TUNE_PRELUDE_GRID = 2 };
+gsnfs_status gsnfs_tune_set(gsnfs_ctx *ctx, int which, uint32_t value);
+gsnfs_status gsnfs_tune_get(gsnfs_ctx *ctx, int which, uint32_t *value);
+
 /* Upper bound of the encoded size of a frame of n points (host only). */
 gsnfs_status gsnfs_max_bitstream_bytes(uint64_t n, uint32_t J, const gsnfs_quant *q, uint64_t *out);
 

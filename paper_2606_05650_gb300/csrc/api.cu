@@ -115,6 +115,8 @@ struct gsnfs_ctx {
     unsigned char *pinned = nullptr;
     size_t pinned_cap = 0;
     DevState *st = nullptr;
+    // launch-shape tunables (gsnfs_tune_set); 0 = built-in default
+    uint32_t tune[3] = {0, 0, 0};
     // CUDA graphs of the encoder (off by default)
     bool graphs = false;
     cudaStream_t gstream = nullptr;  // capture / replay stream, joined to the caller's by events
@@ -491,8 +493,11 @@ struct EncLayout {
     uint32_t slot_words;
 };
 
-void carve_plan(Carve &cv, RahtPlanDev &p, uint64_t nv_cap, uint32_t T)
+void carve_plan(Carve &cv, RahtPlanDev &p, uint64_t nv_cap, uint32_t T, const uint32_t *tune)
 {
+    if (tune && tune[GSNFS_TUNE_RAHT_TILE]) T = tune[GSNFS_TUNE_RAHT_TILE];
+    p.xgrid_mult = tune ? tune[GSNFS_TUNE_RAHT_GRID] : 0u;
+    p.pgrid_mult = tune ? tune[GSNFS_TUNE_PRELUDE_GRID] : 0u;
     uint64_t elems, tiles, surv;
     raht_plan_sizes(nv_cap, T, &elems, &tiles, &surv);
     p.T = T;
@@ -515,7 +520,8 @@ void carve_plan(Carve &cv, RahtPlanDev &p, uint64_t nv_cap, uint32_t T)
     p.npasses = cv.take<uint32_t>(1);
 }
 
-size_t carve_encode(Carve &cv, EncLayout &L, const EncodeReq &rq, int num_sms, bool worst_slots)
+size_t carve_encode(Carve &cv, EncLayout &L, const EncodeReq &rq, int num_sms, bool worst_slots,
+                    const uint32_t *tune)
 {
     const uint32_t F = rq.F, R = rq.R, C = rq.q->num_channels;
     uint64_t N = 0, occ_cap = 0, max_chunks = 0, jobs = 0;
@@ -569,7 +575,7 @@ size_t carve_encode(Carve &cv, EncLayout &L, const EncodeReq &rq, int num_sms, b
     L.chunk_top = cv.take<uint32_t>(max_chunks + 1);
     L.chunk_pos = cv.take<uint32_t>(max_chunks + 1);
     if (C) {
-        carve_plan(cv, L.plan, N, raht_tile_size(C));
+        carve_plan(cv, L.plan, N, raht_tile_size(C), tune);
         uint64_t elems, tiles, surv;
         raht_plan_sizes(N, L.plan.T, &elems, &tiles, &surv);
         L.pool = cv.take<float>(surv * C);
@@ -664,11 +670,11 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
 
     EncLayout L;
     Carve measure(nullptr);
-    size_t need = carve_encode(measure, L, rq, ctx->num_sms, worst_slots);
+    size_t need = carve_encode(measure, L, rq, ctx->num_sms, worst_slots, ctx->tune);
     gsnfs_status st = grow_arena(ctx, need, s);
     if (st) return st;
     Carve cv(ctx->arena);
-    carve_encode(cv, L, rq, ctx->num_sms, worst_slots);
+    carve_encode(cv, L, rq, ctx->num_sms, worst_slots, ctx->tune);
 
     // ---- host parameters -> pinned staging -> one copy
     std::vector<unsigned char> hbuf;
@@ -1000,7 +1006,7 @@ struct DecLayout {
     RahtPlanDev plan;
 };
 
-size_t carve_decode(Carve &cv, DecLayout &L, const ParsedHeader &P, int num_sms)
+size_t carve_decode(Carve &cv, DecLayout &L, const ParsedHeader &P, int num_sms, const uint32_t *tune)
 {
     L.grid = cv.take<FrameGrid>(1);
     L.tabs = cv.take<uint32_t>(rans_table_words());
@@ -1015,7 +1021,7 @@ size_t carve_decode(Carve &cv, DecLayout &L, const ParsedHeader &P, int num_sms)
     L.codes = cv.take<uint64_t>(P.nv + 1);
     L.gap = cv.take<uint8_t>(P.nv + 2);
     if (P.C && P.nv) {
-        carve_plan(cv, L.plan, P.nv, raht_tile_size(P.C));
+        carve_plan(cv, L.plan, P.nv, raht_tile_size(P.C), tune);
         uint64_t elems, tiles, surv;
         raht_plan_sizes(P.nv, L.plan.T, &elems, &tiles, &surv);
         L.pool = cv.take<float>(surv * P.C);
@@ -1037,11 +1043,11 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
     if (P.nv == 0) return GSNFS_OK;
     DecLayout L;
     Carve m(nullptr);
-    size_t need = carve_decode(m, L, P, ctx->num_sms);
+    size_t need = carve_decode(m, L, P, ctx->num_sms, ctx->tune);
     st = grow_arena(ctx, need, s);
     if (st) return st;
     Carve cv(ctx->arena);
-    carve_decode(cv, L, P, ctx->num_sms);
+    carve_decode(cv, L, P, ctx->num_sms, ctx->tune);
     DevState *dst = ctx->st;
     // host-computed grid and steps
     unsigned char *hp = ctx->pinned;
@@ -1193,7 +1199,7 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         L.codes = cv.take<uint64_t>(N + 1);
         L.gap = cv.take<uint8_t>(N + 2);
         if (C) {
-            carve_plan(cv, L.plan, N, raht_tile_size(C));
+            carve_plan(cv, L.plan, N, raht_tile_size(C), ctx->tune);
             uint64_t elems, tiles, surv;
             raht_plan_sizes(N, L.plan.T, &elems, &tiles, &surv);
             L.pool = cv.take<float>(surv * C);
@@ -1411,6 +1417,28 @@ gsnfs_status gsnfs_set_graphs(gsnfs_ctx *ctx, int enable)
     return GSNFS_OK;
 }
 
+gsnfs_status gsnfs_tune_set(gsnfs_ctx *ctx, int which, uint32_t value)
+{
+    if (!ctx || which < 0 || which > GSNFS_TUNE_PRELUDE_GRID) return GSNFS_ERR_INVALID_ARG;
+    if (which == GSNFS_TUNE_RAHT_TILE && value && (!pow2(value) || value < 256 || value > 4096))
+        return GSNFS_ERR_INVALID_ARG;
+    if (which != GSNFS_TUNE_RAHT_TILE && value > 32) return GSNFS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    if (ctx->tune[which] != value && ctx->gstream) {  // captured graphs hold the old launch shapes
+        CK(cudaStreamSynchronize(ctx->gstream));
+        drop_graphs(ctx);
+    }
+    ctx->tune[which] = value;
+    return GSNFS_OK;
+}
+
+gsnfs_status gsnfs_tune_get(gsnfs_ctx *ctx, int which, uint32_t *value)
+{
+    if (!ctx || !value || which < 0 || which > GSNFS_TUNE_PRELUDE_GRID) return GSNFS_ERR_INVALID_ARG;
+    *value = ctx->tune[which];
+    return GSNFS_OK;
+}
+
 gsnfs_status gsnfs_graph_stats(gsnfs_ctx *ctx, uint64_t *out /* 4: replays, captures, failures, cached */)
 {
     if (!ctx || !out) return GSNFS_ERR_INVALID_ARG;
@@ -1449,7 +1477,7 @@ gsnfs_status gsnfs_reserve(gsnfs_ctx *ctx, uint64_t n, uint32_t C, uint32_t J, c
     rq.J = &J;
     EncLayout L;
     Carve m(nullptr);
-    size_t need = carve_encode(m, L, rq, ctx->num_sms, false);
+    size_t need = carve_encode(m, L, rq, ctx->num_sms, false, ctx->tune);
     return grow_arena(ctx, need, 0);
 }
 
@@ -1725,10 +1753,10 @@ gsnfs_status gsnfs_octree_decode(gsnfs_ctx *ctx, void *stream, const uint8_t *d_
     P.nb = 0;
     DecLayout L;
     Carve m(nullptr);
-    gsnfs_status st = grow_arena(ctx, carve_decode(m, L, P, ctx->num_sms), s);
+    gsnfs_status st = grow_arena(ctx, carve_decode(m, L, P, ctx->num_sms, ctx->tune), s);
     if (st) return st;
     Carve cv(ctx->arena);
-    carve_decode(cv, L, P, ctx->num_sms);
+    carve_decode(cv, L, P, ctx->num_sms, ctx->tune);
     st = grow_pinned(ctx, 4096);
     if (st) return st;
     CK(cudaMemsetAsync(ctx->st, 0, 8, s));
@@ -1855,7 +1883,7 @@ gsnfs_status gsnfs_raht_plan_create(gsnfs_ctx *ctx, void *stream, const uint64_t
     uint8_t *gap = nullptr;
     uint64_t *nvd = nullptr;
     auto carve = [&](Carve &cv) {
-        carve_plan(cv, pl->dev, nv, raht_tile_size(C));
+        carve_plan(cv, pl->dev, nv, raht_tile_size(C), ctx->tune);
         uint64_t elems, tiles, surv;
         raht_plan_sizes(nv, pl->dev.T, &elems, &tiles, &surv);
         pl->dev.bf_w = cv.take<uint2>(tiles * pl->dev.T);

@@ -96,6 +96,8 @@ struct RahtPass {  // device-resident description of one pass
 
 struct RahtPlanDev {  // device pointers of a plan
     uint32_t T;            // tile size (elements)
+    uint32_t xgrid_mult;   // transform pass 0: CTAs per SM (0 = default 4)
+    uint32_t pgrid_mult;   // prelude tile passes: CTAs per SM (0 = default 8)
     uint32_t cap_elems;    // capacity of the pooled sequence arrays
     uint32_t cap_tiles;
     uint32_t cap_surv;     // rows in the survivor pool

@@ -712,7 +712,8 @@ void forward_all(const XformArgs<S> &A, uint64_t nv_bound, int num_sms, cudaStre
     const uint32_t T = A.p.T;
     const size_t smem = xform_smem<S>(T, A.Cg);
     uint64_t tiles = (nv_bound + T - 1) / T;
-    uint32_t grid0 = (uint32_t)(tiles < 1 ? 1 : (tiles < (uint64_t)num_sms * 4 ? tiles : (uint64_t)num_sms * 4));
+    const uint64_t gcap = (uint64_t)num_sms * (A.p.xgrid_mult ? A.p.xgrid_mult : 4u);
+    uint32_t grid0 = (uint32_t)(tiles < 1 ? 1 : (tiles < gcap ? tiles : gcap));
     for (int q = 0; q < kRahtMultiPasses; ++q) {
         uint32_t g = q == 0 ? grid0 : (grid0 < (uint32_t)num_sms ? grid0 : (uint32_t)num_sms);
         if (q == 0) stage_begin(s, kStRahtFwd0);
@@ -731,7 +732,8 @@ void inverse_all(const XformArgs<S> &A, uint64_t nv_bound, int num_sms, cudaStre
     const uint32_t T = A.p.T;
     const size_t smem = xform_smem<S>(T, A.Cg);
     uint64_t tiles = (nv_bound + T - 1) / T;
-    uint32_t grid0 = (uint32_t)(tiles < 1 ? 1 : (tiles < (uint64_t)num_sms * 4 ? tiles : (uint64_t)num_sms * 4));
+    const uint64_t gcap = (uint64_t)num_sms * (A.p.xgrid_mult ? A.p.xgrid_mult : 4u);
+    uint32_t grid0 = (uint32_t)(tiles < 1 ? 1 : (tiles < gcap ? tiles : gcap));
     const bool qd = A.io.inv_step != nullptr;
     if (qd)
         launch_finish<S, true, VEC, true>(A, kRahtMultiPasses, smem, s);
@@ -777,7 +779,7 @@ void prelude_launches(const PreludeArgs &a, const RahtPlanDev &p, const DevState
     cudaFuncSetAttribute(prelude_finish_kernel<TMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     prelude_init_kernel<<<1, 32, 0, s>>>(p, st, nv_dev);
     count_launch();
-    uint32_t grid = (uint32_t)num_sms * 8;
+    uint32_t grid = (uint32_t)num_sms * (p.pgrid_mult ? p.pgrid_mult : 8u);
     for (int q = 0; q < kRahtMultiPasses; ++q) {
         prelude_tiles_kernel<TMAX><<<grid, kThreads, smem, s>>>(a, q);
         count_launch();

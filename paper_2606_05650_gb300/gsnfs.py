@@ -77,6 +77,8 @@ def lib():
                 "gsnfs_rlgr_encode_indices": ([p, p, p, u64, u32, u32, p, p], i32),
                 "gsnfs_rlgr_decode_indices": ([p, p, p, p, u64, u32, u32, p], i32),
                 "gsnfs_set_graphs": ([p, i32], i32),
+                "gsnfs_tune_set": ([p, i32, u32], i32),
+                "gsnfs_tune_get": ([p, i32, ct.POINTER(u32)], i32),
                 "gsnfs_graph_stats": ([p, P64], i32),
                 "gsnfs_launch_count": ([], u64),
                 "gsnfs_profile_enable": ([i32], i32),
@@ -114,6 +116,20 @@ def context(device=None):
 def set_graphs(enable: bool, device=None):
     """Turns CUDA-graph capture / replay of the encoder on or off."""
     _check(lib().gsnfs_set_graphs(context(device), 1 if enable else 0), "gsnfs_set_graphs")
+
+
+TUNABLES = {"raht_tile": 0, "raht_grid": 1, "prelude_grid": 2}
+
+
+def tune_set(name: str, value: int, device=None):
+    """Sets a launch-shape tunable (0 = built-in default); outputs do not change."""
+    _check(lib().gsnfs_tune_set(context(device), TUNABLES[name], int(value)), "gsnfs_tune_set")
+
+
+def tune_get(name: str, device=None) -> int:
+    v = ct.c_uint32()
+    _check(lib().gsnfs_tune_get(context(device), TUNABLES[name], ct.byref(v)), "gsnfs_tune_get")
+    return int(v.value)
 
 
 def graph_stats(device=None):
