@@ -133,87 +133,6 @@ struct Rlgr {
     }
 };
 
-struct BitReader {
-    const uint32_t *w;
-    uint32_t nw, pos;
-    uint64_t acc;
-    uint32_t nacc;
-    bool bad;
-    __device__ __forceinline__ void refill()
-    {
-        while (nacc <= 32 && pos < nw) {
-            acc |= (uint64_t)w[pos++] << nacc;
-            nacc += 32;
-        }
-    }
-    __device__ __forceinline__ uint32_t get(uint32_t n)  // n <= 32
-    {
-        if (n == 0) return 0;
-        if (nacc < n) refill();
-        if (nacc < n) {
-            bad = true;
-            return 0;
-        }
-        uint32_t v = (uint32_t)(acc & ((n < 32) ? ((1ull << n) - 1) : 0xFFFFFFFFull));
-        acc = (n < 64) ? (acc >> n) : 0;
-        nacc -= n;
-        return v;
-    }
-    // reads a unary prefix: p < 24 ones terminated by a zero, or 24 ones (escape)
-    __device__ __forceinline__ uint32_t ones()
-    {
-        if (nacc < 32) refill();
-        const uint64_t x = ~acc;
-        uint32_t p = x ? (uint32_t)(__ffsll((long long)x) - 1) : 64u;
-        if (p >= (uint32_t)kUnaryEsc) {
-            if (nacc < (uint32_t)kUnaryEsc) {
-                bad = true;
-                return 0;
-            }
-            acc >>= kUnaryEsc;
-            nacc -= kUnaryEsc;
-            return kUnaryEsc;
-        }
-        if (p + 1 > nacc) {
-            bad = true;
-            return 0;
-        }
-        acc >>= (p + 1);
-        nacc -= p + 1;
-        return p;
-    }
-};
-
-__device__ __forceinline__ uint32_t gr_get(BitReader &br, uint32_t k, int &KR)
-{
-    if (br.nacc < 32) br.refill();
-    const uint64_t a = br.acc;
-    uint32_t p = (~a) ? (uint32_t)(__ffsll((long long)~a) - 1) : 64u;
-    uint32_t v;
-    if (p < (uint32_t)kUnaryEsc && p + 1 + k <= br.nacc) {  // common case: one shift consumes prefix and remainder
-        v = (p << k) | (uint32_t)((a >> (p + 1)) & ((1ull << k) - 1ull));
-        br.acc = a >> (p + 1 + k);
-        br.nacc -= p + 1 + k;
-    } else if ((p = br.ones()) < (uint32_t)kUnaryEsc) {
-        v = (p << k) | br.get(k);
-    } else {
-        uint32_t n = br.get(6);
-        if (n > 32) {
-            br.bad = true;
-            return 0;
-        }
-        v = br.get(n);
-        p = v >> k;
-    }
-    if (p == 0) {
-        KR = KR >= 2 ? KR - 2 : 0;
-    } else if (p > 1) {
-        uint32_t t = (uint32_t)KR + (p > 384u ? 384u : p) + 1u;
-        KR = t > 384u ? 384 : (int)t;
-    }
-    return v;
-}
-
 // ---- encoder: one CTA per (frame, row block); thread = (rung, channel) ----
 // Rows of the block are staged through shared memory in chunks of kChunkRows
 // with asynchronous copies (double-buffered), so every rung's streams are
@@ -311,47 +230,131 @@ __global__ void __launch_bounds__(1024) rlgr_encode_kernel(EncJobs E, const int3
     }
 }
 
-// Decodes one block stream (len coefficients of channel c) into rows
-// row0 .. row0 + len - 1 of a row-major C-channel array.
-template <bool TO_INT>
-__device__ __forceinline__ void decode_stream(const uint32_t *wp, uint32_t nw, uint32_t len, uint64_t row0, uint32_t C,
-                                              uint32_t c, float sc, float *Y, int32_t *qout, DevState *st)
+// ---- decoder ------------------------------------------------------------------
+// Bits are looked at through a 32-bit window over two consecutive words
+// (cur, nxt) at bit offset pos: one funnel shift per look and one word load
+// every 32 bits consumed.  Words past the end of a stream read as zero, so a
+// malformed stream cannot make the reader leave it; whether the stream was
+// overrun is checked once, after its last coefficient, from the bits consumed.
+struct WinReader {
+    const uint32_t *w;
+    uint32_t nw, cur, nxt, pos, idx;
+    __device__ __forceinline__ void init(const uint32_t *p, uint32_t n)
+    {
+        w = p;
+        nw = n;
+        cur = n > 0 ? p[0] : 0u;
+        nxt = n > 1 ? p[1] : 0u;
+        pos = 0;
+        idx = 2;
+    }
+    __device__ __forceinline__ uint32_t peek() const { return __funnelshift_r(cur, nxt, pos); }
+    __device__ __forceinline__ void skip(uint32_t n)  // n <= 32
+    {
+        pos += n;
+        if (pos >= 32u) {
+            pos -= 32u;
+            cur = nxt;
+            nxt = idx < nw ? w[idx] : 0u;
+            ++idx;
+        }
+    }
+    __device__ __forceinline__ bool overrun() const
+    {
+        return (uint64_t)(idx - 2u) * 32u + pos > (uint64_t)nw * 32u;
+    }
+};
+
+__device__ __forceinline__ void adapt_kr(uint32_t p, int &KR)
 {
-        BitReader br{wp, nw, 0u, 0ull, 0u, false};
-        int K = 0, KR = 32;
-        // one output row per iteration in every lane: runs are kept as pending
-        // zeros (and the nonzero that ends a partial run as a pending value), so
-        // the lanes of a warp stay in step and their row stores coalesce
-        uint32_t zeros = 0;
-        bool has_pending = false;
-        int32_t pending = 0;
-        for (uint32_t i = 0; i < len; ++i) {
-            int32_t q = 0;
-            if (zeros) {
-                --zeros;
-            } else if (has_pending) {
-                q = pending;
-                has_pending = false;
-            } else if (!br.bad) {
-                const uint32_t k = (uint32_t)K >> 4;
-                if (k == 0) {
-                    const uint32_t u = gr_get(br, (uint32_t)KR >> 4, KR);
-                    q = unzz(u);
-                    if (u == 0) {
-                        K += 3;
-                        if (K > 240) K = 240;
-                    } else {
-                        K = K >= 3 ? K - 3 : 0;
-                    }
-                } else if (br.get(1) == 0) {  // a full run of 2^k zeros (clamped at the block end)
+    if (p == 0) {
+        KR = KR >= 2 ? KR - 2 : 0;
+    } else if (p > 1) {
+        uint32_t t = (uint32_t)KR + (p > 384u ? 384u : p) + 1u;
+        KR = t > 384u ? 384 : (int)t;
+    }
+}
+
+// Golomb-Rice value with parameter k (<= 24): p ones and a zero, then k low
+// bits; p >= 24 is the escape (24 ones, a 6-bit length n, n bits of value).
+__device__ __forceinline__ uint32_t gr_read(WinReader &r, uint32_t k, int &KR, bool &bad)
+{
+    const uint32_t x = r.peek();
+    uint32_t p = (uint32_t)__ffs(~x) - 1u;  // leading ones (all ones: wraps to >= 32)
+    uint32_t v;
+    if (p < (uint32_t)kUnaryEsc) {
+        const uint32_t mk = (1u << k) - 1u;
+        const uint32_t n = p + 1u + k;
+        if (n <= 32u) {  // prefix and remainder inside the window
+            v = (p << k) | ((x >> (p + 1u)) & mk);
+            r.skip(n);
+        } else {
+            r.skip(p + 1u);
+            v = (p << k) | (r.peek() & mk);
+            r.skip(k);
+        }
+    } else {
+        r.skip(kUnaryEsc);
+        const uint32_t n = r.peek() & 63u;
+        r.skip(6);
+        if (n > 32u) {
+            bad = true;
+            return 0;
+        }
+        const uint32_t y = r.peek();
+        v = n == 32u ? y : (y & ((1u << n) - 1u));
+        r.skip(n);
+        p = v >> k;
+    }
+    adapt_kr(p, KR);
+    return v;
+}
+
+// Decodes one block stream (len coefficients of one channel) to out[i * C],
+// i < len: dequantised (times sc) or as indices.  Runs are kept as pending
+// zeros (and the nonzero that ends a partial run as a pending value), so every
+// lane of a warp writes one row per iteration and the stores coalesce.
+template <bool TO_INT>
+__device__ __forceinline__ void decode_stream(const uint32_t *wp, uint32_t nw, uint32_t len, uint32_t C, float sc,
+                                              float *yout, int32_t *qout, DevState *st)
+{
+    WinReader r;
+    r.init(wp, nw);
+    int K = 0, KR = 32;
+    uint32_t zeros = 0;
+    bool has_pending = false, bad = false;
+    int32_t pending = 0;
+    for (uint32_t i = 0; i < len; ++i) {
+        int32_t q = 0;
+        if (zeros) {
+            --zeros;
+        } else if (has_pending) {
+            q = pending;
+            has_pending = false;
+        } else {
+            const uint32_t k = (uint32_t)K >> 4;
+            if (k == 0) {
+                const uint32_t u = gr_read(r, (uint32_t)KR >> 4, KR, bad);
+                q = unzz(u);
+                if (u == 0) {
+                    K += 3;
+                    if (K > 240) K = 240;
+                } else {
+                    K = K >= 3 ? K - 3 : 0;
+                }
+            } else {
+                const uint32_t x = r.peek();
+                if (!(x & 1u)) {  // a full run of 2^k zeros (clamped at the block end)
+                    r.skip(1);
                     const uint32_t run = 1u << k;
                     zeros = (run < len - i ? run : len - i) - 1;
                     K += 4;
                     if (K > 240) K = 240;
                 } else {  // r < 2^k zeros, then a nonzero
-                    const uint32_t rr = br.get(k);
-                    const uint32_t v = gr_get(br, (uint32_t)KR >> 4, KR);
-                    if (rr >= len - i || v == 0xFFFFFFFFu) br.bad = true;
+                    const uint32_t rr = (x >> 1) & ((1u << k) - 1u);
+                    r.skip(1u + k);
+                    const uint32_t v = gr_read(r, (uint32_t)KR >> 4, KR, bad);
+                    if (rr >= len - i || v == 0xFFFFFFFFu) bad = true;
                     K = K >= 6 ? K - 6 : 0;
                     if (rr == 0) {
                         q = unzz(v + 1u);
@@ -362,60 +365,67 @@ __device__ __forceinline__ void decode_stream(const uint32_t *wp, uint32_t nw, u
                     }
                 }
             }
-            const uint64_t o = (row0 + i) * C + c;
-            if (TO_INT) qout[o] = q; else Y[o] = __fmul_rn((float)q, sc);
         }
-        if (br.bad) set_error(&st->err, kErrCorrupt);
+        if (TO_INT) {
+            *qout = q;
+            qout += C;
+        } else {
+            *yout = __fmul_rn((float)q, sc);
+            yout += C;
+        }
+    }
+    if (bad || r.overrun()) set_error(&st->err, kErrCorrupt);
 }
 
-// ---- decoder: one CTA per row block of one frame; thread = channel --------
-// The block's C streams are contiguous (block-major order); they are copied
-// to shared memory when they fit, then every thread decodes its channel.
+// Row blocks per CTA of the decoders: enough that rb * C fills whole warps
+// (rb = 32 / gcd(C, 32)), at most 512 threads.
+__host__ __device__ inline uint32_t dec_row_blocks(uint32_t C)
+{
+    uint32_t g = 32;
+    while (C % g) g >>= 1;
+    uint32_t rb = 32 / g;
+    if (rb * C > 512) rb = C >= 512 ? 1 : 512 / C;
+    return rb;
+}
+
+// One frame: thread (local row block jl, channel c) of CTA x decodes block
+// b = x * rb + jl of channel c.  Streams at block_off[b*C+c] (words) when
+// block_off is given, else at (b*C+c) * stride.
 template <bool TO_INT>
-__global__ void __launch_bounds__(256) rlgr_decode_kernel(const uint32_t *payload, uint64_t payload_words,
+__global__ void __launch_bounds__(512, 4) rlgr_decode_kernel(const uint32_t *payload, uint64_t payload_words,
                                                           const uint32_t *block_words, const uint64_t *block_off,
                                                           uint32_t stride, uint32_t nv, uint32_t C, uint32_t B,
-                                                          const float *step, float *Y, int32_t *qout, DevState *st,
-                                                          uint32_t stage_cap)
+                                                          uint32_t rb, const float *step, float *Y, int32_t *qout,
+                                                          DevState *st)
 {
-    extern __shared__ __align__(16) unsigned char dsm2[];
-    uint32_t *sw = reinterpret_cast<uint32_t *>(dsm2);
-    const uint32_t b = blockIdx.x;
-    const uint32_t row0 = b * B;
-    const uint32_t len = (nv - row0) < B ? (nv - row0) : B;
-    const uint64_t first = (uint64_t)b * C;
-    uint64_t base = 0, end = 0;
-    bool staged = false;
-    if (block_off) {
-        base = block_off[first];
-        end = block_off[first + C];
-        staged = stage_cap && end >= base && end - base <= stage_cap && end <= payload_words;
-        if (staged)
-            for (uint64_t k = threadIdx.x; k < end - base; k += blockDim.x) sw[k] = payload[base + k];
+    const uint32_t jl = threadIdx.x / C;
+    if (jl >= rb) return;
+    const uint32_t c = threadIdx.x - jl * C;
+    const uint64_t b = (uint64_t)blockIdx.x * rb + jl;
+    const uint64_t row0 = b * B;
+    if (row0 >= nv) return;
+    const uint32_t len = (nv - row0) < B ? (uint32_t)(nv - row0) : B;
+    const uint64_t blk = b * C + c;
+    const uint64_t off = block_off ? block_off[blk] : blk * stride;
+    uint32_t nw = block_words[blk];
+    if (off + nw > payload_words) {
+        set_error(&st->err, kErrCorrupt);
+        nw = 0;
     }
-    __syncthreads();
-    for (uint32_t c = threadIdx.x; c < C; c += blockDim.x) {
-        const uint64_t blk = first + c;
-        const uint64_t off = block_off ? block_off[blk] : blk * stride;
-        uint32_t nw = block_words[blk];
-        const uint32_t *wp = payload + off;
-        if (off + nw > payload_words) {
-            set_error(&st->err, kErrCorrupt);
-            nw = 0;
-        } else if (staged) {
-            wp = sw + (off - base);
-        }
-        decode_stream<TO_INT>(wp, nw, len, (uint64_t)row0, C, c, TO_INT ? 0.f : step[c], Y, qout, st);
-    }
+    decode_stream<TO_INT>(payload + off, nw, len, C, TO_INT ? 0.f : step[c], TO_INT ? nullptr : Y + row0 * C + c,
+                          TO_INT ? qout + row0 * C + c : nullptr, st);
 }
 
-// Batched decoder: one CTA per (frame, row block) over all frames of a batch.
-__global__ void __launch_bounds__(256) rlgr_decode_batch_kernel(const DecFrame *fr, uint32_t F,
+// All frames of a batch: row blocks numbered across frames (job_off), rb per CTA.
+__global__ void __launch_bounds__(512, 4) rlgr_decode_batch_kernel(const DecFrame *fr, uint32_t F,
                                                                 const uint64_t *job_off, const uint32_t *bw_all,
                                                                 const uint64_t *boff_all, const float *steps_all,
-                                                                uint32_t C, float *Y, DevState *st)
+                                                                uint32_t C, uint32_t rb, float *Y, DevState *st)
 {
-    const uint64_t job = blockIdx.x;
+    const uint32_t jl = threadIdx.x / C;
+    if (jl >= rb) return;
+    const uint32_t c = threadIdx.x - jl * C;
+    const uint64_t job = (uint64_t)blockIdx.x * rb + jl;
     if (job >= job_off[F]) return;
     uint32_t lo = 0, hi = F;
     while (hi - lo > 1) {
@@ -427,18 +437,15 @@ __global__ void __launch_bounds__(256) rlgr_decode_batch_kernel(const DecFrame *
     const uint32_t row0 = b * d.B;
     const uint32_t len = (d.nv - row0) < d.B ? (d.nv - row0) : d.B;
     const uint64_t base = boff_all[d.blk_off];
-    for (uint32_t c = threadIdx.x; c < C; c += blockDim.x) {
-        const uint64_t blk = d.blk_off + (uint64_t)b * C + c;
-        const uint64_t off = boff_all[blk] - base;
-        uint32_t nw = bw_all[blk];
-        const uint32_t *wp = d.payload + off;
-        if (off + nw > d.payload_words) {
-            set_error(&st->err, kErrCorrupt);
-            nw = 0;
-        }
-        decode_stream<false>(wp, nw, len, (uint64_t)d.vstart + row0, C, c, steps_all[(uint64_t)lo * C + c], Y, nullptr,
-                             st);
+    const uint64_t blk = d.blk_off + (uint64_t)b * C + c;
+    const uint64_t off = boff_all[blk] - base;
+    uint32_t nw = bw_all[blk];
+    if (off + nw > d.payload_words) {
+        set_error(&st->err, kErrCorrupt);
+        nw = 0;
     }
+    decode_stream<false>(d.payload + off, nw, len, C, steps_all[(uint64_t)lo * C + c],
+                         Y + ((uint64_t)d.vstart + row0) * C + c, nullptr, st);
 }
 
 __global__ void job_offsets_kernel(const uint32_t *vstart, uint32_t F, uint32_t B, uint32_t R, uint32_t C,
@@ -515,13 +522,12 @@ void launch_rlgr_decode(const uint32_t *payload, uint64_t payload_words, const u
                         DevState *st, cudaStream_t s)
 {
     if (nv == 0 || C == 0) return;
-    uint32_t nb = (uint32_t)((nv + B - 1) / B);
-    uint32_t threads = (C + 31) / 32 * 32;
-    if (threads > 256) threads = 256;
+    const uint64_t nb = (nv + B - 1) / B;
+    const uint32_t rb = dec_row_blocks(C);
     // Streams are read in place: staging them in shared memory would cap the
     // number of resident threads, and this sequential decoder needs them all.
-    rlgr_decode_kernel<false><<<nb, threads, 0, s>>>(payload, payload_words, block_words, block_off, 0u,
-                                                    (uint32_t)nv, C, B, step, Y, nullptr, st, 0u);
+    rlgr_decode_kernel<false><<<(uint32_t)((nb + rb - 1) / rb), rb * C, 0, s>>>(
+        payload, payload_words, block_words, block_off, 0u, (uint32_t)nv, C, B, rb, step, Y, nullptr, st);
     count_launch();
 }
 
@@ -530,10 +536,9 @@ void launch_rlgr_decode_batch(const DecFrame *fr, uint32_t F, const uint64_t *jo
                               float *Y, DevState *st, cudaStream_t s)
 {
     if (jobs_bound == 0 || C == 0) return;
-    uint32_t threads = (C + 31) / 32 * 32;
-    if (threads > 256) threads = 256;
-    rlgr_decode_batch_kernel<<<(uint32_t)jobs_bound, threads, 0, s>>>(fr, F, job_off, bw_all, boff_all, steps_all, C,
-                                                                       Y, st);
+    const uint32_t rb = dec_row_blocks(C);
+    rlgr_decode_batch_kernel<<<(uint32_t)((jobs_bound + rb - 1) / rb), rb * C, 0, s>>>(
+        fr, F, job_off, bw_all, boff_all, steps_all, C, rb, Y, st);
     count_launch();
 }
 
@@ -541,11 +546,10 @@ void launch_rlgr_decode_indices(const uint32_t *words, uint64_t total_words, con
                                 uint64_t nv, uint32_t C, uint32_t B, int32_t *q, DevState *st, cudaStream_t s)
 {
     if (nv == 0 || C == 0) return;
-    uint32_t nb = (uint32_t)((nv + B - 1) / B);
-    uint32_t threads = (C + 31) / 32 * 32;
-    if (threads > 256) threads = 256;
-    rlgr_decode_kernel<true><<<nb, threads, 0, s>>>(words, total_words, bw, nullptr, stride, (uint32_t)nv, C, B,
-                                                   nullptr, nullptr, q, st, 0u);
+    const uint64_t nb = (nv + B - 1) / B;
+    const uint32_t rb = dec_row_blocks(C);
+    rlgr_decode_kernel<true><<<(uint32_t)((nb + rb - 1) / rb), rb * C, 0, s>>>(
+        words, total_words, bw, nullptr, stride, (uint32_t)nv, C, B, rb, nullptr, nullptr, q, st);
     count_launch();
 }
 
