@@ -26,8 +26,11 @@ namespace {
 
 constexpr int kUnaryEsc = 24;
 
-struct BitWriter {  // words beyond `cap` are counted but not stored
-    uint64_t acc;
+// Bits are appended LSB first to a 32-bit word (cur, nacc bits used); a value
+// that straddles the word boundary leaves its upper part in the next word via
+// one funnel shift.  Words beyond `cap` are counted but not stored.
+struct BitWriter {
+    uint32_t cur;
     uint32_t nacc;
     uint32_t nw;
     uint32_t *out;
@@ -37,21 +40,22 @@ struct BitWriter {  // words beyond `cap` are counted but not stored
         if (nw < cap) out[nw] = w;
         ++nw;
     }
-    __device__ __forceinline__ void put(uint64_t v, uint32_t n)  // n <= 32
+    __device__ __forceinline__ void put(uint32_t v, uint32_t n)  // n <= 32, v < 2^n
     {
-        acc |= v << nacc;
+        const uint32_t spill = __funnelshift_l(v, 0u, nacc);  // bits of v above the word, if any
+        cur |= v << nacc;  // nacc < 32
         nacc += n;
-        if (nacc >= 32) {
-            emit((uint32_t)acc);
-            acc >>= 32;
-            nacc -= 32;
+        if (nacc >= 32u) {
+            emit(cur);
+            cur = spill;
+            nacc -= 32u;
         }
     }
     __device__ __forceinline__ void flush()
     {
         if (nacc) {
-            emit((uint32_t)acc);
-            acc = 0;
+            emit(cur);
+            cur = 0;
             nacc = 0;
         }
     }
@@ -70,12 +74,15 @@ __device__ __forceinline__ int32_t unzz(uint32_t u)
 __device__ __forceinline__ void gr_put(BitWriter &bw, uint32_t v, uint32_t k, int &KR)
 {
     const uint32_t p = v >> k;
-    if (p < (uint32_t)kUnaryEsc && p + 1 + k <= 32u) {  // common case: unary prefix and remainder in one write
-        const uint64_t low = (uint64_t)(v & ((1u << k) - 1u));
-        bw.put(((1ull << p) - 1ull) | (low << (p + 1)), p + 1 + k);
-    } else if (p < (uint32_t)kUnaryEsc) {
-        bw.put((1u << p) - 1u, p + 1);  // p ones then a zero
-        if (k) bw.put(v & ((k < 32) ? ((1u << k) - 1u) : 0xFFFFFFFFu), k);
+    if (p < (uint32_t)kUnaryEsc) {
+        const uint32_t low = v & ((1u << k) - 1u);  // k <= 24
+        const uint32_t ones = (1u << p) - 1u;       // p ones then a zero
+        if (p + 1u + k <= 32u) {                    // common case: one write
+            bw.put(ones | (low << (p + 1u)), p + 1u + k);
+        } else {
+            bw.put(ones, p + 1u);
+            bw.put(low, k);
+        }
     } else {
         const uint32_t n = 32u - (uint32_t)__clz(v);
         bw.put((1u << kUnaryEsc) - 1u, kUnaryEsc);
@@ -158,48 +165,81 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
+// Row blocks per CTA: enough that rb * W (W = rungs x channels threads per
+// row block) fills whole warps (rb = 32 / gcd(W, 32)), at most 512 threads.
+__host__ __device__ inline uint32_t row_blocks_per_cta(uint32_t W)
+{
+    uint32_t g = 32;
+    while (W % g) g >>= 1;
+    uint32_t rb = 32 / g;
+    if (rb * W > 512) rb = W >= 512 ? 1 : 512 / W;
+    return rb;
+}
+
+struct EncBlock {  // one row block of a CTA
+    uint64_t gbase;  // first coefficient (row-major) of the block
+    uint32_t f, b, nb, len;
+};
+
 template <bool FROM_INT>
-__global__ void __launch_bounds__(1024) rlgr_encode_kernel(EncJobs E, const int32_t *qin)
+__global__ void __launch_bounds__(1024) rlgr_encode_kernel(EncJobs E, const int32_t *qin, uint32_t rb)
 {
     extern __shared__ __align__(16) unsigned char esm[];
+    __shared__ EncBlock blk_info[32];
     const RlgrJob &j = E.j;
-    const uint64_t job = blockIdx.x;
-    if (job >= E.job_off[j.F]) return;
-    uint32_t lo = 0, hi = j.F;  // frame of this row block
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (E.job_off[mid] <= job) lo = mid; else hi = mid;
+    const uint32_t C = j.C, W = j.R * C;
+    const uint64_t njobs = E.job_off[j.F];
+    const uint32_t t = threadIdx.x;
+    if (t < rb) {  // describe the CTA's row blocks
+        EncBlock e{0, 0, 0, 0, 0};
+        const uint64_t job = (uint64_t)blockIdx.x * rb + t;
+        if (job < njobs) {
+            uint32_t lo = 0, hi = j.F;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (E.job_off[mid] <= job) lo = mid; else hi = mid;
+            }
+            const uint32_t vs = j.vstart[lo], nv = j.vstart[lo + 1] - vs;
+            e.f = lo;
+            e.b = (uint32_t)(job - E.job_off[lo]);
+            e.nb = (nv + j.B - 1) / j.B;
+            const uint32_t row0 = e.b * j.B;
+            e.len = (nv - row0) < j.B ? (nv - row0) : j.B;
+            e.gbase = ((uint64_t)vs + row0) * C;
+        }
+        blk_info[t] = e;
     }
-    const uint32_t f = lo;
-    const uint32_t b = (uint32_t)(job - E.job_off[f]);
-    const uint32_t vs = j.vstart[f], nv = j.vstart[f + 1] - vs;
-    const uint32_t nb = (nv + j.B - 1) / j.B;
-    const uint32_t row0 = b * j.B;
-    const uint32_t len = (nv - row0) < j.B ? (nv - row0) : j.B;
-    const uint32_t C = j.C;
+    __syncthreads();
     const uint32_t chunk_elems = kChunkRows * C;
-    uint32_t *buf = reinterpret_cast<uint32_t *>(esm);  // 2 x chunk_elems words
+    uint32_t *buf = reinterpret_cast<uint32_t *>(esm);  // rb x 2 x chunk_elems words
     const uint32_t *src = FROM_INT ? reinterpret_cast<const uint32_t *>(qin) : reinterpret_cast<const uint32_t *>(j.Y);
-    const uint64_t gbase = ((uint64_t)vs + row0) * C;
-    const bool vec = (C % 4 == 0) && ((gbase & 3) == 0) && (((uintptr_t)src & 15) == 0);
-    const uint32_t nchunks = (len + kChunkRows - 1) / kChunkRows;
+    uint32_t maxlen = 0;
+    for (uint32_t q = 0; q < rb; ++q) maxlen = blk_info[q].len > maxlen ? blk_info[q].len : maxlen;
+    const uint32_t nchunks = (maxlen + kChunkRows - 1) / kChunkRows;
     auto issue = [&](uint32_t k) {
         const uint32_t r0 = k * kChunkRows;
-        const uint32_t rows = (len - r0) < kChunkRows ? (len - r0) : kChunkRows;
-        uint32_t *dst = buf + (k & 1) * chunk_elems;
-        const uint32_t *gs = src + gbase + (uint64_t)r0 * C;
-        if (vec) {
-            for (uint32_t v = threadIdx.x; v < rows * C / 4; v += blockDim.x) cp_async16(dst + 4 * v, gs + 4 * v);
-        } else {
-            for (uint32_t v = threadIdx.x; v < rows * C; v += blockDim.x) cp_async4(dst + v, gs + v);
+        for (uint32_t q = 0; q < rb; ++q) {
+            const EncBlock &e = blk_info[q];
+            if (r0 >= e.len) continue;
+            const uint32_t rows = (e.len - r0) < kChunkRows ? (e.len - r0) : kChunkRows;
+            uint32_t *dst = buf + (2 * q + (k & 1)) * chunk_elems;
+            const uint32_t *gs = src + e.gbase + (uint64_t)r0 * C;
+            const bool vec = (C % 4 == 0) && ((e.gbase & 3) == 0) && (((uintptr_t)src & 15) == 0);
+            if (vec) {
+                for (uint32_t v = t; v < rows * C / 4; v += blockDim.x) cp_async16(dst + 4 * v, gs + 4 * v);
+            } else {
+                for (uint32_t v = t; v < rows * C; v += blockDim.x) cp_async4(dst + v, gs + v);
+            }
         }
         cp_async_commit();
     };
-    const uint32_t t = threadIdx.x;
-    const bool act = t < j.R * C;
-    const uint32_t r = act ? t / C : 0u, c = act ? t - r * C : 0u;
-    const uint64_t blk = j.blk_off[f] + ((uint64_t)r * nb + b) * C + c;
-    BitWriter bw{0ull, 0u, 0u, j.slots + blk * j.slot_words, j.slot_words};
+    const uint32_t jl = t / W;
+    const bool act = jl < rb && blk_info[jl < rb ? jl : 0].len > 0;
+    const uint32_t w = act ? t - jl * W : 0u;
+    const uint32_t r = w / C, c = w - r * C;
+    const EncBlock &me = blk_info[act ? jl : 0];
+    const uint64_t blk = act ? j.blk_off[me.f] + ((uint64_t)r * me.nb + me.b) * C + c : 0;
+    BitWriter bw{0u, 0u, 0u, j.slots + blk * j.slot_words, j.slot_words};
     Rlgr st;
     st.init();
     const float inv = (FROM_INT || !act) ? 0.f : j.inv_step[r * C + c];
@@ -212,12 +252,12 @@ __global__ void __launch_bounds__(1024) rlgr_encode_kernel(EncJobs E, const int3
             cp_async_wait_all();
         }
         __syncthreads();
-        const uint32_t rows = (len - k * kChunkRows) < kChunkRows ? (len - k * kChunkRows) : kChunkRows;
-        const uint32_t *cb = buf + (k & 1) * chunk_elems;
-        if (act) {
+        if (act && k * kChunkRows < me.len) {
+            const uint32_t rows = (me.len - k * kChunkRows) < kChunkRows ? (me.len - k * kChunkRows) : kChunkRows;
+            const uint32_t *cb = buf + (2 * jl + (k & 1)) * chunk_elems + c;
             for (uint32_t i = 0; i < rows; ++i) {
-                const uint32_t w = cb[i * C + c];
-                const int32_t q = FROM_INT ? (int32_t)w : quantize_f32(__uint_as_float(w), inv, j.tau);
+                const uint32_t x = cb[i * C];
+                const int32_t q = FROM_INT ? (int32_t)x : quantize_f32(__uint_as_float(x), inv, j.tau);
                 st.code(bw, zz(q));
             }
         }
@@ -377,17 +417,6 @@ __device__ __forceinline__ void decode_stream(const uint32_t *wp, uint32_t nw, u
     if (bad || r.overrun()) set_error(&st->err, kErrCorrupt);
 }
 
-// Row blocks per CTA of the decoders: enough that rb * C fills whole warps
-// (rb = 32 / gcd(C, 32)), at most 512 threads.
-__host__ __device__ inline uint32_t dec_row_blocks(uint32_t C)
-{
-    uint32_t g = 32;
-    while (C % g) g >>= 1;
-    uint32_t rb = 32 / g;
-    if (rb * C > 512) rb = C >= 512 ? 1 : 512 / C;
-    return rb;
-}
-
 // One frame: thread (local row block jl, channel c) of CTA x decodes block
 // b = x * rb + jl of channel c.  Streams at block_off[b*C+c] (words) when
 // block_off is given, else at (b*C+c) * stride.
@@ -480,16 +509,17 @@ void launch_rlgr_offsets(const uint32_t *vstart, uint32_t F, uint32_t B, uint32_
     count_launch();
 }
 
-static size_t enc_smem(uint32_t C) { return (size_t)2 * kChunkRows * C * 4; }
+static size_t enc_smem(uint32_t C, uint32_t rb) { return (size_t)rb * 2 * kChunkRows * C * 4; }
 
 void launch_rlgr_encode(const RlgrJob &j, const uint64_t *job_off, uint64_t jobs_bound, cudaStream_t s)
 {
     if (jobs_bound == 0 || j.C == 0) return;
     EncJobs E{j, job_off};
-    uint32_t threads = (j.R * j.C + 31) / 32 * 32;
-    const size_t smem = enc_smem(j.C);
+    const uint32_t rb = row_blocks_per_cta(j.R * j.C);
+    const uint32_t threads = (rb * j.R * j.C + 31) / 32 * 32;
+    const size_t smem = enc_smem(j.C, rb);
     cudaFuncSetAttribute(rlgr_encode_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    rlgr_encode_kernel<false><<<(uint32_t)jobs_bound, threads, smem, s>>>(E, nullptr);
+    rlgr_encode_kernel<false><<<(uint32_t)((jobs_bound + rb - 1) / rb), threads, smem, s>>>(E, nullptr, rb);
     count_launch();
 }
 
@@ -510,10 +540,11 @@ void launch_rlgr_encode_indices(const int32_t *q, const uint32_t *vstart, uint32
     j.slot_words = slot_words;
     j.overflow = overflow;
     EncJobs E{j, job_off};
-    uint32_t threads = (C + 31) / 32 * 32;
-    const size_t smem = enc_smem(C);
+    const uint32_t rb = row_blocks_per_cta(C);
+    const uint32_t threads = (rb * C + 31) / 32 * 32;
+    const size_t smem = enc_smem(C, rb);
     cudaFuncSetAttribute(rlgr_encode_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    rlgr_encode_kernel<true><<<(uint32_t)jobs_bound, threads, smem, s>>>(E, q);
+    rlgr_encode_kernel<true><<<(uint32_t)((jobs_bound + rb - 1) / rb), threads, smem, s>>>(E, q, rb);
     count_launch();
 }
 
@@ -523,7 +554,7 @@ void launch_rlgr_decode(const uint32_t *payload, uint64_t payload_words, const u
 {
     if (nv == 0 || C == 0) return;
     const uint64_t nb = (nv + B - 1) / B;
-    const uint32_t rb = dec_row_blocks(C);
+    const uint32_t rb = row_blocks_per_cta(C);
     // Streams are read in place: staging them in shared memory would cap the
     // number of resident threads, and this sequential decoder needs them all.
     rlgr_decode_kernel<false><<<(uint32_t)((nb + rb - 1) / rb), rb * C, 0, s>>>(
@@ -536,7 +567,7 @@ void launch_rlgr_decode_batch(const DecFrame *fr, uint32_t F, const uint64_t *jo
                               float *Y, DevState *st, cudaStream_t s)
 {
     if (jobs_bound == 0 || C == 0) return;
-    const uint32_t rb = dec_row_blocks(C);
+    const uint32_t rb = row_blocks_per_cta(C);
     rlgr_decode_batch_kernel<<<(uint32_t)((jobs_bound + rb - 1) / rb), rb * C, 0, s>>>(
         fr, F, job_off, bw_all, boff_all, steps_all, C, rb, Y, st);
     count_launch();
@@ -547,7 +578,7 @@ void launch_rlgr_decode_indices(const uint32_t *words, uint64_t total_words, con
 {
     if (nv == 0 || C == 0) return;
     const uint64_t nb = (nv + B - 1) / B;
-    const uint32_t rb = dec_row_blocks(C);
+    const uint32_t rb = row_blocks_per_cta(C);
     rlgr_decode_kernel<true><<<(uint32_t)((nb + rb - 1) / rb), rb * C, 0, s>>>(
         words, total_words, bw, nullptr, stride, (uint32_t)nv, C, B, rb, nullptr, nullptr, q, st);
     count_launch();
