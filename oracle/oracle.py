@@ -244,7 +244,7 @@ def rans_freqs(data):
     return f
 
 
-def occ_section_encode(occ, chunk_syms=16384):
+def occ_section_encode(occ, chunk_syms=4096):
     occ = np.ascontiguousarray(occ, dtype=np.uint8)
     n = occ.shape[0]
     cap = 64 + 2 * n + 1024 + (n // 32 + 1) * 256
@@ -261,7 +261,7 @@ def occ_section_decode(sec, n):
 
 
 # --- whole frame -------------------------------------------------------------
-def encode_frame(pos, attr, J, groups=None, steps=None, tau=0.5, block=512, chunk_syms=16384,
+def encode_frame(pos, attr, J, groups=None, steps=None, tau=0.5, block=512, chunk_syms=4096,
                  with_coeffs=False):
     """Oracle encoder.  Returns dict(bitstream, nv, codes[, coeffs, q])."""
     pos = np.ascontiguousarray(pos, dtype=np.float32).reshape(-1, 3)

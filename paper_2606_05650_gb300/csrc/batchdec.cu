@@ -4,6 +4,7 @@
 // Frames are described by a device table (DecFrame); every kernel finds the
 // frame of its work item with a binary search over per-frame prefix sums.
 #include "kernels.cuh"
+#include "rans_dec.cuh"
 
 namespace gsnfs {
 
@@ -12,7 +13,6 @@ namespace {
 constexpr uint32_t kProbBits = 15;
 constexpr uint32_t kM = 1u << kProbBits;
 constexpr uint32_t kL = 1u << 16;
-constexpr int kWarpsPerCta = 2;
 
 template <typename T>
 __device__ __forceinline__ uint32_t find_frame(const T *pref, uint32_t F, uint64_t x)
@@ -74,77 +74,45 @@ __global__ void __launch_bounds__(1024) tables_kernel(const DecFrame *fr, uint32
 }
 
 // grid (chunk groups, frames): warp per chunk of frame blockIdx.y
-__global__ void __launch_bounds__(32 * kWarpsPerCta) rans_batch_kernel(const DecFrame *fr, const uint32_t *tabs,
-                                                                       uint64_t tab_words, uint32_t stage_bytes,
-                                                                       uint8_t *occ_all, DevState *st)
+__global__ void __launch_bounds__(32 * ransdec::kMaxWarps) rans_batch_kernel(const DecFrame *fr, const uint32_t *tabs,
+                                                                             uint64_t tab_words, uint32_t chunk_max,
+                                                                             uint8_t *occ_all, DevState *st)
 {
+    using namespace ransdec;
     extern __shared__ __align__(16) unsigned char dsm[];
     const DecFrame &d = fr[blockIdx.y];
     if (d.mode != 1) return;
     const uint32_t *tab = tabs + (uint64_t)blockIdx.y * tab_words;
-    if (tab[kM / 4 + 256] != 0) return;
-    for (uint32_t k = threadIdx.x; k < kM / 4 + 256; k += blockDim.x) reinterpret_cast<uint32_t *>(dsm)[k] = tab[k];
+    if (tab[kTabWords] != 0) return;
+    const uint32_t nch = d.aux, chunk = d.chunk;
+    const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (blockIdx.x * nwarps >= nch) return;  // no chunk of this frame for this CTA
+    load_tables(reinterpret_cast<uint32_t *>(dsm), tab);
     __syncthreads();
     const uint8_t *slot2sym = dsm;
     const uint32_t *fc = reinterpret_cast<const uint32_t *>(dsm + kM);
-    const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    uint8_t *cbuf = dsm + kM + 1024 + (size_t)wl * ((stage_bytes + 15) & ~15u);
-    const uint32_t nch = d.aux, chunk = d.chunk;
+    const bool staged = chunk_max <= 32768;
+    uint32_t *cbuf = reinterpret_cast<uint32_t *>(dsm + kTabWords * 4 + (size_t)wl * stage_bytes(chunk_max));
     const uint8_t *ctab = d.occ_sec + 24 + 512;
     const uint64_t table = (16 + 8 + 512 + 4 * (uint64_t)nch + 7) & ~7ull;
-    const uint32_t ltm = lanemask_lt();
-    for (uint32_t c = blockIdx.x * kWarpsPerCta + wl; c < nch; c += gridDim.x * kWarpsPerCta) {
-        uint64_t off = 0;
-        for (uint32_t k = lane; k < c; k += 32) {
-            const uint8_t *p = ctab + 4 * k;
-            off += (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
-        }
-        for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xFFFFFFFFu, off, o);
+    uint8_t *out = occ_all + d.occ_off;
+    for (uint32_t c = blockIdx.x * nwarps + wl; c < nch; c += gridDim.x * nwarps) {
+        const uint64_t start = table + chunk_offset(ctab, c, lane);
         const uint8_t *cp = ctab + 4 * c;
         const uint32_t cbytes = (uint32_t)cp[0] | ((uint32_t)cp[1] << 8) | ((uint32_t)cp[2] << 16) | ((uint32_t)cp[3] << 24);
-        const uint64_t start = table + off;
         if (cbytes < 128 || (cbytes & 3) || cbytes > 128 + 2 * chunk + 2 || start + cbytes > d.occ_bytes) {
             if (lane == 0) set_error(&st->err, kErrCorrupt);
             continue;
         }
-        const uint8_t *ch = d.occ_sec + start;
-        const uint8_t *src = ch;
-        if (stage_bytes) {
-            __syncwarp();
-            for (uint32_t k = lane; k < cbytes / 4; k += 32)
-                reinterpret_cast<uint32_t *>(cbuf)[k] = reinterpret_cast<const uint32_t *>(ch)[k];
-            __syncwarp();
-            src = cbuf;
+        const uint8_t *src = d.occ_sec + start;
+        if (staged) {
+            stage_chunk(cbuf, reinterpret_cast<const uint32_t *>(src), cbytes / 4, lane);
+            src = reinterpret_cast<const uint8_t *>(cbuf);
         }
-        const uint32_t W = (cbytes - 128) / 2;
-        const uint16_t *words = reinterpret_cast<const uint16_t *>(src + 128);
-        uint32_t x = reinterpret_cast<const uint32_t *>(src)[lane];
         const uint64_t s0 = (uint64_t)c * chunk;
         const uint32_t len = (uint32_t)((d.n_occ - s0) < chunk ? (d.n_occ - s0) : chunk);
-        uint8_t *out = occ_all + d.occ_off;
-        uint32_t wp = 0;
-        bool bad = false;
-        for (uint32_t g = 0; g * 32 < len; ++g) {
-            const uint32_t j = g * 32 + lane;
-            const bool valid = j < len;
-            bool need = false;
-            if (valid) {
-                const uint32_t slot = x & (kM - 1);
-                const uint32_t sy = slot2sym[slot];
-                const uint32_t f = fc[sy];
-                out[s0 + j] = (uint8_t)sy;
-                x = (f >> 16) * (x >> kProbBits) + slot - (f & 0xFFFFu);
-                need = x < kL;
-            }
-            const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
-            if (need) {
-                const uint32_t k = wp + __popc(m & ltm);
-                if (k < W) x = (x << 16) | words[k];
-                else bad = true;
-            }
-            wp += __popc(m);
-        }
-        if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) set_error(&st->err, kErrCorrupt);
+        if (decode_chunk(slot2sym, fc, src, (cbytes - 128) / 2, len, out + s0, lane) && lane == 0)
+            set_error(&st->err, kErrCorrupt);
     }
 }
 
@@ -258,11 +226,12 @@ void launch_batch_rans_decode(const DecFrame *fr, uint32_t F, uint32_t max_chunk
     const uint64_t tab_words = kM / 4 + 256 + 4;
     tables_kernel<<<F, 1024, 0, s>>>(fr, tabs, tab_words, st);
     count_launch();
-    const uint32_t stage = chunk_max <= 32768 ? 128 + 2 * chunk_max : 0u;
-    const size_t smem = kM + 1024 + (size_t)kWarpsPerCta * ((stage + 15) & ~15u);
+    const bool staged = chunk_max <= 32768;
+    const uint32_t warps = staged ? ransdec::warps_per_cta(chunk_max) : ransdec::kMaxWarps;
+    const size_t smem = staged ? ransdec::smem_bytes(chunk_max, warps) : (size_t)ransdec::kTabWords * 4;
     cudaFuncSetAttribute(rans_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const uint32_t X = (max_chunks_per_frame + kWarpsPerCta - 1) / kWarpsPerCta;
-    rans_batch_kernel<<<dim3(X, F), 32 * kWarpsPerCta, smem, s>>>(fr, tabs, tab_words, stage, occ_all, st);
+    const uint32_t X = (max_chunks_per_frame + warps - 1) / warps;
+    rans_batch_kernel<<<dim3(X, F), 32 * warps, smem, s>>>(fr, tabs, tab_words, chunk_max, occ_all, st);
     count_launch();
 }
 

@@ -10,6 +10,7 @@
 // 32 symbols from last to first (lanes 31..0 within a group) pushing words on
 // a stack; the decoder walks forward and pops them in lane order.
 #include "kernels.cuh"
+#include "rans_dec.cuh"
 
 namespace gsnfs {
 
@@ -101,7 +102,8 @@ __global__ void __launch_bounds__(32 * kEncWarps) encode_kernel(const uint8_t *_
                                                                uint32_t *chunk_top)
 {
     __shared__ uint8_t s_sym[kEncWarps][kStageSyms];
-    __shared__ uint32_t s_fc[kEncWarps][256];  // freq << 16 | cum (cum < 2^15)
+    __shared__ uint32_t s_fc[kEncWarps][256];   // freq << 16 | cum (cum < 2^15)
+    __shared__ uint32_t s_rcp[kEncWarps][256];  // ceil(2^32 / freq) for freq >= 2 (0 for freq < 2)
     const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const uint64_t gw = (uint64_t)blockIdx.x * kEncWarps + wl;
     const uint64_t nw = (uint64_t)gridDim.x * kEncWarps;
@@ -112,7 +114,11 @@ __global__ void __launch_bounds__(32 * kEncWarps) encode_kernel(const uint8_t *_
         const uint64_t n = occ_off[f + 1] - occ_off[f];
         const uint8_t *sym = occ + occ_off[f] + c * chunk;
         const uint32_t len = (uint32_t)((n - c * chunk) < chunk ? (n - c * chunk) : chunk);
-        for (uint32_t k = lane; k < 256; k += 32) s_fc[wl][k] = ((uint32_t)freq[f * 256 + k] << 16) | cum[f * 256 + k];
+        for (uint32_t k = lane; k < 256; k += 32) {
+            const uint32_t fk = freq[f * 256 + k];
+            s_fc[wl][k] = (fk << 16) | cum[f * 256 + k];
+            s_rcp[wl][k] = fk >= 2 ? (uint32_t)((0x100000000ull + fk - 1) / fk) : 0u;
+        }
         uint8_t *slot = slots + gc * slot_bytes;
         uint16_t *stack = reinterpret_cast<uint16_t *>(slot + 128);
         uint32_t top = chunk;
@@ -129,7 +135,8 @@ __global__ void __launch_bounds__(32 * kEncWarps) encode_kernel(const uint8_t *_
             for (; g >= (int)win_lo_g; --g) {
                 const uint32_t j = (uint32_t)g * 32 + lane;
                 const bool valid = j < len;
-                const uint32_t fc = s_fc[wl][valid ? s_sym[wl][j - b0] : 0u];
+                const uint32_t sy = valid ? s_sym[wl][j - b0] : 0u;
+                const uint32_t fc = s_fc[wl][sy], rcp = s_rcp[wl][sy];
                 const uint32_t fs = fc >> 16, cs = fc & 0xFFFFu;
                 const bool need = valid && ((uint64_t)x >= ((uint64_t)fs << 17));
                 const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
@@ -139,7 +146,17 @@ __global__ void __launch_bounds__(32 * kEncWarps) encode_kernel(const uint8_t *_
                     x >>= 16;
                 }
                 top -= __popc(m);
-                if (valid) x = ((x / fs) << kProbBits) + (x % fs) + cs;
+                if (valid) {
+                    // x / fs and x % fs: the estimate floor(x * ceil(2^32/fs) / 2^32) is the
+                    // quotient or one more (the error term x / 2^32 is below 1)
+                    uint32_t qt = fs >= 2 ? __umulhi(x, rcp) : x;
+                    int32_t rm = (int32_t)(x - qt * fs);
+                    if (rm < 0) {
+                        --qt;
+                        rm += (int32_t)fs;
+                    }
+                    x = (qt << kProbBits) + (uint32_t)rm + cs;
+                }
             }
         }
         reinterpret_cast<uint32_t *>(slot)[lane] = x;
@@ -151,39 +168,46 @@ __global__ void __launch_bounds__(32 * kEncWarps) encode_kernel(const uint8_t *_
     }
 }
 
-// per frame: occupancy section size and final mode (rANS only when smaller than raw)
-__global__ void section_size_kernel(const uint64_t *occ_off, const uint64_t *chunk_off, uint32_t F,
-                                    const uint32_t *chunk_words, uint32_t *chunk_pos, uint32_t *mode,
-                                    uint64_t *sec_bytes)
+// per frame (one warp each): chunk positions by a warp scan of the chunk
+// sizes, the occupancy section size and the final mode (rANS only when
+// smaller than raw)
+__global__ void __launch_bounds__(256) section_size_kernel(const uint64_t *occ_off, const uint64_t *chunk_off,
+                                                           uint32_t F, const uint32_t *chunk_words,
+                                                           uint32_t *chunk_pos, uint32_t *mode, uint64_t *sec_bytes)
 {
-    const uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint32_t lane = threadIdx.x & 31;
     if (f >= F) return;
     const uint64_t n = occ_off[f + 1] - occ_off[f];
     const uint64_t raw = 16 + ((n + 7) & ~7ull);
-    if (mode[f] == 2) {
-        sec_bytes[f] = 16;
+    const uint32_t md = mode[f];
+    if (md == 2) {
+        if (lane == 0) sec_bytes[f] = 16;
         return;
     }
-    if (mode[f] == 1) {
-        const uint64_t nch = chunk_off[f + 1] - chunk_off[f];
+    if (md == 1) {
+        const uint64_t c0 = chunk_off[f], nch = chunk_off[f + 1] - c0;
         uint64_t t = (16 + 8 + 512 + 4 * nch + 7) & ~7ull;
-        for (uint64_t c = 0; c < nch; ++c) {
-            chunk_pos[chunk_off[f] + c] = (uint32_t)t;
-            t += (128 + 2 * (uint64_t)chunk_words[chunk_off[f] + c] + 3) & ~3ull;
+        for (uint64_t base = 0; base < nch; base += 32) {
+            const uint64_t c = base + lane;
+            const uint32_t sz = c < nch ? (uint32_t)((128 + 2 * (uint64_t)chunk_words[c0 + c] + 3) & ~3ull) : 0u;
+            const uint32_t inc = warp_inclusive_sum(sz);
+            if (c < nch) chunk_pos[c0 + c] = (uint32_t)(t + inc - sz);
+            t += __shfl_sync(0xFFFFFFFFu, inc, 31);
         }
         t = (t + 7) & ~7ull;
         if (t < raw) {
-            sec_bytes[f] = t;
+            if (lane == 0) sec_bytes[f] = t;
             return;
         }
-        mode[f] = 0;
+        __syncwarp();
+        if (lane == 0) mode[f] = 0;
     }
-    sec_bytes[f] = raw;
+    if (lane == 0) sec_bytes[f] = raw;
 }
 
 // ---- decoder: warp per chunk of one frame; the chunk (states and words) is
 // copied to shared memory with coalesced loads, then decoded from there.
-constexpr int kDecWarps = 2;
 
 // slot -> symbol table (kM bytes) and freq << 16 | cum (256 words) of one
 // section, followed by a corruption flag; one CTA of 1024 threads
@@ -220,75 +244,40 @@ __global__ void __launch_bounds__(1024) table_kernel(const uint8_t *__restrict__
     }
 }
 
-__global__ void __launch_bounds__(32 * kDecWarps) decode_kernel(const uint8_t *__restrict__ sec, uint64_t sec_bytes,
-                                                               uint64_t n, uint32_t nch, uint32_t chunk, uint8_t *out,
-                                                               DevState *st, bool staged, const uint32_t *tabs)
+__global__ void __launch_bounds__(32 * ransdec::kMaxWarps) decode_kernel(const uint8_t *__restrict__ sec,
+                                                                         uint64_t sec_bytes, uint64_t n, uint32_t nch,
+                                                                         uint32_t chunk, uint8_t *out, DevState *st,
+                                                                         bool staged, const uint32_t *tabs)
 {
+    using namespace ransdec;
     extern __shared__ __align__(16) unsigned char dsm[];
-    uint8_t *slot2sym = dsm;                                               // kM
-    uint32_t *fc = reinterpret_cast<uint32_t *>(dsm + kM);                 // 256: freq << 16 | cum
-    const uint32_t stage_bytes = staged ? 128 + 2 * chunk : 0u;
-    const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    uint8_t *cbuf = dsm + kM + 1024 + (size_t)wl * ((stage_bytes + 15) & ~15u);
     // decoding tables built once by table_kernel: copy them in
-    if (tabs[kM / 4 + 256] != 0) return;  // frequencies did not sum to M (reported by table_kernel)
-    for (uint32_t k = threadIdx.x; k < kM / 4 + 256; k += blockDim.x)
-        reinterpret_cast<uint32_t *>(dsm)[k] = tabs[k];
+    if (tabs[kTabWords] != 0) return;  // frequencies did not sum to M (reported by table_kernel)
+    load_tables(reinterpret_cast<uint32_t *>(dsm), tabs);
     __syncthreads();
+    const uint8_t *slot2sym = dsm;
+    const uint32_t *fc = reinterpret_cast<const uint32_t *>(dsm + kM);
+    const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    uint32_t *cbuf = reinterpret_cast<uint32_t *>(dsm + kTabWords * 4 + (size_t)wl * stage_bytes(chunk));
     const uint8_t *ctab = sec + 24 + 512;
     const uint64_t table = (16 + 8 + 512 + 4 * (uint64_t)nch + 7) & ~7ull;
-    const uint32_t ltm = lanemask_lt();
-    for (uint32_t c = blockIdx.x * kDecWarps + wl; c < nch; c += gridDim.x * kDecWarps) {
-        uint64_t off = 0;
-        for (uint32_t k = lane; k < c; k += 32) {
-            const uint8_t *p = ctab + 4 * k;
-            off += (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
-        }
-        for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xFFFFFFFFu, off, o);
+    for (uint32_t c = blockIdx.x * nwarps + wl; c < nch; c += gridDim.x * nwarps) {
+        const uint64_t start = table + chunk_offset(ctab, c, lane);
         const uint8_t *cp = ctab + 4 * c;
         const uint32_t cbytes = (uint32_t)cp[0] | ((uint32_t)cp[1] << 8) | ((uint32_t)cp[2] << 16) | ((uint32_t)cp[3] << 24);
-        const uint64_t start = table + off;
         if (cbytes < 128 || (cbytes & 3) || cbytes > 128 + 2 * chunk + 2 || start + cbytes > sec_bytes) {
             if (lane == 0) set_error(&st->err, kErrCorrupt);
             continue;
         }
-        const uint8_t *ch = sec + start;  // 4-byte aligned (sections 8-aligned, chunks padded to 4)
-        const uint8_t *src = ch;
+        const uint8_t *src = sec + start;  // 4-byte aligned (sections 8-aligned, chunks padded to 4)
         if (staged) {
-            __syncwarp();
-            for (uint32_t k = lane; k < cbytes / 4; k += 32)
-                reinterpret_cast<uint32_t *>(cbuf)[k] = reinterpret_cast<const uint32_t *>(ch)[k];
-            __syncwarp();
-            src = cbuf;
+            stage_chunk(cbuf, reinterpret_cast<const uint32_t *>(src), cbytes / 4, lane);
+            src = reinterpret_cast<const uint8_t *>(cbuf);
         }
-        const uint32_t W = (cbytes - 128) / 2;
-        const uint16_t *words = reinterpret_cast<const uint16_t *>(src + 128);
-        uint32_t x = reinterpret_cast<const uint32_t *>(src)[lane];
         const uint64_t s0 = (uint64_t)c * chunk;
         const uint32_t len = (uint32_t)((n - s0) < chunk ? (n - s0) : chunk);
-        uint32_t wp = 0;
-        bool bad = false;
-        for (uint32_t g = 0; g * 32 < len; ++g) {
-            const uint32_t j = g * 32 + lane;
-            const bool valid = j < len;
-            bool need = false;
-            if (valid) {
-                const uint32_t slot = x & (kM - 1);
-                const uint32_t sy = slot2sym[slot];
-                const uint32_t f = fc[sy];
-                out[s0 + j] = (uint8_t)sy;
-                x = (f >> 16) * (x >> kProbBits) + slot - (f & 0xFFFFu);
-                need = x < kL;
-            }
-            const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
-            if (need) {
-                const uint32_t k = wp + __popc(m & ltm);
-                if (k < W) x = (x << 16) | words[k];
-                else bad = true;
-            }
-            wp += __popc(m);
-        }
-        if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) set_error(&st->err, kErrCorrupt);
+        if (decode_chunk(slot2sym, fc, src, (cbytes - 128) / 2, len, out + s0, lane) && lane == 0)
+            set_error(&st->err, kErrCorrupt);
     }
 }
 
@@ -321,8 +310,8 @@ void launch_rans_encode(const RansFrames &r, DevState *st, uint64_t max_chunks, 
                                                         r.chunk_top);
         count_launch();
     }
-    section_size_kernel<<<(r.F + 63) / 64, 64, 0, s>>>(r.occ_off, r.chunk_off, r.F, r.chunk_words, r.chunk_pos,
-                                                       r.mode, r.sec_bytes);
+    section_size_kernel<<<(r.F + 7) / 8, 256, 0, s>>>(r.occ_off, r.chunk_off, r.F, r.chunk_words, r.chunk_pos,
+                                                      r.mode, r.sec_bytes);
     count_launch();
 }
 
@@ -334,13 +323,14 @@ void launch_rans_decode(const uint8_t *sec, uint64_t sec_bytes, uint64_t n, uint
     if (nch == 0) return;
     table_kernel<<<1, 1024, 0, s>>>(sec, tabs, st);
     count_launch();
-    uint32_t blocks = (nch + kDecWarps - 1) / kDecWarps;
-    if (blocks > (uint32_t)num_sms * 4) blocks = (uint32_t)num_sms * 4;
     // chunks of up to 32768 symbols are staged in shared memory; larger ones are read in place
     const bool staged = chunk <= 32768;
-    const size_t smem = kM + 1024 + (staged ? (size_t)kDecWarps * ((128 + 2 * (size_t)chunk + 15) & ~(size_t)15) : 0);
+    const uint32_t warps = staged ? ransdec::warps_per_cta(chunk) : ransdec::kMaxWarps;
+    uint32_t blocks = (nch + warps - 1) / warps;
+    if (blocks > (uint32_t)num_sms * 8) blocks = (uint32_t)num_sms * 8;
+    const size_t smem = staged ? ransdec::smem_bytes(chunk, warps) : (size_t)ransdec::kTabWords * 4;
     cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    decode_kernel<<<blocks, 32 * kDecWarps, smem, s>>>(sec, sec_bytes, n, nch, chunk, out, st, staged, tabs);
+    decode_kernel<<<blocks, 32 * warps, smem, s>>>(sec, sec_bytes, n, nch, chunk, out, st, staged, tabs);
     count_launch();
 }
 

@@ -157,7 +157,7 @@ class QuantParams:
     """Quantisation / entropy parameters (Sec. 3.4): group id per channel, one
     step per group, rounding offset tau, RLGR block size, rANS chunk size."""
 
-    def __init__(self, groups, steps, tau=0.5, rlgr_block=512, rans_chunk=16384):
+    def __init__(self, groups, steps, tau=0.5, rlgr_block=512, rans_chunk=4096):
         self.groups = np.ascontiguousarray(np.asarray(groups, dtype=np.uint8).reshape(-1))
         self.steps = np.ascontiguousarray(np.asarray(steps, dtype=np.float64).reshape(-1))
         self.tau = float(tau)
@@ -181,7 +181,7 @@ class QuantParams:
         return q
 
 
-def geometry_only(rans_chunk=16384):
+def geometry_only(rans_chunk=4096):
     return QuantParams(np.zeros(0, np.uint8), [1.0], rans_chunk=rans_chunk)
 
 
@@ -327,7 +327,7 @@ def octree_decode(occ: torch.Tensor, J: int, level_sizes):
     return codes[:nv]
 
 
-def occupancy_section_encode(data: torch.Tensor, rans_chunk=16384):
+def occupancy_section_encode(data: torch.Tensor, rans_chunk=4096):
     n = data.numel()
     cap = 64 + 2 * n + 1024 + (n // 32 + 1) * 256
     out = torch.empty(cap, dtype=torch.uint8, device=data.device)
