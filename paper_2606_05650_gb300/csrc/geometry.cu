@@ -270,13 +270,43 @@ __global__ void __launch_bounds__(kThreads) occ_down_kernel(const uint64_t *__re
 }
 
 // ------------------------------------------------------- octree decode ---
+// Exclusive prefix of the popcounts of the occupancy bytes (children before
+// each node, Algorithm 3): CTA chunks of whole 16-byte groups, each thread
+// handling 16 consecutive bytes per step (one vector load when aligned).
+constexpr uint32_t kPopcVec = 16;
+
+__device__ __forceinline__ void load16(const uint8_t *p, uint64_t i, uint64_t e, bool vec, uint32_t w[4])
+{
+    if (vec && i + kPopcVec <= e) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(p + i);
+        w[0] = v.x;
+        w[1] = v.y;
+        w[2] = v.z;
+        w[3] = v.w;
+        return;
+    }
+    for (int k = 0; k < 4; ++k) {
+        uint32_t x = 0;
+        for (int b = 0; b < 4; ++b) {
+            const uint64_t j = i + 4 * k + b;
+            if (j < e) x |= (uint32_t)p[j] << (8 * b);
+        }
+        w[k] = x;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) popc_up_kernel(const uint8_t *__restrict__ occ, uint64_t n,
                                                            uint64_t chunk, uint32_t *partials)
 {
     uint64_t b = (uint64_t)blockIdx.x * chunk, e = b + chunk;
     if (e > n) e = n;
+    const bool vec = ((uintptr_t)occ & 15) == 0;
     uint32_t c = 0;
-    for (uint64_t i = b + threadIdx.x; i < e; i += kThreads) c += __popc(occ[i]);
+    for (uint64_t i = b + (uint64_t)threadIdx.x * kPopcVec; i < e; i += (uint64_t)kThreads * kPopcVec) {
+        uint32_t w[4];
+        load16(occ, i, e, vec, w);
+        c += __popc(w[0]) + __popc(w[1]) + __popc(w[2]) + __popc(w[3]);
+    }
     __shared__ uint32_t sh[33];
     uint32_t tot;
     block_exclusive_sum<uint32_t>(c, sh, &tot);
@@ -290,13 +320,30 @@ __global__ void __launch_bounds__(kThreads) popc_down_kernel(const uint8_t *__re
     __shared__ uint32_t sh[33];
     uint64_t b = (uint64_t)blockIdx.x * chunk, e = b + chunk;
     if (e > n) e = n;
+    const bool vec = ((uintptr_t)occ & 15) == 0 && ((uintptr_t)pref & 15) == 0;
     uint32_t run = partials[blockIdx.x];
-    for (uint64_t t0 = b; t0 < e; t0 += kThreads) {
-        uint64_t i = t0 + threadIdx.x;
-        uint32_t c = (i < e) ? __popc(occ[i]) : 0u;
+    for (uint64_t t0 = b; t0 < e; t0 += (uint64_t)kThreads * kPopcVec) {
+        const uint64_t i = t0 + (uint64_t)threadIdx.x * kPopcVec;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (i < e) load16(occ, i, e, vec, w);
+        uint32_t pc[16];
+        uint32_t c = 0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            pc[k] = c;
+            c += __popc((w[k >> 2] >> (8 * (k & 3))) & 0xFFu);
+        }
         uint32_t tot;
-        uint32_t pre = block_exclusive_sum<uint32_t>(c, sh, &tot);
-        if (i < e) pref[i] = run + pre;
+        const uint32_t pre = run + block_exclusive_sum<uint32_t>(c, sh, &tot);
+        if (vec && i + kPopcVec <= e) {
+            uint4 *o = reinterpret_cast<uint4 *>(pref + i);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                o[q] = make_uint4(pre + pc[4 * q], pre + pc[4 * q + 1], pre + pc[4 * q + 2], pre + pc[4 * q + 3]);
+        } else {
+            for (int k = 0; k < 16; ++k)
+                if (i + k < e) pref[i + k] = pre + pc[k];
+        }
         run += tot;
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) pref[n] = partials[gridDim.x];
@@ -436,6 +483,16 @@ Chunks chunks_for(uint64_t n, int num_sms)
     return c;
 }
 
+// CTA chunks of whole 16-byte groups (so vector loads stay aligned), at most 2 per SM
+Chunks popc_chunks(uint64_t n, int num_sms)
+{
+    Chunks c = chunks_for(n, num_sms);
+    c.chunk = (c.chunk + kPopcVec - 1) / kPopcVec * kPopcVec;
+    c.P = (uint32_t)((n + c.chunk - 1) / c.chunk);
+    if (c.P == 0) c.P = 1;
+    return c;
+}
+
 uint32_t occ_x(uint32_t F, int num_sms)
 {
     uint32_t X = (uint32_t)(num_sms * 8) / F;
@@ -504,7 +561,7 @@ void launch_octree_decode(const uint8_t *occ, uint64_t n_occ, uint32_t J, const 
                           DevState *st, int num_sms, cudaStream_t s)
 {
     if (h_level_sizes[0] == 0) return;
-    Chunks c = chunks_for(n_occ, num_sms);
+    Chunks c = popc_chunks(n_occ, num_sms);
     popc_up_kernel<<<c.P, kThreads, 0, s>>>(occ, n_occ, c.chunk, partials);
     count_launch();
     scan_total_kernel<<<1, 1024, 0, s>>>(partials, c.P);
@@ -541,7 +598,7 @@ void launch_octree_decode(const uint8_t *occ, uint64_t n_occ, uint32_t J, const 
 void launch_popc_scan(const uint8_t *occ, uint64_t n, uint32_t *pref, uint32_t *partials, int num_sms,
                       cudaStream_t s)
 {
-    Chunks c = chunks_for(n, num_sms);
+    Chunks c = popc_chunks(n, num_sms);
     popc_up_kernel<<<c.P, kThreads, 0, s>>>(occ, n, c.chunk, partials);
     count_launch();
     scan_total_kernel<<<1, 1024, 0, s>>>(partials, c.P);
