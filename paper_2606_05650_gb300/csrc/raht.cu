@@ -375,6 +375,24 @@ __device__ __forceinline__ double add_rn(double x, double y) { return __dadd_rn(
 __device__ __forceinline__ float div_rn(float x, float y) { return __fdiv_rn(x, y); }
 __device__ __forceinline__ double div_rn(double x, double y) { return __ddiv_rn(x, y); }
 
+// asynchronous global -> shared copy of N bytes (4, 8 or 16; both addresses N-aligned)
+template <int N>
+__device__ __forceinline__ void cp_async_vec(void *smem, const void *gmem)
+{
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    if (N == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+    else if (N == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Eq. (1): forward (a*y0 + b*y1, a*y1 - b*y0); inverse (transposed) (a*y0 - b*y1, b*y0 + a*y1).
 // Each product and sum rounds once (no contraction), in the scalar type.
 template <bool INV>
@@ -471,8 +489,6 @@ __device__ inline XformSmem<S> carve_xform(unsigned char *raw, uint32_t T)
     return X;
 }
 
-constexpr int kUnroll = 4;  // rows loaded per thread before they are used
-
 // butterfly k of a tile: FP32 coefficients come from the plan; FP64 ones are
 // computed here from the integer weights, a = sqrt(w0/(w0+w1)), b = sqrt(w1/(w0+w1))
 __device__ __forceinline__ void load_coeffs(const RahtPlanDev &p, uint64_t at, float *ab)
@@ -541,63 +557,61 @@ __device__ void xform_tile(const XformArgs<S> &A, const XformSmem<S> &X, TileSch
         const uint32_t slot = tid / L, lane = tid - slot * L;
         const uint32_t c = c0 + lane * VEC;
         const bool act = slot < slots;
-        // ---- load rows: kUnroll independent loads in flight per thread
+        // ---- load rows: every element of the tile is copied by an asynchronous
+        // copy (no registers held, all of them in flight at once); the thread
+        // that copied an element then finishes it in place: the average of a
+        // voxel holding several points (forward gather) or the quantise ->
+        // dequantise of a coefficient (inverse with QDQ)
         if (act) {
-            for (uint32_t ib = slot; ib < m; ib += kUnroll * slots) {
-                V v[kUnroll];
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    const uint32_t i = ib + (uint32_t)u * slots;
-                    if (i >= m) break;
-                    const uint64_t j = j0 + i;
-                    if (!INV) {
-                        if (gather) {
-                            const uint32_t s0 = X.s_src[i];
-                            const uint32_t row = staged ? X.s_vals[s0 - g0] : io.vals[s0];
-                            const S *base = io.attr[io.frame_shift < 64 ? X.s_frame[i] : 0];
-                            v[u] = Vec<S, VEC>::ld(base + (uint64_t)row * C + c);
-                        } else if (q == 0) {
-                            v[u] = Vec<S, VEC>::ld(io.in + j * C + c);
-                        } else {
-                            v[u] = Vec<S, VEC>::ld(io.pool + ((uint64_t)ps.surv_off + j) * C + c);
-                        }
+            for (uint32_t i = slot; i < m; i += slots) {
+                const uint64_t j = j0 + i;
+                const S *src;
+                if (!INV) {
+                    if (gather) {
+                        const uint32_t s0 = X.s_src[i];
+                        const uint32_t row = staged ? X.s_vals[s0 - g0] : io.vals[s0];
+                        src = io.attr[io.frame_shift < 64 ? X.s_frame[i] : 0] + (uint64_t)row * C + c;
+                    } else if (q == 0) {
+                        src = io.in + j * C + c;
                     } else {
-                        const uint32_t d = X.s_src[i];
-                        if (d & kCarry) {
-                            v[u] = Vec<S, VEC>::ld(io.pool + ((uint64_t)nx.surv_off + (d & ~kCarry)) * C + c);
-                        } else {
-                            v[u] = Vec<S, VEC>::ld(io.Y + (uint64_t)d * C + c);
-                            if (QDQ) {
-                                S *pv = reinterpret_cast<S *>(&v[u]);
-#pragma unroll
-                                for (int e = 0; e < VEC; ++e)
-                                    pv[e] = qdq(pv[e], io.inv_step[c + e], io.step[c + e], io.tau);
-                            }
-                        }
+                        src = io.pool + ((uint64_t)ps.surv_off + j) * C + c;
                     }
+                } else {
+                    const uint32_t d = X.s_src[i];
+                    src = (d & kCarry) ? io.pool + ((uint64_t)nx.surv_off + (d & ~kCarry)) * C + c
+                                       : io.Y + (uint64_t)d * C + c;
                 }
+                cp_async_vec<sizeof(V)>(X.rows + (uint64_t)i * Cg + lane * VEC, src);
+            }
+        }
+        cp_async_commit_wait_all();
+        if (act && ((GATHER && gather) || QDQ)) {
+            for (uint32_t i = slot; i < m; i += slots) {
+                S *pr = X.rows + (uint64_t)i * Cg + lane * VEC;
+                if (!INV) {
+                    const uint32_t s0 = X.s_src[i], s1 = X.s_src[i + 1];
+                    if (s1 - s0 > 1) {  // voxels holding several points: average in input order
+                        V acc = Vec<S, VEC>::ld(pr);
+                        S *pa = reinterpret_cast<S *>(&acc);
+                        const S *base = io.attr[io.frame_shift < 64 ? X.s_frame[i] : 0];
+                        for (uint32_t g = s0 + 1; g < s1; ++g) {
+                            const uint32_t row = staged ? X.s_vals[g - g0] : io.vals[g];
+                            V xv = Vec<S, VEC>::ld(base + (uint64_t)row * C + c);
+                            const S *px = reinterpret_cast<const S *>(&xv);
 #pragma unroll
-                for (int u = 0; u < kUnroll; ++u) {
-                    const uint32_t i = ib + (uint32_t)u * slots;
-                    if (i >= m) break;
-                    if (gather) {  // voxels holding several points: average in input order
-                        const uint32_t s0 = X.s_src[i], s1 = X.s_src[i + 1];
-                        if (s1 - s0 > 1) {
-                            S *pa = reinterpret_cast<S *>(&v[u]);
-                            const S *base = io.attr[io.frame_shift < 64 ? X.s_frame[i] : 0];
-                            for (uint32_t g = s0 + 1; g < s1; ++g) {
-                                const uint32_t row = staged ? X.s_vals[g - g0] : io.vals[g];
-                                V x = Vec<S, VEC>::ld(base + (uint64_t)row * C + c);
-                                const S *px = reinterpret_cast<const S *>(&x);
-#pragma unroll
-                                for (int e = 0; e < VEC; ++e) pa[e] = add_rn(pa[e], px[e]);
-                            }
-                            const S cnt = (S)(s1 - s0);
-#pragma unroll
-                            for (int e = 0; e < VEC; ++e) pa[e] = div_rn(pa[e], cnt);
+                            for (int e = 0; e < VEC; ++e) pa[e] = add_rn(pa[e], px[e]);
                         }
+                        const S cnt = (S)(s1 - s0);
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) pa[e] = div_rn(pa[e], cnt);
+                        Vec<S, VEC>::st(pr, acc);
                     }
-                    Vec<S, VEC>::st(X.rows + (uint64_t)i * Cg + lane * VEC, v[u]);
+                } else if (QDQ && !(X.s_src[i] & kCarry)) {
+                    V v = Vec<S, VEC>::ld(pr);
+                    S *pv = reinterpret_cast<S *>(&v);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) pv[e] = qdq(pv[e], io.inv_step[c + e], io.step[c + e], io.tau);
+                    Vec<S, VEC>::st(pr, v);
                 }
             }
         }
