@@ -401,14 +401,16 @@ __global__ void occ_copy_kernel(HdrParams hp, OccCopyArgs a, const StreamInfo *s
         const uint8_t *slot = a.slots + gc * a.slot_bytes;
         const uint32_t w = a.chunk_words[gc], top = a.chunk_top[gc];
         uint8_t *dst = sec + a.chunk_pos[gc];
-        const uint32_t bytes = (uint32_t)((128 + 2 * (uint64_t)w + 3) & ~3ull);
-        for (uint32_t i = threadIdx.x; i < bytes; i += blockDim.x) {
-            uint8_t v;
-            if (i < 128) v = slot[i];
-            else if (i < 128 + 2 * w) v = slot[128 + 2 * top + (i - 128)];
-            else v = 0;
-            dst[i] = v;
-        }
+        // states: 32 words; renormalisation words: 16-bit units (slot and
+        // destination are both 2-aligned there); then zero padding to 4 bytes
+        const uint32_t *s32 = reinterpret_cast<const uint32_t *>(slot);
+        uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
+        for (uint32_t i = threadIdx.x; i < 32; i += blockDim.x) d32[i] = s32[i];
+        const uint16_t *s16 = reinterpret_cast<const uint16_t *>(slot + 128 + 2 * (uint64_t)top);
+        uint16_t *d16 = reinterpret_cast<uint16_t *>(dst + 128);
+#pragma unroll 4
+        for (uint32_t i = threadIdx.x; i < w; i += blockDim.x) d16[i] = s16[i];
+        if (threadIdx.x == 0 && (w & 1)) d16[w] = 0;
     }
     if (tid == 0) {  // tail padding of the section
         uint64_t end = nch ? (a.chunk_pos[c0 + nch - 1] + ((128 + 2 * (uint64_t)a.chunk_words[c0 + nch - 1] + 3) & ~3ull)) : table;
@@ -446,11 +448,25 @@ __global__ void attr_copy_kernel(HdrParams hp, AttrCopyArgs a, const StreamInfo 
     const uint64_t base = a.block_off[b0];
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t wid = tid >> 5, nwarps = nt >> 5;
-    for (uint64_t k = wid; k < nblk; k += nwarps) {
-        const uint32_t w = a.block_words[b0 + k];
-        const uint32_t *src = a.slots + (b0 + k) * a.slot_words;
-        uint32_t *dst = pay + (a.block_off[b0 + k] - base);
-        for (uint32_t i = lane; i < w; i += 32) dst[i] = src[i];
+    // a warp takes 32 consecutive block streams: their sizes and offsets in one
+    // load, then the streams one after another (their loads independent)
+    for (uint64_t k0 = wid * 32; k0 < nblk; k0 += nwarps * 32) {
+        const uint64_t k = k0 + lane;
+        uint32_t wl = 0;
+        uint64_t ol = 0;
+        if (k < nblk) {
+            wl = a.block_words[b0 + k];
+            ol = a.block_off[b0 + k] - base;
+        }
+        const uint32_t cnt = (nblk - k0) < 32 ? (uint32_t)(nblk - k0) : 32u;
+        for (uint32_t j = 0; j < cnt; ++j) {
+            const uint32_t w = __shfl_sync(0xFFFFFFFFu, wl, j);
+            const uint64_t o = __shfl_sync(0xFFFFFFFFu, ol, j);
+            const uint32_t *src = a.slots + (b0 + k0 + j) * a.slot_words;
+            uint32_t *dst = pay + o;
+#pragma unroll 4
+            for (uint32_t i = lane; i < w; i += 32) dst[i] = src[i];
+        }
     }
     const uint64_t used = 8 + 4 * nblk + 4 * (a.block_off[b0 + nblk] - base);
     if (tid == 0 && used < x.attr) wr32(reinterpret_cast<uint8_t *>(sec) + used, 0);
@@ -811,12 +827,12 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
         count_launch();
         OccCopyArgs oa{L.occ, L.occ_off, L.mode, L.chunk_off, L.freq, L.chunk_words, L.chunk_top, L.chunk_pos,
                        L.chunk_slots, rans_chunk_slot_bytes(q->rans_chunk)};
-        occ_copy_kernel<<<dim3(std::max<uint32_t>(1, (uint32_t)sms * 2 / (F * R)), F * R), 256, 0, s>>>(hpar, oa, L.si,
+        occ_copy_kernel<<<dim3(std::max<uint32_t>(1, (uint32_t)sms * 4 / (F * R)), F * R), 256, 0, s>>>(hpar, oa, L.si,
                                                                                                       dst, rq.out);
         count_launch();
         if (C) {
             AttrCopyArgs aa{L.vstart, L.blk_off, L.block_off, L.block_words, L.slots, L.slot_words};
-            attr_copy_kernel<<<dim3(std::max<uint32_t>(1, (uint32_t)sms * 4 / (F * R)), F * R), 256, 0, s>>>(
+            attr_copy_kernel<<<dim3(std::max<uint32_t>(1, (uint32_t)sms * 8 / (F * R)), F * R), 256, 0, s>>>(
                 hpar, aa, L.si, dst, rq.out);
             count_launch();
         }

@@ -18,6 +18,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kKeysPerThread = 8;
 constexpr int kTile = kThreads * kKeysPerThread;  // 2048
 constexpr int kRadix = 256;
+constexpr int kCtasPerSm = 4;  // downsweep CTAs resident per SM (registers capped to fit)
 
 struct SortGeom {
     uint32_t P;       // CTAs
@@ -28,7 +29,7 @@ SortGeom sort_geom(uint64_t n, int num_sms)
 {
     SortGeom g;
     uint64_t tiles = (n + kTile - 1) / kTile;
-    uint64_t pmax = (uint64_t)num_sms * 2;
+    uint64_t pmax = (uint64_t)num_sms * kCtasPerSm;
     g.P = (uint32_t)(tiles < 1 ? 1 : (tiles < pmax ? tiles : pmax));
     g.chunk = (n + g.P - 1) / g.P;
     return g;
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(256) scan_cols_kernel(uint32_t *hist, uint32_t
     if (lane == 0) hist[(uint64_t)kRadix * P + d] = run;
 }
 
-__global__ void __launch_bounds__(kThreads) downsweep_kernel(const uint64_t *__restrict__ keys,
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) downsweep_kernel(const uint64_t *__restrict__ keys,
                                                              const uint32_t *__restrict__ vals, uint64_t n,
                                                              uint32_t shift, uint64_t chunk,
                                                              const uint32_t *__restrict__ hist,
