@@ -57,16 +57,19 @@ __device__ __forceinline__ uint32_t seq_end(const RahtPlanDev &p, const RahtPass
     return q == 0 ? (uint32_t)(j + 1) : p.endseq[ps.seq_off + j];
 }
 
+constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
 template <int TMAX>
 struct PreludeSmem {
     static constexpr int kWords = (TMAX + 1 + 31) / 32;  // bit words covering positions 0..T
+    static constexpr int kLog = ilog2(TMAX) + 1;          // range-maximum levels 0 .. log2(TMAX)
     uint8_t g[TMAX + 1];
+    uint8_t mx[kLog][TMAX + 1];  // mx[k][x] = max g[x .. x + 2^k) (k >= 1; level 0 is g)
     uint8_t inl[TMAX];        // gap i is processed inside the tile
     uint32_t p[TMAX + 1];
     uint32_t e[TMAX];
     uint16_t prv[TMAX];
     uint16_t nxt[TMAX];
-    uint32_t lvl[kRounds + 1][kWords];  // bit i of lvl[L] : g[i] >= L
     uint32_t surv[kWords];    // survivors (start a maximal in-tile subtree)
     uint32_t carry[kWords];   // survivors carried to the next pass
     uint32_t cpre[kWords];    // exclusive prefix of carry popcounts
@@ -74,18 +77,6 @@ struct PreludeSmem {
     uint32_t lvl_off[kRounds + 1];
     uint32_t scan[33];
 };
-
-// highest set bit of mask at a position < i, or -1
-__device__ __forceinline__ int prev_set(const uint32_t *mask, uint32_t i)
-{
-    int w = (int)(i >> 5);
-    uint32_t b = mask[w] & ((1u << (i & 31)) - 1u);
-    while (!b) {
-        if (--w < 0) return -1;
-        b = mask[w];
-    }
-    return w * 32 + 31 - __clz(b);
-}
 
 // lowest set bit of mask at a position in (i, lim], or -1
 __device__ __forceinline__ int next_set(const uint32_t *mask, uint32_t i, uint32_t lim)
@@ -119,28 +110,38 @@ __device__ void prelude_tile(const PreludeArgs &a, PreludeSmem<TMAX> &S, int q, 
     }
     for (int i = tid; i <= kRounds; i += kThreads) S.lvl_cnt[i] = 0;
     __syncthreads();
-    // level masks by ballots: one warp per 32 positions
-    for (uint32_t w = wid; w < W; w += kThreads / 32) {
-        const uint32_t i = w * 32 + lane;
-        const uint32_t gi = (i <= m) ? S.g[i] : 0u;
-        for (int L = 1; L <= kRounds; ++L) {
-            const uint32_t b = __ballot_sync(0xFFFFFFFFu, gi >= (uint32_t)L);
-            if (lane == 0) S.lvl[L][w] = b;
+    // range maxima of the gap levels over power-of-two windows
+    constexpr int K = PreludeSmem<TMAX>::kLog;
+    for (int k = 1; k < K; ++k) {
+        const uint32_t half = 1u << (k - 1), span = 1u << k;
+        const uint8_t *src = (k == 1) ? S.g : S.mx[k - 1];
+        for (uint32_t x = tid; x + span <= m + 1; x += kThreads) {
+            const uint8_t u = src[x], v = src[x + half];
+            S.mx[k][x] = u > v ? u : v;
         }
+        __syncthreads();
     }
-    __syncthreads();
-    // nearest larger gap on each side (the tile's boundary gaps g[0], g[m] count)
+    // nearest larger gap on each side (the tile's boundary gaps g[0], g[m]
+    // count), by binary lifting over the range maxima
     for (uint32_t i = tid; i < m; i += kThreads) {
         uint8_t f = 0;
         if (i > 0) {
             const uint32_t gi = S.g[i];  // < kInfLevel whenever a larger gap exists
             if (gi < (uint32_t)kRounds) {
-                const int l = prev_set(S.lvl[gi + 1], i);
-                const int r = (l >= 0) ? next_set(S.lvl[gi + 1], i, m) : -1;
-                if (l >= 0 && r >= 0) {
+                uint32_t lp = i;  // [lp, i) holds no larger gap
+                for (int k = K - 1; k >= 0; --k) {
+                    const uint32_t st = 1u << k;
+                    if (lp >= st && (k ? S.mx[k][lp - st] : S.g[lp - st]) <= gi) lp -= st;
+                }
+                uint32_t rp = i + 1;  // (i, rp) holds no larger gap
+                for (int k = K - 1; k >= 0; --k) {
+                    const uint32_t st = 1u << k;
+                    if (rp + st <= m + 1 && (k ? S.mx[k][rp] : S.g[rp]) <= gi) rp += st;
+                }
+                if (lp > 0 && rp <= m) {
                     f = 1;
-                    S.prv[i] = (uint16_t)l;
-                    S.nxt[i] = (uint16_t)r;
+                    S.prv[i] = (uint16_t)(lp - 1);
+                    S.nxt[i] = (uint16_t)rp;
                     atomicAdd(&S.lvl_cnt[gi], 1u);
                 }
             }
