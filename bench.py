@@ -34,6 +34,15 @@ UNIT = "frames/s"
 N_GAUSS = 1_000_000
 C = 56
 J = 16
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per frame of this
+# workload from one ncu capture of each kernel (2 frames, scaled per frame;
+# summaries under profiles/), with the SHA-1 of the kernel's source file at
+# capture time: reported only while that file is unchanged.
+TRAFFIC = {
+    "rlgr_decode": (251.08e6, "csrc/rlgr.cu", "a2464437a7fc834d0f6afd67e96a6931e0f937b6"),
+    "rlgr_encode": (279.05e6, "csrc/rlgr.cu", "a2464437a7fc834d0f6afd67e96a6931e0f937b6"),
+    "raht_forward_pass0": (533.94e6, "csrc/raht.cu", "11f865c9e617aa1612fc50d66b8628c8e5120d55"),
+}
 REF_SAMPLE = 0.125  # reference arm: each process codes the first 1/8 of a 1M-Gaussian frame per step
 
 
@@ -235,6 +244,23 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def measured_traffic(kernel, frames_per_launch):
+    """Per-launch DRAM traffic from the ncu capture, or None once the kernel's source changed."""
+    import hashlib
+    ent = TRAFFIC.get(kernel)
+    if ent is None:
+        return None
+    per_frame, rel, sha = ent
+    path = os.path.join(ROOT, "paper_2606_05650_gb300", rel)
+    try:
+        with open(path, "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != sha:
+                return None
+    except OSError:
+        return None
+    return int(per_frame * frames_per_launch)
+
+
 def roofline(stages, frames, nv_frames, stream_bytes, steps, F, hbm, src):
     """Dominant kernel of the step with its algorithmic bytes per launch."""
     n_in = sum(p.shape[0] for p, _ in frames)
@@ -265,7 +291,8 @@ def roofline(stages, frames, nv_frames, stream_bytes, steps, F, hbm, src):
     ach = bytes_per_launch / (avg_ms / 1e3) / 1e9
     return {"kernel": best, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(ach / hbm, 4), "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)",
-            "traffic": None, "bytes_per_launch": int(bytes_per_launch), "avg_launch_ms": round(avg_ms, 4),
+            "traffic": measured_traffic(best, F / launches_per_step), "bytes_per_launch": int(bytes_per_launch),
+            "avg_launch_ms": round(avg_ms, 4),
             "all": {k: {"ms_per_launch": round(stages[k][0] / stages[k][1], 4),
                         "GBs": round(alg[k] / (stages[k][1] / steps) / (stages[k][0] / stages[k][1] / 1e3) / 1e9, 1),
                         "frac": round(alg[k] / (stages[k][1] / steps) / (stages[k][0] / stages[k][1] / 1e3) / 1e9 / hbm, 4)}
