@@ -55,8 +55,13 @@ def parse():
     ap.add_argument("--frames", type=int, default=8, help="frames per rank per step")
     ap.add_argument("--block", type=int, default=512, help="RLGR block size")
     ap.add_argument("--no-extras", action="store_true", help="skip plain-path, e2e and CPU-baseline legs")
-    ap.add_argument("--workload", default="headline", choices=["headline", "ladder"],
-                    help="ladder: 64 frames of 50k-2M Gaussians x 5 rungs, batched vs plain (separate JSON line)")
+    ap.add_argument("--workload", default="headline", choices=["headline", "ladder", "sequence", "pointcloud",
+                                                                 "blocksweep"],
+                    help="other workloads, each printing its own JSON line: ladder (64 frames of 50k-2M Gaussians x "
+                         "5 rungs, batched vs plain), sequence (300 frames of ~250k Gaussians, 3 steps), pointcloud "
+                         "(150 frames of ~1M points, depth 10, YCbCr, 5 steps), blocksweep (RLGR block size)")
+    ap.add_argument("--seq-frames", type=int, default=0, help="frames of the sequence / point-cloud workloads "
+                                                              "(default: 300 / 150)")
     return ap.parse_args()
 
 
@@ -568,12 +573,164 @@ def run_ladder(args):
     print(json.dumps(line), flush=True)
 
 
+def _timed_calls(torch, stream, fn, reps):
+    """Per-call device times (ms) of fn() on the stream, after one warm-up call."""
+    fn()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    ev[0].record(stream)
+    for k in range(reps):
+        fn(k)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    return [ev[k].elapsed_time(ev[k + 1]) for k in range(reps)]
+
+
+def _gen_pc_frame(t):
+    from paper_2606_05650_gb300 import synthetic as syn
+    return syn.capsule_humanoids_frame(11, t, 1_000_000)
+
+
+def _gen_seq_frame(t):
+    from paper_2606_05650_gb300 import synthetic as syn
+    return syn.DynamicScene(2000).frame(t)
+
+
+def _gen_frames(fn, count):
+    """Frames generated on the host cores by a spawned pool (before any GPU work)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(max(1, min(os.cpu_count() or 1, 16))) as pool:
+        return pool.map(fn, range(count), chunksize=1)
+
+
+def run_sequence(args, pointcloud=False):
+    """A dynamic sequence coded frame by frame (intra only).  3DGS: 300 frames
+    of ~250k Gaussians (+-10%), depth 16, 56 channels, steps x {1, 2, 4};
+    point cloud: 150 frames of ~1M points on two capsule humanoids, depth 10,
+    YCbCr, steps {0.025 ... 0.4}.  Reports per-frame encode and decode latency
+    (p50/p99) of the plain path, the batched throughput over all frames, and
+    for the point cloud the attribute PSNR per step."""
+    import numpy as np
+    Fn = args.seq_frames or (150 if pointcloud else 300)
+    host_frames = _gen_frames(_gen_pc_frame if pointcloud else _gen_seq_frame, Fn)
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_05650_gb300 import gsnfs as G, synthetic as syn
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    if pointcloud:
+        Jd, C = 10, 3
+        qps = [G.QuantParams(np.zeros(3, np.uint8), [s]) for s in (0.025, 0.05, 0.1, 0.2, 0.4)]
+    else:
+        Jd, C = 16, 56
+        qps = [G.QuantParams(syn.gs_channel_groups(), np.array(syn.GS_BASE_STEPS) * m) for m in (1.0, 2.0, 4.0)]
+    P, A, n_tot = [], [], 0
+    for p, a in host_frames:
+        P.append(torch.from_numpy(p).to(dev))
+        A.append(torch.from_numpy(a).to(dev))
+        n_tot += p.shape[0]
+    del host_frames
+    nmax = max(int(p.shape[0]) for p in P)
+    buf = torch.empty(G.max_bitstream_bytes(nmax, Jd, qps[0]), dtype=torch.uint8, device=dev)
+    legs = []
+    for qi, qp in enumerate(qps):
+        enc, dec, sizes = [], [], []
+        for t in range(Fn):
+            def e(_=0):
+                return G.encode_frame(P[t], A[t], Jd, qp, out=buf)
+            enc += _timed_calls(torch, stream, e, 1)
+            bs, nv, _, _ = e()
+            sizes.append(int(bs.numel()))
+            dec += _timed_calls(torch, stream, lambda _=0: G.decode_frame(bs), 1)
+        leg = {"step_set": qi, "encode_ms_p50": round(float(np.percentile(enc, 50)), 3),
+               "encode_ms_p99": round(float(np.percentile(enc, 99)), 3),
+               "decode_ms_p50": round(float(np.percentile(dec, 50)), 3),
+               "decode_ms_p99": round(float(np.percentile(dec, 99)), 3),
+               "plain_encode_fps": round(1e3 / float(np.mean(enc)), 1),
+               "plain_decode_fps": round(1e3 / float(np.mean(dec)), 1),
+               "bytes_per_frame": int(np.mean(sizes)), "bits_per_point": round(8 * sum(sizes) / n_tot, 3)}
+        if pointcloud:  # attribute PSNR of the decoded frames against the voxel means (peak 1)
+            from oracle import oracle as orc
+            psnr = []
+            for t in range(min(Fn, 3)):
+                bs, nv, _, _ = G.encode_frame(P[t], A[t], Jd, qp, out=buf)
+                gp, ga = G.decode_frame(bs)
+                _, merged, *_ = orc.voxelize(P[t].cpu().numpy(), A[t].cpu().numpy(), Jd)
+                mse = ((ga.cpu().numpy().astype(np.float64) - merged) ** 2).mean(0)
+                psnr.append(10 * np.log10(1.0 / mse))
+            leg["psnr_ycbcr_db"] = [round(float(x), 2) for x in np.mean(psnr, 0)]
+            leg["step"] = float(qp.steps[0])
+        legs.append(leg)
+    # batched: all frames of the sequence, every step set as a rung, 64 frames per call
+    scales = [float(q.steps[0] / qps[0].steps[0]) for q in qps]
+    out = None
+    def batched(_=0):
+        nonlocal out
+        for f0 in range(0, Fn, 64):
+            out, offs = G.encode_batch(P[f0:f0 + 64], A[f0:f0 + 64], [Jd] * len(P[f0:f0 + 64]), scales, qps[0],
+                                       out=out)
+    ms = _timed_calls(torch, stream, batched, 2)
+    line = {"metric": ("point-cloud" if pointcloud else "3DGS sequence") + " per-frame codec (plain latency, batched "
+            "throughput)", "unit": "frames/s", "higher_is_better": True,
+            "value": round(Fn / (float(np.mean(ms)) / 1e3), 1), "dtype": "f32", "data": "synthetic",
+            "config": {"workload": (f"{Fn} frames of ~1M points on two capsule humanoids, depth 10, YCbCr" if pointcloud
+                                    else f"{Fn} dynamic 3DGS frames of ~250k Gaussians (+-10%), depth 16, 56 channels"),
+                       "points_total": n_tot, "step_sets": len(qps)},
+            "batched_all_steps_fps": round(Fn / (float(np.mean(ms)) / 1e3), 1),
+            "batched_gaussians_per_s": round(n_tot / (float(np.mean(ms)) / 1e3), 0), "plain": legs}
+    print(json.dumps(line), flush=True)
+
+
+def run_blocksweep(args):
+    """RLGR block size B against stream size and codec time (8 frames of 1M
+    Gaussians, batched encode + decode)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_05650_gb300 import gsnfs as G, synthetic as syn
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    frames = make_frames(0, args.frames)
+    P = [torch.from_numpy(p).to(dev) for p, _ in frames]
+    A = [torch.from_numpy(a).to(dev) for _, a in frames]
+    F = len(P)
+    res = []
+    for B in (256, 512, 1024, 2048, 4096, 8192):
+        qp = G.QuantParams(syn.gs_channel_groups(), syn.GS_BASE_STEPS, rlgr_block=B)
+        st = {"out": None}
+        G.profile_enable(True)
+        G.profile_read()
+
+        def rt(_=0):
+            st["out"], offs = G.encode_batch(P, A, [J] * F, [1.0], qp, out=st["out"])
+            st["offs"] = offs
+            G.decode_batch(st["out"], offs, C, F * N_GAUSS)
+        ms = _timed_calls(torch, stream, rt, 3)
+        stg = G.profile_read()
+        G.profile_enable(False)
+        per = lambda k: round(stg[k][0] / max(stg[k][1], 1), 4) if k in stg else None
+        res.append({"B": B, "round_trip_ms": round(float(np.mean(ms)), 3),
+                    "bytes_per_frame": int(st["offs"][-1]) // F,
+                    "rlgr_encode_ms": per("rlgr_encode"), "rlgr_decode_ms": per("rlgr_decode")})
+    print(json.dumps({"metric": "RLGR block size sweep", "unit": "ms per 8-frame round trip", "data": "synthetic",
+                      "config": {"workload": f"{F} dynamic 3DGS frames of {N_GAUSS} Gaussians, depth {J}, C = {C}"},
+                      "sweep": res}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "ladder":
         run_ladder(args)
+    elif args.workload in ("sequence", "pointcloud"):
+        run_sequence(args, pointcloud=args.workload == "pointcloud")
+    elif args.workload == "blocksweep":
+        run_blocksweep(args)
     else:
         run_gpu(args)
 

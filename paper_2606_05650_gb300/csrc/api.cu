@@ -501,8 +501,8 @@ struct EncLayout {
         *spart;
     uint16_t *freq;
     uint8_t *gap, *occ, *chunk_slots, *groups;
-    float *inv_step, *step, *Y, *pool;
-    double *steps_rg;
+    float *inv_step, *step, *Y, *pool, *center;
+    double *steps_rg, *dc;
     StreamInfo *si;
     RahtPlanDev plan;
     uint64_t occ_cap, max_chunks, jobs_bound, blocks_bound;
@@ -561,6 +561,8 @@ size_t carve_encode(Carve &cv, EncLayout &L, const EncodeReq &rq, int num_sms, b
     L.inv_step = cv.take<float>((uint64_t)R * C + 1);
     L.step = cv.take<float>((uint64_t)R * C + 1);
     L.steps_rg = cv.take<double>((uint64_t)R * 256);
+    L.center = cv.take<float>((uint64_t)F * (C ? C : 1));
+    L.dc = cv.take<double>((uint64_t)F * (C ? C : 1));
     L.groups = cv.take<uint8_t>(256);
     L.vstart = cv.take<uint32_t>(F + 1);
     L.lsz = cv.take<uint32_t>((uint64_t)F * 22);
@@ -785,18 +787,21 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
             stage_begin(s, kStPrelude);
             launch_raht_prelude(L.plan, L.gap, dst, nullptr, sms, s);
             stage_end(s, kStPrelude);
+            launch_frame_centres(L.attrp, L.poff, F, C, L.center, s);
             RahtIO io{};
             io.C = C;
             io.seg = L.seg;
             io.vals = svals;
             io.codes = L.codes;
             io.attr = L.attrp;
+            io.center = L.center;
             io.frame_shift = frame_shift;
             io.Y = L.Y;
             io.pool = L.pool;
             stage_begin(s, kStRahtFwd);
             launch_raht_forward(L.plan, io, N, sms, s);
             stage_end(s, kStRahtFwd);
+            launch_frame_dc(L.Y, L.vstart, F, C, L.center, L.steps_rg, L.groups, G, q->tau, L.dc, s);
             // a8 + a9: quantise + block RLGR for every rung
             launch_rlgr_offsets(L.vstart, F, q->rlgr_block, R, C, L.job_off, L.blk_off, s);
             RlgrJob j{};
@@ -813,6 +818,11 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
             j.blk_off = L.blk_off;
             j.slot_words = L.slot_words;
             j.overflow = L.overflow;
+            j.dc = L.dc;
+            j.steps_rg = L.steps_rg;
+            j.groups = L.groups;
+            j.G = G;
+            j.tau64 = q->tau;
             stage_begin(s, kStRlgrEnc);
             launch_rlgr_encode(j, L.job_off, L.jobs_bound, s);
             stage_end(s, kStRlgrEnc);

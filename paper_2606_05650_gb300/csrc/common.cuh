@@ -122,4 +122,13 @@ __device__ __forceinline__ int32_t quantize_f32(float y, float inv_step, float t
     return (y < 0.0f) ? -m : m;
 }
 
+// the quantiser of Sec. 3.4 in FP64: sign(y) floor(|y| / step + tau)
+__device__ __forceinline__ int32_t quantize_f64(double y, double step, double tau)
+{
+    double t = floor(__dadd_rn(__ddiv_rn(fabs(y), step), tau));
+    t = fmin(t, 1073741824.0);
+    const int32_t m = (int32_t)t;
+    return (y < 0.0) ? -m : m;
+}
+
 }  // namespace gsnfs

@@ -130,6 +130,7 @@ struct RahtIOT {  // S = float (codec) or double (FP64 instantiation of the same
     const uint32_t *vals;   // forward gather: local point index of sorted points
     const uint64_t *codes;  // forward gather: voxel codes (frame id) for the attr pointer
     const S *const *attr;   // forward gather: per-frame attribute pointers
+    const S *center;        // forward gather: per frame x C value subtracted from every voxel row, or null
     uint32_t frame_shift;
     S *Y;                   // coefficients nv x C
     S *out;                 // inverse output nv x C
@@ -180,7 +181,20 @@ struct RlgrJob {
     const uint64_t *blk_off;    // F + 1: first block of each frame (R x C x nb_f blocks per frame)
     uint32_t slot_words;        // words per slot (a block needing more sets *overflow)
     uint32_t *overflow;
+    const double *dc;           // per frame x C: each frame's DC in FP64, quantised in FP64 (or null: from Y)
+    const double *steps_rg;     // R x G FP64 steps (with dc)
+    const uint8_t *groups;      // C group ids (with dc)
+    uint32_t G;
+    double tau64;
 };
+// Per-frame channel centres: FP32 mean of the first (up to 1024) input rows
+// of each frame, summed in a fixed order.
+void launch_frame_centres(const float *const *attr, const uint64_t *poff, uint32_t F, uint32_t C, float *center,
+                          cudaStream_t s);
+// After a centred forward transform: each frame's DC in FP64 (centred DC +
+// sqrt(N_v) x centre), and in Y the rung-0 dequantised DC.
+void launch_frame_dc(float *Y, const uint32_t *vstart, uint32_t F, uint32_t C, const float *center,
+                     const double *steps_rg, const uint8_t *groups, uint32_t G, double tau, double *dc, cudaStream_t s);
 uint32_t rlgr_slot_words(uint32_t B, bool worst_case);
 void launch_rlgr_offsets(const uint32_t *vstart, uint32_t F, uint32_t B, uint32_t R, uint32_t C, uint64_t *job_off,
                          uint64_t *blk_off, cudaStream_t s);

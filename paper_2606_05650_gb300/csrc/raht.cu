@@ -591,20 +591,29 @@ __device__ void xform_tile(const XformArgs<S> &A, const XformSmem<S> &X, TileSch
                 S *pr = X.rows + (uint64_t)i * Cg + lane * VEC;
                 if (!INV) {
                     const uint32_t s0 = X.s_src[i], s1 = X.s_src[i + 1];
-                    if (s1 - s0 > 1) {  // voxels holding several points: average in input order
+                    const uint32_t fr = io.frame_shift < 64 ? X.s_frame[i] : 0u;
+                    const bool ctr_any = io.center != nullptr;
+                    if (s1 - s0 > 1 || ctr_any) {
                         V acc = Vec<S, VEC>::ld(pr);
                         S *pa = reinterpret_cast<S *>(&acc);
-                        const S *base = io.attr[io.frame_shift < 64 ? X.s_frame[i] : 0];
-                        for (uint32_t g = s0 + 1; g < s1; ++g) {
-                            const uint32_t row = staged ? X.s_vals[g - g0] : io.vals[g];
-                            V xv = Vec<S, VEC>::ld(base + (uint64_t)row * C + c);
-                            const S *px = reinterpret_cast<const S *>(&xv);
+                        if (s1 - s0 > 1) {  // voxels holding several points: average in input order
+                            const S *base = io.attr[fr];
+                            for (uint32_t g = s0 + 1; g < s1; ++g) {
+                                const uint32_t row = staged ? X.s_vals[g - g0] : io.vals[g];
+                                V xv = Vec<S, VEC>::ld(base + (uint64_t)row * C + c);
+                                const S *px = reinterpret_cast<const S *>(&xv);
 #pragma unroll
-                            for (int e = 0; e < VEC; ++e) pa[e] = add_rn(pa[e], px[e]);
+                                for (int e = 0; e < VEC; ++e) pa[e] = add_rn(pa[e], px[e]);
+                            }
+                            const S cnt = (S)(s1 - s0);
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e) pa[e] = div_rn(pa[e], cnt);
                         }
-                        const S cnt = (S)(s1 - s0);
+                        if (ctr_any) {  // centred rows keep the low-pass sums small (FP32 accuracy)
+                            const S *ctr = io.center + (uint64_t)fr * C + c;
 #pragma unroll
-                        for (int e = 0; e < VEC; ++e) pa[e] = div_rn(pa[e], cnt);
+                            for (int e = 0; e < VEC; ++e) pa[e] = add_rn(pa[e], -ctr[e]);
+                        }
                         Vec<S, VEC>::st(pr, acc);
                     }
                 } else if (QDQ && !(X.s_src[i] & kCarry)) {
@@ -856,5 +865,74 @@ template void launch_raht_forward<float>(const RahtPlanDev &, const RahtIOT<floa
 template void launch_raht_forward<double>(const RahtPlanDev &, const RahtIOT<double> &, uint64_t, int, cudaStream_t);
 template void launch_raht_inverse<float>(const RahtPlanDev &, const RahtIOT<float> &, uint64_t, int, cudaStream_t);
 template void launch_raht_inverse<double>(const RahtPlanDev &, const RahtIOT<double> &, uint64_t, int, cudaStream_t);
+
+// ---- centring of the forward transform ---------------------------------------
+// RAHT is linear with T 1 = sqrt(N_v) e_DC (a constant has no high pass), so
+// T (A - c 1) = T A - c sqrt(N_v) e_DC for any c: centring changes only the DC
+// and, in FP32, keeps the low-pass sums near the data's spread instead of its
+// mean (the high-pass coefficients of large nodes are differences of such sums).
+namespace {
+
+constexpr uint32_t kCentreRows = 1024;
+
+__global__ void __launch_bounds__(256) frame_centres_kernel(const float *const *attr, const uint64_t *poff,
+                                                            uint32_t C, float *center)
+{
+    __shared__ float part[256];
+    const uint32_t f = blockIdx.x;
+    const uint32_t lanes = blockDim.x / C;  // row phases
+    const uint32_t t = threadIdx.x, j = t / C, c = t - j * C;
+    const uint64_t n = poff[f + 1] - poff[f];
+    const uint32_t m = (uint32_t)(n < kCentreRows ? n : kCentreRows);
+    const float *a = attr[f];
+    float sum = 0.f;
+    if (j < lanes)
+        for (uint32_t r = j; r < m; r += lanes) sum = __fadd_rn(sum, a[(uint64_t)r * C + c]);
+    if (j < lanes) part[t] = sum;
+    __syncthreads();
+    if (j == 0) {
+        float tot = 0.f;
+        for (uint32_t q = 0; q < lanes; ++q) tot = __fadd_rn(tot, part[q * C + c]);
+        center[(uint64_t)f * C + c] = m ? __fdiv_rn(tot, (float)m) : 0.f;
+    }
+}
+
+__global__ void frame_dc_kernel(float *Y, const uint32_t *vstart, uint32_t C, const float *center,
+                                const double *steps_rg, const uint8_t *groups, uint32_t G, double tau, double *dc)
+{
+    const uint32_t f = blockIdx.x;
+    const uint32_t v0 = vstart[f], nv = vstart[f + 1] - v0;
+    for (uint32_t c = threadIdx.x; c < C; c += blockDim.x) {
+        if (nv == 0) {
+            dc[(uint64_t)f * C + c] = 0.0;
+            continue;
+        }
+        float *y = Y + (uint64_t)v0 * C + c;
+        const double d = __dadd_rn((double)*y, __dmul_rn(__dsqrt_rn((double)nv), (double)center[(uint64_t)f * C + c]));
+        dc[(uint64_t)f * C + c] = d;
+        const double st0 = steps_rg[groups[c]];  // rung 0
+        *y = (float)__dmul_rn((double)quantize_f64(d, st0, tau), st0);
+    }
+}
+
+}  // namespace
+
+void launch_frame_centres(const float *const *attr, const uint64_t *poff, uint32_t F, uint32_t C, float *center,
+                          cudaStream_t s)
+{
+    if (F == 0 || C == 0) return;
+    uint32_t lanes = 256 / C;
+    if (lanes < 1) lanes = 1;
+    frame_centres_kernel<<<F, lanes * C, 0, s>>>(attr, poff, C, center);
+    count_launch();
+}
+
+void launch_frame_dc(float *Y, const uint32_t *vstart, uint32_t F, uint32_t C, const float *center,
+                     const double *steps_rg, const uint8_t *groups, uint32_t G, double tau, double *dc, cudaStream_t s)
+{
+    if (F == 0 || C == 0) return;
+    frame_dc_kernel<<<F, 64, 0, s>>>(Y, vstart, C, center, steps_rg, groups, G, tau, dc);
+    count_launch();
+}
 
 }  // namespace gsnfs

@@ -255,7 +255,13 @@ __global__ void __launch_bounds__(1024) rlgr_encode_kernel(EncJobs E, const int3
         if (act && k * kChunkRows < me.len) {
             const uint32_t rows = (me.len - k * kChunkRows) < kChunkRows ? (me.len - k * kChunkRows) : kChunkRows;
             const uint32_t *cb = buf + (2 * jl + (k & 1)) * chunk_elems + c;
-            for (uint32_t i = 0; i < rows; ++i) {
+            uint32_t i0 = 0;
+            if (!FROM_INT && j.dc && k == 0 && me.b == 0) {  // the frame's DC: quantised from its FP64 value
+                st.code(bw, zz(quantize_f64(j.dc[(uint64_t)me.f * C + c], j.steps_rg[r * j.G + j.groups[c]],
+                                            j.tau64)));
+                i0 = 1;
+            }
+            for (uint32_t i = i0; i < rows; ++i) {
                 const uint32_t x = cb[i * C];
                 const int32_t q = FROM_INT ? (int32_t)x : quantize_f32(__uint_as_float(x), inv, j.tau);
                 st.code(bw, zz(q));

@@ -1,0 +1,41 @@
+"""Comparison of one GPU-written stream with the oracle, shared by the GPU
+parity tests: header and occupancy section byte-identical to the oracle
+encoder's; the oracle decoder reads the GPU stream back to the oracle's exact
+voxel set; quantisation indices equal the oracle's except inside the rounding
+zone (|y|/step + tau within 1e-4 of an integer), counted and below 1e-6 of all
+coefficients; the GPU decoder's output (if given) equals the oracle decoder's
+reading of the same stream within FP32 tolerance."""
+import numpy as np
+
+
+def compare_stream(orc, stream, pos, attr, J, groups, steps, tau, block, chunk, gpu_decoded=None):
+    host = np.ascontiguousarray(stream)
+    C = 0 if attr is None else attr.shape[1]
+    ref = orc.encode_frame(pos, attr if C else None, J, groups, steps, tau, block, chunk, with_coeffs=True)
+    refbs = ref["bitstream"]
+    hb = int.from_bytes(refbs[8:12].tobytes(), "little")
+    occb = int.from_bytes(refbs[72:80].tobytes(), "little")
+    assert np.array_equal(host[:72], refbs[:72]), "fixed header"
+    assert np.array_equal(host[88:hb + occb], refbs[88:hb + occb]), "header tables and occupancy section"
+    dec = orc.decode_frame(host)
+    assert np.array_equal(dec["codes"], ref["codes"]), "voxel set"
+    out = {"nv": int(ref["nv"]), "bytes": int(host.size), "disagree": 0, "dec": dec}
+    if C and ref["nv"]:
+        q_ref, y64 = ref["q"], ref["coeffs"]
+        st = np.asarray(steps, dtype=np.float64)[np.asarray(groups)]
+        dis = dec["q"] != q_ref
+        t = np.abs(y64) / st + tau
+        frac = t - np.floor(t)
+        zone = np.minimum(frac, 1 - frac) < 1e-4
+        assert not (dis & ~zone).any(), "index disagreement outside the rounding-boundary zone"
+        out["disagree"] = int(dis.sum())
+        assert dis.sum() <= 1e-6 * dis.size + (1 if dis.size < 1e6 else 0), dis.sum()
+    if gpu_decoded is not None:
+        gpos, gattr = gpu_decoded
+        assert np.array_equal(gpos, dec["pos"]), "decoded positions"
+        if C and ref["nv"]:
+            st = np.asarray(steps, dtype=np.float64)[np.asarray(groups)]
+            scale = np.sqrt((dec["attr"] ** 2).mean(0)) + st
+            err = np.abs(gattr.astype(np.float64) - dec["attr"]) / scale
+            assert err.max() < 1e-4, err.max()
+    return out

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2606_05650_gb300 import synthetic as syn
+from parity import compare_stream
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -34,45 +35,21 @@ def _qp(G, C, steps=None, **kw):
     return G.QuantParams(np.zeros(C, np.uint8), [0.05] if steps is None else steps, **kw)
 
 
-def check_frame(G, orc, pos, attr, J, qp, sample_rows=None):
-    """Encodes on the GPU and checks the stream against the oracle."""
-    n = pos.shape[0]
+def check_frame(G, orc, pos, attr, J, qp):
+    """Encodes on the GPU and checks the stream against the oracle (tests/parity.py)."""
     C = qp.C
     bs, nv, rpos, rattr = G.encode_frame(_dev(pos), _dev(attr) if C else None, J, qp, recon=True)
-    host = bs.cpu().numpy()
-    ref = orc.encode_frame(pos, attr if C else None, J, qp.groups, qp.steps, qp.tau, qp.rlgr_block, qp.rans_chunk,
-                           with_coeffs=True)
-    refbs = ref["bitstream"]
-    assert nv == ref["nv"]
-    # header and occupancy section are integer work: byte-identical
-    hb = int.from_bytes(refbs[8:12].tobytes(), "little")
-    occb = int.from_bytes(refbs[72:80].tobytes(), "little")
-    assert np.array_equal(host[:hb + occb][:72], refbs[:72])
-    assert np.array_equal(host[88:hb + occb], refbs[88:hb + occb])
-    dec = orc.decode_frame(host)  # GPU stream in the oracle decoder
-    assert np.array_equal(dec["codes"], ref["codes"])
     gpos, gattr = G.decode_frame(bs)
-    assert np.array_equal(gpos.cpu().numpy(), dec["pos"])
-    assert np.array_equal(rpos.cpu().numpy(), dec["pos"])
-    out = {"nv": nv, "bytes": host.size}
+    res = compare_stream(orc, bs.cpu().numpy(), pos, attr if C else None, J, qp.groups, qp.steps, qp.tau,
+                         qp.rlgr_block, qp.rans_chunk,
+                         (gpos.cpu().numpy(), gattr.cpu().numpy() if gattr is not None else None))
+    assert nv == res["nv"]
+    assert np.array_equal(rpos.cpu().numpy(), res["dec"]["pos"])
     if C and nv:
-        q_ref, y64 = ref["q"], ref["coeffs"]
-        steps = qp.steps[qp.groups]
-        dis = dec["q"] != q_ref
-        t = np.abs(y64) / steps + qp.tau
-        frac = t - np.floor(t)
-        zone = np.minimum(frac, 1 - frac) < 1e-4
-        assert not (dis & ~zone).any(), "index disagreement outside the rounding-boundary zone"
-        out["disagree"] = int(dis.sum())
-        assert dis.sum() <= max(1e-6 * dis.size, 0) + (1 if dis.size < 1e6 else 0), dis.sum()
-        # GPU decoding of the GPU stream matches the oracle's decoding of the same stream
-        ga = gattr.cpu().numpy().astype(np.float64)
-        scale = np.sqrt((dec["attr"] ** 2).mean(0)) + steps
-        err = np.abs(ga - dec["attr"]) / scale
-        assert err.max() < 1e-4, err.max()
         # the encoder's reconstruction is the decoder's output
-        assert np.abs(rattr.cpu().numpy() - gattr.cpu().numpy()).max() <= 1e-6 * (1 + np.abs(ga).max())
-    return out
+        ga = gattr.cpu().numpy()
+        assert np.abs(rattr.cpu().numpy() - ga).max() <= 1e-6 * (1 + np.abs(ga).max())
+    return res
 
 
 @pytest.mark.parametrize("n,J,seed", [(10_000, 10, 0), (3001, 10, 1), (25_000, 16, 2), (999, 21, 3), (500, 1, 4),
