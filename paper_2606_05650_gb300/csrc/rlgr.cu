@@ -321,35 +321,41 @@ __device__ __forceinline__ void adapt_kr(uint32_t p, int &KR)
     }
 }
 
+// Rare path of gr_read: the remainder crosses the window, or the escape code.
+__device__ __forceinline__ uint32_t gr_read_slow(WinReader &r, uint32_t k, uint32_t p, bool &bad)
+{
+    if (p < (uint32_t)kUnaryEsc) {
+        r.skip(p + 1u);
+        const uint32_t v = (p << k) | (r.peek() & ((1u << k) - 1u));
+        r.skip(k);
+        return v;
+    }
+    r.skip(kUnaryEsc);  // 24 ones, a 6-bit length n, n bits of value
+    const uint32_t n = r.peek() & 63u;
+    r.skip(6);
+    if (n > 32u) {
+        bad = true;
+        return 0;
+    }
+    const uint32_t y = r.peek();
+    const uint32_t v = n == 32u ? y : (y & ((1u << n) - 1u));
+    r.skip(n);
+    return v;
+}
+
 // Golomb-Rice value with parameter k (<= 24): p ones and a zero, then k low
 // bits; p >= 24 is the escape (24 ones, a 6-bit length n, n bits of value).
 __device__ __forceinline__ uint32_t gr_read(WinReader &r, uint32_t k, int &KR, bool &bad)
 {
     const uint32_t x = r.peek();
     uint32_t p = (uint32_t)__ffs(~x) - 1u;  // leading ones (all ones: wraps to >= 32)
+    const uint32_t n = p + 1u + k;
     uint32_t v;
-    if (p < (uint32_t)kUnaryEsc) {
-        const uint32_t mk = (1u << k) - 1u;
-        const uint32_t n = p + 1u + k;
-        if (n <= 32u) {  // prefix and remainder inside the window
-            v = (p << k) | ((x >> (p + 1u)) & mk);
-            r.skip(n);
-        } else {
-            r.skip(p + 1u);
-            v = (p << k) | (r.peek() & mk);
-            r.skip(k);
-        }
-    } else {
-        r.skip(kUnaryEsc);
-        const uint32_t n = r.peek() & 63u;
-        r.skip(6);
-        if (n > 32u) {
-            bad = true;
-            return 0;
-        }
-        const uint32_t y = r.peek();
-        v = n == 32u ? y : (y & ((1u << n) - 1u));
+    if (__builtin_expect(p < (uint32_t)kUnaryEsc && n <= 32u, 1)) {  // prefix and remainder inside the window
+        v = (p << k) | ((x >> (p + 1u)) & ((1u << k) - 1u));
         r.skip(n);
+    } else {
+        v = gr_read_slow(r, k, p, bad);
         p = v >> k;
     }
     adapt_kr(p, KR);
@@ -372,43 +378,36 @@ __device__ __forceinline__ void decode_stream(const uint32_t *wp, uint32_t nw, u
     int32_t pending = 0;
     for (uint32_t i = 0; i < len; ++i) {
         int32_t q = 0;
-        if (zeros) {
+        const uint32_t k = (uint32_t)K >> 4;
+        if (__builtin_expect(!(zeros | (uint32_t)has_pending | k), 1)) {  // the common case: Golomb-Rice mode
+            const uint32_t u = gr_read(r, (uint32_t)KR >> 4, KR, bad);
+            q = unzz(u);
+            K = u == 0 ? (K + 3 > 240 ? 240 : K + 3) : (K >= 3 ? K - 3 : 0);
+        } else if (zeros) {
             --zeros;
         } else if (has_pending) {
             q = pending;
             has_pending = false;
         } else {
-            const uint32_t k = (uint32_t)K >> 4;
-            if (k == 0) {
-                const uint32_t u = gr_read(r, (uint32_t)KR >> 4, KR, bad);
-                q = unzz(u);
-                if (u == 0) {
-                    K += 3;
-                    if (K > 240) K = 240;
+            const uint32_t x = r.peek();
+            if (!(x & 1u)) {  // a full run of 2^k zeros (clamped at the block end)
+                r.skip(1);
+                const uint32_t run = 1u << k;
+                zeros = (run < len - i ? run : len - i) - 1;
+                K += 4;
+                if (K > 240) K = 240;
+            } else {  // r < 2^k zeros, then a nonzero
+                const uint32_t rr = (x >> 1) & ((1u << k) - 1u);
+                r.skip(1u + k);
+                const uint32_t v = gr_read(r, (uint32_t)KR >> 4, KR, bad);
+                if (rr >= len - i || v == 0xFFFFFFFFu) bad = true;
+                K = K >= 6 ? K - 6 : 0;
+                if (rr == 0) {
+                    q = unzz(v + 1u);
                 } else {
-                    K = K >= 3 ? K - 3 : 0;
-                }
-            } else {
-                const uint32_t x = r.peek();
-                if (!(x & 1u)) {  // a full run of 2^k zeros (clamped at the block end)
-                    r.skip(1);
-                    const uint32_t run = 1u << k;
-                    zeros = (run < len - i ? run : len - i) - 1;
-                    K += 4;
-                    if (K > 240) K = 240;
-                } else {  // r < 2^k zeros, then a nonzero
-                    const uint32_t rr = (x >> 1) & ((1u << k) - 1u);
-                    r.skip(1u + k);
-                    const uint32_t v = gr_read(r, (uint32_t)KR >> 4, KR, bad);
-                    if (rr >= len - i || v == 0xFFFFFFFFu) bad = true;
-                    K = K >= 6 ? K - 6 : 0;
-                    if (rr == 0) {
-                        q = unzz(v + 1u);
-                    } else {
-                        zeros = rr - 1;
-                        pending = unzz(v + 1u);
-                        has_pending = true;
-                    }
+                    zeros = rr - 1;
+                    pending = unzz(v + 1u);
+                    has_pending = true;
                 }
             }
         }
