@@ -74,15 +74,13 @@ __device__ __forceinline__ int32_t unzz(uint32_t u)
 __device__ __forceinline__ void gr_put(BitWriter &bw, uint32_t v, uint32_t k, int &KR)
 {
     const uint32_t p = v >> k;
-    if (p < (uint32_t)kUnaryEsc) {
+    if (__builtin_expect(p + 1u + k <= 32u && p < (uint32_t)kUnaryEsc, 1)) {  // common case: one write
         const uint32_t low = v & ((1u << k) - 1u);  // k <= 24
         const uint32_t ones = (1u << p) - 1u;       // p ones then a zero
-        if (p + 1u + k <= 32u) {                    // common case: one write
-            bw.put(ones | (low << (p + 1u)), p + 1u + k);
-        } else {
-            bw.put(ones, p + 1u);
-            bw.put(low, k);
-        }
+        bw.put(ones | (low << (p + 1u)), p + 1u + k);
+    } else if (p < (uint32_t)kUnaryEsc) {
+        bw.put((1u << p) - 1u, p + 1u);
+        bw.put(v & ((1u << k) - 1u), k);
     } else {
         const uint32_t n = 32u - (uint32_t)__clz(v);
         bw.put((1u << kUnaryEsc) - 1u, kUnaryEsc);
@@ -110,14 +108,9 @@ struct Rlgr {
     __device__ __forceinline__ void code(BitWriter &bw, uint32_t u)
     {
         const uint32_t k = (uint32_t)K >> 4;
-        if (k == 0) {
+        if (__builtin_expect(k == 0, 1)) {  // Golomb-Rice mode
             gr_put(bw, u, (uint32_t)KR >> 4, KR);
-            if (u == 0) {
-                K += 3;
-                if (K > 240) K = 240;
-            } else {
-                K = K >= 3 ? K - 3 : 0;
-            }
+            K = u == 0 ? (K + 3 > 240 ? 240 : K + 3) : (K >= 3 ? K - 3 : 0);
         } else if (u == 0) {
             if (++z == (1u << k)) {
                 bw.put(0, 1);
