@@ -116,10 +116,18 @@ __device__ __forceinline__ uint32_t gap_level(uint64_t a, uint64_t b, uint32_t f
 // q = sign(y) floor(|y| * (1/step) + tau), |q| <= 2^30.
 __device__ __forceinline__ int32_t quantize_f32(float y, float inv_step, float tau)
 {
-    float t = floorf(__fadd_rn(__fmul_rn(fabsf(y), inv_step), tau));
-    t = fminf(t, 1073741824.0f);
-    int32_t m = (int32_t)t;
+    int32_t m = __float2int_rd(__fadd_rn(__fmul_rn(fabsf(y), inv_step), tau));  // floor, saturating
+    m = min(m, 1073741824);
     return (y < 0.0f) ? -m : m;
+}
+
+// zigzag index of the FP32 quantiser in one step: t = floor(|y| inv + tau)
+// (capped at 2^30), u = 2t for q = t >= 0 and 2t - 1 for q = -t < 0
+__device__ __forceinline__ uint32_t quantize_zz_f32(float y, float inv_step, float tau)
+{
+    int32_t t = __float2int_rd(__fadd_rn(__fmul_rn(fabsf(y), inv_step), tau));
+    t = min(t, 1073741824);
+    return ((uint32_t)t << 1) - (uint32_t)(y < 0.0f && t > 0);
 }
 
 // the quantiser of Sec. 3.4 in FP64: sign(y) floor(|y| / step + tau)

@@ -256,8 +256,7 @@ __global__ void __launch_bounds__(1024) rlgr_encode_kernel(EncJobs E, const int3
             }
             for (uint32_t i = i0; i < rows; ++i) {
                 const uint32_t x = cb[i * C];
-                const int32_t q = FROM_INT ? (int32_t)x : quantize_f32(__uint_as_float(x), inv, j.tau);
-                st.code(bw, zz(q));
+                st.code(bw, FROM_INT ? zz((int32_t)x) : quantize_zz_f32(__uint_as_float(x), inv, j.tau));
             }
         }
         __syncthreads();
