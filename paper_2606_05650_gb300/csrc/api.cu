@@ -1207,8 +1207,13 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         uint64_t *lvl_pref, *job_off, *blk_pref, *boff_all, *spart, *nodes, *codes, *nvdev;
         float *steps, *Y, *pool;
         uint8_t *occ, *gap;
+        float *ctab;
         RahtPlanDev plan;
     } L;
+    // voxel-centre tables for frames with 2^J <= N_v (see launch_batch_centre_tables)
+    uint64_t ctab_total = 0;
+    for (uint32_t f = 0; f < F; ++f)
+        if (d_pos && P[f].nv && (1ull << P[f].J) <= P[f].nv) ctab_total += 3ull << P[f].J;
     auto carve = [&](Carve &cv) {
         L.fr = cv.take<DecFrame>(F);
         L.vstart = cv.take<uint32_t>(F + 1);
@@ -1224,6 +1229,7 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         L.nodes = cv.take<uint64_t>(nodes + 1);
         L.codes = cv.take<uint64_t>(N + 1);
         L.gap = cv.take<uint8_t>(N + 2);
+        L.ctab = cv.take<float>(ctab_total + 1);
         if (C) {
             carve_plan(cv, L.plan, N, raht_tile_size(C), ctx->tune);
             uint64_t elems, tiles, surv;
@@ -1259,10 +1265,15 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     uint64_t *hjo = reinterpret_cast<uint64_t *>(tp + o_jo);
     uint64_t *hbp = reinterpret_cast<uint64_t *>(tp + o_bp);
     float *hst = reinterpret_cast<float *>(tp + o_st);
-    uint64_t vs = 0, oo = 0, no = 0, bo = 0, jo = 0;
+    uint64_t vs = 0, oo = 0, no = 0, bo = 0, jo = 0, co = 0;
     for (uint32_t f = 0; f < F; ++f) {
         const ParsedHeader &H = P[f];
         DecFrame d{};
+        d.ctab_off = ~0ull;
+        if (d_pos && H.nv && (1ull << H.J) <= H.nv) {
+            d.ctab_off = co;
+            co += 3ull << H.J;
+        }
         const uint8_t *base = d_in + offs[f];
         d.occ_sec = base + H.hb;
         d.occ_bytes = H.occ_bytes;
@@ -1343,7 +1354,8 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         launch_batch_expand(L.fr, F, lv, L.lvl_pref + (uint64_t)lv * (F + 1), count, L.occ, L.pref, L.nodes, L.codes,
                             dst, sms, s);
     }
-    launch_batch_centres_gaps(L.fr, F, L.vstart, N, L.codes, d_pos, L.gap, sms, s);
+    if (ctab_total) launch_batch_centre_tables(L.fr, F, Jmax, L.ctab, sms, s);
+    launch_batch_centres_gaps(L.fr, F, L.vstart, N, L.codes, L.ctab, d_pos, L.gap, sms, s);
     stage_end(s, kStOctreeDecode);
     // a12: RAHT schedule, RLGR decode + dequantise, inverse RAHT
     if (C && d_attr) {

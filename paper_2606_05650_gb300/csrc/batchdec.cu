@@ -168,8 +168,26 @@ __device__ __forceinline__ uint32_t compact3b(uint64_t m)
 }
 
 // voxel centres (Sec. 2.1) and gap levels of every frame's voxels
+// grid (x, frames): the centre table of frame blockIdx.y, entry a * 2^J + v =
+// (float)(lo_a + (v + 0.5) * cell), the same FP64 expression as per voxel
+__global__ void centre_tables_kernel(const DecFrame *fr, float *ctab)
+{
+    const DecFrame &d = fr[blockIdx.y];
+    if (d.ctab_off == ~0ull) return;
+    const uint64_t side = 1ull << d.J;
+    float *t = ctab + d.ctab_off;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 3 * side;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = (uint32_t)(e >> d.J);
+        const uint64_t v = e & (side - 1);
+        const double off = __dmul_rn(__dadd_rn((double)v, 0.5), d.grid.cell);
+        t[e] = (float)__dadd_rn(d.grid.lo[a], off);
+    }
+}
+
 __global__ void centres_gaps_kernel(const DecFrame *fr, uint32_t F, const uint32_t *vstart, uint64_t nv_total,
-                                    const uint64_t *__restrict__ codes, float *pos, uint8_t *gap)
+                                    const uint64_t *__restrict__ codes, const float *__restrict__ ctab, float *pos,
+                                    uint8_t *gap)
 {
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= nv_total;
          v += (uint64_t)gridDim.x * blockDim.x) {
@@ -181,11 +199,18 @@ __global__ void centres_gaps_kernel(const DecFrame *fr, uint32_t F, const uint32
         const uint64_t m = codes[v];
         gap[v] = (v == vstart[f]) ? (uint8_t)kInfLevel : (uint8_t)gap_level(codes[v - 1], m, 64);
         if (pos) {
-            const FrameGrid g = fr[f].grid;
+            const DecFrame &d = fr[f];
+            if (d.ctab_off != ~0ull) {
+                const float *t = ctab + d.ctab_off;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const double off = __dmul_rn(__dadd_rn((double)compact3b(m >> a), 0.5), g.cell);
-                pos[3 * v + a] = (float)__dadd_rn(g.lo[a], off);
+                for (int a = 0; a < 3; ++a) pos[3 * v + a] = t[((uint64_t)a << d.J) + compact3b(m >> a)];
+            } else {
+                const FrameGrid g = d.grid;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const double off = __dmul_rn(__dadd_rn((double)compact3b(m >> a), 0.5), g.cell);
+                    pos[3 * v + a] = (float)__dadd_rn(g.lo[a], off);
+                }
             }
         }
     }
@@ -251,10 +276,21 @@ void launch_batch_expand(const DecFrame *fr, uint32_t F, uint32_t d, const uint6
     count_launch();
 }
 
-void launch_batch_centres_gaps(const DecFrame *fr, uint32_t F, const uint32_t *vstart, uint64_t nv_total,
-                               const uint64_t *codes, float *pos, uint8_t *gap, int num_sms, cudaStream_t s)
+void launch_batch_centre_tables(const DecFrame *fr, uint32_t F, uint32_t Jmax, float *ctab, int num_sms,
+                                cudaStream_t s)
 {
-    centres_gaps_kernel<<<grid_for(nv_total + 1, num_sms), 256, 0, s>>>(fr, F, vstart, nv_total, codes, pos, gap);
+    if (F == 0) return;
+    uint32_t X = grid_for(3ull << Jmax, num_sms) / F + 1;
+    centre_tables_kernel<<<dim3(X, F), 256, 0, s>>>(fr, ctab);
+    count_launch();
+}
+
+void launch_batch_centres_gaps(const DecFrame *fr, uint32_t F, const uint32_t *vstart, uint64_t nv_total,
+                               const uint64_t *codes, const float *ctab, float *pos, uint8_t *gap, int num_sms,
+                               cudaStream_t s)
+{
+    centres_gaps_kernel<<<grid_for(nv_total + 1, num_sms), 256, 0, s>>>(fr, F, vstart, nv_total, codes, ctab, pos,
+                                                                         gap);
     count_launch();
 }
 

@@ -161,6 +161,7 @@ struct DecFrame {
     uint32_t J, mode, aux, chunk;
     uint32_t B, nb;
     FrameGrid grid;
+    uint64_t ctab_off;          // first entry of the frame's centre table (3 x 2^J floats), or ~0: computed directly
     uint64_t noff[22];          // node-array offset of each level (level J lives in the voxel rows)
     uint64_t boff[22];          // offset of each level's bytes inside the frame's occupancy bytes
     uint32_t lsz[22];
@@ -245,8 +246,14 @@ void launch_batch_expand(const DecFrame *fr, uint32_t F, uint32_t d, const uint6
                          const uint8_t *occ_all, const uint32_t *pref, uint64_t *nodes, uint64_t *codes,
                          DevState *st, int num_sms, cudaStream_t s);
 void launch_batch_roots(const DecFrame *fr, uint32_t F, uint64_t *nodes, uint64_t *codes, cudaStream_t s);
+// Voxel-centre tables: a centre coordinate depends only on that axis' voxel
+// coordinate, so frames with 2^J <= N_v evaluate the FP64 expression once per
+// axis value (3 x 2^J) instead of once per voxel.
+void launch_batch_centre_tables(const DecFrame *fr, uint32_t F, uint32_t Jmax, float *ctab, int num_sms,
+                                cudaStream_t s);
 void launch_batch_centres_gaps(const DecFrame *fr, uint32_t F, const uint32_t *vstart, uint64_t nv_total,
-                               const uint64_t *codes, float *pos, uint8_t *gap, int num_sms, cudaStream_t s);
+                               const uint64_t *codes, const float *ctab, float *pos, uint8_t *gap, int num_sms,
+                               cudaStream_t s);
 void launch_batch_block_tables(const DecFrame *fr, uint32_t F, const uint64_t *blk_pref, uint64_t nblk,
                                uint32_t *bw_all, int num_sms, cudaStream_t s);
 
