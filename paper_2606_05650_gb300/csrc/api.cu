@@ -1027,7 +1027,7 @@ struct DecLayout {
     uint8_t *occ, *gap;
     uint64_t *nodes, *codes, *nvdev, *block_off, *spart;
     uint32_t *pref, *ppart;
-    float *Y, *pool, *step;
+    float *Y, *pool, *step, *ctab;
     FrameGrid *grid;
     RahtPlanDev plan;
 };
@@ -1046,6 +1046,7 @@ size_t carve_decode(Carve &cv, DecLayout &L, const ParsedHeader &P, int num_sms,
     L.nodes = cv.take<uint64_t>(nodes + 1);
     L.codes = cv.take<uint64_t>(P.nv + 1);
     L.gap = cv.take<uint8_t>(P.nv + 2);
+    L.ctab = cv.take<float>(((1ull << P.J) <= P.nv) ? (3ull << P.J) : 1);
     if (P.C && P.nv) {
         carve_plan(cv, L.plan, P.nv, raht_tile_size(P.C), tune);
         uint64_t elems, tiles, surv;
@@ -1103,7 +1104,7 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
     stage_end(s, kStOccDecode);
     stage_begin(s, kStOctreeDecode);
     launch_octree_decode(occ, P.n_occ, P.J, P.lsz, L.nodes, L.pref, L.ppart, L.codes, dst, sms, s);
-    if (d_pos) launch_voxel_centres(L.codes, P.nv, P.J, L.grid, d_pos, s);
+    if (d_pos) launch_voxel_centres(L.codes, P.nv, P.J, L.grid, d_pos, s, L.ctab);
     stage_end(s, kStOctreeDecode);
     // a12: attributes
     if (P.C && d_attr) {

@@ -447,6 +447,29 @@ __global__ void centres_kernel(const uint64_t *__restrict__ codes, uint64_t nv, 
         centre(codes[v], g, pos + 3 * v);
 }
 
+// per-axis centre table of one frame: entry a * 2^J + v = (float)(lo_a + (v + 0.5) cell)
+__global__ void centre_table_kernel(const FrameGrid *grid, uint32_t J, float *ctab)
+{
+    const FrameGrid g = *grid;
+    const uint64_t side = 1ull << J;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 3 * side;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = (uint32_t)(e >> J);
+        const double off = __dmul_rn(__dadd_rn((double)(e & (side - 1)), 0.5), g.cell);
+        ctab[e] = (float)__dadd_rn(g.lo[a], off);
+    }
+}
+
+__global__ void centres_table_kernel(const uint64_t *__restrict__ codes, uint64_t nv, uint32_t J,
+                                     const float *__restrict__ ctab, float *pos)
+{
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t m = codes[v];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) pos[3 * v + a] = ctab[((uint64_t)a << J) + (uint32_t)compact3(m >> a)];
+    }
+}
+
 __global__ void centres_batch_kernel(const uint64_t *__restrict__ codes, const DevState *st, uint32_t frame_shift,
                                      const FrameGrid *grid, float *pos)
 {
@@ -614,11 +637,16 @@ void launch_gap_levels(const uint64_t *codes, uint64_t nv, uint8_t *gap, cudaStr
 }
 
 void launch_voxel_centres(const uint64_t *codes, uint64_t nv, uint32_t J, const FrameGrid *grid, float *pos,
-                          cudaStream_t s)
+                          cudaStream_t s, float *ctab)
 {
-    (void)J;
     if (nv == 0) return;
-    centres_kernel<<<grid_for(nv, 152), kThreads, 0, s>>>(codes, nv, grid, pos);
+    if (ctab && (1ull << J) <= nv) {
+        centre_table_kernel<<<grid_for(3ull << J, 152), kThreads, 0, s>>>(grid, J, ctab);
+        count_launch();
+        centres_table_kernel<<<grid_for(nv, 152), kThreads, 0, s>>>(codes, nv, J, ctab, pos);
+    } else {
+        centres_kernel<<<grid_for(nv, 152), kThreads, 0, s>>>(codes, nv, grid, pos);
+    }
     count_launch();
 }
 

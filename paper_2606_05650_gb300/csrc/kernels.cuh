@@ -74,8 +74,9 @@ uint64_t octree_decode_node_words(const uint32_t *h_level_sizes, uint32_t J);
 // gap levels of ascending codes (one frame), gap[0] = gap[nv] = kInfLevel
 void launch_gap_levels(const uint64_t *codes, uint64_t nv, uint8_t *gap, cudaStream_t s);
 // voxel centres of the codes of one frame (Sec. 2.1)
+// ctab (3 x 2^J floats, or null): per-axis centre table used when 2^J <= nv
 void launch_voxel_centres(const uint64_t *codes, uint64_t nv, uint32_t J, const FrameGrid *grid, float *pos,
-                          cudaStream_t s);
+                          cudaStream_t s, float *ctab = nullptr);
 // voxel centres of a batch: codes carry frame ids above frame_shift
 void launch_voxel_centres_batch(const uint64_t *codes, const DevState *st, uint64_t nv_bound,
                                 uint32_t frame_shift, const uint32_t *J, const FrameGrid *grid, float *pos,
