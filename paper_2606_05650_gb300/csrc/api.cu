@@ -117,6 +117,9 @@ struct gsnfs_ctx {
     DevState *st = nullptr;
     // launch-shape tunables (gsnfs_tune_set); 0 = built-in default
     uint32_t tune[3] = {0, 0, 0};
+    // second stream for the independent branches of one call (geometry and attributes)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // CUDA graphs of the encoder (off by default)
     bool graphs = false;
     cudaStream_t gstream = nullptr;  // capture / replay stream, joined to the caller's by events
@@ -216,6 +219,29 @@ gsnfs_status grow_pinned(gsnfs_ctx *ctx, size_t need)
     size_t cap = need + (1 << 16);
     CK(cudaMallocHost((void **)&ctx->pinned, cap));
     ctx->pinned_cap = cap;
+    return GSNFS_OK;
+}
+
+// Independent branches of one call: the work enqueued on the context's second
+// stream between fork_begin and fork_end starts after everything already on s
+// and s continues only after it (events also order captured graph nodes).
+gsnfs_status fork_begin(gsnfs_ctx *ctx, cudaStream_t s, cudaStream_t *aux)
+{
+    if (!ctx->aux) {
+        CK(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(ctx->ev_fork, s));
+    CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+    *aux = ctx->aux;
+    return GSNFS_OK;
+}
+
+gsnfs_status fork_end(gsnfs_ctx *ctx, cudaStream_t s)
+{
+    CK(cudaEventRecord(ctx->ev_join, ctx->aux));
+    CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
     return GSNFS_OK;
 }
 
@@ -769,17 +795,23 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
         stage_begin(s, kStDedup);
         launch_dedup(skeys, N, frame_shift, F, L.codes, L.seg, L.gap, L.vstart, L.dpart, dst, sms, s);
         stage_end(s, kStDedup);
+        // a4 + a5 (geometry) run beside a6-a9 (attributes) on the context's second stream
+        cudaStream_t ga = nullptr;
+        {
+            const gsnfs_status fst = fork_begin(ctx, s, &ga);
+            if (fst) return fst;
+        }
         // a4: octree occupancy
         OccupancyOut oo{L.occ, L.occ_cap, L.lsz, L.occ_off, L.hoff, L.opart};
-        stage_begin(s, kStOccupancy);
-        launch_occupancy(L.codes, L.gap, L.vstart, L.Jd, F, frame_shift, oo, dst, sms, s);
-        stage_end(s, kStOccupancy);
+        stage_begin(ga, kStOccupancy);
+        launch_occupancy(L.codes, L.gap, L.vstart, L.Jd, F, frame_shift, oo, dst, sms, ga);
+        stage_end(ga, kStOccupancy);
         // a5: occupancy rANS
         RansFrames rf{F, L.occ, L.occ_off, q->rans_chunk, L.chunk_off, L.freq, L.cum, L.mode, L.chunk_words,
                       L.chunk_top, L.chunk_pos, L.chunk_slots, L.sec_bytes};
-        stage_begin(s, kStRans);
-        launch_rans_encode(rf, dst, L.max_chunks, sms, s);
-        stage_end(s, kStRans);
+        stage_begin(ga, kStRans);
+        launch_rans_encode(rf, dst, L.max_chunks, sms, ga);
+        stage_end(ga, kStRans);
 
         HdrParams hpar{F, R, C, G, C ? q->rlgr_block : 1u, q->rans_chunk, q->tau, rq.capacity};
         if (C) {
@@ -827,6 +859,10 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
             launch_rlgr_encode(j, L.job_off, L.jobs_bound, s);
             stage_end(s, kStRlgrEnc);
             launch_scan_u32_to_u64(L.block_words, L.blocks_bound, L.block_off, L.spart, sms, s);
+        }
+        {
+            const gsnfs_status fst = fork_end(ctx, s);
+            if (fst) return fst;
         }
         // a10: container
         stage_begin(s, kStContainer);
@@ -1091,6 +1127,22 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
     if (P.C) CK(cudaMemcpyAsync(L.step, hp + 256, 4 * P.C, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(dst, 0, 8, s));
     const int sms = ctx->num_sms;
+    // a12's RLGR decode needs only the block tables: second stream, beside a11
+    const bool attrs = P.C && d_attr;
+    if (attrs) {
+        cudaStream_t ra = nullptr;
+        st = fork_begin(ctx, s, &ra);
+        if (st) return st;
+        const uint8_t *as = d_in + P.hb + P.occ_bytes;
+        const uint32_t *bw = reinterpret_cast<const uint32_t *>(as + 8);
+        const uint64_t nblk = (uint64_t)P.C * P.nb;
+        const uint32_t *payload = bw + nblk;
+        const uint64_t payload_words = (P.attr_bytes - 8 - 4 * nblk) / 4;
+        launch_scan_u32_to_u64(bw, nblk, L.block_off, L.spart, sms, ra);
+        stage_begin(ra, kStRlgrDec);
+        launch_rlgr_decode(payload, payload_words, bw, L.block_off, P.nv, P.C, P.B, L.step, L.Y, dst, ra);
+        stage_end(ra, kStRlgrDec);
+    }
     // a11: occupancy bytes
     const uint8_t *sec = d_in + P.hb;
     const uint8_t *occ = L.occ;
@@ -1106,21 +1158,14 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
     launch_octree_decode(occ, P.n_occ, P.J, P.lsz, L.nodes, L.pref, L.ppart, L.codes, dst, sms, s);
     if (d_pos) launch_voxel_centres(L.codes, P.nv, P.J, L.grid, d_pos, s, L.ctab);
     stage_end(s, kStOctreeDecode);
-    // a12: attributes
-    if (P.C && d_attr) {
+    // a12: schedule, then (after the RLGR branch) the inverse RAHT
+    if (attrs) {
         stage_begin(s, kStPrelude);
         launch_gap_levels(L.codes, P.nv, L.gap, s);
         launch_raht_prelude(L.plan, L.gap, dst, L.nvdev, sms, s);
         stage_end(s, kStPrelude);
-        const uint8_t *as = d_in + P.hb + P.occ_bytes;
-        const uint32_t *bw = reinterpret_cast<const uint32_t *>(as + 8);
-        const uint64_t nblk = (uint64_t)P.C * P.nb;
-        const uint32_t *payload = bw + nblk;
-        const uint64_t payload_words = (P.attr_bytes - 8 - 4 * nblk) / 4;
-        launch_scan_u32_to_u64(bw, nblk, L.block_off, L.spart, sms, s);
-        stage_begin(s, kStRlgrDec);
-        launch_rlgr_decode(payload, payload_words, bw, L.block_off, P.nv, P.C, P.B, L.step, L.Y, dst, s);
-        stage_end(s, kStRlgrDec);
+        st = fork_end(ctx, s);
+        if (st) return st;
         RahtIO io{};
         io.C = P.C;
         io.Y = L.Y;
@@ -1342,6 +1387,19 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     CK(cudaMemsetAsync(dst, 0, 8, s));
     const int sms = ctx->num_sms;
 
+    // a12's RLGR decode needs only the streams' block tables: it runs on the
+    // context's second stream beside a11 and the prelude
+    const bool attrs = C && d_attr;
+    if (attrs) {
+        cudaStream_t ra = nullptr;
+        st = fork_begin(ctx, s, &ra);
+        if (st) return st;
+        stage_begin(ra, kStRlgrDec);
+        launch_batch_block_tables(L.fr, F, L.blk_pref, nblk, L.bw_all, sms, ra);
+        launch_scan_u32_to_u64(L.bw_all, nblk, L.boff_all, L.spart, sms, ra);
+        launch_rlgr_decode_batch(L.fr, F, L.job_off, jobs, L.bw_all, L.boff_all, L.steps, C, L.Y, dst, ra);
+        stage_end(ra, kStRlgrDec);
+    }
     // a11: occupancy bytes of every frame, octree levels, voxel centres
     stage_begin(s, kStOccDecode);
     launch_batch_occ_bytes(L.fr, F, L.occ, max_occ, sms, s);
@@ -1358,16 +1416,13 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     if (ctab_total) launch_batch_centre_tables(L.fr, F, Jmax, L.ctab, sms, s);
     launch_batch_centres_gaps(L.fr, F, L.vstart, N, L.codes, L.ctab, d_pos, L.gap, sms, s);
     stage_end(s, kStOctreeDecode);
-    // a12: RAHT schedule, RLGR decode + dequantise, inverse RAHT
-    if (C && d_attr) {
+    // a12: RAHT schedule, then (after the RLGR branch) the inverse RAHT
+    if (attrs) {
         stage_begin(s, kStPrelude);
         launch_raht_prelude(L.plan, L.gap, dst, L.nvdev, sms, s);
         stage_end(s, kStPrelude);
-        stage_begin(s, kStRlgrDec);
-        launch_batch_block_tables(L.fr, F, L.blk_pref, nblk, L.bw_all, sms, s);
-        launch_scan_u32_to_u64(L.bw_all, nblk, L.boff_all, L.spart, sms, s);
-        launch_rlgr_decode_batch(L.fr, F, L.job_off, jobs, L.bw_all, L.boff_all, L.steps, C, L.Y, dst, s);
-        stage_end(s, kStRlgrDec);
+        st = fork_end(ctx, s);
+        if (st) return st;
         RahtIO io{};
         io.C = C;
         io.Y = L.Y;
@@ -1435,6 +1490,9 @@ void gsnfs_destroy(gsnfs_ctx *ctx)
     DeviceGuard dg(ctx->device);
     cudaDeviceSynchronize();
     drop_graphs(ctx);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
     if (ctx->gev_in) cudaEventDestroy(ctx->gev_in);
     if (ctx->gev_out) cudaEventDestroy(ctx->gev_out);
