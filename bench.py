@@ -564,6 +564,26 @@ def run_ladder(args):
     ms = timed(plain_multi, 1)
     res["plain_multirung"] = {"ms": round(ms, 2), "frames_per_s": round(F / (ms / 1e3), 1),
                               "gaussians_per_s": round(total_n / (ms / 1e3), 0)}
+    # rate-distortion: the same batched call returning per-stream distortion, hull and budgeted choice
+    from paper_2606_05650_gb300 import rd
+    G.set_graphs(False)
+    st_rd = {}
+
+    def batched_rd():
+        st_rd["r"] = G.encode_batch(P, A, Js, scales, qp, out=out, distortion=True)
+
+    res["batched_with_distortion"] = {"ms": round(timed(batched_rd, 2), 2)}
+    o_rd, offs_rd, dist = st_rd["r"]
+    rate = np.diff(offs_rd.astype(np.int64)).reshape(F, R)
+    nvox = np.array([G.peek_frame(o_rd[int(offs_rd[f * R]):int(offs_rd[f * R]) + 96].cpu().numpy())[0]
+                     for f in range(F)])
+    psnr = rd.psnr(dist, nvox)
+    budget = rate[:, 2]  # e.g. the x4 rung's size
+    sel = rd.select(rate, psnr, budget)
+    res["rd"] = {"psnr_db_mean_per_rung": [round(float(x), 2) for x in psnr.mean(0)],
+                 "bits_per_gaussian_per_rung": [round(float(x), 2) for x in 8 * rate.sum(0) / total_n],
+                 "hull_points_mean": round(float(np.mean([len(rd.upper_hull(rate[f], psnr[f])) for f in range(F)])), 2),
+                 "selected_rung_histogram_at_x4_budget": np.bincount(sel, minlength=R).tolist()}
     line = {"metric": "ladder encode frames/s (each frame at 5 rungs)", "unit": "frames/s", "higher_is_better": True,
             "value": res["batched_graphs"]["frames_per_s"], "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{F} dynamic 3DGS frames, Gaussians log-uniform in [50k, 2M] (total {total_n}), "

@@ -155,6 +155,18 @@ gsnfs_status gsnfs_encode_batch(gsnfs_ctx *ctx, void *stream, uint32_t frames, c
                                 uint32_t rungs, const double *h_rung_scale, const gsnfs_quant *q,
                                 uint8_t *d_out, uint64_t capacity, uint64_t *h_offsets);
 
+/* gsnfs_encode_batch that also returns the distortion of every stream for
+ * rate-distortion selection over the ladder: h_sq_err (host, frames x rungs x
+ * C, in that order) receives, per frame, rung and channel, the sum over the
+ * frame's voxels of the squared difference between each RAHT coefficient and
+ * its dequantised value.  RAHT is orthonormal (Sec. 3.2), so this is also the
+ * squared error of the decoded attributes against the voxel means (Parseval).
+ * Coefficients are taken in FP32 as coded (the DC in FP64). */
+gsnfs_status gsnfs_encode_batch_rd(gsnfs_ctx *ctx, void *stream, uint32_t frames, const float *const *h_pos,
+                                   const float *const *h_attr, const uint64_t *h_n, const uint32_t *h_J,
+                                   uint32_t rungs, const double *h_rung_scale, const gsnfs_quant *q,
+                                   uint8_t *d_out, uint64_t capacity, uint64_t *h_offsets, double *h_sq_err);
+
 /* Batched decoder: decodes `frames` streams; stream f lives at
  * d_in + h_in_offsets[f] with h_in_offsets[f+1] - h_in_offsets[f] bytes.
  * Voxels of frame f are written to rows h_out_rows[f] .. of d_pos / d_attr

@@ -512,6 +512,7 @@ struct EncodeReq {
     uint64_t capacity = 0;
     float *recon_pos = nullptr;
     float *recon_attr = nullptr;
+    double *dist = nullptr;  // host, F x R x C: squared quantisation error sums (or null)
     // results
     uint64_t total_bytes = 0;
     uint64_t nv = 0;
@@ -528,7 +529,7 @@ struct EncLayout {
     uint16_t *freq;
     uint8_t *gap, *occ, *chunk_slots, *groups;
     float *inv_step, *step, *Y, *pool, *center;
-    double *steps_rg, *dc;
+    double *steps_rg, *dc, *sq_err;
     StreamInfo *si;
     RahtPlanDev plan;
     uint64_t occ_cap, max_chunks, jobs_bound, blocks_bound;
@@ -589,6 +590,7 @@ size_t carve_encode(Carve &cv, EncLayout &L, const EncodeReq &rq, int num_sms, b
     L.steps_rg = cv.take<double>((uint64_t)R * 256);
     L.center = cv.take<float>((uint64_t)F * (C ? C : 1));
     L.dc = cv.take<double>((uint64_t)F * (C ? C : 1));
+    L.sq_err = cv.take<double>((uint64_t)F * R * (C ? C : 1));
     L.groups = cv.take<uint8_t>(256);
     L.vstart = cv.take<uint32_t>(F + 1);
     L.lsz = cv.take<uint32_t>((uint64_t)F * 22);
@@ -731,7 +733,9 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
     o_srg = (o_step + 4 * (size_t)R * C + 7) & ~(size_t)7;
     o_grp = o_srg + 8 * (size_t)R * 256;
     o_end = o_grp + 256;
-    st = grow_pinned(ctx, o_end + 64);
+    const size_t o_dist = ((o_end + 63) & ~(size_t)63) + 64;
+    const size_t dist_bytes = rq.dist ? 8 * (size_t)F * R * C : 0;
+    st = grow_pinned(ctx, o_dist + dist_bytes + 64);
     if (st) return st;
     CK(cudaStreamSynchronize(s));  // previous call's staging copies are done
     unsigned char *hp = ctx->pinned;
@@ -851,6 +855,11 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
             j.slot_words = L.slot_words;
             j.overflow = L.overflow;
             j.dc = L.dc;
+            if (rq.dist) {
+                CK(cudaMemsetAsync(L.sq_err, 0, 8 * (size_t)F * R * C, s));
+                j.sq_err = L.sq_err;
+                j.step = L.step;
+            }
             j.steps_rg = L.steps_rg;
             j.groups = L.groups;
             j.G = G;
@@ -904,6 +913,7 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
         CK(cudaMemcpyAsync(res, &dst->err, 8, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(res + 1, &dst->nv_total, 16, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(res + 3, L.overflow, 4, cudaMemcpyDeviceToHost, s));
+        if (dist_bytes) CK(cudaMemcpyAsync(hp + o_dist, L.sq_err, dist_bytes, cudaMemcpyDeviceToHost, s));
         return GSNFS_OK;
     };
     if (ctx->graphs) {
@@ -911,7 +921,7 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
                                      (uint64_t)(uintptr_t)rq.out, (uint64_t)(uintptr_t)rq.recon_pos,
                                      (uint64_t)(uintptr_t)rq.recon_attr, worst_slots ? 1u : 0u,
                                      (uint64_t)(uintptr_t)ctx->arena, ctx->arena_cap,
-                                     (uint64_t)(uintptr_t)ctx->pinned, rq.attr ? 1u : 0u};
+                                     (uint64_t)(uintptr_t)ctx->pinned, rq.attr ? 1u : 0u, rq.dist ? 1u : 0u};
         memcpy(&key[6], &q->tau, 8);
         for (uint32_t f = 0; f < F; ++f) {
             key.push_back(rq.n[f]);
@@ -928,6 +938,7 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
     rq.total_bytes = res[2];
     const uint32_t ovf = (uint32_t)(res[3] & 0xFFFFFFFFu);
     if (ovf && !worst_slots) return encode_impl(ctx, s, rq, true);
+    if (dist_bytes) memcpy(rq.dist, hp + o_dist, dist_bytes);
     if (derr == kErrCapacity) return GSNFS_ERR_CAPACITY;
     if (derr) return map_dev_error(derr);
     if (!rq.offsets.empty()) {
@@ -1608,10 +1619,10 @@ gsnfs_status gsnfs_encode_frame(gsnfs_ctx *ctx, void *stream, const float *d_pos
     return st;
 }
 
-gsnfs_status gsnfs_encode_batch(gsnfs_ctx *ctx, void *stream, uint32_t frames, const float *const *h_pos,
-                                const float *const *h_attr, const uint64_t *h_n, const uint32_t *h_J, uint32_t rungs,
-                                const double *h_rung_scale, const gsnfs_quant *q, uint8_t *d_out, uint64_t capacity,
-                                uint64_t *h_offsets)
+static gsnfs_status encode_batch_impl(gsnfs_ctx *ctx, void *stream, uint32_t frames, const float *const *h_pos,
+                                      const float *const *h_attr, const uint64_t *h_n, const uint32_t *h_J,
+                                      uint32_t rungs, const double *h_rung_scale, const gsnfs_quant *q,
+                                      uint8_t *d_out, uint64_t capacity, uint64_t *h_offsets, double *h_sq_err)
 {
     if (!ctx || frames < 1 || frames > (uint32_t)kMaxFrames || rungs < 1 || rungs > (uint32_t)kMaxRungs || !h_pos ||
         !h_n || !h_J || !d_out || !h_offsets)
@@ -1642,12 +1653,32 @@ gsnfs_status gsnfs_encode_batch(gsnfs_ctx *ctx, void *stream, uint32_t frames, c
     rq.out = d_out;
     rq.capacity = capacity;
     rq.offsets.assign((size_t)frames * rungs + 1, 0);
+    rq.dist = q->num_channels ? h_sq_err : nullptr;
     st = encode_impl(ctx, (cudaStream_t)stream, rq, false);
     if (st == GSNFS_OK)
         for (size_t i = 0; i < rq.offsets.size(); ++i) h_offsets[i] = rq.offsets[i];
     else if (st == GSNFS_ERR_CAPACITY)
         h_offsets[(size_t)frames * rungs] = rq.total_bytes;
     return st;
+}
+
+gsnfs_status gsnfs_encode_batch(gsnfs_ctx *ctx, void *stream, uint32_t frames, const float *const *h_pos,
+                                const float *const *h_attr, const uint64_t *h_n, const uint32_t *h_J, uint32_t rungs,
+                                const double *h_rung_scale, const gsnfs_quant *q, uint8_t *d_out, uint64_t capacity,
+                                uint64_t *h_offsets)
+{
+    return encode_batch_impl(ctx, stream, frames, h_pos, h_attr, h_n, h_J, rungs, h_rung_scale, q, d_out, capacity,
+                             h_offsets, nullptr);
+}
+
+gsnfs_status gsnfs_encode_batch_rd(gsnfs_ctx *ctx, void *stream, uint32_t frames, const float *const *h_pos,
+                                   const float *const *h_attr, const uint64_t *h_n, const uint32_t *h_J,
+                                   uint32_t rungs, const double *h_rung_scale, const gsnfs_quant *q, uint8_t *d_out,
+                                   uint64_t capacity, uint64_t *h_offsets, double *h_sq_err)
+{
+    if (!h_sq_err) return GSNFS_ERR_INVALID_ARG;
+    return encode_batch_impl(ctx, stream, frames, h_pos, h_attr, h_n, h_J, rungs, h_rung_scale, q, d_out, capacity,
+                             h_offsets, h_sq_err);
 }
 
 gsnfs_status gsnfs_peek_frame(const uint8_t *h_header, uint64_t bytes, uint64_t *out_nv, uint32_t *out_C,

@@ -184,6 +184,8 @@ struct RlgrJob {
     uint32_t slot_words;        // words per slot (a block needing more sets *overflow)
     uint32_t *overflow;
     const double *dc;           // per frame x C: each frame's DC in FP64, quantised in FP64 (or null: from Y)
+    double *sq_err;             // per frame x rung x channel: sum of squared quantisation errors, or null
+    const float *step;          // R x C FP32 steps (with sq_err)
     const double *steps_rg;     // R x G FP64 steps (with dc)
     const uint8_t *groups;      // C group ids (with dc)
     uint32_t G;

@@ -174,7 +174,7 @@ struct EncBlock {  // one row block of a CTA
     uint32_t f, b, nb, len;
 };
 
-template <bool FROM_INT>
+template <bool FROM_INT, bool DIST>
 __global__ void __launch_bounds__(1024) rlgr_encode_kernel(EncJobs E, const int32_t *qin, uint32_t rb)
 {
     extern __shared__ __align__(16) unsigned char esm[];
@@ -236,6 +236,9 @@ __global__ void __launch_bounds__(1024) rlgr_encode_kernel(EncJobs E, const int3
     Rlgr st;
     st.init();
     const float inv = (FROM_INT || !act) ? 0.f : j.inv_step[r * C + c];
+    const float stp = (DIST && act) ? j.step[r * C + c] : 0.f;
+    float sq = 0.f;
+    double dc_err = 0.0;
     if (nchunks) issue(0);
     for (uint32_t k = 0; k < nchunks; ++k) {
         if (k + 1 < nchunks) {
@@ -250,13 +253,26 @@ __global__ void __launch_bounds__(1024) rlgr_encode_kernel(EncJobs E, const int3
             const uint32_t *cb = buf + (2 * jl + (k & 1)) * chunk_elems + c;
             uint32_t i0 = 0;
             if (!FROM_INT && j.dc && k == 0 && me.b == 0) {  // the frame's DC: quantised from its FP64 value
-                st.code(bw, zz(quantize_f64(j.dc[(uint64_t)me.f * C + c], j.steps_rg[r * j.G + j.groups[c]],
-                                            j.tau64)));
+                const double y = j.dc[(uint64_t)me.f * C + c], st64 = j.steps_rg[r * j.G + j.groups[c]];
+                const int32_t q = quantize_f64(y, st64, j.tau64);
+                st.code(bw, zz(q));
+                if (DIST) {
+                    const double e = __dsub_rn(y, __dmul_rn((double)q, st64));
+                    dc_err = __dmul_rn(e, e);
+                }
                 i0 = 1;
             }
             for (uint32_t i = i0; i < rows; ++i) {
                 const uint32_t x = cb[i * C];
-                st.code(bw, FROM_INT ? zz((int32_t)x) : quantize_zz_f32(__uint_as_float(x), inv, j.tau));
+                if (DIST) {  // squared error of the dequantised coefficient (Parseval: of the attributes)
+                    const float y = __uint_as_float(x);
+                    const int32_t q = quantize_f32(y, inv, j.tau);
+                    const float e = __fsub_rn(y, __fmul_rn((float)q, stp));
+                    sq = __fadd_rn(sq, __fmul_rn(e, e));
+                    st.code(bw, zz(q));
+                } else {
+                    st.code(bw, FROM_INT ? zz((int32_t)x) : quantize_zz_f32(__uint_as_float(x), inv, j.tau));
+                }
             }
         }
         __syncthreads();
@@ -265,6 +281,7 @@ __global__ void __launch_bounds__(1024) rlgr_encode_kernel(EncJobs E, const int3
         st.finish(bw);
         j.block_words[blk] = bw.nw;
         if (bw.nw > j.slot_words) atomicExch(j.overflow, 1u);
+        if (DIST) atomicAdd(j.sq_err + ((uint64_t)me.f * j.R + r) * C + c, __dadd_rn((double)sq, dc_err));
     }
 }
 
@@ -515,8 +532,13 @@ void launch_rlgr_encode(const RlgrJob &j, const uint64_t *job_off, uint64_t jobs
     const uint32_t rb = row_blocks_per_cta(j.R * j.C);
     const uint32_t threads = (rb * j.R * j.C + 31) / 32 * 32;
     const size_t smem = enc_smem(j.C, rb);
-    cudaFuncSetAttribute(rlgr_encode_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    rlgr_encode_kernel<false><<<(uint32_t)((jobs_bound + rb - 1) / rb), threads, smem, s>>>(E, nullptr, rb);
+    if (j.sq_err) {
+        cudaFuncSetAttribute(rlgr_encode_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        rlgr_encode_kernel<false, true><<<(uint32_t)((jobs_bound + rb - 1) / rb), threads, smem, s>>>(E, nullptr, rb);
+    } else {
+        cudaFuncSetAttribute(rlgr_encode_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        rlgr_encode_kernel<false, false><<<(uint32_t)((jobs_bound + rb - 1) / rb), threads, smem, s>>>(E, nullptr, rb);
+    }
     count_launch();
 }
 
@@ -540,8 +562,8 @@ void launch_rlgr_encode_indices(const int32_t *q, const uint32_t *vstart, uint32
     const uint32_t rb = row_blocks_per_cta(C);
     const uint32_t threads = (rb * C + 31) / 32 * 32;
     const size_t smem = enc_smem(C, rb);
-    cudaFuncSetAttribute(rlgr_encode_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    rlgr_encode_kernel<true><<<(uint32_t)((jobs_bound + rb - 1) / rb), threads, smem, s>>>(E, q, rb);
+    cudaFuncSetAttribute(rlgr_encode_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    rlgr_encode_kernel<true, false><<<(uint32_t)((jobs_bound + rb - 1) / rb), threads, smem, s>>>(E, q, rb);
     count_launch();
 }
 

@@ -61,6 +61,7 @@ def lib():
                 "gsnfs_peek_frame": ([p, u64, P64, ct.POINTER(u32), ct.POINTER(u32)], i32),
                 "gsnfs_decode_frame": ([p, p, p, u64, p, p, u64, P64], i32),
                 "gsnfs_encode_batch": ([p, p, u32, p, p, p, p, u32, p, Q, p, u64, p], i32),
+                "gsnfs_encode_batch_rd": ([p, p, u32, p, p, p, p, u32, p, Q, p, u64, p, p], i32),
                 "gsnfs_decode_batch": ([p, p, u32, p, p, p, p, u64, p], i32),
                 "gsnfs_voxelize": ([p, p, p, u64, u32, p, p, P64], i32),
                 "gsnfs_octree_encode": ([p, p, p, u64, u32, p, u64, p, P64], i32),
@@ -245,8 +246,9 @@ def decode_frame(bitstream: torch.Tensor, with_attr=True):
     return pos[:m], (attr[:m, :C] if attr is not None else None)
 
 
-def encode_batch(pos_list, attr_list, J_list, rung_scales, qp: QuantParams, out=None):
-    """gsnfs_encode_batch: frames x rungs.  Returns (out uint8 tensor, offsets np.uint64[F*R+1])."""
+def encode_batch(pos_list, attr_list, J_list, rung_scales, qp: QuantParams, out=None, distortion=False):
+    """gsnfs_encode_batch: frames x rungs.  Returns (out uint8 tensor, offsets np.uint64[F*R+1]); with
+    distortion=True (gsnfs_encode_batch_rd) also the squared-error sums np.float64[F, R, C]."""
     F = len(pos_list)
     R = len(rung_scales)
     dev = pos_list[0].device
@@ -268,13 +270,23 @@ def encode_batch(pos_list, attr_list, J_list, rung_scales, qp: QuantParams, out=
     hs = (ct.c_double * R)(*[float(s) for s in rung_scales])
     offs = (ct.c_uint64 * (F * R + 1))()
     q = qp.struct()
-    rc = lib().gsnfs_encode_batch(context(dev), _stream(out), F, hp, ha, hn, hJ, R, hs, ct.byref(q), _ptr(out),
-                                  out.numel(), offs)
+    dist = np.zeros((F, R, max(C, 1)), dtype=np.float64) if distortion else None
+
+    def call(buf):
+        if distortion:
+            return lib().gsnfs_encode_batch_rd(context(dev), _stream(buf), F, hp, ha, hn, hJ, R, hs, ct.byref(q),
+                                               _ptr(buf), buf.numel(), offs,
+                                               dist.ctypes.data_as(ct.c_void_p))
+        return lib().gsnfs_encode_batch(context(dev), _stream(buf), F, hp, ha, hn, hJ, R, hs, ct.byref(q), _ptr(buf),
+                                        buf.numel(), offs)
+
+    rc = call(out)
     if rc == -2:  # GSNFS_ERR_CAPACITY: offs[F*R] holds the size needed
         out = torch.empty(int(offs[F * R]) + 4096, dtype=torch.uint8, device=dev)
-        rc = lib().gsnfs_encode_batch(context(dev), _stream(out), F, hp, ha, hn, hJ, R, hs, ct.byref(q), _ptr(out),
-                                      out.numel(), offs)
+        rc = call(out)
     _check(rc, "gsnfs_encode_batch")
+    if distortion:
+        return out, np.array(offs[:], dtype=np.uint64), dist[:, :, :C]
     return out, np.array(offs[:], dtype=np.uint64)
 
 
