@@ -402,6 +402,61 @@ void orc_raht_inverse(const uint64_t *M, int64_t nv, int J, int C, const double 
     if (nv > 1) raht_inv_rec(&cx, 0, nv, 3 * J);
 }
 
+/* Level of detail (decoding to octree depth Jp <= J; A.2's shift read as
+ * J - Jp): the nodes of depth Jp are the distinct codes >> 3(J - Jp); each
+ * gets the centre of its cell at depth Jp and the FP64 mean of its voxels'
+ * attributes.  Returns the node count.                                      */
+int64_t orc_lod(const uint64_t *M, int64_t nv, int J, int Jp, int C, const double *A, const double lo[3],
+                double ext, uint64_t *node_codes, float *node_pos, double *node_attr, int64_t *node_w)
+{
+    if (Jp < 0 || Jp > J) return ORC_ERR_ARG;
+    const int sh = 3 * (J - Jp);
+    int64_t k = -1;
+    for (int64_t i = 0; i < nv; ++i) {
+        const uint64_t m = (sh >= 64) ? 0 : (M[i] >> sh);
+        if (k < 0 || m != node_codes[k]) {
+            ++k;
+            node_codes[k] = m;
+            node_w[k] = 0;
+            for (int c = 0; c < C; ++c) node_attr[(size_t)k * C + c] = 0.0;
+        }
+        node_w[k] += 1;
+        for (int c = 0; c < C; ++c) node_attr[(size_t)k * C + c] += A[(size_t)i * C + c];
+    }
+    const int64_t n = k + 1;
+    for (int64_t j = 0; j < n; ++j)
+        for (int c = 0; c < C; ++c) node_attr[(size_t)j * C + c] /= (double)node_w[j];
+    orc_voxel_centres(node_codes, n, Jp, lo, ext, node_pos);
+    return n;
+}
+
+/* Low-pass coefficient of every node at binary level l (Eq. 1 applied up to
+ * level l inside each node, by the recursion of orc_raht_forward): out[k]
+ * for the k-th node in Morton order, w[k] its voxel count.  By induction on
+ * Eq. (1) it equals sqrt(w) times the mean of the node's values.           */
+int64_t orc_raht_lowpass(const uint64_t *M, int64_t nv, int J, int C, const double *A, int l, double *out,
+                         int64_t *w)
+{
+    double *Y = (double *)malloc(sizeof(double) * (size_t)(nv ? nv : 1) * (size_t)(C ? C : 1));
+    if (!Y) return ORC_ERR_NOMEM;
+    memcpy(Y, A, sizeof(double) * (size_t)nv * (size_t)C);
+    raht_ctx cx = {M, C, Y, NULL};
+    int64_t n = 0;
+    for (int64_t lo = 0; lo < nv;) {
+        const uint64_t key = (l >= 64) ? 0 : (M[lo] >> l);
+        int64_t hi = lo + 1;
+        while (hi < nv && ((l >= 64) ? 0 : (M[hi] >> l)) == key) ++hi;
+        raht_fwd_rec(&cx, lo, hi, l);
+        for (int c = 0; c < C; ++c) out[(size_t)n * C + c] = Y[(size_t)lo * C + c];
+        w[n] = hi - lo;
+        ++n;
+        lo = hi;
+    }
+    free(Y);
+    (void)J;
+    return n;
+}
+
 /* Per-voxel "node weight" of each stored coefficient: w0+w1 of the split that
  * produced the high pass at that index, N_v for the DC at index 0.  Used by
  * the parity tolerance (FP32 error of a weighted sum of w inputs).          */

@@ -57,6 +57,10 @@ def lib():
             L.orc_raht_forward.argtypes = [p, i64, i32, i32, p, p]
             L.orc_raht_inverse.argtypes = [p, i64, i32, i32, p, p]
             L.orc_raht_node_weights.argtypes = [p, i64, i32, p]
+            L.orc_lod.argtypes = [p, i64, i32, i32, i32, p, p, f64, p, p, p, p]
+            L.orc_lod.restype = i64
+            L.orc_raht_lowpass.argtypes = [p, i64, i32, i32, p, i32, p, p]
+            L.orc_raht_lowpass.restype = i64
             L.orc_praht_schedule.argtypes = [p, i64, i32, p, p, p, p, p]
             L.orc_praht_schedule.restype = i64
             L.orc_quantize.argtypes = [p, i64, i32, p, p, f64, p]
@@ -193,6 +197,36 @@ def raht_inverse(codes, Y, J):
     A = np.zeros_like(Y)
     lib().orc_raht_inverse(_p(codes), codes.shape[0], J, Y.shape[1], _p(Y), _p(A))
     return A
+
+
+def lod(codes, A, J, Jp, lo, ext):
+    """Nodes at octree depth Jp: (node codes, centres f32, mean attributes f64, voxel counts)."""
+    codes = np.ascontiguousarray(codes, dtype=np.uint64)
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    if A.ndim == 1:
+        A = A[:, None]
+    nv, C = codes.shape[0], A.shape[1]
+    m = max(nv, 1)
+    nc = np.zeros(m, dtype=np.uint64)
+    npos = np.zeros((m, 3), dtype=np.float32)
+    na = np.zeros((m, max(C, 1)), dtype=np.float64)
+    nw = np.zeros(m, dtype=np.int64)
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    k = _check(lib().orc_lod(_p(codes), nv, J, Jp, C, _p(A), _p(lo), float(ext), _p(nc), _p(npos), _p(na), _p(nw)))
+    return nc[:k], npos[:k], na[:k, :C], nw[:k]
+
+
+def raht_lowpass(codes, A, J, level):
+    """Low-pass coefficient (Eq. 1 applied inside each node) of every node at binary level `level`."""
+    codes = np.ascontiguousarray(codes, dtype=np.uint64)
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    if A.ndim == 1:
+        A = A[:, None]
+    nv, C = codes.shape[0], A.shape[1]
+    out = np.zeros((max(nv, 1), max(C, 1)), dtype=np.float64)
+    w = np.zeros(max(nv, 1), dtype=np.int64)
+    k = _check(lib().orc_raht_lowpass(_p(codes), nv, J, C, _p(A), level, _p(out), _p(w)))
+    return out[:k, :C], w[:k]
 
 
 def raht_node_weights(codes, J):

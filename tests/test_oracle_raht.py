@@ -120,3 +120,33 @@ def test_stopping_at_3J_minus_1_leaves_root_unmerged(orc):
     codes = np.array([0, 4], np.uint64)
     lv, *_ = orc.praht_schedule(codes, 1)
     assert lv.tolist() == [3]
+
+
+# --- level of detail (decoding to a coarser octree depth) ---------------------
+def test_lod_mean_is_lowpass_over_sqrt_weight(orc):
+    # Eq. (1) by induction: a node's low-pass coefficient is sqrt(w) times the mean of its values
+    rng = np.random.default_rng(7)
+    J = 8
+    v = np.unique(rng.integers(0, 2 ** J, size=(3000, 3)), axis=0)
+    codes = np.sort(orc.morton_codes(v, J))
+    A = rng.normal(size=(codes.size, 4))
+    for Jp in (0, 1, 3, 5, 7, 8):
+        nc, npos, na, nw = orc.lod(codes, A, J, Jp, np.zeros(3), 1.0)
+        L, w = orc.raht_lowpass(codes, A, J, 3 * (J - Jp))
+        assert np.array_equal(w, nw)
+        assert np.abs(L / np.sqrt(w)[:, None] - na).max() < 1e-12
+        assert nw.sum() == codes.size and np.array_equal(nc, np.unique(codes >> np.uint64(3 * (J - Jp))))
+
+
+def test_lod_extremes(orc):
+    rng = np.random.default_rng(8)
+    J = 6
+    codes = np.sort(orc.morton_codes(np.unique(rng.integers(0, 64, size=(500, 3)), axis=0), J))
+    A = rng.normal(size=(codes.size, 2))
+    nc, npos, na, nw = orc.lod(codes, A, J, J, np.zeros(3), 1.0)  # full depth: the voxels themselves
+    assert np.array_equal(nc, codes) and np.allclose(na, A, rtol=0, atol=0)
+    nc, npos, na, nw = orc.lod(codes, A, J, 0, np.array([1.0, 2.0, 3.0]), 4.0)  # the root
+    assert nw.tolist() == [codes.size] and np.allclose(na[0], A.mean(0))
+    assert np.allclose(npos[0], [3.0, 4.0, 5.0])  # centre of the whole cube
+    Y = orc.raht_forward(codes, A, J)
+    assert np.allclose(na[0] * np.sqrt(codes.size), Y[0], atol=1e-12)  # the DC
