@@ -372,6 +372,14 @@ def gpu_extras(args, G, torch, P, A, frames, qp, out, offs, dev, stream):
                           "backward_over_forward": round(statistics.median(bwd) / statistics.median(fwd), 3),
                           "forward_GBs": round(16 * C * nv5 / (statistics.median(fwd) / 1e3) / 1e9, 1)}
     del plan5
+    # level of detail: one 1M-Gaussian stream decoded to depths 16, 12, 8
+    s0 = out[int(offs[0]):int(offs[1])].clone()
+    lod = {}
+    for depth in (J, 12, 8):
+        t = _timed_calls(torch, stream, lambda _=0: G.decode_frame_lod(s0, depth), 3)
+        n_nodes = G.decode_frame_lod(s0, depth)[0].shape[0]
+        lod[str(depth)] = {"ms": round(statistics.median(t), 3), "nodes": int(n_nodes)}
+    res["lod_decode"] = lod
     # end to end: pinned host inputs -> H2D -> encode -> D2H streams -> decode -> D2H frames
     hp = [torch.from_numpy(p).pin_memory() for p, _ in frames]
     ha = [torch.from_numpy(a).pin_memory() for _, a in frames]

@@ -141,6 +141,17 @@ gsnfs_status gsnfs_peek_frame(const uint8_t *h_header, uint64_t bytes, uint64_t 
 gsnfs_status gsnfs_decode_frame(gsnfs_ctx *ctx, void *stream, const uint8_t *d_bitstream, uint64_t bytes,
                                 float *d_pos, float *d_attr, uint64_t capacity_nv, uint64_t *out_nv);
 
+/* Level of detail: decodes the frame and reduces it to the nodes of octree
+ * depth `depth` <= J (Algorithm 2's depth shift read as J - depth).  Node k
+ * (in Morton order) gets the centre of its cell at that depth in d_pos (x 3)
+ * and the mean of its voxels' decoded attributes in d_attr (x C), which by
+ * Eq. (1) is its RAHT low-pass coefficient divided by sqrt(voxel count).
+ * *out_nodes receives the node count; GSNFS_ERR_CAPACITY (outputs untouched)
+ * when it exceeds capacity_nodes.  depth = J gives the full decode. */
+gsnfs_status gsnfs_decode_frame_lod(gsnfs_ctx *ctx, void *stream, const uint8_t *d_bitstream, uint64_t bytes,
+                                    uint32_t depth, float *d_pos, float *d_attr, uint64_t capacity_nodes,
+                                    uint64_t *out_nodes);
+
 /* Batched bandwidth ladder (frames x rungs): encodes `frames` frames, frame f
  * with n[f] points at depth J[f] (16..19 supported together, any mix),
  * each at `rungs` quantisation rungs whose steps are q->steps scaled by

@@ -117,6 +117,9 @@ struct gsnfs_ctx {
     DevState *st = nullptr;
     // launch-shape tunables (gsnfs_tune_set); 0 = built-in default
     uint32_t tune[3] = {0, 0, 0};
+    // level-of-detail scratch (full-depth attributes, node index), grown on demand
+    void *lod = nullptr;
+    size_t lod_cap = 0;
     // second stream for the independent branches of one call (geometry and attributes)
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -1107,7 +1110,7 @@ size_t carve_decode(Carve &cv, DecLayout &L, const ParsedHeader &P, int num_sms,
 }
 
 gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, uint64_t bytes, float *d_pos,
-                         float *d_attr, uint64_t capacity_nv, uint64_t *out_nv)
+                         float *d_attr, uint64_t capacity_nv, uint64_t *out_nv, const uint64_t **codes_out = nullptr)
 {
     ParsedHeader P{};
     gsnfs_status st = read_headers(ctx, s, d_in, bytes, P);
@@ -1122,6 +1125,7 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
     if (st) return st;
     Carve cv(ctx->arena);
     carve_decode(cv, L, P, ctx->num_sms, ctx->tune);
+    if (codes_out) *codes_out = L.codes;
     DevState *dst = ctx->st;
     // host-computed grid and steps
     unsigned char *hp = ctx->pinned;
@@ -1501,6 +1505,7 @@ void gsnfs_destroy(gsnfs_ctx *ctx)
     DeviceGuard dg(ctx->device);
     cudaDeviceSynchronize();
     drop_graphs(ctx);
+    if (ctx->lod) cudaFree(ctx->lod);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
@@ -1704,6 +1709,72 @@ gsnfs_status gsnfs_decode_frame(gsnfs_ctx *ctx, void *stream, const uint8_t *d_b
     if ((uintptr_t)d_bitstream % 8 || (uintptr_t)d_attr % 16) return GSNFS_ERR_INVALID_ARG;
     DeviceGuard dg(ctx->device);
     return decode_impl(ctx, (cudaStream_t)stream, d_bitstream, bytes, d_pos, d_attr, capacity_nv, out_nv);
+}
+
+gsnfs_status gsnfs_decode_frame_lod(gsnfs_ctx *ctx, void *stream, const uint8_t *d_bitstream, uint64_t bytes,
+                                    uint32_t depth, float *d_pos, float *d_attr, uint64_t capacity_nodes,
+                                    uint64_t *out_nodes)
+{
+    if (!ctx || !d_bitstream || !out_nodes) return GSNFS_ERR_INVALID_ARG;
+    if ((uintptr_t)d_bitstream % 8 || (uintptr_t)d_attr % 4 || (uintptr_t)d_pos % 4) return GSNFS_ERR_INVALID_ARG;
+    if (bytes < 96) return GSNFS_ERR_CORRUPT;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    uint8_t h[96];
+    CK(cudaMemcpyAsync(h, d_bitstream, 96, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    uint64_t nv = 0;
+    uint32_t C = 0, J = 0;
+    gsnfs_status st = gsnfs_peek_frame(h, 96, &nv, &C, &J);
+    if (st) return st;
+    if (depth > J) return GSNFS_ERR_INVALID_ARG;
+    *out_nodes = 0;
+    if (nv == 0) return GSNFS_OK;
+    // scratch: full-depth attributes, flags, node offsets, node starts, scan partials
+    const int sms = ctx->num_sms;
+    auto carve = [&](Carve &cv, float **attr, uint32_t **flags, uint64_t **offs, uint64_t **starts,
+                     uint64_t **part) {
+        *attr = cv.take<float>(nv * (C ? C : 1) + 4);
+        *flags = cv.take<uint32_t>(nv + 1);
+        *offs = cv.take<uint64_t>(nv + 2);
+        *starts = cv.take<uint64_t>(nv + 2);
+        *part = cv.take<uint64_t>(scan_partial_words(nv, sms) + 1);
+        return cv.off;
+    };
+    float *attr;
+    uint32_t *flags;
+    uint64_t *offs, *starts, *part;
+    Carve m(nullptr);
+    const size_t need = carve(m, &attr, &flags, &offs, &starts, &part);
+    if (need > ctx->lod_cap) {
+        if (ctx->lod) CK(cudaFree(ctx->lod));
+        ctx->lod = nullptr;
+        ctx->lod_cap = 0;
+        CK(cudaMalloc(&ctx->lod, need));
+        ctx->lod_cap = need;
+    }
+    Carve cv(ctx->lod);
+    carve(cv, &attr, &flags, &offs, &starts, &part);
+    const uint64_t *codes = nullptr;
+    uint64_t nv2 = 0;
+    st = decode_impl(ctx, s, d_bitstream, bytes, nullptr, C && d_attr ? attr : nullptr, nv, &nv2, &codes);
+    if (st) return st;
+    const uint32_t sh = 3 * (J - depth);
+    launch_lod_index(codes, nv, sh, flags, offs, part, starts, sms, s);
+    uint64_t n_nodes = 0;
+    CK(cudaMemcpyAsync(&n_nodes, offs + nv, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *out_nodes = n_nodes;
+    if (n_nodes > capacity_nodes) return GSNFS_ERR_CAPACITY;
+    LodGrid g;
+    double ext;
+    memcpy(&ext, h + 56, 8);
+    for (int a = 0; a < 3; ++a) memcpy(&g.lo[a], h + 32 + 8 * a, 8);
+    g.cell = ext / std::ldexp(1.0, (int)depth);
+    launch_lod_nodes(codes, starts, offs, nv, n_nodes, sh, depth, C, attr, g, d_pos, C ? d_attr : nullptr, sms, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return GSNFS_OK;
 }
 
 gsnfs_status gsnfs_decode_batch(gsnfs_ctx *ctx, void *stream, uint32_t frames, const uint8_t *d_in,

@@ -260,6 +260,19 @@ void launch_batch_centres_gaps(const DecFrame *fr, uint32_t F, const uint32_t *v
 void launch_batch_block_tables(const DecFrame *fr, uint32_t F, const uint64_t *blk_pref, uint64_t nblk,
                                uint32_t *bw_all, int num_sms, cudaStream_t s);
 
+// ---- lod.cu: level of detail ------------------------------------------------
+struct LodGrid {
+    double lo[3];
+    double cell;  // ext / 2^Jp
+};
+// node index of every voxel at depth Jp: flags, exclusive offsets (offs[nv] =
+// node count) and the first voxel of each node (starts[n] = nv)
+void launch_lod_index(const uint64_t *codes, uint64_t nv, uint32_t sh, uint32_t *flags, uint64_t *offs,
+                      uint64_t *partials, uint64_t *starts, int num_sms, cudaStream_t s);
+void launch_lod_nodes(const uint64_t *codes, const uint64_t *starts, const uint64_t *offs, uint64_t nv,
+                      uint64_t n_nodes, uint32_t sh, uint32_t Jp, uint32_t C, const float *attr, const LodGrid &g,
+                      float *pos, float *out, int num_sms, cudaStream_t s);
+
 // ---- scan.cu / api.cu helpers -------------------------------------------
 // exclusive scan of n u32 values into u64 offsets (out has n + 1 entries)
 void launch_scan_u32_to_u64(const uint32_t *in, uint64_t n, uint64_t *out, uint64_t *partials, int num_sms,

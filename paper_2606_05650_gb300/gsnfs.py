@@ -63,6 +63,7 @@ def lib():
                 "gsnfs_encode_batch": ([p, p, u32, p, p, p, p, u32, p, Q, p, u64, p], i32),
                 "gsnfs_encode_batch_rd": ([p, p, u32, p, p, p, p, u32, p, Q, p, u64, p, p], i32),
                 "gsnfs_decode_batch": ([p, p, u32, p, p, p, p, u64, p], i32),
+                "gsnfs_decode_frame_lod": ([p, p, p, u64, u32, p, p, u64, P64], i32),
                 "gsnfs_voxelize": ([p, p, p, u64, u32, p, p, P64], i32),
                 "gsnfs_octree_encode": ([p, p, p, u64, u32, p, u64, p, P64], i32),
                 "gsnfs_octree_decode": ([p, p, p, u64, u32, p, p], i32),
@@ -288,6 +289,20 @@ def encode_batch(pos_list, attr_list, J_list, rung_scales, qp: QuantParams, out=
     if distortion:
         return out, np.array(offs[:], dtype=np.uint64), dist[:, :, :C]
     return out, np.array(offs[:], dtype=np.uint64)
+
+
+def decode_frame_lod(bitstream: torch.Tensor, depth: int):
+    """gsnfs_decode_frame_lod: (node centres [n, 3], node mean attributes [n, C] or None) at octree depth `depth`."""
+    host = bitstream[:96].cpu().numpy()
+    nv, C, J = peek_frame(host)
+    dev = bitstream.device
+    pos = torch.empty((max(nv, 1), 3), dtype=torch.float32, device=dev)
+    attr = torch.empty((max(nv, 1), max(C, 1)), dtype=torch.float32, device=dev) if C else None
+    n = ct.c_uint64()
+    _check(lib().gsnfs_decode_frame_lod(context(dev), _stream(bitstream), _ptr(bitstream), bitstream.numel(), depth,
+                                        _ptr(pos), _ptr(attr), max(nv, 1), ct.byref(n)), "gsnfs_decode_frame_lod")
+    k = n.value
+    return pos[:k], (attr[:k, :C] if attr is not None else None)
 
 
 def decode_batch(data: torch.Tensor, offsets, C: int, rows_cap: int):
