@@ -1049,19 +1049,171 @@ int64_t orc_occ_section_decode(const uint8_t *in, int64_t nbytes, uint8_t *occ, 
 /* ------------------------------------------------------------------------ */
 #define ORC_MAGIC 0x314E5347u
 
-static int64_t header_size(int J, int C, int G)
+#define ORC_KLT_N 15                                 /* AC functions of degree-3 SH */
+#define ORC_KLT_BYTES (3 * ORC_KLT_N * ORC_KLT_N * 4) /* three f32 15 x 15 matrices */
+
+static int64_t header_size(int J, int C, int G, int color)
 {
     int64_t h = 96 + 4 * (int64_t)(J + 1) + C;
     h = (h + 7) & ~(int64_t)7;
-    return h + 8 * (int64_t)G;
+    h += 8 * (int64_t)G;
+    if (color) h += (ORC_KLT_BYTES + 7) & ~7;
+    return h;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Colour decorrelation of SH coefficients (Sec. 4): every SH function's RGB
+ * triple goes to YUV; then one KLT per YUV channel over the 15 AC functions,
+ * applied before RAHT.  Channel layout of a 56-channel 3DGS row: scale 0-2,
+ * rotation 3-6, opacity 7, SH DC (R, G, B) 8-10, SH AC 11-55 as R[15] G[15]
+ * B[15].  YUV is the BT.601 analogue matrix; its inverse is computed from it.
+ * KLT of channel ch: K_ch (15 x 15, rows = eigenvectors of the covariance of
+ * that channel's AC vector over a sample of the frame's points, by decreasing
+ * eigenvalue, largest component of each made positive); a' = K_ch a.        */
+/* ------------------------------------------------------------------------ */
+static const double ORC_YUV[3][3] = {{0.299, 0.587, 0.114}, {-0.14713, -0.28886, 0.436}, {0.615, -0.51499, -0.10001}};
+
+static void yuv_inverse_matrix(double inv[3][3])
+{
+    const double(*m)[3] = ORC_YUV;
+    const double det = m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
+                       m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+                       m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+    inv[0][0] = (m[1][1] * m[2][2] - m[1][2] * m[2][1]) / det;
+    inv[0][1] = (m[0][2] * m[2][1] - m[0][1] * m[2][2]) / det;
+    inv[0][2] = (m[0][1] * m[1][2] - m[0][2] * m[1][1]) / det;
+    inv[1][0] = (m[1][2] * m[2][0] - m[1][0] * m[2][2]) / det;
+    inv[1][1] = (m[0][0] * m[2][2] - m[0][2] * m[2][0]) / det;
+    inv[1][2] = (m[0][2] * m[1][0] - m[0][0] * m[1][2]) / det;
+    inv[2][0] = (m[1][0] * m[2][1] - m[1][1] * m[2][0]) / det;
+    inv[2][1] = (m[0][1] * m[2][0] - m[0][0] * m[2][1]) / det;
+    inv[2][2] = (m[0][0] * m[1][1] - m[0][1] * m[1][0]) / det;
+}
+
+/* channel of colour col (0 R/Y, 1 G/U, 2 B/V) of SH function k (0 = DC) */
+static int sh_channel(int k, int col) { return k == 0 ? 8 + col : 11 + ORC_KLT_N * col + (k - 1); }
+
+void orc_yuv_rows(double *A, int64_t nv, int inverse)
+{
+    double inv[3][3];
+    yuv_inverse_matrix(inv);
+    const double(*m)[3] = inverse ? (const double(*)[3])inv : ORC_YUV;
+    for (int64_t i = 0; i < nv; ++i)
+        for (int k = 0; k <= ORC_KLT_N; ++k) {
+            double x[3], y[3];
+            for (int col = 0; col < 3; ++col) x[col] = A[(size_t)i * 56 + sh_channel(k, col)];
+            for (int r = 0; r < 3; ++r) y[r] = m[r][0] * x[0] + m[r][1] * x[1] + m[r][2] * x[2];
+            for (int col = 0; col < 3; ++col) A[(size_t)i * 56 + sh_channel(k, col)] = y[col];
+        }
+}
+
+/* a' = K a (inverse: a = K^T a') for the AC vector of each YUV channel */
+void orc_klt_rows(double *A, int64_t nv, const float *K, int inverse)
+{
+    for (int64_t i = 0; i < nv; ++i)
+        for (int ch = 0; ch < 3; ++ch) {
+            double a[ORC_KLT_N], b[ORC_KLT_N];
+            for (int k = 0; k < ORC_KLT_N; ++k) a[k] = A[(size_t)i * 56 + sh_channel(k + 1, ch)];
+            const float *M = K + ch * ORC_KLT_N * ORC_KLT_N;
+            for (int r = 0; r < ORC_KLT_N; ++r) {
+                double t = 0.0;
+                for (int k = 0; k < ORC_KLT_N; ++k)
+                    t += (inverse ? (double)M[k * ORC_KLT_N + r] : (double)M[r * ORC_KLT_N + k]) * a[k];
+                b[r] = t;
+            }
+            for (int k = 0; k < ORC_KLT_N; ++k) A[(size_t)i * 56 + sh_channel(k + 1, ch)] = b[k];
+        }
+}
+
+/* Eigenvectors of a symmetric n x n matrix by cyclic Jacobi rotations (FP64):
+ * V columns = eigenvectors, d = eigenvalues. */
+static void jacobi_eig(double *S, int n, double *V, double *d)
+{
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) V[i * n + j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += S[p * n + q] * S[p * n + q];
+        if (off < 1e-30) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = S[p * n + q];
+                if (fabs(apq) < 1e-300) continue;
+                const double theta = (S[q * n + q] - S[p * n + p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {  /* rows/columns p, q of S */
+                    const double skp = S[k * n + p], skq = S[k * n + q];
+                    S[k * n + p] = c * skp - s * skq;
+                    S[k * n + q] = s * skp + c * skq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double spk = S[p * n + k], sqk = S[q * n + k];
+                    S[p * n + k] = c * spk - s * sqk;
+                    S[q * n + k] = s * spk + c * sqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - s * vkq;
+                    V[k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < n; ++i) d[i] = S[i * n + i];
+}
+
+/* KLT matrices (f32, 3 x 15 x 15) from the first min(n, 4096) input rows. */
+#define ORC_KLT_SAMPLE 4096
+void orc_klt_matrices(const float *attr, int64_t n, float *K)
+{
+    const int N = ORC_KLT_N;
+    const int64_t m = n < ORC_KLT_SAMPLE ? n : ORC_KLT_SAMPLE;
+    double *rows = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1) * 56);
+    for (int64_t i = 0; i < m * 56; ++i) rows[i] = (double)attr[i];
+    orc_yuv_rows(rows, m, 0);
+    for (int ch = 0; ch < 3; ++ch) {
+        double mu[ORC_KLT_N] = {0}, S[ORC_KLT_N * ORC_KLT_N] = {0}, V[ORC_KLT_N * ORC_KLT_N], d[ORC_KLT_N];
+        for (int64_t i = 0; i < m; ++i)
+            for (int k = 0; k < N; ++k) mu[k] += rows[(size_t)i * 56 + sh_channel(k + 1, ch)];
+        for (int k = 0; k < N; ++k) mu[k] /= (double)(m > 0 ? m : 1);
+        for (int64_t i = 0; i < m; ++i)
+            for (int a = 0; a < N; ++a)
+                for (int b = 0; b < N; ++b)
+                    S[a * N + b] += (rows[(size_t)i * 56 + sh_channel(a + 1, ch)] - mu[a]) *
+                                    (rows[(size_t)i * 56 + sh_channel(b + 1, ch)] - mu[b]);
+        for (int a = 0; a < N * N; ++a) S[a] /= (double)(m > 0 ? m : 1);
+        jacobi_eig(S, N, V, d);
+        int order[ORC_KLT_N];
+        for (int k = 0; k < N; ++k) order[k] = k;
+        for (int a = 0; a < N; ++a)  /* decreasing eigenvalue, stable */
+            for (int b = a + 1; b < N; ++b)
+                if (d[order[b]] > d[order[a]]) {
+                    int t = order[a];
+                    order[a] = order[b];
+                    order[b] = t;
+                }
+        for (int r = 0; r < N; ++r) {
+            const int e = order[r];
+            int big = 0;
+            for (int k = 1; k < N; ++k)
+                if (fabs(V[k * N + e]) > fabs(V[big * N + e])) big = k;
+            const double sg = V[big * N + e] < 0 ? -1.0 : 1.0;
+            for (int k = 0; k < N; ++k) K[(ch * N + r) * N + k] = (float)(sg * V[k * N + e]);
+        }
+    }
+    free(rows);
 }
 
 int64_t orc_encode_frame(const float *pos, const float *attr, int64_t n, int C, int J, int G,
                          const uint8_t *group, const double *steps, double tau, uint32_t B,
                          uint32_t chunk_syms, uint8_t *out, int64_t cap, int64_t *out_nv,
-                         uint64_t *out_codes, double *out_coeff, int32_t *out_q)
+                         uint64_t *out_codes, double *out_coeff, int32_t *out_q, int color,
+                         const float *klt_in, float *klt_out)
 {
     if (J < 1 || J > 21 || C < 0 || (C > 0 && (G < 1 || G > 255)) || n < 0) return ORC_ERR_ARG;
+    if (color && C != 56) return ORC_ERR_ARG;
+    float K[ORC_KLT_BYTES / 4];
     if (C > 0 && (B == 0 || (B & (B - 1)) != 0)) return ORC_ERR_ARG;
     for (int c = 0; c < C; ++c)
         if (group[c] >= G) return ORC_ERR_ARG;
@@ -1103,6 +1255,15 @@ int64_t orc_encode_frame(const float *pos, const float *attr, int64_t n, int C, 
     /* attributes */
     int64_t attr_bytes = 0;
     uint8_t *attrsec = NULL;
+    if (color) {  /* Sec. 4: YUV on every SH function, then the per-channel KLT of the AC part */
+        if (klt_in)
+            memcpy(K, klt_in, sizeof(K));
+        else
+            orc_klt_matrices(attr, n, K);
+        if (klt_out) memcpy(klt_out, K, sizeof(K));
+        orc_yuv_rows(A, nv, 0);
+        orc_klt_rows(A, nv, K, 0);
+    }
     if (C > 0 && nv > 0) {
         double *Y = (double *)malloc(sizeof(double) * (size_t)nv * (size_t)C);
         int32_t *Q = (int32_t *)malloc(sizeof(int32_t) * (size_t)nv * (size_t)C);
@@ -1139,7 +1300,7 @@ int64_t orc_encode_frame(const float *pos, const float *attr, int64_t n, int C, 
         free(Y);
         free(Q);
     }
-    int64_t hb = header_size(J, C, C > 0 ? G : 0);
+    int64_t hb = header_size(J, C, C > 0 ? G : 0, color);
     int64_t total = hb + occ_bytes + attr_bytes;
     if (out_nv) *out_nv = nv;
     if (out_codes) memcpy(out_codes, ucodes, sizeof(uint64_t) * (size_t)nv);
@@ -1164,6 +1325,10 @@ int64_t orc_encode_frame(const float *pos, const float *attr, int64_t n, int C, 
     for (int c = 0; c < C; ++c) out[96 + 4 * (J + 1) + c] = group[c];
     int64_t so = (96 + 4 * (int64_t)(J + 1) + C + 7) & ~(int64_t)7;
     for (int g = 0; g < (C > 0 ? G : 0); ++g) putf64(out + so + 8 * g, steps[g]);
+    if (color) {
+        put32(out + 88, 1u);  /* flags bit 0: colour decorrelation, KLT matrices follow the steps */
+        memcpy(out + so + 8 * G, K, ORC_KLT_BYTES);
+    }
     memcpy(out + hb, occsec, (size_t)occ_bytes);
     if (attr_bytes) memcpy(out + hb + occ_bytes, attrsec, (size_t)attr_bytes);
     free(vox); free(codes); free(ucodes); free(A); free(lsz); free(occsec); free(attrsec);
@@ -1193,7 +1358,10 @@ int64_t orc_decode_frame(const uint8_t *in, int64_t nbytes, int64_t cap_nv, floa
     if (r) return r;
     int G = (int)get32(in + 20);
     int64_t hb = get32(in + 8);
-    if (hb != header_size(J, C, G) || hb > nbytes) return ORC_ERR_CORRUPT;
+    const uint32_t flags = get32(in + 88);
+    const int color = (int)(flags & 1u);
+    if ((flags & ~1u) || (color && C != 56)) return ORC_ERR_CORRUPT;
+    if (hb != header_size(J, C, G, color) || hb > nbytes) return ORC_ERR_CORRUPT;
     if (nv > cap_nv) return ORC_ERR_CAPACITY;
     double lo[3];
     for (int a = 0; a < 3; ++a) lo[a] = getf64(in + 32 + 8 * a);
@@ -1264,6 +1432,12 @@ int64_t orc_decode_frame(const uint8_t *in, int64_t nbytes, int64_t cap_nv, floa
                     Y[(size_t)i * C + c] = (double)Q[(size_t)i * C + c] * steps[grp[c]];
             orc_raht_inverse(codes, nv, J, C, Y, attr);
             free(Y);
+            if (color) {
+                float K[ORC_KLT_BYTES / 4];
+                memcpy(K, in + so + 8 * G, ORC_KLT_BYTES);
+                orc_klt_rows(attr, nv, K, 1);
+                orc_yuv_rows(attr, nv, 1);
+            }
         }
         free(Q);
     }

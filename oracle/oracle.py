@@ -74,7 +74,10 @@ def lib():
             L.orc_occ_section_decode.argtypes = [p, i64, p, i64]
             L.orc_occ_section_decode.restype = i64
             L.orc_encode_frame.argtypes = [p, p, i64, i32, i32, i32, p, p, f64, u32, u32, p, i64,
-                                           p, p, p, p]
+                                           p, p, p, p, i32, p, p]
+            L.orc_yuv_rows.argtypes = [p, i64, i32]
+            L.orc_klt_rows.argtypes = [p, i64, p, i32]
+            L.orc_klt_matrices.argtypes = [p, i64, p]
             L.orc_encode_frame.restype = i64
             L.orc_peek_frame.argtypes = [p, i64, p, p, p]
             L.orc_peek_frame.restype = i32
@@ -296,8 +299,9 @@ def occ_section_decode(sec, n):
 
 # --- whole frame -------------------------------------------------------------
 def encode_frame(pos, attr, J, groups=None, steps=None, tau=0.5, block=512, chunk_syms=4096,
-                 with_coeffs=False):
-    """Oracle encoder.  Returns dict(bitstream, nv, codes[, coeffs, q])."""
+                 with_coeffs=False, color=False, klt=None):
+    """Oracle encoder.  Returns dict(bitstream, nv, codes[, coeffs, q][, klt]).  color: the SH colour
+    decorrelation of Sec. 4 (56-channel 3DGS rows), with the given KLT matrices [3, 15, 15] or its own."""
     pos = np.ascontiguousarray(pos, dtype=np.float32).reshape(-1, 3)
     n = pos.shape[0]
     if attr is None:
@@ -319,16 +323,43 @@ def encode_frame(pos, attr, J, groups=None, steps=None, tau=0.5, block=512, chun
     if with_coeffs and C > 0:
         coeff = np.zeros((max(n, 1), C), dtype=np.float64)
         q = np.zeros((max(n, 1), C), dtype=np.int32)
+    kin = None if klt is None else np.ascontiguousarray(klt, dtype=np.float32).reshape(3, 15, 15)
+    kout = np.zeros((3, 15, 15), dtype=np.float32)
     k = _check(lib().orc_encode_frame(_p(pos), _p(attr), n, C, J, G, _p(groups), _p(steps), float(tau),
                                       block, chunk_syms, _p(out), cap, _p(nv), _p(codes),
                                       _p(coeff) if with_coeffs and C > 0 else None,
-                                      _p(q) if with_coeffs and C > 0 else None))
+                                      _p(q) if with_coeffs and C > 0 else None, 1 if color else 0,
+                                      _p(kin), _p(kout)))
     m = int(nv[0])
     res = {"bitstream": out[:k].copy(), "nv": m, "codes": codes[:m].copy()}
+    if color:
+        res["klt"] = kout
     if with_coeffs and C > 0:
         res["coeffs"] = coeff[:m].copy()
         res["q"] = q[:m].copy()
     return res
+
+
+def yuv_rows(A, inverse=False):
+    """BT.601 YUV of every SH function of 56-channel rows (Sec. 4), in place on a copy."""
+    A = np.array(A, dtype=np.float64, order="C")
+    lib().orc_yuv_rows(_p(A), A.shape[0], 1 if inverse else 0)
+    return A
+
+
+def klt_rows(A, K, inverse=False):
+    A = np.array(A, dtype=np.float64, order="C")
+    K = np.ascontiguousarray(K, dtype=np.float32)
+    lib().orc_klt_rows(_p(A), A.shape[0], _p(K), 1 if inverse else 0)
+    return A
+
+
+def klt_matrices(attr):
+    """KLT matrices [3, 15, 15] (rows = eigenvectors) from the first 4096 rows of a frame's points."""
+    attr = np.ascontiguousarray(attr, dtype=np.float32)
+    K = np.zeros((3, 15, 15), dtype=np.float32)
+    lib().orc_klt_matrices(_p(attr), attr.shape[0], _p(K))
+    return K
 
 
 def peek_frame(bs):

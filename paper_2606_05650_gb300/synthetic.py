@@ -46,6 +46,27 @@ def gs_attributes(rng: np.random.Generator, n: int) -> np.ndarray:
     return a
 
 
+def gs_attributes_correlated_sh(rng: np.random.Generator, n: int) -> np.ndarray:
+    """N x 56 attributes whose SH colours are correlated like real 3DGS ones:
+    each SH function's RGB share a luminance-like component (colour weights
+    near grey), AC energy falls with the SH degree, and the AC functions are
+    mixed by a fixed random matrix (cross-function correlation).  Other
+    channels as in gs_attributes.  For measuring the colour decorrelation."""
+    a = gs_attributes(rng, n)
+    mix_rng = np.random.default_rng(12345)  # the same mixing for every frame
+    mix = mix_rng.normal(0, 1, (15, 15)) * 0.35 + np.eye(15)
+    degree = np.array([1] * 3 + [2] * 5 + [3] * 7)
+    sig = (0.08 / degree).astype(np.float32)
+    lum = (rng.standard_normal((n, 15), dtype=np.float32) * sig) @ mix.T.astype(np.float32)
+    w = np.array([0.95, 1.0, 0.9], dtype=np.float32)
+    for col in range(3):
+        a[:, 11 + 15 * col:26 + 15 * col] = lum * w[col] + rng.standard_normal((n, 15), dtype=np.float32) * \
+            (0.15 * sig)
+    dc = rng.standard_normal((n, 1), dtype=np.float32) * np.float32(0.5)
+    a[:, 8:11] = dc * w + rng.standard_normal((n, 3), dtype=np.float32) * np.float32(0.05)
+    return a
+
+
 def _sphere(rng, n, centre, radius):
     v = rng.normal(size=(n, 3))
     v /= np.maximum(np.linalg.norm(v, axis=1, keepdims=True), 1e-12)
