@@ -372,6 +372,27 @@ def gpu_extras(args, G, torch, P, A, frames, qp, out, offs, dev, stream):
                           "backward_over_forward": round(statistics.median(bwd) / statistics.median(fwd), 3),
                           "forward_GBs": round(16 * C * nv5 / (statistics.median(fwd) / 1e3) / 1e9, 1)}
     del plan5
+    # colour decorrelation (Sec. 4) on a 1M-Gaussian frame with correlated SH colours: size and RGB PSNR
+    from oracle import oracle as orc
+    from paper_2606_05650_gb300 import synthetic as syn
+    pc, _ = frames[0]
+    ac = syn.gs_attributes_correlated_sh(np.random.default_rng(77), pc.shape[0])
+    _, merged, *_ = orc.voxelize(pc, ac, J)
+    dpc, dac = torch.from_numpy(pc).to(dev), torch.from_numpy(ac).to(dev)
+    colour = {}
+    for name, col in (("rgb", False), ("yuv_klt", True)):
+        qcol = G.QuantParams(syn.gs_channel_groups(), syn.GS_BASE_STEPS, color=col)
+        t = _timed_calls(torch, stream, lambda _=0: G.encode_frame(dpc, dac, J, qcol), 3)
+        bsc, *_ = G.encode_frame(dpc, dac, J, qcol)
+        td = _timed_calls(torch, stream, lambda _=0: G.decode_frame(bsc), 3)
+        _, dec = G.decode_frame(bsc)
+        err = (dec.cpu().numpy().astype(np.float64) - merged) ** 2
+        sh = err[:, 8:].mean()
+        colour[name] = {"bytes": int(bsc.numel()), "bits_per_gaussian": round(8 * bsc.numel() / pc.shape[0], 2),
+                        "sh_rgb_psnr_db": round(float(10 * np.log10(1.0 / sh)), 2),
+                        "encode_ms": round(statistics.median(t), 3), "decode_ms": round(statistics.median(td), 3)}
+    colour["size_ratio_rgb_over_klt"] = round(colour["rgb"]["bytes"] / colour["yuv_klt"]["bytes"], 3)
+    res["colour_decorrelation"] = colour
     # level of detail: one 1M-Gaussian stream decoded to depths 16, 12, 8
     s0 = out[int(offs[0]):int(offs[1])].clone()
     lod = {}

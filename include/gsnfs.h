@@ -60,6 +60,10 @@ typedef struct {
     double tau;                    /* rounding offset in (0, 0.5] */
     uint32_t rlgr_block;           /* B: power of two in [32, 65536] */
     uint32_t rans_chunk;           /* occupancy symbols per rANS chunk: multiple of 32 in [32, 1<<20] */
+    uint32_t color;                /* 0, or 1: SH colour decorrelation of Sec. 4 before RAHT (C must be 56:
+                                    * scale 0-2, rotation 3-6, opacity 7, SH DC RGB 8-10, SH AC 11-55 as
+                                    * R[15] G[15] B[15]): BT.601 YUV on every SH function, then one KLT per
+                                    * YUV channel over the 15 AC functions, its matrices in the header */
 } gsnfs_quant;
 
 /* Creates a context on CUDA device `cuda_device` (made current for the

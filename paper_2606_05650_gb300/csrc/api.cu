@@ -261,7 +261,12 @@ gsnfs_status map_dev_error(uint32_t e)
 
 __host__ __device__ inline uint64_t pad8(uint64_t x) { return (x + 7) & ~7ull; }
 
-uint64_t header_bytes(uint32_t J, uint32_t C, uint32_t G) { return pad8(96 + 4ull * (J + 1) + C) + 8ull * G; }
+// the KLT matrices of the colour mode follow the steps: three f32 15 x 15 (Sec. 4)
+__host__ __device__ inline uint64_t klt_bytes_padded() { return pad8(4ull * (uint64_t)kKltFloats); }
+__host__ __device__ inline uint64_t header_bytes(uint32_t J, uint32_t C, uint32_t G, uint32_t color)
+{
+    return pad8(96 + 4ull * (J + 1) + C) + 8ull * G + (color ? klt_bytes_padded() : 0);
+}
 
 uint64_t occ_bound(uint64_t n, uint32_t J)
 {
@@ -284,6 +289,7 @@ gsnfs_status check_quant(const gsnfs_quant *q)
     if (q->num_groups < 1 || q->num_groups > 255 || !q->channel_group || !q->steps) return GSNFS_ERR_INVALID_ARG;
     if (!pow2(q->rlgr_block) || q->rlgr_block < 32 || q->rlgr_block > 65536) return GSNFS_ERR_INVALID_ARG;
     if (!(q->tau > 0.0 && q->tau <= 0.5)) return GSNFS_ERR_INVALID_ARG;
+    if (q->color > 1 || (q->color && q->num_channels != 56)) return GSNFS_ERR_INVALID_ARG;
     for (uint32_t c = 0; c < q->num_channels; ++c)
         if (q->channel_group[c] >= q->num_groups) return GSNFS_ERR_INVALID_ARG;
     for (uint32_t g = 0; g < q->num_groups; ++g)
@@ -297,7 +303,7 @@ struct StreamInfo {
 };
 
 struct HdrParams {
-    uint32_t F, R, C, G, B, chunk;
+    uint32_t F, R, C, G, B, chunk, color;
     double tau;
     uint64_t capacity;
 };
@@ -321,7 +327,7 @@ __global__ void sizes_kernel(HdrParams hp, const uint32_t *J, const uint32_t *vs
         const uint64_t nb = (nv + hp.B - 1) / hp.B;
         for (uint32_t r = 0; r < hp.R; ++r) {
             StreamInfo x;
-            x.hb = pad8(96 + 4ull * (J[f] + 1) + hp.C) + 8ull * (hp.C ? hp.G : 0);
+            x.hb = header_bytes(J[f], hp.C, hp.C ? hp.G : 0, hp.color);
             x.occ = sec_bytes[f];
             x.attr = 0;
             if (hp.C && nv) {
@@ -341,7 +347,7 @@ __global__ void sizes_kernel(HdrParams hp, const uint32_t *J, const uint32_t *vs
 
 __global__ void header_kernel(HdrParams hp, const uint32_t *J, const uint32_t *vstart, const FrameGrid *grid,
                               const uint32_t *lsz, const uint8_t *groups, const double *steps_rg,
-                              const StreamInfo *si, const DevState *st, uint8_t *out)
+                              const float *klt, const StreamInfo *si, const DevState *st, uint8_t *out)
 {
     if (st->total_bytes > hp.capacity) return;
     const uint32_t s = blockIdx.x, f = s / hp.R, r = s % hp.R;
@@ -365,12 +371,16 @@ __global__ void header_kernel(HdrParams hp, const uint32_t *J, const uint32_t *v
         wr64(h + 64, (uint64_t)__double_as_longlong(hp.tau));
         wr64(h + 72, x.occ);
         wr64(h + 80, x.attr);
+        wr32(h + 88, hp.color);  // flags bit 0: colour decorrelation
     }
     for (uint32_t d = threadIdx.x; d <= Jf; d += blockDim.x) wr32(h + 96 + 4 * d, lsz[f * 22 + d]);
     for (uint32_t c = threadIdx.x; c < hp.C; c += blockDim.x) h[96 + 4 * (Jf + 1) + c] = groups[c];
     const uint64_t so = pad8(96 + 4ull * (Jf + 1) + hp.C);
     for (uint32_t g = threadIdx.x; g < G; g += blockDim.x)
         wr64(h + so + 8 * g, (uint64_t)__double_as_longlong(steps_rg[r * G + g]));
+    if (hp.color)
+        for (uint32_t i = threadIdx.x; i < (uint32_t)kKltFloats; i += blockDim.x)
+            wr32(h + so + 8 * G + 4 * i, __float_as_uint(klt[(uint64_t)f * kKltFloats + i]));
 }
 
 struct OccCopyArgs {
@@ -531,7 +541,7 @@ struct EncLayout {
         *spart;
     uint16_t *freq;
     uint8_t *gap, *occ, *chunk_slots, *groups;
-    float *inv_step, *step, *Y, *pool, *center;
+    float *inv_step, *step, *Y, *pool, *center, *klt;
     double *steps_rg, *dc, *sq_err;
     StreamInfo *si;
     RahtPlanDev plan;
@@ -594,6 +604,7 @@ size_t carve_encode(Carve &cv, EncLayout &L, const EncodeReq &rq, int num_sms, b
     L.center = cv.take<float>((uint64_t)F * (C ? C : 1));
     L.dc = cv.take<double>((uint64_t)F * (C ? C : 1));
     L.sq_err = cv.take<double>((uint64_t)F * R * (C ? C : 1));
+    L.klt = cv.take<float>((rq.q->color ? (uint64_t)F : 1) * kKltFloats);
     L.groups = cv.take<uint8_t>(256);
     L.vstart = cv.take<uint32_t>(F + 1);
     L.lsz = cv.take<uint32_t>((uint64_t)F * 22);
@@ -624,7 +635,9 @@ size_t carve_encode(Carve &cv, EncLayout &L, const EncodeReq &rq, int num_sms, b
     L.chunk_top = cv.take<uint32_t>(max_chunks + 1);
     L.chunk_pos = cv.take<uint32_t>(max_chunks + 1);
     if (C) {
-        carve_plan(cv, L.plan, N, raht_tile_size(C), tune);
+        uint32_t tune_c[3] = {tune ? tune[0] : 0u, tune ? tune[1] : 0u, tune ? tune[2] : 0u};
+        if (rq.q->color) tune_c[GSNFS_TUNE_RAHT_TILE] = 0;  // colour transforms need whole rows in a tile
+        carve_plan(cv, L.plan, N, raht_tile_size(C), tune_c);
         uint64_t elems, tiles, surv;
         raht_plan_sizes(N, L.plan.T, &elems, &tiles, &surv);
         L.pool = cv.take<float>(surv * C);
@@ -820,13 +833,14 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
         launch_rans_encode(rf, dst, L.max_chunks, sms, ga);
         stage_end(ga, kStRans);
 
-        HdrParams hpar{F, R, C, G, C ? q->rlgr_block : 1u, q->rans_chunk, q->tau, rq.capacity};
+        HdrParams hpar{F, R, C, G, C ? q->rlgr_block : 1u, q->rans_chunk, C ? q->color : 0u, q->tau, rq.capacity};
         if (C) {
             // a6: RAHT prelude; a7: forward transform with the cluster average fused into the first pass
             stage_begin(s, kStPrelude);
             launch_raht_prelude(L.plan, L.gap, dst, nullptr, sms, s);
             stage_end(s, kStPrelude);
             launch_frame_centres(L.attrp, L.poff, F, C, L.center, s);
+            if (q->color) launch_color_klt(L.attrp, L.poff, F, L.klt, L.center, s);
             RahtIO io{};
             io.C = C;
             io.seg = L.seg;
@@ -834,6 +848,7 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
             io.codes = L.codes;
             io.attr = L.attrp;
             io.center = L.center;
+            io.klt = q->color ? L.klt : nullptr;
             io.frame_shift = frame_shift;
             io.Y = L.Y;
             io.pool = L.pool;
@@ -880,7 +895,7 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
         stage_begin(s, kStContainer);
         sizes_kernel<<<1, 32, 0, s>>>(hpar, L.Jd, L.vstart, L.sec_bytes, L.blk_off, L.block_off, L.si, dst);
         count_launch();
-        header_kernel<<<F * R, 128, 0, s>>>(hpar, L.Jd, L.vstart, L.grid, L.lsz, L.groups, L.steps_rg, L.si, dst,
+        header_kernel<<<F * R, 128, 0, s>>>(hpar, L.Jd, L.vstart, L.grid, L.lsz, L.groups, L.steps_rg, L.klt, L.si, dst,
                                             rq.out);
         count_launch();
         OccCopyArgs oa{L.occ, L.occ_off, L.mode, L.chunk_off, L.freq, L.chunk_words, L.chunk_top, L.chunk_pos,
@@ -908,6 +923,12 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
             io.step = L.step;
             io.tau = (float)q->tau;
             io.frame_shift = frame_shift;
+            if (q->color) {
+                io.klt = L.klt;
+                io.vstart = L.vstart;
+                io.F = F;
+                io.yuv_inv = yuv_inverse();
+            }
             launch_raht_inverse(L.plan, io, N, sms, s);
         }
         stage_end(s, kStRecon);
@@ -924,7 +945,8 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
                                      (uint64_t)(uintptr_t)rq.out, (uint64_t)(uintptr_t)rq.recon_pos,
                                      (uint64_t)(uintptr_t)rq.recon_attr, worst_slots ? 1u : 0u,
                                      (uint64_t)(uintptr_t)ctx->arena, ctx->arena_cap,
-                                     (uint64_t)(uintptr_t)ctx->pinned, rq.attr ? 1u : 0u, rq.dist ? 1u : 0u};
+                                     (uint64_t)(uintptr_t)ctx->pinned, rq.attr ? 1u : 0u, rq.dist ? 1u : 0u,
+                                     C ? q->color : 0u};
         memcpy(&key[6], &q->tau, 8);
         for (uint32_t f = 0; f < F; ++f) {
             key.push_back(rq.n[f]);
@@ -962,6 +984,8 @@ struct ParsedHeader {
     double steps[256];
     uint32_t occ_mode, occ_aux, chunk;
     uint32_t B, nb;
+    uint32_t color;    // header flags bit 0
+    uint64_t klt_off;  // byte offset of the KLT matrices in the stream (colour mode)
 };
 
 uint32_t rd32(const uint8_t *p) { uint32_t v; memcpy(&v, p, 4); return v; }
@@ -981,9 +1005,14 @@ gsnfs_status parse_fixed(const uint8_t *h, uint64_t bytes, ParsedHeader &P)
     P.tau = rdf64(h + 64);
     P.occ_bytes = rd64(h + 72);
     P.attr_bytes = rd64(h + 80);
+    const uint32_t flags = rd32(h + 88);
+    P.color = flags & 1u;
+    if (flags & ~1u) return GSNFS_ERR_CORRUPT;
     if (P.J < 1 || P.J > (uint32_t)kMaxJ || P.C > (uint32_t)kMaxC || P.G > 255) return GSNFS_ERR_CORRUPT;
     if (P.C > 0 && P.G == 0) return GSNFS_ERR_CORRUPT;
-    if (P.hb != header_bytes(P.J, P.C, P.C ? P.G : 0)) return GSNFS_ERR_CORRUPT;
+    if (P.color && P.C != 56) return GSNFS_ERR_CORRUPT;
+    if (P.hb != header_bytes(P.J, P.C, P.C ? P.G : 0, P.color)) return GSNFS_ERR_CORRUPT;
+    P.klt_off = pad8(96 + 4ull * (P.J + 1) + P.C) + 8ull * P.G;
     if (P.occ_bytes < 16 || P.occ_bytes > bytes || P.attr_bytes > bytes ||
         (uint64_t)P.hb + P.occ_bytes + P.attr_bytes > bytes)
         return GSNFS_ERR_CORRUPT;
@@ -1077,7 +1106,8 @@ struct DecLayout {
     uint8_t *occ, *gap;
     uint64_t *nodes, *codes, *nvdev, *block_off, *spart;
     uint32_t *pref, *ppart;
-    float *Y, *pool, *step, *ctab;
+    float *Y, *pool, *step, *ctab, *klt;
+    uint32_t *vst;
     FrameGrid *grid;
     RahtPlanDev plan;
 };
@@ -1097,8 +1127,12 @@ size_t carve_decode(Carve &cv, DecLayout &L, const ParsedHeader &P, int num_sms,
     L.codes = cv.take<uint64_t>(P.nv + 1);
     L.gap = cv.take<uint8_t>(P.nv + 2);
     L.ctab = cv.take<float>(((1ull << P.J) <= P.nv) ? (3ull << P.J) : 1);
+    L.klt = cv.take<float>(kKltFloats);
+    L.vst = cv.take<uint32_t>(2);
     if (P.C && P.nv) {
-        carve_plan(cv, L.plan, P.nv, raht_tile_size(P.C), tune);
+        uint32_t tune_c[3] = {tune ? tune[0] : 0u, tune ? tune[1] : 0u, tune ? tune[2] : 0u};
+        if (P.color) tune_c[GSNFS_TUNE_RAHT_TILE] = 0;  // colour transforms need whole rows in a tile
+        carve_plan(cv, L.plan, P.nv, raht_tile_size(P.C), tune_c);
         uint64_t elems, tiles, surv;
         raht_plan_sizes(P.nv, L.plan.T, &elems, &tiles, &surv);
         L.pool = cv.take<float>(surv * P.C);
@@ -1136,9 +1170,13 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
     g.cell = P.ext / std::ldexp(1.0, (int)P.J);
     memcpy(hp, &g, sizeof(g));
     memcpy(hp + 128, &P.nv, 8);
+    const uint32_t vst_h[2] = {0u, (uint32_t)P.nv};
+    memcpy(hp + 192, vst_h, 8);
     for (uint32_t c = 0; c < P.C; ++c) ((float *)(hp + 256))[c] = (float)P.steps[P.groups[c]];
     CK(cudaMemcpyAsync(L.grid, hp, sizeof(g), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(L.nvdev, hp + 128, 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(L.vst, hp + 192, 8, cudaMemcpyHostToDevice, s));
+    if (P.color) CK(cudaMemcpyAsync(L.klt, d_in + P.klt_off, 4 * kKltFloats, cudaMemcpyDeviceToDevice, s));
     if (P.C) CK(cudaMemcpyAsync(L.step, hp + 256, 4 * P.C, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(dst, 0, 8, s));
     const int sms = ctx->num_sms;
@@ -1187,6 +1225,12 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
         io.out = d_attr;
         io.pool = L.pool;
         io.frame_shift = 64;
+        if (P.color) {
+            io.klt = L.klt;
+            io.vstart = L.vst;
+            io.F = 1;
+            io.yuv_inv = yuv_inverse();
+        }
         stage_begin(s, kStRahtInv);
         launch_raht_inverse(L.plan, io, P.nv, sms, s);
         stage_end(s, kStRahtInv);
@@ -1268,9 +1312,12 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         uint64_t *lvl_pref, *job_off, *blk_pref, *boff_all, *spart, *nodes, *codes, *nvdev;
         float *steps, *Y, *pool;
         uint8_t *occ, *gap;
-        float *ctab;
+        float *ctab, *klt;
+        uint32_t *fcolor;
         RahtPlanDev plan;
     } L;
+    bool any_color = false;
+    for (uint32_t f = 0; f < F; ++f) any_color |= P[f].color != 0;
     // voxel-centre tables for frames with 2^J <= N_v (see launch_batch_centre_tables)
     uint64_t ctab_total = 0;
     for (uint32_t f = 0; f < F; ++f)
@@ -1291,8 +1338,12 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         L.codes = cv.take<uint64_t>(N + 1);
         L.gap = cv.take<uint8_t>(N + 2);
         L.ctab = cv.take<float>(ctab_total + 1);
+        L.klt = cv.take<float>((any_color ? (uint64_t)F : 1) * kKltFloats);
+        L.fcolor = cv.take<uint32_t>(F + 1);
         if (C) {
-            carve_plan(cv, L.plan, N, raht_tile_size(C), ctx->tune);
+            uint32_t tune_c[3] = {ctx->tune[0], ctx->tune[1], ctx->tune[2]};
+            if (any_color) tune_c[GSNFS_TUNE_RAHT_TILE] = 0;  // colour transforms need whole rows in a tile
+            carve_plan(cv, L.plan, N, raht_tile_size(C), tune_c);
             uint64_t elems, tiles, surv;
             raht_plan_sizes(N, L.plan.T, &elems, &tiles, &surv);
             L.pool = cv.take<float>(surv * C);
@@ -1313,7 +1364,7 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     unsigned char *tp = hp + (size_t)F * 8192;
     size_t o_fr = 0, o_vs = o_fr + sizeof(DecFrame) * F, o_lp = (o_vs + 4 * (F + 1) + 7) & ~(size_t)7;
     size_t o_jo = o_lp + 8 * (size_t)(Jmax + 1) * (F + 1), o_bp = o_jo + 8 * (F + 1), o_nv = o_bp + 8 * (F + 1);
-    size_t o_st = o_nv + 8, o_end = o_st + 4 * (size_t)F * C;
+    size_t o_st = o_nv + 8, o_fc = o_st + 4 * (size_t)F * C, o_end = o_fc + 4 * (size_t)(F + 1);
     if ((size_t)F * 8192 + o_end > ctx->pinned_cap) {
         st = grow_pinned(ctx, (size_t)F * 8192 + o_end + 64);  // keeps nothing needed: headers are parsed
         if (st) return st;
@@ -1326,6 +1377,7 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     uint64_t *hjo = reinterpret_cast<uint64_t *>(tp + o_jo);
     uint64_t *hbp = reinterpret_cast<uint64_t *>(tp + o_bp);
     float *hst = reinterpret_cast<float *>(tp + o_st);
+    uint32_t *hfc = reinterpret_cast<uint32_t *>(tp + o_fc);
     uint64_t vs = 0, oo = 0, no = 0, bo = 0, jo = 0, co = 0;
     for (uint32_t f = 0; f < F; ++f) {
         const ParsedHeader &H = P[f];
@@ -1372,6 +1424,7 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         hjo[f] = jo;
         hbp[f] = bo;
         for (uint32_t c = 0; c < C; ++c) hst[(uint64_t)f * C + c] = (float)H.steps[H.groups[c]];
+        hfc[f] = H.color;
         vs += H.nv;
         oo += H.n_occ;
         if (C && H.nv) {
@@ -1398,6 +1451,13 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     CK(cudaMemcpyAsync(L.blk_pref, tp + o_bp, 8 * (F + 1), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(L.nvdev, tp + o_nv, 8, cudaMemcpyHostToDevice, s));
     if (C) CK(cudaMemcpyAsync(L.steps, tp + o_st, 4 * (size_t)F * C, cudaMemcpyHostToDevice, s));
+    if (any_color) {
+        CK(cudaMemcpyAsync(L.fcolor, tp + o_fc, 4 * (size_t)F, cudaMemcpyHostToDevice, s));
+        for (uint32_t f = 0; f < F; ++f)
+            if (P[f].color)
+                CK(cudaMemcpyAsync(L.klt + (uint64_t)f * kKltFloats, d_in + offs[f] + P[f].klt_off, 4 * kKltFloats,
+                                   cudaMemcpyDeviceToDevice, s));
+    }
     DevState *dst = ctx->st;
     CK(cudaMemsetAsync(dst, 0, 8, s));
     const int sms = ctx->num_sms;
@@ -1444,6 +1504,13 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         io.out = d_attr;
         io.pool = L.pool;
         io.frame_shift = 64;
+        if (any_color) {
+            io.klt = L.klt;
+            io.frame_color = L.fcolor;
+            io.vstart = L.vstart;
+            io.F = F;
+            io.yuv_inv = yuv_inverse();
+        }
         stage_begin(s, kStRahtInv);
         launch_raht_inverse(L.plan, io, N, sms, s);
         stage_end(s, kStRahtInv);
@@ -1568,7 +1635,7 @@ gsnfs_status gsnfs_max_bitstream_bytes(uint64_t n, uint32_t J, const gsnfs_quant
     gsnfs_status st = check_quant(q);
     if (st) return st;
     const uint32_t C = q->num_channels;
-    uint64_t b = header_bytes(J, C, C ? q->num_groups : 0);
+    uint64_t b = header_bytes(J, C, C ? q->num_groups : 0, C ? q->color : 0u);
     b += 16 + pad8(occ_bound(n, J));
     if (C) {
         uint64_t nb = (n + q->rlgr_block - 1) / q->rlgr_block;
@@ -2014,7 +2081,7 @@ gsnfs_status gsnfs_occupancy_section_encode(gsnfs_ctx *ctx, void *stream, const 
     launch_rans_encode(rf, ctx->st, nch, ctx->num_sms, s);
     stage_si_kernel<<<1, 1, 0, s>>>(sec, si, ctx->st);
     count_launch();
-    HdrParams hpar{1, 1, 0, 0, 1, rans_chunk, 0.5, capacity};
+    HdrParams hpar{1, 1, 0, 0, 1, rans_chunk, 0u, 0.5, capacity};
     OccCopyArgs oa{d_in, occ_off, mode, chunk_off, freq, cw, ct, cp, slots, rans_chunk_slot_bytes(rans_chunk)};
     occ_copy_kernel<<<dim3(ctx->num_sms, 1), 256, 0, s>>>(hpar, oa, si, ctx->st, d_out);
     count_launch();

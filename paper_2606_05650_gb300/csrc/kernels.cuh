@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "color.cuh"
 
 namespace gsnfs {
 
@@ -139,6 +140,12 @@ struct RahtIOT {  // S = float (codec) or double (FP64 instantiation of the same
     const S *inv_step;      // inverse with quantise->dequantise: per channel 1/step (device), or null
     const S *step;          // per channel step (device)
     S tau;
+    // SH colour decorrelation (FP32 codec path only): per frame K (3 x 15 x 15), or null
+    const float *klt;
+    const uint32_t *frame_color;  // inverse: per frame 1 if colour-coded (null: every frame)
+    const uint32_t *vstart;       // inverse: F + 1 voxel offsets (frame of a row)
+    uint32_t F;
+    YuvInv yuv_inv;
 };
 typedef RahtIOT<float> RahtIO;
 // FP64 transforms need a plan built with integer weights recorded (bf_w)
@@ -191,6 +198,10 @@ struct RlgrJob {
     uint32_t G;
     double tau64;
 };
+// KLT matrices of the colour mode (color.cu): per frame from its first input
+// points; the frame's centres are carried into the decorrelated domain.
+void launch_color_klt(const float *const *attr, const uint64_t *poff, uint32_t F, float *klt, float *center,
+                      cudaStream_t s);
 // Per-frame channel centres: FP32 mean of the first (up to 1024) input rows
 // of each frame, summed in a fixed order.
 void launch_frame_centres(const float *const *attr, const uint64_t *poff, uint32_t F, uint32_t C, float *center,

@@ -23,6 +23,8 @@
 // In-tile butterflies are ordered by level, so each level is one round
 // between barriers.  The inverse runs the passes top-down with the rounds
 // reversed and the transposed rotation.
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace gsnfs {
@@ -451,6 +453,16 @@ __device__ __forceinline__ double qdq(double y, double inv, double step, double 
     return __dmul_rn(y < 0.0 ? -t : t, step);
 }
 
+__device__ __forceinline__ uint32_t frame_of_voxel(const uint32_t *vstart, uint32_t F, uint64_t j)
+{
+    uint32_t lo = 0, hi = F;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((uint64_t)vstart[mid] <= j) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 template <typename S>
 struct XformArgs {
     RahtPlanDev p;
@@ -468,6 +480,7 @@ struct XformSmem {
     uint32_t *s_vals;  // 2T: point indices of the tile's gather
     uint8_t *s_frame;  // T: frame of each voxel (batched gather)
     S *rows;           // T x Cg
+    float *klt_s;      // 3 x 15 x 15: the colour KLT of the tile's first frame
 };
 
 template <typename S>
@@ -477,7 +490,7 @@ __host__ __device__ inline size_t xform_meta_bytes(uint32_t T)
 }
 
 template <typename S>
-__device__ inline XformSmem<S> carve_xform(unsigned char *raw, uint32_t T)
+__device__ inline XformSmem<S> carve_xform(unsigned char *raw, uint32_t T, uint32_t Cg)
 {
     XformSmem<S> X;
     X.s_ab = reinterpret_cast<S *>(raw);
@@ -487,6 +500,8 @@ __device__ inline XformSmem<S> carve_xform(unsigned char *raw, uint32_t T)
     X.s_vals = X.s_dst + T;
     X.s_frame = reinterpret_cast<uint8_t *>(X.s_vals + 2 * T);
     X.rows = reinterpret_cast<S *>(raw + ((xform_meta_bytes<S>(T) + 15) & ~(size_t)15));
+    X.klt_s = reinterpret_cast<float *>(raw + ((xform_meta_bytes<S>(T) + 15) & ~(size_t)15) +
+                                        sizeof(S) * (size_t)T * Cg);
     return X;
 }
 
@@ -536,6 +551,15 @@ __device__ void xform_tile(const XformArgs<S> &A, const XformSmem<S> &X, TileSch
     }
     if (gather && tid == 0) X.s_src[m] = io.seg[j0 + m];
     __syncthreads();
+    // colour mode: the KLT of the tile's first frame, staged for the per-row transforms
+    uint32_t kfr = 0xFFFFFFFFu;
+    if constexpr (std::is_same<S, float>::value) {
+        if (io.klt && ((!INV && gather) || (INV && q == 0))) {
+            kfr = INV ? frame_of_voxel(io.vstart, io.F, j0) : (io.frame_shift < 64 ? X.s_frame[0] : 0u);
+            for (uint32_t k = tid; k < (uint32_t)kKltFloats; k += kXThreads)
+                X.klt_s[k] = io.klt[(uint64_t)kfr * kKltFloats + k];
+        }
+    }
     for (uint32_t r = tid; r < sch.nr; r += kXThreads) sch.re[r] = p.round_end[(uint64_t)tile * kRounds + r];
     for (uint32_t k = tid; k < sch.nbf; k += kXThreads) {
         X.s_idx[k] = p.bf_idx[(uint64_t)tile * T + k];
@@ -592,7 +616,8 @@ __device__ void xform_tile(const XformArgs<S> &A, const XformSmem<S> &X, TileSch
                 if (!INV) {
                     const uint32_t s0 = X.s_src[i], s1 = X.s_src[i + 1];
                     const uint32_t fr = io.frame_shift < 64 ? X.s_frame[i] : 0u;
-                    const bool ctr_any = io.center != nullptr;
+                    bool ctr_any = io.center != nullptr;
+                    if constexpr (std::is_same<S, float>::value) ctr_any = ctr_any && !io.klt;
                     if (s1 - s0 > 1 || ctr_any) {
                         V acc = Vec<S, VEC>::ld(pr);
                         S *pa = reinterpret_cast<S *>(&acc);
@@ -625,6 +650,19 @@ __device__ void xform_tile(const XformArgs<S> &A, const XformSmem<S> &X, TileSch
                 }
             }
         }
+        if constexpr (std::is_same<S, float>::value) {
+            if (!INV && gather && io.klt) {  // colour decorrelation of whole rows (Cg == C), then centring
+                __syncthreads();
+                for (uint32_t i = tid; i < m; i += kXThreads) {
+                    const uint32_t fr = io.frame_shift < 64 ? X.s_frame[i] : 0u;
+                    float *row = X.rows + (uint64_t)i * Cg;
+                    color_forward_row(row, fr == kfr ? X.klt_s : io.klt + (uint64_t)fr * kKltFloats);
+                    if (io.center)
+                        for (uint32_t cc = 0; cc < C; ++cc)
+                            row[cc] = __fadd_rn(row[cc], -io.center[(uint64_t)fr * C + cc]);
+                }
+            }
+        }
         __syncthreads();
         // ---- rounds
         for (uint32_t rr = 0; rr < sch.nr; ++rr) {
@@ -643,6 +681,17 @@ __device__ void xform_tile(const XformArgs<S> &A, const XformSmem<S> &X, TileSch
                 }
             }
             __syncthreads();
+        }
+        if constexpr (std::is_same<S, float>::value) {
+            if (INV && q == 0 && io.klt) {  // undo the colour decorrelation of whole rows (Cg == C)
+                for (uint32_t i = tid; i < m; i += kXThreads) {
+                    const uint32_t fr = frame_of_voxel(io.vstart, io.F, j0 + i);
+                    if (io.frame_color && !io.frame_color[fr]) continue;
+                    color_inverse_row(X.rows + (uint64_t)i * Cg, fr == kfr ? X.klt_s : io.klt + (uint64_t)fr * kKltFloats,
+                                      io.yuv_inv);
+                }
+                __syncthreads();
+            }
         }
         // ---- store rows
         if (act) {
@@ -672,7 +721,7 @@ __global__ void __launch_bounds__(kXThreads, 3) xform_pass_kernel(XformArgs<S> A
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TileSched sch;
-    const XformSmem<S> X = carve_xform<S>(smem_raw, A.p.T);
+    const XformSmem<S> X = carve_xform<S>(smem_raw, A.p.T, A.Cg);
     const RahtPass ps = A.p.passes[q];
     const RahtPass nx = A.p.passes[q + 1];
     for (uint32_t t = blockIdx.x; t < ps.ntiles; t += gridDim.x)
@@ -685,7 +734,7 @@ __global__ void __launch_bounds__(kXThreads, 3) xform_finish_kernel(XformArgs<S>
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TileSched sch;
-    const XformSmem<S> X = carve_xform<S>(smem_raw, A.p.T);
+    const XformSmem<S> X = carve_xform<S>(smem_raw, A.p.T, A.Cg);
     const int np = (int)*A.p.npasses;
     for (int k = 0; k < np - q0; ++k) {
         const int q = INV ? (np - 1 - k) : (q0 + k);
@@ -709,7 +758,7 @@ uint32_t channel_group(uint32_t C, uint32_t T, uint32_t elem)
 template <typename S>
 size_t xform_smem(uint32_t T, uint32_t Cg)
 {
-    return ((xform_meta_bytes<S>(T) + 15) & ~(size_t)15) + sizeof(S) * T * Cg;
+    return ((xform_meta_bytes<S>(T) + 15) & ~(size_t)15) + sizeof(S) * T * Cg + 4 * (size_t)kKltFloats + 16;
 }
 
 template <typename S, bool INV, int VEC, bool GATHER, bool QDQ>

@@ -32,7 +32,8 @@ class GsnfsError(RuntimeError):
 class Quant(ct.Structure):
     _fields_ = [("num_channels", ct.c_uint32), ("num_groups", ct.c_uint32),
                 ("channel_group", ct.POINTER(ct.c_uint8)), ("steps", ct.POINTER(ct.c_double)),
-                ("tau", ct.c_double), ("rlgr_block", ct.c_uint32), ("rans_chunk", ct.c_uint32)]
+                ("tau", ct.c_double), ("rlgr_block", ct.c_uint32), ("rans_chunk", ct.c_uint32),
+                ("color", ct.c_uint32)]
 
 
 _lock = threading.Lock()
@@ -159,12 +160,13 @@ class QuantParams:
     """Quantisation / entropy parameters (Sec. 3.4): group id per channel, one
     step per group, rounding offset tau, RLGR block size, rANS chunk size."""
 
-    def __init__(self, groups, steps, tau=0.5, rlgr_block=512, rans_chunk=4096):
+    def __init__(self, groups, steps, tau=0.5, rlgr_block=512, rans_chunk=4096, color=False):
         self.groups = np.ascontiguousarray(np.asarray(groups, dtype=np.uint8).reshape(-1))
         self.steps = np.ascontiguousarray(np.asarray(steps, dtype=np.float64).reshape(-1))
         self.tau = float(tau)
         self.rlgr_block = int(rlgr_block)
         self.rans_chunk = int(rans_chunk)
+        self.color = bool(color)
 
     @property
     def C(self):
@@ -180,6 +182,7 @@ class QuantParams:
         q.tau = self.tau
         q.rlgr_block = self.rlgr_block
         q.rans_chunk = self.rans_chunk
+        q.color = 1 if self.color else 0
         return q
 
 

@@ -8,10 +8,24 @@ reading of the same stream within FP32 tolerance."""
 import numpy as np
 
 
+def stream_klt(stream):
+    """The colour-mode KLT matrices [3, 15, 15] carried in a stream's header (None without colour)."""
+    h = np.ascontiguousarray(stream)
+    if int.from_bytes(h[88:92].tobytes(), "little") & 1 == 0:
+        return None
+    J = int.from_bytes(h[12:16].tobytes(), "little")
+    C = int.from_bytes(h[16:20].tobytes(), "little")
+    G = int.from_bytes(h[20:24].tobytes(), "little")
+    so = (96 + 4 * (J + 1) + C + 7) // 8 * 8 + 8 * G
+    return np.frombuffer(h[so:so + 2700].tobytes(), dtype=np.float32).reshape(3, 15, 15)
+
+
 def compare_stream(orc, stream, pos, attr, J, groups, steps, tau, block, chunk, gpu_decoded=None):
     host = np.ascontiguousarray(stream)
     C = 0 if attr is None else attr.shape[1]
-    ref = orc.encode_frame(pos, attr if C else None, J, groups, steps, tau, block, chunk, with_coeffs=True)
+    klt = stream_klt(host)  # colour mode: the oracle encodes with the stream's own KLT matrices
+    ref = orc.encode_frame(pos, attr if C else None, J, groups, steps, tau, block, chunk, with_coeffs=True,
+                           color=klt is not None, klt=klt)
     refbs = ref["bitstream"]
     hb = int.from_bytes(refbs[8:12].tobytes(), "little")
     occb = int.from_bytes(refbs[72:80].tobytes(), "little")
