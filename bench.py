@@ -380,8 +380,8 @@ def gpu_extras(args, G, torch, P, A, frames, qp, out, offs, dev, stream):
     _, merged, *_ = orc.voxelize(pc, ac, J)
     dpc, dac = torch.from_numpy(pc).to(dev), torch.from_numpy(ac).to(dev)
     colour = {}
-    for name, col in (("rgb", False), ("yuv_klt", True)):
-        qcol = G.QuantParams(syn.gs_channel_groups(), syn.GS_BASE_STEPS, color=col)
+    for name, col, sc in (("rgb", False, 1.0), ("yuv_klt", True, 1.0), ("yuv_klt_steps_x0.66", True, 0.66)):
+        qcol = G.QuantParams(syn.gs_channel_groups(), np.array(syn.GS_BASE_STEPS) * sc, color=col)
         t = _timed_calls(torch, stream, lambda _=0: G.encode_frame(dpc, dac, J, qcol), 3)
         bsc, *_ = G.encode_frame(dpc, dac, J, qcol)
         td = _timed_calls(torch, stream, lambda _=0: G.decode_frame(bsc), 3)
@@ -392,6 +392,7 @@ def gpu_extras(args, G, torch, P, A, frames, qp, out, offs, dev, stream):
                         "sh_rgb_psnr_db": round(float(10 * np.log10(1.0 / sh)), 2),
                         "encode_ms": round(statistics.median(t), 3), "decode_ms": round(statistics.median(td), 3)}
     colour["size_ratio_rgb_over_klt"] = round(colour["rgb"]["bytes"] / colour["yuv_klt"]["bytes"], 3)
+    colour["size_ratio_rgb_over_klt_x0.66"] = round(colour["rgb"]["bytes"] / colour["yuv_klt_steps_x0.66"]["bytes"], 3)
     res["colour_decorrelation"] = colour
     # level of detail: one 1M-Gaussian stream decoded to depths 16, 12, 8
     s0 = out[int(offs[0]):int(offs[1])].clone()

@@ -542,7 +542,7 @@ struct EncLayout {
     uint16_t *freq;
     uint8_t *gap, *occ, *chunk_slots, *groups;
     float *inv_step, *step, *Y, *pool, *center, *klt;
-    double *steps_rg, *dc, *sq_err;
+    double *steps_rg, *dc, *sq_err, *kltpart;
     StreamInfo *si;
     RahtPlanDev plan;
     uint64_t occ_cap, max_chunks, jobs_bound, blocks_bound;
@@ -605,6 +605,7 @@ size_t carve_encode(Carve &cv, EncLayout &L, const EncodeReq &rq, int num_sms, b
     L.dc = cv.take<double>((uint64_t)F * (C ? C : 1));
     L.sq_err = cv.take<double>((uint64_t)F * R * (C ? C : 1));
     L.klt = cv.take<float>((rq.q->color ? (uint64_t)F : 1) * kKltFloats);
+    L.kltpart = cv.take<double>(rq.q->color ? color_klt_partial_words(F) : 1);
     L.groups = cv.take<uint8_t>(256);
     L.vstart = cv.take<uint32_t>(F + 1);
     L.lsz = cv.take<uint32_t>((uint64_t)F * 22);
@@ -840,7 +841,7 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
             launch_raht_prelude(L.plan, L.gap, dst, nullptr, sms, s);
             stage_end(s, kStPrelude);
             launch_frame_centres(L.attrp, L.poff, F, C, L.center, s);
-            if (q->color) launch_color_klt(L.attrp, L.poff, F, L.klt, L.center, s);
+            if (q->color) launch_color_klt(L.attrp, L.poff, F, L.klt, L.center, L.kltpart, s);
             RahtIO io{};
             io.C = C;
             io.seg = L.seg;

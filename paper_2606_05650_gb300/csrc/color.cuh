@@ -64,6 +64,33 @@ __device__ __forceinline__ void color_inverse_row(float *row, const float *K, co
         yuv3(inv.m, row[sh_chan(k, 0)], row[sh_chan(k, 1)], row[sh_chan(k, 2)]);
 }
 
+// one SH function of a row: RGB -> YUV (forward) or back (inverse matrix)
+__device__ __forceinline__ void color_yuv_task(float *row, int k, const float *m)
+{
+    yuv3(m, row[sh_chan(k, 0)], row[sh_chan(k, 1)], row[sh_chan(k, 2)]);
+}
+
+// one YUV channel's AC vector of a row: a' = K_ch a (forward) or a = K_ch^T a'
+template <bool INV>
+__device__ __forceinline__ void color_klt_task(float *row, int ch, const float *Kc)
+{
+    float a[kKltN];
+    float *p = row + 11 + kKltN * ch;
+#pragma unroll
+    for (int k = 0; k < kKltN; ++k) a[k] = p[k];
+#pragma unroll
+    for (int r = 0; r < kKltN; ++r) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < kKltN; ++k)
+            t = __fadd_rn(t, __fmul_rn(INV ? Kc[k * kKltN + r] : Kc[r * kKltN + k], a[k]));
+        p[r] = t;
+    }
+}
+
+__device__ __constant__ const float kYuvFwd[9] = {0.299f, 0.587f, 0.114f, -0.14713f, -0.28886f, 0.436f,
+                                                   0.615f, -0.51499f, -0.10001f};
+
 YuvInv yuv_inverse();
 
 }  // namespace gsnfs

@@ -201,7 +201,8 @@ struct RlgrJob {
 // KLT matrices of the colour mode (color.cu): per frame from its first input
 // points; the frame's centres are carried into the decorrelated domain.
 void launch_color_klt(const float *const *attr, const uint64_t *poff, uint32_t F, float *klt, float *center,
-                      cudaStream_t s);
+                      double *partials, cudaStream_t s);
+uint64_t color_klt_partial_words(uint32_t F);
 // Per-frame channel centres: FP32 mean of the first (up to 1024) input rows
 // of each frame, summed in a fixed order.
 void launch_frame_centres(const float *const *attr, const uint64_t *poff, uint32_t F, uint32_t C, float *center,

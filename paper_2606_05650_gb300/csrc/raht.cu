@@ -653,13 +653,23 @@ __device__ void xform_tile(const XformArgs<S> &A, const XformSmem<S> &X, TileSch
         if constexpr (std::is_same<S, float>::value) {
             if (!INV && gather && io.klt) {  // colour decorrelation of whole rows (Cg == C), then centring
                 __syncthreads();
-                for (uint32_t i = tid; i < m; i += kXThreads) {
+                for (uint32_t e = tid; e < m * 16; e += kXThreads)  // YUV per (row, SH function)
+                    color_yuv_task(X.rows + (uint64_t)(e >> 4) * Cg, (int)(e & 15), kYuvFwd);
+                __syncthreads();
+                for (uint32_t e = tid; e < m * 3; e += kXThreads) {  // KLT per (row, YUV channel)
+                    const uint32_t i = e / 3, ch = e - 3 * i;
                     const uint32_t fr = io.frame_shift < 64 ? X.s_frame[i] : 0u;
-                    float *row = X.rows + (uint64_t)i * Cg;
-                    color_forward_row(row, fr == kfr ? X.klt_s : io.klt + (uint64_t)fr * kKltFloats);
-                    if (io.center)
-                        for (uint32_t cc = 0; cc < C; ++cc)
-                            row[cc] = __fadd_rn(row[cc], -io.center[(uint64_t)fr * C + cc]);
+                    const float *K = (fr == kfr ? X.klt_s : io.klt + (uint64_t)fr * kKltFloats) + ch * kKltN * kKltN;
+                    color_klt_task<false>(X.rows + (uint64_t)i * Cg, (int)ch, K);
+                }
+                if (io.center) {
+                    __syncthreads();
+                    for (uint32_t e = tid; e < m * C; e += kXThreads) {
+                        const uint32_t i = e / C, cc = e - i * C;
+                        const uint32_t fr = io.frame_shift < 64 ? X.s_frame[i] : 0u;
+                        X.rows[(uint64_t)i * Cg + cc] = __fadd_rn(X.rows[(uint64_t)i * Cg + cc],
+                                                                  -io.center[(uint64_t)fr * C + cc]);
+                    }
                 }
             }
         }
@@ -684,11 +694,19 @@ __device__ void xform_tile(const XformArgs<S> &A, const XformSmem<S> &X, TileSch
         }
         if constexpr (std::is_same<S, float>::value) {
             if (INV && q == 0 && io.klt) {  // undo the colour decorrelation of whole rows (Cg == C)
-                for (uint32_t i = tid; i < m; i += kXThreads) {
+                for (uint32_t e = tid; e < m * 3; e += kXThreads) {  // KLT^T per (row, YUV channel)
+                    const uint32_t i = e / 3, ch = e - 3 * i;
                     const uint32_t fr = frame_of_voxel(io.vstart, io.F, j0 + i);
                     if (io.frame_color && !io.frame_color[fr]) continue;
-                    color_inverse_row(X.rows + (uint64_t)i * Cg, fr == kfr ? X.klt_s : io.klt + (uint64_t)fr * kKltFloats,
-                                      io.yuv_inv);
+                    const float *K = (fr == kfr ? X.klt_s : io.klt + (uint64_t)fr * kKltFloats) + ch * kKltN * kKltN;
+                    color_klt_task<true>(X.rows + (uint64_t)i * Cg, (int)ch, K);
+                }
+                __syncthreads();
+                for (uint32_t e = tid; e < m * 16; e += kXThreads) {  // inverse YUV per (row, SH function)
+                    const uint32_t i = e >> 4;
+                    const uint32_t fr = io.F > 1 ? frame_of_voxel(io.vstart, io.F, j0 + i) : 0u;
+                    if (io.frame_color && !io.frame_color[fr]) continue;
+                    color_yuv_task(X.rows + (uint64_t)i * Cg, (int)(e & 15), io.yuv_inv.m);
                 }
                 __syncthreads();
             }
@@ -756,9 +774,10 @@ uint32_t channel_group(uint32_t C, uint32_t T, uint32_t elem)
 }
 
 template <typename S>
-size_t xform_smem(uint32_t T, uint32_t Cg)
+size_t xform_smem(uint32_t T, uint32_t Cg, bool color)
 {
-    return ((xform_meta_bytes<S>(T) + 15) & ~(size_t)15) + sizeof(S) * T * Cg + 4 * (size_t)kKltFloats + 16;
+    return ((xform_meta_bytes<S>(T) + 15) & ~(size_t)15) + sizeof(S) * T * Cg +
+           (color ? 4 * (size_t)kKltFloats + 16 : 0);
 }
 
 template <typename S, bool INV, int VEC, bool GATHER, bool QDQ>
@@ -783,7 +802,7 @@ template <typename S, int VEC>
 void forward_all(const XformArgs<S> &A, uint64_t nv_bound, int num_sms, cudaStream_t s)
 {
     const uint32_t T = A.p.T;
-    const size_t smem = xform_smem<S>(T, A.Cg);
+    const size_t smem = xform_smem<S>(T, A.Cg, A.io.klt != nullptr);
     uint64_t tiles = (nv_bound + T - 1) / T;
     const uint64_t gcap = (uint64_t)num_sms * (A.p.xgrid_mult ? A.p.xgrid_mult : 4u);
     uint32_t grid0 = (uint32_t)(tiles < 1 ? 1 : (tiles < gcap ? tiles : gcap));
@@ -803,7 +822,7 @@ template <typename S, int VEC>
 void inverse_all(const XformArgs<S> &A, uint64_t nv_bound, int num_sms, cudaStream_t s)
 {
     const uint32_t T = A.p.T;
-    const size_t smem = xform_smem<S>(T, A.Cg);
+    const size_t smem = xform_smem<S>(T, A.Cg, A.io.klt != nullptr);
     uint64_t tiles = (nv_bound + T - 1) / T;
     const uint64_t gcap = (uint64_t)num_sms * (A.p.xgrid_mult ? A.p.xgrid_mult : 4u);
     uint32_t grid0 = (uint32_t)(tiles < 1 ? 1 : (tiles < gcap ? tiles : gcap));
