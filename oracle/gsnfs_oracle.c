@@ -1445,3 +1445,190 @@ int64_t orc_decode_frame(const uint8_t *in, int64_t nbytes, int64_t cap_nv, floa
     free(codes);
     return nv;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Splat rasteriser for rendered-view quality (the paper measures rendered
+ * PSNR of decoded frames; the renderer is the standard 3DGS forward pass,
+ * written here from its definition).  Gaussian i of a 56-channel row: mean
+ * pos[i], scale exp(attr 0-2), rotation quaternion (w, x, y, z) = attr 3-6
+ * normalised, opacity sigmoid(attr 7), colour from degree-3 real SH (DC at
+ * 8-10, AC function k at 11+k-1, 26+k-1, 41+k-1 for R, G, B) at the viewing
+ * direction, plus 0.5, clamped at 0.
+ * Camera: x_cam = R x + t (view[12] = R row-major | t), pixel (x, y) has
+ * centre (x + 0.5, y + 0.5), u = fx x/z + cx, v = fy y/z + cy.  2-D covariance
+ * J R S R^T J^T + 0.3 I (EWA, with the usual dilation); footprint radius
+ * ceil(3 sqrt(largest eigenvalue)); tiles of 16 x 16 pixels overlapped by the
+ * square [u - r, u + r] x [v - r, v + r] list the splat.  A pixel composites
+ * the splats of its tile front to back (view depth, then index): alpha =
+ * min(0.99, opacity exp(-d^T conic d / 2)), skipped below 1/255; stop before
+ * the transmittance falls under 1e-4; background added with the remaining
+ * transmittance.  Splats with z <= near or a singular 2-D covariance are
+ * dropped.                                                                  */
+/* ------------------------------------------------------------------------ */
+#define ORC_TILE 16
+
+typedef struct {
+    double u, v, conic[3], opacity, color[3], depth;
+    int tx0, tx1, ty0, ty1; /* inclusive tile range; tx0 > tx1 when empty */
+} orc_splat;
+
+static void sh_basis(const double d[3], double Y[16])
+{
+    const double x = d[0], y = d[1], z = d[2];
+    const double pi = 3.14159265358979323846;
+    const double c0 = 0.5 / sqrt(pi), c1 = sqrt(3.0 / (4.0 * pi));
+    const double c2a = 0.5 * sqrt(15.0 / pi), c2b = 0.25 * sqrt(5.0 / pi), c2c = 0.25 * sqrt(15.0 / pi);
+    const double c3a = 0.25 * sqrt(35.0 / (2.0 * pi)), c3b = 0.5 * sqrt(105.0 / pi), c3c = 0.25 * sqrt(21.0 / (2.0 * pi));
+    const double c3d = 0.25 * sqrt(7.0 / pi), c3e = 0.25 * sqrt(105.0 / pi);
+    Y[0] = c0;
+    Y[1] = -c1 * y;
+    Y[2] = c1 * z;
+    Y[3] = -c1 * x;
+    Y[4] = c2a * x * y;
+    Y[5] = -c2a * y * z;
+    Y[6] = c2b * (2.0 * z * z - x * x - y * y);
+    Y[7] = -c2a * x * z;
+    Y[8] = c2c * (x * x - y * y);
+    Y[9] = -c3a * y * (3.0 * x * x - y * y);
+    Y[10] = c3b * x * y * z;
+    Y[11] = -c3c * y * (4.0 * z * z - x * x - y * y);
+    Y[12] = c3d * z * (2.0 * z * z - 3.0 * x * x - 3.0 * y * y);
+    Y[13] = -c3c * x * (4.0 * z * z - x * x - y * y);
+    Y[14] = c3e * z * (x * x - y * y);
+    Y[15] = -c3a * x * (x * x - 3.0 * y * y);
+}
+
+static int splat_prepare(const float *p, const float *a, const double view[12], double fx, double fy, double cx,
+                         double cy, int W, int H, double znear, orc_splat *s)
+{
+    const double *R = view;
+    double pc[3];
+    for (int r = 0; r < 3; ++r) pc[r] = R[4 * r] * p[0] + R[4 * r + 1] * p[1] + R[4 * r + 2] * p[2] + R[4 * r + 3];
+    const double z = pc[2];
+    if (!(z > znear)) return 0;
+    double q[4] = {a[3], a[4], a[5], a[6]};
+    double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (!(qn > 0)) {
+        q[0] = 1.0;
+        q[1] = q[2] = q[3] = 0.0;
+        qn = 1.0;
+    }
+    const double w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, zq = q[3] / qn;
+    const double Rq[9] = {1 - 2 * (y * y + zq * zq), 2 * (x * y - w * zq), 2 * (x * zq + w * y),
+                          2 * (x * y + w * zq), 1 - 2 * (x * x + zq * zq), 2 * (y * zq - w * x),
+                          2 * (x * zq - w * y), 2 * (y * zq + w * x), 1 - 2 * (x * x + y * y)};
+    const double sc[3] = {exp(a[0]), exp(a[1]), exp(a[2])};
+    double M[9], S[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) M[3 * r + c] = Rq[3 * r + c] * sc[c];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) S[3 * r + c] = M[3 * r] * M[3 * c] + M[3 * r + 1] * M[3 * c + 1] + M[3 * r + 2] * M[3 * c + 2];
+    /* T = J R (2 x 3) with J the perspective Jacobian at pc */
+    const double J[6] = {fx / z, 0.0, -fx * pc[0] / (z * z), 0.0, fy / z, -fy * pc[1] / (z * z)};
+    double T[6];
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 3; ++c) T[3 * r + c] = J[3 * r] * R[c] + J[3 * r + 1] * R[4 + c] + J[3 * r + 2] * R[8 + c];
+    double TS[6];
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 3; ++c) TS[3 * r + c] = T[3 * r] * S[c] + T[3 * r + 1] * S[3 + c] + T[3 * r + 2] * S[6 + c];
+    double ca = TS[0] * T[0] + TS[1] * T[1] + TS[2] * T[2] + 0.3;
+    double cb = TS[0] * T[3] + TS[1] * T[4] + TS[2] * T[5];
+    double cc = TS[3] * T[3] + TS[4] * T[4] + TS[5] * T[5] + 0.3;
+    const double det = ca * cc - cb * cb;
+    if (!(det > 0)) return 0;
+    s->conic[0] = cc / det;
+    s->conic[1] = -cb / det;
+    s->conic[2] = ca / det;
+    const double mid = 0.5 * (ca + cc);
+    const double disc = mid * mid - det;
+    const double lmax = mid + sqrt(disc > 0.1 ? disc : 0.1);
+    const double rad = ceil(3.0 * sqrt(lmax));
+    s->u = fx * pc[0] / z + cx;
+    s->v = fy * pc[1] / z + cy;
+    s->depth = z;
+    s->opacity = 1.0 / (1.0 + exp(-(double)a[7]));
+    const int TX = (W + ORC_TILE - 1) / ORC_TILE, TY = (H + ORC_TILE - 1) / ORC_TILE;
+    int tx0 = (int)floor((s->u - rad) / ORC_TILE), tx1 = (int)floor((s->u + rad) / ORC_TILE);
+    int ty0 = (int)floor((s->v - rad) / ORC_TILE), ty1 = (int)floor((s->v + rad) / ORC_TILE);
+    s->tx0 = tx0 < 0 ? 0 : tx0;
+    s->tx1 = tx1 > TX - 1 ? TX - 1 : tx1;
+    s->ty0 = ty0 < 0 ? 0 : ty0;
+    s->ty1 = ty1 > TY - 1 ? TY - 1 : ty1;
+    /* colour: degree-3 SH at the direction from the camera centre (-R^T t) */
+    double cam[3], d[3];
+    for (int c = 0; c < 3; ++c) cam[c] = -(R[c] * R[3] + R[4 + c] * R[7] + R[8 + c] * R[11]);
+    for (int c = 0; c < 3; ++c) d[c] = (double)p[c] - cam[c];
+    const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int c = 0; c < 3; ++c) d[c] /= (dn > 0 ? dn : 1.0);
+    double Y[16];
+    sh_basis(d, Y);
+    for (int col = 0; col < 3; ++col) {
+        double v = Y[0] * a[8 + col];
+        for (int k = 1; k < 16; ++k) v += Y[k] * a[11 + 15 * col + (k - 1)];
+        v += 0.5;
+        s->color[col] = v > 0 ? v : 0;
+    }
+    return 1;
+}
+
+typedef struct {
+    double depth;
+    int64_t idx;
+} orc_depth_key;
+
+static int depth_cmp(const void *x, const void *y)
+{
+    const orc_depth_key *a = (const orc_depth_key *)x, *b = (const orc_depth_key *)y;
+    if (a->depth < b->depth) return -1;
+    if (a->depth > b->depth) return 1;
+    return (a->idx > b->idx) - (a->idx < b->idx);
+}
+
+/* Renders n Gaussians into image[H][W][3] (FP64).  Returns 0 or an error. */
+int orc_render(const float *pos, const float *attr, int64_t n, const double view[12], double fx, double fy,
+               double cx, double cy, int W, int H, double znear, const double bg[3], double *image)
+{
+    orc_splat *sp = (orc_splat *)malloc(sizeof(orc_splat) * (size_t)(n > 0 ? n : 1));
+    orc_depth_key *ord = (orc_depth_key *)malloc(sizeof(orc_depth_key) * (size_t)(n > 0 ? n : 1));
+    if (!sp || !ord) {
+        free(sp);
+        free(ord);
+        return ORC_ERR_NOMEM;
+    }
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (splat_prepare(pos + 3 * i, attr + 56 * i, view, fx, fy, cx, cy, W, H, znear, &sp[i]) &&
+            sp[i].tx0 <= sp[i].tx1 && sp[i].ty0 <= sp[i].ty1) {
+            ord[m].depth = sp[i].depth;
+            ord[m].idx = i;
+            ++m;
+        }
+    qsort(ord, (size_t)m, sizeof(orc_depth_key), depth_cmp);
+    for (int py = 0; py < H; ++py)
+        for (int px = 0; px < W; ++px) {
+            const int tx = px / ORC_TILE, ty = py / ORC_TILE;
+            double T = 1.0, col[3] = {0, 0, 0};
+            const double fxp = px + 0.5, fyp = py + 0.5;
+            for (int64_t k = 0; k < m; ++k) {
+                const orc_splat *s = &sp[ord[k].idx];
+                if (tx < s->tx0 || tx > s->tx1 || ty < s->ty0 || ty > s->ty1) continue;
+                const double dx = s->u - fxp, dy = s->v - fyp;
+                const double power = -0.5 * (s->conic[0] * dx * dx + s->conic[2] * dy * dy) - s->conic[1] * dx * dy;
+                if (power > 0) continue;
+                double alpha = s->opacity * exp(power);
+                if (alpha > 0.99) alpha = 0.99;
+                if (alpha < 1.0 / 255.0) continue;
+                const double tn = T * (1.0 - alpha);
+                if (tn < 1e-4) break;
+                for (int c = 0; c < 3; ++c) col[c] += s->color[c] * alpha * T;
+                T = tn;
+            }
+            for (int c = 0; c < 3; ++c) image[((size_t)py * W + px) * 3 + c] = col[c] + T * bg[c];
+        }
+    free(sp);
+    free(ord);
+    return ORC_OK;
+}
+
+/* The 16 real SH basis values (degrees 0-3) at a unit direction (tests). */
+void orc_sh_basis(const double d[3], double Y[16]) { sh_basis(d, Y); }

@@ -57,6 +57,9 @@ def lib():
             L.orc_raht_forward.argtypes = [p, i64, i32, i32, p, p]
             L.orc_raht_inverse.argtypes = [p, i64, i32, i32, p, p]
             L.orc_raht_node_weights.argtypes = [p, i64, i32, p]
+            L.orc_render.argtypes = [p, p, i64, p, f64, f64, f64, f64, i32, i32, f64, p, p]
+            L.orc_sh_basis.argtypes = [p, p]
+            L.orc_render.restype = i32
             L.orc_lod.argtypes = [p, i64, i32, i32, i32, p, p, f64, p, p, p, p]
             L.orc_lod.restype = i64
             L.orc_raht_lowpass.argtypes = [p, i64, i32, i32, p, i32, p, p]
@@ -230,6 +233,25 @@ def raht_lowpass(codes, A, J, level):
     w = np.zeros(max(nv, 1), dtype=np.int64)
     k = _check(lib().orc_raht_lowpass(_p(codes), nv, J, C, _p(A), level, _p(out), _p(w)))
     return out[:k, :C], w[:k]
+
+
+def sh_basis(d):
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    Y = np.zeros(16)
+    lib().orc_sh_basis(_p(d), _p(Y))
+    return Y
+
+
+def render(pos, attr, view, fx, fy, cx, cy, width, height, znear=0.01, bg=(0.0, 0.0, 0.0)):
+    """FP64 splat rasteriser (image [H, W, 3]) of 56-channel Gaussians; view = 3 x 4 world-to-camera [R | t]."""
+    pos = np.ascontiguousarray(pos, dtype=np.float32).reshape(-1, 3)
+    attr = np.ascontiguousarray(attr, dtype=np.float32).reshape(-1, 56)
+    view = np.ascontiguousarray(view, dtype=np.float64).reshape(3, 4)
+    bg = np.ascontiguousarray(bg, dtype=np.float64)
+    img = np.zeros((height, width, 3), dtype=np.float64)
+    _check(lib().orc_render(_p(pos), _p(attr), pos.shape[0], _p(view), float(fx), float(fy), float(cx), float(cy),
+                            width, height, float(znear), _p(bg), _p(img)))
+    return img
 
 
 def raht_node_weights(codes, J):

@@ -1,0 +1,74 @@
+"""Oracle splat rasteriser (the renderer behind rendered-view PSNR): pinned
+by the orthonormality of its real SH basis on the sphere, closed-form pixels
+of one projected Gaussian (EWA footprint with the 0.3 px dilation), the SH
+colour of a known direction, front-to-back occlusion, the background of an
+empty or culled scene."""
+import numpy as np
+
+VIEW = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]], dtype=np.float64)  # camera at the origin, +z
+
+
+def _gauss(pos, logscale, logit, dc, ac=None):
+    a = np.zeros(56, dtype=np.float32)
+    a[0:3] = logscale
+    a[3] = 1.0  # identity rotation
+    a[7] = logit
+    a[8:11] = dc
+    if ac is not None:
+        a[11:56] = ac
+    return np.array(pos, dtype=np.float32), a
+
+
+def test_sh_basis_is_orthonormal(orc):
+    n = 200_000  # Fibonacci sphere quadrature
+    k = np.arange(n) + 0.5
+    z = 1 - 2 * k / n
+    phi = np.pi * (1 + 5 ** 0.5) * k
+    r = np.sqrt(1 - z * z)
+    d = np.stack([r * np.cos(phi), r * np.sin(phi), z], 1)
+    Y = np.array([orc.sh_basis(x) for x in d[:: 20]])  # 10,000 points
+    G = Y.T @ Y * (4 * np.pi / Y.shape[0])
+    assert np.abs(G - np.eye(16)).max() < 5e-3
+
+
+def test_single_gaussian_closed_form(orc):
+    f, W, H = 100.0, 64, 64
+    s, zc = 0.02, 2.0
+    p, a = _gauss([0, 0, zc], np.log(s), 0.0, [1.0, -1.0, 0.5])  # opacity 0.5
+    bg = np.array([0.1, 0.2, 0.3])
+    img = orc.render(p[None], a[None], VIEW, f, f, W / 2 + 0.5, H / 2 + 0.5, W, H, bg=bg)
+    # the mean projects to the centre of pixel (32, 32); footprint variance (f s / z)^2 + 0.3
+    var = (f * s / zc) ** 2 + 0.3
+    c0 = 0.5 / np.sqrt(np.pi)
+    col = np.maximum(c0 * np.array([1.0, -1.0, 0.5]) + 0.5, 0)
+    for dx, dy in ((0, 0), (1, 0), (0, 2), (2, 1), (-1, -1)):
+        alpha = min(0.99, 0.5 * np.exp(-(dx * dx + dy * dy) / (2 * var)))
+        want = col * alpha + (1 - alpha) * bg if alpha >= 1 / 255 else bg
+        assert np.allclose(img[32 + dy, 32 + dx], want, atol=1e-12), (dx, dy)
+    assert np.allclose(img[0, 0], bg)  # outside the footprint square's tiles
+
+
+def test_view_dependent_colour(orc):
+    ac = np.zeros(45, dtype=np.float32)
+    ac[1] = 0.3  # R, degree 1, the z-term (AC function 2)
+    p, a = _gauss([0, 0, 2.0], np.log(0.05), 20.0, [0, 0, 0], ac)  # opaque (alpha capped at 0.99)
+    img = orc.render(p[None], a[None], VIEW, 100, 100, 32.5, 32.5, 64, 64)
+    y = orc.sh_basis([0, 0, 1.0])
+    assert np.isclose(img[32, 32, 0], 0.99 * (0.5 + 0.3 * y[2]))
+    assert np.isclose(img[32, 32, 1], 0.99 * 0.5)
+
+
+def test_front_to_back_occlusion_and_empty(orc):
+    p1, a1 = _gauss([0, 0, 2.0], np.log(0.05), 20.0, [1.5, -1.5, -1.5])
+    p2, a2 = _gauss([0, 0, 3.0], np.log(0.05), 20.0, [-1.5, -1.5, 1.5])
+    for order in ((0, 1), (1, 0)):  # input order does not matter, depth does
+        P = np.stack([p1, p2])[list(order)]
+        A = np.stack([a1, a2])[list(order)]
+        img = orc.render(P, A, VIEW, 100, 100, 32.5, 32.5, 64, 64)
+        c1 = np.maximum(0.5 / np.sqrt(np.pi) * np.array([1.5, -1.5, -1.5]) + 0.5, 0)
+        c2 = np.maximum(0.5 / np.sqrt(np.pi) * np.array([-1.5, -1.5, 1.5]) + 0.5, 0)
+        assert np.allclose(img[32, 32], 0.99 * c1 + 0.01 * 0.99 * c2)
+    bg = np.array([0.3, 0.4, 0.5])
+    assert np.allclose(orc.render(np.zeros((0, 3)), np.zeros((0, 56)), VIEW, 100, 100, 32, 32, 32, 32, bg=bg), bg)
+    behind, ab = _gauss([0, 0, -1.0], np.log(0.05), 20.0, [1, 1, 1])
+    assert np.allclose(orc.render(behind[None], ab[None], VIEW, 100, 100, 16, 16, 32, 32, bg=bg), bg)
