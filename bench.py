@@ -402,6 +402,29 @@ def gpu_extras(args, G, torch, P, A, frames, qp, out, offs, dev, stream):
         n_nodes = G.decode_frame_lod(s0, depth)[0].shape[0]
         lod[str(depth)] = {"ms": round(statistics.median(t), 3), "nodes": int(n_nodes)}
     res["lod_decode"] = lod
+    # rendered-view quality (Sec. 5.1): PSNR of renders of the decoded frame against renders of the
+    # original Gaussians, 960 x 540 from 3 orbit views, per quantisation rung; and the rasteriser's own time
+    views = syn.orbit_views(3, radius=1.2)
+    Wr, Hr, fr = 960, 540, 1000.0
+    p0, a0 = P[0], A[0]
+    ref_imgs = [G.render(p0, a0, v, fr, fr, Wr / 2, Hr / 2, Wr, Hr).clamp_(0, 1) for v in views]
+    img_buf = torch.empty((Hr, Wr, 3), dtype=torch.float32, device=dev)
+    tr = _timed_calls(torch, stream, lambda _=0: G.render(p0, a0, views[0], fr, fr, Wr / 2, Hr / 2, Wr, Hr,
+                                                          out=img_buf), 5)
+    rq = {"gaussians": int(p0.shape[0]), "views": len(views), "image": [Wr, Hr],
+          "render_ms": round(statistics.median(tr), 3), "rungs": []}
+    for sc in (0.5, 1.0, 2.0, 4.0):
+        qr = G.QuantParams(syn.gs_channel_groups(), np.array(syn.GS_BASE_STEPS) * sc)
+        bsr, *_ = G.encode_frame(p0, a0, J, qr)
+        dpos, datt = G.decode_frame(bsr)
+        ps = []
+        for v, ref in zip(views, ref_imgs):
+            img = G.render(dpos, datt.contiguous(), v, fr, fr, Wr / 2, Hr / 2, Wr, Hr).clamp_(0, 1)
+            mse = float(((img - ref) ** 2).mean())
+            ps.append(10 * np.log10(1.0 / max(mse, 1e-20)))
+        rq["rungs"].append({"step_scale": sc, "bits_per_gaussian": round(8 * bsr.numel() / p0.shape[0], 2),
+                            "psnr_db": round(float(np.mean(ps)), 2)})
+    res["rendered_quality"] = rq
     # end to end: pinned host inputs -> H2D -> encode -> D2H streams -> decode -> D2H frames
     hp = [torch.from_numpy(p).pin_memory() for p, _ in frames]
     ha = [torch.from_numpy(a).pin_memory() for _, a in frames]

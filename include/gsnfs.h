@@ -156,6 +156,40 @@ gsnfs_status gsnfs_decode_frame_lod(gsnfs_ctx *ctx, void *stream, const uint8_t 
                                     uint32_t depth, float *d_pos, float *d_attr, uint64_t capacity_nodes,
                                     uint64_t *out_nodes);
 
+/* Pinhole camera of the splat rasteriser.  view is the 3 x 4 world-to-camera
+ * matrix [R | t] in row-major order (camera looks along +z, image x right,
+ * y down); pixel (px, py) has its centre at (px + 0.5, py + 0.5); points with
+ * camera depth <= znear (> 0) are culled; background is the RGB behind all
+ * splats. */
+typedef struct {
+    double view[12];
+    double fx, fy, cx, cy;
+    uint32_t width, height;  /* 1 .. 16384 */
+    double znear;
+    double background[3];
+} gsnfs_camera;
+
+/* Splat rasteriser used to measure rendered-view quality of decoded frames
+ * (Sec. 5.1 scores decoded frames by the PSNR of their renders against
+ * renders of the uncompressed Gaussians).  Standard 3DGS forward pass: per Gaussian, the projected mean,
+ * the EWA 2-D covariance J W Sigma W^T J^T + 0.3 I, a square footprint of
+ * radius ceil(3 sqrt(largest eigenvalue)) over 16 x 16-pixel tiles, opacity
+ * sigmoid(logit) and a degree-3 real-SH colour (+0.5, clamped at 0) seen
+ * from the camera centre; per pixel, front-to-back alpha compositing over the
+ * Gaussians whose footprint covers its tile, ordered by depth then index,
+ * alpha = min(0.99, opacity exp(-d^T conic d / 2)), skipping alpha < 1/255
+ * and stopping before transmittance falls below 1e-4.
+ * d_pos (n x 3) and d_attr (n x 56: log-scales 0-2, rotation w x y z 3-6,
+ * opacity logit 7, SH DC RGB 8-10, SH AC 11-55 as R[15] G[15] B[15]) are
+ * device float32; d_image (device) receives height x width x 3 float32, row
+ * major.  Work is FP32.  Scratch is owned by ctx and grown on demand; the call
+ * synchronises the stream once (to size the tile lists).  Errors:
+ * GSNFS_ERR_INVALID_ARG (null or misaligned pointers, image size or znear out
+ * of range), GSNFS_ERR_CAPACITY (more than 2^32 - 1 tile entries),
+ * GSNFS_ERR_OOM, GSNFS_ERR_CUDA. */
+gsnfs_status gsnfs_render(gsnfs_ctx *ctx, void *stream, const float *d_pos, const float *d_attr, uint64_t n,
+                          const gsnfs_camera *cam, float *d_image);
+
 /* Batched bandwidth ladder (frames x rungs): encodes `frames` frames, frame f
  * with n[f] points at depth J[f] (16..19 supported together, any mix),
  * each at `rungs` quantisation rungs whose steps are q->steps scaled by

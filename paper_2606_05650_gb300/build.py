@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgsnfs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["voxel.cu", "sort.cu", "geometry.cu", "raht.cu", "rlgr.cu", "rans.cu", "scan.cu", "api.cu", "noalloc.cu", "batchdec.cu", "lod.cu", "color.cu"]
+SOURCES = ["voxel.cu", "sort.cu", "geometry.cu", "raht.cu", "rlgr.cu", "rans.cu", "scan.cu", "api.cu", "noalloc.cu", "batchdec.cu", "lod.cu", "color.cu", "render.cu"]
 
 
 def nvcc() -> str:

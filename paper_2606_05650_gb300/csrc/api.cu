@@ -120,6 +120,9 @@ struct gsnfs_ctx {
     // level-of-detail scratch (full-depth attributes, node index), grown on demand
     void *lod = nullptr;
     size_t lod_cap = 0;
+    // splat-rasteriser scratch: per-Gaussian arrays and the per-tile key lists, grown on demand
+    void *rnd = nullptr, *rkeys = nullptr;
+    size_t rnd_cap = 0, rkeys_cap = 0;
     // second stream for the independent branches of one call (geometry and attributes)
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -1574,6 +1577,8 @@ void gsnfs_destroy(gsnfs_ctx *ctx)
     cudaDeviceSynchronize();
     drop_graphs(ctx);
     if (ctx->lod) cudaFree(ctx->lod);
+    if (ctx->rnd) cudaFree(ctx->rnd);
+    if (ctx->rkeys) cudaFree(ctx->rkeys);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
@@ -2428,3 +2433,99 @@ gsnfs_status gsnfs_profile_read(double *ms, uint64_t *count, int cap)
 }
 
 }  // extern "C"
+
+namespace {
+// grows a context-owned scratch buffer to at least `need` bytes (contents not kept)
+gsnfs_status grow(void **buf, size_t *cap, size_t need)
+{
+    if (need <= *cap) return GSNFS_OK;
+    if (*buf) CK(cudaFree(*buf));
+    *buf = nullptr;
+    *cap = 0;
+    CK(cudaMalloc(buf, need));
+    *cap = need;
+    return GSNFS_OK;
+}
+}  // namespace
+
+gsnfs_status gsnfs_render(gsnfs_ctx *ctx, void *stream, const float *d_pos, const float *d_attr, uint64_t n,
+                          const gsnfs_camera *cam, float *d_image)
+{
+    if (!ctx || !cam || !d_image || (n && (!d_pos || !d_attr))) return GSNFS_ERR_INVALID_ARG;
+    if ((uintptr_t)d_pos % 4 || (uintptr_t)d_attr % 4 || (uintptr_t)d_image % 4) return GSNFS_ERR_INVALID_ARG;
+    if (cam->width == 0 || cam->height == 0 || cam->width > 16384 || cam->height > 16384) return GSNFS_ERR_INVALID_ARG;
+    if (!(cam->znear > 0.0) || n >= (1ull << 32)) return GSNFS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int sms = ctx->num_sms;
+    RenderCam rc;
+    const double *V = cam->view;
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) rc.R[3 * r + c] = (float)V[4 * r + c];
+        rc.t[r] = (float)V[4 * r + 3];
+    }
+    for (int c = 0; c < 3; ++c)  // camera centre -R^T t, in FP64
+        rc.campos[c] = (float)(-(V[c] * V[3] + V[4 + c] * V[7] + V[8 + c] * V[11]));
+    rc.fx = (float)cam->fx;
+    rc.fy = (float)cam->fy;
+    rc.cx = (float)cam->cx;
+    rc.cy = (float)cam->cy;
+    rc.znear = (float)cam->znear;
+    rc.W = (int)cam->width;
+    rc.H = (int)cam->height;
+    rc.TX = (rc.W + 15) / 16;
+    rc.TY = (rc.H + 15) / 16;
+    for (int c = 0; c < 3; ++c) rc.bg[c] = (float)cam->background[c];
+    const uint64_t tiles = (uint64_t)rc.TX * rc.TY;
+    const uint64_t m = n ? n : 1;
+    auto carve1 = [&](Carve &cv, void **sp, float **depth, int4 **rect, uint32_t **count, uint64_t **offs,
+                      uint64_t **part, uint2 **ranges) {
+        *sp = cv.take<unsigned char>(m * render_splat_bytes());
+        *depth = cv.take<float>(m);
+        *rect = cv.take<int4>(m);
+        *count = cv.take<uint32_t>(m);
+        *offs = cv.take<uint64_t>(m + 2);
+        *part = cv.take<uint64_t>(scan_partial_words(m, sms) + 1);
+        *ranges = cv.take<uint2>(tiles);
+        return cv.off;
+    };
+    void *sp;
+    float *depth;
+    int4 *rect;
+    uint32_t *count;
+    uint64_t *offs, *part;
+    uint2 *ranges;
+    Carve m1(nullptr);
+    gsnfs_status st = grow(&ctx->rnd, &ctx->rnd_cap, carve1(m1, &sp, &depth, &rect, &count, &offs, &part, &ranges));
+    if (st) return st;
+    Carve c1(ctx->rnd);
+    carve1(c1, &sp, &depth, &rect, &count, &offs, &part, &ranges);
+    uint64_t total = 0;
+    if (n) {
+        launch_render_prepare(d_pos, d_attr, n, rc, sp, depth, rect, count, offs, part, sms, s);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&total, offs + n, 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (total >= (1ull << 32)) return GSNFS_ERR_CAPACITY;
+    }
+    const uint64_t mt = total ? total : 1;
+    auto carve2 = [&](Carve &cv, uint64_t **k, uint32_t **v, uint64_t **ka, uint32_t **va, uint32_t **hist) {
+        *k = cv.take<uint64_t>(mt);
+        *ka = cv.take<uint64_t>(mt);
+        *v = cv.take<uint32_t>(mt);
+        *va = cv.take<uint32_t>(mt);
+        *hist = cv.take<uint32_t>(radix_sort_hist_words(mt, sms));
+        return cv.off;
+    };
+    uint64_t *keys, *keys_alt;
+    uint32_t *vals, *vals_alt, *hist;
+    Carve m2(nullptr);
+    st = grow(&ctx->rkeys, &ctx->rkeys_cap, carve2(m2, &keys, &vals, &keys_alt, &vals_alt, &hist));
+    if (st) return st;
+    Carve c2(ctx->rkeys);
+    carve2(c2, &keys, &vals, &keys_alt, &vals_alt, &hist);
+    launch_render_tiles(n, rect, depth, count, offs, total, rc, sp, keys, vals, keys_alt, vals_alt, hist, ranges,
+                        d_image, sms, s);
+    CK(cudaGetLastError());
+    return GSNFS_OK;
+}

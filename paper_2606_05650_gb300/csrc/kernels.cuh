@@ -285,6 +285,22 @@ void launch_lod_nodes(const uint64_t *codes, const uint64_t *starts, const uint6
                       uint64_t n_nodes, uint32_t sh, uint32_t Jp, uint32_t C, const float *attr, const LodGrid &g,
                       float *pos, float *out, int num_sms, cudaStream_t s);
 
+// ---- render.cu: splat rasteriser ------------------------------------------------
+struct RenderCam {
+    float R[9], t[3], campos[3];
+    float fx, fy, cx, cy, znear;
+    int W, H, TX, TY;
+    float bg[3];
+};
+size_t render_splat_bytes();
+void launch_render_prepare(const float *pos, const float *attr, uint64_t n, const RenderCam &cam, void *splats,
+                           float *depth, int4 *rect, uint32_t *count, uint64_t *offs, uint64_t *partials,
+                           int num_sms, cudaStream_t s);
+void launch_render_tiles(uint64_t n, const int4 *rect, const float *depth, const uint32_t *count,
+                         const uint64_t *offs, uint64_t total, const RenderCam &cam, const void *splats,
+                         uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint32_t *hist,
+                         uint2 *ranges, float *image, int num_sms, cudaStream_t s);
+
 // ---- scan.cu / api.cu helpers -------------------------------------------
 // exclusive scan of n u32 values into u64 offsets (out has n + 1 entries)
 void launch_scan_u32_to_u64(const uint32_t *in, uint64_t n, uint64_t *out, uint64_t *partials, int num_sms,

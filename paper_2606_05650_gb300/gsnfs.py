@@ -65,6 +65,7 @@ def lib():
                 "gsnfs_encode_batch_rd": ([p, p, u32, p, p, p, p, u32, p, Q, p, u64, p, p], i32),
                 "gsnfs_decode_batch": ([p, p, u32, p, p, p, p, u64, p], i32),
                 "gsnfs_decode_frame_lod": ([p, p, p, u64, u32, p, p, u64, P64], i32),
+                "gsnfs_render": ([p, p, p, p, u64, ct.POINTER(Camera), p], i32),
                 "gsnfs_voxelize": ([p, p, p, u64, u32, p, p, P64], i32),
                 "gsnfs_octree_encode": ([p, p, p, u64, u32, p, u64, p, P64], i32),
                 "gsnfs_octree_decode": ([p, p, p, u64, u32, p, p], i32),
@@ -306,6 +307,35 @@ def decode_frame_lod(bitstream: torch.Tensor, depth: int):
                                         _ptr(pos), _ptr(attr), max(nv, 1), ct.byref(n)), "gsnfs_decode_frame_lod")
     k = n.value
     return pos[:k], (attr[:k, :C] if attr is not None else None)
+
+
+class Camera(ct.Structure):
+    """gsnfs_camera: 3 x 4 world-to-camera [R | t] (row major), pinhole intrinsics, image size, near plane, background."""
+    _fields_ = [("view", ct.c_double * 12), ("fx", ct.c_double), ("fy", ct.c_double), ("cx", ct.c_double),
+                ("cy", ct.c_double), ("width", ct.c_uint32), ("height", ct.c_uint32), ("znear", ct.c_double),
+                ("background", ct.c_double * 3)]
+
+
+def render(pos: torch.Tensor, attr: torch.Tensor, view, fx, fy, cx, cy, width: int, height: int, znear=0.01,
+           background=(0.0, 0.0, 0.0), out: torch.Tensor | None = None):
+    """gsnfs_render: splat-rasterised image [height, width, 3] (float32) of n 56-channel Gaussians."""
+    _cuda_f32(pos, 3)
+    _cuda_f32(attr, 56)
+    if pos.shape[0] != attr.shape[0]:
+        raise ValueError("pos and attr row counts differ")
+    cam = Camera()
+    v = np.asarray(view, dtype=np.float64).reshape(12)
+    cam.view[:] = [float(x) for x in v]
+    cam.fx, cam.fy, cam.cx, cam.cy = float(fx), float(fy), float(cx), float(cy)
+    cam.width, cam.height, cam.znear = int(width), int(height), float(znear)
+    cam.background[:] = [float(x) for x in background]
+    if out is None:
+        out = torch.empty((height, width, 3), dtype=torch.float32, device=pos.device)
+    elif out.shape != (height, width, 3) or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float32 [height, width, 3] tensor")
+    _check(lib().gsnfs_render(context(pos.device), _stream(pos), _ptr(pos), _ptr(attr), pos.shape[0], ct.byref(cam),
+                              _ptr(out)), "gsnfs_render")
+    return out
 
 
 def decode_batch(data: torch.Tensor, offsets, C: int, rows_cap: int):

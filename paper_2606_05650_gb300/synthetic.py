@@ -227,3 +227,28 @@ def ladder_sizes(seed: int, frames: int = 64, lo: int = 50_000, hi: int = 2_000_
 
 
 LADDER_RUNG_SCALES = np.array([1.0, 2.0, 4.0, 8.0, 16.0])
+
+
+def look_at_view(eye, target, up=(0.0, 0.0, 1.0)) -> np.ndarray:
+    """3 x 4 world-to-camera [R | t] (FP64) of a pinhole camera at `eye`
+    looking at `target`: camera z forward, x right, y down (image rows)."""
+    eye, target, up = (np.asarray(v, dtype=np.float64) for v in (eye, target, up))
+    z = target - eye
+    z /= np.linalg.norm(z)
+    x = np.cross(z, up)
+    x /= np.linalg.norm(x)
+    y = np.cross(z, x)
+    R = np.stack([x, y, z])
+    return np.concatenate([R, (-R @ eye)[:, None]], 1)
+
+
+def orbit_views(k: int, centre=(0.5, 0.5, 0.5), radius: float = 1.6, elevation: float = 0.35):
+    """k test views on a circle around `centre` (the stand-in for a scene's
+    held-out camera poses)."""
+    c = np.asarray(centre, dtype=np.float64)
+    out = []
+    for i in range(k):
+        a = 2 * np.pi * (i + 0.25) / k
+        eye = c + radius * np.array([np.cos(a) * np.cos(elevation), np.sin(a) * np.cos(elevation), np.sin(elevation)])
+        out.append(look_at_view(eye, c))
+    return out
