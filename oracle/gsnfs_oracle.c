@@ -402,7 +402,7 @@ void orc_raht_inverse(const uint64_t *M, int64_t nv, int J, int C, const double 
     if (nv > 1) raht_inv_rec(&cx, 0, nv, 3 * J);
 }
 
-/* Level of detail (decoding to octree depth Jp <= J; A.2's shift read as
+/* Level of detail (decoding to octree depth Jp <= J; Algorithm 2's shift read as
  * J - Jp): the nodes of depth Jp are the distinct codes >> 3(J - Jp); each
  * gets the centre of its cell at depth Jp and the FP64 mean of its voxels'
  * attributes.  Returns the node count.                                      */

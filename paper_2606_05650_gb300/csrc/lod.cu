@@ -1,5 +1,5 @@
 // Level of detail: a decoded frame reduced to the nodes of octree depth Jp
-// (A.2's shift read as J - Jp).  A node is the run of voxels sharing
+// (Algorithm 2's shift read as J - Jp).  A node is the run of voxels sharing
 // code >> 3(J - Jp); it is placed at the centre of its cell at depth Jp and
 // carries the mean of its voxels' decoded attributes, which by Eq. (1) is
 // its RAHT low-pass coefficient divided by sqrt(voxel count).
