@@ -104,8 +104,13 @@ gsnfs_status gsnfs_graph_stats(gsnfs_ctx *ctx, uint64_t *out);
  *                            [256, 4096] (default: largest whose C rows fit
  *                            56 KB of shared memory, at least 256)
  *   GSNFS_TUNE_RAHT_GRID     CTAs per SM of the first transform pass, 1..32 (4)
- *   GSNFS_TUNE_PRELUDE_GRID  CTAs per SM of the prelude tile passes, 1..32 (8) */
-enum { GSNFS_TUNE_RAHT_TILE = 0, GSNFS_TUNE_RAHT_GRID = 1, GSNFS_TUNE_PRELUDE_GRID = 2 };
+ *   GSNFS_TUNE_PRELUDE_GRID  CTAs per SM of the prelude tile passes, 1..32 (8)
+ *   GSNFS_TUNE_RAHT_PIPE     first pass of FP32 transforms, where its
+ *                            buffers fit shared memory: 0 software-pipelined
+ *                            metadata (three CTAs per SM), 1 plain, 2 deep
+ *                            pipeline (one CTA per SM, rows of the next two
+ *                            tiles in flight) */
+enum { GSNFS_TUNE_RAHT_TILE = 0, GSNFS_TUNE_RAHT_GRID = 1, GSNFS_TUNE_PRELUDE_GRID = 2, GSNFS_TUNE_RAHT_PIPE = 3 };
 gsnfs_status gsnfs_tune_set(gsnfs_ctx *ctx, int which, uint32_t value);
 gsnfs_status gsnfs_tune_get(gsnfs_ctx *ctx, int which, uint32_t *value);
 

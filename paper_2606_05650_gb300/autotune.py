@@ -1,7 +1,8 @@
 """Autotuner of the codec's launch shapes.
 
 The tunables (gsnfs_tune_set: RAHT tile size, CTAs per SM of the first
-transform pass and of the prelude tile passes) change how the work is tiled
+transform pass and of the prelude tile passes, pipelined or plain first
+transform pass) change how the work is tiled
 and spread over the 152 SMs, never what is computed, so the tuner may pick
 any of them: it checks on every candidate that the bitstreams and the decoded
 frames are byte-identical to the default's and drops a candidate that is not.
@@ -19,8 +20,8 @@ import json
 import math
 import os
 
-ORDER = ("raht_tile", "raht_grid", "prelude_grid")
-CANDIDATES = {"raht_tile": [0, 512, 1024], "raht_grid": [0, 2, 3, 6, 8], "prelude_grid": [0, 4, 16]}
+ORDER = ("raht_pipe", "raht_tile", "raht_grid", "prelude_grid")
+CANDIDATES = {"raht_pipe": [0, 1, 2], "raht_tile": [0, 512, 1024], "raht_grid": [0, 2, 3, 6, 8], "prelude_grid": [0, 4, 16]}
 
 
 def default_cache_path() -> str:

@@ -116,7 +116,7 @@ struct gsnfs_ctx {
     size_t pinned_cap = 0;
     DevState *st = nullptr;
     // launch-shape tunables (gsnfs_tune_set); 0 = built-in default
-    uint32_t tune[3] = {0, 0, 0};
+    uint32_t tune[4] = {0, 0, 0, 0};
     // level-of-detail scratch (full-depth attributes, node index), grown on demand
     void *lod = nullptr;
     size_t lod_cap = 0;
@@ -537,7 +537,7 @@ struct EncodeReq {
 
 struct EncLayout {
     FrameGrid *grid;
-    uint32_t *Jd, *vstart, *lsz, *hoff, *mode, *dpart, *opart, *seg, *vals, *vals_alt, *hist, *chunk_words,
+    uint32_t *Jd, *vstart, *lsz, *hoff, *mode, *dpart, *opart, *seg, *row0, *vals, *vals_alt, *hist, *chunk_words,
         *chunk_top, *chunk_pos, *cum, *slots, *block_words, *overflow;
     const float **posp, **attrp;
     uint64_t *poff, *keys, *keys_alt, *codes, *occ_off, *chunk_off, *sec_bytes, *job_off, *blk_off, *block_off,
@@ -557,6 +557,7 @@ void carve_plan(Carve &cv, RahtPlanDev &p, uint64_t nv_cap, uint32_t T, const ui
     if (tune && tune[GSNFS_TUNE_RAHT_TILE]) T = tune[GSNFS_TUNE_RAHT_TILE];
     p.xgrid_mult = tune ? tune[GSNFS_TUNE_RAHT_GRID] : 0u;
     p.pgrid_mult = tune ? tune[GSNFS_TUNE_PRELUDE_GRID] : 0u;
+    p.xpipe_off = tune ? tune[GSNFS_TUNE_RAHT_PIPE] : 0u;
     uint64_t elems, tiles, surv;
     raht_plan_sizes(nv_cap, T, &elems, &tiles, &surv);
     p.T = T;
@@ -630,6 +631,7 @@ size_t carve_encode(Carve &cv, EncLayout &L, const EncodeReq &rq, int num_sms, b
     L.hist = cv.take<uint32_t>(radix_sort_hist_words(N, num_sms));
     L.codes = cv.take<uint64_t>(N + 1);
     L.seg = cv.take<uint32_t>(N + 2);
+    L.row0 = cv.take<uint32_t>(N + 1);
     L.gap = cv.take<uint8_t>(N + 2);
     L.dpart = cv.take<uint32_t>(dedup_partial_words(N, num_sms) + 1);
     L.occ = cv.take<uint8_t>(L.occ_cap);
@@ -639,7 +641,7 @@ size_t carve_encode(Carve &cv, EncLayout &L, const EncodeReq &rq, int num_sms, b
     L.chunk_top = cv.take<uint32_t>(max_chunks + 1);
     L.chunk_pos = cv.take<uint32_t>(max_chunks + 1);
     if (C) {
-        uint32_t tune_c[3] = {tune ? tune[0] : 0u, tune ? tune[1] : 0u, tune ? tune[2] : 0u};
+        uint32_t tune_c[4] = {tune ? tune[0] : 0u, tune ? tune[1] : 0u, tune ? tune[2] : 0u, tune ? tune[3] : 0u};
         if (rq.q->color) tune_c[GSNFS_TUNE_RAHT_TILE] = 0;  // colour transforms need whole rows in a tile
         carve_plan(cv, L.plan, N, raht_tile_size(C), tune_c);
         uint64_t elems, tiles, surv;
@@ -817,7 +819,8 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
         const uint32_t *svals = alt ? L.vals_alt : L.vals;
         // a3: dedup
         stage_begin(s, kStDedup);
-        launch_dedup(skeys, N, frame_shift, F, L.codes, L.seg, L.gap, L.vstart, L.dpart, dst, sms, s);
+        launch_dedup(skeys, N, frame_shift, F, L.codes, L.seg, L.gap, L.vstart, L.dpart, dst, sms, s,
+                     C ? svals : nullptr, L.row0);
         stage_end(s, kStDedup);
         // a4 + a5 (geometry) run beside a6-a9 (attributes) on the context's second stream
         cudaStream_t ga = nullptr;
@@ -849,6 +852,7 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
             io.C = C;
             io.seg = L.seg;
             io.vals = svals;
+            io.row0 = L.row0;
             io.codes = L.codes;
             io.attr = L.attrp;
             io.center = L.center;
@@ -1134,7 +1138,7 @@ size_t carve_decode(Carve &cv, DecLayout &L, const ParsedHeader &P, int num_sms,
     L.klt = cv.take<float>(kKltFloats);
     L.vst = cv.take<uint32_t>(2);
     if (P.C && P.nv) {
-        uint32_t tune_c[3] = {tune ? tune[0] : 0u, tune ? tune[1] : 0u, tune ? tune[2] : 0u};
+        uint32_t tune_c[4] = {tune ? tune[0] : 0u, tune ? tune[1] : 0u, tune ? tune[2] : 0u, tune ? tune[3] : 0u};
         if (P.color) tune_c[GSNFS_TUNE_RAHT_TILE] = 0;  // colour transforms need whole rows in a tile
         carve_plan(cv, L.plan, P.nv, raht_tile_size(P.C), tune_c);
         uint64_t elems, tiles, surv;
@@ -1345,7 +1349,7 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         L.klt = cv.take<float>((any_color ? (uint64_t)F : 1) * kKltFloats);
         L.fcolor = cv.take<uint32_t>(F + 1);
         if (C) {
-            uint32_t tune_c[3] = {ctx->tune[0], ctx->tune[1], ctx->tune[2]};
+            uint32_t tune_c[4] = {ctx->tune[0], ctx->tune[1], ctx->tune[2], ctx->tune[3]};
             if (any_color) tune_c[GSNFS_TUNE_RAHT_TILE] = 0;  // colour transforms need whole rows in a tile
             carve_plan(cv, L.plan, N, raht_tile_size(C), tune_c);
             uint64_t elems, tiles, surv;
@@ -1605,7 +1609,8 @@ gsnfs_status gsnfs_set_graphs(gsnfs_ctx *ctx, int enable)
 
 gsnfs_status gsnfs_tune_set(gsnfs_ctx *ctx, int which, uint32_t value)
 {
-    if (!ctx || which < 0 || which > GSNFS_TUNE_PRELUDE_GRID) return GSNFS_ERR_INVALID_ARG;
+    if (!ctx || which < 0 || which > GSNFS_TUNE_RAHT_PIPE) return GSNFS_ERR_INVALID_ARG;
+    if (which == GSNFS_TUNE_RAHT_PIPE && value > 2) return GSNFS_ERR_INVALID_ARG;
     if (which == GSNFS_TUNE_RAHT_TILE && value && (!pow2(value) || value < 256 || value > 4096))
         return GSNFS_ERR_INVALID_ARG;
     if (which != GSNFS_TUNE_RAHT_TILE && value > 32) return GSNFS_ERR_INVALID_ARG;
@@ -1620,7 +1625,7 @@ gsnfs_status gsnfs_tune_set(gsnfs_ctx *ctx, int which, uint32_t value)
 
 gsnfs_status gsnfs_tune_get(gsnfs_ctx *ctx, int which, uint32_t *value)
 {
-    if (!ctx || !value || which < 0 || which > GSNFS_TUNE_PRELUDE_GRID) return GSNFS_ERR_INVALID_ARG;
+    if (!ctx || !value || which < 0 || which > GSNFS_TUNE_RAHT_PIPE) return GSNFS_ERR_INVALID_ARG;
     *value = ctx->tune[which];
     return GSNFS_OK;
 }

@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(kThreads) dedup_up_kernel(const uint64_t *__re
 __global__ void __launch_bounds__(kThreads) dedup_down_kernel(const uint64_t *__restrict__ keys, uint64_t n,
                                                               uint64_t chunk, const uint32_t *partials,
                                                               uint32_t frame_shift, uint64_t *codes,
-                                                              uint32_t *seg, uint8_t *gap, uint32_t *vstart)
+                                                              uint32_t *seg, uint8_t *gap, uint32_t *vstart,
+                                                              const uint32_t *__restrict__ vals, uint32_t *row0)
 {
     __shared__ uint32_t sh[33];
     uint64_t b = (uint64_t)blockIdx.x * chunk, e = b + chunk;
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(kThreads) dedup_down_kernel(const uint64_t *__
             uint32_t g = (i == 0) ? kInfLevel : gap_level(kp, k, frame_shift);
             gap[v] = (uint8_t)g;
             if (g == kInfLevel) vstart[frame_shift < 64 ? (uint32_t)(k >> frame_shift) : 0u] = v;
+            if (row0) row0[v] = vals[i] | ((i + 1 < n && keys[i + 1] == k) ? kCarry : 0u);
         }
         if (ok && i == n - 1) {
             seg[v + (head ? 1u : 0u)] = (uint32_t)n;
@@ -528,8 +530,9 @@ uint64_t dedup_partial_words(uint64_t n, int num_sms) { return chunks_for(n, num
 
 void launch_dedup(const uint64_t *keys, uint64_t n, uint32_t frame_shift, uint32_t F, uint64_t *codes,
                   uint32_t *seg, uint8_t *gap, uint32_t *vstart, uint32_t *partials, DevState *st, int num_sms,
-                  cudaStream_t s)
+                  cudaStream_t s, const uint32_t *vals, uint32_t *row0)
 {
+    if (!vals) row0 = nullptr;
     cudaMemsetAsync(vstart, 0xFF, sizeof(uint32_t) * (F + 1), s);
     Chunks c = chunks_for(n, num_sms);
     if (n == 0) {
@@ -542,7 +545,7 @@ void launch_dedup(const uint64_t *keys, uint64_t n, uint32_t frame_shift, uint32
         scan_total_kernel<<<1, 1024, 0, s>>>(partials, c.P);
         count_launch();
         dedup_down_kernel<<<c.P, kThreads, 0, s>>>(keys, n, c.chunk, partials, frame_shift, codes, seg, gap,
-                                                   vstart);
+                                                   vstart, vals, row0);
         count_launch();
     }
     dedup_fix_kernel<<<1, 1, 0, s>>>(partials, c.P, vstart, F, st);

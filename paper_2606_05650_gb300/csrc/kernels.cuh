@@ -44,9 +44,10 @@ uint64_t radix_sort_hist_words(uint64_t n, int num_sms);
 // Dedup of sorted keys: codes[v], seg[v] (first sorted point of voxel v,
 // seg[nv] = n), gap[v] (gap level to v-1, kInfLevel at frame starts and at
 // gap[nv]), vstart[F+1] (voxel offset of each frame), nv -> st->nv_total.
+// row0 (optional, with vals): input row of each voxel's first point, | kCarry when the voxel holds several.
 void launch_dedup(const uint64_t *keys, uint64_t n, uint32_t frame_shift, uint32_t F, uint64_t *codes,
                   uint32_t *seg, uint8_t *gap, uint32_t *vstart, uint32_t *partials, DevState *st, int num_sms,
-                  cudaStream_t s);
+                  cudaStream_t s, const uint32_t *vals = nullptr, uint32_t *row0 = nullptr);
 uint64_t dedup_partial_words(uint64_t n, int num_sms);
 
 // Octree occupancy bytes of every frame, all levels at once (Algorithm 1).
@@ -100,6 +101,7 @@ struct RahtPlanDev {  // device pointers of a plan
     uint32_t T;            // tile size (elements)
     uint32_t xgrid_mult;   // transform pass 0: CTAs per SM (0 = default 4)
     uint32_t pgrid_mult;   // prelude tile passes: CTAs per SM (0 = default 8)
+    uint32_t xpipe_off;    // first transform pass: 0 pipelined metadata, 1 plain, 2 deep pipeline
     uint32_t cap_elems;    // capacity of the pooled sequence arrays
     uint32_t cap_tiles;
     uint32_t cap_surv;     // rows in the survivor pool
@@ -130,6 +132,8 @@ struct RahtIOT {  // S = float (codec) or double (FP64 instantiation of the same
     const S *in;            // forward: nv x C input rows (if gather == null)
     const uint32_t *seg;    // forward gather: first sorted point of each voxel
     const uint32_t *vals;   // forward gather: local point index of sorted points
+    const uint32_t *row0;   // forward gather: input row of each voxel's first point, | kCarry if it holds
+                            // several (or null)
     const uint64_t *codes;  // forward gather: voxel codes (frame id) for the attr pointer
     const S *const *attr;   // forward gather: per-frame attribute pointers
     const S *center;        // forward gather: per frame x C value subtracted from every voxel row, or null

@@ -397,17 +397,19 @@ __device__ __forceinline__ void cp_async_commit_wait_all()
 }
 
 // Eq. (1): forward (a*y0 + b*y1, a*y1 - b*y0); inverse (transposed) (a*y0 - b*y1, b*y0 + a*y1).
-// Each product and sum rounds once (no contraction), in the scalar type.
+// FP32: one rounded product, then a fused multiply-add (every kernel uses this
+// same sequence, so all FP32 paths agree bit for bit).  FP64: each product and
+// sum rounds once (no contraction).
 template <bool INV>
 __device__ __forceinline__ void rot(float a, float b, float &y0, float &y1)
 {
     const float u = y0, v = y1;
     if (!INV) {
-        y0 = __fadd_rn(__fmul_rn(a, u), __fmul_rn(b, v));
-        y1 = __fsub_rn(__fmul_rn(a, v), __fmul_rn(b, u));
+        y0 = __fmaf_rn(a, u, __fmul_rn(b, v));
+        y1 = __fmaf_rn(a, v, -__fmul_rn(b, u));
     } else {
-        y0 = __fsub_rn(__fmul_rn(a, u), __fmul_rn(b, v));
-        y1 = __fadd_rn(__fmul_rn(b, u), __fmul_rn(a, v));
+        y0 = __fmaf_rn(a, u, -__fmul_rn(b, v));
+        y1 = __fmaf_rn(b, u, __fmul_rn(a, v));
     }
 }
 
@@ -765,6 +767,393 @@ __global__ void __launch_bounds__(kXThreads, 3) xform_finish_kernel(XformArgs<S>
     }
 }
 
+// ---- software-pipelined first pass (FP32, whole rows in shared memory) -----
+// A CTA walks its tiles (blockIdx.x + k * gridDim.x) with NR row buffers and
+// NR + 1 metadata buffers, loads issued as cp.async groups ahead of use:
+//   NR = 1 (three CTAs per SM): the metadata of tile k + 1 lands while tile k
+//          is transformed; tile k + 1's rows are issued once tile k is stored;
+//   NR = 3 (one CTA per SM): the rows of tiles k + 1 and k + 2 and the
+//          metadata of tile k + 3 are in flight while tile k is transformed.
+// Per tile the arithmetic is that of xform_tile, in the same order, so the
+// results are bit-identical.
+
+struct PipeStage {
+    uint64_t *codes;  // T: voxel codes (frame id), forward gather of several frames
+    float2 *ab;       // T: butterfly coefficients
+    uint32_t *io;     // T: row destination (forward) or source (inverse)
+    uint32_t *row0;   // T: input row of the voxel's first point | kCarry (forward gather)
+    uint32_t *idx;    // T: butterfly i0 | i1 << 16
+    uint16_t *re;     // kRounds: end of each round
+    uint32_t *cnt;    // 2: butterflies, rounds
+};
+
+__host__ __device__ inline size_t pipe_meta_bytes(uint32_t T) { return ((size_t)28 * T + 2 * kRounds + 16 + 15) & ~(size_t)15; }
+
+// Row stride in shared memory (floats): rows are packed.
+__host__ __device__ inline uint32_t pipe_stride(uint32_t C) { return C; }
+
+__host__ __device__ inline size_t pipe_smem(uint32_t NR, uint32_t T, uint32_t C, bool color)
+{
+    return NR * (size_t)T * pipe_stride(C) * 4 + (NR + 1) * pipe_meta_bytes(T) +
+           (color ? 4 * (size_t)kKltFloats + 16 : 0);
+}
+
+__device__ __forceinline__ PipeStage pipe_stage(unsigned char *base, uint32_t T)
+{
+    PipeStage s;
+    s.codes = reinterpret_cast<uint64_t *>(base);
+    s.ab = reinterpret_cast<float2 *>(base + 8 * (size_t)T);
+    s.io = reinterpret_cast<uint32_t *>(base + 16 * (size_t)T);
+    s.row0 = s.io + T;
+    s.idx = s.row0 + T;
+    s.re = reinterpret_cast<uint16_t *>(base + 28 * (size_t)T);
+    s.cnt = reinterpret_cast<uint32_t *>(base + 28 * (size_t)T + 2 * kRounds);
+    return s;
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ float4 lds4(uint32_t a)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(a)
+                 : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts4(uint32_t a, float4 v)
+{
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
+}
+__device__ __forceinline__ void cp_async16_s(uint32_t sa, const void *gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ uint32_t pipe_rows(const RahtPass &ps, uint32_t T, uint32_t t)
+{
+    const uint64_t j0 = (uint64_t)t * T;
+    return (uint32_t)((ps.n - j0) < T ? (ps.n - j0) : T);
+}
+
+template <bool GATHER>
+__device__ void pipe_issue_meta(const XformArgs<float> &A, const RahtPass &ps, uint32_t t, const PipeStage &M)
+{
+    const RahtPlanDev &p = A.p;
+    const RahtIO &io = A.io;
+    const uint32_t T = p.T, m = pipe_rows(ps, T, t), tile = ps.tile_off + t;
+    const uint64_t j0 = (uint64_t)t * T;
+    for (uint32_t i = threadIdx.x; i < m; i += kXThreads) {
+        cp_async_vec<4>(M.io + i, p.dest + ps.seq_off + j0 + i);
+        if (GATHER) {
+            cp_async_vec<4>(M.row0 + i, io.row0 + j0 + i);
+            if (io.frame_shift < 64) cp_async_vec<8>(M.codes + i, io.codes + j0 + i);
+        }
+    }
+    // whole per-tile schedule arrays (T butterflies, kRounds round ends): the
+    // count is not known yet, the entries past it are never read
+    for (uint32_t k = threadIdx.x; k < T; k += kXThreads) {
+        cp_async_vec<4>(M.idx + k, p.bf_idx + (uint64_t)tile * T + k);
+        cp_async_vec<8>(M.ab + k, p.bf_ab + (uint64_t)tile * T + k);
+    }
+    if (threadIdx.x < 2 * kRounds / 16)
+        cp_async_vec<16>(reinterpret_cast<unsigned char *>(M.re) + 16 * threadIdx.x,
+                         reinterpret_cast<const unsigned char *>(p.round_end + (uint64_t)tile * kRounds) +
+                             16 * threadIdx.x);
+    if (threadIdx.x == 0) {
+        cp_async_vec<4>(M.cnt, p.tile_nbf + tile);
+        cp_async_vec<4>(M.cnt + 1, p.tile_nr + tile);
+    }
+}
+
+__device__ __forceinline__ uint32_t pipe_frame(const RahtIO &io, const PipeStage &M, uint32_t i)
+{
+    return io.frame_shift < 64 ? (uint32_t)(uint8_t)(M.codes[i] >> io.frame_shift) : 0u;
+}
+
+template <bool INV, bool GATHER>
+__device__ void pipe_issue_rows(const XformArgs<float> &A, const RahtPass &ps, const RahtPass &nx, uint32_t t,
+                                const PipeStage &M, float *R)
+{
+    const RahtIO &io = A.io;
+    const uint32_t T = A.p.T, C = io.C, m = pipe_rows(ps, T, t);
+    const uint64_t j0 = (uint64_t)t * T;
+    const uint32_t L = C / 4, slots = kXThreads / L, slot = threadIdx.x / L, lane = threadIdx.x - slot * L;
+    const uint32_t c = lane * 4;
+    if (slot >= slots) return;
+    const uint32_t rs = pipe_stride(C) * 4;  // row stride in bytes
+    uint32_t sa = smem_addr(R) + slot * rs + c * 4;
+    const float *base = nullptr;
+    uint32_t bfr = 0xFFFFFFFFu;
+    for (uint32_t i = slot; i < m; i += slots, sa += slots * rs) {
+        const float *src;
+        if (!INV) {
+            if (GATHER) {
+                const uint32_t fr = pipe_frame(io, M, i);
+                if (fr != bfr) {
+                    base = io.attr[fr] + c;
+                    bfr = fr;
+                }
+                src = base + (size_t)(M.row0[i] & ~kCarry) * C;
+            } else {
+                src = io.in + (j0 + i) * C + c;
+            }
+        } else {
+            const uint32_t d = M.io[i];
+            src = (d & kCarry) ? io.pool + ((uint64_t)nx.surv_off + (d & ~kCarry)) * C + c : io.Y + (uint64_t)d * C + c;
+        }
+        cp_async16_s(sa, src);
+    }
+}
+
+// Threads map to (row slot, 4-channel column): 14 consecutive threads cover a
+// 56-channel row, so every butterfly reads and writes whole rows contiguously.
+template <bool INV, bool GATHER, bool QDQ>
+__device__ void pipe_compute(const XformArgs<float> &A, const RahtPass &ps, const RahtPass &nx, uint32_t t,
+                             const PipeStage &M, float *R, float *klt_s, uint32_t &klt_fr)
+{
+    typedef Vec<float, 4> V4;
+    const RahtIO &io = A.io;
+    const uint32_t T = A.p.T, C = io.C, CP = pipe_stride(C), m = pipe_rows(ps, T, t);
+    const uint64_t j0 = (uint64_t)t * T;
+    const int tid = threadIdx.x;
+    const uint32_t L = C / 4, slots = kXThreads / L, slot = tid / L, lane = tid - slot * L;
+    const uint32_t c = lane * 4;
+    const bool act = slot < slots;
+    const uint32_t rs = CP * 4, sR = smem_addr(R), sbase = sR + c * 4;  // byte addresses in shared memory
+    const bool col_fwd = !INV && GATHER && io.klt, col_inv = INV && io.klt;
+    // colour mode: the KLT of the tile's first frame, staged once per change of frame
+    uint32_t kfr = 0xFFFFFFFFu;
+    if (col_fwd || col_inv) {
+        kfr = col_fwd ? pipe_frame(io, M, 0) : frame_of_voxel(io.vstart, io.F, j0);
+        if (kfr != klt_fr) {
+            __syncthreads();  // the previous tile's readers of klt_s are done
+            for (uint32_t k = tid; k < (uint32_t)kKltFloats; k += kXThreads)
+                klt_s[k] = io.klt[(uint64_t)kfr * kKltFloats + k];
+            klt_fr = kfr;
+            __syncthreads();
+        }
+    }
+    // finishing in place: cluster average and centring (forward), quantise -> dequantise (inverse)
+    if (act && !INV && GATHER) {
+        const bool ctr_any = io.center != nullptr && !io.klt;
+        uint32_t cfr = 0xFFFFFFFFu;
+        float4 ctr = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (uint32_t i = slot; i < m; i += slots) {
+            const bool multi = (M.row0[i] & kCarry) != 0;
+            if (!multi && !ctr_any) continue;
+            const uint32_t fr = pipe_frame(io, M, i);
+            const uint32_t pr = sbase + i * rs;
+            float4 acc = lds4(pr);
+            float *pa = reinterpret_cast<float *>(&acc);
+            if (multi) {  // voxels holding several points: average in input order
+                const uint32_t s0 = io.seg[j0 + i], s1 = io.seg[j0 + i + 1];
+                const float *base = io.attr[fr];
+                for (uint32_t g = s0 + 1; g < s1; ++g) {
+                    const float4 xv = V4::ld(base + (uint64_t)io.vals[g] * C + c);
+                    const float *px = reinterpret_cast<const float *>(&xv);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) pa[e] = add_rn(pa[e], px[e]);
+                }
+                const float cnt = (float)(s1 - s0);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) pa[e] = div_rn(pa[e], cnt);
+            }
+            if (ctr_any) {  // centred rows keep the low-pass sums small (FP32 accuracy)
+                if (fr != cfr) {
+                    ctr = V4::ld(io.center + (uint64_t)fr * C + c);
+                    cfr = fr;
+                }
+                const float *pc = reinterpret_cast<const float *>(&ctr);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) pa[e] = add_rn(pa[e], -pc[e]);
+            }
+            sts4(pr, acc);
+        }
+    } else if (act && INV && QDQ) {
+        const float4 inv = V4::ld(io.inv_step + c), stp = V4::ld(io.step + c);
+        const float *pi = reinterpret_cast<const float *>(&inv), *pt = reinterpret_cast<const float *>(&stp);
+        for (uint32_t i = slot; i < m; i += slots) {
+            if (M.io[i] & kCarry) continue;
+            const uint32_t pr = sbase + i * rs;
+            float4 v = lds4(pr);
+            float *pv = reinterpret_cast<float *>(&v);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) pv[e] = qdq(pv[e], pi[e], pt[e], io.tau);
+            sts4(pr, v);
+        }
+    }
+    if (col_fwd) {  // colour decorrelation of whole rows, then centring
+        __syncthreads();
+        for (uint32_t e = tid; e < m * 16; e += kXThreads)
+            color_yuv_task(R + (uint64_t)(e >> 4) * CP, (int)(e & 15), kYuvFwd);
+        __syncthreads();
+        for (uint32_t e = tid; e < m * 3; e += kXThreads) {
+            const uint32_t i = e / 3, ch = e - 3 * i;
+            const uint32_t fr = pipe_frame(io, M, i);
+            const float *K = (fr == kfr ? klt_s : io.klt + (uint64_t)fr * kKltFloats) + ch * kKltN * kKltN;
+            color_klt_task<false>(R + (uint64_t)i * CP, (int)ch, K);
+        }
+        if (io.center) {
+            __syncthreads();
+            for (uint32_t e = tid; e < m * C; e += kXThreads) {
+                const uint32_t i = e / C, cc = e - i * C;
+                const uint32_t fr = pipe_frame(io, M, i);
+                R[(uint64_t)i * CP + cc] = __fadd_rn(R[(uint64_t)i * CP + cc], -io.center[(uint64_t)fr * C + cc]);
+            }
+        }
+    }
+    __syncthreads();
+    // rounds
+    const uint32_t nr = M.cnt[1];
+    for (uint32_t rr = 0; rr < nr; ++rr) {
+        const uint32_t r = INV ? (nr - 1 - rr) : rr;
+        const uint32_t kb = r ? M.re[r - 1] : 0u, ke = M.re[r];
+        if (act) {
+            for (uint32_t k = kb + slot; k < ke; k += slots) {
+                const uint32_t ix = M.idx[k];
+                const float2 ab = M.ab[k];
+                const uint32_t r0 = sbase + (ix & 0xFFFFu) * rs, r1 = sbase + (ix >> 16) * rs;
+                float4 y0 = lds4(r0), y1 = lds4(r1);
+                rot<INV>(ab.x, ab.y, y0, y1);
+                sts4(r0, y0);
+                sts4(r1, y1);
+            }
+        }
+        __syncthreads();
+    }
+    if (col_inv) {  // undo the colour decorrelation of whole rows
+        for (uint32_t e = tid; e < m * 3; e += kXThreads) {
+            const uint32_t i = e / 3, ch = e - 3 * i;
+            const uint32_t fr = frame_of_voxel(io.vstart, io.F, j0 + i);
+            if (io.frame_color && !io.frame_color[fr]) continue;
+            const float *K = (fr == kfr ? klt_s : io.klt + (uint64_t)fr * kKltFloats) + ch * kKltN * kKltN;
+            color_klt_task<true>(R + (uint64_t)i * CP, (int)ch, K);
+        }
+        __syncthreads();
+        for (uint32_t e = tid; e < m * 16; e += kXThreads) {
+            const uint32_t i = e >> 4;
+            const uint32_t fr = io.F > 1 ? frame_of_voxel(io.vstart, io.F, j0 + i) : 0u;
+            if (io.frame_color && !io.frame_color[fr]) continue;
+            color_yuv_task(R + (uint64_t)i * CP, (int)(e & 15), io.yuv_inv.m);
+        }
+        __syncthreads();
+    }
+    // store rows (the buffer is refilled only after a later barrier)
+    if (act) {
+        for (uint32_t i = slot; i < m; i += slots) {
+            const float4 v = lds4(sbase + i * rs);
+            if (!INV) {
+                const uint32_t d = M.io[i];
+                if (d & kCarry)
+                    V4::st(io.pool + ((uint64_t)nx.surv_off + (d & ~kCarry)) * C + c, v);
+                else
+                    V4::st(io.Y + (uint64_t)d * C + c, v);
+            } else {
+                V4::st(io.out + (j0 + i) * C + c, v);
+            }
+        }
+    }
+}
+
+template <int NR, bool INV, bool GATHER, bool QDQ>
+__global__ void __launch_bounds__(kXThreads, NR == 1 ? 3 : 1) xform_pipe_kernel(XformArgs<float> A)
+{
+    constexpr uint32_t NM = NR + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const RahtPass ps = A.p.passes[0];
+    const RahtPass nx = A.p.passes[1];
+    const uint32_t T = A.p.T, C = A.io.C;
+    const size_t rowb = (size_t)T * pipe_stride(C) * 4, metab = pipe_meta_bytes(T);
+    float *klt_s = reinterpret_cast<float *>(smem_raw + NR * rowb + NM * metab);
+    const uint32_t G = gridDim.x, b = blockIdx.x, nt = ps.ntiles;
+    const uint32_t cnt = b < nt ? (nt - 1 - b) / G + 1 : 0u;  // tiles of this CTA
+    auto rows = [&](uint32_t k) { return reinterpret_cast<float *>(smem_raw + (size_t)(k % NR) * rowb); };
+    auto meta = [&](uint32_t k) { return pipe_stage(smem_raw + NR * rowb + (size_t)(k % NM) * metab, T); };
+    uint32_t klt_fr = 0xFFFFFFFFu;
+    // prologue: metadata of tiles 0 .. NR - 1 (NR = 1: 0 and 1), then the rows of tiles 0 .. NR - 2 (NR = 1: 0)
+    constexpr uint32_t kMeta0 = NR == 1 ? 2u : NR, kRows0 = NR == 1 ? 1u : NR - 1;
+    for (uint32_t k = 0; k < kMeta0 && k < cnt; ++k) pipe_issue_meta<GATHER>(A, ps, b + k * G, meta(k));
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    for (uint32_t k = 0; k < kRows0; ++k) {
+        if (k < cnt) pipe_issue_rows<INV, GATHER>(A, ps, nx, b + k * G, meta(k), rows(k));
+        cp_async_commit();
+    }
+    for (uint32_t k = 0; k < cnt; ++k) {
+        if constexpr (NR == 1) {
+            // complete: rows of tile k, metadata of tile k + 1
+            cp_async_wait<0>();
+            __syncthreads();
+            pipe_compute<INV, GATHER, QDQ>(A, ps, nx, b + k * G, meta(k), rows(k), klt_s, klt_fr);
+            __syncthreads();  // the row buffer and tile k's metadata are free
+            if (k + 2 < cnt) pipe_issue_meta<GATHER>(A, ps, b + (k + 2) * G, meta(k + 2));
+            if (k + 1 < cnt) pipe_issue_rows<INV, GATHER>(A, ps, nx, b + (k + 1) * G, meta(k + 1), rows(k + 1));
+            cp_async_commit();
+        } else {
+            // complete: rows of tile k, metadata of tile k + NR - 1 (only the rows of k + NR - 2 may still fly)
+            cp_async_wait<1>();
+            __syncthreads();
+            if (k + NR < cnt) pipe_issue_meta<GATHER>(A, ps, b + (k + NR) * G, meta(k + NR));
+            cp_async_commit();
+            if (k + NR - 1 < cnt)
+                pipe_issue_rows<INV, GATHER>(A, ps, nx, b + (k + NR - 1) * G, meta(k + NR - 1), rows(k + NR - 1));
+            cp_async_commit();
+            pipe_compute<INV, GATHER, QDQ>(A, ps, nx, b + k * G, meta(k), rows(k), klt_s, klt_fr);
+        }
+    }
+    cp_async_wait<0>();
+}
+
+int max_optin_smem()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+// The pipelined first pass applies to FP32 transforms with 4-float vectors and
+// whole rows per tile whose buffers fit one CTA's shared memory.  Returns NR, or
+// 0 for the plain passes.
+template <typename S, int VEC>
+int pipe_depth(const XformArgs<S> &A, size_t *smem)
+{
+    if (!std::is_same<S, float>::value || VEC != 4 || A.p.xpipe_off == 1) return 0;
+    if (A.Cg != A.io.C || A.io.C % 4 || A.io.C / 4 > (uint32_t)kXThreads) return 0;
+    const int nr = A.p.xpipe_off == 2 ? 3 : 1;
+    *smem = pipe_smem(nr, A.p.T, A.io.C, A.io.klt != nullptr);
+    return *smem <= (size_t)max_optin_smem() ? nr : 0;
+}
+
+template <int NR, bool INV, bool GATHER, bool QDQ>
+void launch_pipe(const XformArgs<float> &A, uint64_t nv_bound, size_t smem, int num_sms, cudaStream_t s)
+{
+    auto k = xform_pipe_kernel<NR, INV, GATHER, QDQ>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;  // resident CTAs per SM with this shared memory (one wave)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kXThreads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const uint64_t tiles = (nv_bound + A.p.T - 1) / A.p.T;
+    const uint64_t cap = (uint64_t)num_sms * (uint64_t)per_sm;
+    const uint32_t grid = (uint32_t)(tiles < 1 ? 1 : (tiles < cap ? tiles : cap));
+    k<<<grid, kXThreads, smem, s>>>(A);
+    count_launch();
+}
+
+template <bool INV, bool GATHER, bool QDQ>
+void launch_pipe_nr(int nr, const XformArgs<float> &A, uint64_t nv_bound, size_t smem, int num_sms, cudaStream_t s)
+{
+    if (nr == 3)
+        launch_pipe<3, INV, GATHER, QDQ>(A, nv_bound, smem, num_sms, s);
+    else
+        launch_pipe<1, INV, GATHER, QDQ>(A, nv_bound, smem, num_sms, s);
+}
+
 uint32_t channel_group(uint32_t C, uint32_t T, uint32_t elem)
 {
     uint32_t cg = kSmemRowBytes / (elem * T);
@@ -809,6 +1198,18 @@ void forward_all(const XformArgs<S> &A, uint64_t nv_bound, int num_sms, cudaStre
     for (int q = 0; q < kRahtMultiPasses; ++q) {
         uint32_t g = q == 0 ? grid0 : (grid0 < (uint32_t)num_sms ? grid0 : (uint32_t)num_sms);
         if (q == 0) stage_begin(s, kStRahtFwd0);
+        size_t psm = 0;
+        if constexpr (std::is_same<S, float>::value) {
+            const int nr = q == 0 && (!A.io.seg || A.io.row0) ? pipe_depth<S, VEC>(A, &psm) : 0;
+            if (nr) {
+                if (A.io.seg)
+                    launch_pipe_nr<false, true, false>(nr, A, nv_bound, psm, num_sms, s);
+                else
+                    launch_pipe_nr<false, false, false>(nr, A, nv_bound, psm, num_sms, s);
+                stage_end(s, kStRahtFwd0);
+                continue;
+            }
+        }
         if (q == 0 && A.io.seg)
             launch_pass<S, false, VEC, true, false>(A, q, g, smem, s);
         else
@@ -834,6 +1235,18 @@ void inverse_all(const XformArgs<S> &A, uint64_t nv_bound, int num_sms, cudaStre
     for (int q = kRahtMultiPasses - 1; q >= 0; --q) {
         uint32_t g = q == 0 ? grid0 : (grid0 < (uint32_t)num_sms ? grid0 : (uint32_t)num_sms);
         if (q == 0) stage_begin(s, kStRahtInv0);
+        size_t psm = 0;
+        if constexpr (std::is_same<S, float>::value) {
+            const int nr = q == 0 ? pipe_depth<S, VEC>(A, &psm) : 0;
+            if (nr) {
+                if (qd)
+                    launch_pipe_nr<true, false, true>(nr, A, nv_bound, psm, num_sms, s);
+                else
+                    launch_pipe_nr<true, false, false>(nr, A, nv_bound, psm, num_sms, s);
+                stage_end(s, kStRahtInv0);
+                continue;
+            }
+        }
         if (qd)
             launch_pass<S, true, VEC, false, true>(A, q, g, smem, s);
         else

@@ -122,7 +122,7 @@ def set_graphs(enable: bool, device=None):
     _check(lib().gsnfs_set_graphs(context(device), 1 if enable else 0), "gsnfs_set_graphs")
 
 
-TUNABLES = {"raht_tile": 0, "raht_grid": 1, "prelude_grid": 2}
+TUNABLES = {"raht_tile": 0, "raht_grid": 1, "prelude_grid": 2, "raht_pipe": 3}
 
 
 def tune_set(name: str, value: int, device=None):

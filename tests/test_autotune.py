@@ -17,21 +17,22 @@ def _fake(times, wrong=(), broken=()):
 
 
 def test_descent_finds_the_separable_optimum():
-    cost = {"raht_tile": {0: 5, 512: 3, 1024: 4}, "raht_grid": {0: 5, 2: 6, 3: 4, 6: 2, 8: 3},
-            "prelude_grid": {0: 1, 4: 2, 16: 0.5}}
+    cost = {"raht_pipe": {0: 1, 1: 2, 2: 1.5}, "raht_tile": {0: 5, 512: 3, 1024: 4},
+            "raht_grid": {0: 5, 2: 6, 3: 4, 6: 2, 8: 3}, "prelude_grid": {0: 1, 4: 2, 16: 0.5}}
     measure, calls = _fake(lambda p: sum(cost[k][p[k]] for k in at.ORDER))
     best, ms, d, trials = at.coordinate_descent(measure)
-    assert best == {"raht_tile": 512, "raht_grid": 6, "prelude_grid": 16}
-    assert ms == 3 + 2 + 0.5 and d == 11
-    assert len(calls) == 1 + 2 + 4 + 2  # default, then each other candidate once
+    assert best == {"raht_pipe": 0, "raht_tile": 512, "raht_grid": 6, "prelude_grid": 16}
+    assert ms == 1 + 3 + 2 + 0.5 and d == 12
+    assert len(calls) == 1 + 2 + 2 + 4 + 2  # default, then each other candidate once
 
 
 def test_descent_rejects_wrong_outputs_broken_runs_and_small_gains():
     def t(p):
         return {0: 10.0, 512: 5.0, 1024: 9.95}[p["raht_tile"]] + {0: 0, 2: -1, 3: 0, 6: 0, 8: 0}[p["raht_grid"]]
-    measure, _ = _fake(t, wrong={(512, 0, 0)}, broken={(0, 2, 0)})
+    measure, _ = _fake(t, wrong={(0, 512, 0, 0)}, broken={(0, 0, 2, 0)})
     best, ms, d, trials = at.coordinate_descent(measure)
-    assert best == {"raht_tile": 0, "raht_grid": 0, "prelude_grid": 0}  # 512 wrong, 1024 < 1% gain, grid 2 broken
+    # pipe off no faster, tile 512 wrong, 1024 < 1% gain, grid 2 broken
+    assert best == {"raht_pipe": 0, "raht_tile": 0, "raht_grid": 0, "prelude_grid": 0}
     assert ms == d == 10.0
     assert any(p["raht_tile"] == 512 and ok is False for p, m, ok in trials)
     assert any(p["raht_grid"] == 2 and m is None for p, m, ok in trials)

@@ -1,5 +1,5 @@
-"""Autotuner on the GPU: every candidate launch shape (RAHT tile 256..1024,
-transform and prelude grid sizes) gives byte-identical bitstreams and decoded
+"""Autotuner on the GPU: every candidate launch shape (pipelined or plain first
+transform pass, RAHT tile 256..1024, transform and prelude grid sizes) gives byte-identical bitstreams and decoded
 frames, the best setting is applied and cached, and a cache hit reapplies it."""
 import numpy as np
 import pytest
@@ -31,7 +31,7 @@ def test_every_launch_shape_gives_identical_outputs(G, tmp_path):
     cache = str(tmp_path / "tune.json")
     e = autotune.tune_round_trip(P, A, [16, 17], qp, reps=1, cache=cache)
     ran = [t for t in e["trials"] if t[1] is not None]
-    assert len(ran) == len(e["trials"]) >= 9
+    assert len(ran) == len(e["trials"]) >= 11
     assert all(ok for _, _, ok in ran), e["trials"]
     assert {k: G.tune_get(k) for k in G.TUNABLES} == e["params"]
     for k in G.TUNABLES:
@@ -45,6 +45,8 @@ def test_tunable_validation(G):
         G.tune_set("raht_tile", 300)
     with pytest.raises(G.GsnfsError):
         G.tune_set("raht_grid", 33)
+    with pytest.raises(G.GsnfsError):
+        G.tune_set("raht_pipe", 3)
     G.tune_set("raht_tile", 4096)
     assert G.tune_get("raht_tile") == 4096
     G.tune_set("raht_tile", 0)
@@ -57,10 +59,11 @@ def test_extreme_tiles_give_identical_streams(G):
     ref, nv, rp, ra = G.encode_frame(pd, ad, 16, qp, recon=True)
     ref = ref.cpu().numpy()
     ra = ra.cpu().numpy()
-    for tile, grid, pgrid in ((4096, 1, 1), (256, 32, 32), (2048, 0, 2)):
+    for tile, grid, pgrid, plain in ((4096, 1, 1, 0), (256, 32, 32, 1), (2048, 0, 2, 0), (0, 0, 0, 1), (0, 0, 0, 2)):
         G.tune_set("raht_tile", tile)
         G.tune_set("raht_grid", grid)
         G.tune_set("prelude_grid", pgrid)
+        G.tune_set("raht_pipe", plain)
         got, _, _, ga = G.encode_frame(pd, ad, 16, qp, recon=True)
         assert np.array_equal(got.cpu().numpy(), ref), tile
         assert np.array_equal(ga.cpu().numpy(), ra), tile
