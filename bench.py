@@ -637,6 +637,24 @@ def run_ladder(args):
                  "bits_per_gaussian_per_rung": [round(float(x), 2) for x in 8 * rate.sum(0) / total_n],
                  "hull_points_mean": round(float(np.mean([len(rd.upper_hull(rate[f], psnr[f])) for f in range(F)])), 2),
                  "selected_rung_histogram_at_x4_budget": np.bincount(sel, minlength=R).tolist()}
+    # rendered-view PSNR (Sec. 5.1's measure) for the first frames: decoded streams rendered by the GPU
+    # rasteriser from 2 orbit views (480 x 270) against the same views of the original Gaussians
+    from paper_2606_05650_gb300 import synthetic as syn
+    Fr = min(4, F)
+    views = syn.orbit_views(2, radius=1.2)
+
+    def render(p, a, v):
+        return G.render(p, a.contiguous(), v, 500.0, 500.0, 240, 135, 480, 270)
+    rq = np.zeros((Fr, R))
+    for f in range(Fr):
+        for r in range(R):
+            i = f * R + r
+            dp, da = G.decode_frame(o_rd[int(offs_rd[i]):int(offs_rd[i + 1])])
+            rq[f, r] = rd.rendered_psnr(render, (P[f], A[f]), (dp, da), views)
+    rsel = rd.select(rate[:Fr], rq, budget[:Fr])
+    res["rd"]["rendered"] = {"frames": Fr, "views": len(views), "image": [480, 270],
+                             "psnr_db_mean_per_rung": [round(float(x), 2) for x in rq.mean(0)],
+                             "selected_rung_histogram_at_x4_budget": np.bincount(rsel, minlength=R).tolist()}
     line = {"metric": "ladder encode frames/s (each frame at 5 rungs)", "unit": "frames/s", "higher_is_better": True,
             "value": res["batched_graphs"]["frames_per_s"], "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{F} dynamic 3DGS frames, Gaussians log-uniform in [50k, 2M] (total {total_n}), "

@@ -7,6 +7,9 @@ channel (gsnfs_encode_batch_rd), which equals the squared error of the decoded
 attributes against the voxel means because RAHT is orthonormal.  From those:
 
 * psnr(): PSNR with peak 1 over all channels (or a channel subset) of a frame;
+* rendered_psnr(): PSNR of rendered views of the decoded frame against the
+  same views of the original Gaussians (the quality measure of Sec. 5.1),
+  for any renderer (gsnfs.render on the GPU);
 * upper_hull(): the rungs on the upper convex hull of (bytes, PSNR), i.e. the
   rungs no mixture of two other rungs beats;
 * select(): per frame, the hull rung with the highest PSNR whose stream fits a
@@ -64,3 +67,24 @@ def select(rate, quality, budget):
         fit = [i for i in hull if rate[f, i] <= budget[f]]
         out[f] = max(fit, key=lambda i: quality[f, i]) if fit else int(np.argmin(rate[f]))
     return out
+
+
+def image_psnr(img, ref, peak=1.0):
+    """PSNR (dB) of an image against a reference, both clamped to [0, peak]
+    (numpy arrays or torch tensors of the same shape)."""
+    if hasattr(img, "detach"):
+        a = img.detach().clamp(0, peak).double()
+        b = ref.detach().clamp(0, peak).double()
+        mse = float(((a - b) ** 2).mean())
+    else:
+        a = np.clip(np.asarray(img, dtype=np.float64), 0, peak)
+        b = np.clip(np.asarray(ref, dtype=np.float64), 0, peak)
+        mse = float(((a - b) ** 2).mean())
+    return float(10.0 * np.log10(peak * peak / max(mse, 1e-300)))
+
+
+def rendered_psnr(render, original, decoded, views, peak=1.0):
+    """Mean over views of image_psnr(render(*decoded, view), render(*original, view));
+    original and decoded are (positions, attributes) pairs, render(pos, attr, view) -> image."""
+    vals = [image_psnr(render(decoded[0], decoded[1], v), render(original[0], original[1], v), peak) for v in views]
+    return float(np.mean(vals))

@@ -66,3 +66,31 @@ def test_ladder_hull_and_selection(G):
         assert rd.upper_hull(rate[f], q[f])  # non-empty, increasing by construction
     sel = rd.select(rate, q, rate[:, 2])
     assert (rate[np.arange(3), sel] <= rate[:, 2]).all()
+
+
+def test_rendered_psnr_ladder_and_selection(G):
+    """Rendered-view PSNR (Sec. 5.1's measure) per rung of a ladder: decoded
+    frames rendered by the GPU rasteriser against the original Gaussians fall
+    in quality as the steps grow, the hull keeps the best rung, and a budget
+    picks the best hull rung that fits."""
+    pos, attr = syn.static_gs_frame(7, n=40_000)
+    scales = [0.5, 2.0, 8.0, 32.0]
+    qp = G.QuantParams(syn.gs_channel_groups(), syn.GS_BASE_STEPS)
+    P, A = [_dev(pos)], [_dev(attr)]
+    out, offs = G.encode_batch(P, A, [14], scales, qp)
+    views = syn.orbit_views(2, radius=1.6)
+
+    def render(p, a, v):
+        return G.render(p, a.contiguous(), v, 300.0, 300.0, 160, 120, 320, 240)
+    q = []
+    for r in range(len(scales)):
+        dp, da = G.decode_frame(out[int(offs[r]):int(offs[r + 1])])
+        q.append(rd.rendered_psnr(render, (P[0], A[0]), (dp, da), views))
+    rate = np.diff(offs.astype(np.int64))
+    assert all(q[r] > q[r + 1] for r in range(len(q) - 1)), q
+    assert all(rate[r] > rate[r + 1] for r in range(len(rate) - 1)), rate
+    assert q[0] > 30.0
+    hull = rd.upper_hull(rate, q)
+    assert 0 in hull and (len(scales) - 1) in hull
+    sel = rd.select(rate[None], np.array(q)[None], [rate[1] + 1])
+    assert sel[0] in hull and rate[sel[0]] <= rate[1] + 1 and q[sel[0]] >= q[1]

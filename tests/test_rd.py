@@ -1,5 +1,5 @@
 """R-D selection over a ladder (host logic): upper convex hull of (bytes, PSNR),
-budgeted choice per frame, PSNR from squared-error sums."""
+budgeted choice per frame, PSNR from squared-error sums and of rendered views."""
 import numpy as np
 
 from paper_2606_05650_gb300 import rd
@@ -41,3 +41,22 @@ def test_psnr_from_error_sums():
     p = rd.psnr(e, [100])
     assert np.allclose(p, [[20.0, 10.0]])
     assert np.allclose(rd.psnr(e, [100], channels=[0, 1]), [[20.0, 10.0]])
+
+
+def test_image_psnr_closed_form_and_clamping():
+    ref = np.full((4, 5, 3), 0.5)
+    for d in (0.1, 0.01, 0.001):
+        assert np.isclose(rd.image_psnr(ref + d, ref), -20 * np.log10(d))
+    # values beyond [0, 1] are clamped before the difference
+    assert np.isclose(rd.image_psnr(np.full((2, 2, 3), 1.7), np.full((2, 2, 3), 0.9)), -20 * np.log10(0.1))
+
+
+def test_rendered_psnr_averages_views_of_both_frames():
+    calls = []
+
+    def render(pos, attr, view):
+        calls.append((pos, view))
+        return np.full((2, 2, 3), 0.25 + (0.1 * view if pos == "dec" else 0.0))
+    v = rd.rendered_psnr(render, ("orig", None), ("dec", None), [0.1, 0.01])
+    assert np.isclose(v, np.mean([-20 * np.log10(0.01), -20 * np.log10(0.001)]))
+    assert sorted(calls) == sorted([("dec", 0.1), ("orig", 0.1), ("dec", 0.01), ("orig", 0.01)])
