@@ -110,6 +110,62 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v)
     return v;
 }
 
+// Voxel index of one coordinate: floor(RN64(RN64(p - lo) * scale)) clamped to
+// [0, vmax], exactly as the FP64 definition gives it, mostly without FP64
+// arithmetic (GB300's FP64 rate is a small fraction of its FP32 rate).  The
+// product is first evaluated in double-float arithmetic (Knuth's TwoSum for
+// p - lo, Dekker's exact product via a fused multiply-add) with lo and scale
+// split into two floats each: for x = (p - lo) * scale < 2^23 its value x~ is
+// within 2^-21 + 4 |lo| scale 2^-48 of x (the second term from the split of
+// lo), and the FP64 result within 2^-28 of x, so when x~ lies farther than
+// that margin from every integer both have the same floor.  Otherwise (a
+// coordinate on or next to a voxel face) the FP64 definition decides.
+struct AxisGrid {
+    float lo_hi, lo_lo, sc_hi, sc_lo, margin;
+    double lo, scale;
+};
+
+__device__ __forceinline__ AxisGrid axis_grid(double lo, double scale)
+{
+    AxisGrid a;
+    a.lo = lo;
+    a.scale = scale;
+    a.lo_hi = (float)lo;
+    a.lo_lo = (float)__dsub_rn(lo, (double)a.lo_hi);
+    a.sc_hi = (float)scale;
+    a.sc_lo = (float)__dsub_rn(scale, (double)a.sc_hi);
+    // 2^-20 + 8 |lo| scale 2^-48 (twice the bound above), rounded up
+    const double m = 9.5367431640625e-07 + 8.0 * fabs(lo) * scale * 3.552713678800501e-15;
+    a.margin = m < 0.25 ? (float)(m * 1.0000002) : 2.0f;  // 2: always the FP64 definition
+    return a;
+}
+
+__device__ __forceinline__ uint64_t voxel_index(float p, const AxisGrid &g, uint64_t vmax)
+{
+    // t = p - lo as s + t_lo (TwoSum of p and -lo_hi, then the low part of lo)
+    const float s = __fsub_rn(p, g.lo_hi);
+    const float bv = __fsub_rn(s, p);
+    const float e1 = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bv)), __fsub_rn(-g.lo_hi, bv));
+    const float t_lo = __fsub_rn(e1, g.lo_lo);
+    // x = t * scale as hi + lo (exact product of s and sc_hi, plus the small cross terms)
+    const float hi = __fmul_rn(s, g.sc_hi);
+    const float perr = __fmaf_rn(s, g.sc_hi, -hi);
+    const float lo = __fadd_rn(perr, __fadd_rn(__fmul_rn(s, g.sc_lo), __fmul_rn(t_lo, g.sc_hi)));
+    if (hi >= 1.0f && hi < 8388608.0f) {  // 1 <= x~ < 2^23: fractional part resolvable in FP32
+        const float fh = floorf(hi);
+        const float f = __fadd_rn(__fsub_rn(hi, fh), lo);
+        if (f >= g.margin && f <= 1.0f - g.margin) {  // the same floor as the FP64 definition
+            const uint64_t q = (uint64_t)fh;
+            return q > vmax ? vmax : q;
+        }
+    } else if (hi >= 8388608.0f && (double)hi > (double)vmax + 2.0) {
+        return vmax;  // far beyond the last voxel either way
+    }
+    const double u = floor(__dmul_rn(__dsub_rn((double)p, g.lo), g.scale));
+    const uint64_t q = (u <= 0.0) ? 0ull : (uint64_t)u;
+    return q > vmax ? vmax : q;
+}
+
 __global__ void __launch_bounds__(kThreads) morton_kernel(FrameSet fs, uint64_t *keys, uint32_t *vals)
 {
     const uint32_t f = blockIdx.y;
@@ -120,15 +176,11 @@ __global__ void __launch_bounds__(kThreads) morton_kernel(FrameSet fs, uint64_t 
     const FrameGrid g = fs.grid[f];
     const uint64_t vmax = (1ull << J) - 1;
     const uint64_t fbits = (fs.frame_shift < 64) ? ((uint64_t)f << fs.frame_shift) : 0ull;
+    const AxisGrid ax[3] = {axis_grid(g.lo[0], g.scale), axis_grid(g.lo[1], g.scale), axis_grid(g.lo[2], g.scale)};
     for (uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (uint64_t)gridDim.x * kThreads) {
         uint64_t v[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            double t = __dsub_rn((double)__ldg(pos + 3 * i + a), g.lo[a]);
-            double u = floor(__dmul_rn(t, g.scale));
-            uint64_t q = (u <= 0.0) ? 0ull : (uint64_t)u;
-            v[a] = q > vmax ? vmax : q;
-        }
+        for (int a = 0; a < 3; ++a) v[a] = voxel_index(__ldg(pos + 3 * i + a), ax[a], vmax);
         keys[base + i] = fbits | spread3(v[0]) | (spread3(v[1]) << 1) | (spread3(v[2]) << 2);
         vals[base + i] = (uint32_t)i;
     }

@@ -54,6 +54,22 @@ def test_voxel_grid_edge_cases(G, orc):
             assert np.array_equal(codes.cpu().numpy().astype(np.uint64), ref)
 
 
+def test_voxel_faces_and_far_offsets(G, orc):
+    """Coordinates exactly on voxel faces (lattices of the grid spacing) and
+    grids far from the origin: the cases where the fast double-float voxel
+    index must defer to the FP64 definition."""
+    rng = np.random.default_rng(3)
+    for J, off, span in ((4, 0.0, 1.0), (10, 0.0, 1.0), (16, 0.0, 1.0), (21, 0.0, 1.0), (10, 1000.0, 1.0),
+                         (21, 1000.0, 1.0), (21, -3.0e5, 7.0), (16, 12345.678, 0.001)):
+        k = rng.integers(0, 1 << min(J, 20), (4000, 3))
+        pos = (off + span * k / float(1 << min(J, 20))).astype(np.float32)
+        pos = np.r_[pos, np.float32([[off, off, off], [off + span, off + span, off + span]])]
+        pos = np.r_[pos, (pos[:500] + np.float32(span) * rng.uniform(-1e-6, 1e-6, (500, 3))).astype(np.float32)]
+        codes, lo, ext = G.voxelize(_dev(pos), J)
+        ref, _, _, rlo, rext = orc.voxelize(pos, np.zeros((len(pos), 1), np.float32), J)
+        assert np.array_equal(codes.cpu().numpy().astype(np.uint64), ref), (J, off, span)
+
+
 @pytest.mark.parametrize("name,n,J", CASES)
 def test_occupancy_bytes_bit_exact(G, orc, name, n, J):
     pos, _ = syn.static_gs_frame(12, n)
