@@ -504,10 +504,22 @@ __global__ void attr_copy_kernel(HdrParams hp, AttrCopyArgs a, const StreamInfo 
         for (uint32_t j = 0; j < cnt; ++j) {
             const uint32_t w = __shfl_sync(0xFFFFFFFFu, wl, j);
             const uint64_t o = __shfl_sync(0xFFFFFFFFu, ol, j);
-            const uint32_t *src = a.slots + (b0 + k0 + j) * a.slot_words;
-            uint32_t *dst = pay + o;
-#pragma unroll 4
-            for (uint32_t i = lane; i < w; i += 32) dst[i] = src[i];
+            const uint32_t *__restrict__ src = a.slots + (b0 + k0 + j) * a.slot_words;
+            uint32_t *__restrict__ dst = pay + o;
+            // up to 128 words per round: all loads in flight before the stores
+            for (uint32_t i0 = 0; i0 < w; i0 += 128) {
+                uint32_t v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t i = i0 + lane + 32 * u;
+                    v[u] = i < w ? __ldg(src + i) : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t i = i0 + lane + 32 * u;
+                    if (i < w) dst[i] = v[u];
+                }
+            }
         }
     }
     const uint64_t used = 8 + 4 * nblk + 4 * (a.block_off[b0 + nblk] - base);
