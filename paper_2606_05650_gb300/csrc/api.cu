@@ -251,6 +251,33 @@ gsnfs_status fork_end(gsnfs_ctx *ctx, cudaStream_t s)
     return GSNFS_OK;
 }
 
+// Small transfers between the pinned staging buffer and the device (a call's
+// parameters and results) run as a kernel over the staging buffer's unified
+// address instead of on the copy engines, so they never queue behind a
+// caller's bulk copies in flight on other streams.
+__global__ void stage_copy_kernel(unsigned char *dst, const unsigned char *src, uint64_t n)
+{
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    if ((((uintptr_t)dst | (uintptr_t)src | n) & 3) == 0) {
+        uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+        const uint32_t *q = reinterpret_cast<const uint32_t *>(src);
+        for (uint64_t i = t; i < n / 4; i += nt) d[i] = q[i];
+    } else {
+        for (uint64_t i = t; i < n; i += nt) dst[i] = src[i];
+    }
+}
+
+cudaError_t stage_copy(void *dst, const void *src, size_t n, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const uint64_t words = (n + 3) / 4;
+    const uint32_t blocks = (uint32_t)std::min<uint64_t>((words + 255) / 256, 128);
+    stage_copy_kernel<<<blocks, 256, 0, s>>>(static_cast<unsigned char *>(dst), static_cast<const unsigned char *>(src),
+                                             n);
+    count_launch();
+    return cudaGetLastError();
+}
+
 gsnfs_status map_dev_error(uint32_t e)
 {
     switch (e) {
@@ -796,15 +823,15 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
     // ---- device work: stream-ordered and sized from host values only, so it
     // can be captured once per request shape and replayed as a CUDA graph
     auto enqueue = [&](cudaStream_t s) -> gsnfs_status {
-        CK(cudaMemcpyAsync((void *)L.posp, hp + o_pos, 8 * F, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync((void *)L.attrp, hp + o_attr, 8 * F, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(L.poff, hp + o_poff, 8 * (F + 1), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(L.Jd, hp + o_J, 4 * F, cudaMemcpyHostToDevice, s));
+        CK(stage_copy((void *)L.posp, hp + o_pos, 8 * F, s));
+        CK(stage_copy((void *)L.attrp, hp + o_attr, 8 * F, s));
+        CK(stage_copy(L.poff, hp + o_poff, 8 * (F + 1), s));
+        CK(stage_copy(L.Jd, hp + o_J, 4 * F, s));
         if (C) {
-            CK(cudaMemcpyAsync(L.inv_step, hp + o_inv, 4 * (size_t)R * C, cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(L.step, hp + o_step, 4 * (size_t)R * C, cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(L.steps_rg, hp + o_srg, 8 * (size_t)R * G, cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(L.groups, hp + o_grp, C, cudaMemcpyHostToDevice, s));
+            CK(stage_copy(L.inv_step, hp + o_inv, 4 * (size_t)R * C, s));
+            CK(stage_copy(L.step, hp + o_step, 4 * (size_t)R * C, s));
+            CK(stage_copy(L.steps_rg, hp + o_srg, 8 * (size_t)R * G, s));
+            CK(stage_copy(L.groups, hp + o_grp, C, s));
         }
         CK(cudaMemsetAsync(L.overflow, 0, 16, s));
 
@@ -954,10 +981,10 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
         stage_end(s, kStRecon);
         CK(cudaGetLastError());
         // results
-        CK(cudaMemcpyAsync(res, &dst->err, 8, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(res + 1, &dst->nv_total, 16, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(res + 3, L.overflow, 4, cudaMemcpyDeviceToHost, s));
-        if (dist_bytes) CK(cudaMemcpyAsync(hp + o_dist, L.sq_err, dist_bytes, cudaMemcpyDeviceToHost, s));
+        CK(stage_copy(res, &dst->err, 8, s));
+        CK(stage_copy(res + 1, &dst->nv_total, 16, s));
+        CK(stage_copy(res + 3, L.overflow, 4, s));
+        if (dist_bytes) CK(stage_copy(hp + o_dist, L.sq_err, dist_bytes, s));
         return GSNFS_OK;
     };
     if (ctx->graphs) {
@@ -1108,13 +1135,13 @@ gsnfs_status read_headers(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, u
     CK(cudaStreamSynchronize(s));
     uint8_t *hp = ctx->pinned;
     if (bytes < 96) return GSNFS_ERR_CORRUPT;
-    CK(cudaMemcpyAsync(hp, d_in, 96, cudaMemcpyDeviceToHost, s));
+    CK(stage_copy(hp, d_in, 96, s));
     CK(cudaStreamSynchronize(s));
     st = parse_fixed(hp, bytes, P);
     if (st) return st;
-    CK(cudaMemcpyAsync(hp, d_in, P.hb, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(hp + 4096, d_in + P.hb, 24, cudaMemcpyDeviceToHost, s));
-    if (P.attr_bytes >= 8) CK(cudaMemcpyAsync(hp + 4096 + 64, d_in + P.hb + P.occ_bytes, 8, cudaMemcpyDeviceToHost, s));
+    CK(stage_copy(hp, d_in, P.hb, s));
+    CK(stage_copy(hp + 4096, d_in + P.hb, 24, s));
+    if (P.attr_bytes >= 8) CK(stage_copy(hp + 4096 + 64, d_in + P.hb + P.occ_bytes, 8, s));
     CK(cudaStreamSynchronize(s));
     st = parse_tables(hp, P);
     if (st) return st;
@@ -1193,11 +1220,11 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
     const uint32_t vst_h[2] = {0u, (uint32_t)P.nv};
     memcpy(hp + 192, vst_h, 8);
     for (uint32_t c = 0; c < P.C; ++c) ((float *)(hp + 256))[c] = (float)P.steps[P.groups[c]];
-    CK(cudaMemcpyAsync(L.grid, hp, sizeof(g), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(L.nvdev, hp + 128, 8, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(L.vst, hp + 192, 8, cudaMemcpyHostToDevice, s));
+    CK(stage_copy(L.grid, hp, sizeof(g), s));
+    CK(stage_copy(L.nvdev, hp + 128, 8, s));
+    CK(stage_copy(L.vst, hp + 192, 8, s));
     if (P.color) CK(cudaMemcpyAsync(L.klt, d_in + P.klt_off, 4 * kKltFloats, cudaMemcpyDeviceToDevice, s));
-    if (P.C) CK(cudaMemcpyAsync(L.step, hp + 256, 4 * P.C, cudaMemcpyHostToDevice, s));
+    if (P.C) CK(stage_copy(L.step, hp + 256, 4 * P.C, s));
     CK(cudaMemsetAsync(dst, 0, 8, s));
     const int sms = ctx->num_sms;
     // a12's RLGR decode needs only the block tables: second stream, beside a11
@@ -1257,7 +1284,7 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
     }
     CK(cudaGetLastError());
     uint32_t *res = (uint32_t *)(hp + 1024);
-    CK(cudaMemcpyAsync(res, &dst->err, 4, cudaMemcpyDeviceToHost, s));
+    CK(stage_copy(res, &dst->err, 4, s));
     CK(cudaStreamSynchronize(s));
     return map_dev_error(res[0]);
 }
@@ -1276,7 +1303,7 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     uint8_t *hp = ctx->pinned;
     for (uint32_t f = 0; f < F; ++f) {
         if (offs[f + 1] - offs[f] < 96) return GSNFS_ERR_CORRUPT;
-        CK(cudaMemcpyAsync(hp + (size_t)f * 8192, d_in + offs[f], 96, cudaMemcpyDeviceToHost, s));
+        CK(stage_copy(hp + (size_t)f * 8192, d_in + offs[f], 96, s));
     }
     CK(cudaStreamSynchronize(s));
     for (uint32_t f = 0; f < F; ++f) {
@@ -1286,10 +1313,10 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     }
     for (uint32_t f = 0; f < F; ++f) {
         uint8_t *h = hp + (size_t)f * 8192;
-        CK(cudaMemcpyAsync(h, d_in + offs[f], P[f].hb, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(h + 4096, d_in + offs[f] + P[f].hb, 24, cudaMemcpyDeviceToHost, s));
+        CK(stage_copy(h, d_in + offs[f], P[f].hb, s));
+        CK(stage_copy(h + 4096, d_in + offs[f] + P[f].hb, 24, s));
         if (P[f].attr_bytes >= 8)
-            CK(cudaMemcpyAsync(h + 4096 + 64, d_in + offs[f] + P[f].hb + P[f].occ_bytes, 8, cudaMemcpyDeviceToHost, s));
+            CK(stage_copy(h + 4096 + 64, d_in + offs[f] + P[f].hb + P[f].occ_bytes, 8, s));
     }
     CK(cudaStreamSynchronize(s));
     uint32_t C = 0, Jmax = 0;
@@ -1464,15 +1491,15 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         hlp[(uint64_t)lv * (F + 1) + F] = run;
     }
     memcpy(tp + o_nv, &N, 8);
-    CK(cudaMemcpyAsync(L.fr, tp + o_fr, sizeof(DecFrame) * F, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(L.vstart, tp + o_vs, 4 * (F + 1), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(L.lvl_pref, tp + o_lp, 8 * (size_t)(Jmax + 1) * (F + 1), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(L.job_off, tp + o_jo, 8 * (F + 1), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(L.blk_pref, tp + o_bp, 8 * (F + 1), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(L.nvdev, tp + o_nv, 8, cudaMemcpyHostToDevice, s));
-    if (C) CK(cudaMemcpyAsync(L.steps, tp + o_st, 4 * (size_t)F * C, cudaMemcpyHostToDevice, s));
+    CK(stage_copy(L.fr, tp + o_fr, sizeof(DecFrame) * F, s));
+    CK(stage_copy(L.vstart, tp + o_vs, 4 * (F + 1), s));
+    CK(stage_copy(L.lvl_pref, tp + o_lp, 8 * (size_t)(Jmax + 1) * (F + 1), s));
+    CK(stage_copy(L.job_off, tp + o_jo, 8 * (F + 1), s));
+    CK(stage_copy(L.blk_pref, tp + o_bp, 8 * (F + 1), s));
+    CK(stage_copy(L.nvdev, tp + o_nv, 8, s));
+    if (C) CK(stage_copy(L.steps, tp + o_st, 4 * (size_t)F * C, s));
     if (any_color) {
-        CK(cudaMemcpyAsync(L.fcolor, tp + o_fc, 4 * (size_t)F, cudaMemcpyHostToDevice, s));
+        CK(stage_copy(L.fcolor, tp + o_fc, 4 * (size_t)F, s));
         for (uint32_t f = 0; f < F; ++f)
             if (P[f].color)
                 CK(cudaMemcpyAsync(L.klt + (uint64_t)f * kKltFloats, d_in + offs[f] + P[f].klt_off, 4 * kKltFloats,
@@ -1537,7 +1564,7 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     }
     CK(cudaGetLastError());
     uint32_t *res = reinterpret_cast<uint32_t *>(tp + ((o_end + 63) & ~(size_t)63));
-    CK(cudaMemcpyAsync(res, &dst->err, 4, cudaMemcpyDeviceToHost, s));
+    CK(stage_copy(res, &dst->err, 4, s));
     CK(cudaStreamSynchronize(s));
     return map_dev_error(res[0]);
 }

@@ -338,14 +338,29 @@ def render(pos: torch.Tensor, attr: torch.Tensor, view, fx, fy, cx, cy, width: i
     return out
 
 
-def decode_batch(data: torch.Tensor, offsets, C: int, rows_cap: int):
+def decode_batch(data: torch.Tensor, offsets, C: int, rows_cap: int, pos_out: torch.Tensor | None = None,
+                 attr_out: torch.Tensor | None = None):
     """gsnfs_decode_batch over streams data[offsets[f]:offsets[f+1]].
-    Returns (pos, attr, row offsets)."""
+    Returns (pos, attr, row offsets).  pos_out [rows_cap, 3] and attr_out
+    [rows_cap, C] (contiguous float32 on the same device) receive the rows
+    when given, else new tensors are allocated."""
     F = len(offsets) - 1
     hin = (ct.c_uint64 * (F + 1))(*[int(o) for o in offsets])
     rows = (ct.c_uint64 * (F + 1))()
-    pos = torch.empty((max(rows_cap, 1), 3), dtype=torch.float32, device=data.device)
-    attr = torch.empty((max(rows_cap, 1), max(C, 1)), dtype=torch.float32, device=data.device) if C else None
+    if pos_out is not None:
+        if (pos_out.dtype != torch.float32 or not pos_out.is_contiguous() or pos_out.device != data.device
+                or tuple(pos_out.shape) != (max(rows_cap, 1), 3)):
+            raise ValueError("pos_out must be a contiguous float32 [rows_cap, 3] tensor on the data's device")
+        pos = pos_out
+    else:
+        pos = torch.empty((max(rows_cap, 1), 3), dtype=torch.float32, device=data.device)
+    if C and attr_out is not None:
+        if (attr_out.dtype != torch.float32 or not attr_out.is_contiguous() or attr_out.device != data.device
+                or tuple(attr_out.shape) != (max(rows_cap, 1), C)):
+            raise ValueError("attr_out must be a contiguous float32 [rows_cap, C] tensor on the data's device")
+        attr = attr_out
+    else:
+        attr = torch.empty((max(rows_cap, 1), max(C, 1)), dtype=torch.float32, device=data.device) if C else None
     _check(lib().gsnfs_decode_batch(context(data.device), _stream(data), F, _ptr(data), hin, _ptr(pos), _ptr(attr),
                                     rows_cap, rows), "gsnfs_decode_batch")
     r = np.array(rows[:], dtype=np.uint64)
