@@ -833,7 +833,7 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
             CK(stage_copy(L.steps_rg, hp + o_srg, 8 * (size_t)R * G, s));
             CK(stage_copy(L.groups, hp + o_grp, C, s));
         }
-        CK(cudaMemsetAsync(L.overflow, 0, 16, s));
+        CK(dev_memset(L.overflow, 0, 16, s));
 
         DevState *dst = ctx->st;
         const int sms = ctx->num_sms;
@@ -921,7 +921,7 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
             j.overflow = L.overflow;
             j.dc = L.dc;
             if (rq.dist) {
-                CK(cudaMemsetAsync(L.sq_err, 0, 8 * (size_t)F * R * C, s));
+                CK(dev_memset(L.sq_err, 0, 8 * (size_t)F * R * C, s));
                 j.sq_err = L.sq_err;
                 j.step = L.step;
             }
@@ -1223,9 +1223,9 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
     CK(stage_copy(L.grid, hp, sizeof(g), s));
     CK(stage_copy(L.nvdev, hp + 128, 8, s));
     CK(stage_copy(L.vst, hp + 192, 8, s));
-    if (P.color) CK(cudaMemcpyAsync(L.klt, d_in + P.klt_off, 4 * kKltFloats, cudaMemcpyDeviceToDevice, s));
+    if (P.color) CK(stage_copy(L.klt, d_in + P.klt_off, 4 * kKltFloats, s));
     if (P.C) CK(stage_copy(L.step, hp + 256, 4 * P.C, s));
-    CK(cudaMemsetAsync(dst, 0, 8, s));
+    CK(dev_memset(dst, 0, 8, s));
     const int sms = ctx->num_sms;
     // a12's RLGR decode needs only the block tables: second stream, beside a11
     const bool attrs = P.C && d_attr;
@@ -1502,11 +1502,10 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         CK(stage_copy(L.fcolor, tp + o_fc, 4 * (size_t)F, s));
         for (uint32_t f = 0; f < F; ++f)
             if (P[f].color)
-                CK(cudaMemcpyAsync(L.klt + (uint64_t)f * kKltFloats, d_in + offs[f] + P[f].klt_off, 4 * kKltFloats,
-                                   cudaMemcpyDeviceToDevice, s));
+                CK(stage_copy(L.klt + (uint64_t)f * kKltFloats, d_in + offs[f] + P[f].klt_off, 4 * kKltFloats, s));
     }
     DevState *dst = ctx->st;
-    CK(cudaMemsetAsync(dst, 0, 8, s));
+    CK(dev_memset(dst, 0, 8, s));
     const int sms = ctx->num_sms;
 
     // a12's RLGR decode needs only the streams' block tables: it runs on the
@@ -2025,7 +2024,7 @@ gsnfs_status gsnfs_octree_encode(gsnfs_ctx *ctx, void *stream, const uint64_t *d
     ((uint32_t *)hp)[2] = J;
     CK(cudaMemcpyAsync(L.vstart, hp, 8, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(L.Jd, hp + 8, 4, cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(ctx->st, 0, 8, s));
+    CK(dev_memset(ctx->st, 0, 8, s));
     if (nv) CK(cudaMemcpyAsync(L.codes, d_codes, 8 * nv, cudaMemcpyDeviceToDevice, s));
     launch_gap_levels(L.codes, nv, L.gap, s);
     OccupancyOut oo{L.occ, (ob + 64) & ~(uint64_t)63, L.lsz, L.occ_off, L.hoff, L.opart};
@@ -2075,7 +2074,7 @@ gsnfs_status gsnfs_octree_decode(gsnfs_ctx *ctx, void *stream, const uint8_t *d_
     carve_decode(cv, L, P, ctx->num_sms, ctx->tune);
     st = grow_pinned(ctx, 4096);
     if (st) return st;
-    CK(cudaMemsetAsync(ctx->st, 0, 8, s));
+    CK(dev_memset(ctx->st, 0, 8, s));
     launch_octree_decode(d_occ, P.n_occ, J, P.lsz, L.nodes, L.pref, L.ppart, d_codes, ctx->st, ctx->num_sms, s);
     CK(cudaMemcpyAsync(ctx->pinned, ctx->st, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -2126,7 +2125,7 @@ gsnfs_status gsnfs_occupancy_section_encode(gsnfs_ctx *ctx, void *stream, const 
     hp[0] = 0;
     hp[1] = n;
     CK(cudaMemcpyAsync(occ_off, hp, 16, cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(ctx->st, 0, 8, s));
+    CK(dev_memset(ctx->st, 0, 8, s));
     RansFrames rf{1, d_in, occ_off, rans_chunk, chunk_off, freq, cum, mode, cw, ct, cp, slots, sec};
     launch_rans_encode(rf, ctx->st, nch, ctx->num_sms, s);
     stage_si_kernel<<<1, 1, 0, s>>>(sec, si, ctx->st);
@@ -2161,7 +2160,7 @@ gsnfs_status gsnfs_occupancy_section_decode(gsnfs_ctx *ctx, void *stream, const 
     P.nv = 0;
     st = parse_sections(hp, nullptr, P);
     if (st) return st;
-    CK(cudaMemsetAsync(ctx->st, 0, 8, s));
+    CK(dev_memset(ctx->st, 0, 8, s));
     if (P.occ_mode == 0) {
         if (n) CK(cudaMemcpyAsync(d_out, d_sec + 16, n, cudaMemcpyDeviceToDevice, s));
     } else if (P.occ_mode == 2) {
@@ -2220,7 +2219,7 @@ gsnfs_status gsnfs_raht_plan_create(gsnfs_ctx *ctx, void *stream, const uint64_t
     }
     Carve cv(pl->mem);
     carve(cv);
-    CK(cudaMemsetAsync(pl->st, 0, sizeof(DevState), s));
+    CK(dev_memset(pl->st, 0, sizeof(DevState), s));
     CK(cudaMemcpyAsync(nvd, &pl->nv, 8, cudaMemcpyHostToDevice, s));
     if (nv) launch_gap_levels(d_codes, nv, gap, s);
     launch_raht_prelude(pl->dev, gap, pl->st, nvd, ctx->num_sms, s);
@@ -2406,7 +2405,7 @@ gsnfs_status gsnfs_rlgr_encode_indices(gsnfs_ctx *ctx, void *stream, const int32
     hp[0] = 0;
     hp[1] = (uint32_t)nv;
     CK(cudaMemcpyAsync(vstart, hp, 8, cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(ovf, 0, 16, s));
+    CK(dev_memset(ovf, 0, 16, s));
     launch_rlgr_offsets(vstart, 1, B, 1, C, job_off, blk_off, s);
     launch_rlgr_encode_indices(d_q, vstart, C, B, d_slots, rlgr_slot_words(B, true), d_block_words, job_off, blk_off,
                                (nv + B - 1) / B, ovf, s);
@@ -2424,7 +2423,7 @@ gsnfs_status gsnfs_rlgr_decode_indices(gsnfs_ctx *ctx, void *stream, const uint3
     cudaStream_t s = (cudaStream_t)stream;
     gsnfs_status st = grow_pinned(ctx, 4096);
     if (st) return st;
-    CK(cudaMemsetAsync(ctx->st, 0, 8, s));
+    CK(dev_memset(ctx->st, 0, 8, s));
     const uint32_t sw = rlgr_slot_words(B, true);
     const uint64_t nb = (nv + B - 1) / B;
     launch_rlgr_decode_indices(d_slots, (uint64_t)C * nb * sw, d_block_words, sw, nv, C, B, d_q, ctx->st, s);

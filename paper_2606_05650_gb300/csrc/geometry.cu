@@ -533,12 +533,12 @@ void launch_dedup(const uint64_t *keys, uint64_t n, uint32_t frame_shift, uint32
                   cudaStream_t s, const uint32_t *vals, uint32_t *row0)
 {
     if (!vals) row0 = nullptr;
-    cudaMemsetAsync(vstart, 0xFF, sizeof(uint32_t) * (F + 1), s);
+    dev_memset(vstart, 0xFF, sizeof(uint32_t) * (F + 1), s);
     Chunks c = chunks_for(n, num_sms);
     if (n == 0) {
-        cudaMemsetAsync(partials, 0, sizeof(uint32_t) * (c.P + 1), s);
-        cudaMemsetAsync(seg, 0, sizeof(uint32_t), s);
-        cudaMemsetAsync(gap, (int)kInfLevel, 1, s);
+        dev_memset(partials, 0, sizeof(uint32_t) * (c.P + 1), s);
+        dev_memset(seg, 0, sizeof(uint32_t), s);
+        dev_memset(gap, (int)kInfLevel, 1, s);
     } else {
         dedup_up_kernel<<<c.P, kThreads, 0, s>>>(keys, n, c.chunk, partials);
         count_launch();

@@ -310,5 +310,7 @@ void launch_render_tiles(uint64_t n, const int4 *rect, const float *depth, const
 void launch_scan_u32_to_u64(const uint32_t *in, uint64_t n, uint64_t *out, uint64_t *partials, int num_sms,
                             cudaStream_t s);
 uint64_t scan_partial_words(uint64_t n, int num_sms);
+// stream-ordered device memset run as a kernel (arguments as cudaMemsetAsync)
+cudaError_t dev_memset(void *p, int value, size_t bytes, cudaStream_t s);
 
 }  // namespace gsnfs

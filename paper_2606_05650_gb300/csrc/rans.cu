@@ -293,7 +293,7 @@ uint64_t rans_chunk_slot_bytes(uint32_t chunk) { return 128 + 2 * (uint64_t)chun
 
 void launch_rans_encode(const RansFrames &r, DevState *st, uint64_t max_chunks, int num_sms, cudaStream_t s)
 {
-    cudaMemsetAsync(&st->hist[0][0], 0, sizeof(uint32_t) * 256 * r.F, s);
+    dev_memset(&st->hist[0][0], 0, sizeof(uint32_t) * 256 * r.F, s);
     dim3 g(num_sms, r.F);
     if (r.F > 8) g.x = (num_sms * 8 + r.F - 1) / r.F;
     hist_kernel<<<g, 256, 0, s>>>(r.occ, r.occ_off, st);

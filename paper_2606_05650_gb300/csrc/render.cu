@@ -218,7 +218,7 @@ void launch_render_tiles(uint64_t n, const int4 *rect, const float *depth, const
                          uint2 *ranges, float *image, int num_sms, cudaStream_t s)
 {
     const uint32_t tiles = (uint32_t)(cam.TX * cam.TY);
-    cudaMemsetAsync(ranges, 0, sizeof(uint2) * tiles, s);
+    dev_memset(ranges, 0, sizeof(uint2) * tiles, s);
     if (total) {
         emit_kernel<<<rgrid(n, num_sms), 256, 0, s>>>(n, rect, depth, count, offs, cam.TX, keys, vals);
         count_launch();

@@ -1,5 +1,7 @@
 // Exclusive prefix sums used to lay out variable-length outputs (block word
 // offsets of the RLGR payload).  Reduce-then-scan: no CTA waits on another.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace gsnfs {
@@ -73,7 +75,7 @@ void launch_scan_u32_to_u64(const uint32_t *in, uint64_t n, uint64_t *out, uint6
 {
     Geom g = geom(n, num_sms);
     if (n == 0) {
-        cudaMemsetAsync(out, 0, sizeof(uint64_t), s);
+        dev_memset(out, 0, sizeof(uint64_t), s);
         return;
     }
     up_kernel<<<g.P, kThreads, 0, s>>>(in, n, g.chunk, partials);
@@ -82,6 +84,35 @@ void launch_scan_u32_to_u64(const uint32_t *in, uint64_t n, uint64_t *out, uint6
     count_launch();
     down_kernel<<<g.P, kThreads, 0, s>>>(in, n, g.chunk, partials, out);
     count_launch();
+}
+
+
+// Device memset as a kernel (stream-ordered like cudaMemsetAsync, but never
+// queued on a copy engine behind a caller's bulk copies in flight).
+namespace {
+__global__ void memset_kernel(unsigned char *p, uint32_t v4, unsigned char v, uint64_t n)
+{
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t head = (16 - ((uintptr_t)p & 15)) & 15;
+    const uint64_t h = head < n ? head : n;
+    for (uint64_t i = t; i < h; i += nt) p[i] = v;
+    const uint64_t nvec = (n - h) / 16;
+    uint4 *q = reinterpret_cast<uint4 *>(p + h);
+    for (uint64_t i = t; i < nvec; i += nt) q[i] = make_uint4(v4, v4, v4, v4);
+    for (uint64_t i = h + 16 * nvec + t; i < n; i += nt) p[i] = v;
+}
+}  // namespace
+
+cudaError_t dev_memset(void *p, int value, size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) return cudaSuccess;
+    const unsigned char v = (unsigned char)value;
+    const uint32_t v4 = 0x01010101u * v;
+    const uint64_t units = (bytes + 15) / 16;
+    const uint32_t blocks = (uint32_t)std::min<uint64_t>((units + 255) / 256, 1024);
+    memset_kernel<<<blocks, 256, 0, s>>>(static_cast<unsigned char *>(p), v4, v, bytes);
+    count_launch();
+    return cudaGetLastError();
 }
 
 }  // namespace gsnfs
