@@ -134,10 +134,27 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
-def make_frames(rank, F):
+def make_frames(rank, F, n=N_GAUSS):
+    """The frames rank `rank` codes: its own dynamic scene (frames are independent units, so ranks share
+    no data and need no collective on the data path)."""
     from paper_2606_05650_gb300 import synthetic as syn
     scene = syn.DynamicScene(1000 + rank)
-    return [scene.frame(t, n=N_GAUSS) for t in range(F)]
+    return [scene.frame(t, n=n) for t in range(F)]
+
+
+def max_over_ranks(elapsed_ms, world, dist, device=None):
+    """The job's time: the slowest rank's timed region (all_reduce MAX; no-op at one rank)."""
+    if world <= 1:
+        return float(elapsed_ms)
+    import torch
+    t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, frames_per_rank, steps, elapsed_ms):
+    """Frames encoded and decoded per second by the whole job (weak scaling: every rank codes its own frames)."""
+    return world * frames_per_rank * steps / (elapsed_ms / 1e3)
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -205,11 +222,8 @@ def run_gpu(args):
     elapsed_ms = e0.elapsed_time(e1)
     stages = G.profile_read()
     G.profile_enable(False)
-    t = torch.tensor([elapsed_ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
-    value = world * F * args.steps / (elapsed_ms / 1e3)
+    elapsed_ms = max_over_ranks(elapsed_ms, world, dist, dev)
+    value = job_throughput(world, F, args.steps, elapsed_ms)
     nv_frames = np.diff(rows).astype(np.int64)
     stream_bytes = np.diff(offs).astype(np.int64)
 
