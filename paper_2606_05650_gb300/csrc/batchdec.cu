@@ -124,29 +124,40 @@ __global__ void roots_kernel(const DecFrame *fr, uint32_t F, uint64_t *nodes, ui
     (void)codes;
 }
 
-// one level d of Algorithm 3 for every frame with J > d
+// one level d of Algorithm 3 for every frame with J > d; a thread's nodes
+// mostly stay in one frame, so the frame's tables are looked up once per change
 __global__ void __launch_bounds__(256) expand_batch_kernel(const DecFrame *fr, uint32_t F, uint32_t d,
                                                            const uint64_t *lvl_pref, uint64_t count,
                                                            const uint8_t *__restrict__ occ_all,
                                                            const uint32_t *__restrict__ pref, uint64_t *nodes,
                                                            uint64_t *codes, DevState *st)
 {
+    uint64_t fbeg = 1, fend = 0;  // node range of the cached frame (empty at first)
+    uint32_t Md1 = 0, base = 0;
+    uint64_t bo = 0;
+    const uint64_t *src = nullptr;
+    uint64_t *dst = nullptr;
     for (uint64_t gp = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; gp < count;
          gp += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t f = find_frame(lvl_pref, F, gp);
-        const DecFrame &fd = fr[f];
-        const uint32_t p = (uint32_t)(gp - lvl_pref[f]);
-        const uint32_t Md1 = fd.lsz[d + 1];
-        const uint64_t bo = fd.occ_off + fd.boff[d];
-        const uint32_t base = pref[bo];
-        if (p == 0 && pref[bo + fd.lsz[d]] - base != Md1) set_error(&st->err, kErrCorrupt);
+        if (gp < fbeg || gp >= fend) {
+            const uint32_t f = find_frame(lvl_pref, F, gp);
+            const DecFrame &fd = fr[f];
+            fbeg = lvl_pref[f];
+            fend = lvl_pref[f + 1];
+            Md1 = fd.lsz[d + 1];
+            bo = fd.occ_off + fd.boff[d];
+            base = pref[bo];
+            src = nodes + fd.noff[d];
+            dst = (d + 1 == fd.J) ? codes + fd.vstart : nodes + fd.noff[d + 1];
+            if (gp == fbeg && pref[bo + fd.lsz[d]] - base != Md1) set_error(&st->err, kErrCorrupt);
+        }
+        const uint32_t p = (uint32_t)(gp - fbeg);
         const uint32_t byte = occ_all[bo + p];
         if (byte == 0) {
             set_error(&st->err, kErrCorrupt);
             continue;
         }
-        const uint64_t c = nodes[fd.noff[d] + p] << 3;
-        uint64_t *dst = (d + 1 == fd.J) ? codes + fd.vstart : nodes + fd.noff[d + 1];
+        const uint64_t c = src[p] << 3;
         uint32_t w = pref[bo + p] - base;
         for (uint32_t i = 0; i < 8; ++i)
             if (byte & (1u << i)) {
