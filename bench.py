@@ -457,13 +457,16 @@ def gpu_extras(args, G, torch, P, A, frames, qp, out, offs, dev, stream):
     hpos = torch.empty((F * N_GAUSS, 3), dtype=torch.float32).pin_memory()
     hatt = torch.empty((F * N_GAUSS, C), dtype=torch.float32).pin_memory()
 
+    pos1 = torch.empty((F * N_GAUSS, 3), dtype=torch.float32, device=dev)
+    att1 = torch.empty((F * N_GAUSS, C), dtype=torch.float32, device=dev)
+
     def e2e_step():
         for x, y in zip(hp + ha, dp + da):
             y.copy_(x, non_blocking=True)
         o, off = G.encode_batch(dp, da, [J] * F, [1.0], qp, out=out)
         n = int(off[-1])
         hout[:n].copy_(o[:n], non_blocking=True)
-        pos, attr, rows = G.decode_batch(o, off, C, F * N_GAUSS)
+        pos, attr, rows = G.decode_batch(o, off, C, F * N_GAUSS, pos_out=pos1, attr_out=att1)
         m = int(rows[-1])
         hpos[:m].copy_(pos, non_blocking=True)
         hatt[:m].copy_(attr, non_blocking=True)
@@ -482,8 +485,8 @@ def gpu_extras(args, G, torch, P, A, frames, qp, out, offs, dev, stream):
     dp2 = [dp, [torch.empty_like(x) for x in dp]]
     da2 = [da, [torch.empty_like(x) for x in da]]
     out2 = [out, torch.empty_like(out)]
-    pos2 = [torch.empty((F * N_GAUSS, 3), dtype=torch.float32, device=dev) for _ in range(2)]
-    att2 = [torch.empty((F * N_GAUSS, C), dtype=torch.float32, device=dev) for _ in range(2)]
+    pos2 = [pos1, torch.empty((F * N_GAUSS, 3), dtype=torch.float32, device=dev)]
+    att2 = [att1, torch.empty((F * N_GAUSS, C), dtype=torch.float32, device=dev)]
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_cmp = [torch.cuda.Event() for _ in range(2)]
     ev_out = [torch.cuda.Event() for _ in range(2)]
