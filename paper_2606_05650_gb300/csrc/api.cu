@@ -580,7 +580,8 @@ struct EncLayout {
         *chunk_top, *chunk_pos, *cum, *slots, *block_words, *overflow;
     const float **posp, **attrp;
     uint64_t *poff, *keys, *keys_alt, *codes, *occ_off, *chunk_off, *sec_bytes, *job_off, *blk_off, *block_off,
-        *spart;
+        *spart, *cta_lo;
+    uint32_t *cta_seg;  // segmented sort of several frames: per-CTA element ranges and segment bounds
     uint16_t *freq;
     uint8_t *gap, *occ, *chunk_slots, *groups;
     float *inv_step, *step, *Y, *pool, *center, *klt;
@@ -667,7 +668,9 @@ size_t carve_encode(Carve &cv, EncLayout &L, const EncodeReq &rq, int num_sms, b
     L.keys_alt = cv.take<uint64_t>(N + 1);
     L.vals = cv.take<uint32_t>(N + 1);
     L.vals_alt = cv.take<uint32_t>(N + 1);
-    L.hist = cv.take<uint32_t>(radix_sort_hist_words(N, num_sms));
+    L.hist = cv.take<uint32_t>(radix_sort_hist_words(N, num_sms, F));
+    L.cta_lo = cv.take<uint64_t>(radix_sort_max_ctas(N, num_sms) + F + 1);
+    L.cta_seg = cv.take<uint32_t>(2 * (radix_sort_max_ctas(N, num_sms) + F));
     L.codes = cv.take<uint64_t>(N + 1);
     L.seg = cv.take<uint32_t>(N + 2);
     L.row0 = cv.take<uint32_t>(N + 1);
@@ -793,7 +796,11 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
     o_step = o_inv + 4 * (size_t)R * C;
     o_srg = (o_step + 4 * (size_t)R * C + 7) & ~(size_t)7;
     o_grp = o_srg + 8 * (size_t)R * 256;
-    o_end = o_grp + 256;
+    // several frames: each frame's keys are sorted on their own (its Morton bits only; no frame pass)
+    const uint64_t max_ctas = radix_sort_max_ctas(N, ctx->num_sms) + F;
+    const size_t o_ctalo = (o_grp + 256 + 7) & ~(size_t)7;
+    const size_t o_ctaseg = o_ctalo + 8 * (max_ctas + 1);
+    o_end = o_ctaseg + 8 * max_ctas;
     const size_t o_dist = ((o_end + 63) & ~(size_t)63) + 64;
     const size_t dist_bytes = rq.dist ? 8 * (size_t)F * R * C : 0;
     st = grow_pinned(ctx, o_dist + dist_bytes + 64);
@@ -809,6 +816,9 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
         ((uint32_t *)(hp + o_J))[f] = rq.J[f];
     }
     ((uint64_t *)(hp + o_poff))[F] = acc;
+    const uint32_t sort_ctas = F > 1 ? radix_sort_segment_table((const uint64_t *)(hp + o_poff), F, ctx->num_sms,
+                                                                (uint64_t *)(hp + o_ctalo), (uint32_t *)(hp + o_ctaseg))
+                                     : 0u;
     for (uint32_t r = 0; r < R; ++r) {
         const double sc = rq.rung_scale ? rq.rung_scale[r] : 1.0;
         for (uint32_t c = 0; c < C; ++c) {
@@ -833,6 +843,10 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
             CK(stage_copy(L.steps_rg, hp + o_srg, 8 * (size_t)R * G, s));
             CK(stage_copy(L.groups, hp + o_grp, C, s));
         }
+        if (sort_ctas) {
+            CK(stage_copy(L.cta_lo, hp + o_ctalo, 8 * ((size_t)sort_ctas + 1), s));
+            CK(stage_copy(L.cta_seg, hp + o_ctaseg, 8 * (size_t)sort_ctas, s));
+        }
         CK(dev_memset(L.overflow, 0, 16, s));
 
         DevState *dst = ctx->st;
@@ -852,7 +866,10 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
         stage_end(s, kStVoxelize);
         // a2: radix sort
         stage_begin(s, kStSort);
-        bool alt = radix_sort(L.keys, L.vals, L.keys_alt, L.vals_alt, L.hist, N, nbits, sms, s);
+        // one frame: its Morton bits; several: each frame on its own (the frame bits need no pass)
+        bool alt = sort_ctas ? radix_sort_segments(L.keys, L.vals, L.keys_alt, L.vals_alt, L.hist, N, frame_shift,
+                                                   sort_ctas, L.cta_lo, L.cta_seg, sms, s)
+                             : radix_sort(L.keys, L.vals, L.keys_alt, L.vals_alt, L.hist, N, nbits, sms, s);
         stage_end(s, kStSort);
         const uint64_t *skeys = alt ? L.keys_alt : L.keys;
         const uint32_t *svals = alt ? L.vals_alt : L.vals;

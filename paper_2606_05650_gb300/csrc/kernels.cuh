@@ -38,7 +38,17 @@ void launch_voxelize(const FrameSet &fs, DevState *st, uint64_t n_total, uint64_
 // Returns true when the result is in (keys_alt, vals_alt).
 bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint32_t *hist,
                 uint64_t n, uint32_t nbits, int num_sms, cudaStream_t s);
-uint64_t radix_sort_hist_words(uint64_t n, int num_sms);
+// histogram words for n keys (room for `segments` extra CTAs of a segmented sort)
+uint64_t radix_sort_hist_words(uint64_t n, int num_sms, uint32_t segments = 0);
+// Segmented sort: segment f = elements [seg_lo[f], seg_lo[f + 1]) is sorted on its own (keys never leave it).
+// Host table of the CTAs (cta_lo: ctas + 1 element offsets, cta_seg: 2 per CTA, first CTA of its segment and of
+// the next), at most sort CTAs + segments entries; returns the CTA count.
+uint32_t radix_sort_segment_table(const uint64_t *seg_lo, uint32_t segments, int num_sms, uint64_t *cta_lo,
+                                  uint32_t *cta_seg);
+bool radix_sort_segments(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint32_t *hist,
+                         uint64_t n, uint32_t nbits, uint32_t ctas, const uint64_t *cta_lo, const uint32_t *cta_seg,
+                         int num_sms, cudaStream_t s);
+uint64_t radix_sort_max_ctas(uint64_t n, int num_sms);
 
 // ---- geometry.cu ----------------------------------------------------------
 // Dedup of sorted keys: codes[v], seg[v] (first sorted point of voxel v,

@@ -35,14 +35,30 @@ SortGeom sort_geom(uint64_t n, int num_sms)
     return g;
 }
 
+// CTA p sorts elements [b, e): p * chunk onwards, or cta_lo[p] .. cta_lo[p + 1]
+// when the array is cut into independently sorted segments
+__device__ __forceinline__ void cta_range(const uint64_t *cta_lo, uint64_t chunk, uint64_t n, uint64_t &b,
+                                          uint64_t &e)
+{
+    if (cta_lo) {
+        b = cta_lo[blockIdx.x];
+        e = cta_lo[blockIdx.x + 1];
+    } else {
+        b = (uint64_t)blockIdx.x * chunk;
+        e = b + chunk;
+        if (e > n) e = n;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) upsweep_kernel(const uint64_t *__restrict__ keys, uint64_t n,
-                                                           uint32_t shift, uint64_t chunk, uint32_t *hist)
+                                                           uint32_t shift, uint64_t chunk, uint32_t *hist,
+                                                           const uint64_t *__restrict__ cta_lo)
 {
     __shared__ uint32_t h[kRadix];
     h[threadIdx.x] = 0;
     __syncthreads();
-    uint64_t b = (uint64_t)blockIdx.x * chunk, e = b + chunk;
-    if (e > n) e = n;
+    uint64_t b, e;
+    cta_range(cta_lo, chunk, n, b, e);
     for (uint64_t i = b + threadIdx.x; i < e; i += kThreads) atomicAdd(&h[(keys[i] >> shift) & 0xFF], 1u);
     __syncthreads();
     hist[(uint64_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
@@ -70,7 +86,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) downsweep_kernel(const u
                                                              uint32_t shift, uint64_t chunk,
                                                              const uint32_t *__restrict__ hist,
                                                              uint64_t *__restrict__ keys_out,
-                                                             uint32_t *__restrict__ vals_out)
+                                                             uint32_t *__restrict__ vals_out,
+                                                             const uint64_t *__restrict__ cta_lo,
+                                                             const uint32_t *__restrict__ cta_seg)
 {
     __shared__ uint32_t s_base[kRadix];
     __shared__ uint32_t s_wcnt[kWarps][kRadix];
@@ -81,13 +99,21 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) downsweep_kernel(const u
     __shared__ uint32_t s_scan[33];
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    {  // digit d starts after all smaller digits, then after the same digit of earlier CTAs
+    const uint32_t P = gridDim.x;
+    if (!cta_seg) {  // digit d starts after all smaller digits, then after the same digit of earlier CTAs
         uint32_t tot;
-        const uint32_t doff = block_exclusive_sum<uint32_t>(hist[(uint64_t)kRadix * gridDim.x + tid], s_scan, &tot);
-        s_base[tid] = doff + hist[(uint64_t)tid * gridDim.x + blockIdx.x];
+        const uint32_t doff = block_exclusive_sum<uint32_t>(hist[(uint64_t)kRadix * P + tid], s_scan, &tot);
+        s_base[tid] = doff + hist[(uint64_t)tid * P + blockIdx.x];
+    } else {  // the same within this CTA's segment (CTAs p0 .. p1 - 1), which starts at element cta_lo[p0]
+        const uint32_t p0 = cta_seg[2 * blockIdx.x], p1 = cta_seg[2 * blockIdx.x + 1];
+        const uint32_t c0 = hist[(uint64_t)tid * P + p0];
+        const uint32_t c1 = p1 < P ? hist[(uint64_t)tid * P + p1] : hist[(uint64_t)kRadix * P + tid];
+        uint32_t tot;
+        const uint32_t doff = block_exclusive_sum<uint32_t>(c1 - c0, s_scan, &tot);
+        s_base[tid] = (uint32_t)cta_lo[p0] + doff + (hist[(uint64_t)tid * P + blockIdx.x] - c0);
     }
-    uint64_t cb = (uint64_t)blockIdx.x * chunk, ce = cb + chunk;
-    if (ce > n) ce = n;
+    uint64_t cb, ce;
+    cta_range(cta_lo, chunk, n, cb, ce);
     const uint32_t ltmask = lanemask_lt();
     for (uint64_t t0 = cb; t0 < ce; t0 += kTile) {
         for (int i = tid; i < kWarps * kRadix; i += kThreads) (&s_wcnt[0][0])[i] = 0;
@@ -150,25 +176,43 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) downsweep_kernel(const u
 
 }  // namespace
 
-uint64_t radix_sort_hist_words(uint64_t n, int num_sms)
+uint64_t radix_sort_hist_words(uint64_t n, int num_sms, uint32_t segments)
 {
-    return (uint64_t)kRadix * sort_geom(n, num_sms).P + kRadix;
+    return (uint64_t)kRadix * (sort_geom(n, num_sms).P + segments) + kRadix;
 }
 
-bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint32_t *hist,
-                uint64_t n, uint32_t nbits, int num_sms, cudaStream_t s)
+uint64_t radix_sort_max_ctas(uint64_t n, int num_sms) { return sort_geom(n, num_sms).P; }
+
+uint32_t radix_sort_segment_table(const uint64_t *seg_lo, uint32_t segments, int num_sms, uint64_t *cta_lo,
+                                  uint32_t *cta_seg)
 {
-    if (n <= 1 || nbits == 0) return false;
-    SortGeom g = sort_geom(n, num_sms);
+    const uint64_t n = seg_lo[segments];
+    const SortGeom g = sort_geom(n, num_sms);
+    uint32_t P = 0;
+    for (uint32_t f = 0; f < segments; ++f) {
+        const uint64_t b = seg_lo[f], e = seg_lo[f + 1];
+        const uint32_t p0 = P;
+        for (uint64_t x = b; x < e; x += g.chunk) cta_lo[P++] = x;
+        for (uint32_t p = p0; p < P; ++p) cta_seg[2 * p] = p0;
+        for (uint32_t p = p0; p < P; ++p) cta_seg[2 * p + 1] = P;
+    }
+    cta_lo[P] = n;
+    return P;
+}
+
+static bool sort_passes(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint32_t *hist,
+                        uint64_t n, uint32_t nbits, uint32_t P, uint64_t chunk, const uint64_t *cta_lo,
+                        const uint32_t *cta_seg, cudaStream_t s)
+{
     uint64_t *ki = keys, *ko = keys_alt;
     uint32_t *vi = vals, *vo = vals_alt;
     bool flipped = false;
     for (uint32_t shift = 0; shift < nbits; shift += 8) {
-        upsweep_kernel<<<g.P, kThreads, 0, s>>>(ki, n, shift, g.chunk, hist);
+        upsweep_kernel<<<P, kThreads, 0, s>>>(ki, n, shift, chunk, hist, cta_lo);
         count_launch();
-        scan_cols_kernel<<<kRadix / 8, 256, 0, s>>>(hist, g.P);
+        scan_cols_kernel<<<kRadix / 8, 256, 0, s>>>(hist, P);
         count_launch();
-        downsweep_kernel<<<g.P, kThreads, 0, s>>>(ki, vi, n, shift, g.chunk, hist, ko, vo);
+        downsweep_kernel<<<P, kThreads, 0, s>>>(ki, vi, n, shift, chunk, hist, ko, vo, cta_lo, cta_seg);
         count_launch();
         uint64_t *tk = ki;
         ki = ko;
@@ -179,6 +223,23 @@ bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *va
         flipped = !flipped;
     }
     return flipped;
+}
+
+bool radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint32_t *hist,
+                uint64_t n, uint32_t nbits, int num_sms, cudaStream_t s)
+{
+    if (n <= 1 || nbits == 0) return false;
+    const SortGeom g = sort_geom(n, num_sms);
+    return sort_passes(keys, vals, keys_alt, vals_alt, hist, n, nbits, g.P, g.chunk, nullptr, nullptr, s);
+}
+
+bool radix_sort_segments(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint32_t *hist,
+                         uint64_t n, uint32_t nbits, uint32_t ctas, const uint64_t *cta_lo, const uint32_t *cta_seg,
+                         int num_sms, cudaStream_t s)
+{
+    if (n <= 1 || nbits == 0 || ctas == 0) return false;
+    return sort_passes(keys, vals, keys_alt, vals_alt, hist, n, nbits, ctas, sort_geom(n, num_sms).chunk, cta_lo,
+                       cta_seg, s);
 }
 
 }  // namespace gsnfs
