@@ -250,17 +250,26 @@ __global__ void __launch_bounds__(kThreads) occ_down_kernel(const uint64_t *__re
         }
         __syncthreads();
         for (int h = 1; h <= hw; ++h) {
+            // lane l's node at height h is the last node start at or before l, so the
+            // target words are non-decreasing along the warp: the bits of each word are
+            // OR-ed over its run of lanes (doubling shuffles) and its first lane writes
             uint32_t b = __ballot_sync(0xFFFFFFFFu, s >= h);
             bool child = ok && (s + 1 >= h);
             uint32_t incl = s_run[h] + s_w[w][h] + __popc(b & lemask);
             uint64_t tgt = base + s_hoff[h] + (uint64_t)incl - 1u;
-            uint32_t key = child ? (uint32_t)(tgt >> 2) : (0xFFFFFFE0u | (uint32_t)lane);
-            uint32_t bit = child ? (1u << (((m >> (3 * (h - 1))) & 7u) + 8u * (uint32_t)(tgt & 3u))) : 0u;
-            uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
-            uint32_t orv = __reduce_or_sync(peers, bit);
-            if (child && (uint32_t)lane == (uint32_t)(__ffs(peers) - 1)) {
-                if ((tgt >> 2) < (occ_capacity >> 2))
-                    atomicOr(occ_words + (tgt >> 2), orv);
+            const uint64_t wd = tgt >> 2;
+            uint32_t key = ok ? (wd < 0xFFFFFFFEull ? (uint32_t)wd : 0xFFFFFFFEu) : 0xFFFFFFFFu;
+            uint32_t orv = child ? (1u << (((m >> (3 * (h - 1))) & 7u) + 8u * (uint32_t)(tgt & 3u))) : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_down_sync(0xFFFFFFFFu, orv, o);
+                const uint32_t k2 = __shfl_down_sync(0xFFFFFFFFu, key, o);
+                if (lane + o < 32 && k2 == key) orv |= v;
+            }
+            const uint32_t kp = __shfl_up_sync(0xFFFFFFFFu, key, 1);
+            if (ok && orv && (lane == 0 || kp != key)) {
+                if ((uint64_t)key < (occ_capacity >> 2) && key != 0xFFFFFFFEu)
+                    atomicOr(occ_words + key, orv);
                 else
                     set_error(&st->err, kErrCapacity);
             }
