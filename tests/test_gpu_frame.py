@@ -164,6 +164,22 @@ def test_batched_ladder_equals_plain(G, orc):
     assert d["codes"].size > 0
 
 
+def test_batched_segments_with_empty_and_single_point_frames(G, orc):
+    """The batched encoder sorts each frame as its own segment: frames that are
+    empty, hold one point, fit one sort CTA or span many still give the streams
+    of one-frame calls."""
+    sizes = [0, 1, 70_000, 2, 0, 4096, 300_001]
+    Js = [10, 16, 17, 5, 12, 16, 18]
+    frames = [syn.DynamicScene(13).frame(t, n=n) if n else (np.zeros((0, 3), np.float32), np.zeros((0, 56), np.float32))
+              for t, n in enumerate(sizes)]
+    qp = _qp(G, 56)
+    out, offs = G.encode_batch([_dev(p) for p, _ in frames], [_dev(a) for _, a in frames], Js, [1.0], qp)
+    host = out.cpu().numpy()
+    for f, ((pos, attr), J) in enumerate(zip(frames, Js)):
+        plain, *_ = G.encode_frame(_dev(pos), _dev(attr), J, qp)
+        assert np.array_equal(host[int(offs[f]):int(offs[f + 1])], plain.cpu().numpy()), f
+
+
 def test_batched_decoder_equals_per_frame_decoding(G, orc):
     # frames of uneven size and depth (one empty, one tiny) decoded in one batch
     frames = [syn.DynamicScene(11).frame(t, n=n) for t, n in enumerate([40_000, 3, 150_000, 0, 9_000])]
