@@ -1,0 +1,66 @@
+"""Host logic of the benchmark line: the roofline object (dominant kernel by
+its serialised GPU share, algorithmic bytes over the event time, fraction of
+the measured peak), the ncu traffic figure withdrawn once the kernel's source
+changed, and the clock-sample parser (throttle reasons, median SM clock)."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _frames(F, n):
+    return [(np.zeros((n, 3), np.float32), None) for _ in range(F)]
+
+
+def test_roofline_names_the_dominant_kernel_and_computes_the_fraction():
+    F, n, steps, C = 8, 1000, 10, bench.C
+    nv = np.full(F, n)
+    sb = np.full(F, 50_000)
+    stages = {"raht_forward_pass0": (10.0, steps), "raht_inverse_pass0": (6.0, steps),
+              "rlgr_encode": (9.0, steps), "rlgr_decode": (12.0, steps)}  # decode's event time is the largest
+    r = bench.roofline(stages, _frames(F, n), nv, sb, steps, F, 6000.0, "measured")
+    assert r["kernel"] == bench.DOMINANT == "raht_forward_pass0"
+    alg = 4 * C * (F * n + F * n)  # gathered input rows and written coefficient rows, one launch per step
+    assert r["bytes_per_launch"] == alg
+    assert np.isclose(r["achieved"], round(alg / (1.0 / 1e3) / 1e9, 1))
+    assert np.isclose(r["frac"], round(r["achieved"] / 6000.0, 4), atol=1e-4)
+    assert set(r["all"]) == set(stages)
+    # without the named kernel the largest event time decides
+    del stages["raht_forward_pass0"]
+    r2 = bench.roofline(stages, _frames(F, n), nv, sb, steps, F, 6000.0, "measured")
+    assert r2["kernel"] == "rlgr_decode"
+
+
+def test_traffic_is_withdrawn_when_the_source_changed(monkeypatch):
+    ent = bench.TRAFFIC["raht_forward_pass0"]
+    got = bench.measured_traffic("raht_forward_pass0", 8)
+    path = os.path.join(ROOT, "paper_2606_05650_gb300", ent[1])
+    import hashlib
+    same = hashlib.sha1(open(path, "rb").read()).hexdigest() == ent[2]
+    assert (got == int(ent[0] * 8)) if same else got is None
+    monkeypatch.setitem(bench.TRAFFIC, "raht_forward_pass0", (ent[0], ent[1], "0" * 40))
+    assert bench.measured_traffic("raht_forward_pass0", 8) is None
+    assert bench.measured_traffic("no_such_kernel", 8) is None
+
+
+def test_clock_samples_parse_reasons_and_median():
+    cs = bench.ClockSampler(0)
+
+    class _P:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+    cs.proc = _P()
+    cs.lines = ["0, 2070, 2070, 500.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+                "0, 2055, 2070, 610.5, 0x4, Not Active, Not Active, Not Active, Active",
+                "0, 2070, 2070, 590.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+                "garbage"]
+    r = cs.stop()
+    assert r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0 and r["samples"] == 3
+    assert r["reasons"] == ["sw_power_cap"] and r["power_w_max"] == 610.5
