@@ -1,6 +1,7 @@
 // LSD radix sort of (64-bit Morton key, 32-bit point index) pairs
 // (Algorithm 1: "RadixSort" of the Morton codes).  Only the 3J significant
-// key bits (plus the frame-id bits of a batch) are sorted, 8 bits per pass.
+// key bits are sorted, 8 bits per pass; the frames of a batch, which arrive
+// grouped, are sorted as separate segments so that their id bits need no pass.
 //
 // Each pass is reduce-then-scan: every CTA owns one contiguous chunk of the
 // array, counts its digits (upsweep), one CTA scans the digit-major count
