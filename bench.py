@@ -366,6 +366,9 @@ def gpu_extras(args, G, torch, P, A, frames, qp, out, offs, dev, stream):
                     "encode_decode_fps": round(1e3 / (statistics.mean(enc_ms) + statistics.mean(dec_ms)), 2),
                     "encode_ms_p50": round(q(enc_ms, 50), 3), "encode_ms_p99": round(q(enc_ms, 99), 3),
                     "decode_ms_p50": round(q(dec_ms, 50), 3), "decode_ms_p99": round(q(dec_ms, 99), 3)}
+    # encoder reconstruction (the decoded frame returned by the encode call itself): plain encode with it
+    trec = _timed_calls(torch, stream, lambda k=0: G.encode_frame(P[k % F], A[k % F], J, qp, out=buf, recon=True), F)
+    res["plain"]["encode_with_reconstruction_ms_p50"] = round(q(trec, 50), 3)
     # differentiable codec layer: 500,000 Gaussians at depth 16, forward
     # A_hat = T^T(step q(T A)) and its straight-through backward T^T T g
     from paper_2606_05650_gb300 import synthetic as syn
