@@ -12,7 +12,6 @@ namespace {
 
 constexpr uint32_t kProbBits = 15;
 constexpr uint32_t kM = 1u << kProbBits;
-constexpr uint32_t kL = 1u << 16;
 
 template <typename T>
 __device__ __forceinline__ uint32_t find_frame(const T *pref, uint32_t F, uint64_t x)
@@ -159,11 +158,10 @@ __global__ void __launch_bounds__(256) expand_batch_kernel(const DecFrame *fr, u
         }
         const uint64_t c = src[p] << 3;
         uint32_t w = pref[bo + p] - base;
-        for (uint32_t i = 0; i < 8; ++i)
-            if (byte & (1u << i)) {
-                if (w < Md1) dst[w] = c + i;
-                ++w;
-            }
+        for (uint32_t bits = byte; bits; bits &= bits - 1u) {  // set bits in increasing order
+            if (w < Md1) dst[w] = c + (uint32_t)(__ffs(bits) - 1);
+            ++w;
+        }
     }
 }
 

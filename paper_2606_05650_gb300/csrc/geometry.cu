@@ -378,11 +378,10 @@ __global__ void __launch_bounds__(kThreads) expand_kernel(const uint64_t *__rest
         }
         uint64_t c = Ld[p] << 3;
         uint32_t w = pref[boff + p] - base;
-        for (uint32_t i = 0; i < 8; ++i)
-            if (byte & (1u << i)) {
-                if (w < Md1) Ld1[w] = c + i;
-                ++w;
-            }
+        for (uint32_t bits = byte; bits; bits &= bits - 1u) {  // set bits in increasing order
+            if (w < Md1) Ld1[w] = c + (uint32_t)(__ffs(bits) - 1);
+            ++w;
+        }
     }
 }
 
@@ -413,11 +412,10 @@ __global__ void __launch_bounds__(1024) expand_top_kernel(LevelTable lt, uint32_
             }
             const uint64_t c = Ld[p] << 3;
             uint32_t w = pref[boff + p] - base;
-            for (uint32_t i = 0; i < 8; ++i)
-                if (byte & (1u << i)) {
-                    if (w < Md1) Ld1[w] = c + i;
-                    ++w;
-                }
+            for (uint32_t bits = byte; bits; bits &= bits - 1u) {  // set bits in increasing order
+                if (w < Md1) Ld1[w] = c + (uint32_t)(__ffs(bits) - 1);
+                ++w;
+            }
         }
         __threadfence_block();
         __syncthreads();
