@@ -72,3 +72,45 @@ def test_front_to_back_occlusion_and_empty(orc):
     assert np.allclose(orc.render(np.zeros((0, 3)), np.zeros((0, 56)), VIEW, 100, 100, 32, 32, 32, 32, bg=bg), bg)
     behind, ab = _gauss([0, 0, -1.0], np.log(0.05), 20.0, [1, 1, 1])
     assert np.allclose(orc.render(behind[None], ab[None], VIEW, 100, 100, 16, 16, 32, 32, bg=bg), bg)
+
+
+def test_sh_basis_equals_library_real_harmonics(orc):
+    """Every sign and constant of the 16 functions: the real harmonics built
+    from scipy's complex ones (Condon-Shortley phase kept): sqrt(2) Im Y_l^|m|
+    for m < 0, Y_l^0, sqrt(2) Re Y_l^m for m > 0, in the order l, m = -l..l."""
+    sp = __import__("pytest").importorskip("scipy.special")
+    if not hasattr(sp, "sph_harm_y"):
+        __import__("pytest").skip("scipy without sph_harm_y")
+    rng = np.random.default_rng(4)
+    d = rng.normal(size=(64, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    for v in d:
+        theta, phi = np.arccos(v[2]), np.arctan2(v[1], v[0])
+        ref = []
+        for l in range(4):
+            for m in range(-l, l + 1):
+                Y = sp.sph_harm_y(l, abs(m), theta, phi)
+                ref.append(Y.real if m == 0 else np.sqrt(2) * (Y.real if m > 0 else Y.imag))
+        assert np.allclose(orc.sh_basis(v), ref, atol=1e-12)
+
+
+def test_rotated_anisotropic_gaussian_closed_form(orc):
+    """A Gaussian turned by 0.6 rad about the viewing axis with unequal scales:
+    its footprint is (f/z)^2 R2 diag(s1^2, s2^2) R2^T + 0.3 I, which pins the
+    quaternion-to-rotation convention, the covariance and the conic."""
+    f, W, H, zc, th = 100.0, 64, 64, 2.0, 0.6
+    s = np.array([0.05, 0.01, 0.02])
+    p, a = _gauss([0, 0, zc], np.log(s), 0.0, [0.3, 0.2, 0.1])
+    a[3:7] = [np.cos(th / 2), 0, 0, np.sin(th / 2)]  # (w, x, y, z): rotation by th about z
+    img = orc.render(p[None], a[None], VIEW, f, f, W / 2 + 0.5, H / 2 + 0.5, W, H)
+    R2 = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    S2 = (f / zc) ** 2 * R2 @ np.diag(s[:2] ** 2) @ R2.T + 0.3 * np.eye(2)
+    Q = np.linalg.inv(S2)
+    col = np.maximum(0.5 / np.sqrt(np.pi) * np.array([0.3, 0.2, 0.1]) + 0.5, 0)
+    for dx, dy in ((0, 0), (2, 1), (-2, -1), (1, -2), (3, 2), (0, 3)):
+        d = np.array([dx, dy], dtype=np.float64)
+        alpha = min(0.99, 0.5 * np.exp(-0.5 * d @ Q @ d))
+        want = col * alpha if alpha >= 1 / 255 else np.zeros(3)
+        assert np.allclose(img[32 + dy, 32 + dx], want, atol=1e-12), (dx, dy)
+    # the long axis follows the rotation: (2, 1) lies near it, (1, -2) across it
+    assert img[33, 34, 0] > img[30, 33, 0]
