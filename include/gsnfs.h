@@ -2,7 +2,11 @@
  * gsnfs.h -- C ABI of the GB300 (sm_103a) implementation of the GS-NFS
  * per-frame codec hot path (arxiv 2606.05650): octree geometry coding of
  * voxelised Gaussian positions and RAHT attribute coding with quantisation
- * and entropy coding, plus the matching decoder.
+ * and entropy coding, plus the matching decoder; beside the codec, a batched
+ * frames x rungs ladder with per-stream distortion for rate-distortion
+ * selection, level-of-detail decoding, SH colour decorrelation, the RAHT
+ * transforms as standalone (FP32 and FP64) calls, and a splat rasteriser for
+ * rendered-view quality of decoded frames.
  *
  * Conventions for every entry point
  *   - Pointers named d_* are DEVICE memory owned by the caller; h_* are host
