@@ -154,6 +154,18 @@ def max_over_ranks(elapsed_ms, world, dist, device=None):
     return float(t.item())
 
 
+# Stage-minimum bytes per Gaussian of one encode + decode round trip at C = 56 (each stage reading and writing its
+# compulsory bytes once, stages unfused): encode 1,244 (voxelise 36, sort 24, merge 468, occupancy 15, rANS 5,
+# prelude 24, forward 448, quantise + RLGR 224), decode 758 (geometry 30: occupancy decode, codes, centres;
+# prelude 24; RLGR 256: stream read, coefficients written; inverse 448).
+PIPELINE_BYTES_PER_GAUSSIAN = 1244 + 758
+
+
+def pipeline_fraction(frames_per_s, gaussians_per_frame, peak_gbs):
+    """End-to-end roofline fraction: frames/s x stage-minimum bytes per frame / peak HBM bandwidth."""
+    return frames_per_s * gaussians_per_frame * PIPELINE_BYTES_PER_GAUSSIAN / (peak_gbs * 1e9)
+
+
 def job_throughput(world, frames_per_rank, steps, elapsed_ms):
     """Frames encoded and decoded per second by the whole job (weak scaling: every rank codes its own frames)."""
     return world * frames_per_rank * steps / (elapsed_ms / 1e3)
@@ -252,6 +264,7 @@ def run_gpu(args):
             "voxels_per_frame": int(nv_frames.mean()), "bytes_per_frame": int(stream_bytes.mean()),
             "bits_per_gaussian": round(8 * float(stream_bytes.mean()) / N_GAUSS, 3),
             "roofline": roof,
+            "pipeline_fraction": round(pipeline_fraction(value, N_GAUSS, roof["peak"]), 4) if roof else None,
             "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in stages.items() if v[1]},
             "gpu_launches": int(launches),
             "clocks": ck,

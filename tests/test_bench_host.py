@@ -64,3 +64,10 @@ def test_clock_samples_parse_reasons_and_median():
     r = cs.stop()
     assert r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0 and r["samples"] == 3
     assert r["reasons"] == ["sw_power_cap"] and r["power_w_max"] == 610.5
+
+
+def test_pipeline_fraction():
+    # 1,000 frames/s of 1M Gaussians at the stage-minimum bytes against a 6,781 GB/s peak
+    v = bench.pipeline_fraction(1000.0, 1_000_000, 6781.4)
+    assert np.isclose(v, 1000 * 1e6 * bench.PIPELINE_BYTES_PER_GAUSSIAN / 6781.4e9)
+    assert 1900 < bench.PIPELINE_BYTES_PER_GAUSSIAN < 2300  # about 1.25 KB encode + 0.75 KB decode
