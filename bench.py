@@ -592,13 +592,37 @@ def _oracle_sample(part):
     return _oracle_frame((1000, 0), REF_SAMPLE, part)
 
 
+def host_cpu():
+    """Host CPU description for the baseline: logical cores and the model line of /proc/cpuinfo (or the
+    implementer / part ids on Arm hosts that print no model name)."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        with open("/proc/cpuinfo") as f:
+            lines = f.read().splitlines()
+    except OSError:
+        return info
+    kv = {}
+    for ln in lines:
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            kv.setdefault(k.strip(), v.strip())
+    for k in ("model name", "Model", "Hardware"):
+        if kv.get(k):
+            info["model"] = kv[k]
+            return info
+    if kv.get("CPU implementer"):
+        info["model"] = f"implementer {kv['CPU implementer']} part {kv.get('CPU part', '?')}"
+    return info
+
+
 def cpu_baseline():
     """The oracle as it stands, one 1M-Gaussian frame on one host core."""
     from oracle import oracle as orc
     orc.build()
     dt = _oracle_frame((1000, 0))
     return {"value": round(1.0 / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 frame of {N_GAUSS} Gaussians (encode + decode, FP64 C oracle, single thread), {dt:.1f} s"}
+            "sample": f"1 frame of {N_GAUSS} Gaussians (encode + decode, FP64 C oracle, single thread), {dt:.1f} s",
+            "host": host_cpu()}
 
 
 def run_reference(args):
@@ -631,7 +655,7 @@ def run_reference(args):
            "config": {"workload": f"dynamic 3DGS frames, {N_GAUSS} Gaussians x {C} float32 attributes, depth {J}, "
                                   f"encode + decode of every frame", "frames_per_step": workers * REF_SAMPLE},
            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": workers, "kind": "oracle",
-                            "sample": sample},
+                            "sample": sample, "host": host_cpu()},
            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(res), flush=True)
 

@@ -71,3 +71,9 @@ def test_pipeline_fraction():
     v = bench.pipeline_fraction(1000.0, 1_000_000, 6781.4)
     assert np.isclose(v, 1000 * 1e6 * bench.PIPELINE_BYTES_PER_GAUSSIAN / 6781.4e9)
     assert 1900 < bench.PIPELINE_BYTES_PER_GAUSSIAN < 2300  # about 1.25 KB encode + 0.75 KB decode
+
+
+def test_host_cpu_description():
+    h = bench.host_cpu()
+    assert h["nproc"] >= 1
+    assert "model" not in h or isinstance(h["model"], str)
