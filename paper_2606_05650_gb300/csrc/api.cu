@@ -27,6 +27,7 @@
 
 #include "../../include/gsnfs.h"
 #include "kernels.cuh"
+#include "status.cuh"
 
 using namespace gsnfs;
 
@@ -276,17 +277,6 @@ cudaError_t stage_copy(void *dst, const void *src, size_t n, cudaStream_t s)
                                              n);
     count_launch();
     return cudaGetLastError();
-}
-
-gsnfs_status map_dev_error(uint32_t e)
-{
-    switch (e) {
-    case 0: return GSNFS_OK;
-    case kErrCorrupt: return GSNFS_ERR_CORRUPT;
-    case kErrCapacity: return GSNFS_ERR_CAPACITY;
-    case kErrTimeout: return GSNFS_ERR_TIMEOUT;
-    default: return GSNFS_ERR_CUDA;
-    }
 }
 
 __host__ __device__ inline uint64_t pad8(uint64_t x) { return (x + 7) & ~7ull; }

@@ -21,6 +21,7 @@
 
 #include "../../include/gsnfs.h"
 #include "kernels.cuh"
+#include "status.cuh"
 
 using namespace gsnfs;
 
@@ -94,6 +95,9 @@ extern "C" gsnfs_status gsnfs_octree_encode_static(void *stream, const uint64_t 
     gsnfs_status st = scratch_for_current_device(&ds);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    // A launch error left pending by the caller's earlier work would otherwise
+    // be read below as this call's own; clear it before launching.
+    (void)cudaGetLastError();
     unsigned char *b = ds->base;
     DevState *dst = (DevState *)b;
     unsigned char *small = b + kStatePart;
@@ -121,7 +125,6 @@ extern "C" gsnfs_status gsnfs_octree_encode_static(void *stream, const uint64_t 
         return GSNFS_ERR_CUDA;
     for (uint32_t d = 0; d <= J; ++d) h_level_sizes[d] = h_lsz[d];
     if (out_occ_bytes) *out_occ_bytes = h_off[1];
-    if (h_err == kErrCapacity || h_off[1] > occ_capacity) return GSNFS_ERR_CAPACITY;
-    if (h_err) return GSNFS_ERR_CUDA;
-    return GSNFS_OK;
+    if (h_off[1] > occ_capacity) return GSNFS_ERR_CAPACITY;
+    return map_dev_error(h_err);
 }

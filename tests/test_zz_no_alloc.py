@@ -30,17 +30,23 @@ def G():
     return gsnfs
 
 
-def _static_encode(G, codes, J):
+def _static_call(G, codes, J, cap):
+    """One call through the C ABI: (status, occupancy bytes written, level sizes, reported byte count)."""
     nv = codes.shape[0]
-    cap = (8 * max(nv, 1) * J + 64 + 3) & ~3
-    occ = torch.full((cap,), 0xAB, dtype=torch.uint8, device="cuda")  # garbage the call must not keep
+    occ = torch.full((max(cap, 4),), 0xAB, dtype=torch.uint8, device="cuda")  # garbage the call must not keep
     lsz = (ct.c_uint32 * (J + 1))()
     nb = ct.c_uint64()
     stream = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
     rc = G.lib().gsnfs_octree_encode_static(stream, ct.c_void_p(codes.data_ptr()), nv, J, ct.c_void_p(occ.data_ptr()),
                                             cap, lsz, ct.byref(nb))
+    return rc, occ[: min(nb.value, cap)].cpu().numpy(), np.array(lsz[:], dtype=np.uint32), nb.value
+
+
+def _static_encode(G, codes, J):
+    nv = codes.shape[0]
+    rc, occ, lsz, _ = _static_call(G, codes, J, (8 * max(nv, 1) * J + 64 + 3) & ~3)
     assert rc == 0, G.lib().gsnfs_status_string(rc)
-    return occ[: nb.value].cpu().numpy(), np.array(lsz[:], dtype=np.uint32)
+    return occ, lsz
 
 
 def _codes(orc, seed, n, J):
@@ -68,3 +74,31 @@ def test_static_scratch_rejects_sizes_beyond_its_maximum(G):
                                       ct.c_void_p(codes.data_ptr()), 1048577, 16, ct.c_void_p(occ.data_ptr()), 64,
                                       lsz, ct.byref(nb))
     assert rc == -7  # GSNFS_ERR_UNSUPPORTED
+
+
+def test_static_capacity_is_counted_in_whole_words(G, orc):
+    """Bytes are written as 32-bit words: a capacity equal to a byte count that is not a multiple of 4 is
+    too small (GSNFS_ERR_CAPACITY with the byte count reported); rounded up to 4 it suffices."""
+    for seed in range(3, 40):
+        codes = _codes(orc, seed, 3_000 + 97 * seed, 11)
+        ref_occ, ref_lsz = G.octree_encode(codes, 11)
+        nb = int(ref_occ.numel())
+        if nb % 4:
+            break
+    assert nb % 4, "no test frame with a byte count off a word boundary"
+    rc, _, _, reported = _static_call(G, codes, 11, nb)
+    assert rc == -2 and reported == nb  # GSNFS_ERR_CAPACITY
+    rc, occ, lsz, reported = _static_call(G, codes, 11, (nb + 3) & ~3)
+    assert rc == 0 and reported == nb
+    assert np.array_equal(lsz, ref_lsz)
+    assert np.array_equal(occ, ref_occ.cpu().numpy())
+
+
+def test_static_empty_frame(G):
+    """No voxels: every level is empty, as with the allocating encoder."""
+    codes = torch.zeros(0, dtype=torch.int64, device="cuda")
+    for J in (1, 16):
+        rc, occ, lsz, reported = _static_call(G, codes, J, 64)
+        ref_occ, ref_lsz = G.octree_encode(codes, J)
+        assert rc == 0 and reported == 0 and ref_occ.numel() == 0
+        assert np.array_equal(lsz, ref_lsz)
