@@ -1470,6 +1470,13 @@ int64_t orc_decode_frame(const uint8_t *in, int64_t nbytes, int64_t cap_nv, floa
 typedef struct {
     double u, v, conic[3], opacity, color[3], depth;
     int tx0, tx1, ty0, ty1; /* inclusive tile range; tx0 > tx1 when empty */
+    /* for the threshold check (orc_render_check): condition number of the
+     * 2-D covariance, the tile ranges when the radius and centre move by a
+     * hair inward (in) or outward (out), and whether z is within a hair of
+     * the near plane */
+    double kappa;
+    int in_tx0, in_tx1, in_ty0, in_ty1, out_tx0, out_tx1, out_ty0, out_ty1;
+    int near_edge;
 } orc_splat;
 
 static void sh_basis(const double d[3], double Y[16])
@@ -1505,6 +1512,7 @@ static int splat_prepare(const float *p, const float *a, const double view[12], 
     double pc[3];
     for (int r = 0; r < 3; ++r) pc[r] = R[4 * r] * p[0] + R[4 * r + 1] * p[1] + R[4 * r + 2] * p[2] + R[4 * r + 3];
     const double z = pc[2];
+    s->near_edge = fabs(z - znear) <= 1e-9 * fabs(znear);
     if (!(z > znear)) return 0;
     double q[4] = {a[3], a[4], a[5], a[6]};
     double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
@@ -1543,6 +1551,10 @@ static int splat_prepare(const float *p, const float *a, const double view[12], 
     const double disc = mid * mid - det;
     const double lmax = mid + sqrt(disc > 0.1 ? disc : 0.1);
     const double rad = ceil(3.0 * sqrt(lmax));
+    {
+        const double sd = sqrt(disc > 0 ? disc : 0.0);
+        s->kappa = (mid + sd) / (mid - sd > 0 ? mid - sd : 1e-300);
+    }
     s->u = fx * pc[0] / z + cx;
     s->v = fy * pc[1] / z + cy;
     s->depth = z;
@@ -1554,6 +1566,24 @@ static int splat_prepare(const float *p, const float *a, const double view[12], 
     s->tx1 = tx1 > TX - 1 ? TX - 1 : tx1;
     s->ty0 = ty0 < 0 ? 0 : ty0;
     s->ty1 = ty1 > TY - 1 ? TY - 1 : ty1;
+    {  /* the same rectangle with the radius and centre moved by a hair */
+        const double hr = 1e-9 * sqrt(lmax), hu = 1e-7;
+        const double r_in = ceil(3.0 * (sqrt(lmax) - hr)), r_out = ceil(3.0 * (sqrt(lmax) + hr));
+        int a0 = (int)floor((s->u + hu - r_in) / ORC_TILE), a1 = (int)floor((s->u - hu + r_in) / ORC_TILE);
+        int b0 = (int)floor((s->v + hu - r_in) / ORC_TILE), b1 = (int)floor((s->v - hu + r_in) / ORC_TILE);
+        s->in_tx0 = a0 < 0 ? 0 : a0;
+        s->in_tx1 = a1 > TX - 1 ? TX - 1 : a1;
+        s->in_ty0 = b0 < 0 ? 0 : b0;
+        s->in_ty1 = b1 > TY - 1 ? TY - 1 : b1;
+        a0 = (int)floor((s->u - hu - r_out) / ORC_TILE);
+        a1 = (int)floor((s->u + hu + r_out) / ORC_TILE);
+        b0 = (int)floor((s->v - hu - r_out) / ORC_TILE);
+        b1 = (int)floor((s->v + hu + r_out) / ORC_TILE);
+        s->out_tx0 = a0 < 0 ? 0 : a0;
+        s->out_tx1 = a1 > TX - 1 ? TX - 1 : a1;
+        s->out_ty0 = b0 < 0 ? 0 : b0;
+        s->out_ty1 = b1 > TY - 1 ? TY - 1 : b1;
+    }
     /* colour: degree-3 SH at the direction from the camera centre (-R^T t) */
     double cam[3], d[3];
     for (int c = 0; c < 3; ++c) cam[c] = -(R[c] * R[3] + R[4 + c] * R[7] + R[8 + c] * R[11]);
@@ -1584,9 +1614,35 @@ static int depth_cmp(const void *x, const void *y)
     return (a->idx > b->idx) - (a->idx < b->idx);
 }
 
-/* Renders n Gaussians into image[H][W][3] (FP64).  Returns 0 or an error. */
-int orc_render(const float *pos, const float *attr, int64_t n, const double view[12], double fx, double fy,
-               double cx, double cy, int W, int H, double znear, const double bg[3], double *image)
+static int covers(int tx, int ty, int x0, int x1, int y0, int y1) { return tx >= x0 && tx <= x1 && ty >= y0 && ty <= y1; }
+
+/* Renders n Gaussians into image[H][W][3] (FP64).  When flag and tol are
+ * given, it also marks (flag = 1) every pixel whose value hangs on a decision
+ * taken within a hair of its threshold, where a renderer computing in FP32
+ * may legitimately decide the other way:
+ *   - some splat's alpha within relative 1e-5 of the 1/255 cut;
+ *   - the transmittance after a splat within relative 1e-4 of the 1e-4 stop;
+ *   - a splat whose tile rectangle covers the pixel's tile only for a radius
+ *     or centre moved by a hair (and that reaches alpha 1/255 there);
+ *   - two splats passing the alpha cut whose distinct depths round to the
+ *     same FP32 value (their order is then the index order in FP32);
+ *   - a splat exactly at the pixel centre with a rounded-up positive
+ *     exponent, or a splat at the near plane;
+ * and gives every other pixel a first-order bound tol on the error of an
+ * FP32 evaluation of the same pixel from FP32-rounded per-splat values
+ * (u, v to FP32 of their offsets, conic, opacity, colour):
+ *   tol = sum_k T_k (|c_k| + c_max) alpha_k e_k + 2^-24 (6 + 6 n) c_max,
+ * where the sum runs over the n composited splats, T_k is the transmittance
+ * in front of splat k, c_max the largest colour value among them and the
+ * background, and e_k = 2^-24 (8 + 8 p_k (1 + sqrt(kappa_k))) bounds the
+ * relative error of alpha_k (exponential and opacity rounding, and the
+ * exponent p_k = |d^T conic d| / 2 evaluated as a sum of squares of a
+ * Cholesky factor whose conditioning is that of the 2-D covariance,
+ * kappa_k).  d C / d alpha_k is bounded by T_k (|c_k| + c_max): the splat's
+ * own colour and, through (1 - alpha_k), everything behind it.             */
+static int render_impl(const float *pos, const float *attr, int64_t n, const double view[12], double fx, double fy,
+                       double cx, double cy, int W, int H, double znear, const double bg[3], double *image,
+                       uint8_t *flag, double *tol)
 {
     orc_splat *sp = (orc_splat *)malloc(sizeof(orc_splat) * (size_t)(n > 0 ? n : 1));
     orc_depth_key *ord = (orc_depth_key *)malloc(sizeof(orc_depth_key) * (size_t)(n > 0 ? n : 1));
@@ -1595,39 +1651,94 @@ int orc_render(const float *pos, const float *attr, int64_t n, const double view
         free(ord);
         return ORC_ERR_NOMEM;
     }
-    int64_t m = 0;
-    for (int64_t i = 0; i < n; ++i)
-        if (splat_prepare(pos + 3 * i, attr + 56 * i, view, fx, fy, cx, cy, W, H, znear, &sp[i]) &&
-            sp[i].tx0 <= sp[i].tx1 && sp[i].ty0 <= sp[i].ty1) {
+    const int check = flag != NULL && tol != NULL;
+    const double u24 = ldexp(1.0, -24);
+    int64_t m = 0, near_edge = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int ok = splat_prepare(pos + 3 * i, attr + 56 * i, view, fx, fy, cx, cy, W, H, znear, &sp[i]);
+        near_edge |= sp[i].near_edge;
+        if (ok && (check ? sp[i].out_tx0 <= sp[i].out_tx1 && sp[i].out_ty0 <= sp[i].out_ty1
+                         : sp[i].tx0 <= sp[i].tx1 && sp[i].ty0 <= sp[i].ty1)) {
             ord[m].depth = sp[i].depth;
             ord[m].idx = i;
             ++m;
         }
+    }
     qsort(ord, (size_t)m, sizeof(orc_depth_key), depth_cmp);
     for (int py = 0; py < H; ++py)
         for (int px = 0; px < W; ++px) {
             const int tx = px / ORC_TILE, ty = py / ORC_TILE;
             double T = 1.0, col[3] = {0, 0, 0};
             const double fxp = px + 0.5, fyp = py + 0.5;
+            int marked = near_edge != 0, np = 0, passed = 0;
+            double cmax = fmax(fabs(bg[0]), fmax(fabs(bg[1]), fabs(bg[2])));
+            double s0 = 0.0, s1 = 0.0, relT = 0.0;  /* sum T a e, sum T a e |c|, relative error bound of T */
+            float prev_depth = -1.0f;
+            double prev_depth64 = -1.0;
             for (int64_t k = 0; k < m; ++k) {
                 const orc_splat *s = &sp[ord[k].idx];
-                if (tx < s->tx0 || tx > s->tx1 || ty < s->ty0 || ty > s->ty1) continue;
+                const int in_nominal = covers(tx, ty, s->tx0, s->tx1, s->ty0, s->ty1);
+                if (!in_nominal && !(check && covers(tx, ty, s->out_tx0, s->out_tx1, s->out_ty0, s->out_ty1))) continue;
                 const double dx = s->u - fxp, dy = s->v - fyp;
                 const double power = -0.5 * (s->conic[0] * dx * dx + s->conic[2] * dy * dy) - s->conic[1] * dx * dy;
-                if (power > 0) continue;
-                double alpha = s->opacity * exp(power);
+                double alpha = s->opacity * exp(power > 0 ? 0.0 : power);
                 if (alpha > 0.99) alpha = 0.99;
+                const double ek = u24 * (8.0 + 8.0 * fabs(power) * (1.0 + sqrt(s->kappa)));
+                if (check) {
+                    const int marginal = !covers(tx, ty, s->in_tx0, s->in_tx1, s->in_ty0, s->in_ty1);
+                    if (marginal && alpha >= (1.0 / 255.0) * (1.0 - 2.0 * ek - 1e-6)) marked = 1;
+                    if (fabs(alpha - 1.0 / 255.0) <= (1.0 / 255.0) * (2.0 * ek + 1e-6)) marked = 1;
+                    if (power > 0 && alpha >= 1.0 / 255.0) marked = 1;
+                }
+                if (!in_nominal || power > 0) continue;
                 if (alpha < 1.0 / 255.0) continue;
+                if (check) {
+                    const float fd = (float)s->depth;
+                    if (passed > 0 && fd == prev_depth && s->depth != prev_depth64) marked = 1;
+                    prev_depth = fd;
+                    prev_depth64 = s->depth;
+                    ++passed;
+                }
                 const double tn = T * (1.0 - alpha);
+                if (check) {
+                    relT += alpha * ek / (1.0 - alpha) + 2.0 * u24;
+                    if (fabs(tn - 1e-4) <= 1e-4 * (2.0 * relT + 1e-6)) marked = 1;
+                }
                 if (tn < 1e-4) break;
                 for (int c = 0; c < 3; ++c) col[c] += s->color[c] * alpha * T;
+                if (check) {
+                    const double ck = fmax(s->color[0], fmax(s->color[1], s->color[2]));
+                    cmax = fmax(cmax, ck);
+                    s0 += T * alpha * ek;
+                    s1 += T * alpha * ek * ck;
+                    ++np;
+                }
                 T = tn;
             }
             for (int c = 0; c < 3; ++c) image[((size_t)py * W + px) * 3 + c] = col[c] + T * bg[c];
+            if (check) {
+                flag[(size_t)py * W + px] = (uint8_t)marked;
+                tol[(size_t)py * W + px] = s1 + cmax * s0 + u24 * (6.0 + 6.0 * np) * cmax;
+            }
         }
     free(sp);
     free(ord);
     return ORC_OK;
+}
+
+int orc_render(const float *pos, const float *attr, int64_t n, const double view[12], double fx, double fy,
+               double cx, double cy, int W, int H, double znear, const double bg[3], double *image)
+{
+    return render_impl(pos, attr, n, view, fx, fy, cx, cy, W, H, znear, bg, image, NULL, NULL);
+}
+
+/* orc_render plus the per-pixel threshold flags and error bounds above. */
+int orc_render_check(const float *pos, const float *attr, int64_t n, const double view[12], double fx, double fy,
+                     double cx, double cy, int W, int H, double znear, const double bg[3], double *image,
+                     uint8_t *flag, double *tol)
+{
+    if (!flag || !tol) return ORC_ERR_ARG;
+    return render_impl(pos, attr, n, view, fx, fy, cx, cy, W, H, znear, bg, image, flag, tol);
 }
 
 /* The 16 real SH basis values (degrees 0-3) at a unit direction (tests). */

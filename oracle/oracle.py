@@ -60,6 +60,8 @@ def lib():
             L.orc_render.argtypes = [p, p, i64, p, f64, f64, f64, f64, i32, i32, f64, p, p]
             L.orc_sh_basis.argtypes = [p, p]
             L.orc_render.restype = i32
+            L.orc_render_check.argtypes = [p, p, i64, p, f64, f64, f64, f64, i32, i32, f64, p, p, p, p]
+            L.orc_render_check.restype = i32
             L.orc_lod.argtypes = [p, i64, i32, i32, i32, p, p, f64, p, p, p, p]
             L.orc_lod.restype = i64
             L.orc_raht_lowpass.argtypes = [p, i64, i32, i32, p, i32, p, p]
@@ -242,16 +244,24 @@ def sh_basis(d):
     return Y
 
 
-def render(pos, attr, view, fx, fy, cx, cy, width, height, znear=0.01, bg=(0.0, 0.0, 0.0)):
-    """FP64 splat rasteriser (image [H, W, 3]) of 56-channel Gaussians; view = 3 x 4 world-to-camera [R | t]."""
+def render(pos, attr, view, fx, fy, cx, cy, width, height, znear=0.01, bg=(0.0, 0.0, 0.0), check=False):
+    """FP64 splat rasteriser (image [H, W, 3]) of 56-channel Gaussians; view = 3 x 4 world-to-camera [R | t].
+    With check=True also returns, per pixel, the threshold flag (uint8 [H, W]: the pixel depends on a decision
+    within rounding of its threshold) and the first-order error bound of an FP32 evaluation (float64 [H, W])."""
     pos = np.ascontiguousarray(pos, dtype=np.float32).reshape(-1, 3)
     attr = np.ascontiguousarray(attr, dtype=np.float32).reshape(-1, 56)
     view = np.ascontiguousarray(view, dtype=np.float64).reshape(3, 4)
     bg = np.ascontiguousarray(bg, dtype=np.float64)
     img = np.zeros((height, width, 3), dtype=np.float64)
-    _check(lib().orc_render(_p(pos), _p(attr), pos.shape[0], _p(view), float(fx), float(fy), float(cx), float(cy),
-                            width, height, float(znear), _p(bg), _p(img)))
-    return img
+    if not check:
+        _check(lib().orc_render(_p(pos), _p(attr), pos.shape[0], _p(view), float(fx), float(fy), float(cx),
+                                float(cy), width, height, float(znear), _p(bg), _p(img)))
+        return img
+    flag = np.zeros((height, width), dtype=np.uint8)
+    tol = np.zeros((height, width), dtype=np.float64)
+    _check(lib().orc_render_check(_p(pos), _p(attr), pos.shape[0], _p(view), float(fx), float(fy), float(cx),
+                                  float(cy), width, height, float(znear), _p(bg), _p(img), _p(flag), _p(tol)))
+    return img, flag, tol
 
 
 def raht_node_weights(codes, J):

@@ -2511,16 +2511,16 @@ gsnfs_status gsnfs_render(gsnfs_ctx *ctx, void *stream, const float *d_pos, cons
     RenderCam rc;
     const double *V = cam->view;
     for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) rc.R[3 * r + c] = (float)V[4 * r + c];
-        rc.t[r] = (float)V[4 * r + 3];
+        for (int c = 0; c < 3; ++c) rc.R[3 * r + c] = V[4 * r + c];
+        rc.t[r] = V[4 * r + 3];
     }
-    for (int c = 0; c < 3; ++c)  // camera centre -R^T t, in FP64
-        rc.campos[c] = (float)(-(V[c] * V[3] + V[4 + c] * V[7] + V[8 + c] * V[11]));
-    rc.fx = (float)cam->fx;
-    rc.fy = (float)cam->fy;
-    rc.cx = (float)cam->cx;
-    rc.cy = (float)cam->cy;
-    rc.znear = (float)cam->znear;
+    for (int c = 0; c < 3; ++c)  // camera centre -R^T t
+        rc.campos[c] = -(V[c] * V[3] + V[4 + c] * V[7] + V[8 + c] * V[11]);
+    rc.fx = cam->fx;
+    rc.fy = cam->fy;
+    rc.cx = cam->cx;
+    rc.cy = cam->cy;
+    rc.znear = cam->znear;
     rc.W = (int)cam->width;
     rc.H = (int)cam->height;
     rc.TX = (rc.W + 15) / 16;

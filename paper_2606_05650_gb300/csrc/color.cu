@@ -1,10 +1,14 @@
 // KLT of the SH colour decorrelation (Sec. 4): per frame, the covariance of
 // each YUV channel's 15 AC values over the frame's first (up to 4096) input
-// points (FP32 sums over 16 slices of 256 rows, added in FP64 in a fixed
-// order); its eigenvectors by cyclic Jacobi rotations in FP32 (one warp per
-// channel, lanes over the matrix columns); rows of K = eigenvectors by
-// decreasing eigenvalue, the largest component of each made positive.  The
-// frame's centring constants are then carried into the same domain.
+// points, and its eigenvectors; rows of K = eigenvectors by decreasing
+// eigenvalue, the largest component of each made positive.  Everything here
+// is FP64 (the sample is 4096 rows, so this costs next to nothing): the YUV
+// values of the sample, per-slice means and centred co-moments (16 slices of
+// 256 rows, one CTA each), the slices combined in a fixed order by the
+// pairwise update of Chan, Golub and LeVeque, and cyclic Jacobi rotations
+// (one warp per channel, lanes over the matrix columns).  K is rounded to
+// FP32 once, for the header and the per-row transforms.  The frame's
+// centring constants are then carried into the same domain.
 #include "color.cuh"
 #include "kernels.cuh"
 
@@ -17,7 +21,7 @@ constexpr int kSlices = 16;                   // CTAs per frame for the sample s
 constexpr int kSliceRows = kSample / kSlices;  // 256
 constexpr int kRowsPerChunk = 32;
 constexpr int kPairs = kKltN * (kKltN + 1) / 2;  // 120
-constexpr int kPartWords = 3 * (kPairs + kKltN);  // per slice: pair sums, then sums, per channel
+constexpr int kPartWords = 3 * (kPairs + kKltN) + 1;  // per slice: co-moments, then means, per channel; row count
 
 __device__ __forceinline__ void pair_of(int p, int &x, int &y)
 {
@@ -29,125 +33,163 @@ __device__ __forceinline__ void pair_of(int p, int &x, int &y)
     y = x + p;
 }
 
-// grid (slices, frames), 3 warps (YUV channels): FP32 sums of the AC products
-// and values over one slice of the frame's first 4096 input rows
+// BT.601 analogue YUV of one SH function's RGB in FP64, each product and sum
+// rounded separately (the order of the definition: m0 x + m1 y + m2 z)
+__device__ __forceinline__ void yuv3_f64(const float *row, int k, double out[3])
+{
+    const double M[9] = {0.299, 0.587, 0.114, -0.14713, -0.28886, 0.436, 0.615, -0.51499, -0.10001};
+    const double x = row[sh_chan(k, 0)], y = row[sh_chan(k, 1)], z = row[sh_chan(k, 2)];
+    for (int r = 0; r < 3; ++r)
+        out[r] = __dadd_rn(__dadd_rn(__dmul_rn(M[3 * r], x), __dmul_rn(M[3 * r + 1], y)), __dmul_rn(M[3 * r + 2], z));
+}
+
+// grid (slices, frames), 3 warps (YUV channels): the mean and the centred
+// co-moments (sums of products of deviations) of one slice of the frame's
+// first 4096 input rows, in two passes over the slice
 __global__ void __launch_bounds__(96) klt_partials_kernel(const float *const *attr, const uint64_t *poff,
                                                           double *part)
 {
-    __shared__ float rows[kRowsPerChunk][48];  // YUV of the 16 SH functions of a chunk of rows
+    __shared__ double rows[kRowsPerChunk][48];  // YUV of the 16 SH functions of a chunk of rows
+    __shared__ double mean[3][kKltN];
     const uint32_t f = blockIdx.y, sl = blockIdx.x;
     const int t = threadIdx.x, lane = t & 31, ch = t >> 5;
     const uint64_t n = poff[f + 1] - poff[f];
     const int m = (int)(n < (uint64_t)kSample ? n : (uint64_t)kSample);
     const int rb = sl * kSliceRows, re = (rb + kSliceRows) < m ? (rb + kSliceRows) : m;
+    const int cnt_rows = re > rb ? re - rb : 0;
     const float *a = attr[f];
-    const float M[9] = {0.299f, 0.587f, 0.114f, -0.14713f, -0.28886f, 0.436f, 0.615f, -0.51499f, -0.10001f};
-    float acc[4] = {0.f, 0.f, 0.f, 0.f}, sum = 0.f;
     int px[4], py[4];
     for (int j = 0; j < 4; ++j) pair_of(lane + 32 * j, px[j], py[j]);
-    for (int r0 = rb; r0 < re; r0 += kRowsPerChunk) {
-        const int cnt = (re - r0) < kRowsPerChunk ? (re - r0) : kRowsPerChunk;
-        for (int e = t; e < cnt * 16; e += blockDim.x) {
-            const int r = e >> 4, k = e & 15;
-            const float *row = a + (uint64_t)(r0 + r) * 56;
-            float y0 = row[sh_chan(k, 0)], y1 = row[sh_chan(k, 1)], y2 = row[sh_chan(k, 2)];
-            yuv3(M, y0, y1, y2);
-            rows[r][k * 3 + 0] = y0;
-            rows[r][k * 3 + 1] = y1;
-            rows[r][k * 3 + 2] = y2;
-        }
-        __syncthreads();
-        for (int r = 0; r < cnt; ++r) {
-            const float *rr = rows[r];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0}, sum = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int r0 = rb; r0 < re; r0 += kRowsPerChunk) {
+            const int cnt = (re - r0) < kRowsPerChunk ? (re - r0) : kRowsPerChunk;
+            for (int e = t; e < cnt * 16; e += blockDim.x) {
+                const int r = e >> 4, k = e & 15;
+                double y[3];
+                yuv3_f64(a + (uint64_t)(r0 + r) * 56, k, y);
+                rows[r][k * 3 + 0] = y[0];
+                rows[r][k * 3 + 1] = y[1];
+                rows[r][k * 3 + 2] = y[2];
+            }
+            __syncthreads();
+            for (int r = 0; r < cnt; ++r) {
+                const double *rr = rows[r];
+                if (pass == 0) {
+                    if (lane < kKltN) sum = __dadd_rn(sum, rr[(lane + 1) * 3 + ch]);
+                } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (lane + 32 * j < kPairs)
-                    acc[j] = __fadd_rn(acc[j], __fmul_rn(rr[(px[j] + 1) * 3 + ch], rr[(py[j] + 1) * 3 + ch]));
-            if (lane < kKltN) sum = __fadd_rn(sum, rr[(lane + 1) * 3 + ch]);
+                    for (int j = 0; j < 4; ++j)
+                        if (lane + 32 * j < kPairs) {
+                            const double dx = __dsub_rn(rr[(px[j] + 1) * 3 + ch], mean[ch][px[j]]);
+                            const double dy = __dsub_rn(rr[(py[j] + 1) * 3 + ch], mean[ch][py[j]]);
+                            acc[j] = __dadd_rn(acc[j], __dmul_rn(dx, dy));
+                        }
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        if (pass == 0) {
+            if (lane < kKltN) mean[ch][lane] = cnt_rows ? __ddiv_rn(sum, (double)cnt_rows) : 0.0;
+            __syncthreads();
+        }
     }
-    double *o = part + ((uint64_t)f * kSlices + sl) * kPartWords + ch * (kPairs + kKltN);
+    double *ps = part + ((uint64_t)f * kSlices + sl) * kPartWords;
+    double *o = ps + ch * (kPairs + kKltN);
     for (int j = 0; j < 4; ++j)
-        if (lane + 32 * j < kPairs) o[lane + 32 * j] = (double)acc[j];
-    if (lane < kKltN) o[kPairs + lane] = (double)sum;
+        if (lane + 32 * j < kPairs) o[lane + 32 * j] = acc[j];
+    if (lane < kKltN) o[kPairs + lane] = mean[ch][lane];
+    if (t == 0) ps[kPartWords - 1] = (double)cnt_rows;
 }
 
-// one CTA (3 warps) per frame: covariance from the slices (fixed order, FP64),
-// eigenvectors by cyclic Jacobi (FP32, lanes over columns), ordering and signs
+// one CTA (3 warps) per frame: covariance from the slices (pairwise update,
+// fixed order, FP64), eigenvectors by cyclic Jacobi (FP64, lanes over
+// columns), ordering and signs; K rounded to FP32
 __global__ void __launch_bounds__(96) klt_solve_kernel(const uint64_t *poff, const double *part, float *klt,
                                                        float *center)
 {
-    __shared__ float S[3][kKltN * kKltN];
-    __shared__ float V[3][kKltN * kKltN];
+    __shared__ double S[3][kKltN * kKltN];
+    __shared__ double V[3][kKltN * kKltN];
     __shared__ double mu[3][kKltN];
-    __shared__ float cs[3][2];
+    __shared__ double cs[3][2];
     __shared__ int order[3][kKltN];
     const uint32_t f = blockIdx.x;
     const int t = threadIdx.x, lane = t & 31, ch = t >> 5;
     const uint64_t n = poff[f + 1] - poff[f];
     const int m = (int)(n < (uint64_t)kSample ? n : (uint64_t)kSample);
+    const double *pf = part + (uint64_t)f * kSlices * kPartWords;
+    // running combination over slices: count nA, mean muA (lane < 15), co-moments CA (4 pairs per lane)
+    double nA = 0.0, muA = 0.0, CA[4] = {0.0, 0.0, 0.0, 0.0};
+    int px[4], py[4];
+    for (int j = 0; j < 4; ++j) pair_of(lane + 32 * j, px[j], py[j]);
+    for (int sl = 0; sl < kSlices; ++sl) {
+        const double *ps = pf + (uint64_t)sl * kPartWords;
+        const double nB = ps[kPartWords - 1];
+        if (nB == 0.0) continue;
+        const double *o = ps + ch * (kPairs + kKltN);
+        const double nAB = __dadd_rn(nA, nB);
+        const double w = __ddiv_rn(__dmul_rn(nA, nB), nAB);
+        // delta of the means for both coordinates of each pair (read from this slice's and the running means)
+        if (lane < kKltN) mu[ch][lane] = __dsub_rn(o[kPairs + lane], muA);  // delta_k = muB_k - muA_k
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (lane + 32 * j < kPairs)
+                CA[j] = __dadd_rn(__dadd_rn(CA[j], o[lane + 32 * j]),
+                                  __dmul_rn(w, __dmul_rn(mu[ch][px[j]], mu[ch][py[j]])));
+        if (lane < kKltN) muA = __dadd_rn(muA, __dmul_rn(mu[ch][lane], __ddiv_rn(nB, nAB)));
+        nA = nAB;
+        __syncwarp();
+    }
     const double inv_m = m ? 1.0 / (double)m : 0.0;
-    const double *pf = part + (uint64_t)f * kSlices * kPartWords + ch * (kPairs + kKltN);
-    if (lane < kKltN) {
-        double s = 0.0;
-        for (int sl = 0; sl < kSlices; ++sl) s += pf[(uint64_t)sl * kPartWords + kPairs + lane];
-        mu[ch][lane] = s * inv_m;
-    }
-    __syncwarp();
-    for (int j = 0; j < 4; ++j) {
-        const int p = lane + 32 * j;
-        if (p < kPairs) {
-            double s = 0.0;
-            for (int sl = 0; sl < kSlices; ++sl) s += pf[(uint64_t)sl * kPartWords + p];
-            int x, y;
-            pair_of(p, x, y);
-            const float c = (float)(s * inv_m - mu[ch][x] * mu[ch][y]);
-            S[ch][x * kKltN + y] = c;
-            S[ch][y * kKltN + x] = c;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (lane + 32 * j < kPairs) {
+            const double c = __dmul_rn(CA[j], inv_m);
+            S[ch][px[j] * kKltN + py[j]] = c;
+            S[ch][py[j] * kKltN + px[j]] = c;
         }
-    }
     if (lane < kKltN)
-        for (int k = 0; k < kKltN; ++k) V[ch][lane * kKltN + k] = (lane == k) ? 1.f : 0.f;
+        for (int k = 0; k < kKltN; ++k) V[ch][lane * kKltN + k] = (lane == k) ? 1.0 : 0.0;
     __syncwarp();
-    float *Sc = S[ch], *Vc = V[ch];
-    float tr2 = 0.f;
+    double *Sc = S[ch], *Vc = V[ch];
+    double tr2 = 0.0;
     for (int k = 0; k < kKltN; ++k) tr2 += Sc[k * kKltN + k] * Sc[k * kKltN + k];
-    for (int sweep = 0; sweep < 30; ++sweep) {
-        float off = 0.f;
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        double off = 0.0;
         for (int p = 0; p < kKltN; ++p)
             for (int q = p + 1; q < kKltN; ++q) off += Sc[p * kKltN + q] * Sc[p * kKltN + q];
-        if (!(off > 1e-14f * tr2)) break;
+        if (!(off > 1e-32 * tr2)) break;
         for (int p = 0; p < kKltN; ++p)
             for (int q = p + 1; q < kKltN; ++q) {
                 if (lane == 0) {
-                    const float apq = Sc[p * kKltN + q];
-                    float c = 1.f, s = 0.f;
-                    if (fabsf(apq) > 1e-30f) {
-                        const float theta = (Sc[q * kKltN + q] - Sc[p * kKltN + p]) / (2.f * apq);
-                        const float tt = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
-                        c = 1.f / sqrtf(tt * tt + 1.f);
-                        s = tt * c;
+                    const double apq = Sc[p * kKltN + q];
+                    double c = 1.0, sn = 0.0;
+                    if (fabs(apq) > 1e-300) {
+                        const double theta = (Sc[q * kKltN + q] - Sc[p * kKltN + p]) / (2.0 * apq);
+                        const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        c = 1.0 / sqrt(tt * tt + 1.0);
+                        sn = tt * c;
                     }
                     cs[ch][0] = c;
-                    cs[ch][1] = s;
+                    cs[ch][1] = sn;
                 }
                 __syncwarp();
-                const float c = cs[ch][0], s = cs[ch][1];
-                if (s != 0.f) {
+                const double c = cs[ch][0], sn = cs[ch][1];
+                if (sn != 0.0) {
                     if (lane < kKltN) {  // columns p, q
-                        const float skp = Sc[lane * kKltN + p], skq = Sc[lane * kKltN + q];
-                        Sc[lane * kKltN + p] = c * skp - s * skq;
-                        Sc[lane * kKltN + q] = s * skp + c * skq;
+                        const double skp = Sc[lane * kKltN + p], skq = Sc[lane * kKltN + q];
+                        Sc[lane * kKltN + p] = c * skp - sn * skq;
+                        Sc[lane * kKltN + q] = sn * skp + c * skq;
                     }
                     __syncwarp();
                     if (lane < kKltN) {  // rows p, q; eigenvector columns
-                        const float spk = Sc[p * kKltN + lane], sqk = Sc[q * kKltN + lane];
-                        Sc[p * kKltN + lane] = c * spk - s * sqk;
-                        Sc[q * kKltN + lane] = s * spk + c * sqk;
-                        const float vkp = Vc[lane * kKltN + p], vkq = Vc[lane * kKltN + q];
-                        Vc[lane * kKltN + p] = c * vkp - s * vkq;
-                        Vc[lane * kKltN + q] = s * vkp + c * vkq;
+                        const double spk = Sc[p * kKltN + lane], sqk = Sc[q * kKltN + lane];
+                        Sc[p * kKltN + lane] = c * spk - sn * sqk;
+                        Sc[q * kKltN + lane] = sn * spk + c * sqk;
+                        const double vkp = Vc[lane * kKltN + p], vkq = Vc[lane * kKltN + q];
+                        Vc[lane * kKltN + p] = c * vkp - sn * vkq;
+                        Vc[lane * kKltN + q] = sn * vkp + c * vkq;
                     }
                 }
                 __syncwarp();
@@ -169,9 +211,9 @@ __global__ void __launch_bounds__(96) klt_solve_kernel(const uint64_t *poff, con
         const int e = order[ch][lane];
         int big = 0;
         for (int k = 1; k < kKltN; ++k)
-            if (fabsf(Vc[k * kKltN + e]) > fabsf(Vc[big * kKltN + e])) big = k;
-        const float sg = Vc[big * kKltN + e] < 0.f ? -1.f : 1.f;
-        for (int k = 0; k < kKltN; ++k) Kf[lane * kKltN + k] = sg * Vc[k * kKltN + e];
+            if (fabs(Vc[k * kKltN + e]) > fabs(Vc[big * kKltN + e])) big = k;
+        const double sg = Vc[big * kKltN + e] < 0.0 ? -1.0 : 1.0;
+        for (int k = 0; k < kKltN; ++k) Kf[lane * kKltN + k] = (float)(sg * Vc[k * kKltN + e]);
     }
     __syncthreads();
     if (t == 0 && center) color_forward_row(center + (uint64_t)f * 56, klt + (uint64_t)f * kKltFloats);

@@ -300,9 +300,9 @@ void launch_lod_nodes(const uint64_t *codes, const uint64_t *starts, const uint6
                       float *pos, float *out, int num_sms, cudaStream_t s);
 
 // ---- render.cu: splat rasteriser ------------------------------------------------
-struct RenderCam {
-    float R[9], t[3], campos[3];
-    float fx, fy, cx, cy, znear;
+struct RenderCam {  // camera in FP64: the per-Gaussian projection is evaluated in FP64
+    double R[9], t[3], campos[3];
+    double fx, fy, cx, cy, znear;
     int W, H, TX, TY;
     float bg[3];
 };

@@ -1,9 +1,11 @@
 """SH colour decorrelation on the GPU (gsnfs_quant.color, Sec. 4): streams
-decode in the oracle decoder, the oracle encoder given the stream's KLT
-matrices reproduces header, occupancy and (outside the rounding zone) every
-quantisation index, the GPU's KLT diagonalises the sample covariance, batched
-equals plain, the encoder's reconstruction equals the decoder's output, and
-correlated colours compress markedly better (the direction of Table A.8)."""
+decode in the oracle decoder; the oracle encoder, given the stream's KLT
+matrices or deriving its own, reproduces header, occupancy and (outside the
+rounding zone) every quantisation index; the GPU's KLT rows are eigenvectors
+of the FP64 sample covariance and equal the oracle's FP64 Jacobi row by row
+to FP32 rounding; batched equals plain, the encoder's reconstruction equals
+the decoder's output, and correlated colours compress markedly better (the
+direction of Table A.8)."""
 import numpy as np
 import pytest
 
@@ -45,14 +47,59 @@ def test_colour_stream_parity(G, orc, n, J):
     assert res["nv"] == nv
     ga = ga.cpu().numpy()
     assert np.abs(ra.cpu().numpy() - ga).max() <= 1e-5 * (1 + np.abs(ga).max())
-    # the GPU's KLT (FP32 in the stream) diagonalises the sample covariance of the YUV AC vectors
-    K = stream_klt(host).astype(np.float64)
+    _check_klt(orc, stream_klt(host), attr)
+
+
+U32 = 2.0 ** -24  # unit roundoff of FP32
+
+
+def _check_klt(orc, K32, attr):
+    """The stream's KLT (FP64 on the GPU, rounded to FP32) against the sample covariance S of the YUV AC vectors
+    of the first 4096 input rows, computed here in FP64 from the definition (Sec. 4):
+      - every row is an eigenvector of S up to the FP32 rounding of K: |S k - rho k| <= 8 u |S| (u = 2^-24);
+      - rows are orthonormal to FP32 rounding and ordered by decreasing Rayleigh quotient;
+      - row by row, K equals the oracle's FP64 Jacobi rounded to FP32, within 2 u plus the perturbation bound of
+        an eigenvector, 1e-12 |S| / gap (gap: the row's distance to the other eigenvalues), sign included
+        (largest component positive) unless the two largest components are too close to tell."""
+    K = K32.astype(np.float64)
+    Kor = orc.klt_matrices(attr).astype(np.float64)
     sample = orc.yuv_rows(attr[:4096].astype(np.float64))
     for ch in range(3):
-        S = np.cov(sample[:, 11 + 15 * ch:26 + 15 * ch].T, bias=True)
-        D = K[ch] @ S @ K[ch].T
-        assert np.abs(D - np.diag(np.diag(D))).max() < 1e-5 * np.trace(S)
-        assert np.abs(K[ch] - orc.klt_matrices(attr)[ch]).max() < 1e-3  # same basis as the oracle's KLT
+        a = sample[:, 11 + 15 * ch:26 + 15 * ch]
+        d = a - a.mean(0)
+        S = d.T @ d / a.shape[0]
+        nS = np.linalg.norm(S, 2)
+        lam = np.linalg.eigvalsh(S)[::-1]
+        rho = np.einsum("rk,kl,rl->r", K[ch], S, K[ch])
+        res = np.linalg.norm(K[ch] @ S - rho[:, None] * K[ch], axis=1)
+        assert res.max() <= 8 * U32 * nS, (ch, res.max() / nS)
+        assert np.abs(K[ch] @ K[ch].T - np.eye(15)).max() <= 16 * U32
+        assert np.all(np.diff(rho) <= 16 * U32 * nS)
+        for r in range(15):
+            gap = np.min(np.abs(np.delete(lam, r) - lam[r]))
+            tol = 2 * U32 + 1e-12 * nS / max(gap, 1e-300)
+            top = np.sort(np.abs(Kor[ch, r]))[-2:]
+            sign_clear = top[1] - top[0] > 1e-9
+            diff = np.abs(K[ch, r] - Kor[ch, r]).max()
+            if not sign_clear:
+                diff = min(diff, np.abs(K[ch, r] + Kor[ch, r]).max())
+            assert diff <= tol, (ch, r, diff, tol)
+
+
+@pytest.mark.parametrize("n,J", [(20_000, 12), (150_000, 16)])
+def test_colour_stream_parity_with_own_klt(G, orc, n, J):
+    """Both sides derive the KLT themselves: the oracle's stream (its own FP64 K) and the GPU's agree on header,
+    occupancy and every index, except where the difference of the two K (FP32 rounding) can move a coefficient
+    across a rounding boundary."""
+    pos, attr = _frame(170 + J, n)
+    qp = G.QuantParams(syn.gs_channel_groups(), syn.GS_BASE_STEPS, color=True)
+    bs, nv, _, _ = G.encode_frame(_dev(pos), _dev(attr), J, qp)
+    gp, ga = G.decode_frame(bs)
+    host = bs.cpu().numpy()
+    res = compare_stream(orc, host, pos, attr, J, qp.groups, qp.steps, qp.tau, qp.rlgr_block, qp.rans_chunk,
+                         (gp.cpu().numpy(), ga.cpu().numpy()), own_klt=True)
+    assert res["nv"] == nv
+    _check_klt(orc, stream_klt(host), attr)
 
 
 def test_colour_batch_equals_plain_and_shrinks(G, orc):

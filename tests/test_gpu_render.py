@@ -1,10 +1,12 @@
-"""GPU splat rasteriser (gsnfs_render) against the oracle's FP64 renderer:
-synthetic scenes seen from orbit cameras on ragged image sizes (partial edge
-tiles), the closed-form single Gaussian, an opaque front splat hiding one
-behind it, empty and fully culled scenes, and argument errors.  The GPU works
-in FP32, so a pixel may differ where an alpha or transmittance threshold is
-met within rounding: the bar is a tiny mean error and almost all values
-within 2e-3."""
+"""GPU splat rasteriser (gsnfs_render) against the oracle's FP64 renderer,
+pixel by pixel: synthetic scenes seen from orbit cameras on ragged image
+sizes (partial edge tiles), the closed-form single Gaussian, an opaque front
+splat hiding one behind it, empty and fully culled scenes, and argument
+errors.  The oracle marks the pixels whose value hangs on a decision taken
+within rounding of its threshold (alpha at the 1/255 cut, transmittance at
+the 1e-4 stop, a tile rectangle edge, depths equal in FP32); every other
+pixel must lie within the oracle's first-order bound on the error of an FP32
+evaluation of that pixel (Sec. 5.1 renders decoded frames to score them)."""
 import numpy as np
 import pytest
 
@@ -27,17 +29,24 @@ def G():
 
 
 def _both(G, orc, pos, attr, view, f, W, H, bg=(0.0, 0.0, 0.0)):
+    """GPU image and the oracle's (image, threshold flags, FP32 error bounds)."""
     cx, cy = W / 2, H / 2
-    ref = orc.render(pos, attr, view, f, f, cx, cy, W, H, bg=bg)
+    ref = orc.render(pos, attr, view, f, f, cx, cy, W, H, bg=bg, check=True)
     img = G.render(torch.from_numpy(pos).cuda(), torch.from_numpy(attr).cuda(), view, f, f, cx, cy, W, H,
                    background=bg).cpu().numpy()
     return img, ref
 
 
 def _close(img, ref):
-    d = np.abs(img.astype(np.float64) - ref)
-    assert d.mean() < 2e-4, d.mean()
-    assert (d > 2e-3).mean() < 2e-3, (d > 2e-3).mean()
+    """Every pixel not flagged by the oracle within its error bound, in all three channels; flagged pixels are
+    counted and rare."""
+    want, flag, tol = ref
+    d = np.abs(img.astype(np.float64) - want).max(axis=2)
+    ok = flag == 0
+    bad = ok & (d > tol)
+    assert not bad.any(), (int(bad.sum()), float(d[bad].max()), float(tol[bad].min()))
+    assert flag.mean() < 5e-3, flag.mean()
+    return d, flag
 
 
 @pytest.mark.parametrize("seed,W,H", [(1, 200, 150), (2, 97, 131), (3, 256, 256)])
@@ -46,7 +55,7 @@ def test_scene_matches_oracle(G, orc, seed, W, H):
     for view in syn.orbit_views(2, radius=1.5 + 0.2 * seed):
         img, ref = _both(G, orc, pos, attr, view, 0.9 * W, W, H, bg=(0.1, 0.2, 0.3))
         _close(img, ref)
-        assert ref.std() > 0.02  # the scene is visible
+        assert ref[0].std() > 0.02  # the scene is visible
 
 
 def test_single_gaussian_closed_form(G):
@@ -92,7 +101,7 @@ def test_empty_and_culled(G, orc):
     pos, attr = syn.static_gs_frame(5, n=2000)
     pos = pos - np.float32(5.0)  # every point behind the camera (z < 0)
     img, ref = _both(G, orc, pos, attr, VIEW, 50.0, 40, 33, bg=bg)
-    assert np.array_equal(img, ref.astype(np.float32))
+    assert np.array_equal(img, ref[0].astype(np.float32)) and not ref[1].any()
 
 
 def test_bad_arguments(G):

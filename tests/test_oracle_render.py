@@ -114,3 +114,76 @@ def test_rotated_anisotropic_gaussian_closed_form(orc):
         assert np.allclose(img[32 + dy, 32 + dx], want, atol=1e-12), (dx, dy)
     # the long axis follows the rotation: (2, 1) lies near it, (1, -2) across it
     assert img[33, 34, 0] > img[30, 33, 0]
+
+
+# ---- threshold flags and FP32 error bounds of the check mode (pins of what the GPU parity test excuses) ----
+def _check(orc, ps, As, view, f, cx, cy, W, H, bg=(0.1, 0.2, 0.3)):
+    return orc.render(np.array(ps, np.float32), np.array(As, np.float32), view, f, f, cx, cy, W, H, bg=bg,
+                      check=True)
+
+
+def test_check_mode_image_equals_render_and_generic_pixels_are_not_flagged(orc):
+    from paper_2606_05650_gb300 import synthetic as syn
+    pos, attr = syn.static_gs_frame(4, n=3000)
+    view = syn.orbit_views(1, radius=1.8)[0]
+    img = orc.render(pos, attr, view, 90.0, 90.0, 50, 40, 100, 80)
+    img2, flag, tol = orc.render(pos, attr, view, 90.0, 90.0, 50, 40, 100, 80, check=True)
+    assert np.array_equal(img, img2)
+    assert flag.mean() < 0.01 and (tol >= 0).all()
+    p, a = _gauss([0, 0, 2.0], np.log(0.02), 0.0, [1.0, -1.0, 0.5])
+    _, flag, tol = _check(orc, [p], [a], VIEW, 100.0, 32.5, 32.5, 64, 64)
+    assert not flag.any()
+    # background only: the bound is the accumulation term alone, 6 ulp of the largest value
+    _, flag, tol = _check(orc, np.zeros((0, 3)), np.zeros((0, 56)), VIEW, 100.0, 32, 32, 20, 10, bg=(0.25, 0.5, 1.0))
+    assert not flag.any() and np.allclose(tol, 6 * 2.0 ** -24)
+
+
+def test_flag_alpha_at_the_cut(orc):
+    logit = np.log((1 / 255) / (1 - 1 / 255))  # opacity 1/255 to float rounding: alpha at the centre is the cut
+    p, a = _gauss([0, 0, 2.0], np.log(0.02), logit, [1.0, 1.0, 1.0])
+    _, flag, _ = _check(orc, [p], [a], VIEW, 100.0, 32.5, 32.5, 64, 64)
+    assert flag[32, 32] == 1 and flag.sum() <= 9  # the centre (and at most its neighbours)
+    p, a = _gauss([0, 0, 2.0], np.log(0.02), logit + 0.5, [1.0, 1.0, 1.0])  # clear of the cut: nothing flagged
+    _, flag, _ = _check(orc, [p], [a], VIEW, 100.0, 32.5, 32.5, 64, 64)
+    assert not flag.any()
+
+
+def test_flag_transmittance_at_the_stop(orc):
+    # two splats clamped at alpha 0.99 at the centre: transmittance 0.01 x 0.01 = the 1e-4 stop
+    g = [_gauss([0, 0, z], np.log(0.05), 8.0, [1.0, 0.0, 0.0]) for z in (2.0, 3.0)]
+    _, flag, _ = _check(orc, [x[0] for x in g], [x[1] for x in g], VIEW, 100.0, 32.5, 32.5, 64, 64)
+    assert flag[32, 32] == 1
+    g = [_gauss([0, 0, z], np.log(0.05), 3.0, [1.0, 0.0, 0.0]) for z in (2.0, 3.0)]  # alpha 0.95: well above
+    _, flag, _ = _check(orc, [x[0] for x in g], [x[1] for x in g], VIEW, 100.0, 32.5, 32.5, 64, 64)
+    assert not flag.any()
+
+
+def test_flag_depths_equal_in_fp32(orc):
+    # camera z = z_world + 1e-7 x_world: depths 2 and 2 + 1e-10 are distinct in FP64 and equal in FP32; the
+    # farther splat has the lower index, so FP64 depth order and (FP32 depth, index) order disagree
+    view = VIEW.copy()
+    view[2, 0] = 1e-7
+    g = [_gauss([1e-3, 0, 2.0], np.log(0.03), 0.0, [1.0, 0.0, 0.0]), _gauss([0, 0, 2.0], np.log(0.03), 0.0,
+                                                                               [0.0, 1.0, 0.0])]
+    _, flag, _ = _check(orc, [x[0] for x in g], [x[1] for x in g], view, 100.0, 32.5, 32.5, 64, 64)
+    assert flag[32, 32] == 1
+    # equal in FP64 as well: index order on both sides, nothing to excuse
+    g = [_gauss([0, 0, 2.0], np.log(0.03), 0.0, [1.0, 0.0, 0.0]), _gauss([0, 0, 2.0], np.log(0.03), 0.0,
+                                                                            [0.0, 1.0, 0.0])]
+    _, flag, _ = _check(orc, [x[0] for x in g], [x[1] for x in g], VIEW, 100.0, 32.5, 32.5, 64, 64)
+    assert not flag.any()
+
+
+def test_flag_tile_rectangle_edge(orc):
+    # footprint radius ceil(3 sqrt(lambda_max)) with lambda_max = sigma^2 + sqrt(0.1) (the discriminant floor of an
+    # isotropic footprint) and sigma^2 = (f s / z)^2 + 0.3 chosen so that 3 sqrt(lambda_max) = 11.99: radius 12;
+    # centre u = 32 - 12 puts the rectangle's right edge exactly on the boundary of tile 2, whose first pixel
+    # (12.5 px away) still sees alpha = 0.993 exp(-12.5^2 / (2 sigma^2)) = 0.0068 > 1/255
+    f, z = 100.0, 2.0
+    sig2 = (11.99 / 3) ** 2 - np.sqrt(0.1)
+    s = np.sqrt(sig2 - 0.3) * z / f
+    p, a = _gauss([0, 0, z], np.log(s), 5.0, [1.0, 1.0, 1.0])
+    _, flag, _ = _check(orc, [p], [a], VIEW, f, 32.0 - 12.0, 8.0, 64, 16)
+    assert flag[7, 32] == 1 and flag[7, 31] == 0
+    _, flag, _ = _check(orc, [p], [a], VIEW, f, 32.0 - 15.0, 8.0, 64, 16)  # edge inside tile 1: nothing flagged
+    assert not flag.any()
