@@ -6,7 +6,7 @@
 // values of the sample, per-slice means and centred co-moments (16 slices of
 // 256 rows, one CTA each), the slices combined in a fixed order by the
 // pairwise update of Chan, Golub and LeVeque, and cyclic Jacobi rotations
-// (one warp per channel, lanes over the matrix columns).  K is rounded to
+// (one warp per channel, seven disjoint rotations at a time).  K is rounded to
 // FP32 once, for the header and the per-row transforms.  The frame's
 // centring constants are then carried into the same domain.
 #include "color.cuh"
@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(96) klt_solve_kernel(const uint64_t *poff, con
     __shared__ double S[3][kKltN * kKltN];
     __shared__ double V[3][kKltN * kKltN];
     __shared__ double mu[3][kKltN];
-    __shared__ double cs[3][2];
+    __shared__ double cs[3][7][2];
+    __shared__ int pq[3][7][2];
     __shared__ int order[3][kKltN];
     const uint32_t f = blockIdx.x;
     const int t = threadIdx.x, lane = t & 31, ch = t >> 5;
@@ -155,45 +156,59 @@ __global__ void __launch_bounds__(96) klt_solve_kernel(const uint64_t *poff, con
     double *Sc = S[ch], *Vc = V[ch];
     double tr2 = 0.0;
     for (int k = 0; k < kKltN; ++k) tr2 += Sc[k * kKltN + k] * Sc[k * kKltN + k];
-    for (int sweep = 0; sweep < 40; ++sweep) {
+    // Jacobi sweeps in parallel order: 15 rounds of 7 disjoint (p, q) pairs (a
+    // round-robin over the 15 indices and one idle slot), the 7 rotations of a
+    // round computed from the same S and applied together (they act on
+    // disjoint rows and columns); every pair is met once per sweep.  Stop when
+    // the off-diagonal mass is down to FP64 rounding of the diagonal.
+    for (int sweep = 0; sweep < 20; ++sweep) {
         double off = 0.0;
-        for (int p = 0; p < kKltN; ++p)
-            for (int q = p + 1; q < kKltN; ++q) off += Sc[p * kKltN + q] * Sc[p * kKltN + q];
-        if (!(off > 1e-32 * tr2)) break;
-        for (int p = 0; p < kKltN; ++p)
-            for (int q = p + 1; q < kKltN; ++q) {
-                if (lane == 0) {
-                    const double apq = Sc[p * kKltN + q];
-                    double c = 1.0, sn = 0.0;
-                    if (fabs(apq) > 1e-300) {
-                        const double theta = (Sc[q * kKltN + q] - Sc[p * kKltN + p]) / (2.0 * apq);
-                        const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                        c = 1.0 / sqrt(tt * tt + 1.0);
-                        sn = tt * c;
-                    }
-                    cs[ch][0] = c;
-                    cs[ch][1] = sn;
+        if (lane < kKltN)
+            for (int q = lane + 1; q < kKltN; ++q) off += Sc[lane * kKltN + q] * Sc[lane * kKltN + q];
+        for (int o = 16; o; o >>= 1) off += __shfl_xor_sync(0xFFFFFFFFu, off, o);
+        if (!(off > 1e-28 * tr2)) break;
+        for (int rd = 0; rd < kKltN; ++rd) {
+            if (lane < 7) {
+                const int a = (rd + lane + 1) % kKltN, b = (rd - lane - 1 + kKltN) % kKltN;
+                const int p = a < b ? a : b, q = a < b ? b : a;
+                const double apq = Sc[p * kKltN + q];
+                double c = 1.0, sn = 0.0;
+                if (fabs(apq) > 1e-300) {
+                    const double theta = (Sc[q * kKltN + q] - Sc[p * kKltN + p]) / (2.0 * apq);
+                    const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                    c = 1.0 / sqrt(tt * tt + 1.0);
+                    sn = tt * c;
                 }
-                __syncwarp();
-                const double c = cs[ch][0], sn = cs[ch][1];
-                if (sn != 0.0) {
-                    if (lane < kKltN) {  // columns p, q
-                        const double skp = Sc[lane * kKltN + p], skq = Sc[lane * kKltN + q];
-                        Sc[lane * kKltN + p] = c * skp - sn * skq;
-                        Sc[lane * kKltN + q] = sn * skp + c * skq;
-                    }
-                    __syncwarp();
-                    if (lane < kKltN) {  // rows p, q; eigenvector columns
-                        const double spk = Sc[p * kKltN + lane], sqk = Sc[q * kKltN + lane];
-                        Sc[p * kKltN + lane] = c * spk - sn * sqk;
-                        Sc[q * kKltN + lane] = sn * spk + c * sqk;
-                        const double vkp = Vc[lane * kKltN + p], vkq = Vc[lane * kKltN + q];
-                        Vc[lane * kKltN + p] = c * vkp - sn * vkq;
-                        Vc[lane * kKltN + q] = sn * vkp + c * vkq;
-                    }
-                }
-                __syncwarp();
+                cs[ch][lane][0] = c;
+                cs[ch][lane][1] = sn;
+                pq[ch][lane][0] = p;
+                pq[ch][lane][1] = q;
             }
+            __syncwarp();
+            if (lane < kKltN) {  // columns p, q of S and of V (lane = row)
+                for (int i = 0; i < 7; ++i) {
+                    const int p = pq[ch][i][0], q = pq[ch][i][1];
+                    const double c = cs[ch][i][0], sn = cs[ch][i][1];
+                    const double skp = Sc[lane * kKltN + p], skq = Sc[lane * kKltN + q];
+                    Sc[lane * kKltN + p] = c * skp - sn * skq;
+                    Sc[lane * kKltN + q] = sn * skp + c * skq;
+                    const double vkp = Vc[lane * kKltN + p], vkq = Vc[lane * kKltN + q];
+                    Vc[lane * kKltN + p] = c * vkp - sn * vkq;
+                    Vc[lane * kKltN + q] = sn * vkp + c * vkq;
+                }
+            }
+            __syncwarp();
+            if (lane < kKltN) {  // rows p, q of S (lane = column)
+                for (int i = 0; i < 7; ++i) {
+                    const int p = pq[ch][i][0], q = pq[ch][i][1];
+                    const double c = cs[ch][i][0], sn = cs[ch][i][1];
+                    const double spk = Sc[p * kKltN + lane], sqk = Sc[q * kKltN + lane];
+                    Sc[p * kKltN + lane] = c * spk - sn * sqk;
+                    Sc[q * kKltN + lane] = sn * spk + c * sqk;
+                }
+            }
+            __syncwarp();
+        }
     }
     if (lane == 0) {  // decreasing eigenvalue, stable
         for (int k = 0; k < kKltN; ++k) order[ch][k] = k;

@@ -75,9 +75,10 @@ __device__ __forceinline__ void gr_put(BitWriter &bw, uint32_t v, uint32_t k, in
 {
     const uint32_t p = v >> k;
     if (__builtin_expect(p + 1u + k <= 32u && p < (uint32_t)kUnaryEsc, 1)) {  // common case: one write
-        const uint32_t low = v & ((1u << k) - 1u);  // k <= 24
-        const uint32_t ones = (1u << p) - 1u;       // p ones then a zero
-        bw.put(ones | (low << (p + 1u)), p + 1u + k);
+        // p ones, a zero, then the k low bits of v, least significant first:
+        // ((2 low + 1) << p) - 1, where low = v mod 2^k (k <= 24)
+        const uint32_t low = v & ((1u << k) - 1u);
+        bw.put((((low << 1) | 1u) << p) - 1u, p + 1u + k);
     } else if (p < (uint32_t)kUnaryEsc) {
         bw.put((1u << p) - 1u, p + 1u);
         bw.put(v & ((1u << k) - 1u), k);
@@ -133,30 +134,19 @@ struct Rlgr {
     }
 };
 
-// ---- encoder: one CTA per (frame, row block); thread = (rung, channel) ----
-// Rows of the block are staged through shared memory in chunks of kChunkRows
-// with asynchronous copies (double-buffered), so every rung's streams are
-// coded from one read of the coefficients and no thread waits on HBM.
+// ---- encoder: one CTA per rb row blocks; thread = (row block, rung, channel) --
+// Each thread reads its channel's coefficients straight from global memory
+// (lanes of a warp are consecutive channels of a row, so a warp's load is one
+// contiguous run of the row) with the next kPrefetch rows in flight in
+// registers while the current ones are coded; threads never wait for each
+// other after the CTA's one barrier.  Threads of the other rungs of a row
+// read the same words (served by L1).
 struct EncJobs {
     RlgrJob j;
     const uint64_t *job_off;  // F + 1: first job (row block) of each frame
 };
 
-constexpr uint32_t kChunkRows = 16;
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
-{
-    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
+constexpr uint32_t kPrefetch = 4;
 
 // Row blocks per CTA: enough that rb * W (W = rungs x channels threads per
 // row block) fills whole warps (rb = 32 / gcd(W, 32)), at most 512 threads.
@@ -175,9 +165,8 @@ struct EncBlock {  // one row block of a CTA
 };
 
 template <bool FROM_INT, bool DIST>
-__global__ void __launch_bounds__(1024) rlgr_encode_kernel(EncJobs E, const int32_t *qin, uint32_t rb)
+__global__ void __launch_bounds__(512) rlgr_encode_kernel(EncJobs E, const int32_t *qin, uint32_t rb)
 {
-    extern __shared__ __align__(16) unsigned char esm[];
     __shared__ EncBlock blk_info[32];
     const RlgrJob &j = E.j;
     const uint32_t C = j.C, W = j.R * C;
@@ -203,86 +192,65 @@ __global__ void __launch_bounds__(1024) rlgr_encode_kernel(EncJobs E, const int3
         blk_info[t] = e;
     }
     __syncthreads();
-    const uint32_t chunk_elems = kChunkRows * C;
-    uint32_t *buf = reinterpret_cast<uint32_t *>(esm);  // rb x 2 x chunk_elems words
-    const uint32_t *src = FROM_INT ? reinterpret_cast<const uint32_t *>(qin) : reinterpret_cast<const uint32_t *>(j.Y);
-    uint32_t maxlen = 0;
-    for (uint32_t q = 0; q < rb; ++q) maxlen = blk_info[q].len > maxlen ? blk_info[q].len : maxlen;
-    const uint32_t nchunks = (maxlen + kChunkRows - 1) / kChunkRows;
-    auto issue = [&](uint32_t k) {
-        const uint32_t r0 = k * kChunkRows;
-        for (uint32_t q = 0; q < rb; ++q) {
-            const EncBlock &e = blk_info[q];
-            if (r0 >= e.len) continue;
-            const uint32_t rows = (e.len - r0) < kChunkRows ? (e.len - r0) : kChunkRows;
-            uint32_t *dst = buf + (2 * q + (k & 1)) * chunk_elems;
-            const uint32_t *gs = src + e.gbase + (uint64_t)r0 * C;
-            const bool vec = (C % 4 == 0) && ((e.gbase & 3) == 0) && (((uintptr_t)src & 15) == 0);
-            if (vec) {
-                for (uint32_t v = t; v < rows * C / 4; v += blockDim.x) cp_async16(dst + 4 * v, gs + 4 * v);
-            } else {
-                for (uint32_t v = t; v < rows * C; v += blockDim.x) cp_async4(dst + v, gs + v);
-            }
-        }
-        cp_async_commit();
-    };
     const uint32_t jl = t / W;
-    const bool act = jl < rb && blk_info[jl < rb ? jl : 0].len > 0;
-    const uint32_t w = act ? t - jl * W : 0u;
+    if (jl >= rb) return;
+    const EncBlock me = blk_info[jl];
+    if (me.len == 0) return;
+    const uint32_t w = t - jl * W;
     const uint32_t r = w / C, c = w - r * C;
-    const EncBlock &me = blk_info[act ? jl : 0];
-    const uint64_t blk = act ? j.blk_off[me.f] + ((uint64_t)r * me.nb + me.b) * C + c : 0;
+    const uint64_t blk = j.blk_off[me.f] + ((uint64_t)r * me.nb + me.b) * C + c;
     BitWriter bw{0u, 0u, 0u, j.slots + blk * j.slot_words, j.slot_words};
     Rlgr st;
     st.init();
-    const float inv = (FROM_INT || !act) ? 0.f : j.inv_step[r * C + c];
-    const float stp = (DIST && act) ? j.step[r * C + c] : 0.f;
+    const float inv = FROM_INT ? 0.f : j.inv_step[r * C + c];
+    const float stp = DIST ? j.step[r * C + c] : 0.f;
     float sq = 0.f;
     double dc_err = 0.0;
-    if (nchunks) issue(0);
-    for (uint32_t k = 0; k < nchunks; ++k) {
-        if (k + 1 < nchunks) {
-            issue(k + 1);
-            cp_async_wait_one();
+    const uint32_t *src = FROM_INT ? reinterpret_cast<const uint32_t *>(qin) : reinterpret_cast<const uint32_t *>(j.Y);
+    const uint32_t *col = src + me.gbase + c;  // row i of this channel at col[i * C]
+    const uint32_t len = me.len;
+    uint32_t i = 0;
+    if (!FROM_INT && j.dc && me.b == 0) {  // the frame's DC: quantised from its FP64 value
+        const double y = j.dc[(uint64_t)me.f * C + c], st64 = j.steps_rg[r * j.G + j.groups[c]];
+        const int32_t q = quantize_f64(y, st64, j.tau64);
+        st.code(bw, zz(q));
+        if (DIST) {
+            const double e = __dsub_rn(y, __dmul_rn((double)q, st64));
+            dc_err = __dmul_rn(e, e);
+        }
+        i = 1;
+    }
+    auto code_one = [&](uint32_t x) {
+        if (DIST) {  // squared error of the dequantised coefficient (Parseval: of the attributes)
+            const float y = __uint_as_float(x);
+            const int32_t q = quantize_f32(y, inv, j.tau);
+            const float e = __fsub_rn(y, __fmul_rn((float)q, stp));
+            sq = __fadd_rn(sq, __fmul_rn(e, e));
+            st.code(bw, zz(q));
         } else {
-            cp_async_wait_all();
+            st.code(bw, FROM_INT ? zz((int32_t)x) : quantize_zz_f32(__uint_as_float(x), inv, j.tau));
         }
-        __syncthreads();
-        if (act && k * kChunkRows < me.len) {
-            const uint32_t rows = (me.len - k * kChunkRows) < kChunkRows ? (me.len - k * kChunkRows) : kChunkRows;
-            const uint32_t *cb = buf + (2 * jl + (k & 1)) * chunk_elems + c;
-            uint32_t i0 = 0;
-            if (!FROM_INT && j.dc && k == 0 && me.b == 0) {  // the frame's DC: quantised from its FP64 value
-                const double y = j.dc[(uint64_t)me.f * C + c], st64 = j.steps_rg[r * j.G + j.groups[c]];
-                const int32_t q = quantize_f64(y, st64, j.tau64);
-                st.code(bw, zz(q));
-                if (DIST) {
-                    const double e = __dsub_rn(y, __dmul_rn((double)q, st64));
-                    dc_err = __dmul_rn(e, e);
-                }
-                i0 = 1;
-            }
-            for (uint32_t i = i0; i < rows; ++i) {
-                const uint32_t x = cb[i * C];
-                if (DIST) {  // squared error of the dequantised coefficient (Parseval: of the attributes)
-                    const float y = __uint_as_float(x);
-                    const int32_t q = quantize_f32(y, inv, j.tau);
-                    const float e = __fsub_rn(y, __fmul_rn((float)q, stp));
-                    sq = __fadd_rn(sq, __fmul_rn(e, e));
-                    st.code(bw, zz(q));
-                } else {
-                    st.code(bw, FROM_INT ? zz((int32_t)x) : quantize_zz_f32(__uint_as_float(x), inv, j.tau));
-                }
-            }
-        }
-        __syncthreads();
+    };
+    uint32_t cur[kPrefetch];
+#pragma unroll
+    for (uint32_t d = 0; d < kPrefetch; ++d) cur[d] = (i + d < len) ? __ldg(col + (uint64_t)(i + d) * C) : 0u;
+    for (; i + kPrefetch <= len; i += kPrefetch) {
+        uint32_t nx[kPrefetch];
+        const uint32_t *q = col + (uint64_t)(i + kPrefetch) * C;
+#pragma unroll
+        for (uint32_t d = 0; d < kPrefetch; ++d) nx[d] = (i + kPrefetch + d < len) ? __ldg(q + d * C) : 0u;
+#pragma unroll
+        for (uint32_t d = 0; d < kPrefetch; ++d) code_one(cur[d]);
+#pragma unroll
+        for (uint32_t d = 0; d < kPrefetch; ++d) cur[d] = nx[d];
     }
-    if (act) {
-        st.finish(bw);
-        j.block_words[blk] = bw.nw;
-        if (bw.nw > j.slot_words) atomicExch(j.overflow, 1u);
-        if (DIST) atomicAdd(j.sq_err + ((uint64_t)me.f * j.R + r) * C + c, __dadd_rn((double)sq, dc_err));
-    }
+#pragma unroll
+    for (uint32_t d = 0; d < kPrefetch; ++d)
+        if (i + d < len) code_one(cur[d]);
+    st.finish(bw);
+    j.block_words[blk] = bw.nw;
+    if (bw.nw > j.slot_words) atomicExch(j.overflow, 1u);
+    if (DIST) atomicAdd(j.sq_err + ((uint64_t)me.f * j.R + r) * C + c, __dadd_rn((double)sq, dc_err));
 }
 
 // ---- decoder ------------------------------------------------------------------
@@ -523,22 +491,16 @@ void launch_rlgr_offsets(const uint32_t *vstart, uint32_t F, uint32_t B, uint32_
     count_launch();
 }
 
-static size_t enc_smem(uint32_t C, uint32_t rb) { return (size_t)rb * 2 * kChunkRows * C * 4; }
-
 void launch_rlgr_encode(const RlgrJob &j, const uint64_t *job_off, uint64_t jobs_bound, cudaStream_t s)
 {
     if (jobs_bound == 0 || j.C == 0) return;
     EncJobs E{j, job_off};
     const uint32_t rb = row_blocks_per_cta(j.R * j.C);
     const uint32_t threads = (rb * j.R * j.C + 31) / 32 * 32;
-    const size_t smem = enc_smem(j.C, rb);
-    if (j.sq_err) {
-        cudaFuncSetAttribute(rlgr_encode_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        rlgr_encode_kernel<false, true><<<(uint32_t)((jobs_bound + rb - 1) / rb), threads, smem, s>>>(E, nullptr, rb);
-    } else {
-        cudaFuncSetAttribute(rlgr_encode_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        rlgr_encode_kernel<false, false><<<(uint32_t)((jobs_bound + rb - 1) / rb), threads, smem, s>>>(E, nullptr, rb);
-    }
+    if (j.sq_err)
+        rlgr_encode_kernel<false, true><<<(uint32_t)((jobs_bound + rb - 1) / rb), threads, 0, s>>>(E, nullptr, rb);
+    else
+        rlgr_encode_kernel<false, false><<<(uint32_t)((jobs_bound + rb - 1) / rb), threads, 0, s>>>(E, nullptr, rb);
     count_launch();
 }
 
@@ -561,9 +523,7 @@ void launch_rlgr_encode_indices(const int32_t *q, const uint32_t *vstart, uint32
     EncJobs E{j, job_off};
     const uint32_t rb = row_blocks_per_cta(C);
     const uint32_t threads = (rb * C + 31) / 32 * 32;
-    const size_t smem = enc_smem(C, rb);
-    cudaFuncSetAttribute(rlgr_encode_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    rlgr_encode_kernel<true, false><<<(uint32_t)((jobs_bound + rb - 1) / rb), threads, smem, s>>>(E, q, rb);
+    rlgr_encode_kernel<true, false><<<(uint32_t)((jobs_bound + rb - 1) / rb), threads, 0, s>>>(E, q, rb);
     count_launch();
 }
 
