@@ -3,8 +3,8 @@
 // points, and its eigenvectors; rows of K = eigenvectors by decreasing
 // eigenvalue, the largest component of each made positive.  Everything here
 // is FP64 (the sample is 4096 rows, so this costs next to nothing): the YUV
-// values of the sample, per-slice means and centred co-moments (16 slices of
-// 256 rows, one CTA each), the slices combined in a fixed order by the
+// values of the sample, per-slice means and centred co-moments (64 slices of
+// 64 rows, one CTA each), the slices combined in a fixed order by the
 // pairwise update of Chan, Golub and LeVeque, and cyclic Jacobi rotations
 // (one warp per channel, seven disjoint rotations at a time).  K is rounded to
 // FP32 once, for the header and the per-row transforms.  The frame's
@@ -17,8 +17,8 @@ namespace gsnfs {
 namespace {
 
 constexpr int kSample = 4096;
-constexpr int kSlices = 16;                   // CTAs per frame for the sample sums
-constexpr int kSliceRows = kSample / kSlices;  // 256
+constexpr int kSlices = 64;                   // CTAs per frame for the sample sums
+constexpr int kSliceRows = kSample / kSlices;  // 64
 constexpr int kRowsPerChunk = 32;
 constexpr int kPairs = kKltN * (kKltN + 1) / 2;  // 120
 constexpr int kPartWords = 3 * (kPairs + kKltN) + 1;  // per slice: co-moments, then means, per channel; row count

@@ -504,11 +504,11 @@ struct Chunks {
     uint64_t chunk;
 };
 
-Chunks chunks_for(uint64_t n, int num_sms)
+Chunks chunks_for(uint64_t n, int num_sms, uint32_t per_sm = 2)
 {
     Chunks c;
     uint64_t t = (n + 1023) / 1024;
-    uint64_t pmax = (uint64_t)num_sms * 2;
+    uint64_t pmax = (uint64_t)num_sms * per_sm;
     c.P = (uint32_t)(t < 1 ? 1 : (t < pmax ? t : pmax));
     c.chunk = (n + c.P - 1) / c.P;
     if (c.chunk == 0) c.chunk = 1;
@@ -533,7 +533,10 @@ uint32_t occ_x(uint32_t F, int num_sms)
 
 }  // namespace
 
-uint64_t dedup_partial_words(uint64_t n, int num_sms) { return chunks_for(n, num_sms).P + 1; }
+// dedup: up to 8 CTAs of 256 threads per SM (each CTA scans its chunk in steps of 256 keys, so the SM needs many
+// of them in flight to hide the key loads)
+constexpr uint32_t kDedupPerSm = 8;
+uint64_t dedup_partial_words(uint64_t n, int num_sms) { return chunks_for(n, num_sms, kDedupPerSm).P + 1; }
 
 void launch_dedup(const uint64_t *keys, uint64_t n, uint32_t frame_shift, uint32_t F, uint64_t *codes,
                   uint32_t *seg, uint8_t *gap, uint32_t *vstart, uint32_t *partials, DevState *st, int num_sms,
@@ -541,7 +544,7 @@ void launch_dedup(const uint64_t *keys, uint64_t n, uint32_t frame_shift, uint32
 {
     if (!vals) row0 = nullptr;
     dev_memset(vstart, 0xFF, sizeof(uint32_t) * (F + 1), s);
-    Chunks c = chunks_for(n, num_sms);
+    Chunks c = chunks_for(n, num_sms, kDedupPerSm);
     if (n == 0) {
         dev_memset(partials, 0, sizeof(uint32_t) * (c.P + 1), s);
         dev_memset(seg, 0, sizeof(uint32_t), s);

@@ -20,18 +20,50 @@ constexpr uint32_t kProbBits = 15;
 constexpr uint32_t kM = 1u << kProbBits;
 constexpr uint32_t kL = 1u << 16;
 
+// Byte histogram of each frame's occupancy bytes: 16 bytes per load (the
+// bytes of a 16-byte word are counted from registers, so every thread keeps
+// several loads in flight), counted into per-warp sub-histograms in shared
+// memory (fewer lanes contend for a bin), added up per CTA.
 __global__ void __launch_bounds__(256) hist_kernel(const uint8_t *__restrict__ occ, const uint64_t *occ_off,
                                                    DevState *st)
 {
-    __shared__ uint32_t h[256];
-    const uint32_t f = blockIdx.y;
-    h[threadIdx.x] = 0;
+    __shared__ uint32_t h[8][256];
+    const uint32_t f = blockIdx.y, t = threadIdx.x, wid = t >> 5;
+    for (uint32_t k = t; k < 8 * 256; k += 256) (&h[0][0])[k] = 0;
     __syncthreads();
     const uint64_t b = occ_off[f], n = occ_off[f + 1] - b;
-    for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (uint64_t)gridDim.x * 256)
-        atomicAdd(&h[occ[b + i]], 1u);
+    const uint8_t *base = occ + b;
+    const uint64_t head = n < ((16 - ((uintptr_t)base & 15)) & 15) ? n : ((16 - ((uintptr_t)base & 15)) & 15);
+    const uint64_t n16 = (n - head) >> 4;
+    const uint4 *v = reinterpret_cast<const uint4 *>(base + head);
+    const uint64_t gt = (uint64_t)blockIdx.x * 256 + t, gs = (uint64_t)gridDim.x * 256;
+    uint32_t *hw = h[wid];
+    for (uint64_t i = gt; i < n16; i += 4 * gs) {
+        uint4 x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = (i + u * gs < n16) ? __ldg(v + i + u * gs) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (i + u * gs >= n16) break;
+            const uint32_t w[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                atomicAdd(&hw[w[e] & 255u], 1u);
+                atomicAdd(&hw[(w[e] >> 8) & 255u], 1u);
+                atomicAdd(&hw[(w[e] >> 16) & 255u], 1u);
+                atomicAdd(&hw[w[e] >> 24], 1u);
+            }
+        }
+    }
+    // the bytes before the first 16-byte boundary and after the last one
+    const uint64_t tail0 = head + (n16 << 4);
+    if (gt < head) atomicAdd(&hw[base[gt]], 1u);
+    if (gt < n - tail0) atomicAdd(&hw[base[tail0 + gt]], 1u);
     __syncthreads();
-    if (h[threadIdx.x]) atomicAdd(&st->hist[f][threadIdx.x], h[threadIdx.x]);
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) c += h[w][t];
+    if (c) atomicAdd(&st->hist[f][t], c);
 }
 
 // one CTA (256 threads) per frame: frequencies, cumulative table, mode
@@ -101,7 +133,7 @@ __global__ void __launch_bounds__(32 * kEncWarps) encode_kernel(const uint8_t *_
                                                                uint64_t slot_bytes, uint32_t *chunk_words,
                                                                uint32_t *chunk_top)
 {
-    __shared__ uint8_t s_sym[kEncWarps][kStageSyms];
+    __shared__ __align__(16) uint8_t s_sym[kEncWarps][kStageSyms];
     __shared__ uint32_t s_fc[kEncWarps][256];   // freq << 16 | cum (cum < 2^15)
     __shared__ uint32_t s_rcp[kEncWarps][256];  // ceil(2^32 / freq) for freq >= 2 (0 for freq < 2)
     const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -130,7 +162,31 @@ __global__ void __launch_bounds__(32 * kEncWarps) encode_kernel(const uint8_t *_
             const uint32_t win_lo_g = (uint32_t)g + 1 > kStageSyms / 32 ? (uint32_t)g + 1 - kStageSyms / 32 : 0u;
             const uint32_t b0 = win_lo_g * 32, b1 = ((uint32_t)g + 1) * 32 < len ? ((uint32_t)g + 1) * 32 : len;
             __syncwarp();
-            for (uint32_t k = b0 + lane; k < b1; k += 32) s_sym[wl][k - b0] = sym[k];
+            {  // symbols [b0, b1): 16-byte loads over the aligned middle, bytes at the two ends
+                const uintptr_t a0 = (uintptr_t)(sym + b0), a1 = (uintptr_t)(sym + b1);
+                const uint32_t head = (uint32_t)((((a0 + 15) & ~(uintptr_t)15) - a0) < (a1 - a0)
+                                                     ? ((a0 + 15) & ~(uintptr_t)15) - a0 : a1 - a0);
+                const uint32_t nvec = (uint32_t)((b1 - b0 - head) >> 4);
+                const uint4 *v = reinterpret_cast<const uint4 *>(sym + b0 + head);
+                uint8_t *dst = &s_sym[wl][0];
+                for (uint32_t k = lane; k < nvec; k += 32) {
+                    const uint4 w = __ldg(v + k);
+                    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst + head + 16 * k);  // byte-addressed smem
+                    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (((head + 16 * k) & 3) == 0) {
+                            d32[e] = ws[e];
+                        } else {
+#pragma unroll
+                            for (int bb = 0; bb < 4; ++bb) dst[head + 16 * k + 4 * e + bb] = (uint8_t)(ws[e] >> (8 * bb));
+                        }
+                    }
+                }
+                if (lane < head) dst[lane] = sym[b0 + lane];
+                const uint32_t t0 = head + 16 * nvec;
+                if (lane < (b1 - b0) - t0) dst[t0 + lane] = sym[b0 + t0 + lane];
+            }
             __syncwarp();
             for (; g >= (int)win_lo_g; --g) {
                 const uint32_t j = (uint32_t)g * 32 + lane;
