@@ -111,7 +111,7 @@ struct Rlgr {
         const uint32_t k = (uint32_t)K >> 4;
         if (__builtin_expect(k == 0, 1)) {  // Golomb-Rice mode
             gr_put(bw, u, (uint32_t)KR >> 4, KR);
-            K = u == 0 ? (K + 3 > 240 ? 240 : K + 3) : (K >= 3 ? K - 3 : 0);
+            K = u == 0 ? K + 3 : (K >= 3 ? K - 3 : 0);  // Golomb-Rice mode runs while K < 16: no cap at 240
         } else if (u == 0) {
             if (++z == (1u << k)) {
                 bw.put(0, 1);
@@ -290,12 +290,9 @@ struct WinReader {
 
 __device__ __forceinline__ void adapt_kr(uint32_t p, int &KR)
 {
-    if (p == 0) {
-        KR = KR >= 2 ? KR - 2 : 0;
-    } else if (p > 1) {
-        uint32_t t = (uint32_t)KR + (p > 384u ? 384u : p) + 1u;
-        KR = t > 384u ? 384 : (int)t;
-    }
+    // p = 0: KR - 2, p = 1: unchanged, p > 1: KR + p + 1; within [0, 384]
+    const int d = p >= 2u ? (int)(p > 384u ? 384u : p) + 1 : (p == 1u ? 0 : -2);
+    KR = min(max(KR + d, 0), 384);
 }
 
 // Rare path of gr_read: the remainder crosses the window, or the escape code.
@@ -341,8 +338,10 @@ __device__ __forceinline__ uint32_t gr_read(WinReader &r, uint32_t k, int &KR, b
 
 // Decodes one block stream (len coefficients of one channel) to out[i * C],
 // i < len: dequantised (times sc) or as indices.  Runs are kept as pending
-// zeros (and the nonzero that ends a partial run as a pending value), so every
-// lane of a warp writes one row per iteration and the stores coalesce.
+// zeros (and the nonzero that ends a partial run as a pending value), so a
+// lane writes one or two rows per iteration: a lane that ends an iteration in
+// Golomb-Rice mode decodes a second symbol in the same iteration (fewer loop
+// and mode tests per symbol).
 template <bool TO_INT>
 __device__ __forceinline__ void decode_stream(const uint32_t *wp, uint32_t nw, uint32_t len, uint32_t C, float sc,
                                               float *yout, int32_t *qout, DevState *st)
@@ -359,7 +358,7 @@ __device__ __forceinline__ void decode_stream(const uint32_t *wp, uint32_t nw, u
         if (__builtin_expect(!(zeros | (uint32_t)has_pending | k), 1)) {  // the common case: Golomb-Rice mode
             const uint32_t u = gr_read(r, (uint32_t)KR >> 4, KR, bad);
             q = unzz(u);
-            K = u == 0 ? (K + 3 > 240 ? 240 : K + 3) : (K >= 3 ? K - 3 : 0);
+            K = u == 0 ? K + 3 : (K >= 3 ? K - 3 : 0);  // Golomb-Rice mode runs while K < 16: no cap at 240
         } else if (zeros) {
             --zeros;
         } else if (has_pending) {
@@ -394,6 +393,19 @@ __device__ __forceinline__ void decode_stream(const uint32_t *wp, uint32_t nw, u
         } else {
             *yout = __fmul_rn((float)q, sc);
             yout += C;
+        }
+        if (i + 1 < len && !(zeros | (uint32_t)has_pending | ((uint32_t)K >> 4))) {  // a second GR-mode symbol
+            const uint32_t u = gr_read(r, (uint32_t)KR >> 4, KR, bad);
+            const int32_t q2 = unzz(u);
+            K = u == 0 ? K + 3 : (K >= 3 ? K - 3 : 0);
+            ++i;
+            if (TO_INT) {
+                *qout = q2;
+                qout += C;
+            } else {
+                *yout = __fmul_rn((float)q2, sc);
+                yout += C;
+            }
         }
     }
     if (bad || r.overrun()) set_error(&st->err, kErrCorrupt);
