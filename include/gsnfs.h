@@ -154,13 +154,16 @@ gsnfs_status gsnfs_peek_frame(const uint8_t *h_header, uint64_t bytes, uint64_t 
 gsnfs_status gsnfs_decode_frame(gsnfs_ctx *ctx, void *stream, const uint8_t *d_bitstream, uint64_t bytes,
                                 float *d_pos, float *d_attr, uint64_t capacity_nv, uint64_t *out_nv);
 
-/* Level of detail: decodes the frame and reduces it to the nodes of octree
- * depth `depth` <= J (Algorithm 2's depth shift read as J - depth).  Node k
- * (in Morton order) gets the centre of its cell at that depth in d_pos (x 3)
- * and the mean of its voxels' decoded attributes in d_attr (x C), which by
- * Eq. (1) is its RAHT low-pass coefficient divided by sqrt(voxel count).
- * *out_nodes receives the node count; GSNFS_ERR_CAPACITY (outputs untouched)
- * when it exceeds capacity_nodes.  depth = J gives the full decode. */
+/* Level of detail: decodes the frame to the nodes of octree depth
+ * `depth` <= J (Algorithm 2's depth shift read as J - depth).  Node k (in
+ * Morton order) gets the centre of its cell at that depth in d_pos (x 3) and
+ * the mean of its voxels' decoded attributes in d_attr (x C), which by Eq. (1)
+ * is its RAHT low-pass coefficient divided by sqrt(voxel count): the geometry
+ * and the coefficients are decoded in full, but the inverse RAHT runs over
+ * the node sequence only (the butterflies inside nodes are never applied) and
+ * no per-voxel output is formed.  *out_nodes receives the node count;
+ * GSNFS_ERR_CAPACITY (outputs untouched) when it exceeds capacity_nodes.
+ * depth = J gives the full decode.  d_pos and d_attr may each be NULL. */
 gsnfs_status gsnfs_decode_frame_lod(gsnfs_ctx *ctx, void *stream, const uint8_t *d_bitstream, uint64_t bytes,
                                     uint32_t depth, float *d_pos, float *d_attr, uint64_t capacity_nodes,
                                     uint64_t *out_nodes);
@@ -233,6 +236,35 @@ gsnfs_status gsnfs_encode_batch_rd(gsnfs_ctx *ctx, void *stream, uint32_t frames
 gsnfs_status gsnfs_decode_batch(gsnfs_ctx *ctx, void *stream, uint32_t frames, const uint8_t *d_in,
                                 const uint64_t *h_in_offsets, float *d_pos, float *d_attr,
                                 uint64_t capacity_rows, uint64_t *h_out_rows);
+
+/* Header records for the decoder: GSNFS_HEADER_RECORD_BYTES per stream, holding the stream's header tables
+ * (bytes [0, header size) of the stream, at most 4096) at offset 0, the first 24 bytes of its occupancy section at
+ * 4096 and the first 8 bytes of its attribute section at 4160 (zeros where a section is shorter). */
+#define GSNFS_HEADER_RECORD_BYTES 4224u
+
+/* gsnfs_encode_batch that also returns the header record of every stream in h_headers (host, frames x rungs
+ * records, in stream order), read back together with the offsets.  A decoder given these records
+ * (gsnfs_decode_batch_async) needs no read of the streams from the host. */
+gsnfs_status gsnfs_encode_batch_headers(gsnfs_ctx *ctx, void *stream, uint32_t frames, const float *const *h_pos,
+                                        const float *const *h_attr, const uint64_t *h_n, const uint32_t *h_J,
+                                        uint32_t rungs, const double *h_rung_scale, const gsnfs_quant *q,
+                                        uint8_t *d_out, uint64_t capacity, uint64_t *h_offsets,
+                                        uint8_t *h_headers);
+
+/* gsnfs_decode_batch without host synchronisation: with the streams' header records given (h_headers, host,
+ * frames records in stream order, as gsnfs_encode_batch_headers returns them) nothing is read back from the
+ * device; the call validates the records on the host, fills h_out_rows, enqueues the decode on `stream` and
+ * returns.  The device's status (0, or 1 = corrupt stream, 2 = capacity, 4 = a bounded wait expired) is written
+ * into *status (device memory, or pinned host memory the device can write) in stream order after the last
+ * kernel; the outputs are valid once the stream has reached that point.  With h_headers NULL the headers are read
+ * from d_in with host synchronisations first (the decode itself is still asynchronous).  Host-detected errors are
+ * returned as usual.  The call stages its frame tables in a pinned buffer of its own (one of four, reused once
+ * the decode that last used it has completed).  As for every call on a context, calls must not overlap: keep
+ * the context's calls on one stream (or order them with events). */
+gsnfs_status gsnfs_decode_batch_async(gsnfs_ctx *ctx, void *stream, uint32_t frames, const uint8_t *d_in,
+                                      const uint64_t *h_in_offsets, const uint8_t *h_headers, float *d_pos,
+                                      float *d_attr, uint64_t capacity_rows, uint64_t *h_out_rows,
+                                      uint32_t *status);
 
 /* ---- stage entry points (each is one step of the path above) ---------- */
 

@@ -133,6 +133,11 @@ struct gsnfs_ctx {
     cudaEvent_t gev_in = nullptr, gev_out = nullptr;
     std::vector<GraphEntry> gcache;
     uint64_t gtick = 0, ghits = 0, gcaptures = 0, gfailures = 0;
+    // pinned staging of the asynchronous decoder: a ring of slots, each free once its event has completed
+    unsigned char *aring[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t aring_cap[4] = {0, 0, 0, 0};
+    cudaEvent_t aring_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint32_t aring_next = 0;
 };
 
 struct gsnfs_raht_plan {
@@ -321,6 +326,30 @@ gsnfs_status check_quant(const gsnfs_quant *q)
 struct StreamInfo {
     uint64_t off, hb, occ, attr;
 };
+
+// Header records of every stream, for a decoder that is given them instead of
+// reading them back (GSNFS_HEADER_RECORD_BYTES each): the stream's header
+// tables at 0, the first 24 bytes of its occupancy section at 4096 and the
+// first 8 of its attribute section at 4160.  One CTA per stream.
+__global__ void header_records_kernel(const uint8_t *out, const StreamInfo *si, uint32_t n, uint8_t *rec)
+{
+    const uint32_t i = blockIdx.x;
+    if (i >= n) return;
+    const StreamInfo x = si[i];
+    uint8_t *r = rec + (uint64_t)i * GSNFS_HEADER_RECORD_BYTES;
+    const uint8_t *b = out + x.off;
+    const uint32_t hb = x.hb < 4096 ? (uint32_t)x.hb : 4096u;
+    for (uint32_t k = threadIdx.x; k < GSNFS_HEADER_RECORD_BYTES; k += blockDim.x) {  // every byte: zeros elsewhere
+        uint8_t v = 0;
+        if (k < hb)
+            v = b[k];
+        else if (k >= 4096 && k < 4096 + 24 && k - 4096 < x.occ + x.attr)
+            v = b[x.hb + (k - 4096)];
+        else if (k >= 4160 && k < 4168 && x.attr >= 8)
+            v = b[x.hb + x.occ + (k - 4160)];
+        r[k] = v;
+    }
+}
 
 struct HdrParams {
     uint32_t F, R, C, G, B, chunk, color;
@@ -558,6 +587,7 @@ struct EncodeReq {
     float *recon_pos = nullptr;
     float *recon_attr = nullptr;
     double *dist = nullptr;  // host, F x R x C: squared quantisation error sums (or null)
+    uint8_t *headers = nullptr;  // host, F x R records of GSNFS_HEADER_RECORD_BYTES (or null)
     // results
     uint64_t total_bytes = 0;
     uint64_t nv = 0;
@@ -608,6 +638,9 @@ void carve_plan(Carve &cv, RahtPlanDev &p, uint64_t nv_cap, uint32_t T, const ui
     p.tile_carry = cv.take<uint32_t>(tiles);
     p.passes = cv.take<RahtPass>(kRahtMaxPasses + 1);
     p.npasses = cv.take<uint32_t>(1);
+    p.pos0 = nullptr;
+    p.end0 = nullptr;
+    p.pipe_ctr = cv.take<uint32_t>(2);
 }
 
 size_t carve_encode(Carve &cv, EncLayout &L, const EncodeReq &rq, int num_sms, bool worst_slots,
@@ -1025,6 +1058,16 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
         CK(cudaMemcpy(si.data(), L.si, sizeof(StreamInfo) * si.size(), cudaMemcpyDeviceToHost));
         for (size_t i = 0; i < si.size(); ++i) rq.offsets[i] = si[i].off;
     }
+    if (rq.headers) {  // header records through the pinned staging buffer (the stream is idle here)
+        const size_t nrec = (size_t)F * R, bytes = nrec * GSNFS_HEADER_RECORD_BYTES;
+        st = grow_pinned(ctx, bytes);
+        if (st) return st;
+        header_records_kernel<<<(uint32_t)nrec, 256, 0, s>>>(rq.out, L.si, (uint32_t)nrec, ctx->pinned);
+        count_launch();
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s));
+        memcpy(rq.headers, ctx->pinned, bytes);
+    }
     return GSNFS_OK;
 }
 
@@ -1197,8 +1240,20 @@ size_t carve_decode(Carve &cv, DecLayout &L, const ParsedHeader &P, int num_sms,
     return cv.off;
 }
 
+// Level-of-detail request of decode_impl: node centres and means at octree depth `depth` < J.
+struct LodReq {
+    uint32_t depth;
+    float *pos, *attr;     // caller's outputs (either may be null)
+    uint64_t capacity;     // rows of both
+    uint64_t *out_nodes;
+};
+
+gsnfs_status lod_from_voxels(gsnfs_ctx *ctx, cudaStream_t s, const ParsedHeader &P, DecLayout &L, bool attrs,
+                             const LodReq &lod);
+
 gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, uint64_t bytes, float *d_pos,
-                         float *d_attr, uint64_t capacity_nv, uint64_t *out_nv, const uint64_t **codes_out = nullptr)
+                         float *d_attr, uint64_t capacity_nv, uint64_t *out_nv, const uint64_t **codes_out = nullptr,
+                         const LodReq *lod = nullptr)
 {
     ParsedHeader P{};
     gsnfs_status st = read_headers(ctx, s, d_in, bytes, P);
@@ -1265,6 +1320,7 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
     launch_octree_decode(occ, P.n_occ, P.J, P.lsz, L.nodes, L.pref, L.ppart, L.codes, dst, sms, s);
     if (d_pos) launch_voxel_centres(L.codes, P.nv, P.J, L.grid, d_pos, s, L.ctab);
     stage_end(s, kStOctreeDecode);
+    if (lod) return lod_from_voxels(ctx, s, P, L, attrs, *lod);
     // a12: schedule, then (after the RLGR branch) the inverse RAHT
     if (attrs) {
         stage_begin(s, kStPrelude);
@@ -1296,42 +1352,186 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
     return map_dev_error(res[0]);
 }
 
+// Level of detail from a decoded voxel set (geometry decoded on s; the
+// dequantised coefficients Y being decoded on the context's second stream
+// when attrs): the nodes of depth lod.depth are runs of voxels sharing
+// code >> 3(J - depth).  Each node becomes one element of a coarser RAHT
+// sequence (its voxel run, the gap before its first voxel): its weight is its
+// voxel count and its coefficients sit at its first voxel's row of Y, the
+// rows that hold the high passes of the butterflies above the depth (Eq. 1,
+// Algorithm 6).  The inverse over that sequence stops at the nodes, so the
+// butterflies inside nodes are never applied; a node's result is its
+// low-pass coefficient, and its mean attribute is that divided by sqrt(w).
+gsnfs_status lod_from_voxels(gsnfs_ctx *ctx, cudaStream_t s, const ParsedHeader &P, DecLayout &L, bool attrs,
+                             const LodReq &lod)
+{
+    const int sms = ctx->num_sms;
+    const uint64_t nv = P.nv;
+    const uint32_t C = attrs && lod.attr ? P.C : 0;
+    DevState *dst = ctx->st;
+    uint32_t *flags = nullptr, *pos0 = nullptr, *end0 = nullptr;
+    uint64_t *offs = nullptr, *starts = nullptr, *part = nullptr;
+    uint8_t *gap0 = nullptr;
+    float *rows = nullptr;
+    auto carve = [&](Carve &cv) {
+        flags = cv.take<uint32_t>(nv + 1);
+        offs = cv.take<uint64_t>(nv + 2);
+        starts = cv.take<uint64_t>(nv + 2);
+        part = cv.take<uint64_t>(scan_partial_words(nv, sms) + 1);
+        pos0 = cv.take<uint32_t>(nv + 1);
+        end0 = cv.take<uint32_t>(nv + 1);
+        gap0 = cv.take<uint8_t>(nv + 2);
+        rows = cv.take<float>(nv * (C ? C : 1) + 4);
+        return cv.off;
+    };
+    Carve m(nullptr);
+    const size_t need = carve(m);
+    gsnfs_status res = GSNFS_OK;
+    if (need > ctx->lod_cap) {
+        if (ctx->lod) cudaFree(ctx->lod);
+        ctx->lod = nullptr;
+        ctx->lod_cap = 0;
+        if (cudaMalloc(&ctx->lod, need) != cudaSuccess) {
+            ctx->lod = nullptr;
+            res = GSNFS_ERR_OOM;
+        } else {
+            ctx->lod_cap = need;
+        }
+    }
+    // node count: known on the device only; with room for every voxel the outputs need no check before the
+    // kernels, so the count is read back at the end (else once here, before anything is written)
+    uint64_t nn = nv;
+    const bool room = lod.capacity >= nv;
+    uint64_t *hn = reinterpret_cast<uint64_t *>(ctx->pinned + 2048);
+    const uint32_t sh = 3 * (P.J - lod.depth);
+    if (!res) {
+        Carve cv(ctx->lod);
+        carve(cv);
+        launch_lod_index(L.codes, nv, sh, flags, offs, part, starts, sms, s);
+        if (!room) {
+            if (stage_copy(hn, offs + nv, 8, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+                res = GSNFS_ERR_CUDA;
+            else
+                nn = *hn;
+            *lod.out_nodes = nn;
+            if (!res && nn > lod.capacity) res = GSNFS_ERR_CAPACITY;
+        }
+        if (!res && C) {
+            launch_gap_levels(L.codes, nv, L.gap, s);
+            launch_lod_sequence(starts, offs + nv, nv, nn, L.gap, pos0, end0, gap0, sms, s);
+            L.plan.pos0 = pos0;
+            L.plan.end0 = end0;
+            stage_begin(s, kStPrelude);
+            launch_raht_prelude(L.plan, gap0, dst, offs + nv, sms, s);
+            stage_end(s, kStPrelude);
+        }
+    }
+    if (attrs) {  // join the coefficient branch before anything returns
+        const gsnfs_status fst = fork_end(ctx, s);
+        if (fst) return fst;
+    }
+    if (res) {
+        cudaStreamSynchronize(s);
+        return res;
+    }
+    if (C) {
+        RahtIO io{};
+        io.C = C;
+        io.Y = L.Y;
+        io.out = rows;
+        io.pool = L.pool;
+        io.frame_shift = 64;
+        if (P.color) {
+            io.klt = L.klt;
+            io.vstart = L.vst;
+            io.F = 1;
+            io.yuv_inv = yuv_inverse();
+        }
+        stage_begin(s, kStRahtInv);
+        launch_raht_inverse(L.plan, io, nn, sms, s);
+        stage_end(s, kStRahtInv);
+    }
+    LodGrid g;
+    for (int a = 0; a < 3; ++a) g.lo[a] = P.lo[a];
+    g.cell = P.ext / std::ldexp(1.0, (int)lod.depth);
+    launch_lod_means(rows, L.codes, starts, offs + nv, nn, sh, lod.depth, C, g, lod.pos, C ? lod.attr : nullptr, sms,
+                     s);
+    CK(cudaGetLastError());
+    uint32_t *hres = reinterpret_cast<uint32_t *>(ctx->pinned + 1024);
+    CK(stage_copy(hres, &dst->err, 4, s));
+    if (room) CK(stage_copy(hn, offs + nv, 8, s));
+    CK(cudaStreamSynchronize(s));
+    if (room) *lod.out_nodes = *hn;
+    return map_dev_error(hres[0]);
+}
+
 // ------------------------------------------------------- batched decoder ---
 // All frames of a batch are decoded by one sequence of launches: headers are
 // read with two host synchronisations for the whole batch, then every stage
 // runs over all frames at once (frame tables on the device).
 gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const uint8_t *d_in, const uint64_t *offs,
-                               float *d_pos, float *d_attr, uint64_t capacity_rows, uint64_t *rows_out)
+                               float *d_pos, float *d_attr, uint64_t capacity_rows, uint64_t *rows_out,
+                               const uint8_t *h_headers = nullptr, uint32_t *status = nullptr)
 {
     std::vector<ParsedHeader> P(F);
-    gsnfs_status st = grow_pinned(ctx, (size_t)F * 8192 + 65536);
-    if (st) return st;
-    CK(cudaStreamSynchronize(s));
-    uint8_t *hp = ctx->pinned;
+    gsnfs_status st = GSNFS_OK;
+    const size_t stage_need = (size_t)F * 8192 + 65536;
+    uint8_t *hp = nullptr;
+    int ring = -1;
+    if (status) {  // asynchronous: staging slot of its own, reused only once its last use has completed
+        ring = (int)(ctx->aring_next++ & 3u);
+        if (!ctx->aring_ev[ring]) {
+            CK(cudaEventCreateWithFlags(&ctx->aring_ev[ring], cudaEventDisableTiming));
+        } else {
+            CK(cudaEventSynchronize(ctx->aring_ev[ring]));
+        }
+        if (ctx->aring_cap[ring] < stage_need) {
+            if (ctx->aring[ring]) CK(cudaFreeHost(ctx->aring[ring]));
+            ctx->aring[ring] = nullptr;
+            ctx->aring_cap[ring] = 0;
+            CK(cudaMallocHost((void **)&ctx->aring[ring], stage_need));
+            ctx->aring_cap[ring] = stage_need;
+        }
+        hp = ctx->aring[ring];
+    } else {
+        st = grow_pinned(ctx, stage_need);
+        if (st) return st;
+        CK(cudaStreamSynchronize(s));
+        hp = ctx->pinned;
+    }
+    // header record of frame f: given by the caller, or read back into the staging buffer
+    auto rec = [&](uint32_t f) -> const uint8_t * {
+        return h_headers ? h_headers + (size_t)f * GSNFS_HEADER_RECORD_BYTES : hp + (size_t)f * 8192;
+    };
+    if (!h_headers) {
+        for (uint32_t f = 0; f < F; ++f) {
+            if (offs[f + 1] - offs[f] < 96) return GSNFS_ERR_CORRUPT;
+            CK(stage_copy(hp + (size_t)f * 8192, d_in + offs[f], 96, s));
+        }
+        CK(cudaStreamSynchronize(s));
+    }
     for (uint32_t f = 0; f < F; ++f) {
         if (offs[f + 1] - offs[f] < 96) return GSNFS_ERR_CORRUPT;
-        CK(stage_copy(hp + (size_t)f * 8192, d_in + offs[f], 96, s));
-    }
-    CK(cudaStreamSynchronize(s));
-    for (uint32_t f = 0; f < F; ++f) {
-        st = parse_fixed(hp + (size_t)f * 8192, offs[f + 1] - offs[f], P[f]);
+        st = parse_fixed(rec(f), offs[f + 1] - offs[f], P[f]);
         if (st) return st;
         if (P[f].hb > 4096) return GSNFS_ERR_CORRUPT;
     }
-    for (uint32_t f = 0; f < F; ++f) {
-        uint8_t *h = hp + (size_t)f * 8192;
-        CK(stage_copy(h, d_in + offs[f], P[f].hb, s));
-        CK(stage_copy(h + 4096, d_in + offs[f] + P[f].hb, 24, s));
-        if (P[f].attr_bytes >= 8)
-            CK(stage_copy(h + 4096 + 64, d_in + offs[f] + P[f].hb + P[f].occ_bytes, 8, s));
+    if (!h_headers) {
+        for (uint32_t f = 0; f < F; ++f) {
+            uint8_t *h = hp + (size_t)f * 8192;
+            CK(stage_copy(h, d_in + offs[f], P[f].hb, s));
+            CK(stage_copy(h + 4096, d_in + offs[f] + P[f].hb, 24, s));
+            if (P[f].attr_bytes >= 8)
+                CK(stage_copy(h + 4096 + 64, d_in + offs[f] + P[f].hb + P[f].occ_bytes, 8, s));
+        }
+        CK(cudaStreamSynchronize(s));
     }
-    CK(cudaStreamSynchronize(s));
     uint32_t C = 0, Jmax = 0;
     uint64_t N = 0, n_occ = 0, nodes = 0, nblk = 0, jobs = 0, max_occ = 0;
     uint32_t max_nch = 0, chunk_max = 0;
     bool any_rans = false;
     for (uint32_t f = 0; f < F; ++f) {
-        uint8_t *h = hp + (size_t)f * 8192;
+        const uint8_t *h = rec(f);
         st = parse_tables(h, P[f]);
         if (st) return st;
         st = parse_sections(h + 4096, h + 4096 + 64, P[f]);
@@ -1536,10 +1736,24 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     stage_begin(s, kStOctreeDecode);
     launch_popc_scan(L.occ, n_occ, L.pref, L.ppart, sms, s);
     launch_batch_roots(L.fr, F, L.nodes, L.codes, s);
-    for (uint32_t lv = 0; lv < Jmax; ++lv) {
-        const uint64_t count = hlp[(uint64_t)lv * (F + 1) + F];
-        launch_batch_expand(L.fr, F, lv, L.lvl_pref + (uint64_t)lv * (F + 1), count, L.occ, L.pref, L.nodes, L.codes,
-                            dst, sms, s);
+    {  // two levels per launch where the second level holds at most 4 nodes per node of the first (the deep,
+       // sparse levels: a thread's walk stays short), one level elsewhere
+        auto level_total = [&](uint32_t l) {
+            uint64_t t = 0;
+            for (uint32_t f = 0; f < F; ++f)
+                if (l <= P[f].J) t += P[f].lsz[l];
+            return t;
+        };
+        const uint32_t kmax = std::min<uint32_t>(2, batch_expand_max_levels());
+        for (uint32_t lv = 0; lv < Jmax;) {
+            const uint64_t count = hlp[(uint64_t)lv * (F + 1) + F];
+            const uint64_t t0 = std::max<uint64_t>(level_total(lv), 1);
+            uint32_t K = 1;
+            while (K < kmax && lv + K < Jmax && level_total(lv + K + 1) <= 4 * t0) ++K;
+            launch_batch_expand(L.fr, F, lv, K, L.lvl_pref + (uint64_t)lv * (F + 1), count, L.occ, L.pref, L.nodes,
+                                L.codes, dst, sms, s);
+            lv += K;
+        }
     }
     if (ctab_total) launch_batch_centre_tables(L.fr, F, Jmax, L.ctab, sms, s);
     launch_batch_centres_gaps(L.fr, F, L.vstart, N, L.codes, L.ctab, d_pos, L.gap, sms, s);
@@ -1569,6 +1783,11 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         stage_end(s, kStRahtInv);
     }
     CK(cudaGetLastError());
+    if (status) {  // the device's status word goes to the caller's word; the staging slot is busy until here
+        CK(stage_copy(status, &dst->err, 4, s));
+        CK(cudaEventRecord(ctx->aring_ev[ring], s));
+        return GSNFS_OK;
+    }
     uint32_t *res = reinterpret_cast<uint32_t *>(tp + ((o_end + 63) & ~(size_t)63));
     CK(stage_copy(res, &dst->err, 4, s));
     CK(cudaStreamSynchronize(s));
@@ -1636,6 +1855,10 @@ void gsnfs_destroy(gsnfs_ctx *ctx)
     if (ctx->gev_out) cudaEventDestroy(ctx->gev_out);
     if (ctx->arena) cudaFree(ctx->arena);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    for (int k = 0; k < 4; ++k) {
+        if (ctx->aring[k]) cudaFreeHost(ctx->aring[k]);
+        if (ctx->aring_ev[k]) cudaEventDestroy(ctx->aring_ev[k]);
+    }
     if (ctx->st) cudaFree(ctx->st);
     delete ctx;
 }
@@ -1750,7 +1973,8 @@ gsnfs_status gsnfs_encode_frame(gsnfs_ctx *ctx, void *stream, const float *d_pos
 static gsnfs_status encode_batch_impl(gsnfs_ctx *ctx, void *stream, uint32_t frames, const float *const *h_pos,
                                       const float *const *h_attr, const uint64_t *h_n, const uint32_t *h_J,
                                       uint32_t rungs, const double *h_rung_scale, const gsnfs_quant *q,
-                                      uint8_t *d_out, uint64_t capacity, uint64_t *h_offsets, double *h_sq_err)
+                                      uint8_t *d_out, uint64_t capacity, uint64_t *h_offsets, double *h_sq_err,
+                                      uint8_t *h_headers = nullptr)
 {
     if (!ctx || frames < 1 || frames > (uint32_t)kMaxFrames || rungs < 1 || rungs > (uint32_t)kMaxRungs || !h_pos ||
         !h_n || !h_J || !d_out || !h_offsets)
@@ -1782,6 +2006,7 @@ static gsnfs_status encode_batch_impl(gsnfs_ctx *ctx, void *stream, uint32_t fra
     rq.capacity = capacity;
     rq.offsets.assign((size_t)frames * rungs + 1, 0);
     rq.dist = q->num_channels ? h_sq_err : nullptr;
+    rq.headers = h_headers;
     st = encode_impl(ctx, (cudaStream_t)stream, rq, false);
     if (st == GSNFS_OK)
         for (size_t i = 0; i < rq.offsets.size(); ++i) h_offsets[i] = rq.offsets[i];
@@ -1797,6 +2022,16 @@ gsnfs_status gsnfs_encode_batch(gsnfs_ctx *ctx, void *stream, uint32_t frames, c
 {
     return encode_batch_impl(ctx, stream, frames, h_pos, h_attr, h_n, h_J, rungs, h_rung_scale, q, d_out, capacity,
                              h_offsets, nullptr);
+}
+
+gsnfs_status gsnfs_encode_batch_headers(gsnfs_ctx *ctx, void *stream, uint32_t frames, const float *const *h_pos,
+                                        const float *const *h_attr, const uint64_t *h_n, const uint32_t *h_J,
+                                        uint32_t rungs, const double *h_rung_scale, const gsnfs_quant *q,
+                                        uint8_t *d_out, uint64_t capacity, uint64_t *h_offsets, uint8_t *h_headers)
+{
+    if (!h_headers) return GSNFS_ERR_INVALID_ARG;
+    return encode_batch_impl(ctx, stream, frames, h_pos, h_attr, h_n, h_J, rungs, h_rung_scale, q, d_out, capacity,
+                             h_offsets, nullptr, h_headers);
 }
 
 gsnfs_status gsnfs_encode_batch_rd(gsnfs_ctx *ctx, void *stream, uint32_t frames, const float *const *h_pos,
@@ -1853,51 +2088,29 @@ gsnfs_status gsnfs_decode_frame_lod(gsnfs_ctx *ctx, void *stream, const uint8_t 
     if (depth > J) return GSNFS_ERR_INVALID_ARG;
     *out_nodes = 0;
     if (nv == 0) return GSNFS_OK;
-    // scratch: full-depth attributes, flags, node offsets, node starts, scan partials
-    const int sms = ctx->num_sms;
-    auto carve = [&](Carve &cv, float **attr, uint32_t **flags, uint64_t **offs, uint64_t **starts,
-                     uint64_t **part) {
-        *attr = cv.take<float>(nv * (C ? C : 1) + 4);
-        *flags = cv.take<uint32_t>(nv + 1);
-        *offs = cv.take<uint64_t>(nv + 2);
-        *starts = cv.take<uint64_t>(nv + 2);
-        *part = cv.take<uint64_t>(scan_partial_words(nv, sms) + 1);
-        return cv.off;
-    };
-    float *attr;
-    uint32_t *flags;
-    uint64_t *offs, *starts, *part;
-    Carve m(nullptr);
-    const size_t need = carve(m, &attr, &flags, &offs, &starts, &part);
-    if (need > ctx->lod_cap) {
-        if (ctx->lod) CK(cudaFree(ctx->lod));
-        ctx->lod = nullptr;
-        ctx->lod_cap = 0;
-        CK(cudaMalloc(&ctx->lod, need));
-        ctx->lod_cap = need;
+    if (depth == J) {  // the nodes are the voxels: the plain decode
+        uint64_t n = 0;
+        st = decode_impl(ctx, s, d_bitstream, bytes, d_pos, d_attr, capacity_nodes, &n);
+        *out_nodes = n;
+        return st;
     }
-    Carve cv(ctx->lod);
-    carve(cv, &attr, &flags, &offs, &starts, &part);
-    const uint64_t *codes = nullptr;
-    uint64_t nv2 = 0;
-    st = decode_impl(ctx, s, d_bitstream, bytes, nullptr, C && d_attr ? attr : nullptr, nv, &nv2, &codes);
-    if (st) return st;
-    const uint32_t sh = 3 * (J - depth);
-    launch_lod_index(codes, nv, sh, flags, offs, part, starts, sms, s);
-    uint64_t n_nodes = 0;
-    CK(cudaMemcpyAsync(&n_nodes, offs + nv, 8, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    *out_nodes = n_nodes;
-    if (n_nodes > capacity_nodes) return GSNFS_ERR_CAPACITY;
-    LodGrid g;
-    double ext;
-    memcpy(&ext, h + 56, 8);
-    for (int a = 0; a < 3; ++a) memcpy(&g.lo[a], h + 32 + 8 * a, 8);
-    g.cell = ext / std::ldexp(1.0, (int)depth);
-    launch_lod_nodes(codes, starts, offs, nv, n_nodes, sh, depth, C, attr, g, d_pos, C ? d_attr : nullptr, sms, s);
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(s));
-    return GSNFS_OK;
+    LodReq r{depth, d_pos, d_attr, capacity_nodes, out_nodes};
+    uint64_t n = 0;
+    return decode_impl(ctx, s, d_bitstream, bytes, nullptr, d_attr, ~0ull, &n, nullptr, &r);
+}
+
+gsnfs_status gsnfs_decode_batch_async(gsnfs_ctx *ctx, void *stream, uint32_t frames, const uint8_t *d_in,
+                                      const uint64_t *h_in_offsets, const uint8_t *h_headers, float *d_pos,
+                                      float *d_attr, uint64_t capacity_rows, uint64_t *h_out_rows, uint32_t *status)
+{
+    if (!ctx || !d_in || !h_in_offsets || !h_out_rows || !status || frames == 0 || frames > (uint32_t)kMaxFrames)
+        return GSNFS_ERR_INVALID_ARG;
+    for (uint32_t f = 0; f < frames; ++f)
+        if (h_in_offsets[f + 1] < h_in_offsets[f] || (h_in_offsets[f] % 8)) return GSNFS_ERR_INVALID_ARG;
+    if ((uintptr_t)d_in % 8 || (uintptr_t)d_attr % 16 || (uintptr_t)status % 4) return GSNFS_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    return decode_batch_impl(ctx, (cudaStream_t)stream, frames, d_in, h_in_offsets, d_pos, d_attr, capacity_rows,
+                             h_out_rows, h_headers, status);
 }
 
 gsnfs_status gsnfs_decode_batch(gsnfs_ctx *ctx, void *stream, uint32_t frames, const uint8_t *d_in,

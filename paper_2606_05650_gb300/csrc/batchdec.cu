@@ -123,19 +123,61 @@ __global__ void roots_kernel(const DecFrame *fr, uint32_t F, uint64_t *nodes, ui
     (void)codes;
 }
 
-// one level d of Algorithm 3 for every frame with J > d; a thread's nodes
-// mostly stay in one frame, so the frame's tables are looked up once per change
-__global__ void __launch_bounds__(256) expand_batch_kernel(const DecFrame *fr, uint32_t F, uint32_t d,
+// Levels d .. d + K (K <= 2) of Algorithm 3 for every frame with J > d in one
+// launch: a thread takes one node of level d and walks its descendants depth
+// first down to level min(d + K, J) (children in increasing bit order, so
+// every level's nodes are visited in their breadth-first order), writing only
+// that last level; the level in between is never stored.  K = 2 only where
+// the second level holds at most 4 nodes per node of the first (chosen on the
+// host): longer walks were measured slower (a thread's chain of dependent
+// loads and the divergence of uneven subtrees outweigh the saved traffic).
+// A thread's nodes mostly stay in one frame, so the frame's tables are looked
+// up once per change.
+constexpr int kExpandMaxLevels = 2;
+
+struct ExpandFrame {
+    const uint64_t *src;                    // level d codes
+    uint64_t *dst;                          // last level's codes
+    uint64_t bo[kExpandMaxLevels];          // byte offset of level d + k in the batch occupancy buffer
+    uint32_t base[kExpandMaxLevels];        // popcount prefix at the start of level d + k
+    uint32_t M[kExpandMaxLevels + 1];       // node count of level d + k
+    int levels;                             // levels walked: min(K, J - d)
+};
+
+template <int k>
+__device__ __forceinline__ void expand_walk(const ExpandFrame &x, const uint8_t *__restrict__ occ,
+                                            const uint32_t *__restrict__ pref, uint64_t code, uint32_t w,
+                                            DevState *st)
+{
+    // node w of level d + k, with its code
+    if (k == x.levels) {
+        x.dst[w] = code;
+        return;
+    }
+    if constexpr (k < kExpandMaxLevels) {
+        const uint32_t byte = occ[x.bo[k] + w];
+        if (byte == 0) {
+            set_error(&st->err, kErrCorrupt);
+            return;
+        }
+        const uint64_t c = code << 3;
+        uint32_t cw = pref[x.bo[k] + w] - x.base[k];
+        for (uint32_t bits = byte; bits; bits &= bits - 1u) {  // set bits in increasing order
+            if (cw < x.M[k + 1]) expand_walk<k + 1>(x, occ, pref, c + (uint32_t)(__ffs(bits) - 1), cw, st);
+            else set_error(&st->err, kErrCorrupt);
+            ++cw;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) expand_batch_kernel(const DecFrame *fr, uint32_t F, uint32_t d, uint32_t K,
                                                            const uint64_t *lvl_pref, uint64_t count,
                                                            const uint8_t *__restrict__ occ_all,
                                                            const uint32_t *__restrict__ pref, uint64_t *nodes,
                                                            uint64_t *codes, DevState *st)
 {
     uint64_t fbeg = 1, fend = 0;  // node range of the cached frame (empty at first)
-    uint32_t Md1 = 0, base = 0;
-    uint64_t bo = 0;
-    const uint64_t *src = nullptr;
-    uint64_t *dst = nullptr;
+    ExpandFrame x;
     for (uint64_t gp = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; gp < count;
          gp += (uint64_t)gridDim.x * blockDim.x) {
         if (gp < fbeg || gp >= fend) {
@@ -143,25 +185,24 @@ __global__ void __launch_bounds__(256) expand_batch_kernel(const DecFrame *fr, u
             const DecFrame &fd = fr[f];
             fbeg = lvl_pref[f];
             fend = lvl_pref[f + 1];
-            Md1 = fd.lsz[d + 1];
-            bo = fd.occ_off + fd.boff[d];
-            base = pref[bo];
-            src = nodes + fd.noff[d];
-            dst = (d + 1 == fd.J) ? codes + fd.vstart : nodes + fd.noff[d + 1];
-            if (gp == fbeg && pref[bo + fd.lsz[d]] - base != Md1) set_error(&st->err, kErrCorrupt);
+            x.levels = (int)min(K, fd.J - d);
+            x.src = nodes + fd.noff[d];
+            x.dst = (d + (uint32_t)x.levels == fd.J) ? codes + fd.vstart : nodes + fd.noff[d + x.levels];
+            x.M[0] = fd.lsz[d];
+#pragma unroll
+            for (int k = 0; k < kExpandMaxLevels; ++k) {
+                if (k < x.levels) {
+                    x.bo[k] = fd.occ_off + fd.boff[d + k];
+                    x.base[k] = pref[x.bo[k]];
+                    x.M[k + 1] = fd.lsz[d + k + 1];
+                    // the popcounts of level d + k add up to the size of level d + k + 1
+                    if (gp == fbeg && pref[x.bo[k] + x.M[k]] - x.base[k] != x.M[k + 1])
+                        set_error(&st->err, kErrCorrupt);
+                }
+            }
         }
         const uint32_t p = (uint32_t)(gp - fbeg);
-        const uint32_t byte = occ_all[bo + p];
-        if (byte == 0) {
-            set_error(&st->err, kErrCorrupt);
-            continue;
-        }
-        const uint64_t c = src[p] << 3;
-        uint32_t w = pref[bo + p] - base;
-        for (uint32_t bits = byte; bits; bits &= bits - 1u) {  // set bits in increasing order
-            if (w < Md1) dst[w] = c + (uint32_t)(__ffs(bits) - 1);
-            ++w;
-        }
+        expand_walk<0>(x, occ_all, pref, x.src[p], p, st);
     }
 }
 
@@ -275,12 +316,13 @@ void launch_batch_roots(const DecFrame *fr, uint32_t F, uint64_t *nodes, uint64_
     count_launch();
 }
 
-void launch_batch_expand(const DecFrame *fr, uint32_t F, uint32_t d, const uint64_t *lvl_pref, uint64_t count,
+void launch_batch_expand(const DecFrame *fr, uint32_t F, uint32_t d, uint32_t K, const uint64_t *lvl_pref,
+                         uint64_t count,
                          const uint8_t *occ_all, const uint32_t *pref, uint64_t *nodes, uint64_t *codes,
                          DevState *st, int num_sms, cudaStream_t s)
 {
     if (count == 0) return;
-    expand_batch_kernel<<<grid_for(count, num_sms), 256, 0, s>>>(fr, F, d, lvl_pref, count, occ_all, pref, nodes,
+    expand_batch_kernel<<<grid_for(count, num_sms), 256, 0, s>>>(fr, F, d, K, lvl_pref, count, occ_all, pref, nodes,
                                                                  codes, st);
     count_launch();
 }
@@ -311,4 +353,8 @@ void launch_batch_block_tables(const DecFrame *fr, uint32_t F, const uint64_t *b
     count_launch();
 }
 
+}  // namespace gsnfs
+
+namespace gsnfs {
+uint32_t batch_expand_max_levels() { return (uint32_t)kExpandMaxLevels; }
 }  // namespace gsnfs

@@ -129,6 +129,12 @@ struct RahtPlanDev {  // device pointers of a plan
     uint32_t *tile_carry;  // per tile carried count, then exclusive base
     RahtPass *passes;      // kRahtMaxPasses
     uint32_t *npasses;     // device counter
+    // pass 0 elements: first voxel and one past the last voxel of element j, or null when element j is voxel j
+    // (a coarser sequence: the nodes of an octree depth, each a run of voxels, for level-of-detail decoding)
+    const uint32_t *pos0;
+    const uint32_t *end0;
+    uint32_t *pipe_ctr;    // 2 words: tiles claimed and CTAs finished in the pipelined first transform pass
+                           // (zeroed by the prelude; the last CTA of every launch puts them back to zero)
 };
 
 uint32_t raht_tile_size(uint32_t C);
@@ -271,7 +277,10 @@ void launch_batch_rans_decode(const DecFrame *fr, uint32_t F, uint32_t max_chunk
                               uint8_t *occ_all, uint32_t *tabs, DevState *st, cudaStream_t s);
 void launch_popc_scan(const uint8_t *occ, uint64_t n, uint32_t *pref, uint32_t *partials, int num_sms,
                       cudaStream_t s);
-void launch_batch_expand(const DecFrame *fr, uint32_t F, uint32_t d, const uint64_t *lvl_pref, uint64_t count,
+// levels d .. d + K (K <= batch_expand_max_levels()) of every frame with J > d in one launch; only the last
+// level's codes are written
+uint32_t batch_expand_max_levels();
+void launch_batch_expand(const DecFrame *fr, uint32_t F, uint32_t d, uint32_t K, const uint64_t *lvl_pref, uint64_t count,
                          const uint8_t *occ_all, const uint32_t *pref, uint64_t *nodes, uint64_t *codes,
                          DevState *st, int num_sms, cudaStream_t s);
 void launch_batch_roots(const DecFrame *fr, uint32_t F, uint64_t *nodes, uint64_t *codes, cudaStream_t s);
@@ -295,9 +304,15 @@ struct LodGrid {
 // node count) and the first voxel of each node (starts[n] = nv)
 void launch_lod_index(const uint64_t *codes, uint64_t nv, uint32_t sh, uint32_t *flags, uint64_t *offs,
                       uint64_t *partials, uint64_t *starts, int num_sms, cudaStream_t s);
-void launch_lod_nodes(const uint64_t *codes, const uint64_t *starts, const uint64_t *offs, uint64_t nv,
-                      uint64_t n_nodes, uint32_t sh, uint32_t Jp, uint32_t C, const float *attr, const LodGrid &g,
-                      float *pos, float *out, int num_sms, cudaStream_t s);
+// The nodes of a depth as the first pass of a coarser RAHT sequence (pos0, end0, gap0 of n_nodes + 1 entries), and
+// the node means from their low-pass coefficients after the coarse inverse (n_nodes: a bound for the launch
+// shape; the count itself is read on the device).
+void launch_lod_sequence(const uint64_t *starts, const uint64_t *n_nodes_dev, uint64_t nv, uint64_t n_nodes,
+                         const uint8_t *gap, uint32_t *pos0, uint32_t *end0, uint8_t *gap0, int num_sms,
+                         cudaStream_t s);
+void launch_lod_means(const float *low, const uint64_t *codes, const uint64_t *starts, const uint64_t *n_nodes_dev,
+                      uint64_t n_nodes, uint32_t sh, uint32_t Jp, uint32_t C, const LodGrid &g, float *pos, float *out,
+                      int num_sms, cudaStream_t s);
 
 // ---- render.cu: splat rasteriser ------------------------------------------------
 struct RenderCam {  // camera in FP64: the per-Gaussian projection is evaluated in FP64

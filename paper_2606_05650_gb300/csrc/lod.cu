@@ -1,8 +1,10 @@
-// Level of detail: a decoded frame reduced to the nodes of octree depth Jp
+// Level of detail: a frame decoded to the nodes of octree depth Jp
 // (Algorithm 2's shift read as J - Jp).  A node is the run of voxels sharing
 // code >> 3(J - Jp); it is placed at the centre of its cell at depth Jp and
 // carries the mean of its voxels' decoded attributes, which by Eq. (1) is
-// its RAHT low-pass coefficient divided by sqrt(voxel count).
+// its RAHT low-pass coefficient divided by sqrt(voxel count).  The low-pass
+// coefficients come from an inverse RAHT over the node sequence (the
+// butterflies inside nodes are never applied).
 #include "kernels.cuh"
 
 namespace gsnfs {
@@ -23,33 +25,51 @@ __global__ void lod_starts_kernel(const uint32_t *__restrict__ flags, const uint
     if (blockIdx.x == 0 && threadIdx.x == 0) starts[offs[nv]] = nv;
 }
 
-// thread per (node, channel): FP64 mean over the node's voxels in voxel order;
-// channel 0's thread also writes the node centre
-__global__ void lod_nodes_kernel(const uint64_t *__restrict__ codes, const uint64_t *__restrict__ starts,
-                                 const uint64_t *__restrict__ offs, uint64_t nv, uint32_t sh, uint32_t Jp,
-                                 uint32_t C, const float *__restrict__ attr, LodGrid g, float *pos, float *out)
+// The nodes as the first pass of a coarser RAHT sequence: element k covers
+// voxels [starts[k], starts[k + 1]) and follows a gap of the voxel sequence
+// (the gap before its first voxel, above the depth's level, or a frame edge);
+// sentinels after the last node.
+__global__ void lod_sequence_kernel(const uint64_t *__restrict__ starts, const uint64_t *__restrict__ n_nodes_dev,
+                                    uint64_t nv, const uint8_t *__restrict__ gap, uint32_t *pos0, uint32_t *end0,
+                                    uint8_t *gap0)
 {
-    const uint64_t nn = offs[nv];
-    const uint32_t Cw = C ? C : 1;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn * Cw;
-         t += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t k = t / Cw;
-        const uint32_t c = (uint32_t)(t - k * Cw);
-        const uint64_t b = starts[k], e = starts[k + 1];
-        if (C && out) {
-            double sum = 0.0;
-            for (uint64_t i = b; i < e; ++i) sum = __dadd_rn(sum, (double)attr[i * C + c]);
-            out[k * C + c] = (float)__ddiv_rn(sum, (double)(e - b));
+    const uint64_t nn = *n_nodes_dev;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= nn; k += (uint64_t)gridDim.x * blockDim.x) {
+        if (k < nn) {
+            const uint64_t b = starts[k];
+            pos0[k] = (uint32_t)b;
+            end0[k] = (uint32_t)starts[k + 1];
+            gap0[k] = k == 0 ? (uint8_t)kInfLevel : gap[b];
+        } else {
+            pos0[k] = (uint32_t)nv;
+            gap0[k] = (uint8_t)kInfLevel;
         }
-        if (c == 0 && pos) {
+    }
+}
+
+// block (channels, nodes): thread (c, k) divides node k's low-pass
+// coefficient of channel c from the coarse inverse by sqrt(voxel count) (Eq. 1:
+// the low pass of a node is sqrt(w) times the mean of its voxels); threads
+// c < 3 of a node write its centre coordinate c.  No index division: node rows
+// are whole block rows.
+__global__ void lod_means_kernel(const float *__restrict__ low, const uint64_t *__restrict__ codes,
+                                 const uint64_t *__restrict__ starts, const uint64_t *__restrict__ n_nodes_dev,
+                                 uint32_t sh, uint32_t Jp, uint32_t C, LodGrid g, float *pos, float *out)
+{
+    const uint32_t c = threadIdx.x;
+    const uint64_t nn = *n_nodes_dev;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.y + threadIdx.y; k < nn; k += (uint64_t)gridDim.x * blockDim.y) {
+        const uint64_t b = starts[k];
+        if (out && c < C) {
+            const float w = (float)(starts[k + 1] - b);
+            out[k * C + c] = __fdiv_rn(low[k * C + c], __fsqrt_rn(w));
+        }
+        if (pos && c < 3) {
             const uint64_t m = codes[b] >> sh;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                uint32_t v = 0;
-                for (uint32_t bit = 0; bit < Jp; ++bit) v |= (uint32_t)((m >> (3 * bit + a)) & 1u) << bit;
-                const double off = __dmul_rn(__dadd_rn((double)v, 0.5), g.cell);
-                pos[3 * k + a] = (float)__dadd_rn(g.lo[a], off);
-            }
+            uint32_t v = 0;
+            for (uint32_t bit = 0; bit < Jp; ++bit) v |= (uint32_t)((m >> (3 * bit + c)) & 1u) << bit;
+            const double off = __dmul_rn(__dadd_rn((double)v, 0.5), g.cell);
+            pos[3 * k + c] = (float)__dadd_rn(g.lo[c], off);
         }
     }
 }
@@ -73,12 +93,31 @@ void launch_lod_index(const uint64_t *codes, uint64_t nv, uint32_t sh, uint32_t 
     count_launch();
 }
 
-void launch_lod_nodes(const uint64_t *codes, const uint64_t *starts, const uint64_t *offs, uint64_t nv,
-                      uint64_t n_nodes, uint32_t sh, uint32_t Jp, uint32_t C, const float *attr, const LodGrid &g,
-                      float *pos, float *out, int num_sms, cudaStream_t s)
+
+}  // namespace gsnfs
+
+namespace gsnfs {
+
+void launch_lod_sequence(const uint64_t *starts, const uint64_t *n_nodes_dev, uint64_t nv, uint64_t n_nodes,
+                         const uint8_t *gap, uint32_t *pos0, uint32_t *end0, uint8_t *gap0, int num_sms,
+                         cudaStream_t s)
 {
-    lod_nodes_kernel<<<lod_grid(n_nodes * (C ? C : 1), num_sms), 256, 0, s>>>(codes, starts, offs, nv, sh, Jp, C,
-                                                                               attr, g, pos, out);
+    lod_sequence_kernel<<<lod_grid(n_nodes + 1, num_sms), 256, 0, s>>>(starts, n_nodes_dev, nv, gap, pos0, end0, gap0);
+    count_launch();
+}
+
+void launch_lod_means(const float *low, const uint64_t *codes, const uint64_t *starts, const uint64_t *n_nodes_dev,
+                      uint64_t n_nodes, uint32_t sh, uint32_t Jp, uint32_t C, const LodGrid &g, float *pos, float *out,
+                      int num_sms, cudaStream_t s)
+{
+    const uint32_t cw = C > 3 ? C : 3;                        // threads per node row
+    const uint32_t ny = cw >= 256 ? 1u : 256u / cw;               // node rows per block
+    uint64_t blocks = (n_nodes + ny - 1) / ny;
+    const uint64_t cap = (uint64_t)num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    lod_means_kernel<<<(uint32_t)blocks, dim3(cw, ny), 0, s>>>(low, codes, starts, n_nodes_dev, sh, Jp, C, g, pos,
+                                                               out);
     count_launch();
 }
 

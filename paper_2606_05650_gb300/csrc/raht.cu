@@ -45,7 +45,7 @@ struct PreludeArgs {
 
 __device__ __forceinline__ uint32_t seq_pos(const RahtPlanDev &p, const RahtPass &ps, int q, uint64_t j)
 {
-    return q == 0 ? (uint32_t)j : p.pos[ps.seq_off + j];
+    return q == 0 ? (p.pos0 ? p.pos0[j] : (uint32_t)j) : p.pos[ps.seq_off + j];
 }
 
 __device__ __forceinline__ uint8_t seq_gap(const PreludeArgs &a, const RahtPass &ps, int q, uint64_t j)
@@ -56,7 +56,7 @@ __device__ __forceinline__ uint8_t seq_gap(const PreludeArgs &a, const RahtPass 
 // one past the last voxel covered by element j (its subtree is contiguous)
 __device__ __forceinline__ uint32_t seq_end(const RahtPlanDev &p, const RahtPass &ps, int q, uint64_t j)
 {
-    return q == 0 ? (uint32_t)(j + 1) : p.endseq[ps.seq_off + j];
+    return q == 0 ? (p.end0 ? p.end0[j] : (uint32_t)(j + 1)) : p.endseq[ps.seq_off + j];
 }
 
 constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
@@ -247,6 +247,8 @@ __global__ void __launch_bounds__(kThreads) prelude_init_kernel(RahtPlanDev p, c
         p.passes[0] = ps;
         for (int q = 1; q <= kRahtMaxPasses; ++q) p.passes[q] = RahtPass{};
         *p.npasses = n ? 1u : 0u;
+        p.pipe_ctr[0] = 0;
+        p.pipe_ctr[1] = 0;
     }
 }
 
@@ -300,14 +302,24 @@ __device__ void prelude_compact_body(const PreludeArgs &a, int q, uint64_t first
     const RahtPlanDev &p = a.p;
     const RahtPass ps = p.passes[q];
     const RahtPass nx = p.passes[q + 1];
-    for (uint64_t j = first; j < ps.n; j += stride) {
-        uint32_t d = p.dest[ps.seq_off + j];
-        if (d & kCarry) {
-            uint32_t gi = p.tile_carry[ps.tile_off + (uint32_t)(j / p.T)] + (d & ~kCarry);
-            p.dest[ps.seq_off + j] = kCarry | gi;
-            p.pos[nx.seq_off + gi] = seq_pos(p, ps, q, j);
-            p.gapseq[nx.seq_off + gi] = seq_gap(a, ps, q, j);
-            p.endseq[nx.seq_off + gi] = p.send[ps.seq_off + j];
+    constexpr int U = 4;  // elements per thread in flight (their loads are independent)
+    for (uint64_t j0 = first; j0 < ps.n; j0 += U * stride) {
+        uint32_t d[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t j = j0 + u * stride;
+            d[u] = j < ps.n ? p.dest[ps.seq_off + j] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t j = j0 + u * stride;
+            if (j < ps.n && (d[u] & kCarry)) {
+                uint32_t gi = p.tile_carry[ps.tile_off + (uint32_t)(j / p.T)] + (d[u] & ~kCarry);
+                p.dest[ps.seq_off + j] = kCarry | gi;
+                p.pos[nx.seq_off + gi] = seq_pos(p, ps, q, j);
+                p.gapseq[nx.seq_off + gi] = seq_gap(a, ps, q, j);
+                p.endseq[nx.seq_off + gi] = p.send[ps.seq_off + j];
+            }
         }
     }
     if (first == 0 && nx.n) {
@@ -1074,7 +1086,49 @@ __global__ void __launch_bounds__(kXThreads, NR == 1 ? 3 : 1) xform_pipe_kernel(
     auto rows = [&](uint32_t k) { return reinterpret_cast<float *>(smem_raw + (size_t)(k % NR) * rowb); };
     auto meta = [&](uint32_t k) { return pipe_stage(smem_raw + NR * rowb + (size_t)(k % NM) * metab, T); };
     uint32_t klt_fr = 0xFFFFFFFFu;
-    // prologue: metadata of tiles 0 .. NR - 1 (NR = 1: 0 and 1), then the rows of tiles 0 .. NR - 2 (NR = 1: 0)
+    if constexpr (NR == 1) {
+        // Tiles are claimed from a global counter as the CTA goes (the next but one while the current one is
+        // transformed), so a CTA that starts late or runs slow (its SM shared with other work) takes fewer
+        // tiles; the claims ascend, so a claim past the last tile ends the CTA's loop.
+        __shared__ uint32_t s_claim[4];
+        if (threadIdx.x == 0) {
+            s_claim[0] = atomicAdd(A.p.pipe_ctr, 1u);
+            s_claim[1] = atomicAdd(A.p.pipe_ctr, 1u);
+        }
+        __syncthreads();
+        if (s_claim[0] < nt) pipe_issue_meta<GATHER>(A, ps, s_claim[0], meta(0));
+        if (s_claim[1] < nt) pipe_issue_meta<GATHER>(A, ps, s_claim[1], meta(1));
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        if (s_claim[0] < nt) pipe_issue_rows<INV, GATHER>(A, ps, nx, s_claim[0], meta(0), rows(0));
+        cp_async_commit();
+        for (uint32_t k = 0;; ++k) {
+            const uint32_t tk = s_claim[k & 3];
+            if (tk >= nt) break;
+            // complete: rows of tile k, metadata of tile k + 1
+            cp_async_wait<0>();
+            __syncthreads();
+            pipe_compute<INV, GATHER, QDQ>(A, ps, nx, tk, meta(k), rows(k), klt_s, klt_fr);
+            if (threadIdx.x == 0) s_claim[(k + 2) & 3] = atomicAdd(A.p.pipe_ctr, 1u);
+            __syncthreads();  // the row buffer and tile k's metadata are free; the new claim is visible
+            const uint32_t t1 = s_claim[(k + 1) & 3], t2 = s_claim[(k + 2) & 3];
+            if (t2 < nt) pipe_issue_meta<GATHER>(A, ps, t2, meta(k + 2));
+            if (t1 < nt) pipe_issue_rows<INV, GATHER>(A, ps, nx, t1, meta(k + 1), rows(k + 1));
+            cp_async_commit();
+        }
+        cp_async_wait<0>();
+        if (threadIdx.x == 0) {  // the last CTA to finish leaves the counters at zero for the next launch
+            __threadfence();
+            if (atomicAdd(A.p.pipe_ctr + 1, 1u) == gridDim.x - 1) {
+                A.p.pipe_ctr[0] = 0;
+                A.p.pipe_ctr[1] = 0;
+                __threadfence();
+            }
+        }
+        return;
+    }
+    // prologue: metadata of tiles 0 .. NR - 1, then the rows of tiles 0 .. NR - 2
     constexpr uint32_t kMeta0 = NR == 1 ? 2u : NR, kRows0 = NR == 1 ? 1u : NR - 1;
     for (uint32_t k = 0; k < kMeta0 && k < cnt; ++k) pipe_issue_meta<GATHER>(A, ps, b + k * G, meta(k));
     cp_async_commit();
@@ -1086,14 +1140,7 @@ __global__ void __launch_bounds__(kXThreads, NR == 1 ? 3 : 1) xform_pipe_kernel(
     }
     for (uint32_t k = 0; k < cnt; ++k) {
         if constexpr (NR == 1) {
-            // complete: rows of tile k, metadata of tile k + 1
-            cp_async_wait<0>();
-            __syncthreads();
-            pipe_compute<INV, GATHER, QDQ>(A, ps, nx, b + k * G, meta(k), rows(k), klt_s, klt_fr);
-            __syncthreads();  // the row buffer and tile k's metadata are free
-            if (k + 2 < cnt) pipe_issue_meta<GATHER>(A, ps, b + (k + 2) * G, meta(k + 2));
-            if (k + 1 < cnt) pipe_issue_rows<INV, GATHER>(A, ps, nx, b + (k + 1) * G, meta(k + 1), rows(k + 1));
-            cp_async_commit();
+            break;  // tiles are claimed dynamically below
         } else {
             // complete: rows of tile k, metadata of tile k + NR - 1 (only the rows of k + NR - 2 may still fly)
             cp_async_wait<1>();
@@ -1367,8 +1414,18 @@ __global__ void __launch_bounds__(256) frame_centres_kernel(const float *const *
     const uint32_t m = (uint32_t)(n < kCentreRows ? n : kCentreRows);
     const float *a = attr[f];
     float sum = 0.f;
-    if (j < lanes)
-        for (uint32_t r = j; r < m; r += lanes) sum = __fadd_rn(sum, a[(uint64_t)r * C + c]);
+    if (j < lanes) {  // rows j, j + lanes, ... added in that order; 16 loads in flight at a time
+        constexpr uint32_t kAhead = 16;
+        uint32_t r = j;
+        for (; r + (kAhead - 1) * lanes < m; r += kAhead * lanes) {
+            float x[kAhead];
+#pragma unroll
+            for (uint32_t u = 0; u < kAhead; ++u) x[u] = __ldg(a + (uint64_t)(r + u * lanes) * C + c);
+#pragma unroll
+            for (uint32_t u = 0; u < kAhead; ++u) sum = __fadd_rn(sum, x[u]);
+        }
+        for (; r < m; r += lanes) sum = __fadd_rn(sum, a[(uint64_t)r * C + c]);
+    }
     if (j < lanes) part[t] = sum;
     __syncthreads();
     if (j == 0) {

@@ -64,6 +64,8 @@ def lib():
                 "gsnfs_encode_batch": ([p, p, u32, p, p, p, p, u32, p, Q, p, u64, p], i32),
                 "gsnfs_encode_batch_rd": ([p, p, u32, p, p, p, p, u32, p, Q, p, u64, p, p], i32),
                 "gsnfs_decode_batch": ([p, p, u32, p, p, p, p, u64, p], i32),
+                "gsnfs_encode_batch_headers": ([p, p, u32, p, p, p, p, u32, p, Q, p, u64, p, p], i32),
+                "gsnfs_decode_batch_async": ([p, p, u32, p, p, p, p, p, u64, p, p], i32),
                 "gsnfs_decode_frame_lod": ([p, p, p, u64, u32, p, p, u64, P64], i32),
                 "gsnfs_render": ([p, p, p, p, u64, ct.POINTER(Camera), p], i32),
                 "gsnfs_voxelize": ([p, p, p, u64, u32, p, p, P64], i32),
@@ -251,9 +253,17 @@ def decode_frame(bitstream: torch.Tensor, with_attr=True):
     return pos[:m], (attr[:m, :C] if attr is not None else None)
 
 
-def encode_batch(pos_list, attr_list, J_list, rung_scales, qp: QuantParams, out=None, distortion=False):
+HEADER_RECORD_BYTES = 4224  # GSNFS_HEADER_RECORD_BYTES
+
+
+def encode_batch(pos_list, attr_list, J_list, rung_scales, qp: QuantParams, out=None, distortion=False,
+                 headers=False):
     """gsnfs_encode_batch: frames x rungs.  Returns (out uint8 tensor, offsets np.uint64[F*R+1]); with
-    distortion=True (gsnfs_encode_batch_rd) also the squared-error sums np.float64[F, R, C]."""
+    distortion=True (gsnfs_encode_batch_rd) also the squared-error sums np.float64[F, R, C]; with headers=True
+    (gsnfs_encode_batch_headers) also the streams' header records np.uint8[F*R, HEADER_RECORD_BYTES] for
+    decode_batch_async."""
+    if distortion and headers:
+        raise ValueError("distortion and headers are separate calls")
     F = len(pos_list)
     R = len(rung_scales)
     dev = pos_list[0].device
@@ -276,8 +286,12 @@ def encode_batch(pos_list, attr_list, J_list, rung_scales, qp: QuantParams, out=
     offs = (ct.c_uint64 * (F * R + 1))()
     q = qp.struct()
     dist = np.zeros((F, R, max(C, 1)), dtype=np.float64) if distortion else None
+    hdr = np.zeros((F * R, HEADER_RECORD_BYTES), dtype=np.uint8) if headers else None
 
     def call(buf):
+        if headers:
+            return lib().gsnfs_encode_batch_headers(context(dev), _stream(buf), F, hp, ha, hn, hJ, R, hs, ct.byref(q),
+                                                    _ptr(buf), buf.numel(), offs, hdr.ctypes.data_as(ct.c_void_p))
         if distortion:
             return lib().gsnfs_encode_batch_rd(context(dev), _stream(buf), F, hp, ha, hn, hJ, R, hs, ct.byref(q),
                                                _ptr(buf), buf.numel(), offs,
@@ -292,6 +306,8 @@ def encode_batch(pos_list, attr_list, J_list, rung_scales, qp: QuantParams, out=
     _check(rc, "gsnfs_encode_batch")
     if distortion:
         return out, np.array(offs[:], dtype=np.uint64), dist[:, :, :C]
+    if headers:
+        return out, np.array(offs[:], dtype=np.uint64), hdr
     return out, np.array(offs[:], dtype=np.uint64)
 
 
@@ -366,6 +382,31 @@ def decode_batch(data: torch.Tensor, offsets, C: int, rows_cap: int, pos_out: to
     r = np.array(rows[:], dtype=np.uint64)
     n = int(r[-1])
     return pos[:n], (attr[:n, :C] if attr is not None else None), r
+
+
+def decode_batch_async(data: torch.Tensor, offsets, headers, C: int, rows_cap: int, pos_out: torch.Tensor,
+                       attr_out: torch.Tensor | None, status: torch.Tensor):
+    """gsnfs_decode_batch_async: decode_batch given the streams' header records (np.uint8[F, HEADER_RECORD_BYTES]
+    from encode_batch(..., headers=True)); enqueues the decode on the current stream and returns at once.
+    status: an int32 tensor of one element (device, or pinned host memory) receiving the device status once the
+    stream reaches the end of the decode (0 = ok).  Returns the row offsets (np.uint64[F+1])."""
+    F = len(offsets) - 1
+    hin = (ct.c_uint64 * (F + 1))(*[int(o) for o in offsets])
+    rows = (ct.c_uint64 * (F + 1))()
+    hdr = np.ascontiguousarray(headers, dtype=np.uint8)
+    if hdr.shape != (F, HEADER_RECORD_BYTES):
+        raise ValueError("headers must be uint8 [frames, HEADER_RECORD_BYTES]")
+    for t, cols in ((pos_out, 3), (attr_out, C)):
+        if t is not None and (t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != (max(rows_cap, 1),
+                                                                                                      cols)):
+            raise ValueError("outputs must be contiguous float32 [rows_cap, 3] and [rows_cap, C] tensors")
+    if status.dtype != torch.int32 or status.numel() != 1:
+        raise ValueError("status must be a one-element int32 tensor")
+    _check(lib().gsnfs_decode_batch_async(context(data.device), _stream(data), F, _ptr(data), hin,
+                                          hdr.ctypes.data_as(ct.c_void_p), _ptr(pos_out),
+                                          _ptr(attr_out) if C else ct.c_void_p(0), rows_cap, rows,
+                                          ct.c_void_p(status.data_ptr())), "gsnfs_decode_batch_async")
+    return np.array(rows[:], dtype=np.uint64)
 
 
 # ---- stage entry points ---------------------------------------------------
