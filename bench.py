@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--frames", type=int, default=N_FRAMES, help="frames per rank per step")
     ap.add_argument("--block", type=int, default=512, help="RLGR block size")
     ap.add_argument("--no-extras", action="store_true", help="skip plain-path, e2e and CPU-baseline legs")
+    ap.add_argument("--no-tune", action="store_true", help="built-in launch shapes instead of autotuning them "
+                                                            "(short profiling runs)")
     ap.add_argument("--workload", default="headline", choices=["headline", "ladder", "sequence", "pointcloud",
                                                                  "blocksweep"],
                     help="other workloads, each printing its own JSON line: ladder (64 frames of 50k-2M Gaussians x "
@@ -270,7 +272,8 @@ def run_gpu(args):
 
     # launch shapes tuned on this workload (outputs checked identical for every candidate)
     from paper_2606_05650_gb300 import autotune
-    tuning = autotune.tune_round_trip(P, A, Js, qp, use_cache=False)
+    tuning = ({"params": "built-in", "ms": None, "default_ms": None} if args.no_tune else
+              autotune.tune_round_trip(P, A, Js, qp, use_cache=False))
     for _ in range(max(args.warmup, 1)):
         offs, rows = step()
     torch.cuda.synchronize()
@@ -559,72 +562,127 @@ def gpu_extras(args, G, torch, P, A, frames, qp, out, offs, dev, stream):
     for _ in range(K2):
         n, m = e2e_step()
     dt_serial = (time.perf_counter() - t0) / K2
-    # streaming: step k+1's inputs go up and step k-1's results come down while step k is coded
-    # (copy engines and SMs busy at once; every step still carries its own copies both ways)
-    s_in, s_cmp, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    dp2 = [dp, [torch.empty_like(x) for x in dp]]
-    da2 = [da, [torch.empty_like(x) for x in da]]
-    out2 = [out, torch.empty_like(out)]
-    pos2 = [pos1, torch.empty((F * N_GAUSS, 3), dtype=torch.float32, device=dev)]
-    att2 = [att1, torch.empty((F * N_GAUSS, C), dtype=torch.float32, device=dev)]
-    ev_in = [torch.cuda.Event() for _ in range(2)]
-    ev_cmp = [torch.cuda.Event() for _ in range(2)]
-    ev_out = [torch.cuda.Event() for _ in range(2)]
-
-    CH = 1 << 24  # elements per copy (64 MB of float32): the coder's own small copies queue behind at most one
-
-    def chunked(dst, src):
-        d, s_ = dst.view(-1), src.view(-1)
-        for i in range(0, d.numel(), CH):
-            d[i:i + CH].copy_(s_[i:i + CH], non_blocking=True)
-
-    def upload(k):
-        b = k % 2
-        with torch.cuda.stream(s_in):
-            s_in.wait_event(ev_cmp[b])  # step k-2 has finished reading these inputs
-            for x, y in zip(hp + ha, dp2[b] + da2[b]):
-                chunked(y, x)
-            ev_in[b].record(s_in)
-
-    def code_and_download(k):
-        b = k % 2
-        with torch.cuda.stream(s_cmp):
-            s_cmp.wait_event(ev_in[b])
-            s_cmp.wait_event(ev_out[b])  # step k-2's results have left these buffers
-            o, off = G.encode_batch(dp2[b], da2[b], [J] * F, [1.0], qp, out=out2[b])
-            pos, attr, rows = G.decode_batch(o, off, C, F * N_GAUSS, pos_out=pos2[b], attr_out=att2[b])
-            ev_cmp[b].record(s_cmp)
-        n, m = int(off[-1]), int(rows[-1])
-        with torch.cuda.stream(s_out):
-            s_out.wait_event(ev_cmp[b])
-            chunked(hout[:n], o[:n])
-            chunked(hpos[:m], pos)
-            chunked(hatt[:m], attr)
-            ev_out[b].record(s_out)
-        return n, m
-
-    def streamed(K):
-        upload(0)
-        for k in range(K):
-            if k + 1 < K:
-                upload(k + 1)
-            n, m = code_and_download(k)
-        torch.cuda.synchronize()
-        return n, m
-
-    streamed(2)
-    torch.cuda.synchronize()
-    K3 = max(4, min(args.steps, 10))
-    t0 = time.perf_counter()
-    n, m = streamed(K3)
-    dt = (time.perf_counter() - t0) / K3
+    K3 = max(6, min(args.steps, 12))
+    dt, n, m, timeline = e2e_streamed(G, torch, dev, qp, F, hp, ha, dp, da, out, pos1, att1, hout, hpos, hatt, K3)
     h2d = sum(x.numel() * 4 for x in hp + ha)
     d2h = n + m * (3 + C) * 4
     res["e2e"] = {"value": round(F / dt, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                   "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 3), "steps": K3,
-                  "mode": "streamed: uploads, coding and downloads of consecutive steps overlap",
+                  "mode": "streamed: uploads, coding and downloads of consecutive steps overlap (3 buffer sets; "
+                          "encoder returns header records, decoder asynchronous)",
+                  "timeline": timeline,
                   "serial": {"value": round(F / dt_serial, 2), "ms_per_step": round(dt_serial * 1e3, 3)}}
     return res
+
+
+def e2e_streamed(G, torch, dev, qp, F, hp, ha, dp, da, out, pos1, att1, hout, hpos, hatt, steps, chunk=1 << 24, NB=3):
+    """End-to-end streamed loop through the public API: pinned host inputs -> H2D -> batched encode -> batched
+    decode -> D2H of the streams and the decoded frames, every step.  The encoder hands back the streams' header
+    records with its offsets (gsnfs_encode_batch_headers), so the decoder (gsnfs_decode_batch_async) reads nothing
+    back and does not block; the only host read of a step is the encoder's own, at its end.  A step's results go
+    down right after the next step's encoder has read back (a small device-to-host read queues behind a bulk
+    download on the link, so no bulk download is in flight while the encoder reads back, except the one being
+    overtaken); the upload of step k+1 overlaps everything.  NB sets of device buffers: step k reuses those of step
+    k-NB.  Copies are issued in pieces of `chunk` elements.  Returns (seconds per step, stream bytes, voxel rows,
+    timeline of the steady steps); decode statuses are checked after the loop."""
+    import time
+    s_in, s_cmp, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    dpN = [dp] + [[torch.empty_like(x) for x in dp] for _ in range(NB - 1)]
+    daN = [da] + [[torch.empty_like(x) for x in da] for _ in range(NB - 1)]
+    outN = [out] + [torch.empty_like(out) for _ in range(NB - 1)]
+    posN = [pos1] + [torch.empty((F * N_GAUSS, 3), dtype=torch.float32, device=dev) for _ in range(NB - 1)]
+    attN = [att1] + [torch.empty((F * N_GAUSS, C), dtype=torch.float32, device=dev) for _ in range(NB - 1)]
+    ev_in = [torch.cuda.Event() for _ in range(NB)]
+    ev_cmp = [torch.cuda.Event() for _ in range(NB)]
+    ev_out = [torch.cuda.Event() for _ in range(NB)]
+    status = torch.full((steps + 8,), -1, dtype=torch.int32, device=dev)
+    tl = []  # per step: timing events of the three streams and host seconds spent in the coding calls
+
+    def chunked(dst, src):
+        d, s_ = dst.view(-1), src.view(-1)
+        for i in range(0, d.numel(), chunk):
+            d[i:i + chunk].copy_(s_[i:i + chunk], non_blocking=True)
+
+    def tev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def upload(k, rec):
+        b = k % NB
+        with torch.cuda.stream(s_in):
+            s_in.wait_event(ev_cmp[b])  # step k-NB has finished reading these inputs
+            rec["up"] = (tev(), tev())
+            rec["up"][0].record(s_in)
+            for x, y in zip(hp + ha, dpN[b] + daN[b]):
+                chunked(y, x)
+            rec["up"][1].record(s_in)
+            ev_in[b].record(s_in)
+
+    def download(k, rec, n, m):
+        b = k % NB
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev_cmp[b])
+            rec["down"] = (tev(), tev())
+            rec["down"][0].record(s_out)
+            chunked(hout[:n], outN[b][:n])
+            chunked(hpos[:m], posN[b][:m])
+            chunked(hatt[:m], attN[b][:m])
+            rec["down"][1].record(s_out)
+            ev_out[b].record(s_out)
+
+    def streamed(K, base):
+        recs = [dict() for _ in range(K)]
+        upload(0, recs[0])
+        prev = None
+        n = m = 0
+        for k in range(K):
+            if k + 1 < K:
+                upload(k + 1, recs[k + 1])
+            b = k % NB
+            h0 = time.perf_counter()
+            with torch.cuda.stream(s_cmp):
+                s_cmp.wait_event(ev_in[b])
+                s_cmp.wait_event(ev_out[b])  # step k-NB's results have left these buffers
+                recs[k]["code"] = (tev(), tev())
+                recs[k]["code"][0].record(s_cmp)
+                o, off, hdr = G.encode_batch(dpN[b], daN[b], [J] * F, [1.0], qp, out=outN[b], headers=True)
+            if prev is not None:
+                download(*prev)
+            with torch.cuda.stream(s_cmp):
+                rows = G.decode_batch_async(o, off, hdr, C, F * N_GAUSS, posN[b], attN[b],
+                                            status[base + k:base + k + 1])
+                recs[k]["code"][1].record(s_cmp)
+                ev_cmp[b].record(s_cmp)
+            recs[k]["host_in_calls_s"] = time.perf_counter() - h0
+            n, m = int(off[-1]), int(rows[-1])
+            prev = (k, recs[k], n, m)
+        download(*prev)
+        torch.cuda.synchronize()
+        tl[:] = recs
+        return n, m
+
+    streamed(3, 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n, m = streamed(steps, 3)
+    dt = (time.perf_counter() - t0) / steps
+    st = status[:3 + steps].cpu().tolist()
+    if any(v != 0 for v in st):
+        raise RuntimeError(f"asynchronous decode reported status {st}")
+    # timeline of the timed steps (skipping the first two, which fill the pipeline)
+    zero = tl[0]["up"][0]
+    span = lambda ev: (zero.elapsed_time(ev[0]), zero.elapsed_time(ev[1]))
+    steady = tl[2:]
+    mean = lambda xs: round(float(sum(xs) / max(len(xs), 1)), 3)
+    timeline = {"steps_summarised": len(steady),
+                "upload_ms": mean([span(r["up"])[1] - span(r["up"])[0] for r in steady]),
+                "coding_ms": mean([span(r["code"])[1] - span(r["code"])[0] for r in steady]),
+                "download_ms": mean([span(r["down"])[1] - span(r["down"])[0] for r in steady]),
+                "coding_start_interval_ms": mean([span(b_["code"])[0] - span(a_["code"])[0]
+                                                  for a_, b_ in zip(steady, steady[1:])]),
+                "host_ms_in_coding_calls": mean([1e3 * r["host_in_calls_s"] for r in steady]),
+                "link_floor_ms": round((sum(x.numel() * 4 for x in hp + ha) + n + m * (3 + C) * 4) / 340e9 * 1e3, 3),
+                "note": "link_floor_ms: the step's bytes at the 340 GB/s measured for uploads and downloads at once"}
+    return dt, n, m, timeline
 
 
 def ladder_leg(G, torch, dev, stream, frames, Js, block, idx):
