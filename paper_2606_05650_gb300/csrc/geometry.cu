@@ -196,6 +196,17 @@ __global__ void zero_words_kernel(uint32_t *p, const uint64_t *nbytes_at, uint64
         p[i] = 0u;
 }
 
+// Occupancy bytes of one tile of kThreads voxels, all heights at once.  Voxel v
+// starts a node at heights 1..s_v and is a child start at heights 1..s_v + 1;
+// its node at height h is the last node start at or before it, whose byte
+// index is the count of node starts up to v (per-height counts carried from
+// earlier tiles and CTAs).  Child bits are OR-ed into the tile's bytes in
+// shared memory (byte j of height h = the tile's j-th node start there; byte
+// 0 = the node a previous tile started), then every nonzero word goes out
+// with one atomic OR (the buffer is zeroed first; a word on the edge of a
+// tile's range is shared with its neighbours).
+constexpr int kOccWords = kThreads / 4 + 2;  // per height: bytes 0 .. kThreads, word-aligned either way
+
 __global__ void __launch_bounds__(kThreads) occ_down_kernel(const uint64_t *__restrict__ codes,
                                                             const uint8_t *__restrict__ gap,
                                                             const uint32_t *__restrict__ vstart,
@@ -211,6 +222,7 @@ __global__ void __launch_bounds__(kThreads) occ_down_kernel(const uint64_t *__re
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     __shared__ uint32_t s_run[kH], s_hoff[kH], s_tot[kH];
     __shared__ uint32_t s_w[kThreads / 32][kH];
+    __shared__ uint32_t s_byte[kH][kOccWords];
     __shared__ int s_hm;
     if (tid < kH) {
         s_run[tid] = partials[((uint64_t)f * kH + tid) * X + x];
@@ -218,31 +230,31 @@ __global__ void __launch_bounds__(kThreads) occ_down_kernel(const uint64_t *__re
     }
     const uint64_t base = occ_off[f];
     const uint32_t lemask = lanemask_lt() | (1u << lane);
+    const uint64_t cap_words = occ_capacity >> 2;
     Range r = cta_range(vstart[f], vstart[f + 1], x, X);
     for (uint64_t t0 = r.b; t0 < r.e; t0 += kThreads) {
         if (tid == 0) s_hm = 0;
         __syncthreads();
-        uint64_t v = t0 + tid;
-        bool ok = v < r.e;
-        int s = ok ? height_of(gap[v], J) : -1;
-        uint64_t m = ok ? codes[v] : 0ull;
-        int cm = ok ? ((s + 1) < (int)J ? (s + 1) : (int)J) : 0;
-        int wm = (int)__reduce_max_sync(0xFFFFFFFFu, (uint32_t)cm);
-        if (lane == 0) atomicMax(&s_hm, wm);
+        const uint64_t v = t0 + tid;
+        const bool ok = v < r.e;
+        const int s = ok ? height_of(gap[v], J) : -1;
+        const uint64_t m = ok ? codes[v] : 0ull;
+        const int cm = ok ? ((s + 1) < (int)J ? (s + 1) : (int)J) : 0;
+        // this warp's own highest height: above it the warp holds no node start and no child
+        const int hw = (int)__reduce_max_sync(0xFFFFFFFFu, (uint32_t)cm);
+        if (lane == 0) atomicMax(&s_hm, hw);
         __syncthreads();
         const int hm = s_hm;
-        // this warp's own highest height: above it the warp holds no node start
-        // and no child, so its counts there are zero and it has nothing to emit
-        const int hw = (int)__reduce_max_sync(0xFFFFFFFFu, (uint32_t)cm);
+        for (int i = tid; i < hm * kOccWords; i += kThreads) (&s_byte[1][0])[i] = 0u;
         for (int h = 1; h <= hm; ++h) {
             const uint32_t b = (h <= hw) ? __ballot_sync(0xFFFFFFFFu, s >= h) : 0u;
             if (lane == 0) s_w[w][h] = __popc(b);
         }
         __syncthreads();
-        if (tid >= 1 && tid <= hm) {
+        if (tid >= 1 && tid <= hm) {  // per height: exclusive prefix over warps, tile total
             uint32_t run = 0;
             for (int ww = 0; ww < kThreads / 32; ++ww) {
-                uint32_t c = s_w[ww][tid];
+                const uint32_t c = s_w[ww][tid];
                 s_w[ww][tid] = run;
                 run += c;
             }
@@ -250,26 +262,28 @@ __global__ void __launch_bounds__(kThreads) occ_down_kernel(const uint64_t *__re
         }
         __syncthreads();
         for (int h = 1; h <= hw; ++h) {
-            // lane l's node at height h is the last node start at or before l, so the
-            // target words are non-decreasing along the warp: the bits of each word are
-            // OR-ed over its run of lanes (doubling shuffles) and its first lane writes
-            uint32_t b = __ballot_sync(0xFFFFFFFFu, s >= h);
-            bool child = ok && (s + 1 >= h);
-            uint32_t incl = s_run[h] + s_w[w][h] + __popc(b & lemask);
-            uint64_t tgt = base + s_hoff[h] + (uint64_t)incl - 1u;
-            const uint64_t wd = tgt >> 2;
-            uint32_t key = ok ? (wd < 0xFFFFFFFEull ? (uint32_t)wd : 0xFFFFFFFEu) : 0xFFFFFFFFu;
-            uint32_t orv = child ? (1u << (((m >> (3 * (h - 1))) & 7u) + 8u * (uint32_t)(tgt & 3u))) : 0u;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t v = __shfl_down_sync(0xFFFFFFFFu, orv, o);
-                const uint32_t k2 = __shfl_down_sync(0xFFFFFFFFu, key, o);
-                if (lane + o < 32 && k2 == key) orv |= v;
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, s >= h);
+            if (h <= cm) {
+                // byte index in the tile: node starts at height h up to and including this voxel
+                const uint32_t j = s_w[w][h] + __popc(b & lemask);
+                const uint32_t bit = (uint32_t)(m >> (3 * (h - 1))) & 7u;
+                atomicOr(&s_byte[h][j >> 2], 1u << (bit + 8u * (j & 3u)));
             }
-            const uint32_t kp = __shfl_up_sync(0xFFFFFFFFu, key, 1);
-            if (ok && orv && (lane == 0 || kp != key)) {
-                if ((uint64_t)key < (occ_capacity >> 2) && key != 0xFFFFFFFEu)
-                    atomicOr(occ_words + key, orv);
+        }
+        __syncthreads();
+        // out: global word W = (g0 >> 2) + k of height h (g0 = the global byte of tile byte 0, one before
+        // the tile's first node start there) holds tile bytes 4k - r .. 4k - r + 3, r = g0 mod 4
+        for (int i = tid; i < hm * kOccWords; i += kThreads) {
+            const int h = 1 + i / kOccWords, k = i - (h - 1) * kOccWords;
+            const int64_t g0 = (int64_t)(base + s_hoff[h] + s_run[h]) - 1;
+            const uint32_t r = (uint32_t)(g0 & 3);
+            if (k > (int)((s_tot[h] + r) >> 2)) continue;
+            const uint32_t lo = k >= 1 ? s_byte[h][k - 1] : 0u, hi = k < kOccWords - 1 ? s_byte[h][k] : 0u;
+            const uint32_t val = __funnelshift_rc(lo, hi, 8u * (4u - r));
+            if (val) {
+                const int64_t W = (g0 >> 2) + k;  // arithmetic shift: floor
+                if (W >= 0 && (uint64_t)W < cap_words)
+                    atomicOr(occ_words + W, val);
                 else
                     set_error(&st->err, kErrCapacity);
             }
@@ -629,18 +643,6 @@ void launch_octree_decode(const uint8_t *occ, uint64_t n_occ, uint32_t J, const 
         expand_kernel<<<grid_for(Md, num_sms), kThreads, 0, s>>>(Ld, Md, occ, lt.boff[d], pref, Ld1, Md1, st);
         count_launch();
     }
-}
-
-void launch_popc_scan(const uint8_t *occ, uint64_t n, uint32_t *pref, uint32_t *partials, int num_sms,
-                      cudaStream_t s)
-{
-    Chunks c = popc_chunks(n, num_sms);
-    popc_up_kernel<<<c.P, kThreads, 0, s>>>(occ, n, c.chunk, partials);
-    count_launch();
-    scan_total_kernel<<<1, 1024, 0, s>>>(partials, c.P);
-    count_launch();
-    popc_down_kernel<<<c.P, kThreads, 0, s>>>(occ, n, c.chunk, partials, pref);
-    count_launch();
 }
 
 void launch_gap_levels(const uint64_t *codes, uint64_t nv, uint8_t *gap, cudaStream_t s)
