@@ -127,6 +127,10 @@ struct gsnfs_ctx {
     // second stream for the independent branches of one call (geometry and attributes)
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // high-priority side stream: the longer branch of a batched call, so that CTAs of the shorter branch
+    // (on the caller's stream) take the SMs that branch leaves idle instead of delaying it
+    cudaStream_t aux_hi = nullptr;
+    cudaEvent_t ev_fork_hi = nullptr, ev_join_hi = nullptr;
     // CUDA graphs of the encoder (off by default)
     bool graphs = false;
     cudaStream_t gstream = nullptr;  // capture / replay stream, joined to the caller's by events
@@ -257,6 +261,30 @@ gsnfs_status fork_end(gsnfs_ctx *ctx, cudaStream_t s)
     return GSNFS_OK;
 }
 
+// The same fork and join onto the context's high-priority stream (the block
+// scheduler starts pending CTAs of a higher-priority stream first).
+gsnfs_status fork_hi_begin(gsnfs_ctx *ctx, cudaStream_t s, cudaStream_t *hi)
+{
+    if (!ctx->aux_hi) {
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CK(cudaStreamCreateWithPriority(&ctx->aux_hi, cudaStreamNonBlocking, greatest));
+        CK(cudaEventCreateWithFlags(&ctx->ev_fork_hi, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_join_hi, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(ctx->ev_fork_hi, s));
+    CK(cudaStreamWaitEvent(ctx->aux_hi, ctx->ev_fork_hi, 0));
+    *hi = ctx->aux_hi;
+    return GSNFS_OK;
+}
+
+gsnfs_status fork_hi_end(gsnfs_ctx *ctx, cudaStream_t s)
+{
+    CK(cudaEventRecord(ctx->ev_join_hi, ctx->aux_hi));
+    CK(cudaStreamWaitEvent(s, ctx->ev_join_hi, 0));
+    return GSNFS_OK;
+}
+
 // Small transfers between the pinned staging buffer and the device (a call's
 // parameters and results) run as a kernel over the staging buffer's unified
 // address instead of on the copy engines, so they never queue behind a
@@ -347,6 +375,53 @@ __global__ void header_records_kernel(const uint8_t *out, const StreamInfo *si, 
             v = b[x.hb + (k - 4096)];
         else if (k >= 4160 && k < 4168 && x.attr >= 8)
             v = b[x.hb + x.occ + (k - 4160)];
+        r[k] = v;
+    }
+}
+
+// The same records read out of the streams themselves (a decoder not given
+// them): frame f0 + i of a launch is CTA i, its stream at in + off[i] of
+// off[i + 1] - off[i] bytes; record at rec + (f0 + i) * stride.  The section
+// sizes come from the stream's fixed header; nothing outside the stream is
+// read (a stream too short for its header gives a record the host rejects).
+constexpr uint32_t kRecFrames = 64;
+struct RecLaunch {
+    const uint8_t *in;
+    uint8_t *rec;
+    uint64_t stride;
+    uint32_t f0;
+    uint64_t off[kRecFrames + 1];
+};
+
+__device__ __forceinline__ uint64_t rd_le(const uint8_t *p, int n)
+{
+    uint64_t v = 0;
+    for (int k = n - 1; k >= 0; --k) v = (v << 8) | p[k];
+    return v;
+}
+
+__global__ void stream_records_kernel(RecLaunch a)
+{
+    const uint32_t i = blockIdx.x;
+    const uint64_t o = a.off[i], bytes = a.off[i + 1] - o;
+    const uint8_t *b = a.in + o;
+    uint8_t *r = a.rec + (uint64_t)(a.f0 + i) * a.stride;
+    uint64_t hb = 0, occ = 0, attr = 0;
+    if (bytes >= 96) {
+        hb = rd_le(b + 8, 4);
+        occ = rd_le(b + 72, 8);
+        attr = rd_le(b + 80, 8);
+    }
+    const uint64_t nh = bytes < 96 ? bytes : (hb < 96 ? 96 : (hb > 4096 ? 4096 : hb));
+    const bool heads = bytes >= 96 && hb <= 4096 && hb < bytes;
+    for (uint32_t k = threadIdx.x; k < GSNFS_HEADER_RECORD_BYTES; k += blockDim.x) {  // every byte: zeros elsewhere
+        uint8_t v = 0;
+        if (k < nh && k < bytes)
+            v = b[k];
+        else if (heads && k >= 4096 && k < 4096 + 24 && hb + (k - 4096) < bytes)
+            v = b[hb + (k - 4096)];
+        else if (heads && k >= 4160 && k < 4168 && attr >= 8 && occ < bytes && hb + occ + (k - 4160) < bytes)
+            v = b[hb + occ + (k - 4160)];
         r[k] = v;
     }
 }
@@ -753,7 +828,7 @@ gsnfs_status run_graphed(gsnfs_ctx *ctx, cudaStream_t s, std::vector<uint64_t> k
         t_capture_launches = nullptr;
         cudaError_t e = cudaStreamEndCapture(ctx->gstream, &graph);
         cudaGraphExec_t exec = nullptr;
-        if (st == GSNFS_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (st == GSNFS_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
         if (graph) cudaGraphDestroy(graph);
         if (st != GSNFS_OK || e != cudaSuccess || !exec) {
             cudaGetLastError();
@@ -901,32 +976,31 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
         launch_dedup(skeys, N, frame_shift, F, L.codes, L.seg, L.gap, L.vstart, L.dpart, dst, sms, s,
                      C ? svals : nullptr, L.row0);
         stage_end(s, kStDedup);
-        // a4 + a5 (geometry) run beside a6-a9 (attributes) on the context's second stream
-        cudaStream_t ga = nullptr;
-        {
-            const gsnfs_status fst = fork_begin(ctx, s, &ga);
+        // a4 + a5 (geometry) run on s beside a6-a9 (attributes, the longer branch) on the high-priority stream
+        cudaStream_t sa = s;
+        if (C) {
+            const gsnfs_status fst = fork_hi_begin(ctx, s, &sa);
             if (fst) return fst;
         }
         // a4: octree occupancy
         OccupancyOut oo{L.occ, L.occ_cap, L.lsz, L.occ_off, L.hoff, L.opart};
-        stage_begin(ga, kStOccupancy);
-        launch_occupancy(L.codes, L.gap, L.vstart, L.Jd, F, frame_shift, oo, dst, sms, ga);
-        stage_end(ga, kStOccupancy);
+        stage_begin(s, kStOccupancy);
+        launch_occupancy(L.codes, L.gap, L.vstart, L.Jd, F, frame_shift, oo, dst, sms, s);
+        stage_end(s, kStOccupancy);
         // a5: occupancy rANS
         RansFrames rf{F, L.occ, L.occ_off, q->rans_chunk, L.chunk_off, L.freq, L.cum, L.mode, L.chunk_words,
                       L.chunk_top, L.chunk_pos, L.chunk_slots, L.sec_bytes};
-        stage_begin(ga, kStRans);
-        launch_rans_encode(rf, dst, L.max_chunks, sms, ga);
-        stage_end(ga, kStRans);
-
+        stage_begin(s, kStRans);
+        launch_rans_encode(rf, dst, L.max_chunks, sms, s);
+        stage_end(s, kStRans);
         HdrParams hpar{F, R, C, G, C ? q->rlgr_block : 1u, q->rans_chunk, C ? q->color : 0u, q->tau, rq.capacity};
         if (C) {
             // a6: RAHT prelude; a7: forward transform with the cluster average fused into the first pass
-            stage_begin(s, kStPrelude);
-            launch_raht_prelude(L.plan, L.gap, dst, nullptr, sms, s);
-            stage_end(s, kStPrelude);
-            launch_frame_centres(L.attrp, L.poff, F, C, L.center, s);
-            if (q->color) launch_color_klt(L.attrp, L.poff, F, L.klt, L.center, L.kltpart, s);
+            stage_begin(sa, kStPrelude);
+            launch_raht_prelude(L.plan, L.gap, dst, nullptr, sms, sa);
+            stage_end(sa, kStPrelude);
+            launch_frame_centres(L.attrp, L.poff, F, C, L.center, sa);
+            if (q->color) launch_color_klt(L.attrp, L.poff, F, L.klt, L.center, L.kltpart, sa);
             RahtIO io{};
             io.C = C;
             io.seg = L.seg;
@@ -939,12 +1013,12 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
             io.frame_shift = frame_shift;
             io.Y = L.Y;
             io.pool = L.pool;
-            stage_begin(s, kStRahtFwd);
-            launch_raht_forward(L.plan, io, N, sms, s);
-            stage_end(s, kStRahtFwd);
-            launch_frame_dc(L.Y, L.vstart, F, C, L.center, L.steps_rg, L.groups, G, q->tau, L.dc, s);
+            stage_begin(sa, kStRahtFwd);
+            launch_raht_forward(L.plan, io, N, sms, sa);
+            stage_end(sa, kStRahtFwd);
+            launch_frame_dc(L.Y, L.vstart, F, C, L.center, L.steps_rg, L.groups, G, q->tau, L.dc, sa);
             // a8 + a9: quantise + block RLGR for every rung
-            launch_rlgr_offsets(L.vstart, F, q->rlgr_block, R, C, L.job_off, L.blk_off, s);
+            launch_rlgr_offsets(L.vstart, F, q->rlgr_block, R, C, L.job_off, L.blk_off, sa);
             RlgrJob j{};
             j.C = C;
             j.B = q->rlgr_block;
@@ -961,7 +1035,7 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
             j.overflow = L.overflow;
             j.dc = L.dc;
             if (rq.dist) {
-                CK(dev_memset(L.sq_err, 0, 8 * (size_t)F * R * C, s));
+                CK(dev_memset(L.sq_err, 0, 8 * (size_t)F * R * C, sa));
                 j.sq_err = L.sq_err;
                 j.step = L.step;
             }
@@ -969,13 +1043,13 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
             j.groups = L.groups;
             j.G = G;
             j.tau64 = q->tau;
-            stage_begin(s, kStRlgrEnc);
-            launch_rlgr_encode(j, L.job_off, L.jobs_bound, s);
-            stage_end(s, kStRlgrEnc);
-            launch_scan_u32_to_u64(L.block_words, L.blocks_bound, L.block_off, L.spart, sms, s);
+            stage_begin(sa, kStRlgrEnc);
+            launch_rlgr_encode(j, L.job_off, L.jobs_bound, sa);
+            stage_end(sa, kStRlgrEnc);
+            launch_scan_u32_to_u64(L.block_words, L.blocks_bound, L.block_off, L.spart, sms, sa);
         }
-        {
-            const gsnfs_status fst = fork_end(ctx, s);
+        if (C) {
+            const gsnfs_status fst = fork_hi_end(ctx, s);
             if (fst) return fst;
         }
         // a10: container
@@ -1503,11 +1577,21 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     auto rec = [&](uint32_t f) -> const uint8_t * {
         return h_headers ? h_headers + (size_t)f * GSNFS_HEADER_RECORD_BYTES : hp + (size_t)f * 8192;
     };
-    if (!h_headers) {
-        for (uint32_t f = 0; f < F; ++f) {
+    if (!h_headers) {  // every frame's record read out of its stream by one launch per 64 frames, one wait
+        for (uint32_t f = 0; f < F; ++f)
             if (offs[f + 1] - offs[f] < 96) return GSNFS_ERR_CORRUPT;
-            CK(stage_copy(hp + (size_t)f * 8192, d_in + offs[f], 96, s));
+        for (uint32_t f0 = 0; f0 < F; f0 += kRecFrames) {
+            RecLaunch a;
+            a.in = d_in;
+            a.rec = hp;
+            a.stride = 8192;
+            a.f0 = f0;
+            const uint32_t n = std::min<uint32_t>(kRecFrames, F - f0);
+            for (uint32_t i = 0; i <= n; ++i) a.off[i] = offs[f0 + i];
+            stream_records_kernel<<<n, 256, 0, s>>>(a);
+            count_launch();
         }
+        CK(cudaGetLastError());
         CK(cudaStreamSynchronize(s));
     }
     for (uint32_t f = 0; f < F; ++f) {
@@ -1515,16 +1599,6 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         st = parse_fixed(rec(f), offs[f + 1] - offs[f], P[f]);
         if (st) return st;
         if (P[f].hb > 4096) return GSNFS_ERR_CORRUPT;
-    }
-    if (!h_headers) {
-        for (uint32_t f = 0; f < F; ++f) {
-            uint8_t *h = hp + (size_t)f * 8192;
-            CK(stage_copy(h, d_in + offs[f], P[f].hb, s));
-            CK(stage_copy(h + 4096, d_in + offs[f] + P[f].hb, 24, s));
-            if (P[f].attr_bytes >= 8)
-                CK(stage_copy(h + 4096 + 64, d_in + offs[f] + P[f].hb + P[f].occ_bytes, 8, s));
-        }
-        CK(cudaStreamSynchronize(s));
     }
     uint32_t C = 0, Jmax = 0;
     uint64_t N = 0, n_occ = 0, nodes = 0, nblk = 0, jobs = 0, max_occ = 0;
@@ -1562,8 +1636,8 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     // ---- layout
     struct L_ {
         DecFrame *fr;
-        uint32_t *vstart, *bw_all, *tabs, *pref, *ppart;
-        uint64_t *lvl_pref, *job_off, *blk_pref, *boff_all, *spart, *nodes, *codes, *nvdev;
+        uint32_t *vstart, *bw_all, *tabs, *tsum, *tile_pref;
+        uint64_t *lvl_pref, *job_off, *blk_pref, *boff_all, *spart, *tbase, *tpart, *nodes, *nvdev;
         float *steps, *Y, *pool;
         uint8_t *occ, *gap;
         float *ctab, *klt;
@@ -1586,10 +1660,11 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         L.steps = cv.take<float>((uint64_t)F * C + 1);
         L.tabs = cv.take<uint32_t>(any_rans ? (uint64_t)F * rans_table_words() : 1);
         L.occ = cv.take<uint8_t>(n_occ + 8);
-        L.pref = cv.take<uint32_t>(n_occ + 2);
-        L.ppart = cv.take<uint32_t>(2 * (uint64_t)ctx->num_sms + 8);
+        L.tsum = cv.take<uint32_t>(occ_tiles(n_occ) + 1);
+        L.tbase = cv.take<uint64_t>(occ_tiles(n_occ) + 2);
+        L.tpart = cv.take<uint64_t>(scan_partial_words(occ_tiles(n_occ), ctx->num_sms) + 1);
+        L.tile_pref = cv.take<uint32_t>((uint64_t)Jmax * (F + 1) + 1);
         L.nodes = cv.take<uint64_t>(nodes + 1);
-        L.codes = cv.take<uint64_t>(N + 1);
         L.gap = cv.take<uint8_t>(N + 2);
         L.ctab = cv.take<float>(ctab_total + 1);
         L.klt = cv.take<float>((any_color ? (uint64_t)F : 1) * kKltFloats);
@@ -1618,11 +1693,23 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     unsigned char *tp = hp + (size_t)F * 8192;
     size_t o_fr = 0, o_vs = o_fr + sizeof(DecFrame) * F, o_lp = (o_vs + 4 * (F + 1) + 7) & ~(size_t)7;
     size_t o_jo = o_lp + 8 * (size_t)(Jmax + 1) * (F + 1), o_bp = o_jo + 8 * (F + 1), o_nv = o_bp + 8 * (F + 1);
-    size_t o_st = o_nv + 8, o_fc = o_st + 4 * (size_t)F * C, o_end = o_fc + 4 * (size_t)(F + 1);
-    if ((size_t)F * 8192 + o_end > ctx->pinned_cap) {
-        st = grow_pinned(ctx, (size_t)F * 8192 + o_end + 64);  // keeps nothing needed: headers are parsed
-        if (st) return st;
-        hp = ctx->pinned;
+    size_t o_st = o_nv + 8, o_fc = o_st + 4 * (size_t)F * C, o_tp = o_fc + 4 * (size_t)(F + 1);
+    size_t o_end = o_tp + 4 * ((size_t)Jmax * (F + 1) + 1);
+    const size_t need = (size_t)F * 8192 + o_end + 128;  // and the status word after the tables
+    if (status ? ctx->aring_cap[ring] < need : ctx->pinned_cap < need) {
+        // the headers are parsed by now: the staging buffer holds nothing still needed
+        if (status) {  // the slot's last use has completed (its event was waited on above)
+            CK(cudaFreeHost(ctx->aring[ring]));
+            ctx->aring[ring] = nullptr;
+            ctx->aring_cap[ring] = 0;
+            CK(cudaMallocHost((void **)&ctx->aring[ring], need));
+            ctx->aring_cap[ring] = need;
+            hp = ctx->aring[ring];
+        } else {
+            st = grow_pinned(ctx, need);
+            if (st) return st;
+            hp = ctx->pinned;
+        }
         tp = hp + (size_t)F * 8192;
     }
     DecFrame *hf = reinterpret_cast<DecFrame *>(tp + o_fr);
@@ -1632,7 +1719,8 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     uint64_t *hbp = reinterpret_cast<uint64_t *>(tp + o_bp);
     float *hst = reinterpret_cast<float *>(tp + o_st);
     uint32_t *hfc = reinterpret_cast<uint32_t *>(tp + o_fc);
-    uint64_t vs = 0, oo = 0, no = 0, bo = 0, jo = 0, co = 0;
+    uint32_t *htp = reinterpret_cast<uint32_t *>(tp + o_tp);
+    uint64_t vs = 0, oo = 0, no = 0, bo = 0, jo = 0, co = 0, pb = 0;
     for (uint32_t f = 0; f < F; ++f) {
         const ParsedHeader &H = P[f];
         DecFrame d{};
@@ -1669,8 +1757,10 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
             d.boff[lv] = b2;
             if (lv < H.J) {
                 d.noff[lv] = no;
+                d.pbase[lv] = pb;  // the bytes of a level hold as many set bits as the next level has nodes
                 no += H.lsz[lv];
                 b2 += H.lsz[lv];
+                pb += H.lsz[lv + 1];
             }
         }
         hf[f] = d;
@@ -1697,6 +1787,19 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         }
         hlp[(uint64_t)lv * (F + 1) + F] = run;
     }
+    std::vector<uint32_t> level_tiles(Jmax);  // CTAs of each level launch
+    for (uint32_t lv = 0; lv < Jmax; ++lv) {
+        uint32_t run = 0;
+        for (uint32_t f = 0; f < F; ++f) {
+            htp[(uint64_t)lv * (F + 1) + f] = run;
+            if (lv < P[f].J && P[f].lsz[lv]) {
+                const uint64_t a0 = hf[f].occ_off + hf[f].boff[lv];
+                run += (uint32_t)(occ_tile_first(a0 + P[f].lsz[lv] - 1) - occ_tile_first(a0) + 1);
+            }
+        }
+        htp[(uint64_t)lv * (F + 1) + F] = run;
+        level_tiles[lv] = run;
+    }
     memcpy(tp + o_nv, &N, 8);
     CK(stage_copy(L.fr, tp + o_fr, sizeof(DecFrame) * F, s));
     CK(stage_copy(L.vstart, tp + o_vs, 4 * (F + 1), s));
@@ -1704,6 +1807,7 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     CK(stage_copy(L.job_off, tp + o_jo, 8 * (F + 1), s));
     CK(stage_copy(L.blk_pref, tp + o_bp, 8 * (F + 1), s));
     CK(stage_copy(L.nvdev, tp + o_nv, 8, s));
+    if (Jmax) CK(stage_copy(L.tile_pref, tp + o_tp, 4 * (size_t)Jmax * (F + 1), s));
     if (C) CK(stage_copy(L.steps, tp + o_st, 4 * (size_t)F * C, s));
     if (any_color) {
         CK(stage_copy(L.fcolor, tp + o_fc, 4 * (size_t)F, s));
@@ -1715,55 +1819,38 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     CK(dev_memset(dst, 0, 8, s));
     const int sms = ctx->num_sms;
 
-    // a12's RLGR decode needs only the streams' block tables: it runs on the
-    // context's second stream beside a11 and the prelude
+    // a12's RLGR decode needs only the streams' block tables: it runs on s beside a11 and the prelude (the
+    // longer branch), which run on the context's high-priority stream
     const bool attrs = C && d_attr;
+    cudaStream_t sg = s;
     if (attrs) {
-        cudaStream_t ra = nullptr;
-        st = fork_begin(ctx, s, &ra);
+        st = fork_hi_begin(ctx, s, &sg);
         if (st) return st;
-        stage_begin(ra, kStRlgrDec);
-        launch_batch_block_tables(L.fr, F, L.blk_pref, nblk, L.bw_all, sms, ra);
-        launch_scan_u32_to_u64(L.bw_all, nblk, L.boff_all, L.spart, sms, ra);
-        launch_rlgr_decode_batch(L.fr, F, L.job_off, jobs, L.bw_all, L.boff_all, L.steps, C, L.Y, dst, ra);
-        stage_end(ra, kStRlgrDec);
+        stage_begin(s, kStRlgrDec);
+        launch_batch_block_tables(L.fr, F, L.blk_pref, nblk, L.bw_all, sms, s);
+        launch_scan_u32_to_u64(L.bw_all, nblk, L.boff_all, L.spart, sms, s);
+        launch_rlgr_decode_batch(L.fr, F, L.job_off, jobs, L.bw_all, L.boff_all, L.steps, C, L.Y, dst, s);
+        stage_end(s, kStRlgrDec);
     }
     // a11: occupancy bytes of every frame, octree levels, voxel centres
-    stage_begin(s, kStOccDecode);
-    launch_batch_occ_bytes(L.fr, F, L.occ, max_occ, sms, s);
-    if (any_rans) launch_batch_rans_decode(L.fr, F, max_nch, chunk_max, L.occ, L.tabs, dst, s);
-    stage_end(s, kStOccDecode);
-    stage_begin(s, kStOctreeDecode);
-    launch_popc_scan(L.occ, n_occ, L.pref, L.ppart, sms, s);
-    launch_batch_roots(L.fr, F, L.nodes, L.codes, s);
-    {  // two levels per launch where the second level holds at most 4 nodes per node of the first (the deep,
-       // sparse levels: a thread's walk stays short), one level elsewhere
-        auto level_total = [&](uint32_t l) {
-            uint64_t t = 0;
-            for (uint32_t f = 0; f < F; ++f)
-                if (l <= P[f].J) t += P[f].lsz[l];
-            return t;
-        };
-        const uint32_t kmax = std::min<uint32_t>(2, batch_expand_max_levels());
-        for (uint32_t lv = 0; lv < Jmax;) {
-            const uint64_t count = hlp[(uint64_t)lv * (F + 1) + F];
-            const uint64_t t0 = std::max<uint64_t>(level_total(lv), 1);
-            uint32_t K = 1;
-            while (K < kmax && lv + K < Jmax && level_total(lv + K + 1) <= 4 * t0) ++K;
-            launch_batch_expand(L.fr, F, lv, K, L.lvl_pref + (uint64_t)lv * (F + 1), count, L.occ, L.pref, L.nodes,
-                                L.codes, dst, sms, s);
-            lv += K;
-        }
-    }
-    if (ctab_total) launch_batch_centre_tables(L.fr, F, Jmax, L.ctab, sms, s);
-    launch_batch_centres_gaps(L.fr, F, L.vstart, N, L.codes, L.ctab, d_pos, L.gap, sms, s);
-    stage_end(s, kStOctreeDecode);
+    stage_begin(sg, kStOccDecode);
+    launch_batch_occ_bytes(L.fr, F, L.occ, max_occ, sms, sg);
+    if (any_rans) launch_batch_rans_decode(L.fr, F, max_nch, chunk_max, L.occ, L.tabs, dst, sg);
+    stage_end(sg, kStOccDecode);
+    stage_begin(sg, kStOctreeDecode);
+    if (ctab_total) launch_batch_centre_tables(L.fr, F, Jmax, L.ctab, sms, sg);
+    launch_occ_tile_bases(L.occ, n_occ, L.tsum, L.tbase, L.tpart, sms, sg);
+    launch_batch_roots(L.fr, F, L.nodes, L.gap, N, sg);
+    for (uint32_t lv = 0; lv < Jmax; ++lv)
+        launch_batch_level(L.fr, F, lv, L.tile_pref + (uint64_t)lv * (F + 1), level_tiles[lv], L.occ, n_occ,
+                           L.tbase, L.nodes, L.ctab, d_pos, L.gap, dst, sg);
+    stage_end(sg, kStOctreeDecode);
     // a12: RAHT schedule, then (after the RLGR branch) the inverse RAHT
     if (attrs) {
-        stage_begin(s, kStPrelude);
-        launch_raht_prelude(L.plan, L.gap, dst, L.nvdev, sms, s);
-        stage_end(s, kStPrelude);
-        st = fork_end(ctx, s);
+        stage_begin(sg, kStPrelude);
+        launch_raht_prelude(L.plan, L.gap, dst, L.nvdev, sms, sg);
+        stage_end(sg, kStPrelude);
+        st = fork_hi_end(ctx, s);
         if (st) return st;
         RahtIO io{};
         io.C = C;
@@ -1850,6 +1937,9 @@ void gsnfs_destroy(gsnfs_ctx *ctx)
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->aux_hi) cudaStreamDestroy(ctx->aux_hi);
+    if (ctx->ev_fork_hi) cudaEventDestroy(ctx->ev_fork_hi);
+    if (ctx->ev_join_hi) cudaEventDestroy(ctx->ev_join_hi);
     if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
     if (ctx->gev_in) cudaEventDestroy(ctx->gev_in);
     if (ctx->gev_out) cudaEventDestroy(ctx->gev_out);

@@ -115,97 +115,6 @@ __global__ void __launch_bounds__(32 * ransdec::kMaxWarps) rans_batch_kernel(con
     }
 }
 
-__global__ void roots_kernel(const DecFrame *fr, uint32_t F, uint64_t *nodes, uint64_t *codes)
-{
-    const uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= F || fr[f].nv == 0) return;
-    nodes[fr[f].noff[0]] = 0ull;  // implicit root code of Algorithm 2
-    (void)codes;
-}
-
-// Levels d .. d + K (K <= 2) of Algorithm 3 for every frame with J > d in one
-// launch: a thread takes one node of level d and walks its descendants depth
-// first down to level min(d + K, J) (children in increasing bit order, so
-// every level's nodes are visited in their breadth-first order), writing only
-// that last level; the level in between is never stored.  K = 2 only where
-// the second level holds at most 4 nodes per node of the first (chosen on the
-// host): longer walks were measured slower (a thread's chain of dependent
-// loads and the divergence of uneven subtrees outweigh the saved traffic).
-// A thread's nodes mostly stay in one frame, so the frame's tables are looked
-// up once per change.
-constexpr int kExpandMaxLevels = 2;
-
-struct ExpandFrame {
-    const uint64_t *src;                    // level d codes
-    uint64_t *dst;                          // last level's codes
-    uint64_t bo[kExpandMaxLevels];          // byte offset of level d + k in the batch occupancy buffer
-    uint32_t base[kExpandMaxLevels];        // popcount prefix at the start of level d + k
-    uint32_t M[kExpandMaxLevels + 1];       // node count of level d + k
-    int levels;                             // levels walked: min(K, J - d)
-};
-
-template <int k>
-__device__ __forceinline__ void expand_walk(const ExpandFrame &x, const uint8_t *__restrict__ occ,
-                                            const uint32_t *__restrict__ pref, uint64_t code, uint32_t w,
-                                            DevState *st)
-{
-    // node w of level d + k, with its code
-    if (k == x.levels) {
-        x.dst[w] = code;
-        return;
-    }
-    if constexpr (k < kExpandMaxLevels) {
-        const uint32_t byte = occ[x.bo[k] + w];
-        if (byte == 0) {
-            set_error(&st->err, kErrCorrupt);
-            return;
-        }
-        const uint64_t c = code << 3;
-        uint32_t cw = pref[x.bo[k] + w] - x.base[k];
-        for (uint32_t bits = byte; bits; bits &= bits - 1u) {  // set bits in increasing order
-            if (cw < x.M[k + 1]) expand_walk<k + 1>(x, occ, pref, c + (uint32_t)(__ffs(bits) - 1), cw, st);
-            else set_error(&st->err, kErrCorrupt);
-            ++cw;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(256) expand_batch_kernel(const DecFrame *fr, uint32_t F, uint32_t d, uint32_t K,
-                                                           const uint64_t *lvl_pref, uint64_t count,
-                                                           const uint8_t *__restrict__ occ_all,
-                                                           const uint32_t *__restrict__ pref, uint64_t *nodes,
-                                                           uint64_t *codes, DevState *st)
-{
-    uint64_t fbeg = 1, fend = 0;  // node range of the cached frame (empty at first)
-    ExpandFrame x;
-    for (uint64_t gp = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; gp < count;
-         gp += (uint64_t)gridDim.x * blockDim.x) {
-        if (gp < fbeg || gp >= fend) {
-            const uint32_t f = find_frame(lvl_pref, F, gp);
-            const DecFrame &fd = fr[f];
-            fbeg = lvl_pref[f];
-            fend = lvl_pref[f + 1];
-            x.levels = (int)min(K, fd.J - d);
-            x.src = nodes + fd.noff[d];
-            x.dst = (d + (uint32_t)x.levels == fd.J) ? codes + fd.vstart : nodes + fd.noff[d + x.levels];
-            x.M[0] = fd.lsz[d];
-#pragma unroll
-            for (int k = 0; k < kExpandMaxLevels; ++k) {
-                if (k < x.levels) {
-                    x.bo[k] = fd.occ_off + fd.boff[d + k];
-                    x.base[k] = pref[x.bo[k]];
-                    x.M[k + 1] = fd.lsz[d + k + 1];
-                    // the popcounts of level d + k add up to the size of level d + k + 1
-                    if (gp == fbeg && pref[x.bo[k] + x.M[k]] - x.base[k] != x.M[k + 1])
-                        set_error(&st->err, kErrCorrupt);
-                }
-            }
-        }
-        const uint32_t p = (uint32_t)(gp - fbeg);
-        expand_walk<0>(x, occ_all, pref, x.src[p], p, st);
-    }
-}
-
 __device__ __forceinline__ uint32_t compact3b(uint64_t m)
 {
     m &= 0x1249249249249249ull;
@@ -217,8 +126,190 @@ __device__ __forceinline__ uint32_t compact3b(uint64_t m)
     return (uint32_t)m;
 }
 
-// voxel centres (Sec. 2.1) and gap levels of every frame's voxels
-// grid (x, frames): the centre table of frame blockIdx.y, entry a * 2^J + v =
+__global__ void roots_kernel(const DecFrame *fr, uint32_t F, uint64_t *nodes, uint8_t *gap, uint64_t nv_total)
+{
+    const uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f == 0) gap[nv_total] = (uint8_t)kInfLevel;  // sentinel after the last voxel
+    if (f >= F || fr[f].nv == 0) return;
+    nodes[fr[f].noff[0]] = 0ull;  // implicit root code of Algorithm 2
+}
+
+// ---- octree levels (Algorithm 3) by tiles of the batch occupancy buffer ----
+// P(x) = number of set bits in the batch occupancy bytes before byte x.  Node w
+// of level d of frame f (byte x = occ_off + boff[d] + w) has its children at
+// indices P(x) - P(a0) .. of level d + 1, a0 the level's first byte.  P(a0) is
+// known on the host (a level's popcounts add up to the next level's size);
+// P at every kOccTile-byte boundary comes from a scan of tile popcounts, and
+// a tile's CTA finds P(x) for its bytes with one block scan.  One launch per
+// level covers every frame: its CTAs are the tiles that hold bytes of that
+// level (a tile on a level boundary is visited by both levels' launches).
+// At a frame's last level the leaf codes are not stored: the CTA writes the
+// voxel centres (Sec. 2.1) and the gap levels of consecutive voxels instead.
+constexpr uint32_t kOccTile = 1024;  // bytes per tile
+
+__device__ __forceinline__ uint32_t word_at(const uint8_t *occ, uint64_t n, uint64_t x)  // bytes >= n read 0
+{
+    if (x >= n) return 0u;
+    uint32_t v = *reinterpret_cast<const uint32_t *>(occ + x);  // x % 4 == 0; the buffer has 8 bytes of slack
+    if (x + 4 > n) v &= (1u << (8u * (uint32_t)(n - x))) - 1u;
+    return v;
+}
+
+__global__ void __launch_bounds__(256) occ_tile_popc_kernel(const uint8_t *__restrict__ occ, uint64_t n,
+                                                            uint64_t ntiles, uint32_t *tsum)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint64_t t = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles;
+         t += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+        uint32_t c = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < kOccTile / 128; ++k) c += __popc(word_at(occ, n, t * kOccTile + 4ull * (lane + 32 * k)));
+        c = __reduce_add_sync(0xFFFFFFFFu, c);
+        if (lane == 0) tsum[t] = c;
+    }
+}
+
+__device__ __forceinline__ void leaf_out(const DecFrame &d, const float *__restrict__ ctab, uint32_t v, uint64_t m,
+                                         float *pos)
+{
+    if (d.ctab_off != ~0ull) {
+        const float *t = ctab + d.ctab_off;
+        float c[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) c[a] = __ldg(t + ((uint64_t)a << d.J) + compact3b(m >> a));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) pos[3ull * v + a] = c[a];
+    } else {
+        const FrameGrid g = d.grid;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double off = __dmul_rn(__dadd_rn((double)compact3b(m >> a), 0.5), g.cell);
+            pos[3ull * v + a] = (float)__dadd_rn(g.lo[a], off);
+        }
+    }
+}
+
+struct LevelArgs {
+    const DecFrame *fr;
+    uint32_t F, d;
+    const uint32_t *tile_pref;  // F + 1: first CTA of each frame at this level
+    const uint8_t *occ;
+    uint64_t n_occ;
+    const uint64_t *tbase;      // P at each tile's first byte
+    uint64_t *nodes;
+    const float *ctab;
+    float *pos;                 // or null: no centres
+    uint8_t *gap;
+    DevState *st;
+};
+
+// A CTA of kLevelThreads threads takes one tile, 8 bytes (nodes) per thread.
+// Internal level: children codes go straight to the next level.  Leaf level:
+// gap levels are written as the children are formed, and the children's
+// codes are staged in shared memory (at their rank among the tile's set bits)
+// so that the centres are computed afterwards one child per thread, with
+// independent table loads and coalesced stores (a tile with more set bits
+// than the stage holds writes its centres directly).
+constexpr uint32_t kLevelThreads = kOccTile / 8;
+constexpr uint32_t kLeafStage = 2048;
+
+__device__ __forceinline__ uint64_t word8_at(const uint8_t *occ, uint64_t n, uint64_t x)  // bytes >= n read 0
+{
+    if (x >= n) return 0ull;
+    uint64_t v = *reinterpret_cast<const uint64_t *>(occ + x);  // x % 8 == 0; the buffer has 8 bytes of slack
+    if (x + 8 > n) v &= (1ull << (8u * (uint32_t)(n - x))) - 1ull;
+    return v;
+}
+
+__global__ void __launch_bounds__(kLevelThreads) expand_level_kernel(LevelArgs a)
+{
+    __shared__ uint64_t sh[33];
+    __shared__ uint64_t s_leaf[kLeafStage];
+    __shared__ uint32_t s_lo, s_hi;
+    const uint32_t g = blockIdx.x, t = threadIdx.x;
+    const uint32_t f = find_frame(a.tile_pref, a.F, g);
+    const DecFrame &fd = a.fr[f];
+    const uint32_t d = a.d;
+    const uint64_t a0 = fd.occ_off + fd.boff[d], a1 = a0 + fd.lsz[d];
+    const uint64_t tile = a0 / kOccTile + (g - a.tile_pref[f]);
+    const uint64_t x0 = tile * kOccTile + 8ull * t;
+    const uint64_t wv = word8_at(a.occ, a.n_occ, x0);
+    const bool leaf = d + 1 == fd.J;
+    const uint64_t *src = a.nodes + fd.noff[d];
+    // this thread's nodes' codes (and, at a leaf level, the node before its first) are loaded before the
+    // scan, so that their latency overlaps it
+    uint64_t code[8];
+#pragma unroll
+    for (uint32_t k = 0; k < 8; ++k) code[k] = (x0 + k >= a0 && x0 + k < a1) ? src[x0 + k - a0] : 0ull;
+    const uint64_t xf = x0 > a0 ? x0 : a0;  // first byte of the level in this thread's word
+    bool have_prev = false;
+    uint64_t prev = 0;
+    if (leaf && xf > a0 && xf < x0 + 8 && xf < a1) {  // the voxel before: the last child of node xf - 1 - a0
+        const uint32_t pb = a.occ[xf - 1];
+        prev = (src[xf - 1 - a0] << 3) + (pb ? 31u - (uint32_t)__clz(pb) : 0u);
+        have_prev = true;
+    }
+    const uint64_t tb = a.tbase[tile];
+    uint64_t tot;
+    const uint64_t lp0 = block_exclusive_sum<uint64_t>((uint64_t)__popcll(wv), sh, &tot);  // P(x0) - tb
+    const uint64_t base = fd.pbase[d];
+    const uint32_t M1 = fd.lsz[d + 1];
+    const bool stage = leaf && tot <= kLeafStage;
+    if (t == 0) {  // the staged range: the tile's bytes of this level
+        s_lo = 0;
+        s_hi = (uint32_t)tot;
+    }
+    __syncthreads();
+    uint64_t lp = lp0;  // set bits of the tile before byte x
+    bool bad = false;
+#pragma unroll
+    for (uint32_t k = 0; k < 8; ++k) {
+        const uint64_t x = x0 + k;
+        const uint32_t byte = (uint32_t)(wv >> (8u * k)) & 0xFFu;
+        if (x == a0) s_lo = (uint32_t)lp;
+        if (x >= a0 && x < a1) {
+            const uint64_t cw = tb + lp - base;
+            if (byte == 0 || cw + (uint64_t)__popc(byte) > M1) {
+                bad = true;
+            } else {
+                const uint64_t c = code[k] << 3;
+                if (!leaf) {
+                    uint64_t *dst = a.nodes + fd.noff[d + 1] + cw;
+                    for (uint32_t bits = byte; bits; bits &= bits - 1u) *dst++ = c + (uint32_t)(__ffs(bits) - 1);
+                } else {
+                    uint32_t v = fd.vstart + (uint32_t)cw;
+                    uint32_t sl = (uint32_t)lp;
+                    for (uint32_t bits = byte; bits; bits &= bits - 1u) {
+                        const uint64_t m = c + (uint32_t)(__ffs(bits) - 1);
+                        a.gap[v] = have_prev ? (uint8_t)gap_level(prev, m, 64) : (uint8_t)kInfLevel;
+                        if (stage)
+                            s_leaf[sl] = m;
+                        else if (a.pos)
+                            leaf_out(fd, a.ctab, v, m, a.pos);
+                        prev = m;
+                        have_prev = true;
+                        ++v;
+                        ++sl;
+                    }
+                }
+            }
+        }
+        lp += __popc(byte);
+        if (x + 1 == a1) {
+            if (tb + lp - base != M1) bad = true;  // the level's popcounts add up to the next level's size
+            s_hi = (uint32_t)lp;
+        }
+    }
+    if (bad) set_error(&a.st->err, kErrCorrupt);
+    if (stage && a.pos) {
+        __syncthreads();
+        const uint32_t lo = s_lo, hi = s_hi;
+        const uint64_t vb = (uint64_t)fd.vstart + tb - base;  // voxel row of staged slot i: vb + i
+        for (uint32_t i = lo + t; i < hi; i += kLevelThreads) leaf_out(fd, a.ctab, (uint32_t)(vb + i), s_leaf[i], a.pos);
+    }
+}
+
+// voxel-centre tables (Sec. 2.1), grid (x, frames): the centre table of frame blockIdx.y, entry a * 2^J + v =
 // (float)(lo_a + (v + 0.5) * cell), the same FP64 expression as per voxel
 __global__ void centre_tables_kernel(const DecFrame *fr, float *ctab)
 {
@@ -232,37 +323,6 @@ __global__ void centre_tables_kernel(const DecFrame *fr, float *ctab)
         const uint64_t v = e & (side - 1);
         const double off = __dmul_rn(__dadd_rn((double)v, 0.5), d.grid.cell);
         t[e] = (float)__dadd_rn(d.grid.lo[a], off);
-    }
-}
-
-__global__ void centres_gaps_kernel(const DecFrame *fr, uint32_t F, const uint32_t *vstart, uint64_t nv_total,
-                                    const uint64_t *__restrict__ codes, const float *__restrict__ ctab, float *pos,
-                                    uint8_t *gap)
-{
-    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= nv_total;
-         v += (uint64_t)gridDim.x * blockDim.x) {
-        if (v == nv_total) {
-            gap[v] = (uint8_t)kInfLevel;
-            continue;
-        }
-        const uint32_t f = find_frame(vstart, F, v);
-        const uint64_t m = codes[v];
-        gap[v] = (v == vstart[f]) ? (uint8_t)kInfLevel : (uint8_t)gap_level(codes[v - 1], m, 64);
-        if (pos) {
-            const DecFrame &d = fr[f];
-            if (d.ctab_off != ~0ull) {
-                const float *t = ctab + d.ctab_off;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) pos[3 * v + a] = t[((uint64_t)a << d.J) + compact3b(m >> a)];
-            } else {
-                const FrameGrid g = d.grid;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const double off = __dmul_rn(__dadd_rn((double)compact3b(m >> a), 0.5), g.cell);
-                    pos[3 * v + a] = (float)__dadd_rn(g.lo[a], off);
-                }
-            }
-        }
     }
 }
 
@@ -310,22 +370,38 @@ void launch_batch_rans_decode(const DecFrame *fr, uint32_t F, uint32_t max_chunk
     count_launch();
 }
 
-void launch_batch_roots(const DecFrame *fr, uint32_t F, uint64_t *nodes, uint64_t *codes, cudaStream_t s)
+void launch_batch_roots(const DecFrame *fr, uint32_t F, uint64_t *nodes, uint8_t *gap, uint64_t nv_total,
+                        cudaStream_t s)
 {
-    roots_kernel<<<(F + 63) / 64, 64, 0, s>>>(fr, F, nodes, codes);
+    roots_kernel<<<(F + 63) / 64, 64, 0, s>>>(fr, F, nodes, gap, nv_total);
     count_launch();
 }
 
-void launch_batch_expand(const DecFrame *fr, uint32_t F, uint32_t d, uint32_t K, const uint64_t *lvl_pref,
-                         uint64_t count,
-                         const uint8_t *occ_all, const uint32_t *pref, uint64_t *nodes, uint64_t *codes,
-                         DevState *st, int num_sms, cudaStream_t s)
+uint64_t occ_tiles(uint64_t n_occ) { return (n_occ + kOccTile - 1) / kOccTile; }
+
+void launch_occ_tile_bases(const uint8_t *occ, uint64_t n_occ, uint32_t *tsum, uint64_t *tbase, uint64_t *partials,
+                           int num_sms, cudaStream_t s)
 {
-    if (count == 0) return;
-    expand_batch_kernel<<<grid_for(count, num_sms), 256, 0, s>>>(fr, F, d, K, lvl_pref, count, occ_all, pref, nodes,
-                                                                 codes, st);
+    const uint64_t nt = occ_tiles(n_occ);
+    if (nt) {
+        const uint64_t want = (nt + 7) / 8, cap = (uint64_t)num_sms * 8;
+        occ_tile_popc_kernel<<<(uint32_t)(want < cap ? want : cap), 256, 0, s>>>(occ, n_occ, nt, tsum);
+        count_launch();
+    }
+    launch_scan_u32_to_u64(tsum, nt, tbase, partials, num_sms, s);
+}
+
+void launch_batch_level(const DecFrame *fr, uint32_t F, uint32_t d, const uint32_t *tile_pref, uint32_t tiles,
+                        const uint8_t *occ, uint64_t n_occ, const uint64_t *tbase, uint64_t *nodes, const float *ctab,
+                        float *pos, uint8_t *gap, DevState *st, cudaStream_t s)
+{
+    if (tiles == 0) return;
+    LevelArgs a{fr, F, d, tile_pref, occ, n_occ, tbase, nodes, ctab, pos, gap, st};
+    expand_level_kernel<<<tiles, kLevelThreads, 0, s>>>(a);
     count_launch();
 }
+
+uint64_t occ_tile_first(uint64_t byte) { return byte / kOccTile; }
 
 void launch_batch_centre_tables(const DecFrame *fr, uint32_t F, uint32_t Jmax, float *ctab, int num_sms,
                                 cudaStream_t s)
@@ -333,15 +409,6 @@ void launch_batch_centre_tables(const DecFrame *fr, uint32_t F, uint32_t Jmax, f
     if (F == 0) return;
     uint32_t X = grid_for(3ull << Jmax, num_sms) / F + 1;
     centre_tables_kernel<<<dim3(X, F), 256, 0, s>>>(fr, ctab);
-    count_launch();
-}
-
-void launch_batch_centres_gaps(const DecFrame *fr, uint32_t F, const uint32_t *vstart, uint64_t nv_total,
-                               const uint64_t *codes, const float *ctab, float *pos, uint8_t *gap, int num_sms,
-                               cudaStream_t s)
-{
-    centres_gaps_kernel<<<grid_for(nv_total + 1, num_sms), 256, 0, s>>>(fr, F, vstart, nv_total, codes, ctab, pos,
-                                                                         gap);
     count_launch();
 }
 
@@ -353,8 +420,4 @@ void launch_batch_block_tables(const DecFrame *fr, uint32_t F, const uint64_t *b
     count_launch();
 }
 
-}  // namespace gsnfs
-
-namespace gsnfs {
-uint32_t batch_expand_max_levels() { return (uint32_t)kExpandMaxLevels; }
 }  // namespace gsnfs

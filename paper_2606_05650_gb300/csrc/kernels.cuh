@@ -192,6 +192,7 @@ struct DecFrame {
     uint64_t ctab_off;          // first entry of the frame's centre table (3 x 2^J floats), or ~0: computed directly
     uint64_t noff[22];          // node-array offset of each level (level J lives in the voxel rows)
     uint64_t boff[22];          // offset of each level's bytes inside the frame's occupancy bytes
+    uint64_t pbase[22];         // set bits of the batch occupancy bytes before each level's first byte
     uint32_t lsz[22];
 };
 
@@ -275,23 +276,25 @@ void launch_batch_occ_bytes(const DecFrame *fr, uint32_t F, uint8_t *occ_all, ui
                             cudaStream_t s);
 void launch_batch_rans_decode(const DecFrame *fr, uint32_t F, uint32_t max_chunks_per_frame, uint32_t chunk_max,
                               uint8_t *occ_all, uint32_t *tabs, DevState *st, cudaStream_t s);
-void launch_popc_scan(const uint8_t *occ, uint64_t n, uint32_t *pref, uint32_t *partials, int num_sms,
-                      cudaStream_t s);
-// levels d .. d + K (K <= batch_expand_max_levels()) of every frame with J > d in one launch; only the last
-// level's codes are written
-uint32_t batch_expand_max_levels();
-void launch_batch_expand(const DecFrame *fr, uint32_t F, uint32_t d, uint32_t K, const uint64_t *lvl_pref, uint64_t count,
-                         const uint8_t *occ_all, const uint32_t *pref, uint64_t *nodes, uint64_t *codes,
-                         DevState *st, int num_sms, cudaStream_t s);
-void launch_batch_roots(const DecFrame *fr, uint32_t F, uint64_t *nodes, uint64_t *codes, cudaStream_t s);
+// Octree levels of every frame (Algorithm 3), one launch per level: tile popcounts of the batch occupancy
+// bytes and their exclusive scan (tbase, tiles + 1 entries), then per level the CTAs of the tiles holding
+// that level's bytes (tile_pref: F + 1 CTA offsets per frame; a frame's CTAs start at tile
+// occ_tile_first(first byte of the level)).  A frame's last level writes voxel centres and gap levels, not
+// codes.  The roots launch writes every frame's root and the gap sentinel gap[nv_total].
+uint64_t occ_tiles(uint64_t n_occ);
+uint64_t occ_tile_first(uint64_t byte);
+void launch_occ_tile_bases(const uint8_t *occ, uint64_t n_occ, uint32_t *tsum, uint64_t *tbase, uint64_t *partials,
+                           int num_sms, cudaStream_t s);
+void launch_batch_roots(const DecFrame *fr, uint32_t F, uint64_t *nodes, uint8_t *gap, uint64_t nv_total,
+                        cudaStream_t s);
+void launch_batch_level(const DecFrame *fr, uint32_t F, uint32_t d, const uint32_t *tile_pref, uint32_t tiles,
+                        const uint8_t *occ, uint64_t n_occ, const uint64_t *tbase, uint64_t *nodes, const float *ctab,
+                        float *pos, uint8_t *gap, DevState *st, cudaStream_t s);
 // Voxel-centre tables: a centre coordinate depends only on that axis' voxel
 // coordinate, so frames with 2^J <= N_v evaluate the FP64 expression once per
 // axis value (3 x 2^J) instead of once per voxel.
 void launch_batch_centre_tables(const DecFrame *fr, uint32_t F, uint32_t Jmax, float *ctab, int num_sms,
                                 cudaStream_t s);
-void launch_batch_centres_gaps(const DecFrame *fr, uint32_t F, const uint32_t *vstart, uint64_t nv_total,
-                               const uint64_t *codes, const float *ctab, float *pos, uint8_t *gap, int num_sms,
-                               cudaStream_t s);
 void launch_batch_block_tables(const DecFrame *fr, uint32_t F, const uint64_t *blk_pref, uint64_t nblk,
                                uint32_t *bw_all, int num_sms, cudaStream_t s);
 
