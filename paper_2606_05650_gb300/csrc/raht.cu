@@ -95,37 +95,53 @@ __device__ __forceinline__ int next_set(const uint32_t *mask, uint32_t i, uint32
     return r <= (int)lim ? r : -1;
 }
 
-// Builds the schedule of tile t of pass q (one CTA).
-template <int TMAX>
-__device__ void prelude_tile(const PreludeArgs &a, PreludeSmem<TMAX> &S, int q, const RahtPass &ps, uint32_t t)
+// The threads that build one tile's schedule: a whole CTA (barriers between
+// phases) or, for tiles of at most 256 elements, one warp (each warp of a CTA
+// its own tile and its own shared-memory slice, so no phase waits on the
+// CTA's other warps).
+struct CtaGroup {
+    uint32_t rank, wid;
+    static constexpr uint32_t size = kThreads, nwarps = kThreads / 32;
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+struct WarpGroup {
+    uint32_t rank, wid;  // wid = 0
+    static constexpr uint32_t size = 32, nwarps = 1;
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+};
+
+// Builds the schedule of tile t of pass q (one thread group).
+template <int TMAX, class Grp>
+__device__ void prelude_tile(const PreludeArgs &a, PreludeSmem<TMAX> &S, int q, const RahtPass &ps, uint32_t t,
+                             const Grp &G)
 {
     const RahtPlanDev &p = a.p;
     const uint32_t T = p.T;
     const uint64_t j0 = (uint64_t)t * T;
     const uint32_t m = (uint32_t)((ps.n - j0) < T ? (ps.n - j0) : T);
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t tid = G.rank, lane = threadIdx.x & 31, wid = G.wid;
     const uint32_t W = (m + 1 + 31) / 32;  // words covering positions 0..m
-    for (uint32_t i = tid; i <= m; i += kThreads) {
+    for (uint32_t i = tid; i <= m; i += Grp::size) {
         S.g[i] = seq_gap(a, ps, q, j0 + i);
         S.p[i] = seq_pos(p, ps, q, j0 + i);
         if (i < m) S.e[i] = seq_end(p, ps, q, j0 + i);
     }
-    for (int i = tid; i <= kRounds; i += kThreads) S.lvl_cnt[i] = 0;
-    __syncthreads();
+    for (int i = (int)tid; i <= kRounds; i += Grp::size) S.lvl_cnt[i] = 0;
+    G.sync();
     // range maxima of the gap levels over power-of-two windows
     constexpr int K = PreludeSmem<TMAX>::kLog;
     for (int k = 1; k < K; ++k) {
         const uint32_t half = 1u << (k - 1), span = 1u << k;
         const uint8_t *src = (k == 1) ? S.g : S.mx[k - 1];
-        for (uint32_t x = tid; x + span <= m + 1; x += kThreads) {
+        for (uint32_t x = tid; x + span <= m + 1; x += Grp::size) {
             const uint8_t u = src[x], v = src[x + half];
             S.mx[k][x] = u > v ? u : v;
         }
-        __syncthreads();
+        G.sync();
     }
     // nearest larger gap on each side (the tile's boundary gaps g[0], g[m]
     // count), by binary lifting over the range maxima
-    for (uint32_t i = tid; i < m; i += kThreads) {
+    for (uint32_t i = tid; i < m; i += Grp::size) {
         uint8_t f = 0;
         if (i > 0) {
             const uint32_t gi = S.g[i];  // < kInfLevel whenever a larger gap exists
@@ -150,9 +166,9 @@ __device__ void prelude_tile(const PreludeArgs &a, PreludeSmem<TMAX> &S, int q, 
         }
         S.inl[i] = f;
     }
-    __syncthreads();
+    G.sync();
     // survivor mask; rounds = nonempty levels in ascending order (one warp)
-    for (uint32_t w = wid; w < W; w += kThreads / 32) {
+    for (uint32_t w = wid; w < W; w += Grp::nwarps) {
         const uint32_t i = w * 32 + lane;
         const uint32_t b = __ballot_sync(0xFFFFFFFFu, i < m && !S.inl[i]);
         if (lane == 0) S.surv[w] = b;
@@ -175,12 +191,12 @@ __device__ void prelude_tile(const PreludeArgs &a, PreludeSmem<TMAX> &S, int q, 
             p.tile_nr[ps.tile_off + t] = nr;
         }
     }
-    __syncthreads();
-    for (int l = tid; l <= kRounds; l += kThreads) S.lvl_cnt[l] = 0;  // reused as fill counters
-    __syncthreads();
+    G.sync();
+    for (int l = (int)tid; l <= kRounds; l += Grp::size) S.lvl_cnt[l] = 0;  // reused as fill counters
+    G.sync();
     // butterflies, destinations, frame roots; carried survivors marked in S.inl (2)
     const uint64_t sbase = (uint64_t)(ps.tile_off + t) * T;
-    for (uint32_t i = tid; i < m; i += kThreads) {
+    for (uint32_t i = tid; i < m; i += Grp::size) {
         if (S.inl[i]) {
             // children cover elements [l, i) and [i, r); neither range crosses a frame
             // boundary, so their voxels are contiguous.  The right end is taken from
@@ -207,14 +223,14 @@ __device__ void prelude_tile(const PreludeArgs &a, PreludeSmem<TMAX> &S, int q, 
             }
         }
     }
-    __syncthreads();
+    G.sync();
     // local carried ranks: popcounts of the carried mask
-    for (uint32_t w = wid; w < W; w += kThreads / 32) {
+    for (uint32_t w = wid; w < W; w += Grp::nwarps) {
         const uint32_t i = w * 32 + lane;
         const uint32_t b = __ballot_sync(0xFFFFFFFFu, i < m && S.inl[i] == 2);
         if (lane == 0) S.carry[w] = b;
     }
-    __syncthreads();
+    G.sync();
     if (wid == 0) {
         uint32_t run = 0;
         for (uint32_t base = 0; base < W; base += 32) {
@@ -226,14 +242,14 @@ __device__ void prelude_tile(const PreludeArgs &a, PreludeSmem<TMAX> &S, int q, 
         }
         if (lane == 0) p.tile_carry[ps.tile_off + t] = run;
     }
-    __syncthreads();
-    for (uint32_t i = tid; i < m; i += kThreads)
+    G.sync();
+    for (uint32_t i = tid; i < m; i += Grp::size)
         if (S.inl[i] == 2) {
             const uint32_t w = i >> 5;
             const uint32_t rank = S.cpre[w] + __popc(S.carry[w] & ((1u << (i & 31)) - 1u));
             p.dest[ps.seq_off + j0 + i] = kCarry | rank;
         }
-    __syncthreads();
+    G.sync();
 }
 
 __global__ void __launch_bounds__(kThreads) prelude_init_kernel(RahtPlanDev p, const DevState *st,
@@ -252,13 +268,32 @@ __global__ void __launch_bounds__(kThreads) prelude_init_kernel(RahtPlanDev p, c
     }
 }
 
+// tiles of at most 256 elements: one warp per tile; larger tiles: one CTA per tile
+template <int TMAX>
+constexpr bool kWarpTiles = TMAX <= 256;
+
+template <int TMAX>
+constexpr size_t prelude_smem_bytes()
+{
+    return (kWarpTiles<TMAX> ? (size_t)(kThreads / 32) : (size_t)1) * sizeof(PreludeSmem<TMAX>);
+}
+
 template <int TMAX>
 __global__ void __launch_bounds__(kThreads) prelude_tiles_kernel(PreludeArgs a, int q)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PreludeSmem<TMAX> &S = *reinterpret_cast<PreludeSmem<TMAX> *>(smem_raw);
     const RahtPass ps = a.p.passes[q];
-    for (uint32_t t = blockIdx.x; t < ps.ntiles; t += gridDim.x) prelude_tile(a, S, q, ps, t);
+    if constexpr (kWarpTiles<TMAX>) {
+        const uint32_t wid = threadIdx.x >> 5;
+        PreludeSmem<TMAX> &S = reinterpret_cast<PreludeSmem<TMAX> *>(smem_raw)[wid];
+        const WarpGroup G{threadIdx.x & 31u, 0u};
+        const uint32_t nw = gridDim.x * (kThreads / 32);
+        for (uint32_t t = blockIdx.x * (kThreads / 32) + wid; t < ps.ntiles; t += nw) prelude_tile(a, S, q, ps, t, G);
+    } else {
+        PreludeSmem<TMAX> &S = *reinterpret_cast<PreludeSmem<TMAX> *>(smem_raw);
+        const CtaGroup G{threadIdx.x, threadIdx.x >> 5};
+        for (uint32_t t = blockIdx.x; t < ps.ntiles; t += gridDim.x) prelude_tile(a, S, q, ps, t, G);
+    }
 }
 
 // one CTA: exclusive scan of carried counts over the pass's tiles, next pass
@@ -339,13 +374,20 @@ template <int TMAX>
 __global__ void __launch_bounds__(kThreads) prelude_finish_kernel(PreludeArgs a, int q0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PreludeSmem<TMAX> &S = *reinterpret_cast<PreludeSmem<TMAX> *>(smem_raw);
+    PreludeSmem<TMAX> *S = reinterpret_cast<PreludeSmem<TMAX> *>(smem_raw);
     for (int q = q0; q + 1 < kRahtMaxPasses; ++q) {
         const RahtPass ps = a.p.passes[q];
         if (ps.n == 0) break;
-        for (uint32_t t = 0; t < ps.ntiles; ++t) prelude_tile(a, S, q, ps, t);
+        if constexpr (kWarpTiles<TMAX>) {
+            const uint32_t wid = threadIdx.x >> 5;
+            const WarpGroup G{threadIdx.x & 31u, 0u};
+            for (uint32_t t = wid; t < ps.ntiles; t += kThreads / 32) prelude_tile(a, S[wid], q, ps, t, G);
+        } else {
+            const CtaGroup G{threadIdx.x, threadIdx.x >> 5};
+            for (uint32_t t = 0; t < ps.ntiles; ++t) prelude_tile(a, S[0], q, ps, t, G);
+        }
         __syncthreads();
-        prelude_scan_body(a.p, q, S.scan);
+        prelude_scan_body(a.p, q, S[0].scan);
         __syncthreads();
         prelude_compact_body(a, q, threadIdx.x, kThreads);
         __syncthreads();
@@ -1326,7 +1368,7 @@ template <int TMAX>
 void prelude_launches(const PreludeArgs &a, const RahtPlanDev &p, const DevState *st, const uint64_t *nv_dev,
                       int num_sms, cudaStream_t s)
 {
-    const size_t smem = sizeof(PreludeSmem<TMAX>);
+    const size_t smem = prelude_smem_bytes<TMAX>();
     cudaFuncSetAttribute(prelude_tiles_kernel<TMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(prelude_finish_kernel<TMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     prelude_init_kernel<<<1, 32, 0, s>>>(p, st, nv_dev);
