@@ -203,13 +203,16 @@ struct LevelArgs {
     DevState *st;
 };
 
-// A CTA of kLevelThreads threads takes one tile, 8 bytes (nodes) per thread.
-// Internal level: children codes go straight to the next level.  Leaf level:
-// gap levels are written as the children are formed, and the children's
-// codes are staged in shared memory (at their rank among the tile's set bits)
-// so that the centres are computed afterwards one child per thread, with
-// independent table loads and coalesced stores (a tile with more set bits
-// than the stage holds writes its centres directly).
+// A CTA of kLevelThreads threads takes one tile.  Its bytes are loaded 8 per
+// thread and their set bits scanned; the per-byte prefixes go to shared
+// memory, and the nodes are then taken strided (node j of the tile by thread
+// j mod kLevelThreads), so that code loads and child stores of consecutive
+// threads are consecutive.  Internal level: children codes go straight to
+// the next level.  Leaf level: the children's codes are staged in shared
+// memory at their rank among the tile's set bits, then one child per thread
+// gets its gap level (from the staged code before it) and its centre, with
+// coalesced stores (a tile with more set bits than the stage holds writes its
+// voxels directly).
 constexpr uint32_t kLevelThreads = kOccTile / 8;
 constexpr uint32_t kLeafStage = 2048;
 
@@ -221,37 +224,53 @@ __device__ __forceinline__ uint64_t word8_at(const uint8_t *occ, uint64_t n, uin
     return v;
 }
 
+// the last child's code of node w (byte b) of a level, shifted to the next level
+__device__ __forceinline__ uint64_t last_child(uint64_t code, uint32_t b)
+{
+    return (code << 3) + (b ? 31u - (uint32_t)__clz(b) : 0u);
+}
+
 __global__ void __launch_bounds__(kLevelThreads) expand_level_kernel(LevelArgs a)
 {
     __shared__ uint64_t sh[33];
     __shared__ uint64_t s_leaf[kLeafStage];
+    __shared__ uint16_t s_pref[kOccTile];
+    __shared__ uint8_t s_occ[kOccTile];
     __shared__ uint32_t s_lo, s_hi;
+    __shared__ uint64_t s_prev;
+    __shared__ int s_first;  // the tile holds the level's first node (its first voxel starts a frame)
     const uint32_t g = blockIdx.x, t = threadIdx.x;
     const uint32_t f = find_frame(a.tile_pref, a.F, g);
     const DecFrame &fd = a.fr[f];
     const uint32_t d = a.d;
     const uint64_t a0 = fd.occ_off + fd.boff[d], a1 = a0 + fd.lsz[d];
     const uint64_t tile = a0 / kOccTile + (g - a.tile_pref[f]);
-    const uint64_t x0 = tile * kOccTile + 8ull * t;
-    const uint64_t wv = word8_at(a.occ, a.n_occ, x0);
+    const uint64_t tx = tile * kOccTile;
     const bool leaf = d + 1 == fd.J;
     const uint64_t *src = a.nodes + fd.noff[d];
-    // this thread's nodes' codes (and, at a leaf level, the node before its first) are loaded before the
-    // scan, so that their latency overlaps it
+    const uint64_t wv = word8_at(a.occ, a.n_occ, tx + 8ull * t);
+    // the codes of this thread's nodes (tile bytes t, t + 128, ...) are loaded before the scan
     uint64_t code[8];
 #pragma unroll
-    for (uint32_t k = 0; k < 8; ++k) code[k] = (x0 + k >= a0 && x0 + k < a1) ? src[x0 + k - a0] : 0ull;
-    const uint64_t xf = x0 > a0 ? x0 : a0;  // first byte of the level in this thread's word
-    bool have_prev = false;
-    uint64_t prev = 0;
-    if (leaf && xf > a0 && xf < x0 + 8 && xf < a1) {  // the voxel before: the last child of node xf - 1 - a0
-        const uint32_t pb = a.occ[xf - 1];
-        prev = (src[xf - 1 - a0] << 3) + (pb ? 31u - (uint32_t)__clz(pb) : 0u);
-        have_prev = true;
+    for (uint32_t k = 0; k < 8; ++k) {
+        const uint64_t x = tx + k * kLevelThreads + t;
+        code[k] = (x >= a0 && x < a1) ? src[x - a0] : 0ull;
+    }
+    const uint64_t xs = tx > a0 ? tx : a0;  // the tile's first byte of this level
+    if (t == 0) {
+        s_first = xs == a0;
+        s_prev = (leaf && xs > a0 && xs < a1) ? last_child(src[xs - 1 - a0], a.occ[xs - 1]) : 0ull;
     }
     const uint64_t tb = a.tbase[tile];
     uint64_t tot;
-    const uint64_t lp0 = block_exclusive_sum<uint64_t>((uint64_t)__popcll(wv), sh, &tot);  // P(x0) - tb
+    uint32_t lp = (uint32_t)block_exclusive_sum<uint64_t>((uint64_t)__popcll(wv), sh, &tot);
+#pragma unroll
+    for (uint32_t k = 0; k < 8; ++k) {  // per byte: set bits of the tile before it
+        const uint32_t b = (uint32_t)(wv >> (8u * k)) & 0xFFu;
+        s_pref[8 * t + k] = (uint16_t)lp;
+        s_occ[8 * t + k] = (uint8_t)b;
+        lp += __popc(b);
+    }
     const uint64_t base = fd.pbase[d];
     const uint32_t M1 = fd.lsz[d + 1];
     const bool stage = leaf && tot <= kLeafStage;
@@ -260,52 +279,57 @@ __global__ void __launch_bounds__(kLevelThreads) expand_level_kernel(LevelArgs a
         s_hi = (uint32_t)tot;
     }
     __syncthreads();
-    uint64_t lp = lp0;  // set bits of the tile before byte x
     bool bad = false;
 #pragma unroll
     for (uint32_t k = 0; k < 8; ++k) {
-        const uint64_t x = x0 + k;
-        const uint32_t byte = (uint32_t)(wv >> (8u * k)) & 0xFFu;
-        if (x == a0) s_lo = (uint32_t)lp;
-        if (x >= a0 && x < a1) {
-            const uint64_t cw = tb + lp - base;
-            if (byte == 0 || cw + (uint64_t)__popc(byte) > M1) {
-                bad = true;
-            } else {
-                const uint64_t c = code[k] << 3;
-                if (!leaf) {
-                    uint64_t *dst = a.nodes + fd.noff[d + 1] + cw;
-                    for (uint32_t bits = byte; bits; bits &= bits - 1u) *dst++ = c + (uint32_t)(__ffs(bits) - 1);
-                } else {
-                    uint32_t v = fd.vstart + (uint32_t)cw;
-                    uint32_t sl = (uint32_t)lp;
-                    for (uint32_t bits = byte; bits; bits &= bits - 1u) {
-                        const uint64_t m = c + (uint32_t)(__ffs(bits) - 1);
-                        a.gap[v] = have_prev ? (uint8_t)gap_level(prev, m, 64) : (uint8_t)kInfLevel;
-                        if (stage)
-                            s_leaf[sl] = m;
-                        else if (a.pos)
-                            leaf_out(fd, a.ctab, v, m, a.pos);
-                        prev = m;
-                        have_prev = true;
-                        ++v;
-                        ++sl;
-                    }
-                }
-            }
-        }
-        lp += __popc(byte);
+        const uint32_t j = k * kLevelThreads + t;
+        const uint64_t x = tx + j;
+        if (x < a0 || x >= a1) continue;
+        const uint32_t byte = s_occ[j];
+        const uint32_t pj = s_pref[j];
+        if (x == a0) s_lo = pj;
         if (x + 1 == a1) {
-            if (tb + lp - base != M1) bad = true;  // the level's popcounts add up to the next level's size
-            s_hi = (uint32_t)lp;
+            if (tb + pj + __popc(byte) - base != M1) bad = true;  // the level's popcounts add up to the next level
+            s_hi = pj + __popc(byte);
+        }
+        const uint64_t cw = tb + pj - base;
+        if (byte == 0 || cw + (uint64_t)__popc(byte) > M1) {
+            bad = true;
+            continue;
+        }
+        const uint64_t c = code[k] << 3;
+        if (!leaf) {
+            uint64_t *dst = a.nodes + fd.noff[d + 1] + cw;
+            for (uint32_t bits = byte; bits; bits &= bits - 1u) *dst++ = c + (uint32_t)(__ffs(bits) - 1);
+        } else if (stage) {
+            uint32_t sl = pj;
+            for (uint32_t bits = byte; bits; bits &= bits - 1u) s_leaf[sl++] = c + (uint32_t)(__ffs(bits) - 1);
+        } else {  // unstaged voxels: the one before comes from node x - 1
+            uint32_t v = fd.vstart + (uint32_t)cw;
+            bool have_prev = x > a0;
+            uint64_t prev = have_prev ? last_child(src[x - 1 - a0], x > tx ? s_occ[j - 1] : a.occ[x - 1]) : 0ull;
+            for (uint32_t bits = byte; bits; bits &= bits - 1u) {
+                const uint64_t m = c + (uint32_t)(__ffs(bits) - 1);
+                a.gap[v] = have_prev ? (uint8_t)gap_level(prev, m, 64) : (uint8_t)kInfLevel;
+                if (a.pos) leaf_out(fd, a.ctab, v, m, a.pos);
+                prev = m;
+                have_prev = true;
+                ++v;
+            }
         }
     }
     if (bad) set_error(&a.st->err, kErrCorrupt);
-    if (stage && a.pos) {
+    if (stage) {
         __syncthreads();
         const uint32_t lo = s_lo, hi = s_hi;
         const uint64_t vb = (uint64_t)fd.vstart + tb - base;  // voxel row of staged slot i: vb + i
-        for (uint32_t i = lo + t; i < hi; i += kLevelThreads) leaf_out(fd, a.ctab, (uint32_t)(vb + i), s_leaf[i], a.pos);
+        for (uint32_t i = lo + t; i < hi; i += kLevelThreads) {
+            const uint64_t m = s_leaf[i];
+            const uint32_t v = (uint32_t)(vb + i);
+            a.gap[v] = (i > lo) ? (uint8_t)gap_level(s_leaf[i - 1], m, 64)
+                                : (s_first ? (uint8_t)kInfLevel : (uint8_t)gap_level(s_prev, m, 64));
+            if (a.pos) leaf_out(fd, a.ctab, v, m, a.pos);
+        }
     }
 }
 
