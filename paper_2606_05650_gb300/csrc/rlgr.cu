@@ -71,6 +71,13 @@ __device__ __forceinline__ int32_t unzz(uint32_t u)
     return (u & 1u) ? -(int32_t)(u >> 1) - 1 : (int32_t)(u >> 1);
 }
 
+__device__ __forceinline__ void adapt_kr(uint32_t p, int &KR)
+{
+    // p = 0: KR - 2, p = 1: unchanged, p > 1: KR + p + 1; within [0, 384]
+    const int d = p >= 2u ? (int)(p > 384u ? 384u : p) + 1 : (p == 1u ? 0 : -2);
+    KR = min(max(KR + d, 0), 384);
+}
+
 __device__ __forceinline__ void gr_put(BitWriter &bw, uint32_t v, uint32_t k, int &KR)
 {
     const uint32_t p = v >> k;
@@ -88,12 +95,7 @@ __device__ __forceinline__ void gr_put(BitWriter &bw, uint32_t v, uint32_t k, in
         bw.put(n, 6);
         bw.put(v, n);
     }
-    if (p == 0) {
-        KR = KR >= 2 ? KR - 2 : 0;
-    } else if (p > 1) {
-        uint32_t t = (uint32_t)KR + (p > 384u ? 384u : p) + 1u;
-        KR = t > 384u ? 384 : (int)t;
-    }
+    adapt_kr(p, KR);
 }
 
 // Streaming RLGR coder state of one block.
@@ -288,12 +290,6 @@ struct WinReader {
     }
 };
 
-__device__ __forceinline__ void adapt_kr(uint32_t p, int &KR)
-{
-    // p = 0: KR - 2, p = 1: unchanged, p > 1: KR + p + 1; within [0, 384]
-    const int d = p >= 2u ? (int)(p > 384u ? 384u : p) + 1 : (p == 1u ? 0 : -2);
-    KR = min(max(KR + d, 0), 384);
-}
 
 // Rare path of gr_read: the remainder crosses the window, or the escape code.
 __device__ __forceinline__ uint32_t gr_read_slow(WinReader &r, uint32_t k, uint32_t p, bool &bad)
