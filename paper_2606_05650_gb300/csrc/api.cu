@@ -711,6 +711,7 @@ void carve_plan(Carve &cv, RahtPlanDev &p, uint64_t nv_cap, uint32_t T, const ui
     p.bf_ab = cv.take<float2>(tiles * T);
     p.bf_w = nullptr;
     p.tile_carry = cv.take<uint32_t>(tiles);
+    p.carry_list = cv.take<uint16_t>(tiles * kRahtCarrySlots);
     p.passes = cv.take<RahtPass>(kRahtMaxPasses + 1);
     p.npasses = cv.take<uint32_t>(1);
     p.pos0 = nullptr;

@@ -95,6 +95,8 @@ void launch_voxel_centres_batch(const uint64_t *codes, const DevState *st, uint6
                                 cudaStream_t s);
 
 // ---- raht.cu: prelude and tile transforms (Sec. 3, Algorithms 4-6) -------
+constexpr uint32_t kRahtCarrySlots = 128;  // survivors of a tile: at most 2 x 64 (strictly rising gap levels
+                                           // from either tile edge)
 constexpr int kRahtMultiPasses = 3;  // passes launched grid-wide; the rest run in one CTA
 constexpr int kRahtMaxPasses = 40;
 
@@ -127,6 +129,7 @@ struct RahtPlanDev {  // device pointers of a plan
     float2 *bf_ab;         // per tile x T: FP32 coefficients (a, b)
     uint2 *bf_w;           // per tile x T: integer weights (w0, w1), or null (not recorded)
     uint32_t *tile_carry;  // per tile carried count, then exclusive base
+    uint16_t *carry_list;  // per tile x kRahtCarrySlots: in-tile index of each carried survivor, by rank
     RahtPass *passes;      // kRahtMaxPasses
     uint32_t *npasses;     // device counter
     // pass 0 elements: first voxel and one past the last voxel of element j, or null when element j is voxel j

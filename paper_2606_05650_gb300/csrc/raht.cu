@@ -248,6 +248,7 @@ __device__ void prelude_tile(const PreludeArgs &a, PreludeSmem<TMAX> &S, int q, 
             const uint32_t w = i >> 5;
             const uint32_t rank = S.cpre[w] + __popc(S.carry[w] & ((1u << (i & 31)) - 1u));
             p.dest[ps.seq_off + j0 + i] = kCarry | rank;
+            if (rank < kRahtCarrySlots) p.carry_list[(uint64_t)(ps.tile_off + t) * kRahtCarrySlots + rank] = (uint16_t)i;
         }
     G.sync();
 }
@@ -331,33 +332,30 @@ __global__ void __launch_bounds__(1024) prelude_scan_kernel(RahtPlanDev p, int q
     prelude_scan_body(p, q, sh);
 }
 
-// carried elements: global index, next sequence arrays, sentinel
-__device__ void prelude_compact_body(const PreludeArgs &a, int q, uint64_t first, uint64_t stride)
+// carried elements: global index, next sequence arrays, sentinel.  A warp
+// per tile walks the tile's list of carried survivors (their global index is
+// the tile's scanned base plus their rank), so elements that are not carried
+// are never read.
+__device__ void prelude_compact_body(const PreludeArgs &a, int q, uint32_t warp0, uint32_t nwarps)
 {
     const RahtPlanDev &p = a.p;
     const RahtPass ps = p.passes[q];
     const RahtPass nx = p.passes[q + 1];
-    constexpr int U = 4;  // elements per thread in flight (their loads are independent)
-    for (uint64_t j0 = first; j0 < ps.n; j0 += U * stride) {
-        uint32_t d[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint64_t j = j0 + u * stride;
-            d[u] = j < ps.n ? p.dest[ps.seq_off + j] : 0u;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint64_t j = j0 + u * stride;
-            if (j < ps.n && (d[u] & kCarry)) {
-                uint32_t gi = p.tile_carry[ps.tile_off + (uint32_t)(j / p.T)] + (d[u] & ~kCarry);
-                p.dest[ps.seq_off + j] = kCarry | gi;
-                p.pos[nx.seq_off + gi] = seq_pos(p, ps, q, j);
-                p.gapseq[nx.seq_off + gi] = seq_gap(a, ps, q, j);
-                p.endseq[nx.seq_off + gi] = p.send[ps.seq_off + j];
-            }
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t t = warp0; t < ps.ntiles; t += nwarps) {
+        const uint32_t b0 = p.tile_carry[ps.tile_off + t];
+        const uint32_t b1 = t + 1 < ps.ntiles ? p.tile_carry[ps.tile_off + t + 1] : nx.n;
+        for (uint32_t r = lane; r < b1 - b0 && r < kRahtCarrySlots; r += 32) {
+            const uint32_t i = p.carry_list[(uint64_t)(ps.tile_off + t) * kRahtCarrySlots + r];
+            const uint64_t j = (uint64_t)t * p.T + i;
+            const uint32_t gi = b0 + r;
+            p.dest[ps.seq_off + j] = kCarry | gi;
+            p.pos[nx.seq_off + gi] = seq_pos(p, ps, q, j);
+            p.gapseq[nx.seq_off + gi] = seq_gap(a, ps, q, j);
+            p.endseq[nx.seq_off + gi] = p.send[ps.seq_off + j];
         }
     }
-    if (first == 0 && nx.n) {
+    if (warp0 == 0 && lane == 0 && nx.n) {
         p.pos[nx.seq_off + nx.n] = seq_pos(p, ps, q, ps.n);
         p.gapseq[nx.seq_off + nx.n] = (uint8_t)kInfLevel;
     }
@@ -366,7 +364,7 @@ __device__ void prelude_compact_body(const PreludeArgs &a, int q, uint64_t first
 __global__ void __launch_bounds__(kThreads) prelude_compact_kernel(PreludeArgs a, int q)
 {
     if (a.p.passes[q].n == 0 || q + 1 >= kRahtMaxPasses) return;
-    prelude_compact_body(a, q, (uint64_t)blockIdx.x * kThreads + threadIdx.x, (uint64_t)gridDim.x * kThreads);
+    prelude_compact_body(a, q, blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5), gridDim.x * (kThreads / 32));
 }
 
 // remaining passes inside one CTA
@@ -389,7 +387,7 @@ __global__ void __launch_bounds__(kThreads) prelude_finish_kernel(PreludeArgs a,
         __syncthreads();
         prelude_scan_body(a.p, q, S[0].scan);
         __syncthreads();
-        prelude_compact_body(a, q, threadIdx.x, kThreads);
+        prelude_compact_body(a, q, threadIdx.x >> 5, kThreads / 32);
         __syncthreads();
     }
 }
