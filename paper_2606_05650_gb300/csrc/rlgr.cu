@@ -122,8 +122,7 @@ struct Rlgr {
                 z = 0;
             }
         } else {
-            bw.put(1, 1);
-            bw.put(z, k);
+            bw.put(1u | (z << 1), 1u + k);  // bit 1, then the run length in k bits (z < 2^k, k <= 15)
             gr_put(bw, u - 1u, (uint32_t)KR >> 4, KR);
             K = K >= 6 ? K - 6 : 0;
             z = 0;
