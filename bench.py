@@ -503,7 +503,7 @@ def gpu_extras(args, G, torch, P, A, frames, qp, out, offs, dev, stream):
     s0 = out[int(offs[0]):int(offs[1])].clone()
     lod = {}
     for depth in (J, 12, 8):
-        t = _timed_calls(torch, stream, lambda _=0: G.decode_frame_lod(s0, depth), 3)
+        t = _timed_calls(torch, stream, lambda _=0: G.decode_frame_lod(s0, depth), 10)
         n_nodes = G.decode_frame_lod(s0, depth)[0].shape[0]
         lod[str(depth)] = {"ms": round(statistics.median(t), 3), "nodes": int(n_nodes)}
     res["lod_decode"] = lod

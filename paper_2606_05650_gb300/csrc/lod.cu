@@ -112,10 +112,12 @@ void launch_lod_means(const float *low, const uint64_t *codes, const uint64_t *s
 {
     const uint32_t cw = C > 3 ? C : 3;                        // threads per node row
     const uint32_t ny = cw >= 256 ? 1u : 256u / cw;               // node rows per block
+    // one node row per thread row and no grid-stride loop: every row's loads are in flight at once (a capped
+    // grid walking the rows in turn was bound by one load latency per row)
     uint64_t blocks = (n_nodes + ny - 1) / ny;
-    const uint64_t cap = (uint64_t)num_sms * 16;
-    if (blocks > cap) blocks = cap;
+    if (blocks > 0x7FFFFFFFull) blocks = 0x7FFFFFFFull;
     if (blocks < 1) blocks = 1;
+    (void)num_sms;
     lod_means_kernel<<<(uint32_t)blocks, dim3(cw, ny), 0, s>>>(low, codes, starts, n_nodes_dev, sh, Jp, C, g, pos,
                                                                out);
     count_launch();
