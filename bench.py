@@ -51,11 +51,12 @@ SEQ_FRAMES = 30  # of the 300-frame sequence, every 10th
 # summaries under profiles/), with the SHA-1 of the kernel's source file at
 # capture time: reported only while that file is unchanged.
 TRAFFIC = {
-    "raht_forward_pass0": (528.76e6, "csrc/raht.cu", "7da8d1eb969f8c7ab378523f92de0bb1e9ebc717"),
-    "rlgr_encode": (276.61e6, "csrc/rlgr.cu", "aeb4737a320d440723cbe31e6bc344aa2e6e76c0"),
-    "rlgr_decode": (253.82e6, "csrc/rlgr.cu", "aeb4737a320d440723cbe31e6bc344aa2e6e76c0"),
+    "raht_forward_pass0": (521.18e6, "csrc/raht.cu", "fcf37cc9814fbded9145f425903bbdfe3a4b0724"),
+    "raht_inverse_pass0": (441.18e6, "csrc/raht.cu", "fcf37cc9814fbded9145f425903bbdfe3a4b0724"),
+    "rlgr_encode": (278.79e6, "csrc/rlgr.cu", "4e2e1fc2ff5a6d4b5b09d83a4d1bd52db792c215"),
+    "rlgr_decode": (253.11e6, "csrc/rlgr.cu", "4e2e1fc2ff5a6d4b5b09d83a4d1bd52db792c215"),
 }
-# largest share of serialised GPU time in the ncu launch list of the headline workload (13.6% of the timed steps)
+# largest share of serialised GPU time in the ncu launch list of the headline workload (16.5% of the timed steps)
 DOMINANT = "raht_forward_pass0"
 
 
@@ -70,6 +71,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip plain-path, e2e and CPU-baseline legs")
     ap.add_argument("--no-tune", action="store_true", help="built-in launch shapes instead of autotuning them "
                                                             "(short profiling runs)")
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                    help="replay the headline encoder's device work as a CUDA graph (captured once per request "
+                         "shape during the warm-up steps)")
     ap.add_argument("--workload", default="headline", choices=["headline", "ladder", "sequence", "pointcloud",
                                                                  "blocksweep"],
                     help="other workloads, each printing its own JSON line: ladder (64 frames of 50k-2M Gaussians x "
@@ -274,6 +278,7 @@ def run_gpu(args):
     from paper_2606_05650_gb300 import autotune
     tuning = ({"params": "built-in", "ms": None, "default_ms": None} if args.no_tune else
               autotune.tune_round_trip(P, A, Js, qp, use_cache=False))
+    G.set_graphs(bool(args.graphs))
     for _ in range(max(args.warmup, 1)):
         offs, rows = step()
     torch.cuda.synchronize()
@@ -325,7 +330,8 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": headline_config(F, args.block, world),
-            "path": "batched: one encode call and one decode call per step for all frames of the rank",
+            "path": "batched: one encode call and one decode call per step for all frames of the rank"
+                    + ("; encoder replayed as a CUDA graph" if args.graphs else ""),
             "tuning": {"params": tuning["params"], "tuned_ms": tuning["ms"], "default_ms": tuning["default_ms"]},
             "encode_decode_fps": round(value, 2),
             "voxels_per_frame": int(nv_frames.mean()), "bytes_per_frame": int(stream_bytes.mean()),

@@ -66,9 +66,12 @@ const char *kStageNames[kStCount] = {"voxelize", "sort", "dedup", "occupancy", "
 }  // namespace
 
 // While a call is being captured into a CUDA graph, its launches are counted
-// into the graph (and added to the total at every replay) and stage events are
-// not recorded.
+// into the graph (and added to the total at every replay), and its stage
+// events become event-record nodes of the graph (events of their own, read
+// after every replay while profiling is on).
 thread_local uint64_t *t_capture_launches = nullptr;
+thread_local std::vector<Profiler::Rec> *t_capture_stages = nullptr;
+thread_local std::vector<Profiler::Rec> t_capture_open;
 
 namespace gsnfs {
 void count_launch()
@@ -80,6 +83,14 @@ void count_launch()
 }
 void stage_begin(cudaStream_t s, int id)
 {
+    if (t_capture_stages) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) == cudaSuccess && cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) == cudaSuccess)
+            t_capture_open.push_back({id, e, nullptr});
+        else if (e)
+            cudaEventDestroy(e);
+        return;
+    }
     if (!g_prof.on || t_capture_launches) return;
     std::lock_guard<std::mutex> lk(g_prof.mu);
     cudaEvent_t e = g_prof.get();
@@ -88,6 +99,22 @@ void stage_begin(cudaStream_t s, int id)
 }
 void stage_end(cudaStream_t s, int id)
 {
+    if (t_capture_stages) {
+        for (size_t k = t_capture_open.size(); k-- > 0;) {
+            if (t_capture_open[k].id != id) continue;
+            Profiler::Rec r = t_capture_open[k];
+            t_capture_open.erase(t_capture_open.begin() + (long)k);
+            if (cudaEventCreate(&r.b) == cudaSuccess &&
+                cudaEventRecordWithFlags(r.b, s, cudaEventRecordExternal) == cudaSuccess) {
+                t_capture_stages->push_back(r);
+            } else {
+                cudaEventDestroy(r.a);
+                if (r.b) cudaEventDestroy(r.b);
+            }
+            break;
+        }
+        return;
+    }
     if (!g_prof.on || t_capture_launches) return;
     std::lock_guard<std::mutex> lk(g_prof.mu);
     if (g_prof.open[id].empty()) return;
@@ -106,7 +133,33 @@ struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     uint64_t launches = 0;  // kernels in the graph
     uint64_t last_use = 0;
+    std::vector<Profiler::Rec> stages;  // stage events recorded by the graph (owned)
 };
+
+void destroy_graph(GraphEntry &g)
+{
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    for (auto &r : g.stages) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g.stages.clear();
+}
+
+// After a replay has completed: its stage times, while profiling is on.
+void add_graph_stage_times(const std::vector<Profiler::Rec> &stages)
+{
+    if (!g_prof.on) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    for (const auto &r : stages) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            g_prof.ms[r.id] += t;
+            g_prof.cnt[r.id] += 1;
+        }
+    }
+}
 
 struct gsnfs_ctx {
     int device = 0;
@@ -205,8 +258,7 @@ struct Carve {
 // Captured graphs hold arena and staging addresses: drop them when either moves.
 void drop_graphs(gsnfs_ctx *ctx)
 {
-    for (auto &g : ctx->gcache)
-        if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto &g : ctx->gcache) destroy_graph(g);
     ctx->gcache.clear();
 }
 
@@ -810,7 +862,8 @@ constexpr size_t kGraphCacheSize = 64;
 // by one event and joined back by another.  A capture that fails runs the
 // work eagerly instead (counted in gfailures).
 template <typename Enqueue>
-gsnfs_status run_graphed(gsnfs_ctx *ctx, cudaStream_t s, std::vector<uint64_t> key, Enqueue &enqueue)
+gsnfs_status run_graphed(gsnfs_ctx *ctx, cudaStream_t s, std::vector<uint64_t> key, Enqueue &enqueue,
+                         std::vector<Profiler::Rec> *stages_out)
 {
     if (!ctx->gstream) {
         CK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
@@ -822,16 +875,27 @@ gsnfs_status run_graphed(gsnfs_ctx *ctx, cudaStream_t s, std::vector<uint64_t> k
         if (g.key == key) hit = &g;
     if (!hit) {
         uint64_t launches = 0;
+        std::vector<Profiler::Rec> stages;
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal));
         t_capture_launches = &launches;
+        t_capture_stages = &stages;
+        t_capture_open.clear();
         gsnfs_status st = enqueue(ctx->gstream);
         t_capture_launches = nullptr;
+        t_capture_stages = nullptr;
+        for (auto &r : t_capture_open) cudaEventDestroy(r.a);  // a stage left open: not timed
+        t_capture_open.clear();
         cudaError_t e = cudaStreamEndCapture(ctx->gstream, &graph);
         cudaGraphExec_t exec = nullptr;
-        if (st == GSNFS_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
+        if (st == GSNFS_OK && e == cudaSuccess && graph)
+            e = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
         if (graph) cudaGraphDestroy(graph);
         if (st != GSNFS_OK || e != cudaSuccess || !exec) {
+            for (auto &r : stages) {
+                cudaEventDestroy(r.a);
+                cudaEventDestroy(r.b);
+            }
             cudaGetLastError();
             ++ctx->gfailures;
             return enqueue(s);
@@ -839,10 +903,10 @@ gsnfs_status run_graphed(gsnfs_ctx *ctx, cudaStream_t s, std::vector<uint64_t> k
         if (ctx->gcache.size() >= kGraphCacheSize) {
             auto lru = std::min_element(ctx->gcache.begin(), ctx->gcache.end(),
                                         [](const GraphEntry &a, const GraphEntry &b) { return a.last_use < b.last_use; });
-            cudaGraphExecDestroy(lru->exec);
+            destroy_graph(*lru);
             ctx->gcache.erase(lru);
         }
-        ctx->gcache.push_back(GraphEntry{std::move(key), exec, launches, 0});
+        ctx->gcache.push_back(GraphEntry{std::move(key), exec, launches, 0, std::move(stages)});
         hit = &ctx->gcache.back();
         ++ctx->gcaptures;
     } else {
@@ -855,6 +919,7 @@ gsnfs_status run_graphed(gsnfs_ctx *ctx, cudaStream_t s, std::vector<uint64_t> k
     CK(cudaEventRecord(ctx->gev_out, ctx->gstream));
     CK(cudaStreamWaitEvent(s, ctx->gev_out, 0));
     g_launches.fetch_add(hit->launches, std::memory_order_relaxed);
+    if (stages_out) *stages_out = hit->stages;
     return GSNFS_OK;
 }
 
@@ -1102,6 +1167,7 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
         if (dist_bytes) CK(stage_copy(hp + o_dist, L.sq_err, dist_bytes, s));
         return GSNFS_OK;
     };
+    std::vector<Profiler::Rec> gstages;  // the replayed graph's stage events
     if (ctx->graphs) {
         std::vector<uint64_t> key = {F, R, C, G, C ? q->rlgr_block : 0u, q->rans_chunk, 0, rq.capacity,
                                      (uint64_t)(uintptr_t)rq.out, (uint64_t)(uintptr_t)rq.recon_pos,
@@ -1114,12 +1180,13 @@ gsnfs_status encode_impl(gsnfs_ctx *ctx, cudaStream_t s, EncodeReq &rq, bool wor
             key.push_back(rq.n[f]);
             key.push_back(rq.J[f]);
         }
-        st = run_graphed(ctx, s, std::move(key), enqueue);
+        st = run_graphed(ctx, s, std::move(key), enqueue, &gstages);
     } else {
         st = enqueue(s);
     }
     if (st) return st;
     CK(cudaStreamSynchronize(s));
+    add_graph_stage_times(gstages);
     const uint32_t derr = (uint32_t)(res[0] & 0xFFFFFFFFu);
     rq.nv = res[1];
     rq.total_bytes = res[2];
@@ -1604,6 +1671,7 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     uint32_t C = 0, Jmax = 0;
     uint64_t N = 0, n_occ = 0, nodes = 0, nblk = 0, jobs = 0, max_occ = 0;
     uint32_t max_nch = 0, chunk_max = 0;
+    uint64_t n_chunks = 0;
     bool any_rans = false;
     for (uint32_t f = 0; f < F; ++f) {
         const uint8_t *h = rec(f);
@@ -1625,6 +1693,7 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         if (P[f].occ_mode == 1) {
             any_rans = true;
             max_nch = std::max(max_nch, P[f].occ_aux);
+            n_chunks += P[f].occ_aux;
             chunk_max = std::max(chunk_max, P[f].chunk);
         }
     }
@@ -1643,6 +1712,7 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         uint8_t *occ, *gap;
         float *ctab, *klt;
         uint32_t *fcolor;
+        uint64_t *cstart;  // byte offset of every rANS chunk inside its frame's occupancy section
         RahtPlanDev plan;
     } L;
     bool any_color = false;
@@ -1660,6 +1730,7 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         L.nvdev = cv.take<uint64_t>(1);
         L.steps = cv.take<float>((uint64_t)F * C + 1);
         L.tabs = cv.take<uint32_t>(any_rans ? (uint64_t)F * rans_table_words() : 1);
+        L.cstart = cv.take<uint64_t>(n_chunks + 1);
         L.occ = cv.take<uint8_t>(n_occ + 8);
         L.tsum = cv.take<uint32_t>(occ_tiles(n_occ) + 1);
         L.tbase = cv.take<uint64_t>(occ_tiles(n_occ) + 2);
@@ -1721,7 +1792,7 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     float *hst = reinterpret_cast<float *>(tp + o_st);
     uint32_t *hfc = reinterpret_cast<uint32_t *>(tp + o_fc);
     uint32_t *htp = reinterpret_cast<uint32_t *>(tp + o_tp);
-    uint64_t vs = 0, oo = 0, no = 0, bo = 0, jo = 0, co = 0, pb = 0;
+    uint64_t vs = 0, oo = 0, no = 0, bo = 0, jo = 0, co = 0, pb = 0, cho = 0;
     for (uint32_t f = 0; f < F; ++f) {
         const ParsedHeader &H = P[f];
         DecFrame d{};
@@ -1739,6 +1810,8 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
         d.payload_words = (C && H.nv) ? (H.attr_bytes - 8 - 4ull * C * H.nb) / 4 : 0;
         d.occ_off = oo;
         d.n_occ = H.n_occ;
+        d.chunk_off = cho;
+        if (H.occ_mode == 1) cho += H.occ_aux;
         d.blk_off = bo;
         d.vstart = (uint32_t)vs;
         d.nv = (uint32_t)H.nv;
@@ -1836,7 +1909,7 @@ gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const
     // a11: occupancy bytes of every frame, octree levels, voxel centres
     stage_begin(sg, kStOccDecode);
     launch_batch_occ_bytes(L.fr, F, L.occ, max_occ, sms, sg);
-    if (any_rans) launch_batch_rans_decode(L.fr, F, max_nch, chunk_max, L.occ, L.tabs, dst, sg);
+    if (any_rans) launch_batch_rans_decode(L.fr, F, max_nch, chunk_max, L.occ, L.tabs, L.cstart, dst, sg);
     stage_end(sg, kStOccDecode);
     stage_begin(sg, kStOctreeDecode);
     if (ctab_total) launch_batch_centre_tables(L.fr, F, Jmax, L.ctab, sms, sg);
