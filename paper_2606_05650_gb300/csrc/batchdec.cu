@@ -34,9 +34,10 @@ __global__ void occ_bytes_kernel(const DecFrame *fr, uint8_t *occ_all)
         dst[i] = (d.mode == 2) ? (uint8_t)d.aux : d.occ_sec[16 + i];
 }
 
-// per frame: slot -> symbol table and freq << 16 | cum, then a corruption flag
+// per frame: slot -> symbol table and freq << 16 | cum, then a corruption flag; and the byte offset of
+// every chunk inside the section (a scan of the chunk size table)
 __global__ void __launch_bounds__(1024) tables_kernel(const DecFrame *fr, uint32_t *tabs, uint64_t tab_words,
-                                                      DevState *st)
+                                                      uint64_t *cstart, DevState *st)
 {
     const DecFrame &d = fr[blockIdx.x];
     if (d.mode != 1) return;
@@ -70,12 +71,32 @@ __global__ void __launch_bounds__(1024) tables_kernel(const DecFrame *fr, uint32
         }
         slot2sym[t] = (uint8_t)lo;
     }
+    // chunk offsets: after the section header, the frequency table and the size table (8-byte aligned)
+    __shared__ uint64_t sh64[33];
+    const uint32_t nch = d.aux;
+    const uint8_t *ctab = d.occ_sec + 24 + 512;
+    uint64_t run = (16 + 8 + 512 + 4 * (uint64_t)nch + 7) & ~7ull;
+    for (uint32_t b = 0; b < nch; b += blockDim.x) {
+        const uint32_t c = b + threadIdx.x;
+        uint64_t sz = 0;
+        if (c < nch) {
+            const uint8_t *q = ctab + 4 * (uint64_t)c;
+            sz = (uint32_t)q[0] | ((uint32_t)q[1] << 8) | ((uint32_t)q[2] << 16) | ((uint32_t)q[3] << 24);
+        }
+        uint64_t tot;
+        const uint64_t ex = block_exclusive_sum<uint64_t>(sz, sh64, &tot);
+        if (c < nch) cstart[d.chunk_off + c] = run + ex;
+        run += tot;
+    }
 }
 
-// grid (chunk groups, frames): warp per chunk of frame blockIdx.y
-__global__ void __launch_bounds__(32 * ransdec::kMaxWarps) rans_batch_kernel(const DecFrame *fr, const uint32_t *tabs,
-                                                                             uint64_t tab_words, uint32_t chunk_max,
-                                                                             uint8_t *occ_all, DevState *st)
+// grid (chunk groups, frames): warp per chunk of frame blockIdx.y, the chunk read in place (its words are
+// consumed in order, so they come from L1 after the first lane of a sector asks), the tables in shared memory
+constexpr uint32_t kRansWarps = 8;
+
+__global__ void __launch_bounds__(32 * kRansWarps) rans_batch_kernel(const DecFrame *fr, const uint32_t *tabs,
+                                                                     uint64_t tab_words, const uint64_t *cstart,
+                                                                     uint8_t *occ_all, DevState *st)
 {
     using namespace ransdec;
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -90,27 +111,19 @@ __global__ void __launch_bounds__(32 * ransdec::kMaxWarps) rans_batch_kernel(con
     __syncthreads();
     const uint8_t *slot2sym = dsm;
     const uint32_t *fc = reinterpret_cast<const uint32_t *>(dsm + kM);
-    const bool staged = chunk_max <= 32768;
-    uint32_t *cbuf = reinterpret_cast<uint32_t *>(dsm + kTabWords * 4 + (size_t)wl * stage_bytes(chunk_max));
     const uint8_t *ctab = d.occ_sec + 24 + 512;
-    const uint64_t table = (16 + 8 + 512 + 4 * (uint64_t)nch + 7) & ~7ull;
     uint8_t *out = occ_all + d.occ_off;
     for (uint32_t c = blockIdx.x * nwarps + wl; c < nch; c += gridDim.x * nwarps) {
-        const uint64_t start = table + chunk_offset(ctab, c, lane);
+        const uint64_t start = cstart[d.chunk_off + c];
         const uint8_t *cp = ctab + 4 * c;
         const uint32_t cbytes = (uint32_t)cp[0] | ((uint32_t)cp[1] << 8) | ((uint32_t)cp[2] << 16) | ((uint32_t)cp[3] << 24);
         if (cbytes < 128 || (cbytes & 3) || cbytes > 128 + 2 * chunk + 2 || start + cbytes > d.occ_bytes) {
             if (lane == 0) set_error(&st->err, kErrCorrupt);
             continue;
         }
-        const uint8_t *src = d.occ_sec + start;
-        if (staged) {
-            stage_chunk(cbuf, reinterpret_cast<const uint32_t *>(src), cbytes / 4, lane);
-            src = reinterpret_cast<const uint8_t *>(cbuf);
-        }
         const uint64_t s0 = (uint64_t)c * chunk;
         const uint32_t len = (uint32_t)((d.n_occ - s0) < chunk ? (d.n_occ - s0) : chunk);
-        if (decode_chunk(slot2sym, fc, src, (cbytes - 128) / 2, len, out + s0, lane) && lane == 0)
+        if (decode_chunk(slot2sym, fc, d.occ_sec + start, (cbytes - 128) / 2, len, out + s0, lane) && lane == 0)
             set_error(&st->err, kErrCorrupt);
     }
 }
@@ -379,18 +392,17 @@ void launch_batch_occ_bytes(const DecFrame *fr, uint32_t F, uint8_t *occ_all, ui
 }
 
 void launch_batch_rans_decode(const DecFrame *fr, uint32_t F, uint32_t max_chunks_per_frame, uint32_t chunk_max,
-                              uint8_t *occ_all, uint32_t *tabs, DevState *st, cudaStream_t s)
+                              uint8_t *occ_all, uint32_t *tabs, uint64_t *cstart, DevState *st, cudaStream_t s)
 {
+    (void)chunk_max;
     if (max_chunks_per_frame == 0) return;
     const uint64_t tab_words = kM / 4 + 256 + 4;
-    tables_kernel<<<F, 1024, 0, s>>>(fr, tabs, tab_words, st);
+    tables_kernel<<<F, 1024, 0, s>>>(fr, tabs, tab_words, cstart, st);
     count_launch();
-    const bool staged = chunk_max <= 32768;
-    const uint32_t warps = staged ? ransdec::warps_per_cta(chunk_max) : ransdec::kMaxWarps;
-    const size_t smem = staged ? ransdec::smem_bytes(chunk_max, warps) : (size_t)ransdec::kTabWords * 4;
+    const size_t smem = (size_t)ransdec::kTabWords * 4;
     cudaFuncSetAttribute(rans_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const uint32_t X = (max_chunks_per_frame + warps - 1) / warps;
-    rans_batch_kernel<<<dim3(X, F), 32 * warps, smem, s>>>(fr, tabs, tab_words, chunk_max, occ_all, st);
+    const uint32_t X = (max_chunks_per_frame + kRansWarps - 1) / kRansWarps;
+    rans_batch_kernel<<<dim3(X, F), 32 * kRansWarps, smem, s>>>(fr, tabs, tab_words, cstart, occ_all, st);
     count_launch();
 }
 

@@ -187,7 +187,7 @@ struct DecFrame {
     uint64_t occ_off;           // first byte of the frame's occupancy bytes in the batch buffer
     uint64_t n_occ;
     uint64_t blk_off;           // first RLGR block of the frame (nb * C blocks)
-    uint64_t chunk_off;         // first rANS chunk of the frame
+    uint64_t chunk_off;         // first rANS chunk of the frame (among the batch's rANS chunks)
     uint32_t vstart, nv;        // first output row, voxels
     uint32_t J, mode, aux, chunk;
     uint32_t B, nb;
@@ -277,8 +277,10 @@ void launch_fill(uint8_t *out, uint64_t n, uint8_t v, cudaStream_t s);
 // ---- batchdec.cu: batch-wide decoding steps --------------------------------
 void launch_batch_occ_bytes(const DecFrame *fr, uint32_t F, uint8_t *occ_all, uint64_t max_occ, int num_sms,
                             cudaStream_t s);
+// cstart: one word per rANS chunk of the batch (frames' chunks from DecFrame::chunk_off): scratch for the
+// chunks' byte offsets
 void launch_batch_rans_decode(const DecFrame *fr, uint32_t F, uint32_t max_chunks_per_frame, uint32_t chunk_max,
-                              uint8_t *occ_all, uint32_t *tabs, DevState *st, cudaStream_t s);
+                              uint8_t *occ_all, uint32_t *tabs, uint64_t *cstart, DevState *st, cudaStream_t s);
 // Octree levels of every frame (Algorithm 3), one launch per level: tile popcounts of the batch occupancy
 // bytes and their exclusive scan (tbase, tiles + 1 entries), then per level the CTAs of the tiles holding
 // that level's bytes (tile_pref: F + 1 CTA offsets per frame; a frame's CTAs start at tile

@@ -123,9 +123,11 @@ __device__ __forceinline__ uint32_t frame_of(const uint64_t *off, uint32_t F, ui
 }
 
 // warp per chunk; slot layout: u32 state[32] at 0, u16 word stack [128, 128 + 2*chunk).
-// The chunk's symbols and the frame's tables are staged in shared memory first.
-constexpr int kEncWarps = 4;
-constexpr uint32_t kStageSyms = 8192;  // symbols staged per pass
+// Grid (x, frames): the CTAs of frame blockIdx.y share its coding tables in
+// shared memory (reciprocals computed once per CTA); each warp stages its
+// chunk's symbols in shared memory, 4,096 at a time.
+constexpr int kEncWarps = 8;
+constexpr uint32_t kStageSyms = 4096;  // symbols staged per pass
 
 __global__ void __launch_bounds__(32 * kEncWarps) encode_kernel(const uint8_t *__restrict__ occ, const uint64_t *occ_off,
                                                                const uint64_t *chunk_off, uint32_t F, uint32_t chunk,
@@ -134,23 +136,24 @@ __global__ void __launch_bounds__(32 * kEncWarps) encode_kernel(const uint8_t *_
                                                                uint32_t *chunk_top)
 {
     __shared__ __align__(16) uint8_t s_sym[kEncWarps][kStageSyms];
-    __shared__ uint32_t s_fc[kEncWarps][256];   // freq << 16 | cum (cum < 2^15)
-    __shared__ uint32_t s_rcp[kEncWarps][256];  // ceil(2^32 / freq) for freq >= 2 (0 for freq < 2)
+    __shared__ uint32_t s_fc[256];   // freq << 16 | cum (cum < 2^15)
+    __shared__ uint32_t s_rcp[256];  // ceil(2^32 / freq) for freq >= 2 (0 for freq < 2)
     const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const uint64_t gw = (uint64_t)blockIdx.x * kEncWarps + wl;
-    const uint64_t nw = (uint64_t)gridDim.x * kEncWarps;
-    const uint64_t total = chunk_off[F];
-    for (uint64_t gc = gw; gc < total; gc += nw) {
-        const uint32_t f = frame_of(chunk_off, F, gc);
-        const uint64_t c = gc - chunk_off[f];
-        const uint64_t n = occ_off[f + 1] - occ_off[f];
+    const uint32_t f = blockIdx.y;
+    (void)F;
+    const uint64_t c0 = chunk_off[f], nch = chunk_off[f + 1] - c0;
+    if ((uint64_t)blockIdx.x * kEncWarps >= nch) return;  // no chunk of this frame for this CTA
+    for (uint32_t k = threadIdx.x; k < 256; k += blockDim.x) {
+        const uint32_t fk = freq[f * 256 + k];
+        s_fc[k] = (fk << 16) | cum[f * 256 + k];
+        s_rcp[k] = fk >= 2 ? (uint32_t)((0x100000000ull + fk - 1) / fk) : 0u;
+    }
+    __syncthreads();
+    const uint64_t n = occ_off[f + 1] - occ_off[f];
+    for (uint64_t c = (uint64_t)blockIdx.x * kEncWarps + wl; c < nch; c += (uint64_t)gridDim.x * kEncWarps) {
+        const uint64_t gc = c0 + c;
         const uint8_t *sym = occ + occ_off[f] + c * chunk;
         const uint32_t len = (uint32_t)((n - c * chunk) < chunk ? (n - c * chunk) : chunk);
-        for (uint32_t k = lane; k < 256; k += 32) {
-            const uint32_t fk = freq[f * 256 + k];
-            s_fc[wl][k] = (fk << 16) | cum[f * 256 + k];
-            s_rcp[wl][k] = fk >= 2 ? (uint32_t)((0x100000000ull + fk - 1) / fk) : 0u;
-        }
         uint8_t *slot = slots + gc * slot_bytes;
         uint16_t *stack = reinterpret_cast<uint16_t *>(slot + 128);
         uint32_t top = chunk;
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(32 * kEncWarps) encode_kernel(const uint8_t *_
                 const uint32_t j = (uint32_t)g * 32 + lane;
                 const bool valid = j < len;
                 const uint32_t sy = valid ? s_sym[wl][j - b0] : 0u;
-                const uint32_t fc = s_fc[wl][sy], rcp = s_rcp[wl][sy];
+                const uint32_t fc = s_fc[sy], rcp = s_rcp[sy];
                 const uint32_t fs = fc >> 16, cs = fc & 0xFFFFu;
                 const bool need = valid && ((uint64_t)x >= ((uint64_t)fs << 17));
                 const uint32_t m = __ballot_sync(0xFFFFFFFFu, need);
@@ -359,9 +362,12 @@ void launch_rans_encode(const RansFrames &r, DevState *st, uint64_t max_chunks, 
     chunk_offsets_kernel<<<1, 32, 0, s>>>(r.occ_off, r.mode, r.F, r.chunk, r.chunk_off);
     count_launch();
     if (max_chunks) {
-        uint64_t blocks = (max_chunks + kEncWarps - 1) / kEncWarps;
-        if (blocks > (uint64_t)num_sms * 16) blocks = (uint64_t)num_sms * 16;
-        encode_kernel<<<(uint32_t)blocks, 32 * kEncWarps, 0, s>>>(r.occ, r.occ_off, r.chunk_off, r.F, r.chunk, r.freq, r.cum,
+        // per frame: enough CTAs to fill the GPU when every frame has chunks, at most one chunk per warp
+        uint64_t per = ((uint64_t)num_sms * 8 + r.F - 1) / r.F;
+        const uint64_t need = (max_chunks + kEncWarps - 1) / kEncWarps;
+        if (per > need) per = need;
+        if (per < 1) per = 1;
+        encode_kernel<<<dim3((uint32_t)per, r.F), 32 * kEncWarps, 0, s>>>(r.occ, r.occ_off, r.chunk_off, r.F, r.chunk, r.freq, r.cum,
                                                         r.chunk_slots, rans_chunk_slot_bytes(r.chunk), r.chunk_words,
                                                         r.chunk_top);
         count_launch();
