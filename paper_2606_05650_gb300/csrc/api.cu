@@ -664,7 +664,9 @@ __global__ void attr_copy_kernel(HdrParams hp, AttrCopyArgs a, const StreamInfo 
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t wid = tid >> 5, nwarps = nt >> 5;
     // a warp takes 32 consecutive block streams: their sizes and offsets in one
-    // load, then the streams one after another (their loads independent)
+    // load, then four streams at a time, the first 96 words of all four loaded
+    // before any is stored (a stream is ~75 words at the headline's rates)
+    constexpr uint32_t kGroup = 4, kPerLane = 3;
     for (uint64_t k0 = wid * 32; k0 < nblk; k0 += nwarps * 32) {
         const uint64_t k = k0 + lane;
         uint32_t wl = 0;
@@ -674,24 +676,33 @@ __global__ void attr_copy_kernel(HdrParams hp, AttrCopyArgs a, const StreamInfo 
             ol = a.block_off[b0 + k] - base;
         }
         const uint32_t cnt = (nblk - k0) < 32 ? (uint32_t)(nblk - k0) : 32u;
-        for (uint32_t j = 0; j < cnt; ++j) {
-            const uint32_t w = __shfl_sync(0xFFFFFFFFu, wl, j);
-            const uint64_t o = __shfl_sync(0xFFFFFFFFu, ol, j);
-            const uint32_t *__restrict__ src = a.slots + (b0 + k0 + j) * a.slot_words;
-            uint32_t *__restrict__ dst = pay + o;
-            // up to 128 words per round: all loads in flight before the stores
-            for (uint32_t i0 = 0; i0 < w; i0 += 128) {
-                uint32_t v[4];
+        for (uint32_t j0 = 0; j0 < cnt; j0 += kGroup) {
+            uint32_t w[kGroup], v[kGroup][kPerLane];
+            uint64_t o[kGroup];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const uint32_t i = i0 + lane + 32 * u;
-                    v[u] = i < w ? __ldg(src + i) : 0u;
-                }
+            for (uint32_t q = 0; q < kGroup; ++q) {
+                const uint32_t j = j0 + q < cnt ? j0 + q : 0u;
+                w[q] = __shfl_sync(0xFFFFFFFFu, wl, j);
+                o[q] = __shfl_sync(0xFFFFFFFFu, ol, j);
+                if (j0 + q >= cnt) w[q] = 0;
+                const uint32_t *__restrict__ src = a.slots + (b0 + k0 + j0 + q) * a.slot_words;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const uint32_t i = i0 + lane + 32 * u;
-                    if (i < w) dst[i] = v[u];
+                for (uint32_t u = 0; u < kPerLane; ++u) {
+                    const uint32_t i = lane + 32 * u;
+                    v[q][u] = i < w[q] ? __ldg(src + i) : 0u;
                 }
+            }
+#pragma unroll
+            for (uint32_t q = 0; q < kGroup; ++q) {
+                uint32_t *__restrict__ dst = pay + o[q];
+#pragma unroll
+                for (uint32_t u = 0; u < kPerLane; ++u) {
+                    const uint32_t i = lane + 32 * u;
+                    if (i < w[q]) dst[i] = v[q][u];
+                }
+                // the rest of a longer stream
+                const uint32_t *__restrict__ src = a.slots + (b0 + k0 + j0 + q) * a.slot_words;
+                for (uint32_t i = 32 * kPerLane + lane; i < w[q]; i += 32) dst[i] = __ldg(src + i);
             }
         }
     }

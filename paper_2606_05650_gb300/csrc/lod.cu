@@ -49,27 +49,49 @@ __global__ void lod_sequence_kernel(const uint64_t *__restrict__ starts, const u
 
 // block (channels, nodes): thread (c, k) divides node k's low-pass
 // coefficient of channel c from the coarse inverse by sqrt(voxel count) (Eq. 1:
-// the low pass of a node is sqrt(w) times the mean of its voxels); threads
-// c < 3 of a node write its centre coordinate c.  No index division: node rows
-// are whole block rows.
-__global__ void lod_means_kernel(const float *__restrict__ low, const uint64_t *__restrict__ codes,
-                                 const uint64_t *__restrict__ starts, const uint64_t *__restrict__ n_nodes_dev,
-                                 uint32_t sh, uint32_t Jp, uint32_t C, LodGrid g, float *pos, float *out)
+// the low pass of a node is sqrt(w) times the mean of its voxels).  No index
+// division: node rows are whole block rows; each thread takes four rows per
+// step with their loads issued first.
+constexpr uint32_t kMeanRows = 4;
+
+__global__ void lod_means_kernel(const float *__restrict__ low, const uint64_t *__restrict__ starts,
+                                 const uint64_t *__restrict__ n_nodes_dev, uint32_t C, float *out)
 {
     const uint32_t c = threadIdx.x;
     const uint64_t nn = *n_nodes_dev;
-    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.y + threadIdx.y; k < nn; k += (uint64_t)gridDim.x * blockDim.y) {
-        const uint64_t b = starts[k];
-        if (out && c < C) {
-            const float w = (float)(starts[k + 1] - b);
-            out[k * C + c] = __fdiv_rn(low[k * C + c], __fsqrt_rn(w));
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.y * kMeanRows;
+    for (uint64_t k0 = (uint64_t)blockIdx.x * blockDim.y * kMeanRows + threadIdx.y; k0 < nn; k0 += step) {
+        float lw[kMeanRows];
+        uint64_t w[kMeanRows];
+#pragma unroll
+        for (uint32_t u = 0; u < kMeanRows; ++u) {
+            const uint64_t k = k0 + (uint64_t)u * blockDim.y;
+            const bool ok = k < nn && c < C;
+            lw[u] = ok ? low[k * C + c] : 0.f;
+            w[u] = ok ? starts[k + 1] - starts[k] : 1;
         }
-        if (pos && c < 3) {
-            const uint64_t m = codes[b] >> sh;
+#pragma unroll
+        for (uint32_t u = 0; u < kMeanRows; ++u) {
+            const uint64_t k = k0 + (uint64_t)u * blockDim.y;
+            if (k < nn && c < C) out[k * C + c] = __fdiv_rn(lw[u], __fsqrt_rn((float)w[u]));
+        }
+    }
+}
+
+// thread per node: its cell centre at depth Jp (the same FP64 expression as a voxel centre at that depth)
+__global__ void lod_centres_kernel(const uint64_t *__restrict__ codes, const uint64_t *__restrict__ starts,
+                                   const uint64_t *__restrict__ n_nodes_dev, uint32_t sh, uint32_t Jp, LodGrid g,
+                                   float *pos)
+{
+    const uint64_t nn = *n_nodes_dev;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t m = codes[starts[k]] >> sh;
+#pragma unroll
+        for (uint32_t a = 0; a < 3; ++a) {
             uint32_t v = 0;
-            for (uint32_t bit = 0; bit < Jp; ++bit) v |= (uint32_t)((m >> (3 * bit + c)) & 1u) << bit;
+            for (uint32_t bit = 0; bit < Jp; ++bit) v |= (uint32_t)((m >> (3 * bit + a)) & 1u) << bit;
             const double off = __dmul_rn(__dadd_rn((double)v, 0.5), g.cell);
-            pos[3 * k + c] = (float)__dadd_rn(g.lo[c], off);
+            pos[3 * k + a] = (float)__dadd_rn(g.lo[a], off);
         }
     }
 }
@@ -110,17 +132,20 @@ void launch_lod_means(const float *low, const uint64_t *codes, const uint64_t *s
                       uint64_t n_nodes, uint32_t sh, uint32_t Jp, uint32_t C, const LodGrid &g, float *pos, float *out,
                       int num_sms, cudaStream_t s)
 {
-    const uint32_t cw = C > 3 ? C : 3;                        // threads per node row
-    const uint32_t ny = cw >= 256 ? 1u : 256u / cw;               // node rows per block
-    // one node row per thread row and no grid-stride loop: every row's loads are in flight at once (a capped
-    // grid walking the rows in turn was bound by one load latency per row)
-    uint64_t blocks = (n_nodes + ny - 1) / ny;
-    if (blocks > 0x7FFFFFFFull) blocks = 0x7FFFFFFFull;
-    if (blocks < 1) blocks = 1;
-    (void)num_sms;
-    lod_means_kernel<<<(uint32_t)blocks, dim3(cw, ny), 0, s>>>(low, codes, starts, n_nodes_dev, sh, Jp, C, g, pos,
-                                                               out);
-    count_launch();
+    if (out && C) {
+        const uint32_t cw = C;                          // threads per node row
+        const uint32_t ny = cw >= 256 ? 1u : 256u / cw;  // node rows per block
+        uint64_t blocks = (n_nodes + ny * kMeanRows - 1) / (ny * kMeanRows);
+        const uint64_t cap = (uint64_t)num_sms * 16;
+        if (blocks > cap) blocks = cap;
+        if (blocks < 1) blocks = 1;
+        lod_means_kernel<<<(uint32_t)blocks, dim3(cw, ny), 0, s>>>(low, starts, n_nodes_dev, C, out);
+        count_launch();
+    }
+    if (pos) {
+        lod_centres_kernel<<<lod_grid(n_nodes, num_sms), 256, 0, s>>>(codes, starts, n_nodes_dev, sh, Jp, g, pos);
+        count_launch();
+    }
 }
 
 }  // namespace gsnfs
