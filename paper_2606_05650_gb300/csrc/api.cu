@@ -411,6 +411,16 @@ struct StreamInfo {
 // reading them back (GSNFS_HEADER_RECORD_BYTES each): the stream's header
 // tables at 0, the first 24 bytes of its occupancy section at 4096 and the
 // first 8 of its attribute section at 4160.  One CTA per stream.
+// A record assembled in shared memory goes to the (pinned host) destination in
+// 16-byte stores: byte stores to host memory would each cross the link alone.
+static_assert(GSNFS_HEADER_RECORD_BYTES % 16 == 0, "records are copied in 16-byte words");
+__device__ __forceinline__ void copy_record_out(uint8_t *r, const uint8_t *sr)
+{
+    uint4 *d = reinterpret_cast<uint4 *>(r);  // records start 16-byte aligned (4,224 = 264 x 16)
+    const uint4 *q = reinterpret_cast<const uint4 *>(sr);
+    for (uint32_t k = threadIdx.x; k < GSNFS_HEADER_RECORD_BYTES / 16; k += blockDim.x) d[k] = q[k];
+}
+
 __global__ void header_records_kernel(const uint8_t *out, const StreamInfo *si, uint32_t n, uint8_t *rec)
 {
     const uint32_t i = blockIdx.x;
@@ -419,6 +429,7 @@ __global__ void header_records_kernel(const uint8_t *out, const StreamInfo *si, 
     uint8_t *r = rec + (uint64_t)i * GSNFS_HEADER_RECORD_BYTES;
     const uint8_t *b = out + x.off;
     const uint32_t hb = x.hb < 4096 ? (uint32_t)x.hb : 4096u;
+    __shared__ __align__(16) uint8_t sr[GSNFS_HEADER_RECORD_BYTES];
     for (uint32_t k = threadIdx.x; k < GSNFS_HEADER_RECORD_BYTES; k += blockDim.x) {  // every byte: zeros elsewhere
         uint8_t v = 0;
         if (k < hb)
@@ -427,8 +438,10 @@ __global__ void header_records_kernel(const uint8_t *out, const StreamInfo *si, 
             v = b[x.hb + (k - 4096)];
         else if (k >= 4160 && k < 4168 && x.attr >= 8)
             v = b[x.hb + x.occ + (k - 4160)];
-        r[k] = v;
+        sr[k] = v;
     }
+    __syncthreads();
+    copy_record_out(r, sr);
 }
 
 // The same records read out of the streams themselves (a decoder not given
@@ -466,6 +479,7 @@ __global__ void stream_records_kernel(RecLaunch a)
     }
     const uint64_t nh = bytes < 96 ? bytes : (hb < 96 ? 96 : (hb > 4096 ? 4096 : hb));
     const bool heads = bytes >= 96 && hb <= 4096 && hb < bytes;
+    __shared__ __align__(16) uint8_t sr[GSNFS_HEADER_RECORD_BYTES];
     for (uint32_t k = threadIdx.x; k < GSNFS_HEADER_RECORD_BYTES; k += blockDim.x) {  // every byte: zeros elsewhere
         uint8_t v = 0;
         if (k < nh && k < bytes)
@@ -474,8 +488,10 @@ __global__ void stream_records_kernel(RecLaunch a)
             v = b[hb + (k - 4096)];
         else if (heads && k >= 4160 && k < 4168 && attr >= 8 && occ < bytes && hb + occ + (k - 4160) < bytes)
             v = b[hb + occ + (k - 4160)];
-        r[k] = v;
+        sr[k] = v;
     }
+    __syncthreads();
+    copy_record_out(r, sr);
 }
 
 struct HdrParams {

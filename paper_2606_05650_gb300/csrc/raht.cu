@@ -33,7 +33,7 @@ namespace {
 
 constexpr int kThreads = 256;   // prelude kernels
 constexpr int kXThreads = 512;  // transform kernels: 16 warps per tile, 3 tiles per SM
-constexpr int kRounds = 64;
+constexpr int kRounds = 64;  // gap levels of in-tile butterflies are below kRounds (a 64-bit level mask)
 constexpr uint32_t kSmemRowBytes = 56 * 1024;
 
 // ------------------------------------------------------------- prelude ---
@@ -167,23 +167,69 @@ __device__ void prelude_tile(const PreludeArgs &a, PreludeSmem<TMAX> &S, int q, 
         S.inl[i] = f;
     }
     G.sync();
-    // survivor mask; rounds = nonempty levels in ascending order (one warp)
+    // survivor mask; level offsets of the butterflies (one warp)
     for (uint32_t w = wid; w < W; w += Grp::nwarps) {
         const uint32_t i = w * 32 + lane;
         const uint32_t b = __ballot_sync(0xFFFFFFFFu, i < m && !S.inl[i]);
         if (lane == 0) S.surv[w] = b;
     }
     if (wid == 0) {
-        uint32_t run = 0, nr = 0;
-        uint16_t *re = p.round_end + (uint64_t)(ps.tile_off + t) * kRounds;
+        uint32_t run = 0;
         for (int base = 0; base <= kRounds; base += 32) {
             const int l = base + lane;
             const uint32_t c = (l <= kRounds) ? S.lvl_cnt[l] : 0u;
             const uint32_t inc = warp_inclusive_sum(c);
             if (l <= kRounds) S.lvl_off[l] = run + inc - c;
-            const uint32_t ne = __ballot_sync(0xFFFFFFFFu, c != 0);
-            if (c) re[nr + __popc(ne & lanemask_lt())] = (uint16_t)(run + inc);
-            nr += __popc(ne);
+            run += __shfl_sync(0xFFFFFFFFu, inc, 31);
+        }
+    }
+    G.sync();
+    // Rounds as early as possible (the range-maximum table is dead now and holds the scratch): a
+    // butterfly's round is one more than the later of its two children's, so the butterflies are walked
+    // level by level (children before parents) keeping, per node start, the round that completed it.
+    // Butterflies of one level touch disjoint nodes; the arithmetic of each is unchanged, so the
+    // coefficients do not depend on the order.
+    static_assert((PreludeSmem<TMAX>::kLog - 1) * (TMAX + 1) >= 4 * TMAX + 1, "round scratch exceeds the table");
+    uint16_t *ord = reinterpret_cast<uint16_t *>(&S.mx[1][0]);   // butterflies in level order (mx[0] is unused;
+                                                                 // mx[1] starts at an even offset)
+    uint8_t *dep = reinterpret_cast<uint8_t *>(ord + TMAX);       // round of the butterfly at element i
+    uint8_t *dnode = dep + TMAX;                                 // round that completed the node starting at x
+    for (int l = (int)tid; l <= kRounds; l += Grp::size) S.lvl_cnt[l] = 0;  // fill counters
+    for (uint32_t x = tid; x <= m; x += Grp::size) dnode[x] = 0;
+    G.sync();
+    for (uint32_t i = tid; i < m; i += Grp::size)
+        if (S.inl[i]) ord[S.lvl_off[S.g[i]] + atomicAdd(&S.lvl_cnt[S.g[i]], 1u)] = (uint16_t)i;
+    G.sync();
+    // the nonempty levels (butterflies have levels below kRounds = 64), lowest first
+    uint64_t levels = (uint64_t)__ballot_sync(0xFFFFFFFFu, S.lvl_cnt[lane] != 0) |
+                      ((uint64_t)__ballot_sync(0xFFFFFFFFu, S.lvl_cnt[lane + 32] != 0) << 32);
+    for (; levels; levels &= levels - 1) {
+        const int l = __ffsll((long long)levels) - 1;
+        const uint32_t cnt = S.lvl_cnt[l];
+        const uint32_t off = S.lvl_off[l];
+        for (uint32_t k = tid; k < cnt; k += Grp::size) {
+            const uint32_t i = ord[off + k], lft = S.prv[i];
+            const uint32_t d = 1u + (dnode[lft] > dnode[i] ? dnode[lft] : dnode[i]);
+            dep[i] = (uint8_t)d;
+            dnode[lft] = (uint8_t)d;
+        }
+        G.sync();
+    }
+    for (int l = (int)tid; l <= kRounds; l += Grp::size) S.lvl_cnt[l] = 0;  // butterflies per round
+    G.sync();
+    for (uint32_t i = tid; i < m; i += Grp::size)
+        if (S.inl[i]) atomicAdd(&S.lvl_cnt[dep[i]], 1u);
+    G.sync();
+    if (wid == 0) {  // round offsets and ends (rounds 1 .. nr are all nonempty)
+        uint32_t run = 0, nr = 0;
+        uint16_t *re = p.round_end + (uint64_t)(ps.tile_off + t) * kRounds;
+        for (int base = 1; base <= kRounds; base += 32) {
+            const int l = base + lane;
+            const uint32_t c = (l <= kRounds) ? S.lvl_cnt[l] : 0u;
+            const uint32_t inc = warp_inclusive_sum(c);
+            if (l <= kRounds) S.lvl_off[l] = run + inc - c;
+            if (c) re[l - 1] = (uint16_t)(run + inc);
+            nr += __popc(__ballot_sync(0xFFFFFFFFu, c != 0));
             run += __shfl_sync(0xFFFFFFFFu, inc, 31);
         }
         if (lane == 0) {
@@ -206,7 +252,7 @@ __device__ void prelude_tile(const PreludeArgs &a, PreludeSmem<TMAX> &S, int q, 
             const uint32_t w0 = S.p[i] - S.p[l], w1 = S.e[r - 1] - S.p[i];
             const float fw0 = (float)w0, fw1 = (float)w1, fs = (float)(w0 + w1);
             const float ca = __fsqrt_rn(__fdiv_rn(fw0, fs)), cb = __fsqrt_rn(__fdiv_rn(fw1, fs));
-            const uint32_t slot = S.lvl_off[S.g[i]] + atomicAdd(&S.lvl_cnt[S.g[i]], 1u);
+            const uint32_t slot = S.lvl_off[dep[i]] + atomicAdd(&S.lvl_cnt[dep[i]], 1u);
             p.bf_idx[sbase + slot] = l | (i << 16);
             p.bf_ab[sbase + slot] = make_float2(ca, cb);
             if (p.bf_w) p.bf_w[sbase + slot] = make_uint2(w0, w1);
