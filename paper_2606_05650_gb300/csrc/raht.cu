@@ -347,14 +347,20 @@ __global__ void __launch_bounds__(kThreads) prelude_tiles_kernel(PreludeArgs a, 
 __device__ void prelude_scan_body(const RahtPlanDev &p, int q, uint32_t *sh)
 {
     const RahtPass ps = p.passes[q];
-    uint32_t run = 0;
-    for (uint32_t b = 0; b < ps.ntiles; b += blockDim.x) {
-        uint32_t t = b + threadIdx.x;
-        uint32_t c = (t < ps.ntiles) ? p.tile_carry[ps.tile_off + t] : 0u;
-        uint32_t tot;
-        uint32_t pre = block_exclusive_sum<uint32_t>(c, sh, &tot);
-        if (t < ps.ntiles) p.tile_carry[ps.tile_off + t] = run + pre;
-        run += tot;
+    // each thread sums a contiguous run of tiles (all its loads in flight together), one block scan of the
+    // run totals, then each thread writes its run's prefixes
+    const uint32_t per = (ps.ntiles + blockDim.x - 1) / blockDim.x;
+    const uint32_t b = threadIdx.x * per < ps.ntiles ? threadIdx.x * per : ps.ntiles;
+    const uint32_t e = b + per < ps.ntiles ? b + per : ps.ntiles;
+    uint32_t *tc = p.tile_carry + ps.tile_off;
+    uint32_t sum = 0;
+    for (uint32_t t = b; t < e; ++t) sum += tc[t];
+    uint32_t run;
+    uint32_t pre = block_exclusive_sum<uint32_t>(sum, sh, &run);
+    for (uint32_t t = b; t < e; ++t) {
+        const uint32_t c = tc[t];
+        tc[t] = pre;
+        pre += c;
     }
     if (threadIdx.x == 0) {
         RahtPass nx = {};
