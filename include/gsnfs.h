@@ -95,7 +95,9 @@ gsnfs_status gsnfs_reserve(gsnfs_ctx *ctx, uint64_t n, uint32_t C, uint32_t J, c
  * change between replays.  Up to 64 graphs are kept (least recently used
  * dropped); growing the scratch drops them all.  The graph runs on a stream
  * of the context ordered after the caller's stream and joined back to it.
- * A capture that fails falls back to running the work directly. */
+ * A capture that fails falls back to running the work directly.  Replays
+ * report the same per-stage times as direct calls while profiling is on (the
+ * graph records its own stage events). */
 gsnfs_status gsnfs_set_graphs(gsnfs_ctx *ctx, int enable);
 /* out[0] replays, out[1] captures, out[2] failed captures, out[3] graphs cached. */
 gsnfs_status gsnfs_graph_stats(gsnfs_ctx *ctx, uint64_t *out);

@@ -177,9 +177,7 @@ struct gsnfs_ctx {
     // splat-rasteriser scratch: per-Gaussian arrays and the per-tile key lists, grown on demand
     void *rnd = nullptr, *rkeys = nullptr;
     size_t rnd_cap = 0, rkeys_cap = 0;
-    // second stream for the independent branches of one call (geometry and attributes)
-    cudaStream_t aux = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_join = nullptr;  // stream_wait
     // high-priority side stream: the longer branch of a batched call, so that CTAs of the shorter branch
     // (on the caller's stream) take the SMs that branch leaves idle instead of delaying it
     cudaStream_t aux_hi = nullptr;
@@ -290,31 +288,11 @@ gsnfs_status grow_pinned(gsnfs_ctx *ctx, size_t need)
     return GSNFS_OK;
 }
 
-// Independent branches of one call: the work enqueued on the context's second
-// stream between fork_begin and fork_end starts after everything already on s
-// and s continues only after it (events also order captured graph nodes).
-gsnfs_status fork_begin(gsnfs_ctx *ctx, cudaStream_t s, cudaStream_t *aux)
-{
-    if (!ctx->aux) {
-        CK(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
-    }
-    CK(cudaEventRecord(ctx->ev_fork, s));
-    CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
-    *aux = ctx->aux;
-    return GSNFS_OK;
-}
-
-gsnfs_status fork_end(gsnfs_ctx *ctx, cudaStream_t s)
-{
-    CK(cudaEventRecord(ctx->ev_join, ctx->aux));
-    CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
-    return GSNFS_OK;
-}
-
-// The same fork and join onto the context's high-priority stream (the block
-// scheduler starts pending CTAs of a higher-priority stream first).
+// Independent branches of one call: the work enqueued on the context's
+// high-priority stream between fork_hi_begin and fork_hi_end starts after
+// everything already on s, and s continues only after it (events also order
+// captured graph nodes).  The block scheduler starts pending CTAs of a
+// higher-priority stream first, so the longer branch goes there.
 gsnfs_status fork_hi_begin(gsnfs_ctx *ctx, cudaStream_t s, cudaStream_t *hi)
 {
     if (!ctx->aux_hi) {
@@ -334,6 +312,15 @@ gsnfs_status fork_hi_end(gsnfs_ctx *ctx, cudaStream_t s)
 {
     CK(cudaEventRecord(ctx->ev_join_hi, ctx->aux_hi));
     CK(cudaStreamWaitEvent(s, ctx->ev_join_hi, 0));
+    return GSNFS_OK;
+}
+
+// Work on `waiter` enqueued from now on runs after everything enqueued on `from` so far.
+gsnfs_status stream_wait(gsnfs_ctx *ctx, cudaStream_t waiter, cudaStream_t from)
+{
+    if (!ctx->ev_join) CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    CK(cudaEventRecord(ctx->ev_join, from));
+    CK(cudaStreamWaitEvent(waiter, ctx->ev_join, 0));
     return GSNFS_OK;
 }
 
@@ -1417,7 +1404,8 @@ struct LodReq {
     uint64_t *out_nodes;
 };
 
-gsnfs_status lod_from_voxels(gsnfs_ctx *ctx, cudaStream_t s, const ParsedHeader &P, DecLayout &L, bool attrs,
+gsnfs_status lod_from_voxels(gsnfs_ctx *ctx, cudaStream_t s, cudaStream_t cs, const ParsedHeader &P, DecLayout &L,
+                             bool attrs,
                              const LodReq &lod);
 
 gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, uint64_t bytes, float *d_pos,
@@ -1458,45 +1446,46 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
     if (P.C) CK(stage_copy(L.step, hp + 256, 4 * P.C, s));
     CK(dev_memset(dst, 0, 8, s));
     const int sms = ctx->num_sms;
-    // a12's RLGR decode needs only the block tables: second stream, beside a11
+    // a12's RLGR decode needs only the block tables: it runs on s beside a11 and the schedule (the longer
+    // branch), which run on the context's high-priority stream sg and take the RLGR branch's results last
     const bool attrs = P.C && d_attr;
+    cudaStream_t sg = s;
     if (attrs) {
-        cudaStream_t ra = nullptr;
-        st = fork_begin(ctx, s, &ra);
+        st = fork_hi_begin(ctx, s, &sg);
         if (st) return st;
         const uint8_t *as = d_in + P.hb + P.occ_bytes;
         const uint32_t *bw = reinterpret_cast<const uint32_t *>(as + 8);
         const uint64_t nblk = (uint64_t)P.C * P.nb;
         const uint32_t *payload = bw + nblk;
         const uint64_t payload_words = (P.attr_bytes - 8 - 4 * nblk) / 4;
-        launch_scan_u32_to_u64(bw, nblk, L.block_off, L.spart, sms, ra);
-        stage_begin(ra, kStRlgrDec);
-        launch_rlgr_decode(payload, payload_words, bw, L.block_off, P.nv, P.C, P.B, L.step, L.Y, dst, ra);
-        stage_end(ra, kStRlgrDec);
+        launch_scan_u32_to_u64(bw, nblk, L.block_off, L.spart, sms, s);
+        stage_begin(s, kStRlgrDec);
+        launch_rlgr_decode(payload, payload_words, bw, L.block_off, P.nv, P.C, P.B, L.step, L.Y, dst, s);
+        stage_end(s, kStRlgrDec);
     }
     // a11: occupancy bytes
     const uint8_t *sec = d_in + P.hb;
     const uint8_t *occ = L.occ;
-    stage_begin(s, kStOccDecode);
+    stage_begin(sg, kStOccDecode);
     if (P.occ_mode == 0)
         occ = sec + 16;
     else if (P.occ_mode == 2)
-        launch_fill(L.occ, P.n_occ, (uint8_t)P.occ_aux, s);
+        launch_fill(L.occ, P.n_occ, (uint8_t)P.occ_aux, sg);
     else
-        launch_rans_decode(sec, P.occ_bytes, P.n_occ, P.occ_aux, P.chunk, L.occ, L.tabs, dst, sms, s);
-    stage_end(s, kStOccDecode);
-    stage_begin(s, kStOctreeDecode);
-    launch_octree_decode(occ, P.n_occ, P.J, P.lsz, L.nodes, L.pref, L.ppart, L.codes, dst, sms, s);
-    if (d_pos) launch_voxel_centres(L.codes, P.nv, P.J, L.grid, d_pos, s, L.ctab);
-    stage_end(s, kStOctreeDecode);
-    if (lod) return lod_from_voxels(ctx, s, P, L, attrs, *lod);
+        launch_rans_decode(sec, P.occ_bytes, P.n_occ, P.occ_aux, P.chunk, L.occ, L.tabs, dst, sms, sg);
+    stage_end(sg, kStOccDecode);
+    stage_begin(sg, kStOctreeDecode);
+    launch_octree_decode(occ, P.n_occ, P.J, P.lsz, L.nodes, L.pref, L.ppart, L.codes, dst, sms, sg);
+    if (d_pos) launch_voxel_centres(L.codes, P.nv, P.J, L.grid, d_pos, sg, L.ctab);
+    stage_end(sg, kStOctreeDecode);
+    if (lod) return lod_from_voxels(ctx, sg, s, P, L, attrs, *lod);
     // a12: schedule, then (after the RLGR branch) the inverse RAHT
     if (attrs) {
-        stage_begin(s, kStPrelude);
-        launch_gap_levels(L.codes, P.nv, L.gap, s);
-        launch_raht_prelude(L.plan, L.gap, dst, L.nvdev, sms, s);
-        stage_end(s, kStPrelude);
-        st = fork_end(ctx, s);
+        stage_begin(sg, kStPrelude);
+        launch_gap_levels(L.codes, P.nv, L.gap, sg);
+        launch_raht_prelude(L.plan, L.gap, dst, L.nvdev, sms, sg);
+        stage_end(sg, kStPrelude);
+        st = stream_wait(ctx, sg, s);  // the coefficients
         if (st) return st;
         RahtIO io{};
         io.C = P.C;
@@ -1510,9 +1499,11 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
             io.F = 1;
             io.yuv_inv = yuv_inverse();
         }
-        stage_begin(s, kStRahtInv);
-        launch_raht_inverse(L.plan, io, P.nv, sms, s);
-        stage_end(s, kStRahtInv);
+        stage_begin(sg, kStRahtInv);
+        launch_raht_inverse(L.plan, io, P.nv, sms, sg);
+        stage_end(sg, kStRahtInv);
+        st = fork_hi_end(ctx, s);  // the caller's stream sees all of it
+        if (st) return st;
     }
     CK(cudaGetLastError());
     uint32_t *res = (uint32_t *)(hp + 1024);
@@ -1521,9 +1512,9 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
     return map_dev_error(res[0]);
 }
 
-// Level of detail from a decoded voxel set (geometry decoded on s; the
-// dequantised coefficients Y being decoded on the context's second stream
-// when attrs): the nodes of depth lod.depth are runs of voxels sharing
+// Level of detail from a decoded voxel set (geometry decoded on s, the
+// context's high-priority stream when attrs; the dequantised coefficients Y
+// being decoded on the caller's stream cs): the nodes of depth lod.depth are runs of voxels sharing
 // code >> 3(J - depth).  Each node becomes one element of a coarser RAHT
 // sequence (its voxel run, the gap before its first voxel): its weight is its
 // voxel count and its coefficients sit at its first voxel's row of Y, the
@@ -1531,7 +1522,8 @@ gsnfs_status decode_impl(gsnfs_ctx *ctx, cudaStream_t s, const uint8_t *d_in, ui
 // Algorithm 6).  The inverse over that sequence stops at the nodes, so the
 // butterflies inside nodes are never applied; a node's result is its
 // low-pass coefficient, and its mean attribute is that divided by sqrt(w).
-gsnfs_status lod_from_voxels(gsnfs_ctx *ctx, cudaStream_t s, const ParsedHeader &P, DecLayout &L, bool attrs,
+gsnfs_status lod_from_voxels(gsnfs_ctx *ctx, cudaStream_t s, cudaStream_t cs, const ParsedHeader &P, DecLayout &L,
+                             bool attrs,
                              const LodReq &lod)
 {
     const int sms = ctx->num_sms;
@@ -1595,8 +1587,8 @@ gsnfs_status lod_from_voxels(gsnfs_ctx *ctx, cudaStream_t s, const ParsedHeader 
             stage_end(s, kStPrelude);
         }
     }
-    if (attrs) {  // join the coefficient branch before anything returns
-        const gsnfs_status fst = fork_end(ctx, s);
+    if (attrs) {  // join the coefficient branch (on cs) before anything returns
+        const gsnfs_status fst = stream_wait(ctx, s, cs);
         if (fst) return fst;
     }
     if (res) {
@@ -1626,10 +1618,14 @@ gsnfs_status lod_from_voxels(gsnfs_ctx *ctx, cudaStream_t s, const ParsedHeader 
     launch_lod_means(rows, L.codes, starts, offs + nv, nn, sh, lod.depth, C, g, lod.pos, C ? lod.attr : nullptr, sms,
                      s);
     CK(cudaGetLastError());
+    if (attrs) {  // the caller's stream sees all of it
+        const gsnfs_status fst = fork_hi_end(ctx, cs);
+        if (fst) return fst;
+    }
     uint32_t *hres = reinterpret_cast<uint32_t *>(ctx->pinned + 1024);
-    CK(stage_copy(hres, &dst->err, 4, s));
-    if (room) CK(stage_copy(hn, offs + nv, 8, s));
-    CK(cudaStreamSynchronize(s));
+    CK(stage_copy(hres, &dst->err, 4, cs));
+    if (room) CK(stage_copy(hn, offs + nv, 8, cs));
+    CK(cudaStreamSynchronize(cs));
     if (room) *lod.out_nodes = *hn;
     return map_dev_error(hres[0]);
 }
@@ -2035,8 +2031,6 @@ void gsnfs_destroy(gsnfs_ctx *ctx)
     if (ctx->lod) cudaFree(ctx->lod);
     if (ctx->rnd) cudaFree(ctx->rnd);
     if (ctx->rkeys) cudaFree(ctx->rkeys);
-    if (ctx->aux) cudaStreamDestroy(ctx->aux);
-    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->aux_hi) cudaStreamDestroy(ctx->aux_hi);
     if (ctx->ev_fork_hi) cudaEventDestroy(ctx->ev_fork_hi);

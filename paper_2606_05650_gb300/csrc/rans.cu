@@ -303,39 +303,57 @@ __global__ void __launch_bounds__(1024) table_kernel(const uint8_t *__restrict__
     }
 }
 
+// One frame's chunks, a warp per chunk read in place (its words are consumed
+// in order, so they come from L1).  Each CTA first turns the chunk size table
+// into chunk offsets in shared memory (one block scan per 1,024 chunks) when
+// they fit (kSmemChunks), else each warp sums the sizes before its chunk.
+constexpr uint32_t kSmemChunks = 4096;
+
 __global__ void __launch_bounds__(32 * ransdec::kMaxWarps) decode_kernel(const uint8_t *__restrict__ sec,
                                                                          uint64_t sec_bytes, uint64_t n, uint32_t nch,
                                                                          uint32_t chunk, uint8_t *out, DevState *st,
-                                                                         bool staged, const uint32_t *tabs)
+                                                                         const uint32_t *tabs)
 {
     using namespace ransdec;
     extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ uint32_t sh[33];
     // decoding tables built once by table_kernel: copy them in
     if (tabs[kTabWords] != 0) return;  // frequencies did not sum to M (reported by table_kernel)
     load_tables(reinterpret_cast<uint32_t *>(dsm), tabs);
+    const uint8_t *ctab = sec + 24 + 512;
+    const uint64_t table = (16 + 8 + 512 + 4 * (uint64_t)nch + 7) & ~7ull;
+    const bool local = nch <= kSmemChunks && sec_bytes < (1ull << 32);
+    uint32_t *s_start = reinterpret_cast<uint32_t *>(dsm + kTabWords * 4);
+    if (local) {
+        uint32_t run = (uint32_t)table;
+        for (uint32_t b = 0; b < nch; b += blockDim.x) {
+            const uint32_t c = b + threadIdx.x;
+            uint32_t sz = 0;
+            if (c < nch) {
+                const uint8_t *q = ctab + 4 * c;
+                sz = (uint32_t)q[0] | ((uint32_t)q[1] << 8) | ((uint32_t)q[2] << 16) | ((uint32_t)q[3] << 24);
+            }
+            uint32_t tot;
+            const uint32_t ex = block_exclusive_sum<uint32_t>(sz, sh, &tot);
+            if (c < nch) s_start[c] = run + ex;  // wraps only for sizes that fail the bounds check below
+            run += tot;
+        }
+    }
     __syncthreads();
     const uint8_t *slot2sym = dsm;
     const uint32_t *fc = reinterpret_cast<const uint32_t *>(dsm + kM);
     const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    uint32_t *cbuf = reinterpret_cast<uint32_t *>(dsm + kTabWords * 4 + (size_t)wl * stage_bytes(chunk));
-    const uint8_t *ctab = sec + 24 + 512;
-    const uint64_t table = (16 + 8 + 512 + 4 * (uint64_t)nch + 7) & ~7ull;
     for (uint32_t c = blockIdx.x * nwarps + wl; c < nch; c += gridDim.x * nwarps) {
-        const uint64_t start = table + chunk_offset(ctab, c, lane);
+        const uint64_t start = local ? s_start[c] : table + chunk_offset(ctab, c, lane);
         const uint8_t *cp = ctab + 4 * c;
         const uint32_t cbytes = (uint32_t)cp[0] | ((uint32_t)cp[1] << 8) | ((uint32_t)cp[2] << 16) | ((uint32_t)cp[3] << 24);
         if (cbytes < 128 || (cbytes & 3) || cbytes > 128 + 2 * chunk + 2 || start + cbytes > sec_bytes) {
             if (lane == 0) set_error(&st->err, kErrCorrupt);
             continue;
         }
-        const uint8_t *src = sec + start;  // 4-byte aligned (sections 8-aligned, chunks padded to 4)
-        if (staged) {
-            stage_chunk(cbuf, reinterpret_cast<const uint32_t *>(src), cbytes / 4, lane);
-            src = reinterpret_cast<const uint8_t *>(cbuf);
-        }
         const uint64_t s0 = (uint64_t)c * chunk;
         const uint32_t len = (uint32_t)((n - s0) < chunk ? (n - s0) : chunk);
-        if (decode_chunk(slot2sym, fc, src, (cbytes - 128) / 2, len, out + s0, lane) && lane == 0)
+        if (decode_chunk(slot2sym, fc, sec + start, (cbytes - 128) / 2, len, out + s0, lane) && lane == 0)
             set_error(&st->err, kErrCorrupt);
     }
 }
@@ -385,14 +403,12 @@ void launch_rans_decode(const uint8_t *sec, uint64_t sec_bytes, uint64_t n, uint
     if (nch == 0) return;
     table_kernel<<<1, 1024, 0, s>>>(sec, tabs, st);
     count_launch();
-    // chunks of up to 32768 symbols are staged in shared memory; larger ones are read in place
-    const bool staged = chunk <= 32768;
-    const uint32_t warps = staged ? ransdec::warps_per_cta(chunk) : ransdec::kMaxWarps;
+    const uint32_t warps = ransdec::kMaxWarps;
     uint32_t blocks = (nch + warps - 1) / warps;
-    if (blocks > (uint32_t)num_sms * 8) blocks = (uint32_t)num_sms * 8;
-    const size_t smem = staged ? ransdec::smem_bytes(chunk, warps) : (size_t)ransdec::kTabWords * 4;
+    if (blocks > (uint32_t)num_sms * 4) blocks = (uint32_t)num_sms * 4;
+    const size_t smem = (size_t)ransdec::kTabWords * 4 + 4 * (size_t)kSmemChunks;
     cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    decode_kernel<<<blocks, 32 * warps, smem, s>>>(sec, sec_bytes, n, nch, chunk, out, st, staged, tabs);
+    decode_kernel<<<blocks, 32 * warps, smem, s>>>(sec, sec_bytes, n, nch, chunk, out, st, tabs);
     count_launch();
 }
 

@@ -15,17 +15,6 @@ constexpr uint32_t kM = 1u << kProbBits;
 constexpr uint32_t kL = 1u << 16;
 constexpr uint32_t kTabWords = kM / 4 + 256;  // slot -> symbol bytes, then freq << 16 | cum per symbol
 constexpr uint32_t kMaxWarps = 8;
-constexpr size_t kSmemBudget = 200 * 1024;
-
-// shared memory of a decoder CTA: tables, then one staging buffer per warp
-__host__ __device__ inline uint32_t stage_bytes(uint32_t chunk) { return (128u + 2u * chunk + 15u) & ~15u; }
-inline uint32_t warps_per_cta(uint32_t chunk)
-{
-    const size_t room = kSmemBudget - (size_t)kTabWords * 4;
-    const size_t w = room / stage_bytes(chunk);
-    return (uint32_t)(w < 1 ? 1 : (w > kMaxWarps ? kMaxWarps : w));
-}
-inline size_t smem_bytes(uint32_t chunk, uint32_t warps) { return (size_t)kTabWords * 4 + (size_t)warps * stage_bytes(chunk); }
 
 // whole CTA: copies the decoding tables (16-byte aligned, kTabWords words) into shared memory
 __device__ __forceinline__ void load_tables(uint32_t *dst, const uint32_t *tab)
@@ -33,19 +22,6 @@ __device__ __forceinline__ void load_tables(uint32_t *dst, const uint32_t *tab)
     const uint4 *s = reinterpret_cast<const uint4 *>(tab);
     uint4 *d = reinterpret_cast<uint4 *>(dst);
     for (uint32_t k = threadIdx.x; k < kTabWords / 4; k += blockDim.x) d[k] = s[k];
-}
-
-// one warp: asynchronous 4-byte copies of a chunk into its staging buffer
-__device__ __forceinline__ void stage_chunk(uint32_t *dst, const uint32_t *src, uint32_t nwords, uint32_t lane)
-{
-    __syncwarp();
-    for (uint32_t k = lane; k < nwords; k += 32) {
-        const uint32_t sa = (uint32_t)__cvta_generic_to_shared(dst + k);
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src + k));
-    }
-    asm volatile("cp.async.commit_group;\n" ::);
-    asm volatile("cp.async.wait_group 0;\n" ::);
-    __syncwarp();
 }
 
 // one warp: decodes len symbols of a chunk (states then W words at src) to out;
