@@ -1631,9 +1631,10 @@ gsnfs_status lod_from_voxels(gsnfs_ctx *ctx, cudaStream_t s, cudaStream_t cs, co
 }
 
 // ------------------------------------------------------- batched decoder ---
-// All frames of a batch are decoded by one sequence of launches: headers are
-// read with two host synchronisations for the whole batch, then every stage
-// runs over all frames at once (frame tables on the device).
+// All frames of a batch are decoded by one sequence of launches: the header
+// records are given (asynchronous decode) or read out of the streams by one
+// kernel and one host wait for the whole batch, then every stage runs over all
+// frames at once (frame tables on the device).
 gsnfs_status decode_batch_impl(gsnfs_ctx *ctx, cudaStream_t s, uint32_t F, const uint8_t *d_in, const uint64_t *offs,
                                float *d_pos, float *d_attr, uint64_t capacity_rows, uint64_t *rows_out,
                                const uint8_t *h_headers = nullptr, uint32_t *status = nullptr)

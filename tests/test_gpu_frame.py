@@ -208,3 +208,56 @@ def test_batched_decoder_equals_per_frame_decoding(G, orc):
         if a1 is not None and r1 > r0:
             assert np.array_equal(attr[r0:r1], a1.cpu().numpy())
         assert np.array_equal(pos[r0:r1], orc.decode_frame(b)["pos"])
+
+
+def test_batched_decoder_corrupt_streams_fail_cleanly(G, orc):
+    """The batched decoder reads every frame's header record out of the streams on the device: truncated
+    streams, a bad magic, a header size pointing past the stream and flipped bytes give an error or a valid
+    decode, never a fault, and the context decodes a good batch afterwards."""
+    frames = [syn.DynamicScene(21).frame(t, n=n) for t, n in enumerate([20_000, 7_000, 30_000])]
+    streams = []
+    for pos, attr in frames:
+        bs, *_ = G.encode_frame(_dev(pos), _dev(attr), 14, _qp(G, 56))
+        streams.append(bs.cpu().numpy())
+
+    def batch(parts):
+        offs = np.zeros(len(parts) + 1, np.uint64)
+        for i, b in enumerate(parts):
+            offs[i + 1] = offs[i] + ((b.size + 7) // 8) * 8
+        buf = np.zeros(max(int(offs[-1]), 8), np.uint8)
+        for i, b in enumerate(parts):
+            buf[int(offs[i]):int(offs[i]) + b.size] = b
+        bounds = np.array([int(o) for o in offs[:-1]] + [int(offs[-2]) + parts[-1].size], np.uint64)
+        return _dev(buf), bounds
+
+    cap = sum(p.shape[0] for p, _ in frames) + 8
+    bad_cases = []
+    for cut in (40, 96, 200, streams[1].size // 2):  # a truncated middle stream
+        bad_cases.append([streams[0], streams[1][:cut].copy(), streams[2]])
+    s = streams[1].copy()
+    s[0] ^= 0xFF  # magic
+    bad_cases.append([streams[0], s, streams[2]])
+    s = streams[2].copy()
+    s[8:12] = np.frombuffer(np.uint32(1 << 30).tobytes(), np.uint8)  # header size far past the stream
+    bad_cases.append([streams[0], streams[1], s])
+    for parts in bad_cases:
+        buf, bounds = batch(parts)
+        with pytest.raises(G.GsnfsError):
+            G.decode_batch(buf, bounds, 56, cap)
+    rng = np.random.default_rng(5)
+    for _ in range(12):  # flipped bytes past the fixed header: an error or a valid decode
+        parts = [x.copy() for x in streams]
+        f = int(rng.integers(0, 3))
+        k = int(rng.integers(96, parts[f].size))
+        parts[f][k] ^= np.uint8(1 << int(rng.integers(0, 8)))
+        buf, bounds = batch(parts)
+        try:
+            G.decode_batch(buf, bounds, 56, cap)
+        except G.GsnfsError:
+            pass
+    torch.cuda.synchronize()
+    buf, bounds = batch(streams)
+    pos, attr, rows = G.decode_batch(buf, bounds, 56, cap)
+    for i, b in enumerate(streams):
+        r0, r1 = int(rows[i]), int(rows[i + 1])
+        assert np.array_equal(pos[r0:r1].cpu().numpy(), orc.decode_frame(b)["pos"])
