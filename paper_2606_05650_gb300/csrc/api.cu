@@ -1533,7 +1533,6 @@ gsnfs_status lod_from_voxels(gsnfs_ctx *ctx, cudaStream_t s, cudaStream_t cs, co
     uint32_t *flags = nullptr, *pos0 = nullptr, *end0 = nullptr;
     uint64_t *offs = nullptr, *starts = nullptr, *part = nullptr;
     uint8_t *gap0 = nullptr;
-    float *rows = nullptr;
     auto carve = [&](Carve &cv) {
         flags = cv.take<uint32_t>(nv + 1);
         offs = cv.take<uint64_t>(nv + 2);
@@ -1542,7 +1541,6 @@ gsnfs_status lod_from_voxels(gsnfs_ctx *ctx, cudaStream_t s, cudaStream_t cs, co
         pos0 = cv.take<uint32_t>(nv + 1);
         end0 = cv.take<uint32_t>(nv + 1);
         gap0 = cv.take<uint8_t>(nv + 2);
-        rows = cv.take<float>(nv * (C ? C : 1) + 4);
         return cv.off;
     };
     Carve m(nullptr);
@@ -1599,7 +1597,8 @@ gsnfs_status lod_from_voxels(gsnfs_ctx *ctx, cudaStream_t s, cudaStream_t cs, co
         RahtIO io{};
         io.C = C;
         io.Y = L.Y;
-        io.out = rows;
+        io.out = lod.attr;  // node rows, divided by sqrt(voxel count) as they are stored: the means
+        io.lod_mean = 1;
         io.pool = L.pool;
         io.frame_shift = 64;
         if (P.color) {
@@ -1615,8 +1614,7 @@ gsnfs_status lod_from_voxels(gsnfs_ctx *ctx, cudaStream_t s, cudaStream_t cs, co
     LodGrid g;
     for (int a = 0; a < 3; ++a) g.lo[a] = P.lo[a];
     g.cell = P.ext / std::ldexp(1.0, (int)lod.depth);
-    launch_lod_means(rows, L.codes, starts, offs + nv, nn, sh, lod.depth, C, g, lod.pos, C ? lod.attr : nullptr, sms,
-                     s);
+    launch_lod_centres(L.codes, starts, offs + nv, nn, sh, lod.depth, g, lod.pos, sms, s);
     CK(cudaGetLastError());
     if (attrs) {  // the caller's stream sees all of it
         const gsnfs_status fst = fork_hi_end(ctx, cs);

@@ -169,6 +169,9 @@ struct RahtIOT {  // S = float (codec) or double (FP64 instantiation of the same
     const uint32_t *vstart;       // inverse: F + 1 voxel offsets (frame of a row)
     uint32_t F;
     YuvInv yuv_inv;
+    // inverse over a coarse first pass (plan pos0/end0: level of detail): each output row is divided by
+    // sqrt(its element's voxel count), a node's low pass becoming its voxels' mean (Eq. 1)
+    uint32_t lod_mean;
 };
 typedef RahtIOT<float> RahtIO;
 // FP64 transforms need a plan built with integer weights recorded (bf_w)
@@ -313,14 +316,12 @@ struct LodGrid {
 void launch_lod_index(const uint64_t *codes, uint64_t nv, uint32_t sh, uint32_t *flags, uint64_t *offs,
                       uint64_t *partials, uint64_t *starts, int num_sms, cudaStream_t s);
 // The nodes of a depth as the first pass of a coarser RAHT sequence (pos0, end0, gap0 of n_nodes + 1 entries), and
-// the node means from their low-pass coefficients after the coarse inverse (n_nodes: a bound for the launch
-// shape; the count itself is read on the device).
+// the nodes' cell centres (n_nodes: a bound for the launch shape; the count itself is read on the device).
 void launch_lod_sequence(const uint64_t *starts, const uint64_t *n_nodes_dev, uint64_t nv, uint64_t n_nodes,
                          const uint8_t *gap, uint32_t *pos0, uint32_t *end0, uint8_t *gap0, int num_sms,
                          cudaStream_t s);
-void launch_lod_means(const float *low, const uint64_t *codes, const uint64_t *starts, const uint64_t *n_nodes_dev,
-                      uint64_t n_nodes, uint32_t sh, uint32_t Jp, uint32_t C, const LodGrid &g, float *pos, float *out,
-                      int num_sms, cudaStream_t s);
+void launch_lod_centres(const uint64_t *codes, const uint64_t *starts, const uint64_t *n_nodes_dev, uint64_t n_nodes,
+                        uint32_t sh, uint32_t Jp, const LodGrid &g, float *pos, int num_sms, cudaStream_t s);
 
 // ---- render.cu: splat rasteriser ------------------------------------------------
 struct RenderCam {  // camera in FP64: the per-Gaussian projection is evaluated in FP64

@@ -4,7 +4,8 @@
 // carries the mean of its voxels' decoded attributes, which by Eq. (1) is
 // its RAHT low-pass coefficient divided by sqrt(voxel count).  The low-pass
 // coefficients come from an inverse RAHT over the node sequence (the
-// butterflies inside nodes are never applied).
+// butterflies inside nodes are never applied), which divides them as it
+// stores them; this file builds the node sequence and the node centres.
 #include "kernels.cuh"
 
 namespace gsnfs {
@@ -47,37 +48,6 @@ __global__ void lod_sequence_kernel(const uint64_t *__restrict__ starts, const u
     }
 }
 
-// block (channels, nodes): thread (c, k) divides node k's low-pass
-// coefficient of channel c from the coarse inverse by sqrt(voxel count) (Eq. 1:
-// the low pass of a node is sqrt(w) times the mean of its voxels).  No index
-// division: node rows are whole block rows; each thread takes four rows per
-// step with their loads issued first.
-constexpr uint32_t kMeanRows = 4;
-
-__global__ void lod_means_kernel(const float *__restrict__ low, const uint64_t *__restrict__ starts,
-                                 const uint64_t *__restrict__ n_nodes_dev, uint32_t C, float *out)
-{
-    const uint32_t c = threadIdx.x;
-    const uint64_t nn = *n_nodes_dev;
-    const uint64_t step = (uint64_t)gridDim.x * blockDim.y * kMeanRows;
-    for (uint64_t k0 = (uint64_t)blockIdx.x * blockDim.y * kMeanRows + threadIdx.y; k0 < nn; k0 += step) {
-        float lw[kMeanRows];
-        uint64_t w[kMeanRows];
-#pragma unroll
-        for (uint32_t u = 0; u < kMeanRows; ++u) {
-            const uint64_t k = k0 + (uint64_t)u * blockDim.y;
-            const bool ok = k < nn && c < C;
-            lw[u] = ok ? low[k * C + c] : 0.f;
-            w[u] = ok ? starts[k + 1] - starts[k] : 1;
-        }
-#pragma unroll
-        for (uint32_t u = 0; u < kMeanRows; ++u) {
-            const uint64_t k = k0 + (uint64_t)u * blockDim.y;
-            if (k < nn && c < C) out[k * C + c] = __fdiv_rn(lw[u], __fsqrt_rn((float)w[u]));
-        }
-    }
-}
-
 // thread per node: its cell centre at depth Jp (the same FP64 expression as a voxel centre at that depth)
 __global__ void lod_centres_kernel(const uint64_t *__restrict__ codes, const uint64_t *__restrict__ starts,
                                    const uint64_t *__restrict__ n_nodes_dev, uint32_t sh, uint32_t Jp, LodGrid g,
@@ -115,11 +85,6 @@ void launch_lod_index(const uint64_t *codes, uint64_t nv, uint32_t sh, uint32_t 
     count_launch();
 }
 
-
-}  // namespace gsnfs
-
-namespace gsnfs {
-
 void launch_lod_sequence(const uint64_t *starts, const uint64_t *n_nodes_dev, uint64_t nv, uint64_t n_nodes,
                          const uint8_t *gap, uint32_t *pos0, uint32_t *end0, uint8_t *gap0, int num_sms,
                          cudaStream_t s)
@@ -128,24 +93,12 @@ void launch_lod_sequence(const uint64_t *starts, const uint64_t *n_nodes_dev, ui
     count_launch();
 }
 
-void launch_lod_means(const float *low, const uint64_t *codes, const uint64_t *starts, const uint64_t *n_nodes_dev,
-                      uint64_t n_nodes, uint32_t sh, uint32_t Jp, uint32_t C, const LodGrid &g, float *pos, float *out,
-                      int num_sms, cudaStream_t s)
+void launch_lod_centres(const uint64_t *codes, const uint64_t *starts, const uint64_t *n_nodes_dev, uint64_t n_nodes,
+                        uint32_t sh, uint32_t Jp, const LodGrid &g, float *pos, int num_sms, cudaStream_t s)
 {
-    if (out && C) {
-        const uint32_t cw = C;                          // threads per node row
-        const uint32_t ny = cw >= 256 ? 1u : 256u / cw;  // node rows per block
-        uint64_t blocks = (n_nodes + ny * kMeanRows - 1) / (ny * kMeanRows);
-        const uint64_t cap = (uint64_t)num_sms * 16;
-        if (blocks > cap) blocks = cap;
-        if (blocks < 1) blocks = 1;
-        lod_means_kernel<<<(uint32_t)blocks, dim3(cw, ny), 0, s>>>(low, starts, n_nodes_dev, C, out);
-        count_launch();
-    }
-    if (pos) {
-        lod_centres_kernel<<<lod_grid(n_nodes, num_sms), 256, 0, s>>>(codes, starts, n_nodes_dev, sh, Jp, g, pos);
-        count_launch();
-    }
+    if (!pos) return;
+    lod_centres_kernel<<<lod_grid(n_nodes, num_sms), 256, 0, s>>>(codes, starts, n_nodes_dev, sh, Jp, g, pos);
+    count_launch();
 }
 
 }  // namespace gsnfs

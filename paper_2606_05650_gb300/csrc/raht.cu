@@ -611,6 +611,14 @@ __device__ inline XformSmem<S> carve_xform(unsigned char *raw, uint32_t T, uint3
     return X;
 }
 
+// level of detail: element j of the coarse first pass is a node of w voxels; its low pass over sqrt(w) is
+// the mean of its voxels (the same expression as a per-node division after the transform)
+template <typename S>
+__device__ __forceinline__ S lod_divisor(const RahtPlanDev &p, uint64_t j)
+{
+    return (S)__fsqrt_rn((float)(p.end0[j] - p.pos0[j]));
+}
+
 // butterfly k of a tile: FP32 coefficients come from the plan; FP64 ones are
 // computed here from the integer weights, a = sqrt(w0/(w0+w1)), b = sqrt(w1/(w0+w1))
 __device__ __forceinline__ void load_coeffs(const RahtPlanDev &p, uint64_t at, float *ab)
@@ -829,6 +837,12 @@ __device__ void xform_tile(const XformArgs<S> &A, const XformSmem<S> &X, TileSch
                     else
                         Vec<S, VEC>::st(io.Y + (uint64_t)d * C + c, v);
                 } else {
+                    if (q == 0 && io.lod_mean) {
+                        S *pv = reinterpret_cast<S *>(&v);
+                        const S dv = lod_divisor<S>(p, j);
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) pv[e] = div_rn(pv[e], dv);
+                    }
                     if (q == 0)
                         Vec<S, VEC>::st(io.out + j * C + c, v);
                     else
@@ -1156,6 +1170,10 @@ __device__ void pipe_compute(const XformArgs<float> &A, const RahtPass &ps, cons
                     V4::st(io.pool + ((uint64_t)nx.surv_off + (d & ~kCarry)) * C + c, v);
                 else
                     V4::st(io.Y + (uint64_t)d * C + c, v);
+            } else if (io.lod_mean) {
+                const float dv = lod_divisor<float>(A.p, j0 + i);
+                V4::st(io.out + (j0 + i) * C + c, make_float4(__fdiv_rn(v.x, dv), __fdiv_rn(v.y, dv),
+                                                              __fdiv_rn(v.z, dv), __fdiv_rn(v.w, dv)));
             } else {
                 V4::st(io.out + (j0 + i) * C + c, v);
             }
