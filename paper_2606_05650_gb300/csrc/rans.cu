@@ -126,7 +126,7 @@ __device__ __forceinline__ uint32_t frame_of(const uint64_t *off, uint32_t F, ui
 // Grid (x, frames): the CTAs of frame blockIdx.y share its coding tables in
 // shared memory (reciprocals computed once per CTA); each warp stages its
 // chunk's symbols in shared memory, 4,096 at a time.
-constexpr int kEncWarps = 8;
+constexpr int kEncWarps = 4;
 constexpr uint32_t kStageSyms = 4096;  // symbols staged per pass
 
 __global__ void __launch_bounds__(32 * kEncWarps) encode_kernel(const uint8_t *__restrict__ occ, const uint64_t *occ_off,
