@@ -45,11 +45,11 @@ def _record_from_stream(host, off, end, R):
     return r
 
 
-@pytest.mark.parametrize("rungs", [[1.0], [1.0, 4.0]])
-def test_async_decode_equals_sync_decode(G, rungs):
+@pytest.mark.parametrize("rungs,color", [([1.0], False), ([1.0, 4.0], False), ([1.0, 2.0], True)])
+def test_async_decode_equals_sync_decode(G, rungs, color):
     frames = _frames([30_000, 5_000, 1, 60_000, 0, 12_000])
     Js = [16, 12, 10, 17, 9, 14]
-    qp = G.QuantParams(syn.gs_channel_groups(), syn.GS_BASE_STEPS)
+    qp = G.QuantParams(syn.gs_channel_groups(), syn.GS_BASE_STEPS, color=color)
     out, offs, hdr = G.encode_batch([p for p, _ in frames], [a for _, a in frames], Js, rungs, qp, headers=True)
     out2, offs2 = G.encode_batch([p for p, _ in frames], [a for _, a in frames], Js, rungs, qp)
     assert np.array_equal(offs, offs2) and torch.equal(out[:int(offs[-1])], out2[:int(offs[-1])])

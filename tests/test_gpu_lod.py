@@ -21,10 +21,12 @@ def G():
     return gsnfs
 
 
-@pytest.mark.parametrize("J", [12, 16])
-def test_lod_matches_oracle(G, orc, J):
+@pytest.mark.parametrize("J,color", [(12, False), (16, False), (13, True)])
+def test_lod_matches_oracle(G, orc, J, color):
     pos, attr = syn.DynamicScene(60).frame(0, n=60_000)
-    qp = G.QuantParams(syn.gs_channel_groups(), syn.GS_BASE_STEPS)
+    if color:  # SH rows with correlated colour channels, coded with YUV + KLT
+        attr = syn.gs_attributes_correlated_sh(np.random.default_rng(61), pos.shape[0])
+    qp = G.QuantParams(syn.gs_channel_groups(), syn.GS_BASE_STEPS, color=color)
     bs, nv, _, _ = G.encode_frame(torch.from_numpy(pos).cuda(), torch.from_numpy(attr).cuda(), J, qp)
     host = bs.cpu().numpy()
     dec = orc.decode_frame(host)
