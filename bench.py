@@ -56,6 +56,12 @@ TRAFFIC = {
     "rlgr_encode": (277.95e6, "csrc/rlgr.cu", "4e2e1fc2ff5a6d4b5b09d83a4d1bd52db792c215"),
     "rlgr_decode": (253.00e6, "csrc/rlgr.cu", "4e2e1fc2ff5a6d4b5b09d83a4d1bd52db792c215"),
 }
+# warp instructions executed per frame (ncu smsp__inst_executed.sum on 2 frames of 1M Gaussians, halved) and the
+# source they were counted on: the RLGR coders are bound by instruction issue, not by DRAM
+INSTR = {
+    "rlgr_encode": (112873533, "csrc/rlgr.cu", "4e2e1fc2ff5a6d4b5b09d83a4d1bd52db792c215"),
+    "rlgr_decode": (116638655, "csrc/rlgr.cu", "4e2e1fc2ff5a6d4b5b09d83a4d1bd52db792c215"),
+}
 # largest share of serialised GPU time in the ncu launch list of the headline workload (16.2% of the timed steps)
 DOMINANT = "raht_forward_pass0"
 
@@ -335,7 +341,9 @@ def run_gpu(args):
     if rank == 0:
         peaks, src = measured_peaks()
         hbm = float(peaks["hbm_gbs"])
-        roof = roofline(stages, frames, nv_frames, stream_bytes, args.steps, F, hbm, src)
+        smax = ck.get("sm_max_mhz") or 2070.0
+        issue_peak = torch.cuda.get_device_properties(dev).multi_processor_count * 4 * float(smax) * 1e6
+        roof = roofline(stages, frames, nv_frames, stream_bytes, args.steps, F, hbm, src, issue_peak)
         res = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 3), "higher_is_better": True,
@@ -363,10 +371,11 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def measured_traffic(kernel, frames_per_launch):
-    """Per-launch DRAM traffic from the ncu capture, or None once the kernel's source changed."""
+def measured_traffic(kernel, frames_per_launch, table=None):
+    """Per-launch DRAM traffic (or warp instructions, from INSTR) from the ncu capture, or None once the kernel's
+    source changed."""
     import hashlib
-    ent = TRAFFIC.get(kernel)
+    ent = (TRAFFIC if table is None else table).get(kernel)
     if ent is None:
         return None
     per_frame, rel, sha = ent
@@ -380,8 +389,9 @@ def measured_traffic(kernel, frames_per_launch):
     return int(per_frame * frames_per_launch)
 
 
-def roofline(stages, frames, nv_frames, stream_bytes, steps, F, hbm, src):
-    """Dominant kernel of the step with its algorithmic bytes per launch."""
+def roofline(stages, frames, nv_frames, stream_bytes, steps, F, hbm, src, issue_peak=None):
+    """Dominant kernel of the step with its algorithmic bytes per launch; issue_peak (warp instructions per
+    second: SMs x 4 schedulers x maximum SM clock) adds the issue-rate fraction of the kernels in INSTR."""
     n_in = sum(p.shape[0] for p, _ in frames)
     nv = int(nv_frames.sum())
     comp = int(stream_bytes.sum())
@@ -418,10 +428,19 @@ def roofline(stages, frames, nv_frames, stream_bytes, steps, F, hbm, src):
             "frac": round(ach / hbm, 4), "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)",
             "traffic": measured_traffic(best, F / launches_per_step), "bytes_per_launch": int(bytes_per_launch),
             "avg_launch_ms": round(avg_ms, 4),
-            "all": {k: {"ms_per_launch": round(stages[k][0] / stages[k][1], 4),
-                        "GBs": round(alg[k] / (stages[k][1] / steps) / (stages[k][0] / stages[k][1] / 1e3) / 1e9, 1),
-                        "frac": round(alg[k] / (stages[k][1] / steps) / (stages[k][0] / stages[k][1] / 1e3) / 1e9 / hbm, 4)}
-                    for k in alg if stages.get(k, (0, 0))[1]}}
+            "all": {k: per_kernel(k, stages, alg, steps, F, hbm, issue_peak) for k in alg if stages.get(k, (0, 0))[1]}}
+
+
+def per_kernel(k, stages, alg, steps, F, hbm, issue_peak):
+    ms = stages[k][0] / stages[k][1]
+    per_step = stages[k][1] / steps
+    gbs = alg[k] / per_step / (ms / 1e3) / 1e9
+    ent = {"ms_per_launch": round(ms, 4), "GBs": round(gbs, 1), "frac": round(gbs / hbm, 4)}
+    inst = measured_traffic(k, F / per_step, INSTR)
+    if inst is not None and issue_peak:
+        ent["issue"] = {"warp_inst_per_launch": inst, "warp_inst_per_s": round(inst / (ms / 1e3) / 1e12, 4),
+                        "unit": "T/s", "peak": round(issue_peak / 1e12, 4), "frac": round(inst / (ms / 1e3) / issue_peak, 4)}
+    return ent
 
 
 def gpu_extras(args, G, torch, P, A, frames, qp, out, offs, dev, stream):

@@ -77,3 +77,24 @@ def test_host_cpu_description():
     h = bench.host_cpu()
     assert h["nproc"] >= 1
     assert "model" not in h or isinstance(h["model"], str)
+
+
+def test_issue_rate_entry_for_instruction_bound_coders():
+    F, n, steps = 16, 1000, 4
+    nv = np.full(F, n)
+    sb = np.full(F, 50_000)
+    stages = {"raht_forward_pass0": (8.0, steps), "rlgr_encode": (7.2, steps)}
+    peak = 152 * 4 * 2070e6
+    r = bench.roofline(stages, _frames(F, n), nv, sb, steps, F, 6000.0, "measured", peak)
+    enc = r["all"]["rlgr_encode"]
+    inst = bench.measured_traffic("rlgr_encode", F, bench.INSTR)
+    if inst is None:  # counts withdrawn after a source change
+        assert "issue" not in enc
+        return
+    assert inst == int(bench.INSTR["rlgr_encode"][0] * F)
+    ms = 7.2 / steps
+    assert np.isclose(enc["issue"]["frac"], inst / (ms / 1e3) / peak, atol=1e-4)
+    assert "issue" not in r["all"]["raht_forward_pass0"]
+    # no peak given: no issue entry
+    r0 = bench.roofline(stages, _frames(F, n), nv, sb, steps, F, 6000.0, "measured")
+    assert "issue" not in r0["all"]["rlgr_encode"]
