@@ -599,7 +599,8 @@ def gpu_extras(args, G, torch, P, A, frames, qp, out, offs, dev, stream):
     for _ in range(K2):
         n, m = e2e_step()
     dt_serial = (time.perf_counter() - t0) / K2
-    K3 = max(6, min(args.steps, 32))  # enough steps that filling and draining the pipeline is a small part
+    K3 = max(6, min(args.steps, 96))  # as many steps as the headline loop: filling and draining the pipeline
+    # (about two steps) is then a small part
     dt, n, m, timeline = e2e_streamed(G, torch, dev, qp, F, hp, ha, dp, da, out, pos1, att1, hout, hpos, hatt, K3)
     h2d = sum(x.numel() * 4 for x in hp + ha)
     d2h = n + m * (3 + C) * 4
