@@ -359,6 +359,7 @@ def run_gpu(args):
             "roofline": roof,
             "pipeline_fraction": round(pipeline_fraction(value, N_GAUSS, roof["peak"]), 4) if roof else None,
             "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in stages.items() if v[1]},
+            "stages_roofline": stage_roofline(stages, sum(p.shape[0] for p, _ in frames), args.steps, hbm, C, J),
             "gpu_launches": int(launches),
             "clocks": ck,
         }
@@ -429,6 +430,42 @@ def roofline(stages, frames, nv_frames, stream_bytes, steps, F, hbm, src, issue_
             "traffic": measured_traffic(best, F / launches_per_step), "bytes_per_launch": int(bytes_per_launch),
             "avg_launch_ms": round(avg_ms, 4),
             "all": {k: per_kernel(k, stages, alg, steps, F, hbm, issue_peak) for k in alg if stages.get(k, (0, 0))[1]}}
+
+
+# Algorithmic bytes per Gaussian of each timed stage (the compulsory reads and writes of the stage at C channels
+# of 4 bytes), and whether the stage runs on one of the two concurrent branches of a call, where its event time
+# includes the other branch's use of the SMs (a lower bound on the stage's own rate).
+def stage_bytes(C, J):
+    passes = (3 * J + 7) // 8
+    return {
+        "voxelize": (36, False),             # positions read twice (box, codes), codes and indices written
+        "sort": (24 * passes, False),        # per 8-bit digit pass: 12-byte pairs read and written
+        "dedup": (29, False),                # sorted codes read; voxel codes, first rows, segments written
+        "occupancy": (16, True),             # codes and gap levels read, occupancy bytes written
+        "rans": (9.5, True),                 # occupancy bytes read, compressed occupancy written
+        "raht_prelude": (48, True),          # encoder and decoder schedules, 24 bytes each
+        "raht_forward": (8 * C, True),       # rows gathered and coefficient rows written
+        "rlgr_encode": (4 * C + 32, True),   # coefficients read, attribute payload written
+        "container": (66, False),            # both sections read and written once
+        "occupancy_decode": (9.5, True),     # compressed occupancy read, occupancy bytes written
+        "octree_decode": (131, True),        # levels of nodes and the voxel centres
+        "rlgr_decode": (32 + 4 * C, True),   # payload read, dequantised coefficients written
+        "raht_inverse": (8 * C, True),       # coefficient rows read, attribute rows written
+    }
+
+
+def stage_roofline(stages, n_gauss, steps, hbm, C, J):
+    """Per-stage algorithmic GB/s and fraction of the HBM peak from the stages' event times."""
+    out = {}
+    for k, (per, conc) in stage_bytes(C, J).items():
+        ms, cnt = stages.get(k, (0.0, 0))
+        if not cnt or ms <= 0:
+            continue
+        b = per * n_gauss
+        gbs = b / (ms / steps / 1e3) / 1e9
+        out[k] = {"ms_per_step": round(ms / steps, 4), "bytes_per_step": int(b), "GBs": round(gbs, 1),
+                  "frac": round(gbs / hbm, 4), "branch": "concurrent" if conc else "serial"}
+    return out
 
 
 def per_kernel(k, stages, alg, steps, F, hbm, issue_peak):

@@ -98,3 +98,15 @@ def test_issue_rate_entry_for_instruction_bound_coders():
     # no peak given: no issue entry
     r0 = bench.roofline(stages, _frames(F, n), nv, sb, steps, F, 6000.0, "measured")
     assert "issue" not in r0["all"]["rlgr_encode"]
+
+
+def test_stage_roofline_uses_the_per_gaussian_bytes():
+    steps, n = 4, 16_000_000
+    stages = {"sort": (4 * 1.2, steps), "occupancy": (4 * 0.8, steps), "reconstruction": (0.01, steps)}
+    r = bench.stage_roofline(stages, n, steps, 6000.0, 56, 16)
+    assert set(r) == {"sort", "occupancy"}  # stages without algorithmic bytes are left out
+    assert r["sort"]["bytes_per_step"] == 24 * 6 * n  # six 8-bit passes over 48 code bits
+    assert np.isclose(r["sort"]["GBs"], round(24 * 6 * n / 1.2e-3 / 1e9, 1))
+    assert np.isclose(r["sort"]["frac"], round(r["sort"]["GBs"] / 6000.0, 4), atol=1e-4)
+    assert r["sort"]["branch"] == "serial" and r["occupancy"]["branch"] == "concurrent"
+    assert bench.stage_bytes(56, 16)["raht_forward"][0] == 448
