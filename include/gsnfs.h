@@ -142,9 +142,13 @@ gsnfs_status gsnfs_encode_frame(gsnfs_ctx *ctx, void *stream, const float *d_pos
                                 uint64_t capacity, uint64_t *out_bytes, float *d_recon_pos,
                                 float *d_recon_attr, uint64_t *out_nv);
 
-/* Reads the fixed header of a stream held in HOST memory (>= 96 bytes):
- * number of voxels, channels and depth. */
-gsnfs_status gsnfs_peek_frame(const uint8_t *h_header, uint64_t bytes, uint64_t *out_nv, uint32_t *out_C,
+/* Reads the fixed header of a stream (>= 96 bytes): number of voxels,
+ * channels and depth.  `header` may point to host memory (pageable, pinned
+ * or managed) or to device memory; from device memory the first 96 bytes
+ * are copied to the host first (a synchronous copy: call it outside stream
+ * capture).  Returns GSNFS_ERR_CORRUPT for fewer than 96 bytes or a bad
+ * magic, version or depth, GSNFS_ERR_CUDA if that copy fails. */
+gsnfs_status gsnfs_peek_frame(const uint8_t *header, uint64_t bytes, uint64_t *out_nv, uint32_t *out_C,
                               uint32_t *out_J);
 
 /* Decodes one frame (Sec. 2.3, Algorithms 2-3; inverse of Algorithm 6):

@@ -2228,12 +2228,27 @@ gsnfs_status gsnfs_encode_batch_rd(gsnfs_ctx *ctx, void *stream, uint32_t frames
                              h_offsets, h_sq_err);
 }
 
-gsnfs_status gsnfs_peek_frame(const uint8_t *h_header, uint64_t bytes, uint64_t *out_nv, uint32_t *out_C,
+gsnfs_status gsnfs_peek_frame(const uint8_t *header, uint64_t bytes, uint64_t *out_nv, uint32_t *out_C,
                               uint32_t *out_J)
 {
-    if (!h_header) return GSNFS_ERR_INVALID_ARG;
+    if (!header) return GSNFS_ERR_INVALID_ARG;
+    if (bytes < 96) return GSNFS_ERR_CORRUPT;
+    // device memory: its first 96 bytes are copied to the host; host, pinned and managed memory are read in place
+    // (a pointer the runtime does not know, or no device at all, counts as host memory)
+    cudaPointerAttributes pa{};
+    const bool on_device = cudaPointerGetAttributes(&pa, header) == cudaSuccess && pa.type == cudaMemoryTypeDevice;
+    (void)cudaGetLastError();
+    uint8_t copy[96];
+    const uint8_t *h_header = header;
+    if (on_device) {
+        if (cudaMemcpy(copy, header, sizeof copy, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return GSNFS_ERR_CUDA;
+        }
+        h_header = copy;
+    }
     ParsedHeader P{};
-    if (bytes < 96 || rd32(h_header) != kMagic || rd32(h_header + 4) != 1) return GSNFS_ERR_CORRUPT;
+    if (rd32(h_header) != kMagic || rd32(h_header + 4) != 1) return GSNFS_ERR_CORRUPT;
     P.J = rd32(h_header + 12);
     P.C = rd32(h_header + 16);
     P.nv = rd64(h_header + 24);

@@ -229,12 +229,18 @@ def encode_frame(pos: torch.Tensor, attr, J: int, qp: QuantParams, recon=False, 
             ra[:m, :C] if ra is not None else None)
 
 
-def peek_frame(header: bytes | np.ndarray):
-    h = np.frombuffer(bytes(header), dtype=np.uint8) if not isinstance(header, np.ndarray) else header
-    h = np.ascontiguousarray(h, dtype=np.uint8)
+def peek_frame(header):
+    """gsnfs_peek_frame on host bytes, a numpy array or a uint8 tensor (host or CUDA).  Returns (N_v, C, J)."""
     nv, C, J = ct.c_uint64(), ct.c_uint32(), ct.c_uint32()
-    _check(lib().gsnfs_peek_frame(h.ctypes.data_as(ct.c_void_p), h.shape[0], ct.byref(nv), ct.byref(C), ct.byref(J)),
-           "gsnfs_peek_frame")
+    if isinstance(header, torch.Tensor):
+        if header.dtype != torch.uint8 or not header.is_contiguous():
+            raise ValueError("header must be a contiguous uint8 tensor")
+        ptr, n = ct.c_void_p(header.data_ptr()), header.numel()
+    else:
+        h = np.frombuffer(bytes(header), dtype=np.uint8) if not isinstance(header, np.ndarray) else header
+        h = np.ascontiguousarray(h, dtype=np.uint8)
+        ptr, n = h.ctypes.data_as(ct.c_void_p), h.shape[0]
+    _check(lib().gsnfs_peek_frame(ptr, n, ct.byref(nv), ct.byref(C), ct.byref(J)), "gsnfs_peek_frame")
     return nv.value, C.value, J.value
 
 

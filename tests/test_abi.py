@@ -64,3 +64,17 @@ def test_host_side_bounds_and_validation(libpath):
         gsnfs.max_bitstream_bytes(10, 22, qp)  # J > 21
     with pytest.raises(gsnfs.GsnfsError):
         gsnfs.peek_frame(bytes(96))  # no magic
+    # a hand-built header in host memory: magic "GSN1", version 1, J at byte 12, C at 16, N_v at 24
+    import struct
+    h = bytearray(96)
+    struct.pack_into("<II", h, 0, 0x314E5347, 1)
+    struct.pack_into("<II", h, 12, 16, 56)
+    struct.pack_into("<Q", h, 24, 999_999)
+    assert gsnfs.peek_frame(bytes(h)) == (999_999, 56, 16)
+    import torch
+    assert gsnfs.peek_frame(torch.frombuffer(bytearray(h), dtype=torch.uint8)) == (999_999, 56, 16)
+    with pytest.raises(gsnfs.GsnfsError):
+        gsnfs.peek_frame(bytes(h[:95]))  # fewer than 96 bytes
+    struct.pack_into("<I", h, 12, 22)  # J beyond 21
+    with pytest.raises(gsnfs.GsnfsError):
+        gsnfs.peek_frame(bytes(h))

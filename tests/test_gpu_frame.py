@@ -261,3 +261,23 @@ def test_batched_decoder_corrupt_streams_fail_cleanly(G, orc):
     for i, b in enumerate(streams):
         r0, r1 = int(rows[i]), int(rows[i + 1])
         assert np.array_equal(pos[r0:r1].cpu().numpy(), orc.decode_frame(b)["pos"])
+
+
+def test_peek_reads_host_and_device_headers(G, orc):
+    """gsnfs_peek_frame takes the header in device memory as well as in host memory, and agrees with the
+    oracle's decoding of the same stream."""
+    qp = _qp(G, 56)
+    p, a = syn.DynamicScene(7).frame(0, n=20_000)
+    bs, nv, _, _ = G.encode_frame(_dev(p), _dev(a), 14, qp)
+    want = (nv, 56, 14)
+    assert G.peek_frame(bs) == want  # device tensor
+    assert G.peek_frame(bs[:96].contiguous()) == want
+    assert G.peek_frame(bs.cpu()) == want  # host tensor
+    assert G.peek_frame(bs.cpu().numpy()) == want
+    assert orc.decode_frame(bs.cpu().numpy())["pos"].shape[0] == nv
+    with pytest.raises(G.GsnfsError):
+        G.peek_frame(bs[:95].contiguous())  # fewer than 96 bytes
+    bad = bs[:96].clone()
+    bad[0] ^= 0xFF  # magic
+    with pytest.raises(G.GsnfsError):
+        G.peek_frame(bad)
