@@ -93,7 +93,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) downsweep_kernel(const u
 {
     __shared__ uint32_t s_base[kRadix];
     __shared__ uint32_t s_wcnt[kWarps][kRadix];
-    __shared__ uint32_t s_tcnt[kRadix];
     __shared__ uint32_t s_toff[kRadix];
     __shared__ uint64_t s_keys[kTile];
     __shared__ uint32_t s_vals[kTile];
@@ -116,9 +115,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) downsweep_kernel(const u
     uint64_t cb, ce;
     cta_range(cta_lo, chunk, n, cb, ce);
     const uint32_t ltmask = lanemask_lt();
+    // Five barriers per tile.  Thread t owns digit t's column of the warp counters and digit t's output base:
+    // it zeroes the column once the tile's ranks are placed (the write-out does not read the counters) and
+    // advances the base after the write-out, so neither needs a barrier or a pass of its own.
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) s_wcnt[ww][tid] = 0;
+    __syncthreads();
     for (uint64_t t0 = cb; t0 < ce; t0 += kTile) {
-        for (int i = tid; i < kWarps * kRadix; i += kThreads) (&s_wcnt[0][0])[i] = 0;
-        __syncthreads();
         uint64_t k[kKeysPerThread];
         uint32_t v[kKeysPerThread], rk[kKeysPerThread];
         uint32_t dg[kKeysPerThread];
@@ -139,18 +142,21 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) downsweep_kernel(const u
             __syncwarp();
         }
         __syncthreads();
-        {  // per digit: exclusive prefix over warps, tile totals
-            uint32_t run = 0;
+        // per digit: exclusive prefix over warps, then the tile's exclusive prefix over digits
+        uint32_t run = 0;
 #pragma unroll
-            for (int ww = 0; ww < kWarps; ++ww) {
-                uint32_t c = s_wcnt[ww][tid];
-                s_wcnt[ww][tid] = run;
-                run += c;
-            }
-            s_tcnt[tid] = run;
-            uint32_t tot;
-            s_toff[tid] = block_exclusive_sum<uint32_t>(run, s_scan, &tot);
+        for (int ww = 0; ww < kWarps; ++ww) {
+            uint32_t c = s_wcnt[ww][tid];
+            s_wcnt[ww][tid] = run;
+            run += c;
         }
+        const uint32_t inc = warp_inclusive_sum(run);
+        if (lane == 31) s_scan[w] = inc;
+        __syncthreads();
+        uint32_t woff = 0;
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww) woff += ww < w ? s_scan[ww] : 0u;
+        s_toff[tid] = woff + inc - run;
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < kKeysPerThread; ++r) {
@@ -161,6 +167,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) downsweep_kernel(const u
             }
         }
         __syncthreads();
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww) s_wcnt[ww][tid] = 0;
         uint32_t cnt = (uint32_t)((ce - t0) < (uint64_t)kTile ? (ce - t0) : (uint64_t)kTile);
         for (uint32_t slot = tid; slot < cnt; slot += kThreads) {
             uint64_t key = s_keys[slot];
@@ -170,8 +178,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) downsweep_kernel(const u
             vals_out[op] = s_vals[slot];
         }
         __syncthreads();
-        s_base[tid] += s_tcnt[tid];
-        __syncthreads();
+        s_base[tid] += run;  // read again only after the next tile's barriers
     }
 }
 
