@@ -502,18 +502,19 @@ def gpu_extras(args, G, torch, P, A, frames, qp, out, offs, dev, stream):
     # plain path, one frame per call
     enc_ms, dec_ms = [], []
     buf = torch.empty(G.max_bitstream_bytes(N_GAUSS, J, qp), dtype=torch.uint8, device=dev)
-    for rep in range(2):
-        for f in range(F):
-            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            a.record(stream)
-            bs, nv, _, _ = G.encode_frame(P[f], A[f], J, qp, out=buf)
-            b.record(stream)
-            G.decode_frame(bs)
-            c.record(stream)
-            torch.cuda.synchronize()
-            if rep:
-                enc_ms.append(a.elapsed_time(b))
-                dec_ms.append(b.elapsed_time(c))
+    with _no_gc():
+        for rep in range(2):
+            for f in range(F):
+                a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                a.record(stream)
+                bs, nv, _, _ = G.encode_frame(P[f], A[f], J, qp, out=buf)
+                b.record(stream)
+                G.decode_frame(bs)
+                c.record(stream)
+                torch.cuda.synchronize()
+                if rep:
+                    enc_ms.append(a.elapsed_time(b))
+                    dec_ms.append(b.elapsed_time(c))
     q = lambda v, p: float(np.percentile(v, p))
     res["plain"] = {"encode_fps": round(1e3 / statistics.mean(enc_ms), 2),
                     "decode_fps": round(1e3 / statistics.mean(dec_ms), 2),
@@ -851,18 +852,19 @@ def sequence_leg(G, torch, dev, stream, frames, block):
     nmax = max(int(p.shape[0]) for p in P)
     buf = torch.empty(G.max_bitstream_bytes(nmax, J, qp), dtype=torch.uint8, device=dev)
     enc, dec = [], []
-    for rep in range(2):
-        for f in range(F):
-            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            a.record(stream)
-            bs, nv, _, _ = G.encode_frame(P[f], A[f], J, qp, out=buf)
-            b.record(stream)
-            G.decode_frame(bs)
-            c.record(stream)
-            torch.cuda.synchronize()
-            if rep:
-                enc.append(a.elapsed_time(b))
-                dec.append(b.elapsed_time(c))
+    with _no_gc():
+        for rep in range(2):
+            for f in range(F):
+                a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                a.record(stream)
+                bs, nv, _, _ = G.encode_frame(P[f], A[f], J, qp, out=buf)
+                b.record(stream)
+                G.decode_frame(bs)
+                c.record(stream)
+                torch.cuda.synchronize()
+                if rep:
+                    enc.append(a.elapsed_time(b))
+                    dec.append(b.elapsed_time(c))
     n_tot = sum(int(p.shape[0]) for p in P)
     st = {"out": None}
 
@@ -1120,6 +1122,23 @@ def run_ladder(args):
     print(json.dumps(line), flush=True)
 
 
+class _no_gc:
+    """Per-call latency legs run with Python's garbage collector collected beforehand and paused: a collection
+    inside a timed call (the events bracket the host's enqueue and its wait) would be charged to the codec."""
+
+    def __enter__(self):
+        import gc
+        gc.collect()
+        self.was = gc.isenabled()
+        gc.disable()
+
+    def __exit__(self, *exc):
+        import gc
+        if self.was:
+            gc.enable()
+        return False
+
+
 def _timed_calls(torch, stream, fn, reps):
     """Per-call device times (ms) of fn() on the stream, after one warm-up call."""
     fn()
@@ -1184,13 +1203,14 @@ def run_sequence(args, pointcloud=False):
     legs = []
     for qi, qp in enumerate(qps):
         enc, dec, sizes = [], [], []
-        for t in range(Fn):
-            def e(_=0):
-                return G.encode_frame(P[t], A[t], Jd, qp, out=buf)
-            enc += _timed_calls(torch, stream, e, 1)
-            bs, nv, _, _ = e()
-            sizes.append(int(bs.numel()))
-            dec += _timed_calls(torch, stream, lambda _=0: G.decode_frame(bs), 1)
+        with _no_gc():
+            for t in range(Fn):
+                def e(_=0):
+                    return G.encode_frame(P[t], A[t], Jd, qp, out=buf)
+                enc += _timed_calls(torch, stream, e, 1)
+                bs, nv, _, _ = e()
+                sizes.append(int(bs.numel()))
+                dec += _timed_calls(torch, stream, lambda _=0: G.decode_frame(bs), 1)
         leg = {"step_set": qi, "encode_ms_p50": round(float(np.percentile(enc, 50)), 3),
                "encode_ms_p99": round(float(np.percentile(enc, 99)), 3),
                "decode_ms_p50": round(float(np.percentile(dec, 50)), 3),

@@ -110,3 +110,11 @@ def test_stage_roofline_uses_the_per_gaussian_bytes():
     assert np.isclose(r["sort"]["frac"], round(r["sort"]["GBs"] / 6000.0, 4), atol=1e-4)
     assert r["sort"]["branch"] == "serial" and r["occupancy"]["branch"] == "concurrent"
     assert bench.stage_bytes(56, 16)["raht_forward"][0] == 448
+
+
+def test_latency_legs_pause_the_garbage_collector():
+    import gc
+    was = gc.isenabled()
+    with bench._no_gc():
+        assert not gc.isenabled()
+    assert gc.isenabled() == was
