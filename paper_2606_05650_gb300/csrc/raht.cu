@@ -1216,9 +1216,12 @@ __global__ void __launch_bounds__(kXThreads, NR == 1 ? 3 : 1) xform_pipe_kernel(
         for (uint32_t k = 0;; ++k) {
             const uint32_t tk = s_claim[k & 3];
             if (tk >= nt) break;
-            // complete: rows of tile k, metadata of tile k + 1
+            // complete: rows of tile k, metadata of tile k + 1.  Without colour transforms no barrier is needed
+            // here: a thread first touches only the row chunks it copied itself (same thread-to-chunk mapping
+            // for the copy and the finishing step, complete for it after its own wait), tile k's metadata became
+            // visible at the previous tile's first barrier, and the barrier before the rounds orders the rest.
             cp_async_wait<0>();
-            __syncthreads();
+            if (A.io.klt) __syncthreads();  // the colour steps read other threads' rows
             pipe_compute<INV, GATHER, QDQ>(A, ps, nx, tk, meta(k), rows(k), klt_s, klt_fr);
             if (threadIdx.x == 0) s_claim[(k + 2) & 3] = atomicAdd(A.p.pipe_ctr, 1u);
             __syncthreads();  // the row buffer and tile k's metadata are free; the new claim is visible
