@@ -62,7 +62,7 @@ INSTR = {
     "rlgr_encode": (112873533, "csrc/rlgr.cu", "4e2e1fc2ff5a6d4b5b09d83a4d1bd52db792c215"),
     "rlgr_decode": (116638655, "csrc/rlgr.cu", "4e2e1fc2ff5a6d4b5b09d83a4d1bd52db792c215"),
 }
-# largest share of serialised GPU time in the ncu launch list of the headline workload (16.1% of the timed steps)
+# largest share of serialised GPU time in the ncu launch list of the headline workload (16.0% of the timed steps)
 DOMINANT = "raht_forward_pass0"
 
 
