@@ -2236,8 +2236,9 @@ gsnfs_status gsnfs_peek_frame(const uint8_t *header, uint64_t bytes, uint64_t *o
     // device memory: its first 96 bytes are copied to the host; host, pinned and managed memory are read in place
     // (a pointer the runtime does not know, or no device at all, counts as host memory)
     cudaPointerAttributes pa{};
-    const bool on_device = cudaPointerGetAttributes(&pa, header) == cudaSuccess && pa.type == cudaMemoryTypeDevice;
-    (void)cudaGetLastError();
+    const cudaError_t pe = cudaPointerGetAttributes(&pa, header);
+    if (pe != cudaSuccess) (void)cudaGetLastError();  // clear only the error this query set
+    const bool on_device = pe == cudaSuccess && pa.type == cudaMemoryTypeDevice;
     uint8_t copy[96];
     const uint8_t *h_header = header;
     if (on_device) {
